@@ -1,0 +1,88 @@
+"""Seeded synthetic workloads (inputs only; no arithmetic of the method lives here).
+
+Each generator returns plain numpy arrays and a dict of problem parameters.  The shapes and
+distributions follow the paper's validation and scaling workloads (Sec. IV: single blobs and
+pairs near walls; Sec. V.A: a dense sedimented layer of microrollers near one wall), replaced
+by seeded random draws because the paper's configurations are not available:
+
+* ``bw_small``    - N = 100 above one wall, box 64 x 64, z in [0, 12], heights U[1.5, 10],
+                    forces N(0,1), no torques; grid 128^2 x 65, m = 6, beta = 10.2 (FP64 case).
+* ``slit_16k``    - N = 16384 in a slit z in [0, 20], box 256^2, heights U[1.2, 18.8], forces
+                    and torques N(0,1); grid 384^2 x 97, h = 2/3, m = 5 with Table I betas.
+* ``rollers_1m``  - N = 2^20 microrollers above one wall, box 2048^2, z in [0, 8], heights
+                    max(|N(1.6, 0.3)|, 1.05), force (0, 0, -1) (gravity) and torque (0, 1, 0)
+                    on every particle; grid 3072^2 x 65, h = 2/3, m = 5 with Table I betas.
+
+Seeds are 20221004 + the workload's index (1, 2, 3).
+"""
+
+import numpy as np
+
+SEED_BASE = 20221004
+
+# Table I of the paper (force and torque, m = 5): R_h/h, beta_M/m, beta_D/m
+_T1_M5 = (1.560, 1.305, 2.232)
+
+
+def _uniform_xy(rng, n, L):
+    return rng.uniform(0.0, L, n), rng.uniform(0.0, L, n)
+
+
+def bw_small(n=100, seed_offset=1):
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    L = 64.0
+    x, y = _uniform_xy(rng, n, L)
+    z = rng.uniform(1.5, 10.0, n)
+    pos = np.stack([x, y, z], axis=1)
+    F = rng.standard_normal((n, 3))
+    params = dict(Lx=L, Ly=L, zmin=0.0, zmax=12.0, mode="bottom_wall", nx=128, ny=128, nz=65,
+                  m_M=6, beta_M=10.2, m_D=0, beta_D=0.0, eta=1.0)
+    return params, pos, F, None
+
+
+def slit_16k(n=16384, seed_offset=2, nxy=384, L=256.0, nz=97):
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    x, y = _uniform_xy(rng, n, L)
+    z = rng.uniform(1.2, 18.8, n)
+    pos = np.stack([x, y, z], axis=1)
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3))
+    m = 5
+    params = dict(Lx=L, Ly=L, zmin=0.0, zmax=20.0, mode="slit", nx=nxy, ny=nxy, nz=nz,
+                  m_M=m, beta_M=m * _T1_M5[1], m_D=m, beta_D=m * _T1_M5[2], eta=1.0)
+    return params, pos, F, T
+
+
+def rollers_1m(n=1 << 20, seed_offset=3, nxy=3072, L=2048.0):
+    """Sedimented roller layer.  Smaller n/nxy/L give the same layer at reduced size (density
+    n/L^2 and h = L/nxy are kept by the callers that shrink it)."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    x, y = _uniform_xy(rng, n, L)
+    z = np.maximum(np.abs(rng.normal(1.6, 0.3, n)), 1.05)
+    pos = np.stack([x, y, z], axis=1)
+    F = np.zeros((n, 3))
+    F[:, 2] = -1.0
+    T = np.zeros((n, 3))
+    T[:, 1] = 1.0
+    m = 5
+    params = dict(Lx=L, Ly=L, zmin=0.0, zmax=8.0, mode="bottom_wall", nx=nxy, ny=nxy, nz=65,
+                  m_M=m, beta_M=m * _T1_M5[1], m_D=m, beta_D=m * _T1_M5[2], eta=1.0)
+    return params, pos, F, T
+
+
+def random_particles(params, n, seed, torques=True, margin=None):
+    """Uniform random particles inside a given box, heights kept where the envelope is legal
+    for the wall mode (at least alpha from an open boundary).  Forces/torques N(0,1)."""
+    rng = np.random.default_rng(seed)
+    h = params["Lx"] / params["nx"]
+    a = 0.5 * max(params["m_M"], params.get("m_D", 0) or 0) * h
+    zlo, zhi = params["zmin"], params["zmax"]
+    if margin is None:
+        margin = 0.0
+    lo = zlo + (a if params["mode"] == "free" else 0.0) + margin
+    hi = zhi - (a if params["mode"] in ("free", "bottom_wall") else 0.0) - margin
+    pos = np.stack([rng.uniform(0, params["Lx"], n), rng.uniform(0, params["Ly"], n),
+                    rng.uniform(lo, hi, n)], axis=1)
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3)) if torques else None
+    return pos, F, T

@@ -1,0 +1,206 @@
+"""Pins for the full oracle mobility product against physics and exact discrete properties.
+
+* Self mobility above one wall vs the Rotne-Prager-Blake closed forms (Sec. IV.A; the paper
+  reports agreement for z >~ 2 R_h) and the classical leading wall corrections for rotation.
+* Exact discrete invariances: xy translation by whole cells or periods, x-mirror, slit midplane
+  reflection; linearity; a particle on a wall is immobile (Eq. 9).
+* Symmetry (to the z-discretisation accuracy; Sec. IV.A reports five digits at its resolution)
+  and positive definiteness (Sec. I) of the grand
+  mobility (Eq. 58) built column by column on tiny N.
+* Spreading and interpolation are adjoint under the quadrature inner product.
+* Spectral convergence in Nz.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import Params, mobility, table1, table2
+from oracle import cheb
+from oracle.transfer import interpolate, spread
+
+
+def _rpb_parallel(a_over_z):
+    x = a_over_z
+    return 1 - 9 / 16 * x + 1 / 8 * x**3 - 1 / 16 * x**5
+
+
+def _rpb_perpendicular(a_over_z):
+    x = a_over_z
+    return 1 - 9 / 8 * x + 1 / 2 * x**3 - 1 / 8 * x**5
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("zr", [2.0, 3.0, 4.0])
+def test_self_translation_vs_rotne_prager_blake(zr):
+    rh_h, bm = table2(6)
+    p = Params(Lx=160.0, Ly=160.0, zmin=0.0, zmax=16.0, mode="bottom_wall", nx=160, ny=160, nz=33,
+               m_M=6, beta_M=6 * bm)
+    Rh = rh_h * p.h
+    pos = np.array([[80.3, 80.7, zr * Rh]])
+    Ux, _ = mobility(p, pos, np.array([[1.0, 0, 0]]))
+    Uz, _ = mobility(p, pos, np.array([[0, 0, 1.0]]))
+    mu_par = 6 * np.pi * p.eta * Rh * Ux[0, 0]
+    mu_perp = 6 * np.pi * p.eta * Rh * Uz[0, 2]
+    assert mu_par == pytest.approx(_rpb_parallel(1 / zr), rel=1e-2)
+    assert mu_perp == pytest.approx(_rpb_perpendicular(1 / zr), rel=1e-2)
+    assert abs(Ux[0, 1]) < 1e-12 and abs(Ux[0, 2]) < 1e-12
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("zr", [2.0, 3.0, 4.0])
+def test_self_rotation_vs_wall_asymptotics(zr):
+    # Leading wall corrections to the rotational mobility of a sphere: 1 - (5/16)(a/z)^3 about an
+    # axis parallel to the wall, 1 - (1/8)(a/z)^3 about the normal.
+    rh_h, bm, bd = table1(6)
+    p = Params(Lx=160.0, Ly=160.0, zmin=0.0, zmax=16.0, mode="bottom_wall", nx=160, ny=160, nz=33,
+               m_M=6, beta_M=6 * bm, m_D=6, beta_D=6 * bd)
+    Rh = rh_h * p.h
+    pos = np.array([[80.3, 80.7, zr * Rh]])
+    zero = np.zeros((1, 3))
+    _, Wx = mobility(p, pos, zero, np.array([[1.0, 0, 0]]))
+    _, Wz = mobility(p, pos, zero, np.array([[0, 0, 1.0]]))
+    norm = 8 * np.pi * p.eta * Rh**3
+    assert norm * Wx[0, 0] == pytest.approx(1 - 5 / 16 / zr**3, rel=1e-2)
+    assert norm * Wz[0, 2] == pytest.approx(1 - 1 / 8 / zr**3, rel=1e-2)
+
+
+def _small(mode, nz=25, torque=True):
+    rh, bm, bd = table1(5)
+    zmax = 10.0
+    return Params(Lx=24.0, Ly=24.0, zmin=0.0, zmax=zmax, mode=mode, nx=36, ny=36, nz=nz, m_M=5,
+                  beta_M=5 * bm, m_D=5 if torque else 0, beta_D=5 * bd if torque else 0.0, eta=0.9)
+
+
+def _particles(p, n, seed, zlo, zhi):
+    rng = np.random.default_rng(seed)
+    pos = np.stack([rng.uniform(0, p.Lx, n), rng.uniform(0, p.Ly, n), rng.uniform(zlo, zhi, n)], 1)
+    return pos, rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
+
+
+@pytest.mark.parametrize("mode", ["bottom_wall", "slit", "free"])
+def test_translation_by_cells_and_periods(mode):
+    p = _small(mode)
+    pos, F, T = _particles(p, 4, 11, 2.0, 7.5)
+    U, W = mobility(p, pos, F, T)
+    for shift in ([3 * p.h, -5 * p.h, 0.0], [p.Lx, -2 * p.Ly, 0.0]):
+        U2, W2 = mobility(p, pos + np.array(shift), F, T)
+        assert np.max(np.abs(U2 - U)) < 1e-12 * np.max(np.abs(U))
+        assert np.max(np.abs(W2 - W)) < 1e-12 * np.max(np.abs(W))
+
+
+def test_linearity():
+    p = _small("slit")
+    pos, F, T = _particles(p, 3, 12, 0.5, 9.5)
+    _, G, S = _particles(p, 3, 13, 0.5, 9.5)
+    a, b = 0.7, -1.9
+    U1, W1 = mobility(p, pos, F, T)
+    U2, W2 = mobility(p, pos, G, S)
+    U3, W3 = mobility(p, pos, a * F + b * G, a * T + b * S)
+    assert np.allclose(U3, a * U1 + b * U2, rtol=0, atol=1e-13 * np.max(np.abs(U3)))
+    assert np.allclose(W3, a * W1 + b * W2, rtol=0, atol=1e-13 * np.max(np.abs(W3)))
+
+
+@pytest.mark.parametrize("mode", ["bottom_wall", "slit"])
+def test_particle_on_wall_is_immobile(mode):
+    # Eq. 9: the envelope and its negative image cancel for a particle on the wall.
+    p = _small(mode)
+    pos, F, T = _particles(p, 2, 14, 2.0, 7.0)
+    pos[0, 2] = 0.0
+    U, W = mobility(p, pos, F, T)
+    assert np.all(U[0] == 0.0) and np.all(W[0] == 0.0)
+    U1, W1 = mobility(p, pos[1:], F[1:], T[1:])
+    assert np.allclose(U[1], U1[0], atol=1e-14) and np.allclose(W[1], W1[0], atol=1e-14)
+
+
+def _grand_mobility(p, pos):
+    n = pos.shape[0]
+    M = np.zeros((6 * n, 6 * n))
+    for col in range(6 * n):
+        e = np.zeros(6 * n)
+        e[col] = 1.0
+        F = e[: 3 * n].reshape(n, 3)
+        T = e[3 * n:].reshape(n, 3)
+        U, W = mobility(p, pos, F, T)
+        M[:, col] = np.concatenate([U.ravel(), W.ravel()])
+    return M
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", ["bottom_wall", "slit"])
+def test_grand_mobility_symmetric_positive_definite(mode):
+    # The discrete operator is symmetric up to the z-discretisation error, which falls quickly
+    # with Nz (about 5e-3 at Nz = 33 and 5e-5 at Nz = 65 for this box).
+    p = Params(Lx=20.0, Ly=20.0, zmin=0.0, zmax=10.0, mode=mode, nx=40, ny=40, nz=65, m_M=6,
+               beta_M=6 * table1(6)[1], m_D=6, beta_D=6 * table1(6)[2])
+    pos = np.array([[4.1, 5.3, 2.6], [7.2, 4.4, 3.9]])
+    M = _grand_mobility(p, pos)
+    asym = np.linalg.norm(M - M.T) / np.linalg.norm(M)
+    assert asym < 2e-4
+    assert np.min(np.linalg.eigvalsh(0.5 * (M + M.T))) > 0.0
+
+
+def test_slit_midplane_reflection():
+    p = _small("slit")
+    pos, F, T = _particles(p, 3, 15, 0.5, 9.5)
+    U, W = mobility(p, pos, F, T)
+    ref = np.array([1.0, 1.0, -1.0])          # polar vectors under z -> zmin + zmax - z
+    pref = np.array([-1.0, -1.0, 1.0])        # pseudovectors (torque, angular velocity)
+    pos2 = pos.copy()
+    pos2[:, 2] = p.zmin + p.zmax - pos[:, 2]
+    U2, W2 = mobility(p, pos2, F * ref, T * pref)
+    assert np.max(np.abs(U2 - U * ref)) < 1e-12 * np.max(np.abs(U))
+    assert np.max(np.abs(W2 - W * pref)) < 1e-12 * np.max(np.abs(W))
+
+
+def test_slit_midplane_translation_rotation_coupling_vanishes():
+    # mu^tr_yx(H/2) = 0 in the slit by symmetry (Sec. IV.A).
+    p = _small("slit")
+    pos = np.array([[7.3, 8.1, 5.0]])
+    U, W = mobility(p, pos, np.array([[1.0, 0, 0]]), np.zeros((1, 3)))
+    assert abs(W[0, 1]) < 1e-13 * abs(U[0, 0])
+
+
+@pytest.mark.parametrize("mode", ["bottom_wall", "free"])
+def test_x_mirror(mode):
+    p = _small(mode)
+    pos, F, T = _particles(p, 3, 16, 2.0, 7.5)
+    U, W = mobility(p, pos, F, T)
+    ref = np.array([-1.0, 1.0, 1.0])
+    pref = np.array([1.0, -1.0, -1.0])
+    pos2 = pos.copy()
+    pos2[:, 0] = -pos[:, 0]
+    U2, W2 = mobility(p, pos2, F * ref, T * pref)
+    assert np.max(np.abs(U2 - U * ref)) < 1e-12 * np.max(np.abs(U))
+    assert np.max(np.abs(W2 - W * pref)) < 1e-12 * np.max(np.abs(W))
+
+
+@pytest.mark.parametrize("which", ["M", "D"])
+def test_spread_and_interpolation_are_adjoint(which):
+    p = _small("bottom_wall")
+    pos, F, _ = _particles(p, 5, 17, 0.3, 7.5)
+    rng = np.random.default_rng(18)
+    u = rng.standard_normal((3, p.nz, p.ny, p.nx))
+    lhs = np.sum(interpolate(p, pos, u, which) * F)
+    wz = cheb.clenshaw_curtis_weights(p.nz, p.H)
+    rhs = p.h * p.h * np.sum(spread(p, pos, F, which) * u * wz[None, :, None, None])
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+@pytest.mark.slow
+def test_spectral_convergence_in_nz():
+    # The ES kernel jumps by e^{-beta}/Z at the edge of its support, which limits the z quadrature
+    # to first order at that level; with beta = 18 the jump is ~1e-8 and the convergence in Nz is
+    # geometric down to it.
+    pos = np.array([[6.3, 7.1, 1.4], [9.0, 5.2, 3.3]])
+    F = np.array([[1.0, -0.5, 0.3], [0.2, 0.8, -1.0]])
+    T = np.array([[0.3, 0.1, -0.2], [-0.4, 0.5, 0.6]])
+    res = []
+    for nz in (17, 33, 65, 129):
+        p = Params(Lx=24.0, Ly=24.0, zmin=0.0, zmax=10.0, mode="bottom_wall", nx=36, ny=36, nz=nz,
+                   m_M=6, beta_M=18.0, m_D=6, beta_D=18.0)
+        U, W = mobility(p, pos, F, T)
+        res.append(np.concatenate([U.ravel(), W.ravel()]))
+    scale = np.max(np.abs(res[-1]))
+    d = [np.max(np.abs(res[i + 1] - res[i])) / scale for i in range(3)]
+    assert d[1] < 0.1 * d[0] and d[2] < 1e-3 * d[1]
+    assert d[2] < 1e-6
