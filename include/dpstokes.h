@@ -1,0 +1,143 @@
+/*
+ * dpstokes.h - C ABI of the GB300 doubly-periodic FCM mobility library.
+ *
+ * The library computes the mobility product [U; Omega] = M [F; T] (Eq. 58 of Hashemi et al.,
+ * "Computing hydrodynamic interactions in confined doubly-periodic geometries in linear time")
+ * for N particles in a box that is periodic in x and y, with one of three conditions in z:
+ * open (free space), a no-slip wall at zmin (bottom wall), or no-slip walls at zmin and zmax
+ * (slit channel).  The product follows the eight steps of Sec. III.D: ES-kernel spreading
+ * (Eqs. 7, 9, 53-54), xy FFT + Chebyshev transform in z, the doubly-periodic pressure and
+ * velocity boundary-value problems per wavenumber (Eqs. 15-24), the wall correction
+ * (Eqs. 41-44; Appendix A, Eqs. A4-A10 with zero slip lengths), the k = 0 mode (Sec. III.C,
+ * Eq. A12), inverse transforms with the curl for angular velocities, and ES interpolation
+ * (Eqs. 10-11).
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - The xy box is [0, Lx) x [0, Ly); Lx, Ly are full periods, h = Lx/nx = Ly/ny (must agree),
+ *   wavenumbers are k = 2 pi n / L.  x and y are wrapped modulo the periods.
+ * - z nodes are the nz Chebyshev extrema nodes on [zmin, zmax], both ends included (Sec. III.D).
+ * - The ES support of the monopole (M) and dipole (D) kernels is alpha = m h / 2 (Sec. III.E).
+ * - Particle arrays are row-major [n][3] double (x, y, z / Fx, Fy, Fz / ...).
+ * - Every function returns a dps_status; nothing traps or aborts.  Errors that can be seen on
+ *   the host return at once.  Errors that depend on the data (a height outside [zmin, zmax], an
+ *   envelope crossing an open boundary, a non-finite input) set a device status word that
+ *   dpstokes_status() reads; the outputs of that apply are then undefined.
+ * - Buffers passed to the library stay owned by the caller.  The plan owns all grids, spectra,
+ *   tables and workspaces and frees them in dpstokes_destroy().
+ */
+#ifndef DPSTOKES_H
+#define DPSTOKES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dps_plan_s* dps_plan_t;
+
+/* z boundary condition (Sec. II; Appendix A) */
+typedef enum {
+  DPS_FREE = 0,         /* open in z: no wall, kernels must stay inside [zmin, zmax]          */
+  DPS_BOTTOM_WALL = 1,  /* no-slip wall at zmin, open above; kernels must stay below zmax     */
+  DPS_SLIT = 2          /* no-slip walls at zmin and zmax                                      */
+} dps_wall_mode;
+
+/* arithmetic of the hot path */
+typedef enum {
+  DPS_FP64 = 0,   /* every stage in double precision                                           */
+  DPS_MIXED = 1   /* spreading, FFTs, Chebyshev transforms, interpolation in float (float
+                     accumulation); the banded BVP solves and the wall-correction boundary rows
+                     in double                                                                   */
+} dps_precision;
+
+typedef enum {
+  DPS_OK = 0,
+  DPS_ERR_INVALID_ARG = -1,   /* bad sizes or parameters, inconsistent pointer combination      */
+  DPS_ERR_OUT_OF_DOMAIN = -2, /* a height outside [zmin, zmax] or an envelope through an open
+                                 boundary (footnote to step 1 of Sec. III.D)                     */
+  DPS_ERR_OOM = -3,           /* device allocation failed in dpstokes_plan_create               */
+  DPS_ERR_CUDA = -4,          /* a CUDA runtime call failed                                      */
+  DPS_ERR_TIMEOUT = -5,       /* reserved for bounded device waits                               */
+  DPS_ERR_NONFINITE = -6      /* a non-finite position, force or torque                          */
+} dps_status;
+
+typedef struct {
+  int32_t nx, ny;  /* xy grid; nx, ny >= 8 and 2,3,5,7-smooth                                   */
+  int32_t nz;      /* Chebyshev nodes on [zmin, zmax] including both ends, 5 <= nz <= 257      */
+} dps_grid;
+
+typedef struct {
+  int32_t m_M;     /* monopole ES support in cells, 2 <= m <= 12; alpha_M = m_M h / 2          */
+  double beta_M;   /* monopole ES shape parameter beta (Eq. 54), > 0                            */
+  int32_t m_D;     /* dipole support (used only with torques)                                  */
+  double beta_D;   /* dipole shape parameter                                                    */
+  double eta;      /* viscosity (Eq. 4), > 0                                                    */
+  int32_t with_torque;  /* 1: applies take torques and return angular velocities             */
+  int32_t precision;    /* dps_precision                                                       */
+  int64_t max_n;        /* largest particle count an apply may pass                           */
+} dps_kernel_params;
+
+/* Build a plan: validates the box, grid and kernels, builds the Chebyshev/quadrature/transform
+ * tables and allocates every device buffer an apply needs (no allocation happens in apply).
+ * Host-detectable errors: non-positive sizes, h_x != h_y, nz out of range, a non-smooth xy size,
+ * m out of range or its envelope wider than half the box, a slit narrower than 2 alpha.
+ * The current CUDA device at the call is the plan's device.  *out is NULL on error. */
+dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zmin, double zmax,
+                                int32_t wall_mode, const dps_grid* grid,
+                                const dps_kernel_params* kp);
+
+/* One mobility product, enqueued on `stream` (a cudaStream_t, NULL for the legacy stream).
+ * positions, forces: device [n][3]; torques: device [n][3] or NULL; out_vel: device [n][3];
+ * out_angvel: device [n][3] or NULL.  torques and out_angvel must both be NULL for a plan built
+ * without torques and both non-NULL for one built with torques.  0 <= n <= max_n.  Outputs are
+ * fully overwritten.  Asynchronous: no host synchronisation, no allocation.  Two applies on the
+ * same plan must not run concurrently (they share the plan's buffers). */
+dps_status dpstokes_apply(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
+                          const double* torques, double* out_vel, double* out_angvel, void* stream);
+
+/* Same product from HOST arrays: copies the inputs to plan-owned device staging buffers, runs
+ * dpstokes_apply on `stream`, copies the outputs back and synchronises the stream.  Pinned host
+ * memory gives the fastest copies.  Returns the device status of the apply. */
+dps_status dpstokes_apply_host(dps_plan_t plan, int64_t n, const double* positions,
+                               const double* forces, const double* torques, double* out_vel,
+                               double* out_angvel, void* stream);
+
+/* Synchronises `stream`, reads and clears the device status word of the plan's last apply. */
+dps_status dpstokes_status(dps_plan_t plan, void* stream);
+
+/* Frees every buffer of the plan (synchronises the device first).  NULL is ignored. */
+void dpstokes_destroy(dps_plan_t plan);
+
+/* Static description of the error code (never NULL). */
+const char* dpstokes_error_string(dps_status status);
+
+/* Plan facts for callers and diagnostics. */
+typedef struct {
+  int64_t device_bytes;     /* device memory owned by the plan                                  */
+  int32_t nkx;              /* nx/2 + 1 stored wavenumbers in x                                 */
+  int32_t pitch;            /* complex elements per stored grid row                             */
+  int32_t nfields;          /* 3 (forces) or 6 (forces and torques)                            */
+  int32_t record_words;     /* 32-bit words per particle kernel record                          */
+  double h;                 /* grid spacing                                                     */
+  double alpha_M, alpha_D;  /* kernel supports                                                  */
+} dps_plan_info;
+dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
+
+/* Diagnostics for tests: run the apply pipeline on `stream` up to and including stage
+ * `last_stage` (1 = particle records, 2 = spread, 3 = forward xy FFT, 4 = per-k solve,
+ * 5 = inverse xy FFT, 6 = interpolation) and copy plan buffer `which` (0 = grid/spectrum,
+ * 1 = particle records, 2 = occupied plane range [2 x int32]) to the device pointer dst
+ * (at most dst_bytes).  Returns DPS_ERR_INVALID_ARG for unknown stages or buffers. */
+dps_status dpstokes_debug_run(dps_plan_t plan, int64_t n, const double* positions,
+                              const double* forces, const double* torques, double* out_vel,
+                              double* out_angvel, void* stream, int32_t last_stage);
+dps_status dpstokes_debug_copy(dps_plan_t plan, int32_t which, void* dst, int64_t dst_bytes,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPSTOKES_H */

@@ -1,0 +1,131 @@
+// Internal declarations of the GB300 doubly-periodic FCM mobility library.
+// Everything here is private to the library; the public C ABI is include/dpstokes.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/dpstokes.h"
+
+namespace dps {
+
+// ---------------------------------------------------------------------------------------------
+// complex helpers (interleaved re/im, 8- or 16-byte aligned)
+// ---------------------------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct __align__(8) cplx<float> { float x, y; };
+template <> struct __align__(16) cplx<double> { double x, y; };
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T a, T b) { cplx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ cplx<T> scl(cplx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { return mk<T>(a.x, -a.y); }
+// multiply by i
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mul_i(cplx<T> a) { return mk<T>(-a.y, a.x); }
+
+// ---------------------------------------------------------------------------------------------
+// tiling constants
+// ---------------------------------------------------------------------------------------------
+constexpr int kTileX = 32;          // spread tile / particle bin, nodes in x
+constexpr int kTileY = 8;           // nodes in y
+constexpr int kSpreadThreads = kTileX * kTileY;
+constexpr int kMaxFftRadices = 24;
+constexpr int kMaxM = 12;           // largest ES support in cells
+constexpr int kBvpThreads = 128;    // threads (wavenumbers) per block in the per-k solver
+
+// FFT factorisation (radices applied in order, Stockham autosort)
+struct FftPlan {
+  int n;
+  int nstages;
+  int radix[kMaxFftRadices];
+};
+
+// Per-kernel (monopole / dipole) ES parameters on the device
+struct EsKernel {
+  double alpha;     // support half width
+  double beta;      // shape
+  double inv_norm;  // 1 / integral of exp(beta (sqrt(1-(t/alpha)^2) - 1)) over [-alpha, alpha]
+  int px;           // x/y node slots per particle (m + 1)
+};
+
+// Everything a kernel needs to know about the problem (passed by value)
+struct Geometry {
+  double Lx, Ly, zmin, zmax, H, h, inv_h;
+  double eta;
+  int mode;          // dps_wall_mode
+  int nx, ny, nz;
+  int nkx;           // nx/2 + 1
+  int pitch;         // complex elements per stored row (>= nkx); real rows hold 2*pitch values
+  int nfields;       // 3 or 6
+  int with_torque;
+  int nbx, nby;      // bins (spread tiles) in x and y
+  int rbx, rby;      // bin radius searched around a tile
+  EsKernel kM, kD;
+  int pxc;           // x/y slots in a particle record (max over kernels)
+  int lzc;           // z slots in a particle record
+  int rec_words;     // 32-bit words per particle record
+  int nkernels;      // 1 (M) or 2 (M and D)
+};
+
+// Device tables owned by the plan
+struct Tables {
+  double* zc;      // [nz] node heights, c = 0 at zmax
+  void* wz;        // [nz] T Clenshaw-Curtis weights (times h^2 is applied in interpolation)
+  void* dct;       // [nz][nz] T  forward DCT-I  C[n][c]
+  void* dctd;      // [nz][nz] T  (2/H) * Chebyshev derivative of the forward DCT-I
+  void* idct;      // [nz][nz] T  inverse DCT-I  IC[c][n]
+  void* zeta;      // [nz] T  z_c - zmin
+  double* band;    // [5][nz] doubles: l_n, d_n, u_n, P_n, Q_n of the spectral-integration operator
+  void* twx;       // [nx] cplx<T>  exp(-2 pi i t / nx)
+  void* twy;       // [ny] cplx<T>  exp(-2 pi i t / ny)
+};
+
+struct Plan {
+  int device;
+  int precision;        // dps_precision
+  int64_t max_n;
+  Geometry g;
+  FftPlan fx, fy;
+  Tables tab;
+  // device buffers
+  void* grid;           // [nfields][nz][ny][pitch] cplx<T> (real rows: 2*pitch T)
+  uint32_t* records;    // [max_n][rec_words]
+  int* bin_of;          // [max_n]
+  int* bin_count;       // [nbins]
+  int* bin_start;       // [nbins + 1]
+  int* bin_cursor;      // [nbins]
+  int* sorted;          // [max_n]
+  int* zrange;          // [2] occupied Chebyshev plane range (c_lo, c_hi)
+  int* status;          // [1] device status bits
+  void* ws;             // per-slot workspace of the per-k solver
+  int bvp_blocks;       // persistent grid size of the per-k solver
+  int64_t ws_bytes;
+  // host-input staging (dpstokes_apply_host)
+  double* stage_in;     // [max_n][9]
+  double* stage_out;    // [max_n][6]
+  int64_t device_bytes;
+};
+
+// status bits written by kernels
+enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4 };
+
+// launchers (stream-ordered, no host sync)
+template <typename T> void launch_records(const Plan& p, int64_t n, const double* pos, const double* F,
+                                          const double* Tq, cudaStream_t s);
+void launch_bins(const Plan& p, int64_t n, cudaStream_t s);
+template <typename T> void launch_spread(const Plan& p, cudaStream_t s);
+template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s);
+template <typename T> void launch_fft_forward(const Plan& p, cudaStream_t s);
+template <typename T> void launch_fft_inverse(const Plan& p, cudaStream_t s);
+template <typename T> void launch_bvp(const Plan& p, cudaStream_t s);
+template <typename T> int bvp_occupancy_blocks(const Plan& p);
+template <typename T> size_t bvp_slot_bytes(const Plan& p);
+template <typename T> int fft_smem_ok(const Plan& p);
+
+}  // namespace dps

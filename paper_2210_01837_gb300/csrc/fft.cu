@@ -1,0 +1,308 @@
+// In-house xy FFTs of the Chebyshev planes (steps 2 and 7 of Sec. III.D, xy part).
+//
+// Forward: f_hat(k) = sum_x f(x) exp(-i k.x) (unnormalised).  Inverse: sum_k f_hat(k) exp(+i k.x);
+// the 1/(Nx Ny) factor is applied by the per-k solver when it writes its outputs.
+//
+// Layout of one field/plane: ny rows; each row holds nx reals in real space and nx/2+1 complex
+// values (pitch >= nx/2+1 complex) in x-Fourier space, in place.
+//   * row pass:    one block transforms two real rows packed as one complex sequence
+//                  (z = r0 + i r1), then separates the two half spectra; inverse likewise.
+//   * column pass: one block transforms `cw` adjacent x-wavenumber columns along y.
+// Each 1D transform is a self-sorting (Stockham) mixed-radix FFT in shared memory written from the
+// textbook formulation: stage s with radix R and span Ns multiplies input j + r n/R by
+// W_{Ns R}^{(j mod Ns) r}, applies an R-point DFT, and stores to (j / Ns) Ns R + (j mod Ns) + r Ns.
+// Radices 8, 4, 2 (hand-written butterflies) and 3, 5, 7 (direct DFT with exact constants).
+// Twiddles W_n^t = exp(-2 pi i t/n) come from a table built in double precision on the host.
+#include "dps_internal.cuh"
+
+namespace dps {
+
+namespace {
+
+// cos(2 pi m / R), sin(2 pi m / R)
+__device__ __constant__ double c_cos3[3] = {1.0, -0.5, -0.5};
+__device__ __constant__ double c_sin3[3] = {0.0, 0.86602540378443865, -0.86602540378443865};
+__device__ __constant__ double c_cos5[5] = {1.0, 0.30901699437494742, -0.80901699437494742, -0.80901699437494742,
+                                            0.30901699437494742};
+__device__ __constant__ double c_sin5[5] = {0.0, 0.95105651629515357, 0.58778525229247314, -0.58778525229247314,
+                                            -0.95105651629515357};
+__device__ __constant__ double c_cos7[7] = {1.0, 0.62348980185873353, -0.22252093395631440, -0.90096886790241913,
+                                            -0.90096886790241913, -0.22252093395631440, 0.62348980185873353};
+__device__ __constant__ double c_sin7[7] = {0.0, 0.78183148246802981, 0.97492791218182361, 0.43388373911755812,
+                                            -0.43388373911755812, -0.97492791218182361, -0.78183148246802981};
+
+template <typename T, int DIR>
+__device__ __forceinline__ cplx<T> rot_quarter(cplx<T> a) {
+  // multiply by -i (forward) or +i (inverse)
+  return DIR < 0 ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
+}
+
+template <typename T, int R, int DIR> struct Dft;
+
+template <typename T, int DIR> struct Dft<T, 2, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) {
+    const cplx<T> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  }
+};
+
+template <typename T, int DIR> struct Dft<T, 4, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) {
+    const cplx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3];
+    const cplx<T> t3 = rot_quarter<T, DIR>(v[1] - v[3]);
+    v[0] = t0 + t2;
+    v[2] = t0 - t2;
+    v[1] = t1 + t3;
+    v[3] = t1 - t3;
+  }
+};
+
+template <typename T, int DIR> struct Dft<T, 8, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) {
+    cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
+    cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<T, 4, DIR>::run(e);
+    Dft<T, 4, DIR>::run(o);
+    const T s = (T)0.70710678118654752440;
+    // W8^k, k = 0..3, for the transform direction
+    const cplx<T> w1 = mk<T>(s, (T)DIR * s);
+    const cplx<T> w3 = mk<T>(-s, (T)DIR * s);
+    const cplx<T> o1 = o[1] * w1;
+    const cplx<T> o2 = rot_quarter<T, DIR>(o[2]);
+    const cplx<T> o3 = o[3] * w3;
+    v[0] = e[0] + o[0];
+    v[4] = e[0] - o[0];
+    v[1] = e[1] + o1;
+    v[5] = e[1] - o1;
+    v[2] = e[2] + o2;
+    v[6] = e[2] - o2;
+    v[3] = e[3] + o3;
+    v[7] = e[3] - o3;
+  }
+};
+
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft_direct(cplx<T>* v, const double* cs, const double* sn) {
+  cplx<T> out[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    cplx<T> acc = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const int m = (r * k) % R;
+      const cplx<T> w = mk<T>((T)cs[m], (T)(DIR * sn[m]));
+      acc = acc + v[r] * w;
+    }
+    out[k] = acc;
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = out[k];
+}
+
+template <typename T, int DIR> struct Dft<T, 3, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 3, DIR>(v, c_cos3, c_sin3); }
+};
+template <typename T, int DIR> struct Dft<T, 5, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 5, DIR>(v, c_cos5, c_sin5); }
+};
+template <typename T, int DIR> struct Dft<T, 7, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 7, DIR>(v, c_cos7, c_sin7); }
+};
+
+// One Stockham stage over `batch` interleaved sequences (element e of sequence b at e*batch + b).
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int n, int Ns,
+                                      int batch, const cplx<T>* __restrict__ tw) {
+  const int nr = n / R;
+  const int total = nr * batch;
+  const int tstep = n / (Ns * R);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int b = t % batch;
+    const int jj = t / batch;
+    const int k = jj % Ns;
+    cplx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[(jj + r * nr) * batch + b];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = tw[k * r * tstep];
+        if (DIR > 0) w.y = -w.y;
+        v[r] = v[r] * w;
+      }
+    }
+    Dft<T, R, DIR>::run(v);
+    const int base = (jj / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[(base + r * Ns) * batch + b] = v[r];
+  }
+}
+
+// Full transform; returns the buffer that holds the result.
+template <typename T, int DIR>
+__device__ cplx<T>* fft_smem(cplx<T>* b0, cplx<T>* b1, const FftPlan& fp, int batch, const cplx<T>* tw) {
+  int Ns = 1;
+  cplx<T>* in = b0;
+  cplx<T>* out = b1;
+  for (int s = 0; s < fp.nstages; ++s) {
+    const int R = fp.radix[s];
+    switch (R) {
+      case 8: stage<T, 8, DIR>(in, out, fp.n, Ns, batch, tw); break;
+      case 4: stage<T, 4, DIR>(in, out, fp.n, Ns, batch, tw); break;
+      case 2: stage<T, 2, DIR>(in, out, fp.n, Ns, batch, tw); break;
+      case 3: stage<T, 3, DIR>(in, out, fp.n, Ns, batch, tw); break;
+      case 5: stage<T, 5, DIR>(in, out, fp.n, Ns, batch, tw); break;
+      default: stage<T, 7, DIR>(in, out, fp.n, Ns, batch, tw); break;
+    }
+    __syncthreads();
+    Ns *= R;
+    cplx<T>* t = in;
+    in = out;
+    out = t;
+  }
+  return in;
+}
+
+__device__ __forceinline__ bool plane_live(const int* zrange, int c) { return c >= zrange[0] && c <= zrange[1]; }
+
+template <typename T>
+__global__ void row_r2c_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, T* __restrict__ grid,
+                               const int* __restrict__ zrange) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* b1 = b0 + g.nx;
+  const int c = blockIdx.y, f = blockIdx.z;
+  if (!plane_live(zrange, c)) return;
+  const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
+  const bool has1 = y1 < g.ny;
+  const size_t rowlen = (size_t)2 * g.pitch;
+  T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + y0) * rowlen;
+  T* row1 = row0 + rowlen;
+  for (int a = threadIdx.x; a < g.nx; a += blockDim.x) b0[a] = mk<T>(row0[a], has1 ? row1[a] : (T)0);
+  __syncthreads();
+  const cplx<T>* res = fft_smem<T, -1>(b0, b1, fp, 1, tw);
+  cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
+  cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row1);
+  const T half = (T)0.5;
+  for (int k = threadIdx.x; k <= g.nx / 2; k += blockDim.x) {
+    const cplx<T> zk = res[k];
+    const cplx<T> zm = conjg(res[(g.nx - k) % g.nx]);
+    c0[k] = scl(zk + zm, half);
+    if (has1) {
+      const cplx<T> d = zk - zm;  // (zk - conj z_{-k}) / (2i)
+      c1[k] = mk<T>(half * d.y, -half * d.x);
+    }
+  }
+}
+
+template <typename T>
+__global__ void row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, T* __restrict__ grid,
+                               const int* __restrict__ zrange) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* b1 = b0 + g.nx;
+  const int c = blockIdx.y, f = blockIdx.z;
+  if (!plane_live(zrange, c)) return;
+  const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
+  const bool has1 = y1 < g.ny;
+  const size_t rowlen = (size_t)2 * g.pitch;
+  T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + y0) * rowlen;
+  T* row1 = row0 + rowlen;
+  const cplx<T>* c0 = reinterpret_cast<const cplx<T>*>(row0);
+  const cplx<T>* c1 = reinterpret_cast<const cplx<T>*>(row1);
+  for (int k = threadIdx.x; k <= g.nx / 2; k += blockDim.x) {
+    const cplx<T> x0 = c0[k];
+    const cplx<T> x1 = has1 ? c1[k] : mk<T>((T)0, (T)0);
+    b0[k] = x0 + mul_i(x1);
+    if (k > 0 && k < g.nx - k) b0[g.nx - k] = conjg(x0) + mul_i(conjg(x1));
+  }
+  __syncthreads();
+  const cplx<T>* res = fft_smem<T, +1>(b0, b1, fp, 1, tw);
+  for (int a = threadIdx.x; a < g.nx; a += blockDim.x) {
+    const cplx<T> v = res[a];
+    row0[a] = v.x;
+    if (has1) row1[a] = v.y;
+  }
+}
+
+template <typename T, int DIR>
+__global__ void col_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ grid,
+                           const int* __restrict__ zrange, int cw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* b1 = b0 + (size_t)g.ny * cw;
+  const int c = blockIdx.y, f = blockIdx.z;
+  if (!plane_live(zrange, c)) return;
+  const int kx0 = blockIdx.x * cw;
+  const int ncols = min(cw, g.nkx - kx0);
+  cplx<T>* base = grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
+  const int tot = g.ny * cw;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int y = t / cw, b = t - y * cw;
+    b0[t] = (b < ncols) ? base[(size_t)y * g.pitch + b] : mk<T>((T)0, (T)0);
+  }
+  __syncthreads();
+  const cplx<T>* res = fft_smem<T, DIR>(b0, b1, fp, cw, tw);
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int y = t / cw, b = t - y * cw;
+    if (b < ncols) base[(size_t)y * g.pitch + b] = res[t];
+  }
+}
+
+template <typename T>
+int col_width(const Plan& p) {
+  // widest power-of-two column block whose two buffers fit in 200 KB of shared memory
+  int cw = 16;
+  while (cw > 1 && (size_t)2 * p.g.ny * cw * sizeof(cplx<T>) > 200 * 1024) cw >>= 1;
+  return cw;
+}
+
+}  // namespace
+
+template <typename T>
+int fft_smem_ok(const Plan& p) {
+  const size_t row = (size_t)2 * p.g.nx * sizeof(cplx<T>);
+  const size_t col = (size_t)2 * p.g.ny * col_width<T>(p) * sizeof(cplx<T>);
+  if (row > 220 * 1024 || col > 220 * 1024) return 0;
+  cudaFuncSetAttribute(row_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row);
+  cudaFuncSetAttribute(row_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row);
+  cudaFuncSetAttribute(col_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col);
+  cudaFuncSetAttribute(col_kernel<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col);
+  return 1;
+}
+
+template <typename T>
+void launch_fft_forward(const Plan& p, cudaStream_t s) {
+  const Geometry& g = p.g;
+  const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
+  const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
+  dim3 gr((g.ny + 1) / 2, g.nz, g.nfields);
+  row_r2c_kernel<T><<<gr, 256, 2 * g.nx * sizeof(cplx<T>), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
+  const int cw = col_width<T>(p);
+  dim3 gc((g.nkx + cw - 1) / cw, g.nz, g.nfields);
+  col_kernel<T, -1><<<gc, 512, 2 * (size_t)g.ny * cw * sizeof(cplx<T>), s>>>(
+      g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
+}
+
+template <typename T>
+void launch_fft_inverse(const Plan& p, cudaStream_t s) {
+  const Geometry& g = p.g;
+  const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
+  const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
+  const int cw = col_width<T>(p);
+  dim3 gc((g.nkx + cw - 1) / cw, g.nz, g.nfields);
+  col_kernel<T, +1><<<gc, 512, 2 * (size_t)g.ny * cw * sizeof(cplx<T>), s>>>(
+      g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
+  dim3 gr((g.ny + 1) / 2, g.nz, g.nfields);
+  row_c2r_kernel<T><<<gr, 256, 2 * g.nx * sizeof(cplx<T>), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
+}
+
+template int fft_smem_ok<float>(const Plan&);
+template int fft_smem_ok<double>(const Plan&);
+template void launch_fft_forward<float>(const Plan&, cudaStream_t);
+template void launch_fft_forward<double>(const Plan&, cudaStream_t);
+template void launch_fft_inverse<float>(const Plan&, cudaStream_t);
+template void launch_fft_inverse<double>(const Plan&, cudaStream_t);
+
+}  // namespace dps

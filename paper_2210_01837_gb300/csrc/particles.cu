@@ -1,0 +1,448 @@
+// Particle-side kernels: envelope records, binning, spreading (step 1 of Sec. III.D) and
+// interpolation (step 8, Eqs. 10-11) of the doubly-periodic FCM mobility product.
+//
+// Envelope: Delta^W(x - r_j) = phi(dx) phi(dy) [phi(dz) - s_b phi(z - z_im,bottom)
+//                                                      - s_t phi(z - z_im,top)]   (Eqs. 9, 53, 54)
+// phi(t) = exp(beta (sqrt(1 - (t/alpha)^2) - 1)) / Z on |t| <= alpha, zero outside.
+//
+// Each particle gets one record per apply holding its force/torque and the separable envelope
+// factors at the nodes of its support (x and y slots, and the Chebyshev nodes of its z support
+// with the wall images folded in).  Spreading and interpolation both read these records, so the
+// two operators use bit-identical weights (they are adjoint under the quadrature).
+//
+// Spreading is a gather: one block owns a 32 x 8 tile of xy nodes over all occupied Chebyshev
+// planes, collects the particles whose support touches the tile from the surrounding bins, and
+// writes every node of its tile exactly once with plain stores (no atomics, no zero-fill pass).
+// Interpolation is a warp per particle: lanes walk the x run of each (z, y) row of the support,
+// so every row is read as one contiguous segment.
+#include <math.h>
+
+#include "dps_internal.cuh"
+
+namespace dps {
+
+namespace {
+
+__device__ __forceinline__ double es_eval(double t, const EsKernel& k) {
+  const double r = t / k.alpha;
+  if (fabs(r) > 1.0) return 0.0;
+  return exp(k.beta * (sqrt(1.0 - r * r) - 1.0)) * k.inv_norm;
+}
+
+__device__ __forceinline__ float es_eval_f(double t, const EsKernel& k) {
+  // argument relative to the support in double, the exponential in float
+  const double r = t / k.alpha;
+  if (fabs(r) > 1.0) return 0.0f;
+  const float q = (float)(1.0 - r * r);
+  return expf((float)k.beta * (sqrtf(q) - 1.0f)) * (float)k.inv_norm;
+}
+
+template <typename T> __device__ __forceinline__ T es_t(double t, const EsKernel& k);
+template <> __device__ __forceinline__ double es_t<double>(double t, const EsKernel& k) { return es_eval(t, k); }
+template <> __device__ __forceinline__ float es_t<float>(double t, const EsKernel& k) { return es_eval_f(t, k); }
+
+__device__ __forceinline__ int wrap_idx(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// first node index a with |a h - x| <= alpha (candidates start at floor((x - alpha)/h))
+__device__ __forceinline__ int first_node(double x, double h, double inv_h, double alpha) {
+  int a = (int)floor((x - alpha) * inv_h);
+  if (fabs((double)a * h - x) > alpha) ++a;
+  return a;
+}
+
+// number of Chebyshev nodes with z_c > v (nodes decrease with c)
+__device__ __forceinline__ int count_above(const double* zc, int nz, double v) {
+  int lo = 0, hi = nz;  // answer in [0, nz]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (zc[mid] > v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__ pos,
+                               const double* __restrict__ F, const double* __restrict__ Tq,
+                               const double* __restrict__ zc, uint32_t* __restrict__ rec,
+                               int* __restrict__ bin_of, int* __restrict__ bin_count,
+                               int* __restrict__ zrange, int* __restrict__ status) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  uint32_t* r = rec + (size_t)j * g.rec_words;
+  T* tv = reinterpret_cast<T*>(r + 8);
+  double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+  double f[3] = {F[3 * j], F[3 * j + 1], F[3 * j + 2]};
+  double tq[3] = {0.0, 0.0, 0.0};
+  if (g.with_torque) { tq[0] = Tq[3 * j]; tq[1] = Tq[3 * j + 1]; tq[2] = Tq[3 * j + 2]; }
+  bool finite = isfinite(x) && isfinite(y) && isfinite(z);
+  for (int i = 0; i < 3; ++i) finite = finite && isfinite(f[i]) && isfinite(tq[i]);
+  bool ok = finite;
+  if (!finite) atomicOr(status, kStatNonfinite);
+  double amax = g.kM.alpha;
+  if (g.with_torque && g.kD.alpha > amax) amax = g.kD.alpha;
+  if (ok) {
+    bool in_dom = (z >= g.zmin) && (z <= g.zmax);
+    if (g.mode == DPS_FREE && z - amax < g.zmin) in_dom = false;
+    if ((g.mode == DPS_FREE || g.mode == DPS_BOTTOM_WALL) && z + amax > g.zmax) in_dom = false;
+    if (!in_dom) { atomicOr(status, kStatDomain); ok = false; }
+  }
+  // wrap x, y into [0, L)
+  double xw = 0.0, yw = 0.0;
+  if (ok) {
+    xw = x - g.Lx * floor(x / g.Lx);
+    if (xw >= g.Lx) xw -= g.Lx;
+    if (xw < 0.0) xw = 0.0;
+    yw = y - g.Ly * floor(y / g.Ly);
+    if (yw >= g.Ly) yw -= g.Ly;
+    if (yw < 0.0) yw = 0.0;
+  }
+  for (int i = 0; i < 3; ++i) {
+    tv[i] = ok ? (T)f[i] : (T)0;
+    tv[3 + i] = ok ? (T)tq[i] : (T)0;
+  }
+  int cmin = g.nz, cmax = -1;
+  const int stride = 2 * g.pxc + g.lzc;
+  for (int K = 0; K < g.nkernels; ++K) {
+    const EsKernel& k = (K == 0) ? g.kM : g.kD;
+    int4 hd = make_int4(0, 0, 0, 0);
+    T* ph = tv + 6 + K * stride;
+    if (ok) {
+      const int ax = first_node(xw, g.h, g.inv_h, k.alpha);
+      const int ay = first_node(yw, g.h, g.inv_h, k.alpha);
+      for (int i = 0; i < g.pxc; ++i) {
+        ph[i] = (i < k.px) ? es_t<T>((double)(ax + i) * g.h - xw, k) : (T)0;
+        ph[g.pxc + i] = (i < k.px) ? es_t<T>((double)(ay + i) * g.h - yw, k) : (T)0;
+      }
+      hd.x = wrap_idx(ax, g.nx);
+      hd.y = wrap_idx(ay, g.ny);
+      // z support: nodes with z_c in [max(zmin, z - alpha), min(zmax, z + alpha)], widened by a
+      // hair so that the exact |t| <= alpha tests below decide membership
+      const double eps = 1e-12 * (g.H + fabs(z));
+      const int c0 = count_above(zc, g.nz, z + k.alpha + eps);
+      const int c1 = count_above(zc, g.nz, z - k.alpha - eps) - 1;
+      int cnt = c1 - c0 + 1;
+      if (cnt < 0) cnt = 0;
+      if (cnt > g.lzc) { cnt = g.lzc; atomicOr(status, kStatInternal); }
+      hd.z = c0;
+      hd.w = cnt;
+      const bool bottom_img = (g.mode == DPS_BOTTOM_WALL || g.mode == DPS_SLIT);
+      const bool top_img = (g.mode == DPS_SLIT);
+      for (int i = 0; i < g.lzc; ++i) {
+        T v = (T)0;
+        if (i < cnt) {
+          const double zz = zc[c0 + i];
+          double acc = (double)es_t<T>(zz - z, k);
+          if (bottom_img) acc -= (double)es_t<T>(zz - (2.0 * g.zmin - z), k);
+          if (top_img) acc -= (double)es_t<T>(zz - (2.0 * g.zmax - z), k);
+          v = (T)acc;
+        }
+        ph[2 * g.pxc + i] = v;
+      }
+      if (cnt > 0) {
+        cmin = min(cmin, c0);
+        cmax = max(cmax, c0 + cnt - 1);
+      }
+    } else {
+      for (int i = 0; i < stride; ++i) ph[i] = (T)0;
+    }
+    reinterpret_cast<int4*>(r)[K] = hd;
+  }
+  if (g.nkernels == 1) reinterpret_cast<int4*>(r)[1] = make_int4(0, 0, 0, 0);
+  int bx = 0, by = 0;
+  if (ok) {
+    bx = min((int)floor(xw * g.inv_h) / kTileX, g.nbx - 1);
+    by = min((int)floor(yw * g.inv_h) / kTileY, g.nby - 1);
+  }
+  const int b = by * g.nbx + bx;
+  bin_of[j] = b;
+  atomicAdd(&bin_count[b], 1);
+  if (cmax >= 0) {
+    atomicMin(&zrange[0], cmin);
+    atomicMax(&zrange[1], cmax);
+  }
+}
+
+// exclusive scan of bin counts (one block; bins handled in contiguous chunks per thread)
+__global__ void bin_scan_kernel(const int* __restrict__ count, int* __restrict__ start,
+                                int* __restrict__ cursor, int nbins) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int per = (nbins + blockDim.x - 1) / blockDim.x;
+  const int b0 = t * per, b1 = min(nbins, b0 + per);
+  int s = 0;
+  for (int b = b0; b < b1; ++b) s += count[b];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const int v = (t >= off) ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - s;
+  for (int b = b0; b < b1; ++b) {
+    start[b] = run;
+    cursor[b] = run;
+    run += count[b];
+  }
+  if (t == blockDim.x - 1) start[nbins] = part[t];
+}
+
+__global__ void bin_scatter_kernel(int64_t n, const int* __restrict__ bin_of, int* __restrict__ cursor,
+                                   int* __restrict__ sorted) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int p = atomicAdd(&cursor[bin_of[j]], 1);
+  sorted[p] = (int)j;
+}
+
+// does the cyclic node interval [a, a+len_a) intersect [b, b+len_b) (mod n)?
+__device__ __forceinline__ bool cyc_overlap(int a, int len_a, int b, int len_b, int n) {
+  int d1 = b - a; if (d1 < 0) d1 += n;
+  int d2 = a - b; if (d2 < 0) d2 += n;
+  return d1 < len_a || d2 < len_b;
+}
+
+constexpr int kCandCap = 2048;
+
+template <typename T, int NF, int ZC>
+__global__ void __launch_bounds__(kSpreadThreads)
+spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
+              const int* __restrict__ sorted, const int* __restrict__ zrange, T* __restrict__ grid) {
+  __shared__ int s_bins[64];
+  __shared__ int s_pref[65];
+  __shared__ int s_nb;
+  __shared__ int s_cand[kCandCap];
+  __shared__ int s_warp[kSpreadThreads / 32];
+  const int clo = zrange[0], chi = zrange[1];
+  if (chi < clo) return;
+  const int bx = blockIdx.x % g.nbx, by = blockIdx.x / g.nbx;
+  const int tx0 = bx * kTileX, ty0 = by * kTileY;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gx = tx0 + (tid % kTileX), gy = ty0 + (tid / kTileX);
+  const bool active = (gx < g.nx) && (gy < g.ny);
+  const int tw = min(kTileX, g.nx - tx0), th = min(kTileY, g.ny - ty0);
+  if (tid == 0) {
+    int nb = 0;
+    for (int dy = -g.rby; dy <= g.rby; ++dy) {
+      for (int dx = -g.rbx; dx <= g.rbx; ++dx) {
+        const int b = wrap_idx(by + dy, g.nby) * g.nbx + wrap_idx(bx + dx, g.nbx);
+        bool dup = false;
+        for (int i = 0; i < nb; ++i) dup = dup || (s_bins[i] == b);
+        if (!dup && nb < 64) s_bins[nb++] = b;
+      }
+    }
+    s_nb = nb;
+    int acc = 0;
+    for (int i = 0; i < nb; ++i) {
+      s_pref[i] = acc;
+      acc += bin_start[s_bins[i] + 1] - bin_start[s_bins[i]];
+    }
+    s_pref[nb] = acc;
+  }
+  __syncthreads();
+  const int nb = s_nb;
+  const int total = s_pref[nb];
+  const size_t plane = (size_t)g.ny * 2 * g.pitch;          // T values per z plane (real rows)
+  const size_t fstride = plane * g.nz;
+  const size_t node = (size_t)gy * 2 * g.pitch + gx;
+  const int stride = 2 * g.pxc + g.lzc;
+  // rounds over windows of kCandCap passing candidates (one round unless the tile is crowded)
+  for (int round = 0;; ++round) {
+    const int win0 = round * kCandCap, win1 = win0 + kCandCap;
+    int passed = 0;  // passing candidates seen so far (uniform)
+    for (int e0 = 0; e0 < total; e0 += kSpreadThreads) {
+      const int e = e0 + tid;
+      bool pass = false;
+      int j = 0;
+      if (e < total) {
+        int b = 0;
+        while (b + 1 < nb && s_pref[b + 1] <= e) ++b;
+        j = sorted[bin_start[s_bins[b]] + (e - s_pref[b])];
+        const uint32_t* r = rec + (size_t)j * g.rec_words;
+        for (int K = 0; K < g.nkernels; ++K) {
+          const int4 hd = reinterpret_cast<const int4*>(r)[K];
+          const int px = (K == 0) ? g.kM.px : g.kD.px;
+          if (hd.w > 0 && cyc_overlap(hd.x, px, tx0, tw, g.nx) && cyc_overlap(hd.y, px, ty0, th, g.ny))
+            pass = true;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (lane == 0) s_warp[warp] = __popc(m);
+      __syncthreads();
+      int woff = 0, btot = 0;
+      for (int w = 0; w < kSpreadThreads / 32; ++w) {
+        if (w < warp) woff += s_warp[w];
+        btot += s_warp[w];
+      }
+      const int rank = passed + woff + __popc(m & ((1u << lane) - 1u));
+      if (pass && rank >= win0 && rank < win1) s_cand[rank - win0] = j;
+      passed += btot;
+      __syncthreads();
+    }
+    const int ncand = min(passed, win1) - win0;
+    if (ncand <= 0 && round > 0) break;
+    for (int zb = clo; zb <= chi; zb += ZC) {
+      T acc[ZC][NF];
+#pragma unroll
+      for (int zz = 0; zz < ZC; ++zz)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          T v = (T)0;
+          if (round > 0 && active && zb + zz <= chi) v = grid[f * fstride + (size_t)(zb + zz) * plane + node];
+          acc[zz][f] = v;
+        }
+      if (active) {
+        for (int i = 0; i < ncand; ++i) {
+          const uint32_t* r = rec + (size_t)s_cand[i] * g.rec_words;
+          const T* tv = reinterpret_cast<const T*>(r + 8);
+#pragma unroll
+          for (int K = 0; K < NF / 3; ++K) {
+            const int4 hd = reinterpret_cast<const int4*>(r)[K];
+            const int px = (K == 0) ? g.kM.px : g.kD.px;
+            int dx = gx - hd.x; if (dx < 0) dx += g.nx;
+            int dy = gy - hd.y; if (dy < 0) dy += g.ny;
+            if (dx < px && dy < px) {
+              const T* ph = tv + 6 + K * stride;
+              const T wxy = ph[dx] * ph[g.pxc + dy];
+              const T f0 = tv[3 * K], f1 = tv[3 * K + 1], f2 = tv[3 * K + 2];
+#pragma unroll
+              for (int zz = 0; zz < ZC; ++zz) {
+                const int iz = zb + zz - hd.z;
+                if (iz >= 0 && iz < hd.w) {
+                  const T w = wxy * ph[2 * g.pxc + iz];
+                  acc[zz][3 * K] += f0 * w;
+                  acc[zz][3 * K + 1] += f1 * w;
+                  acc[zz][3 * K + 2] += f2 * w;
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int zz = 0; zz < ZC; ++zz) {
+          if (zb + zz <= chi) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) grid[f * fstride + (size_t)(zb + zz) * plane + node] = acc[zz][f];
+          }
+        }
+      }
+    }
+    if (passed <= win1) break;
+    __syncthreads();
+  }
+}
+
+template <typename T, int LR>
+__global__ void interp_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec,
+                              const T* __restrict__ grid, const T* __restrict__ wz,
+                              double* __restrict__ U, double* __restrict__ W) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= n) return;
+  const uint32_t* r = rec + (size_t)j * g.rec_words;
+  const T* tv = reinterpret_cast<const T*>(r + 8);
+  const int lx = lane % LR, grp = lane / LR;
+  constexpr int NG = 32 / LR;
+  const size_t rowlen = (size_t)2 * g.pitch;
+  const size_t plane = (size_t)g.ny * rowlen;
+  const size_t fstride = plane * g.nz;
+  const int stride = 2 * g.pxc + g.lzc;
+  const double h2 = g.h * g.h;
+  for (int K = 0; K < g.nkernels; ++K) {
+    const int4 hd = reinterpret_cast<const int4*>(r)[K];
+    const int px = (K == 0) ? g.kM.px : g.kD.px;
+    const T* ph = tv + 6 + K * stride;
+    const bool vx = lx < px;
+    int xi = hd.x + lx;
+    if (xi >= g.nx) xi -= g.nx;
+    const T phx = vx ? ph[lx] : (T)0;
+    T a0 = 0, a1 = 0, a2 = 0;
+    const int rows = hd.w * px;
+    const T* gbase = grid + (size_t)(3 * K) * fstride;
+    for (int rr = grp; rr < rows; rr += NG) {
+      const int iz = rr / px, iy = rr - iz * px;
+      const int c = hd.z + iz;
+      int yi = hd.y + iy;
+      if (yi >= g.ny) yi -= g.ny;
+      if (vx) {
+        const T w = ph[2 * g.pxc + iz] * wz[c] * ph[g.pxc + iy] * phx;
+        const size_t o = (size_t)c * plane + (size_t)yi * rowlen + xi;
+        a0 += gbase[o] * w;
+        a1 += gbase[fstride + o] * w;
+        a2 += gbase[2 * fstride + o] * w;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    }
+    double* out = (K == 0) ? U : W;
+    if (lane == 0) {
+      out[3 * j] = h2 * (double)a0;
+      out[3 * j + 1] = h2 * (double)a1;
+      out[3 * j + 2] = h2 * (double)a2;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_records(const Plan& p, int64_t n, const double* pos, const double* F, const double* Tq,
+                    cudaStream_t s) {
+  if (n <= 0) return;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  records_kernel<T><<<blocks, threads, 0, s>>>(p.g, n, pos, F, Tq, p.tab.zc, p.records, p.bin_of,
+                                               p.bin_count, p.zrange, p.status);
+}
+
+void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
+  const int nbins = p.g.nbx * p.g.nby;
+  bin_scan_kernel<<<1, 1024, 0, s>>>(p.bin_count, p.bin_start, p.bin_cursor, nbins);
+  if (n > 0) {
+    const int threads = 256;
+    bin_scatter_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(n, p.bin_of, p.bin_cursor,
+                                                                                  p.sorted);
+  }
+}
+
+template <typename T>
+void launch_spread(const Plan& p, cudaStream_t s) {
+  const unsigned blocks = (unsigned)(p.g.nbx * p.g.nby);
+  constexpr int ZC = sizeof(T) == 4 ? 8 : 4;
+  if (p.g.nfields == 6)
+    spread_kernel<T, 6, ZC><<<blocks, kSpreadThreads, 0, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                              reinterpret_cast<T*>(p.grid));
+  else
+    spread_kernel<T, 3, ZC><<<blocks, kSpreadThreads, 0, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                              reinterpret_cast<T*>(p.grid));
+}
+
+template <typename T>
+void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s) {
+  if (n <= 0) return;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n * 32 + threads - 1) / threads);
+  if (p.g.pxc <= 8)
+    interp_kernel<T, 8><<<blocks, threads, 0, s>>>(p.g, n, p.records, reinterpret_cast<const T*>(p.grid),
+                                                   reinterpret_cast<const T*>(p.tab.wz), U, W);
+  else
+    interp_kernel<T, 16><<<blocks, threads, 0, s>>>(p.g, n, p.records, reinterpret_cast<const T*>(p.grid),
+                                                    reinterpret_cast<const T*>(p.tab.wz), U, W);
+}
+
+template void launch_records<float>(const Plan&, int64_t, const double*, const double*, const double*, cudaStream_t);
+template void launch_records<double>(const Plan&, int64_t, const double*, const double*, const double*, cudaStream_t);
+template void launch_spread<float>(const Plan&, cudaStream_t);
+template void launch_spread<double>(const Plan&, cudaStream_t);
+template void launch_interp<float>(const Plan&, int64_t, double*, double*, cudaStream_t);
+template void launch_interp<double>(const Plan&, int64_t, double*, double*, cudaStream_t);
+
+}  // namespace dps

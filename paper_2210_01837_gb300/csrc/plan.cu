@@ -1,0 +1,458 @@
+// Host side of the library: plan construction (validation, tables, device buffers), the apply
+// pipeline (steps 1-8 of Sec. III.D enqueued on one stream) and the C ABI of include/dpstokes.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "dps_internal.cuh"
+
+namespace dps {
+namespace {
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n (three-term recurrence).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      // p1 = P_n(z), p0 = P_{n-1}(z)
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// integral of exp(beta (sqrt(1 - (t/alpha)^2) - 1)) over [-alpha, alpha]; t = alpha sin(theta)
+double es_norm(double alpha, double beta) {
+  std::vector<double> x, w;
+  gauss_legendre(128, x, w);
+  double s = 0.0;
+  for (size_t i = 0; i < x.size(); ++i) {
+    const double th = 0.5 * M_PI * x[i];
+    s += w[i] * exp(beta * (cos(th) - 1.0)) * cos(th);
+  }
+  return alpha * 0.5 * M_PI * s;
+}
+
+bool smooth_7(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+bool fft_plan(int n, FftPlan& fp) {
+  fp.n = n;
+  fp.nstages = 0;
+  int m = n;
+  while (m % 8 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 8; m /= 8; }
+  while (m % 4 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 4; m /= 4; }
+  while (m % 2 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 2; m /= 2; }
+  for (int p : {3, 5, 7})
+    while (m % p == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = p; m /= p; }
+  return m == 1;
+}
+
+template <typename T>
+cudaError_t upload(void** dst, const std::vector<double>& v, int64_t& bytes) {
+  std::vector<T> h(v.begin(), v.end());
+  cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, h.size() * sizeof(T)));
+  if (e != cudaSuccess) return e;
+  bytes += (int64_t)(h.size() * sizeof(T));
+  return cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+cudaError_t upload_twiddles(void** dst, int n, int64_t& bytes) {
+  std::vector<T> h(2 * (size_t)n);
+  for (int t = 0; t < n; ++t) {
+    // exp(-2 pi i t / n), argument reduced to t/n in [0, 1)
+    const double a = -2.0 * M_PI * (double)t / (double)n;
+    h[2 * t] = (T)cos(a);
+    h[2 * t + 1] = (T)sin(a);
+  }
+  cudaError_t e = cudaMalloc(dst, h.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  bytes += (int64_t)(h.size() * sizeof(T));
+  return cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+__global__ void apply_init_kernel(int* zrange, int nz, int* bin_count, int nbins) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    zrange[0] = nz;
+    zrange[1] = -1;
+  }
+  for (int b = i; b < nbins; b += gridDim.x * blockDim.x) bin_count[b] = 0;
+}
+
+void free_plan(Plan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.dct, p->tab.dctd, p->tab.idct, p->tab.zeta, p->tab.band,
+                  p->tab.twx, p->tab.twy, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
+                  p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+template <typename T>
+dps_status build_tables(Plan* p) {
+  const Geometry& g = p->g;
+  const int N = g.nz;
+  const int n1 = N - 1;
+  int64_t& bytes = p->device_bytes;
+  // Chebyshev extrema nodes, c = 0 at zmax
+  std::vector<double> zc(N), zeta(N);
+  for (int c = 0; c < N; ++c) {
+    zc[c] = g.zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / n1));
+    zeta[c] = zc[c] - g.zmin;
+  }
+  // forward DCT-I: a_n = (2/n1) sum'' g_c cos(pi n c / n1), a_0 and a_n1 halved
+  std::vector<double> C((size_t)N * N), IC((size_t)N * N), DC((size_t)N * N, 0.0);
+  for (int n = 0; n < N; ++n)
+    for (int c = 0; c < N; ++c) {
+      const double cs = cos(M_PI * (double)((int64_t)n * c % (2 * n1)) / n1);
+      double v = 2.0 / n1 * cs;
+      if (c == 0 || c == n1) v *= 0.5;
+      if (n == 0 || n == n1) v *= 0.5;
+      C[(size_t)n * N + c] = v;
+      IC[(size_t)c * N + n] = cs;
+    }
+  // Chebyshev derivative of each column of C by the recurrence b_n = b_{n+2} + 2 (n+1) a_{n+1},
+  // b_0 halved; times 2/H
+  for (int c = 0; c < N; ++c) {
+    std::vector<double> b(N + 2, 0.0);
+    for (int n = N - 2; n >= 0; --n) b[n] = b[n + 2] + 2.0 * (n + 1) * C[(size_t)(n + 1) * N + c];
+    b[0] *= 0.5;
+    for (int n = 0; n < N; ++n) DC[(size_t)n * N + c] = (2.0 / g.H) * b[n];
+  }
+  // Clenshaw-Curtis weights: integral of the interpolant, w = C^T I, I_n = 2/(1-n^2) (n even)
+  std::vector<double> wz(N, 0.0);
+  for (int c = 0; c < N; ++c) {
+    double s = 0.0;
+    for (int n = 0; n < N; n += 2) s += C[(size_t)n * N + c] * 2.0 / (1.0 - (double)n * n);
+    wz[c] = 0.5 * g.H * s;
+  }
+  // banded spectral-integration operator: (B B c)_m = l_m c_{m-2} + d_m c_m + u_m c_{m+2}
+  std::vector<double> band(5 * (size_t)N, 0.0);
+  double* l = band.data();
+  double* d = l + N;
+  double* u = d + N;
+  double* P = u + N;
+  double* Q = P + N;
+  for (int m = 1; m < N; ++m) {
+    if (m == 1) { l[m] = 0.0; d[m] = -1.0 / 8.0; u[m] = 1.0 / 8.0; }
+    else if (m == 2) { l[m] = 0.25; d[m] = -1.0 / 6.0; u[m] = 1.0 / 24.0; }
+    else { l[m] = 1.0 / (4.0 * m * (m - 1)); d[m] = -1.0 / (2.0 * ((double)m * m - 1.0)); u[m] = 1.0 / (4.0 * m * (m + 1)); }
+    if (m + 2 >= N) u[m] = 0.0;
+  }
+  // column sums: Q_j = sum_m BB[m][j], P_j = sum_m m^2 BB[m][j]
+  for (int j = 0; j < N; ++j) {
+    double q = d[j], pp = (double)j * j * d[j];
+    if (j + 2 < N) { q += l[j + 2]; pp += (double)(j + 2) * (j + 2) * l[j + 2]; }
+    if (j - 2 >= 0) { q += u[j - 2]; pp += (double)(j - 2) * (j - 2) * u[j - 2]; }
+    Q[j] = q;
+    P[j] = pp;
+  }
+  cudaError_t e = cudaSuccess;
+  if ((e = upload<double>((void**)&p->tab.zc, zc, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<double>((void**)&p->tab.band, band, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->tab.wz, wz, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->tab.dct, C, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->tab.dctd, DC, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->tab.idct, IC, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->tab.zeta, zeta, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload_twiddles<T>(&p->tab.twx, g.nx, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload_twiddles<T>(&p->tab.twy, g.ny, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  return DPS_OK;
+}
+
+template <typename T>
+dps_status allocate(Plan* p) {
+  Geometry& g = p->g;
+  int64_t& bytes = p->device_bytes;
+  auto alloc = [&](void** q, size_t sz) -> bool {
+    if (cudaMalloc(q, std::max<size_t>(sz, 16)) != cudaSuccess) return false;
+    bytes += (int64_t)sz;
+    return true;
+  };
+  const size_t nmax = (size_t)std::max<int64_t>(p->max_n, 1);
+  const int nbins = g.nbx * g.nby;
+  if (!alloc(&p->grid, (size_t)g.nfields * g.nz * g.ny * g.pitch * sizeof(cplx<T>))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->records, nmax * g.rec_words * sizeof(uint32_t))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->bin_of, nmax * sizeof(int))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->sorted, nmax * sizeof(int))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->bin_count, (size_t)nbins * sizeof(int))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->bin_start, (size_t)(nbins + 1) * sizeof(int))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->bin_cursor, (size_t)nbins * sizeof(int))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->zrange, 2 * sizeof(int))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->status, sizeof(int))) return DPS_ERR_OOM;
+  if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return DPS_ERR_CUDA;
+  p->bvp_blocks = bvp_occupancy_blocks<T>(*p);
+  const int64_t K = (int64_t)g.nkx * g.ny;
+  const int64_t need_blocks = (K + kBvpThreads - 1) / kBvpThreads;
+  if (p->bvp_blocks > need_blocks) p->bvp_blocks = (int)std::max<int64_t>(1, need_blocks);
+  p->ws_bytes = (int64_t)p->bvp_blocks * kBvpThreads * (int64_t)bvp_slot_bytes<T>(*p);
+  if (!alloc(&p->ws, (size_t)p->ws_bytes)) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->stage_in, nmax * 9 * sizeof(double))) return DPS_ERR_OOM;
+  if (!alloc((void**)&p->stage_out, nmax * 6 * sizeof(double))) return DPS_ERR_OOM;
+  if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
+  return DPS_OK;
+}
+
+template <typename T>
+void enqueue(const Plan& p, int64_t n, const double* pos, const double* F, const double* Tq, double* U,
+             double* W, cudaStream_t s, int last_stage) {
+  const int nbins = p.g.nbx * p.g.nby;
+  apply_init_kernel<<<std::min(1024, (nbins + 255) / 256 + 1), 256, 0, s>>>(p.zrange, p.g.nz, p.bin_count, nbins);
+  launch_records<T>(p, n, pos, F, Tq, s);
+  if (last_stage <= 1) return;
+  launch_bins(p, n, s);
+  launch_spread<T>(p, s);
+  if (last_stage <= 2) return;
+  launch_fft_forward<T>(p, s);
+  if (last_stage <= 3) return;
+  launch_bvp<T>(p, s);
+  if (last_stage <= 4) return;
+  launch_fft_inverse<T>(p, s);
+  if (last_stage <= 5) return;
+  launch_interp<T>(p, n, U, W, s);
+}
+
+dps_status check_apply_args(const Plan* p, int64_t n, const double* pos, const double* F, const double* Tq,
+                            const double* U, const double* W) {
+  if (!p || n < 0 || n > p->max_n) return DPS_ERR_INVALID_ARG;
+  if (n > 0 && (!pos || !F || !U)) return DPS_ERR_INVALID_ARG;
+  if (p->g.with_torque) {
+    if (n > 0 && (!Tq || !W)) return DPS_ERR_INVALID_ARG;
+  } else if (Tq || W) {
+    return DPS_ERR_INVALID_ARG;
+  }
+  return DPS_OK;
+}
+
+dps_status run(Plan* p, int64_t n, const double* pos, const double* F, const double* Tq, double* U, double* W,
+               cudaStream_t s, int last_stage) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) cudaSetDevice(p->device);
+  if (p->precision == DPS_MIXED)
+    enqueue<float>(*p, n, pos, F, Tq, U, W, s, last_stage);
+  else
+    enqueue<double>(*p, n, pos, F, Tq, U, W, s, last_stage);
+  const cudaError_t e = cudaGetLastError();
+  if (dev != p->device && dev >= 0) cudaSetDevice(dev);
+  return e == cudaSuccess ? DPS_OK : DPS_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace dps
+
+using dps::Plan;
+
+extern "C" {
+
+const char* dpstokes_error_string(dps_status st) {
+  switch (st) {
+    case DPS_OK: return "ok";
+    case DPS_ERR_INVALID_ARG: return "invalid argument";
+    case DPS_ERR_OUT_OF_DOMAIN: return "particle height outside the domain or envelope through an open boundary";
+    case DPS_ERR_OOM: return "device allocation failed";
+    case DPS_ERR_CUDA: return "CUDA runtime error";
+    case DPS_ERR_TIMEOUT: return "bounded device wait expired";
+    case DPS_ERR_NONFINITE: return "non-finite input";
+  }
+  return "unknown status";
+}
+
+dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zmin, double zmax, int32_t wall_mode,
+                                const dps_grid* grid, const dps_kernel_params* kp) {
+  if (!out) return DPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!grid || !kp) return DPS_ERR_INVALID_ARG;
+  if (!(Lx > 0) || !(Ly > 0) || !(zmax > zmin) || !isfinite(Lx) || !isfinite(Ly) || !isfinite(zmin) || !isfinite(zmax))
+    return DPS_ERR_INVALID_ARG;
+  if (wall_mode < DPS_FREE || wall_mode > DPS_SLIT) return DPS_ERR_INVALID_ARG;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  if (nx < 8 || ny < 8 || nz < 5 || nz > 257 || !dps::smooth_7(nx) || !dps::smooth_7(ny)) return DPS_ERR_INVALID_ARG;
+  const double hx = Lx / nx, hy = Ly / ny;
+  if (fabs(hx - hy) > 1e-12 * hx) return DPS_ERR_INVALID_ARG;
+  if (kp->precision != DPS_FP64 && kp->precision != DPS_MIXED) return DPS_ERR_INVALID_ARG;
+  if (kp->max_n < 0 || kp->max_n > (int64_t)1 << 30) return DPS_ERR_INVALID_ARG;
+  if (!(kp->eta > 0) || !isfinite(kp->eta)) return DPS_ERR_INVALID_ARG;
+  const bool torque = kp->with_torque != 0;
+  auto bad_kernel = [&](int m, double beta) {
+    return m < 2 || m > dps::kMaxM || !(beta > 0) || !isfinite(beta) || m + 1 > nx / 2 || m + 1 > ny / 2;
+  };
+  if (bad_kernel(kp->m_M, kp->beta_M)) return DPS_ERR_INVALID_ARG;
+  if (torque && bad_kernel(kp->m_D, kp->beta_D)) return DPS_ERR_INVALID_ARG;
+
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return DPS_ERR_OOM;
+  memset(p, 0, sizeof(Plan));
+  cudaGetDevice(&p->device);
+  p->precision = kp->precision;
+  p->max_n = kp->max_n;
+  dps::Geometry& g = p->g;
+  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin;
+  g.h = hx; g.inv_h = 1.0 / hx; g.eta = kp->eta; g.mode = wall_mode;
+  g.nx = nx; g.ny = ny; g.nz = nz; g.nkx = nx / 2 + 1;
+  g.pitch = (g.nkx + 31) / 32 * 32;
+  g.with_torque = torque ? 1 : 0;
+  g.nfields = torque ? 6 : 3;
+  g.nkernels = torque ? 2 : 1;
+  auto setk = [&](dps::EsKernel& k, int m, double beta) {
+    k.alpha = 0.5 * m * hx;
+    k.beta = beta;
+    k.inv_norm = 1.0 / dps::es_norm(k.alpha, beta);
+    k.px = m + 1;
+  };
+  setk(g.kM, kp->m_M, kp->beta_M);
+  if (torque) setk(g.kD, kp->m_D, kp->beta_D); else g.kD = g.kM;
+  const double amax = std::max(g.kM.alpha, torque ? g.kD.alpha : 0.0);
+  if (wall_mode == DPS_SLIT && g.H < 2.0 * amax) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
+  if (wall_mode == DPS_FREE && g.H <= 2.0 * amax) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
+  g.pxc = std::max(g.kM.px, torque ? g.kD.px : 0);
+  // z slots: most Chebyshev nodes inside any closed window of length 2 alpha (plus margin)
+  {
+    int best = 0;
+    for (int c = 0; c < nz; ++c) {
+      const double zc0 = zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / (nz - 1)));
+      int cnt = 0;
+      for (int q = 0; q < nz; ++q) {
+        const double zq = zmin + 0.5 * g.H * (1.0 + cos(M_PI * q / (nz - 1)));
+        if (zq <= zc0 && zq >= zc0 - 2.0 * amax * (1.0 + 1e-9) - 1e-12 * g.H) ++cnt;
+      }
+      best = std::max(best, cnt);
+    }
+    g.lzc = std::min(nz, best + 2);
+  }
+  const int tsize = (p->precision == DPS_FP64) ? 2 : 1;  // 32-bit words per stored value
+  const int tvals = 6 + g.nkernels * (2 * g.pxc + g.lzc);
+  g.rec_words = (8 + tvals * tsize + 3) / 4 * 4;
+  g.nbx = (nx + dps::kTileX - 1) / dps::kTileX;
+  g.nby = (ny + dps::kTileY - 1) / dps::kTileY;
+  g.rbx = (g.pxc + dps::kTileX - 1) / dps::kTileX + ((nx % dps::kTileX) ? 1 : 0);
+  g.rby = (g.pxc + dps::kTileY - 1) / dps::kTileY + ((ny % dps::kTileY) ? 1 : 0);
+  if ((2 * g.rbx + 1) * (2 * g.rby + 1) > 64) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
+  if (!dps::fft_plan(nx, p->fx) || !dps::fft_plan(ny, p->fy)) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
+  dps_status st = (p->precision == DPS_MIXED) ? dps::build_tables<float>(p) : dps::build_tables<double>(p);
+  if (st == DPS_OK) st = (p->precision == DPS_MIXED) ? dps::allocate<float>(p) : dps::allocate<double>(p);
+  if (st != DPS_OK) { dps::free_plan(p); cudaGetLastError(); return st; }
+  if (cudaDeviceSynchronize() != cudaSuccess) { dps::free_plan(p); cudaGetLastError(); return DPS_ERR_CUDA; }
+  *out = reinterpret_cast<dps_plan_t>(p);
+  return DPS_OK;
+}
+
+dps_status dpstokes_apply(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
+                          const double* torques, double* out_vel, double* out_angvel, void* stream) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  const dps_status st = dps::check_apply_args(p, n, positions, forces, torques, out_vel, out_angvel);
+  if (st != DPS_OK) return st;
+  return dps::run(p, n, positions, forces, torques, out_vel, out_angvel, (cudaStream_t)stream, 99);
+}
+
+dps_status dpstokes_apply_host(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
+                               const double* torques, double* out_vel, double* out_angvel, void* stream) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  dps_status st = dps::check_apply_args(p, n, positions, forces, torques, out_vel, out_angvel);
+  if (st != DPS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* dpos = p->stage_in;
+  double* dF = dpos + 3 * (size_t)p->max_n;
+  double* dT = p->g.with_torque ? dF + 3 * (size_t)p->max_n : nullptr;
+  double* dU = p->stage_out;
+  double* dW = p->g.with_torque ? dU + 3 * (size_t)p->max_n : nullptr;
+  const size_t b = 3 * (size_t)n * sizeof(double);
+  if (n > 0) {
+    if (cudaMemcpyAsync(dpos, positions, b, cudaMemcpyHostToDevice, s) != cudaSuccess) return DPS_ERR_CUDA;
+    if (cudaMemcpyAsync(dF, forces, b, cudaMemcpyHostToDevice, s) != cudaSuccess) return DPS_ERR_CUDA;
+    if (dT && cudaMemcpyAsync(dT, torques, b, cudaMemcpyHostToDevice, s) != cudaSuccess) return DPS_ERR_CUDA;
+  }
+  st = dps::run(p, n, dpos, dF, dT, dU, dW, s, 99);
+  if (st != DPS_OK) return st;
+  if (n > 0) {
+    if (cudaMemcpyAsync(out_vel, dU, b, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DPS_ERR_CUDA;
+    if (dW && cudaMemcpyAsync(out_angvel, dW, b, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DPS_ERR_CUDA;
+  }
+  return dpstokes_status(plan, stream);
+}
+
+dps_status dpstokes_status(dps_plan_t plan, void* stream) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p) return DPS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DPS_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DPS_ERR_CUDA;
+  if (v != 0 && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return DPS_ERR_CUDA;
+  if (v & dps::kStatNonfinite) return DPS_ERR_NONFINITE;
+  if (v & dps::kStatDomain) return DPS_ERR_OUT_OF_DOMAIN;
+  if (v & dps::kStatInternal) return DPS_ERR_CUDA;
+  return DPS_OK;
+}
+
+void dpstokes_destroy(dps_plan_t plan) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p) return;
+  cudaDeviceSynchronize();
+  dps::free_plan(p);
+}
+
+dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || !out) return DPS_ERR_INVALID_ARG;
+  out->device_bytes = p->device_bytes;
+  out->nkx = p->g.nkx;
+  out->pitch = p->g.pitch;
+  out->nfields = p->g.nfields;
+  out->record_words = p->g.rec_words;
+  out->h = p->g.h;
+  out->alpha_M = p->g.kM.alpha;
+  out->alpha_D = p->g.with_torque ? p->g.kD.alpha : 0.0;
+  return DPS_OK;
+}
+
+dps_status dpstokes_debug_run(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
+                              const double* torques, double* out_vel, double* out_angvel, void* stream,
+                              int32_t last_stage) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (last_stage < 1 || last_stage > 6) return DPS_ERR_INVALID_ARG;
+  const dps_status st = dps::check_apply_args(p, n, positions, forces, torques, out_vel, out_angvel);
+  if (st != DPS_OK) return st;
+  return dps::run(p, n, positions, forces, torques, out_vel, out_angvel, (cudaStream_t)stream, last_stage);
+}
+
+dps_status dpstokes_debug_copy(dps_plan_t plan, int32_t which, void* dst, int64_t dst_bytes, void* stream) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || !dst || dst_bytes < 0) return DPS_ERR_INVALID_ARG;
+  const size_t tsz = p->precision == DPS_MIXED ? sizeof(float) : sizeof(double);
+  const void* src = nullptr;
+  size_t sz = 0;
+  if (which == 0) { src = p->grid; sz = (size_t)p->g.nfields * p->g.nz * p->g.ny * p->g.pitch * 2 * tsz; }
+  else if (which == 1) { src = p->records; sz = (size_t)std::max<int64_t>(p->max_n, 1) * p->g.rec_words * 4; }
+  else if (which == 2) { src = p->zrange; sz = 2 * sizeof(int); }
+  else return DPS_ERR_INVALID_ARG;
+  sz = std::min(sz, (size_t)dst_bytes);
+  if (cudaMemcpyAsync(dst, src, sz, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess) return DPS_ERR_CUDA;
+  return DPS_OK;
+}
+
+}  // extern "C"
