@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the doubly-periodic FCM mobility product on GB300.
+
+Workload (one "step" = one mobility product M [F; T] -> [U; Omega], every stage of the hot path):
+a sedimented layer of N = 2^20 microrollers above one no-slip wall, box 2048 x 2048 x [0, 8],
+heights max(|N(1.6, 0.3)|, 1.05), force (0, 0, -1) and torque (0, 1, 0) on every particle, grid
+3072^2 x 65 (h = 2/3), ES kernels m = 5 with the Table I shape parameters.  Inputs are synthetic and
+seeded (paper_2210_01837_gb300.workloads.rollers_1m).  The working set (15 GB of grid in mixed
+precision) is far larger than L2, so no explicit flush is needed between steps.
+
+Headline: products/s of the mixed-precision path (float transforms, FP64 banded solves); the
+all-FP64 path is timed on the same GPU and reported beside it, with the relative L2 difference of
+the two outputs.  Per-stage CUDA-event timings give the roofline of each kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank runs its own replica (independent systems, no collective on the
+data path: weak scaling); the max time over ranks is used and rank 0 prints one JSON line.
+--impl reference times the CPU oracle (the FP64 restatement under oracle/) on a bounded tile of the
+same workload, on the host cores, and extrapolates to products/s of the full workload.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mobility products/s at N=1M single wall (mixed vs FP64, same GPU); p99 served"
+LAUNCHES_PER_APPLY = 11
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk/SM x 2 flop x max SM clock
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic work per stage (bytes that must cross HBM once; FP64 flops of the banded solves)
+# ---------------------------------------------------------------------------------------------
+def algorithmic(params, n, zocc, tsize, rec_bytes):
+    nx, ny, nz = params["nx"], params["ny"], params["nz"]
+    nkx = nx // 2 + 1
+    F = 6
+    real = F * zocc * ny * nx * tsize
+    cpx = F * zocc * ny * nkx * 2 * tsize
+    K = nkx * ny
+    return {
+        "records": n * 9 * 8 + n * rec_bytes,
+        "spread": real + n * rec_bytes,
+        "fft_x_fwd": real + cpx,
+        "fft_y_fwd": 2 * cpx,
+        "bvp": 2 * cpx,
+        "fft_y_inv": 2 * cpx,
+        "fft_x_inv": cpx + real,
+        "interp": real + n * rec_bytes + n * 6 * 8,
+        "bvp_fp64_flops": K * 134 * nz,
+    }
+
+
+def occupied_planes(params, pos, alpha):
+    """Chebyshev planes within alpha of some particle or of its wall image (the planes the
+    library transforms); computed here only to size the algorithmic byte counts."""
+    nz = params["nz"]
+    c = np.arange(nz)
+    zc = params["zmin"] + 0.5 * (params["zmax"] - params["zmin"]) * (1 + np.cos(np.pi * c / (nz - 1)))
+    lo = max(params["zmin"], pos[:, 2].min() - alpha)
+    hi = min(params["zmax"], pos[:, 2].max() + alpha)
+    return int(np.count_nonzero((zc >= lo - 1e-12) & (zc <= hi + 1e-12)))
+
+
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle samples of this GPU during the timed region."""
+
+    FIELDS = ("uuid,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None, index=0):
+        self.proc = None
+        self.lines = []
+        self.uuid = uuid
+        self.index = index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [[p.strip() for p in line.split(",")] for line in self.lines]
+        rows = [r for r in rows if len(r) >= 10]
+        mine = [r for r in rows if self.uuid and r[0].lower() == self.uuid.lower()]
+        if not mine:
+            mine = [r for r in rows if r[1] == str(self.index)]
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in mine:
+            try:
+                sm.append(float(r[2]))
+                smax.append(float(r[3]))
+                power.append(float(r[4]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------------
+def cpu_oracle_tile(div, seed_offset=3):
+    """One oracle product on a 1/div^2-area tile of the roller workload; returns (seconds, n)."""
+    from oracle import Params, mobility
+    from paper_2210_01837_gb300.workloads import rollers_1m
+    params, pos, F, T = rollers_1m(n=(1 << 20) // (div * div), nxy=3072 // div, L=2048.0 / div,
+                                   seed_offset=seed_offset)
+    t0 = time.perf_counter()
+    mobility(Params(**params), pos, F, T)
+    return time.perf_counter() - t0, len(pos), params["nx"]
+
+
+def cpu_baseline(div=16):
+    """The oracle as it stands on the host, one thread, on a bounded tile; run in a child process
+    started with spawn so that no CUDA state is inherited."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "t, n, nx = bench.cpu_oracle_tile(%d); print(json.dumps([t, n, nx]))" % (ROOT, div))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    t, n, nx = json.loads(r.stdout.strip().splitlines()[-1])
+    scale = div * div
+    return {"value": 1.0 / (t * scale), "unit": "products/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle (numpy FP64) on a 1/{scale}-area tile of the same workload (N={n}, {nx}^2x65, "
+                      f"same density, heights, h, kernels): {t:.1f} s; time x {scale} extrapolated to the full "
+                      f"product (work is linear in N and in grid nodes; the FFT log factor is ignored)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    div = 32
+    for _ in range(args.warmup):
+        cpu_oracle_tile(div)
+    times = []
+    n = nx = 0
+    for _ in range(args.steps):
+        t, n, nx = cpu_oracle_tile(div)
+        times.append(t)
+    t = float(np.mean(times)) * div * div
+    value = 1.0 / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "rollers_1m: N=1048576 above one wall, 3072^2x65, m=5 Table I",
+                      "sample": f"1/{div * div}-area tile per step (N={n}, {nx}^2x65), extrapolated"},
+           "cpu_baseline": {"value": value, "unit": "products/s", "cores": 1, "kind": "oracle",
+                            "sample": f"1/{div * div}-area tile of the roller workload per step, time x {div * div}"},
+           "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--div", type=int, default=1, help="shrink the workload by div^2 in area (testing only)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2210_01837_gb300 import binding, build
+    from paper_2210_01837_gb300.workloads import rollers_1m
+    build.build()
+    binding.load()
+
+    div = args.div
+    params, pos, F, T = rollers_1m(n=(1 << 20) // (div * div), nxy=3072 // div, L=2048.0 / div, seed_offset=3 + rank)
+    n = len(pos)
+    dev = torch.device("cuda", local)
+    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    d_pos, d_F, d_T = tdev(pos), tdev(F), tdev(T)
+    U = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    W = torch.empty_like(U)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def time_plan(plan, steps, warmup, stage_log=None):
+        for _ in range(warmup):
+            plan.apply(d_pos, d_F, d_T, U, W)
+        plan.check()
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.apply(d_pos, d_F, d_T, U, W)
+            if stage_log is not None:
+                stage_log.append(plan.stage_times())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        plan.check()
+        return e0.elapsed_time(e1) / 1e3
+
+    # ---- mixed precision (headline) --------------------------------------------------------
+    plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=n)
+    info = plan.info()
+    plan.enable_timing(True)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid=uuid, index=local)
+    stage_log = []
+    t_mixed = time_plan(plan, args.steps, args.warmup, stage_log)
+    clocks = sampler.stop()
+    t_mixed = max_over_ranks(t_mixed)
+    ms_step = t_mixed / args.steps * 1e3
+    value = world * args.steps / t_mixed
+    U_mixed = U.clone()
+    W_mixed = W.clone()
+
+    stages = {k: float(np.mean([s[k] for s in stage_log])) for k in stage_log[0]}
+    zocc = occupied_planes(params, pos, info.alpha_M)
+    hbm, peak_kind = peaks()
+    work = algorithmic(params, n, zocc, 4, info.record_words * 4)
+    stage_roof = {}
+    for k, ms in stages.items():
+        if k in work and k != "bvp":
+            gbs = work[k] / (ms * 1e-3) / 1e9
+            stage_roof[k] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3)}
+    bvp_tflops = work["bvp_fp64_flops"] / (stages["bvp"] * 1e-3) / 1e12
+    stage_roof["bvp"] = {"ms": round(stages["bvp"], 4), "fp64_TFLOP/s": round(bvp_tflops, 3),
+                         "frac_fp64_nominal": round(bvp_tflops / FP64_NOMINAL_TFLOPS, 3),
+                         "GB/s": round(work["bvp"] / (stages["bvp"] * 1e-3) / 1e9, 1)}
+    dom = max(stages, key=stages.get)
+    if dom == "bvp":
+        roofline = {"bound": "alu", "kernel": "bvp_kernel (FP64 banded solves)", "achieved": round(bvp_tflops, 4),
+                    "peak": round(FP64_NOMINAL_TFLOPS, 3), "unit": "TFLOP/s",
+                    "frac": round(bvp_tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                    "peak_kind": "FP64 nominal from unit counts x max clock"}
+    else:
+        gbs = work[dom] / (stages[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(gbs / hbm, 4), "traffic": None, "peak_kind": peak_kind}
+    plan.enable_timing(False)
+
+    # ---- end to end through the public API with host buffers -------------------------------
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_pos, h_F, h_T = pin(pos), pin(F), pin(T)
+    h_U = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    h_W = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    plan.apply_host(h_pos, h_F, h_T, h_U, h_W)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        plan.apply_host(h_pos, h_F, h_T, h_U, h_W)
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * e2e_steps / t_e2e, "unit": "products/s", "h2d_bytes_per_step": 3 * h_pos.nbytes,
+           "d2h_bytes_per_step": 2 * h_U.nbytes, "steps": e2e_steps}
+    plan.close()
+    del plan
+
+    # ---- all-FP64 path on the same GPU -------------------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = binding.Plan.from_params(params, with_torque=True, precision="fp64", max_n=n)
+        t64 = max_over_ranks(time_plan(plan64, args.fp64_steps, 1))
+        d = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        fp64 = {"value": world * args.fp64_steps / t64, "unit": "products/s",
+                "ms_per_step": t64 / args.fp64_steps * 1e3, "steps": args.fp64_steps,
+                "mixed_speedup": (world * args.steps / t_mixed) / (world * args.fp64_steps / t64),
+                "mixed_vs_fp64_rel_l2": {"U": d(U_mixed, U), "Omega": d(W_mixed, W)}}
+        plan64.close()
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+               "config": {"workload": "rollers_1m" if div == 1 else f"rollers_1m/{div * div}",
+                          "n": n, "grid": f"{params['nx']}x{params['ny']}x{params['nz']}", "wall": "bottom_wall",
+                          "box": f"{params['Lx']:g}x{params['Ly']:g}x[0,8]",
+                          "kernels": "ES m=5, beta_M=6.525, beta_D=11.16 (Table I)", "precision": "mixed",
+                          "occupied_planes": zocc, "l2": "working set >> L2 (no flush needed)",
+                          "parallelism": "replicas" if world > 1 else "1 GPU"},
+               "particles_per_s": value * n, "fp64": fp64, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+               "stage_roofline": stage_roof, "roofline": roofline, "e2e": e2e,
+               "gpu_launches": LAUNCHES_PER_APPLY * args.steps, "clocks": clocks}
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -125,9 +125,20 @@ typedef struct {
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 
+/* Per-stage timing.  With timing enabled, every apply records CUDA events on its stream between
+ * its kernels; dpstokes_stage_times() waits for the last apply to finish and writes the duration in
+ * milliseconds of each stage, in this order (DPS_NUM_STAGES values):
+ *   0 init, 1 particle records, 2 binning, 3 spread, 4 x-FFT forward, 5 y-FFT forward,
+ *   6 per-wavenumber solve, 7 y-FFT inverse, 8 x-FFT inverse, 9 interpolation.
+ * *count receives the number written (min(capacity, DPS_NUM_STAGES)); DPS_ERR_INVALID_ARG if no
+ * timed apply has been enqueued since timing was enabled. */
+#define DPS_NUM_STAGES 10
+dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable);
+dps_status dpstokes_stage_times(dps_plan_t plan, double* ms_out, int32_t capacity, int32_t* count);
+
 /* Diagnostics for tests: run the apply pipeline on `stream` up to and including stage
  * `last_stage` (1 = particle records, 2 = spread, 3 = forward xy FFT, 4 = per-k solve,
- * 5 = inverse xy FFT, 6 = interpolation) and copy plan buffer `which` (0 = grid/spectrum,
+ * 5 = inverse xy FFT, 6 = interpolation; the outputs may be NULL below stage 6) and copy plan buffer `which` (0 = grid/spectrum,
  * 1 = particle records, 2 = occupied plane range [2 x int32]) to the device pointer dst
  * (at most dst_bytes).  Returns DPS_ERR_INVALID_ARG for unknown stages or buffers. */
 dps_status dpstokes_debug_run(dps_plan_t plan, int64_t n, const double* positions,

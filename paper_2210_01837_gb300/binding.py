@@ -71,6 +71,8 @@ def load(path=None):
         "dpstokes_destroy": (None, [_P]),
         "dpstokes_error_string": (ctypes.c_char_p, [_I32]),
         "dpstokes_plan_info": (_I32, [_P, ctypes.POINTER(dps_plan_info)]),
+        "dpstokes_enable_timing": (_I32, [_P, _I32]),
+        "dpstokes_stage_times": (_I32, [_P, ctypes.POINTER(ctypes.c_double), _I32, ctypes.POINTER(_I32)]),
         "dpstokes_debug_run": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, _I32]),
         "dpstokes_debug_copy": (_I32, [_P, _I32, _P, _I64, _P]),
     }
@@ -118,6 +120,22 @@ def dpstokes_plan_info(plan):
     info = dps_plan_info()
     st = load().dpstokes_plan_info(plan, ctypes.byref(info))
     return st, info
+
+
+STAGES = ("init", "records", "bins", "spread", "fft_x_fwd", "fft_y_fwd", "bvp", "fft_y_inv", "fft_x_inv",
+          "interp")
+
+
+def dpstokes_enable_timing(plan, enable):
+    return load().dpstokes_enable_timing(plan, int(enable))
+
+
+def dpstokes_stage_times(plan):
+    """Returns (status, list of per-stage milliseconds of the last timed apply)."""
+    buf = (ctypes.c_double * len(STAGES))()
+    cnt = _I32(0)
+    st = load().dpstokes_stage_times(plan, buf, len(STAGES), ctypes.byref(cnt))
+    return st, list(buf)[: cnt.value]
 
 
 def dpstokes_debug_run(plan, n, positions, forces, torques, out_vel, out_angvel, stream, last_stage):
@@ -206,6 +224,17 @@ class Plan:
         st = self.status(stream)
         if st != DPS_OK:
             raise DpsError(st, "device status")
+
+    def enable_timing(self, enable=True):
+        st = dpstokes_enable_timing(self.handle, enable)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_enable_timing")
+
+    def stage_times(self):
+        st, ms = dpstokes_stage_times(self.handle)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_stage_times")
+        return dict(zip(STAGES, ms))
 
     def debug_run(self, pos, F, T, last_stage, U=None, W=None, stream=None):
         st = dpstokes_debug_run(self.handle, pos.shape[0], _ptr(pos), _ptr(F), _ptr(T), _ptr(U), _ptr(W),

@@ -110,6 +110,10 @@ struct Plan {
   double* stage_in;     // [max_n][9]
   double* stage_out;    // [max_n][6]
   int64_t device_bytes;
+  // per-stage timing (dpstokes_enable_timing)
+  int timing;
+  int timed_apply;
+  cudaEvent_t ev[DPS_NUM_STAGES + 1];
 };
 
 // status bits written by kernels
@@ -121,8 +125,8 @@ template <typename T> void launch_records(const Plan& p, int64_t n, const double
 void launch_bins(const Plan& p, int64_t n, cudaStream_t s);
 template <typename T> void launch_spread(const Plan& p, cudaStream_t s);
 template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s);
-template <typename T> void launch_fft_forward(const Plan& p, cudaStream_t s);
-template <typename T> void launch_fft_inverse(const Plan& p, cudaStream_t s);
+template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
+template <typename T> void launch_fft_cols(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_bvp(const Plan& p, cudaStream_t s);
 template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);

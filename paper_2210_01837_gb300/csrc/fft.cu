@@ -273,36 +273,35 @@ int fft_smem_ok(const Plan& p) {
 }
 
 template <typename T>
-void launch_fft_forward(const Plan& p, cudaStream_t s) {
+void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
-  const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   dim3 gr((g.ny + 1) / 2, g.nz, g.nfields);
-  row_r2c_kernel<T><<<gr, 256, 2 * g.nx * sizeof(cplx<T>), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
-  const int cw = col_width<T>(p);
-  dim3 gc((g.nkx + cw - 1) / cw, g.nz, g.nfields);
-  col_kernel<T, -1><<<gc, 512, 2 * (size_t)g.ny * cw * sizeof(cplx<T>), s>>>(
-      g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
+  const size_t sm = 2 * (size_t)g.nx * sizeof(cplx<T>);
+  if (dir < 0)
+    row_r2c_kernel<T><<<gr, 256, sm, s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
+  else
+    row_c2r_kernel<T><<<gr, 256, sm, s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
 }
 
 template <typename T>
-void launch_fft_inverse(const Plan& p, cudaStream_t s) {
+void launch_fft_cols(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
-  const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   const int cw = col_width<T>(p);
   dim3 gc((g.nkx + cw - 1) / cw, g.nz, g.nfields);
-  col_kernel<T, +1><<<gc, 512, 2 * (size_t)g.ny * cw * sizeof(cplx<T>), s>>>(
-      g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
-  dim3 gr((g.ny + 1) / 2, g.nz, g.nfields);
-  row_c2r_kernel<T><<<gr, 256, 2 * g.nx * sizeof(cplx<T>), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
+  const size_t sm = 2 * (size_t)g.ny * cw * sizeof(cplx<T>);
+  if (dir < 0)
+    col_kernel<T, -1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
+  else
+    col_kernel<T, +1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
 }
 
 template int fft_smem_ok<float>(const Plan&);
 template int fft_smem_ok<double>(const Plan&);
-template void launch_fft_forward<float>(const Plan&, cudaStream_t);
-template void launch_fft_forward<double>(const Plan&, cudaStream_t);
-template void launch_fft_inverse<float>(const Plan&, cudaStream_t);
-template void launch_fft_inverse<double>(const Plan&, cudaStream_t);
+template void launch_fft_rows<float>(const Plan&, int, cudaStream_t);
+template void launch_fft_rows<double>(const Plan&, int, cudaStream_t);
+template void launch_fft_cols<float>(const Plan&, int, cudaStream_t);
+template void launch_fft_cols<double>(const Plan&, int, cudaStream_t);
 
 }  // namespace dps

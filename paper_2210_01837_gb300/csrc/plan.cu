@@ -104,6 +104,8 @@ __global__ void apply_init_kernel(int* zrange, int nz, int* bin_count, int nbins
 
 void free_plan(Plan* p) {
   if (!p) return;
+  for (int i = 0; i <= DPS_NUM_STAGES; ++i)
+    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.dct, p->tab.dctd, p->tab.idct, p->tab.zeta, p->tab.band,
                   p->tab.twx, p->tab.twy, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
                   p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
@@ -218,30 +220,49 @@ dps_status allocate(Plan* p) {
 }
 
 template <typename T>
-void enqueue(const Plan& p, int64_t n, const double* pos, const double* F, const double* Tq, double* U,
-             double* W, cudaStream_t s, int last_stage) {
+void enqueue(Plan& p, int64_t n, const double* pos, const double* F, const double* Tq, double* U, double* W,
+             cudaStream_t s, int last_stage) {
   const int nbins = p.g.nbx * p.g.nby;
+  const bool tm = p.timing != 0 && last_stage >= 6;
+  int e = 0;
+  auto mark = [&]() {
+    if (tm) cudaEventRecord(p.ev[e++], s);
+  };
+  mark();
   apply_init_kernel<<<std::min(1024, (nbins + 255) / 256 + 1), 256, 0, s>>>(p.zrange, p.g.nz, p.bin_count, nbins);
+  mark();
   launch_records<T>(p, n, pos, F, Tq, s);
+  mark();
   if (last_stage <= 1) return;
   launch_bins(p, n, s);
+  mark();
   launch_spread<T>(p, s);
+  mark();
   if (last_stage <= 2) return;
-  launch_fft_forward<T>(p, s);
+  launch_fft_rows<T>(p, -1, s);
+  mark();
+  launch_fft_cols<T>(p, -1, s);
+  mark();
   if (last_stage <= 3) return;
   launch_bvp<T>(p, s);
+  mark();
   if (last_stage <= 4) return;
-  launch_fft_inverse<T>(p, s);
+  launch_fft_cols<T>(p, +1, s);
+  mark();
+  launch_fft_rows<T>(p, +1, s);
+  mark();
   if (last_stage <= 5) return;
   launch_interp<T>(p, n, U, W, s);
+  mark();
+  if (tm) p.timed_apply = 1;
 }
 
 dps_status check_apply_args(const Plan* p, int64_t n, const double* pos, const double* F, const double* Tq,
-                            const double* U, const double* W) {
+                            const double* U, const double* W, bool need_out = true) {
   if (!p || n < 0 || n > p->max_n) return DPS_ERR_INVALID_ARG;
-  if (n > 0 && (!pos || !F || !U)) return DPS_ERR_INVALID_ARG;
+  if (n > 0 && (!pos || !F || (need_out && !U))) return DPS_ERR_INVALID_ARG;
   if (p->g.with_torque) {
-    if (n > 0 && (!Tq || !W)) return DPS_ERR_INVALID_ARG;
+    if (n > 0 && (!Tq || (need_out && !W))) return DPS_ERR_INVALID_ARG;
   } else if (Tq || W) {
     return DPS_ERR_INVALID_ARG;
   }
@@ -430,12 +451,38 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   return DPS_OK;
 }
 
+dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p) return DPS_ERR_INVALID_ARG;
+  if (enable && !p->ev[0]) {
+    for (int i = 0; i <= DPS_NUM_STAGES; ++i)
+      if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return DPS_ERR_CUDA;
+  }
+  p->timing = enable ? 1 : 0;
+  p->timed_apply = 0;
+  return DPS_OK;
+}
+
+dps_status dpstokes_stage_times(dps_plan_t plan, double* ms_out, int32_t capacity, int32_t* count) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || !ms_out || capacity < 0 || !p->timing || !p->timed_apply) return DPS_ERR_INVALID_ARG;
+  if (cudaEventSynchronize(p->ev[DPS_NUM_STAGES]) != cudaSuccess) return DPS_ERR_CUDA;
+  const int m = std::min<int>(capacity, DPS_NUM_STAGES);
+  for (int i = 0; i < m; ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]) != cudaSuccess) return DPS_ERR_CUDA;
+    ms_out[i] = ms;
+  }
+  if (count) *count = m;
+  return DPS_OK;
+}
+
 dps_status dpstokes_debug_run(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
                               const double* torques, double* out_vel, double* out_angvel, void* stream,
                               int32_t last_stage) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (last_stage < 1 || last_stage > 6) return DPS_ERR_INVALID_ARG;
-  const dps_status st = dps::check_apply_args(p, n, positions, forces, torques, out_vel, out_angvel);
+  const dps_status st = dps::check_apply_args(p, n, positions, forces, torques, out_vel, out_angvel, last_stage >= 6);
   if (st != DPS_OK) return st;
   return dps::run(p, n, positions, forces, torques, out_vel, out_angvel, (cudaStream_t)stream, last_stage);
 }
