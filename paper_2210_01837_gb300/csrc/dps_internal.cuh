@@ -77,13 +77,24 @@ struct Geometry {
 struct Tables {
   double* zc;      // [nz] node heights, c = 0 at zmax
   void* wz;        // [nz] T Clenshaw-Curtis weights (times h^2 is applied in interpolation)
-  void* dct;       // [nz][nz] T  forward DCT-I  C[n][c]
-  void* dctd;      // [nz][nz] T  (2/H) * Chebyshev derivative of the forward DCT-I
-  void* idct;      // [nz][nz] T  inverse DCT-I  IC[c][n]
   void* zeta;      // [nz] T  z_c - zmin
   double* band;    // [5][nz] doubles: l_n, d_n, u_n, P_n, Q_n of the spectral-integration operator
   void* twx;       // [nx] cplx<T>  exp(-2 pi i t / nx)
   void* twy;       // [ny] cplx<T>  exp(-2 pi i t / ny)
+};
+
+// per-wavenumber stage: transform tables (T, padded for vector loads) and buffers
+struct KTabs {
+  void* ct;        // [N][npad]  forward DCT-I, transposed: ct[c][n] = C[n][c]
+  void* dct;       // [N][npad]  (2/H) D C transposed
+  void* ict;       // [N][cpad]  inverse DCT-I transposed: ict[n][c] = IC[c][n]
+  void* icdt;      // [N][cpad]  (2/H) IC D transposed (derivative at the nodes from coefficients)
+  void* sdt;       // [N][cpad]  spectral differentiation at the nodes, transposed: sdt[j][c] = SD[c][j]
+  void* bandT;     // [3][N]     l, d, u of the B B map in T
+  void* kbuf;      // [3][N][K]  Chebyshev coefficients per wavenumber (forces, then DP velocity)
+  void* kaux;      // [12][K]    wall-correction amplitudes per wavenumber
+  int npad, cpad;
+  int fwd_smem, bwd_smem;
 };
 
 struct Plan {
@@ -93,6 +104,7 @@ struct Plan {
   Geometry g;
   FftPlan fx, fy;
   Tables tab;
+  KTabs kt;
   // device buffers
   void* grid;           // [nfields][nz][ny][pitch] cplx<T> (real rows: 2*pitch T)
   uint32_t* records;    // [max_n][rec_words]
@@ -129,6 +141,7 @@ template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t 
 template <typename T> void launch_fft_cols(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_bvp(const Plan& p, cudaStream_t s);
 template <typename T> int bvp_occupancy_blocks(const Plan& p);
+template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(const Plan& p);
 

@@ -19,17 +19,49 @@ namespace dps {
 
 namespace {
 
-// cos(2 pi m / R), sin(2 pi m / R)
-__device__ __constant__ double c_cos3[3] = {1.0, -0.5, -0.5};
-__device__ __constant__ double c_sin3[3] = {0.0, 0.86602540378443865, -0.86602540378443865};
-__device__ __constant__ double c_cos5[5] = {1.0, 0.30901699437494742, -0.80901699437494742, -0.80901699437494742,
-                                            0.30901699437494742};
-__device__ __constant__ double c_sin5[5] = {0.0, 0.95105651629515357, 0.58778525229247314, -0.58778525229247314,
-                                            -0.95105651629515357};
-__device__ __constant__ double c_cos7[7] = {1.0, 0.62348980185873353, -0.22252093395631440, -0.90096886790241913,
-                                            -0.90096886790241913, -0.22252093395631440, 0.62348980185873353};
-__device__ __constant__ double c_sin7[7] = {0.0, 0.78183148246802981, 0.97492791218182361, 0.43388373911755812,
-                                            -0.43388373911755812, -0.97492791218182361, -0.78183148246802981};
+// cos(2 pi m / R) and sin(2 pi m / R) as literals in the transform's own precision (no conversions
+// in the butterflies: on this GPU a float<->double conversion occupies the scarce FP64 pipe).  The
+// butterfly loops are fully unrolled, so m is a compile-time constant and the switches fold away.
+template <typename T, int R>
+__device__ __forceinline__ T root_cos(int m) {
+  if (R == 3) return m == 0 ? (T)1.0 : (T)-0.5;
+  if (R == 5) {
+    switch (m) {
+      case 0: return (T)1.0;
+      case 1: case 4: return (T)0.30901699437494742;
+      default: return (T)-0.80901699437494742;
+    }
+  }
+  switch (m) {
+    case 0: return (T)1.0;
+    case 1: case 6: return (T)0.62348980185873353;
+    case 2: case 5: return (T)-0.22252093395631440;
+    default: return (T)-0.90096886790241913;
+  }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ T root_sin(int m) {
+  if (R == 3) return m == 0 ? (T)0.0 : (m == 1 ? (T)0.86602540378443865 : (T)-0.86602540378443865);
+  if (R == 5) {
+    switch (m) {
+      case 0: return (T)0.0;
+      case 1: return (T)0.95105651629515357;
+      case 2: return (T)0.58778525229247314;
+      case 3: return (T)-0.58778525229247314;
+      default: return (T)-0.95105651629515357;
+    }
+  }
+  switch (m) {
+    case 0: return (T)0.0;
+    case 1: return (T)0.78183148246802981;
+    case 2: return (T)0.97492791218182361;
+    case 3: return (T)0.43388373911755812;
+    case 4: return (T)-0.43388373911755812;
+    case 5: return (T)-0.97492791218182361;
+    default: return (T)-0.78183148246802981;
+  }
+}
 
 template <typename T, int DIR>
 __device__ __forceinline__ cplx<T> rot_quarter(cplx<T> a) {
@@ -83,7 +115,7 @@ template <typename T, int DIR> struct Dft<T, 8, DIR> {
 };
 
 template <typename T, int R, int DIR>
-__device__ __forceinline__ void dft_direct(cplx<T>* v, const double* cs, const double* sn) {
+__device__ __forceinline__ void dft_direct(cplx<T>* v) {
   cplx<T> out[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) {
@@ -91,7 +123,7 @@ __device__ __forceinline__ void dft_direct(cplx<T>* v, const double* cs, const d
 #pragma unroll
     for (int r = 1; r < R; ++r) {
       const int m = (r * k) % R;
-      const cplx<T> w = mk<T>((T)cs[m], (T)(DIR * sn[m]));
+      const cplx<T> w = mk<T>(root_cos<T, R>(m), DIR > 0 ? root_sin<T, R>(m) : -root_sin<T, R>(m));
       acc = acc + v[r] * w;
     }
     out[k] = acc;
@@ -101,13 +133,13 @@ __device__ __forceinline__ void dft_direct(cplx<T>* v, const double* cs, const d
 }
 
 template <typename T, int DIR> struct Dft<T, 3, DIR> {
-  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 3, DIR>(v, c_cos3, c_sin3); }
+  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 3, DIR>(v); }
 };
 template <typename T, int DIR> struct Dft<T, 5, DIR> {
-  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 5, DIR>(v, c_cos5, c_sin5); }
+  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 5, DIR>(v); }
 };
 template <typename T, int DIR> struct Dft<T, 7, DIR> {
-  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 7, DIR>(v, c_cos7, c_sin7); }
+  static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 7, DIR>(v); }
 };
 
 // One Stockham stage over `batch` interleaved sequences (element e of sequence b at e*batch + b).

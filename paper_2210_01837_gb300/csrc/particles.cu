@@ -30,10 +30,11 @@ __device__ __forceinline__ double es_eval(double t, const EsKernel& k) {
 }
 
 __device__ __forceinline__ float es_eval_f(double t, const EsKernel& k) {
-  // argument relative to the support in double, the exponential in float
-  const double r = t / k.alpha;
-  if (fabs(r) > 1.0) return 0.0f;
-  const float q = (float)(1.0 - r * r);
+  // the offset t is formed in double by the caller (a difference of nearby large numbers); the
+  // rest runs in float (a division or a conversion in double occupies the scarce FP64 pipe)
+  const float r = (float)t * (float)(1.0 / k.alpha);
+  if (fabsf(r) > 1.0f) return 0.0f;
+  const float q = fmaxf(0.0f, 1.0f - r * r);
   return expf((float)k.beta * (sqrtf(q) - 1.0f)) * (float)k.inv_norm;
 }
 
@@ -134,10 +135,10 @@ __global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__
         T v = (T)0;
         if (i < cnt) {
           const double zz = zc[c0 + i];
-          double acc = (double)es_t<T>(zz - z, k);
-          if (bottom_img) acc -= (double)es_t<T>(zz - (2.0 * g.zmin - z), k);
-          if (top_img) acc -= (double)es_t<T>(zz - (2.0 * g.zmax - z), k);
-          v = (T)acc;
+          T acc = es_t<T>(zz - z, k);
+          if (bottom_img) acc -= es_t<T>(zz - (2.0 * g.zmin - z), k);
+          if (top_img) acc -= es_t<T>(zz - (2.0 * g.zmax - z), k);
+          v = acc;
         }
         ph[2 * g.pxc + i] = v;
       }
@@ -339,10 +340,11 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
 template <typename T, int LR>
 __global__ void interp_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec,
                               const T* __restrict__ grid, const T* __restrict__ wz,
-                              double* __restrict__ U, double* __restrict__ W) {
-  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                              const int* __restrict__ order, double* __restrict__ U, double* __restrict__ W) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (j >= n) return;
+  if (i >= n) return;
+  const int64_t j = order[i];  // particles in bin order
   const uint32_t* r = rec + (size_t)j * g.rec_words;
   const T* tv = reinterpret_cast<const T*>(r + 8);
   const int lx = lane % LR, grp = lane / LR;
@@ -432,10 +434,10 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
   const unsigned blocks = (unsigned)((n * 32 + threads - 1) / threads);
   if (p.g.pxc <= 8)
     interp_kernel<T, 8><<<blocks, threads, 0, s>>>(p.g, n, p.records, reinterpret_cast<const T*>(p.grid),
-                                                   reinterpret_cast<const T*>(p.tab.wz), U, W);
+                                                   reinterpret_cast<const T*>(p.tab.wz), p.sorted, U, W);
   else
     interp_kernel<T, 16><<<blocks, threads, 0, s>>>(p.g, n, p.records, reinterpret_cast<const T*>(p.grid),
-                                                    reinterpret_cast<const T*>(p.tab.wz), U, W);
+                                                    reinterpret_cast<const T*>(p.tab.wz), p.sorted, U, W);
 }
 
 template void launch_records<float>(const Plan&, int64_t, const double*, const double*, const double*, cudaStream_t);

@@ -106,8 +106,8 @@ void free_plan(Plan* p) {
   if (!p) return;
   for (int i = 0; i <= DPS_NUM_STAGES; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
-  void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.dct, p->tab.dctd, p->tab.idct, p->tab.zeta, p->tab.band,
-                  p->tab.twx, p->tab.twy, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
+  void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->kt.ct, p->kt.dct,
+                  p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
                   p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -126,8 +126,8 @@ dps_status build_tables(Plan* p) {
     zc[c] = g.zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / n1));
     zeta[c] = zc[c] - g.zmin;
   }
-  // forward DCT-I: a_n = (2/n1) sum'' g_c cos(pi n c / n1), a_0 and a_n1 halved
-  std::vector<double> C((size_t)N * N), IC((size_t)N * N), DC((size_t)N * N, 0.0);
+  // forward DCT-I: a_n = (2/n1) sum'' g_c cos(pi n c / n1), a_0 and a_n1 halved; inverse IC[c][n]
+  std::vector<double> C((size_t)N * N), IC((size_t)N * N);
   for (int n = 0; n < N; ++n)
     for (int c = 0; c < N; ++c) {
       const double cs = cos(M_PI * (double)((int64_t)n * c % (2 * n1)) / n1);
@@ -137,14 +137,46 @@ dps_status build_tables(Plan* p) {
       C[(size_t)n * N + c] = v;
       IC[(size_t)c * N + n] = cs;
     }
-  // Chebyshev derivative of each column of C by the recurrence b_n = b_{n+2} + 2 (n+1) a_{n+1},
-  // b_0 halved; times 2/H
-  for (int c = 0; c < N; ++c) {
+  // Chebyshev derivative matrix Dm[m][n] (coefficient m of d/ds T_n) by the recurrence
+  // b_m = b_{m+2} + 2 (m+1) a_{m+1}, b_0 halved
+  std::vector<double> Dm((size_t)N * N, 0.0);
+  for (int n = 0; n < N; ++n) {
     std::vector<double> b(N + 2, 0.0);
-    for (int n = N - 2; n >= 0; --n) b[n] = b[n + 2] + 2.0 * (n + 1) * C[(size_t)(n + 1) * N + c];
+    for (int m = N - 2; m >= 0; --m) b[m] = b[m + 2] + ((m + 1 == n) ? 2.0 * (m + 1) : 0.0);
     b[0] *= 0.5;
-    for (int n = 0; n < N; ++n) DC[(size_t)n * N + c] = (2.0 / g.H) * b[n];
+    for (int m = 0; m < N; ++m) Dm[(size_t)m * N + n] = b[m];
   }
+  const double sH = 2.0 / g.H;
+  std::vector<double> DC((size_t)N * N, 0.0), ICD((size_t)N * N, 0.0), SD((size_t)N * N, 0.0);
+  for (int m = 0; m < N; ++m)
+    for (int c = 0; c < N; ++c) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int q = 0; q < N; ++q) {
+        s1 += Dm[(size_t)m * N + q] * C[(size_t)q * N + c];   // (D C)[m][c]
+        s2 += IC[(size_t)c * N + q] * Dm[(size_t)q * N + m];  // (IC D)[c][m]
+      }
+      DC[(size_t)m * N + c] = sH * s1;
+      ICD[(size_t)c * N + m] = sH * s2;
+    }
+  for (int c = 0; c < N; ++c)
+    for (int j = 0; j < N; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < N; ++q) s += ICD[(size_t)c * N + q] * C[(size_t)q * N + j];
+      SD[(size_t)c * N + j] = s;
+    }
+  const int npad = (N + 24 + 3) / 4 * 4, cpad = (N + 8 + 3) / 4 * 4;
+  p->kt.npad = npad;
+  p->kt.cpad = cpad;
+  std::vector<double> ct((size_t)N * npad, 0.0), dct((size_t)N * npad, 0.0);
+  std::vector<double> ict((size_t)N * cpad, 0.0), icdt((size_t)N * cpad, 0.0), sdt((size_t)N * cpad, 0.0);
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      ct[(size_t)a * npad + b] = C[(size_t)b * N + a];     // [c][n]
+      dct[(size_t)a * npad + b] = DC[(size_t)b * N + a];
+      ict[(size_t)a * cpad + b] = IC[(size_t)b * N + a];   // [n][c]
+      icdt[(size_t)a * cpad + b] = ICD[(size_t)b * N + a];
+      sdt[(size_t)a * cpad + b] = SD[(size_t)b * N + a];   // [j][c]
+    }
   // Clenshaw-Curtis weights: integral of the interpolant, w = C^T I, I_n = 2/(1-n^2) (n even)
   std::vector<double> wz(N, 0.0);
   for (int c = 0; c < N; ++c) {
@@ -177,9 +209,16 @@ dps_status build_tables(Plan* p) {
   if ((e = upload<double>((void**)&p->tab.zc, zc, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload<double>((void**)&p->tab.band, band, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload<T>(&p->tab.wz, wz, bytes)) != cudaSuccess) return DPS_ERR_OOM;
-  if ((e = upload<T>(&p->tab.dct, C, bytes)) != cudaSuccess) return DPS_ERR_OOM;
-  if ((e = upload<T>(&p->tab.dctd, DC, bytes)) != cudaSuccess) return DPS_ERR_OOM;
-  if ((e = upload<T>(&p->tab.idct, IC, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->kt.ct, ct, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->kt.dct, dct, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->kt.ict, ict, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->kt.icdt, icdt, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->kt.sdt, sdt, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  {
+    std::vector<double> bt(3 * (size_t)N);
+    for (size_t i = 0; i < 3 * (size_t)N; ++i) bt[i] = band[i];
+    if ((e = upload<T>(&p->kt.bandT, bt, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  }
   if ((e = upload<T>(&p->tab.zeta, zeta, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twx, g.nx, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twy, g.ny, bytes)) != cudaSuccess) return DPS_ERR_OOM;
@@ -213,6 +252,9 @@ dps_status allocate(Plan* p) {
   if (p->bvp_blocks > need_blocks) p->bvp_blocks = (int)std::max<int64_t>(1, need_blocks);
   p->ws_bytes = (int64_t)p->bvp_blocks * kBvpThreads * (int64_t)bvp_slot_bytes<T>(*p);
   if (!alloc(&p->ws, (size_t)p->ws_bytes)) return DPS_ERR_OOM;
+  if (!alloc(&p->kt.kbuf, 3 * (size_t)g.nz * (size_t)K * sizeof(cplx<T>))) return DPS_ERR_OOM;
+  if (!alloc(&p->kt.kaux, 12 * (size_t)K * sizeof(cplx<T>))) return DPS_ERR_OOM;
+  if (!bvp_prepare<T>(*p)) return DPS_ERR_INVALID_ARG;
   if (!alloc((void**)&p->stage_in, nmax * 9 * sizeof(double))) return DPS_ERR_OOM;
   if (!alloc((void**)&p->stage_out, nmax * 6 * sizeof(double))) return DPS_ERR_OOM;
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
