@@ -136,6 +136,33 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable);
 dps_status dpstokes_stage_times(dps_plan_t plan, double* ms_out, int32_t capacity, int32_t* count);
 
+/* Spreading without device allocation (no counterpart in the paper: this is a deployment aid).
+ * Some callers cannot call cudaMalloc: a host application whose memory manager owns every byte of
+ * device memory and hands out nothing outside its own pool, or a latency-critical loop that cannot
+ * afford the implicit device synchronisation of an allocation.  This entry point runs the library's
+ * spreading stage (particle envelope records, binning and the tile-gather spread of step 1 of
+ * Sec. III.D, in double precision) using only a scratch array of fixed size, 64 MiB, compiled into
+ * the library as device memory; every GPU that loads the library holds that array until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - out_grid: caller-owned device buffer of nfields * nz * ny * ldx doubles (nfields = 3, or 6
+ *     with torques: force fields, then torque fields), laid out [field][c][y][x] with row stride
+ *     ldx (even, >= nx); it is zeroed and then receives the spread node values.
+ *   - The other arguments mean what they mean in dpstokes_plan_create / dpstokes_apply;
+ *     kp->precision, kp->eta and kp->max_n are ignored.
+ *   - Returns DPS_ERR_INVALID_ARG when the problem needs more scratch than the fixed array holds
+ *     (roughly 80k particles with torques at m = 5, 33 Chebyshev nodes) or when an argument is
+ *     invalid.  Particles outside the domain contribute nothing; their errors are not reported.
+ *   - The first call on a device looks up the array's device address (once per device, with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call shares the one array and keeps the previous call's contents in it (everything the
+ *     stage needs zeroed is cleared on each call); calls that overlap on the GPU, on any streams,
+ *     race with each other. */
+dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin, double zmax, int32_t wall_mode,
+                                   const dps_grid* grid, const dps_kernel_params* kp, int64_t n,
+                                   const double* positions, const double* forces,
+                                   const double* torques, double* out_grid, int64_t ldx,
+                                   void* stream);
+
 /* Diagnostics for tests: run the apply pipeline on `stream` up to and including stage
  * `last_stage` (1 = particle records, 2 = spread, 3 = forward xy FFT, 4 = per-k solve,
  * 5 = inverse xy FFT, 6 = interpolation; the outputs may be NULL below stage 6) and copy plan buffer `which` (0 = grid/spectrum,

@@ -73,6 +73,8 @@ def load(path=None):
         "dpstokes_plan_info": (_I32, [_P, ctypes.POINTER(dps_plan_info)]),
         "dpstokes_enable_timing": (_I32, [_P, _I32]),
         "dpstokes_stage_times": (_I32, [_P, ctypes.POINTER(ctypes.c_double), _I32, ctypes.POINTER(_I32)]),
+        "dpstokes_spread_noalloc": (_I32, [_D, _D, _D, _D, _I32, ctypes.POINTER(dps_grid),
+                                           ctypes.POINTER(dps_kernel_params), _I64, _P, _P, _P, _P, _I64, _P]),
         "dpstokes_debug_run": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, _I32]),
         "dpstokes_debug_copy": (_I32, [_P, _I32, _P, _I64, _P]),
     }
@@ -136,6 +138,13 @@ def dpstokes_stage_times(plan):
     cnt = _I32(0)
     st = load().dpstokes_stage_times(plan, buf, len(STAGES), ctypes.byref(cnt))
     return st, list(buf)[: cnt.value]
+
+
+def dpstokes_spread_noalloc(Lx, Ly, zmin, zmax, wall_mode, grid, kp, n, positions, forces, torques, out_grid,
+                            ldx, stream):
+    """Spreading stage with no device allocation (scratch is a fixed array inside the library)."""
+    return load().dpstokes_spread_noalloc(Lx, Ly, zmin, zmax, wall_mode, ctypes.byref(grid), ctypes.byref(kp), n,
+                                          positions, forces, torques, out_grid, ldx, stream)
 
 
 def dpstokes_debug_run(plan, n, positions, forces, torques, out_vel, out_angvel, stream, last_stage):

@@ -1,0 +1,192 @@
+// dpstokes_spread_noalloc: the spreading stage (particle records, binning, tile-gather spread) for
+// callers that cannot allocate device memory.  Its scratch lives in one file-scope device array of
+// fixed size that every GPU loading the library holds until the process exits; nothing here calls
+// cudaMalloc, cudaFree or any allocating routine.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "dps_internal.cuh"
+
+namespace dps {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;  // 64 MiB per device
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Host-side addresses of the array, one per device; filled on the first call made on that device.
+constexpr int kMaxDevices = 64;
+std::mutex g_addr_mutex;
+void* g_addr[kMaxDevices] = {nullptr};
+
+dps_status scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) return DPS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_addr_mutex);
+  if (!g_addr[dev]) {
+    void* ptr = nullptr;
+    // the symbol's name is a host-side stand-in; only this call yields the device address
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return DPS_ERR_CUDA;
+    g_addr[dev] = ptr;
+  }
+  *out = reinterpret_cast<unsigned char*>(g_addr[dev]);
+  return DPS_OK;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+double es_norm_noalloc(double alpha, double beta) {
+  const int n = 128;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    const double w = 2.0 / ((1.0 - z * z) * dp * dp);
+    const double th = 0.5 * M_PI * z;
+    s += w * exp(beta * (cos(th) - 1.0)) * cos(th);
+  }
+  return alpha * 0.5 * M_PI * s;
+}
+
+__global__ void noalloc_init_kernel(double* zc, int nz, double zmin, double H, int* zrange, int* status,
+                                    int* bin_count, int nbins) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nz) zc[i] = zmin + 0.5 * H * (1.0 + cos(M_PI * (double)i / (double)(nz - 1)));
+  if (i == 0) {
+    zrange[0] = nz;
+    zrange[1] = -1;
+    status[0] = 0;
+  }
+  for (int b = i; b < nbins; b += gridDim.x * blockDim.x) bin_count[b] = 0;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace dps
+
+extern "C" dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin, double zmax, int32_t wall_mode,
+                                              const dps_grid* grid, const dps_kernel_params* kp, int64_t n,
+                                              const double* positions, const double* forces,
+                                              const double* torques, double* out_grid, int64_t ldx,
+                                              void* stream) {
+  using namespace dps;
+  if (!grid || !kp || n < 0 || !out_grid) return DPS_ERR_INVALID_ARG;
+  if (!(Lx > 0) || !(Ly > 0) || !(zmax > zmin) || !isfinite(Lx) || !isfinite(Ly) || !isfinite(zmin) ||
+      !isfinite(zmax))
+    return DPS_ERR_INVALID_ARG;
+  if (wall_mode < DPS_FREE || wall_mode > DPS_SLIT) return DPS_ERR_INVALID_ARG;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  if (nx < 8 || ny < 8 || nz < 5 || nz > 257) return DPS_ERR_INVALID_ARG;
+  if (ldx < nx || (ldx & 1)) return DPS_ERR_INVALID_ARG;
+  const double hx = Lx / nx, hy = Ly / ny;
+  if (fabs(hx - hy) > 1e-12 * hx) return DPS_ERR_INVALID_ARG;
+  const bool torque = kp->with_torque != 0;
+  if (n > 0 && (!positions || !forces || (torque && !torques))) return DPS_ERR_INVALID_ARG;
+  if (!torque && torques) return DPS_ERR_INVALID_ARG;
+  auto bad_kernel = [&](int m, double beta) {
+    return m < 2 || m > kMaxM || !(beta > 0) || !isfinite(beta) || m + 1 > nx / 2 || m + 1 > ny / 2;
+  };
+  if (bad_kernel(kp->m_M, kp->beta_M) || (torque && bad_kernel(kp->m_D, kp->beta_D))) return DPS_ERR_INVALID_ARG;
+
+  // geometry of the spreading stage, double precision, caller's row stride
+  Plan p;
+  memset(&p, 0, sizeof(Plan));
+  Geometry& g = p.g;
+  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin;
+  g.h = hx; g.inv_h = 1.0 / hx; g.eta = 1.0; g.mode = wall_mode;
+  g.nx = nx; g.ny = ny; g.nz = nz; g.nkx = nx / 2 + 1;
+  g.pitch = (int)(ldx / 2);  // the spreading kernel writes rows of 2 * pitch values
+  g.with_torque = torque ? 1 : 0;
+  g.nfields = torque ? 6 : 3;
+  g.nkernels = torque ? 2 : 1;
+  auto setk = [&](EsKernel& k, int m, double beta) {
+    k.alpha = 0.5 * m * hx;
+    k.beta = beta;
+    k.inv_norm = 1.0 / es_norm_noalloc(k.alpha, beta);
+    k.px = m + 1;
+  };
+  setk(g.kM, kp->m_M, kp->beta_M);
+  if (torque) setk(g.kD, kp->m_D, kp->beta_D); else g.kD = g.kM;
+  const double amax = std::max(g.kM.alpha, torque ? g.kD.alpha : 0.0);
+  if (wall_mode == DPS_SLIT && g.H < 2.0 * amax) return DPS_ERR_INVALID_ARG;
+  if (wall_mode == DPS_FREE && g.H <= 2.0 * amax) return DPS_ERR_INVALID_ARG;
+  g.pxc = std::max(g.kM.px, torque ? g.kD.px : 0);
+  int best = 0;
+  for (int c = 0; c < nz; ++c) {
+    const double zc0 = zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / (nz - 1)));
+    int cnt = 0;
+    for (int q = 0; q < nz; ++q) {
+      const double zq = zmin + 0.5 * g.H * (1.0 + cos(M_PI * q / (nz - 1)));
+      if (zq <= zc0 && zq >= zc0 - 2.0 * amax * (1.0 + 1e-9) - 1e-12 * g.H) ++cnt;
+    }
+    best = std::max(best, cnt);
+  }
+  g.lzc = std::min(nz, best + 2);
+  const int tvals = 6 + g.nkernels * (2 * g.pxc + g.lzc);
+  g.rec_words = (8 + tvals * 2 + 3) / 4 * 4;
+  g.nbx = (nx + kTileX - 1) / kTileX;
+  g.nby = (ny + kTileY - 1) / kTileY;
+  g.rbx = (g.pxc + kTileX - 1) / kTileX + ((nx % kTileX) ? 1 : 0);
+  g.rby = (g.pxc + kTileY - 1) / kTileY + ((ny % kTileY) ? 1 : 0);
+  if ((2 * g.rbx + 1) * (2 * g.rby + 1) > 64) return DPS_ERR_INVALID_ARG;
+
+  // carve the scratch: node table, plane range, status, bins, particle records
+  const int nbins = g.nbx * g.nby;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  size_t off = 0;
+  const size_t o_zc = off; off = align256(off + (size_t)nz * sizeof(double));
+  const size_t o_zr = off; off = align256(off + 2 * sizeof(int));
+  const size_t o_st = off; off = align256(off + sizeof(int));
+  const size_t o_bc = off; off = align256(off + (size_t)nbins * sizeof(int));
+  const size_t o_bs = off; off = align256(off + (size_t)(nbins + 1) * sizeof(int));
+  const size_t o_bu = off; off = align256(off + (size_t)nbins * sizeof(int));
+  const size_t o_bo = off; off = align256(off + nn * sizeof(int));
+  const size_t o_so = off; off = align256(off + nn * sizeof(int));
+  const size_t o_rc = off; off = align256(off + nn * (size_t)g.rec_words * sizeof(uint32_t));
+  if (off > kNoAllocScratchBytes) return DPS_ERR_INVALID_ARG;  // problem larger than the fixed scratch
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DPS_ERR_CUDA;
+  unsigned char* base = nullptr;
+  const dps_status st = scratch_address(dev, &base);
+  if (st != DPS_OK) return st;
+  p.device = dev;
+  p.precision = DPS_FP64;
+  p.max_n = n;
+  p.tab.zc = reinterpret_cast<double*>(base + o_zc);
+  p.zrange = reinterpret_cast<int*>(base + o_zr);
+  p.status = reinterpret_cast<int*>(base + o_st);
+  p.bin_count = reinterpret_cast<int*>(base + o_bc);
+  p.bin_start = reinterpret_cast<int*>(base + o_bs);
+  p.bin_cursor = reinterpret_cast<int*>(base + o_bu);
+  p.bin_of = reinterpret_cast<int*>(base + o_bo);
+  p.sorted = reinterpret_cast<int*>(base + o_so);
+  p.records = reinterpret_cast<uint32_t*>(base + o_rc);
+  p.grid = out_grid;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  // every plane of the output starts at zero; the spread overwrites the occupied planes
+  if (cudaMemsetAsync(out_grid, 0, (size_t)g.nfields * nz * ny * (size_t)ldx * sizeof(double), s) != cudaSuccess)
+    return DPS_ERR_CUDA;
+  const int blocks = std::min(1024, std::max(nz, nbins) / 256 + 1);
+  noalloc_init_kernel<<<blocks, 256, 0, s>>>(p.tab.zc, nz, zmin, g.H, p.zrange, p.status, p.bin_count, nbins);
+  launch_records<double>(p, n, positions, forces, torques, s);
+  launch_bins(p, n, s);
+  launch_spread<double>(p, s);
+  return cudaGetLastError() == cudaSuccess ? DPS_OK : DPS_ERR_CUDA;
+}
