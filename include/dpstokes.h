@@ -129,10 +129,11 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
  * its kernels; dpstokes_stage_times() waits for the last apply to finish and writes the duration in
  * milliseconds of each stage, in this order (DPS_NUM_STAGES values):
  *   0 init, 1 particle records, 2 binning, 3 spread, 4 x-FFT forward, 5 y-FFT forward,
- *   6 per-wavenumber solve, 7 y-FFT inverse, 8 x-FFT inverse, 9 interpolation.
+ *   6 Chebyshev forward transform, 7 FP64 per-wavenumber solves, 8 correction + curl + inverse
+ *   Chebyshev transform, 9 y-FFT inverse, 10 x-FFT inverse, 11 interpolation.
  * *count receives the number written (min(capacity, DPS_NUM_STAGES)); DPS_ERR_INVALID_ARG if no
  * timed apply has been enqueued since timing was enabled. */
-#define DPS_NUM_STAGES 10
+#define DPS_NUM_STAGES 12
 dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable);
 dps_status dpstokes_stage_times(dps_plan_t plan, double* ms_out, int32_t capacity, int32_t* count);
 

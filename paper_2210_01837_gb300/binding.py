@@ -124,8 +124,8 @@ def dpstokes_plan_info(plan):
     return st, info
 
 
-STAGES = ("init", "records", "bins", "spread", "fft_x_fwd", "fft_y_fwd", "bvp", "fft_y_inv", "fft_x_inv",
-          "interp")
+STAGES = ("init", "records", "bins", "spread", "fft_x_fwd", "fft_y_fwd", "cheb_fwd", "solve", "cheb_bwd",
+          "fft_y_inv", "fft_x_inv", "interp")
 
 
 def dpstokes_enable_timing(plan, enable):

@@ -630,7 +630,7 @@ int bvp_prepare(Plan& p) {
 }
 
 template <typename T>
-void launch_bvp(const Plan& p, cudaStream_t s) {
+void launch_bvp(const Plan& p, int part, cudaStream_t s) {
   const Geometry& g = p.g;
   const int64_t K = (int64_t)g.nkx * g.ny;
   const unsigned blocks = (unsigned)((K + kBvpThreads - 1) / kBvpThreads);
@@ -638,26 +638,29 @@ void launch_bvp(const Plan& p, cudaStream_t s) {
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
   cplx<T>* kbuf = reinterpret_cast<cplx<T>*>(p.kt.kbuf);
   cplx<T>* kaux = reinterpret_cast<cplx<T>*>(p.kt.kaux);
-  fwd_kernel<T, NB><<<blocks, kBvpThreads, p.kt.fwd_smem, s>>>(
-      g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, p.kt.fwd_smem > 0, grid,
-      kbuf, p.zrange);
-  const size_t N = (size_t)g.nz;
-  const size_t slots = (size_t)p.bvp_blocks * kBvpThreads;
-  unsigned char* base = reinterpret_cast<unsigned char*>(p.ws);
-  cplx<double>* sw = reinterpret_cast<cplx<double>*>(base);
-  double* fr = reinterpret_cast<double*>(base + 3 * N * slots * sizeof(cplx<double>));
-  cplx<T>* pws = reinterpret_cast<cplx<T>*>(base + 3 * N * slots * (sizeof(cplx<double>) + sizeof(double)));
-  solve_kernel<T><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT), kbuf,
-                                                       kaux, pws, sw, fr);
-  if (g.with_torque)
+  if (part == 0) {
+    fwd_kernel<T, NB><<<blocks, kBvpThreads, p.kt.fwd_smem, s>>>(
+        g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, p.kt.fwd_smem > 0,
+        grid, kbuf, p.zrange);
+  } else if (part == 1) {
+    const size_t N = (size_t)g.nz;
+    const size_t slots = (size_t)p.bvp_blocks * kBvpThreads;
+    unsigned char* base = reinterpret_cast<unsigned char*>(p.ws);
+    cplx<double>* sw = reinterpret_cast<cplx<double>*>(base);
+    double* fr = reinterpret_cast<double*>(base + 3 * N * slots * sizeof(cplx<double>));
+    cplx<T>* pws = reinterpret_cast<cplx<T>*>(base + 3 * N * slots * (sizeof(cplx<double>) + sizeof(double)));
+    solve_kernel<T><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT), kbuf,
+                                                         kaux, pws, sw, fr);
+  } else if (g.with_torque) {
     bwd_kernel<T, CB, true><<<blocks, kBvpThreads, p.kt.bwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ict), reinterpret_cast<const T*>(p.kt.icdt),
         reinterpret_cast<const T*>(p.kt.sdt), reinterpret_cast<const T*>(p.tab.zeta), p.kt.cpad, p.kt.bwd_smem > 0, kbuf,
         kaux, grid, p.zrange);
-  else
+  } else {
     bwd_kernel<T, CB, false><<<blocks, kBvpThreads, p.kt.bwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ict), nullptr, nullptr, reinterpret_cast<const T*>(p.tab.zeta), p.kt.cpad,
         p.kt.bwd_smem > 0, kbuf, kaux, grid, p.zrange);
+  }
 }
 
 template size_t bvp_slot_bytes<float>(const Plan&);
@@ -666,7 +669,7 @@ template int bvp_occupancy_blocks<float>(const Plan&);
 template int bvp_occupancy_blocks<double>(const Plan&);
 template int bvp_prepare<float>(Plan&);
 template int bvp_prepare<double>(Plan&);
-template void launch_bvp<float>(const Plan&, cudaStream_t);
-template void launch_bvp<double>(const Plan&, cudaStream_t);
+template void launch_bvp<float>(const Plan&, int, cudaStream_t);
+template void launch_bvp<double>(const Plan&, int, cudaStream_t);
 
 }  // namespace dps

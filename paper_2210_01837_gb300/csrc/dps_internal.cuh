@@ -44,6 +44,7 @@ struct FftPlan {
   int n;
   int nstages;
   int radix[kMaxFftRadices];
+  unsigned long long magic[kMaxFftRadices];  // floor(2^40 / Ns) + 1 for the span Ns of each stage
 };
 
 // Per-kernel (monopole / dipole) ES parameters on the device
@@ -139,7 +140,7 @@ template <typename T> void launch_spread(const Plan& p, cudaStream_t s);
 template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s);
 template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_fft_cols(const Plan& p, int dir, cudaStream_t s);
-template <typename T> void launch_bvp(const Plan& p, cudaStream_t s);
+template <typename T> void launch_bvp(const Plan& p, int part, cudaStream_t s);  // 0 fwd, 1 solve, 2 bwd
 template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);

@@ -114,6 +114,40 @@ template <typename T, int DIR> struct Dft<T, 8, DIR> {
   }
 };
 
+// 16-point DFT as 4 x 4: x[4a + b] -> X[c + 4d];  inner DFT4 over a, twiddle W16^(b c), outer DFT4 over b
+template <typename T, int DIR> struct Dft<T, 16, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) {
+    // cos(2 pi m / 16), m = 0..3, and the matching sines
+    const T c1 = (T)0.92387953251128676, s1 = (T)0.38268343236508977, h = (T)0.70710678118654752;
+    cplx<T> t[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      cplx<T> w[4] = {v[b], v[4 + b], v[8 + b], v[12 + b]};
+      Dft<T, 4, DIR>::run(w);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) t[b][c] = w[c];
+    }
+    // twiddles W16^(b c) for b, c in 1..3 (sign of the imaginary part follows the direction)
+    const T sg = (T)DIR;
+    t[1][1] = t[1][1] * mk<T>(c1, sg * s1);
+    t[1][2] = t[1][2] * mk<T>(h, sg * h);
+    t[1][3] = t[1][3] * mk<T>(s1, sg * c1);
+    t[2][1] = t[2][1] * mk<T>(h, sg * h);
+    t[2][2] = rot_quarter<T, DIR>(t[2][2]);
+    t[2][3] = t[2][3] * mk<T>(-h, sg * h);
+    t[3][1] = t[3][1] * mk<T>(s1, sg * c1);
+    t[3][2] = t[3][2] * mk<T>(-h, sg * h);
+    t[3][3] = t[3][3] * mk<T>(-c1, -sg * s1);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      cplx<T> w[4] = {t[0][c], t[1][c], t[2][c], t[3][c]};
+      Dft<T, 4, DIR>::run(w);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) v[c + 4 * d] = w[d];
+    }
+  }
+};
+
 template <typename T, int R, int DIR>
 __device__ __forceinline__ void dft_direct(cplx<T>* v) {
   cplx<T> out[R];
@@ -142,20 +176,28 @@ template <typename T, int DIR> struct Dft<T, 7, DIR> {
   static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 7, DIR>(v); }
 };
 
-// One Stockham stage over `batch` interleaved sequences (element e of sequence b at e*batch + b).
+// Shared-memory index with one pad element per 16: breaks the power-of-two strides of the
+// Stockham writes across bank groups.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// One Stockham stage over `batch` interleaved sequences (element e of sequence b at e*batch + b,
+// batch a power of two given by its log).  Division by the span Ns uses a multiply-high with a
+// per-stage magic number (exact for indices below 2^20).
 template <typename T, int R, int DIR>
 __device__ __forceinline__ void stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int n, int Ns,
-                                      int batch, const cplx<T>* __restrict__ tw) {
+                                      unsigned long long magic, int lbatch, const cplx<T>* __restrict__ tw) {
   const int nr = n / R;
-  const int total = nr * batch;
+  const int batch = 1 << lbatch;
+  const int total = nr << lbatch;
   const int tstep = n / (Ns * R);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int b = t % batch;
-    const int jj = t / batch;
-    const int k = jj % Ns;
+    const int b = t & (batch - 1);
+    const int jj = t >> lbatch;
+    const int q = (int)(((unsigned long long)jj * magic) >> 40);
+    const int k = jj - q * Ns;
     cplx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[(jj + r * nr) * batch + b];
+    for (int r = 0; r < R; ++r) v[r] = in[pad16(((jj + r * nr) << lbatch) + b)];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -165,27 +207,29 @@ __device__ __forceinline__ void stage(const cplx<T>* __restrict__ in, cplx<T>* _
       }
     }
     Dft<T, R, DIR>::run(v);
-    const int base = (jj / Ns) * Ns * R + k;
+    const int base = q * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[(base + r * Ns) * batch + b] = v[r];
+    for (int r = 0; r < R; ++r) out[pad16(((base + r * Ns) << lbatch) + b)] = v[r];
   }
 }
 
 // Full transform; returns the buffer that holds the result.
 template <typename T, int DIR>
-__device__ cplx<T>* fft_smem(cplx<T>* b0, cplx<T>* b1, const FftPlan& fp, int batch, const cplx<T>* tw) {
+__device__ cplx<T>* fft_smem(cplx<T>* b0, cplx<T>* b1, const FftPlan& fp, int lbatch, const cplx<T>* tw) {
   int Ns = 1;
   cplx<T>* in = b0;
   cplx<T>* out = b1;
   for (int s = 0; s < fp.nstages; ++s) {
     const int R = fp.radix[s];
+    const unsigned long long mg = fp.magic[s];
     switch (R) {
-      case 8: stage<T, 8, DIR>(in, out, fp.n, Ns, batch, tw); break;
-      case 4: stage<T, 4, DIR>(in, out, fp.n, Ns, batch, tw); break;
-      case 2: stage<T, 2, DIR>(in, out, fp.n, Ns, batch, tw); break;
-      case 3: stage<T, 3, DIR>(in, out, fp.n, Ns, batch, tw); break;
-      case 5: stage<T, 5, DIR>(in, out, fp.n, Ns, batch, tw); break;
-      default: stage<T, 7, DIR>(in, out, fp.n, Ns, batch, tw); break;
+      case 16: stage<T, 16, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
+      case 8: stage<T, 8, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
+      case 4: stage<T, 4, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
+      case 2: stage<T, 2, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
+      case 3: stage<T, 3, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
+      case 5: stage<T, 5, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
+      default: stage<T, 7, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
     }
     __syncthreads();
     Ns *= R;
@@ -203,7 +247,7 @@ __global__ void row_r2c_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict
                                const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* b1 = b0 + g.nx;
+  cplx<T>* b1 = b0 + pad16(g.nx);
   const int c = blockIdx.y, f = blockIdx.z;
   if (!plane_live(zrange, c)) return;
   const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
@@ -211,15 +255,15 @@ __global__ void row_r2c_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict
   const size_t rowlen = (size_t)2 * g.pitch;
   T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + y0) * rowlen;
   T* row1 = row0 + rowlen;
-  for (int a = threadIdx.x; a < g.nx; a += blockDim.x) b0[a] = mk<T>(row0[a], has1 ? row1[a] : (T)0);
+  for (int a = threadIdx.x; a < g.nx; a += blockDim.x) b0[pad16(a)] = mk<T>(row0[a], has1 ? row1[a] : (T)0);
   __syncthreads();
-  const cplx<T>* res = fft_smem<T, -1>(b0, b1, fp, 1, tw);
+  const cplx<T>* res = fft_smem<T, -1>(b0, b1, fp, 0, tw);
   cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
   cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row1);
   const T half = (T)0.5;
   for (int k = threadIdx.x; k <= g.nx / 2; k += blockDim.x) {
-    const cplx<T> zk = res[k];
-    const cplx<T> zm = conjg(res[(g.nx - k) % g.nx]);
+    const cplx<T> zk = res[pad16(k)];
+    const cplx<T> zm = conjg(res[pad16(k == 0 ? 0 : g.nx - k)]);
     c0[k] = scl(zk + zm, half);
     if (has1) {
       const cplx<T> d = zk - zm;  // (zk - conj z_{-k}) / (2i)
@@ -233,7 +277,7 @@ __global__ void row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict
                                const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* b1 = b0 + g.nx;
+  cplx<T>* b1 = b0 + pad16(g.nx);
   const int c = blockIdx.y, f = blockIdx.z;
   if (!plane_live(zrange, c)) return;
   const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
@@ -246,13 +290,13 @@ __global__ void row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict
   for (int k = threadIdx.x; k <= g.nx / 2; k += blockDim.x) {
     const cplx<T> x0 = c0[k];
     const cplx<T> x1 = has1 ? c1[k] : mk<T>((T)0, (T)0);
-    b0[k] = x0 + mul_i(x1);
-    if (k > 0 && k < g.nx - k) b0[g.nx - k] = conjg(x0) + mul_i(conjg(x1));
+    b0[pad16(k)] = x0 + mul_i(x1);
+    if (k > 0 && k < g.nx - k) b0[pad16(g.nx - k)] = conjg(x0) + mul_i(conjg(x1));
   }
   __syncthreads();
-  const cplx<T>* res = fft_smem<T, +1>(b0, b1, fp, 1, tw);
+  const cplx<T>* res = fft_smem<T, +1>(b0, b1, fp, 0, tw);
   for (int a = threadIdx.x; a < g.nx; a += blockDim.x) {
-    const cplx<T> v = res[a];
+    const cplx<T> v = res[pad16(a)];
     row0[a] = v.x;
     if (has1) row1[a] = v.y;
   }
@@ -260,42 +304,48 @@ __global__ void row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict
 
 template <typename T, int DIR>
 __global__ void col_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ grid,
-                           const int* __restrict__ zrange, int cw) {
+                           const int* __restrict__ zrange, int lcw) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  const int cw = 1 << lcw;
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* b1 = b0 + (size_t)g.ny * cw;
+  cplx<T>* b1 = b0 + pad16(g.ny * cw);
   const int c = blockIdx.y, f = blockIdx.z;
   if (!plane_live(zrange, c)) return;
   const int kx0 = blockIdx.x * cw;
   const int ncols = min(cw, g.nkx - kx0);
   cplx<T>* base = grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
-  const int tot = g.ny * cw;
+  const int tot = g.ny << lcw;
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int y = t / cw, b = t - y * cw;
-    b0[t] = (b < ncols) ? base[(size_t)y * g.pitch + b] : mk<T>((T)0, (T)0);
+    const int y = t >> lcw, b = t & (cw - 1);
+    b0[pad16(t)] = (b < ncols) ? base[(size_t)y * g.pitch + b] : mk<T>((T)0, (T)0);
   }
   __syncthreads();
-  const cplx<T>* res = fft_smem<T, DIR>(b0, b1, fp, cw, tw);
+  const cplx<T>* res = fft_smem<T, DIR>(b0, b1, fp, lcw, tw);
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int y = t / cw, b = t - y * cw;
-    if (b < ncols) base[(size_t)y * g.pitch + b] = res[t];
+    const int y = t >> lcw, b = t & (cw - 1);
+    if (b < ncols) base[(size_t)y * g.pitch + b] = res[pad16(t)];
   }
 }
 
+size_t padded_bytes(int n, size_t esz) { return (size_t)(n + (n >> 4) + 1) * esz; }
+
+// log2 of the column block: widest power of two (at most 8) whose two padded buffers leave room for
+// two blocks per SM (100 KB each), else one block (200 KB)
 template <typename T>
-int col_width(const Plan& p) {
-  // widest power-of-two column block whose two buffers fit in 200 KB of shared memory
-  int cw = 16;
-  while (cw > 1 && (size_t)2 * p.g.ny * cw * sizeof(cplx<T>) > 200 * 1024) cw >>= 1;
-  return cw;
+int col_lwidth(const Plan& p) {
+  for (int l = 3; l > 0; --l)
+    if (2 * padded_bytes(p.g.ny << l, sizeof(cplx<T>)) <= 100 * 1024) return l;
+  for (int l = 3; l > 0; --l)
+    if (2 * padded_bytes(p.g.ny << l, sizeof(cplx<T>)) <= 200 * 1024) return l;
+  return 0;
 }
 
 }  // namespace
 
 template <typename T>
 int fft_smem_ok(const Plan& p) {
-  const size_t row = (size_t)2 * p.g.nx * sizeof(cplx<T>);
-  const size_t col = (size_t)2 * p.g.ny * col_width<T>(p) * sizeof(cplx<T>);
+  const size_t row = 2 * padded_bytes(p.g.nx, sizeof(cplx<T>));
+  const size_t col = 2 * padded_bytes(p.g.ny << col_lwidth<T>(p), sizeof(cplx<T>));
   if (row > 220 * 1024 || col > 220 * 1024) return 0;
   cudaFuncSetAttribute(row_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row);
   cudaFuncSetAttribute(row_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row);
@@ -309,7 +359,7 @@ void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
   dim3 gr((g.ny + 1) / 2, g.nz, g.nfields);
-  const size_t sm = 2 * (size_t)g.nx * sizeof(cplx<T>);
+  const size_t sm = 2 * padded_bytes(g.nx, sizeof(cplx<T>));
   if (dir < 0)
     row_r2c_kernel<T><<<gr, 256, sm, s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
   else
@@ -320,13 +370,14 @@ template <typename T>
 void launch_fft_cols(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
-  const int cw = col_width<T>(p);
+  const int lcw = col_lwidth<T>(p);
+  const int cw = 1 << lcw;
   dim3 gc((g.nkx + cw - 1) / cw, g.nz, g.nfields);
-  const size_t sm = 2 * (size_t)g.ny * cw * sizeof(cplx<T>);
+  const size_t sm = 2 * padded_bytes(g.ny << lcw, sizeof(cplx<T>));
   if (dir < 0)
-    col_kernel<T, -1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
+    col_kernel<T, -1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw);
   else
-    col_kernel<T, +1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, cw);
+    col_kernel<T, +1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw);
 }
 
 template int fft_smem_ok<float>(const Plan&);

@@ -61,12 +61,18 @@ bool fft_plan(int n, FftPlan& fp) {
   fp.n = n;
   fp.nstages = 0;
   int m = n;
+  while (m % 16 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 16; m /= 16; }
   while (m % 8 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 8; m /= 8; }
   while (m % 4 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 4; m /= 4; }
   while (m % 2 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 2; m /= 2; }
   for (int p : {3, 5, 7})
     while (m % p == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = p; m /= p; }
-  return m == 1;
+  unsigned long long ns = 1;
+  for (int s = 0; s < fp.nstages; ++s) {
+    fp.magic[s] = (1ull << 40) / ns + 1;
+    ns *= (unsigned long long)fp.radix[s];
+  }
+  return m == 1 && n < (1 << 20);
 }
 
 template <typename T>
@@ -286,7 +292,11 @@ void enqueue(Plan& p, int64_t n, const double* pos, const double* F, const doubl
   launch_fft_cols<T>(p, -1, s);
   mark();
   if (last_stage <= 3) return;
-  launch_bvp<T>(p, s);
+  launch_bvp<T>(p, 0, s);
+  mark();
+  launch_bvp<T>(p, 1, s);
+  mark();
+  launch_bvp<T>(p, 2, s);
   mark();
   if (last_stage <= 4) return;
   launch_fft_cols<T>(p, +1, s);
