@@ -35,7 +35,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "mobility products/s at N=1M single wall (mixed vs FP64, same GPU); p99 served"
-LAUNCHES_PER_APPLY = 13
 FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk/SM x 2 flop x max SM clock
 
 
@@ -265,6 +264,7 @@ def main():
     # ---- mixed precision (headline) --------------------------------------------------------
     plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=n)
     info = plan.info()
+    launches_per_apply = info.launches_per_apply
     plan.enable_timing(True)
     uuid = None
     try:
@@ -346,7 +346,7 @@ def main():
                           "parallelism": "replicas" if world > 1 else "1 GPU"},
                "particles_per_s": value * n, "fp64": fp64, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                "stage_roofline": stage_roof, "roofline": roofline, "e2e": e2e,
-               "gpu_launches": LAUNCHES_PER_APPLY * args.steps, "clocks": clocks}
+               "gpu_launches": launches_per_apply * args.steps, "clocks": clocks}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

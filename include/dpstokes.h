@@ -88,7 +88,10 @@ dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zm
                                 int32_t wall_mode, const dps_grid* grid,
                                 const dps_kernel_params* kp);
 
-/* One mobility product, enqueued on `stream` (a cudaStream_t, NULL for the legacy stream).
+/* One mobility product, enqueued on `stream` (a cudaStream_t, NULL for the legacy stream).  The
+ * wavenumber-space stages fork onto two plan-owned streams and join back to `stream` before the
+ * apply's last kernels, so all of an apply's work is ordered after earlier work on `stream` and
+ * before later work on it.
  * positions, forces: device [n][3]; torques: device [n][3] or NULL; out_vel: device [n][3];
  * out_angvel: device [n][3] or NULL.  torques and out_angvel must both be NULL for a plan built
  * without torques and both non-NULL for one built with torques.  0 <= n <= max_n.  Outputs are
@@ -122,12 +125,16 @@ typedef struct {
   int32_t record_words;     /* 32-bit words per particle kernel record                          */
   double h;                 /* grid spacing                                                     */
   double alpha_M, alpha_D;  /* kernel supports                                                  */
+  int32_t launches_per_apply; /* kernels one apply launches                                       */
+  int32_t nchunks;          /* column chunks of the wavenumber-space pipeline                     */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 
-/* Per-stage timing.  With timing enabled, every apply records CUDA events on its stream between
- * its kernels; dpstokes_stage_times() waits for the last apply to finish and writes the duration in
- * milliseconds of each stage, in this order (DPS_NUM_STAGES values):
+/* Per-stage timing.  With timing enabled, every apply brackets each kernel launch with a pair of
+ * CUDA events on the stream that launch runs on (the wavenumber-space stages run in column chunks
+ * on two internal streams forked from and joined back to the caller's stream, so their kernels
+ * overlap); dpstokes_stage_times() waits for the last apply to finish and writes, per stage, the sum
+ * of its launch durations in milliseconds, in this order (DPS_NUM_STAGES values):
  *   0 init, 1 particle records, 2 binning, 3 spread, 4 x-FFT forward, 5 y-FFT forward,
  *   6 Chebyshev forward transform, 7 FP64 per-wavenumber solves, 8 correction + curl + inverse
  *   Chebyshev transform, 9 y-FFT inverse, 10 x-FFT inverse, 11 interpolation.

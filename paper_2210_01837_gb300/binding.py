@@ -33,7 +33,8 @@ class dps_kernel_params(ctypes.Structure):
 class dps_plan_info(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("nkx", ctypes.c_int32), ("pitch", ctypes.c_int32),
                 ("nfields", ctypes.c_int32), ("record_words", ctypes.c_int32), ("h", ctypes.c_double),
-                ("alpha_M", ctypes.c_double), ("alpha_D", ctypes.c_double)]
+                ("alpha_M", ctypes.c_double), ("alpha_D", ctypes.c_double), ("launches_per_apply", ctypes.c_int32),
+                ("nchunks", ctypes.c_int32)]
 
 
 class DpsError(RuntimeError):

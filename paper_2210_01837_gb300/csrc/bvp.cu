@@ -79,6 +79,12 @@ struct KInfo {
   double kx, ky, kk;
 };
 
+// thread i of a chunk (columns [kx0, kx0 + w), every ky) -> wavenumber column; kidx = kyi*nkx + kxi
+__device__ __forceinline__ int64_t chunk_kidx(const Geometry& g, int64_t i, int kx0, int w) {
+  const int kyi = (int)(i / w);
+  return (int64_t)kyi * g.nkx + kx0 + (int)(i - (int64_t)kyi * w);
+}
+
 __device__ __forceinline__ KInfo kinfo(const Geometry& g, int64_t kidx) {
   KInfo r;
   r.kxi = (int)(kidx % g.nkx);
@@ -97,6 +103,16 @@ __device__ __forceinline__ size_t gidx(const Geometry& g, int f, int c, int kyi,
   return (((size_t)f * g.nz + c) * g.ny + kyi) * g.pitch + kxi;
 }
 
+// four consecutive table values (16-byte aligned)
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], c = reinterpret_cast<const double2*>(p)[1];
+  o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+}
+
 // stage a table into shared memory when it fits, else read it from global memory
 template <typename T>
 __device__ __forceinline__ const T* stage_table(T* sm, const T* gsrc, int count, bool use) {
@@ -112,7 +128,7 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(kBvpThreads) fwd_kernel(Geometry g, const T* __restrict__ ct_g,
                                                           const T* __restrict__ dct_g, int npad, int smem_tabs,
                                                           const cplx<T>* __restrict__ grid, cplx<T>* __restrict__ kbuf,
-                                                          const int* __restrict__ zrange) {
+                                                          const int* __restrict__ zrange, int kx0, int w) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = g.nz;
   T* sm = reinterpret_cast<T*>(smraw);
@@ -120,8 +136,9 @@ __global__ void __launch_bounds__(kBvpThreads) fwd_kernel(Geometry g, const T* _
   const T* DCt = stage_table<T>(sm + N * npad, dct_g, N * npad, smem_tabs != 0);
   __syncthreads();
   const int64_t K = (int64_t)g.nkx * g.ny;
-  const int64_t kidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (kidx >= K) return;
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= (int64_t)w * g.ny) return;
+  const int64_t kidx = chunk_kidx(g, it, kx0, w);
   const KInfo ki = kinfo(g, kidx);
   if (ki.nyq) return;
   const int clo = zrange[0], chi = zrange[1];
@@ -151,14 +168,22 @@ __global__ void __launch_bounds__(kBvpThreads) fwd_kernel(Geometry g, const T* _
         const T* crow = Ct + (size_t)c * npad + n0;
         const T* drow = DCt + (size_t)c * npad + n0;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          const T cm = crow[j];
-          acc[j].x += cm * a.x;
-          acc[j].y += cm * a.y;
+        for (int j4 = 0; j4 < NB; j4 += 4) {
+          T cm[4];
+          ld4(crow + j4, cm);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[j4 + q].x += cm[q] * a.x;
+            acc[j4 + q].y += cm[q] * a.y;
+          }
           if (use_b) {
-            const T dm = drow[j];
-            acc[j].x += dm * b.x;
-            acc[j].y += dm * b.y;
+            T dm[4];
+            ld4(drow + j4, dm);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc[j4 + q].x += dm[q] * b.x;
+              acc[j4 + q].y += dm[q] * b.y;
+            }
           }
         }
       }
@@ -458,11 +483,14 @@ template <typename T>
 __global__ void __launch_bounds__(kBvpThreads) solve_kernel(Geometry g, const double* __restrict__ band,
                                                             const T* __restrict__ bandT, cplx<T>* __restrict__ kbuf,
                                                             cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ pws,
-                                                            cplx<double>* __restrict__ sw, double* __restrict__ fr) {
+                                                            cplx<double>* __restrict__ sw, double* __restrict__ fr,
+                                                            int kx0, int w) {
   const int64_t K = (int64_t)g.nkx * g.ny;
+  const int64_t total = (int64_t)w * g.ny;
   const int slots = gridDim.x * blockDim.x;
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int64_t k = slot; k < K; k += slots) solve_one<T>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k, K);
+  for (int64_t i = slot; i < total; i += slots)
+    solve_one<T>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, chunk_kidx(g, i, kx0, w), K);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -474,7 +502,7 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
                                                           const T* __restrict__ zeta_g, int cpad, int smem_tabs,
                                                           const cplx<T>* __restrict__ kbuf,
                                                           const cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ grid,
-                                                          const int* __restrict__ zrange) {
+                                                          const int* __restrict__ zrange, int kx0, int w) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = g.nz;
   T* sm = reinterpret_cast<T*>(smraw);
@@ -484,8 +512,9 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
   const T* SDt = CURL ? stage_table<T>(sm + 2 * tab, sdt_g, tab, smem_tabs != 0) : nullptr;
   __syncthreads();
   const int64_t K = (int64_t)g.nkx * g.ny;
-  const int64_t kidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (kidx >= K) return;
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= (int64_t)w * g.ny) return;
+  const int64_t kidx = chunk_kidx(g, it, kx0, w);
   const KInfo ki = kinfo(g, kidx);
   const int clo = zrange[0], chi = zrange[1];
   const int nfo = CURL ? 6 : 3;
@@ -514,7 +543,7 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
   };
   auto expk = [&](T z) -> T { return (sizeof(T) == 4) ? (T)expf((float)(-kt * z)) : (T)exp((double)(-kt * z)); };
   const T hkx = (T)(0.5 * ki.kx), hky = (T)(0.5 * ki.ky);
-  for (int c0 = clo; c0 <= chi; c0 += CB) {
+  for (int c0 = clo & ~3; c0 <= chi; c0 += CB) {  // 16-byte aligned table rows
     cplx<T> au[CB], av[CB], aw[CB], du[CB], dv[CB];
 #pragma unroll
     for (int j = 0; j < CB; ++j) {
@@ -528,15 +557,25 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
       const T* irow = ICt + (size_t)n * cpad + c0;
       const T* drow = CURL ? ICDt + (size_t)n * cpad + c0 : nullptr;
 #pragma unroll
-      for (int j = 0; j < CB; ++j) {
-        const T im = irow[j];
-        au[j].x += im * yu.x; au[j].y += im * yu.y;
-        av[j].x += im * yv.x; av[j].y += im * yv.y;
-        aw[j].x += im * yw.x; aw[j].y += im * yw.y;
+      for (int j4 = 0; j4 < CB; j4 += 4) {
+        T im[4];
+        ld4(irow + j4, im);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = j4 + q;
+          au[j].x += im[q] * yu.x; au[j].y += im[q] * yu.y;
+          av[j].x += im[q] * yv.x; av[j].y += im[q] * yv.y;
+          aw[j].x += im[q] * yw.x; aw[j].y += im[q] * yw.y;
+        }
         if (CURL) {
-          const T dm = drow[j];
-          du[j].x += dm * yu.x; du[j].y += dm * yu.y;
-          dv[j].x += dm * yv.x; dv[j].y += dm * yv.y;
+          T dm[4];
+          ld4(drow + j4, dm);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j4 + q;
+            du[j].x += dm[q] * yu.x; du[j].y += dm[q] * yu.y;
+            dv[j].x += dm[q] * yv.x; dv[j].y += dm[q] * yv.y;
+          }
         }
       }
     }
@@ -549,10 +588,15 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
         const cplx<T> cu = corr_at(0, zt, eb, et), cv = corr_at(1, zt, eb, et);
         const T* srow = SDt + (size_t)jn * cpad + c0;
 #pragma unroll
-        for (int j = 0; j < CB; ++j) {
-          const T sd = srow[j];
-          du[j].x += sd * cu.x; du[j].y += sd * cu.y;
-          dv[j].x += sd * cv.x; dv[j].y += sd * cv.y;
+        for (int j4 = 0; j4 < CB; j4 += 4) {
+          T sd[4];
+          ld4(srow + j4, sd);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j4 + q;
+            du[j].x += sd[q] * cu.x; du[j].y += sd[q] * cu.y;
+            dv[j].x += sd[q] * cv.x; dv[j].y += sd[q] * cv.y;
+          }
         }
       }
     }
@@ -560,6 +604,7 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
     for (int j = 0; j < CB; ++j) {
       const int c = c0 + j;
       if (c > chi) break;
+      if (c < clo) continue;
       cplx<T> u = au[j], v = av[j], w = aw[j];
       if (corr) {
         const T zt = zeta_g[c];
@@ -586,7 +631,7 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
 }
 
 template <typename T> constexpr int fwd_nb() { return sizeof(T) == 4 ? 24 : 12; }
-template <typename T> constexpr int bwd_cb() { return sizeof(T) == 4 ? 8 : 4; }
+template <typename T> constexpr int bwd_cb() { return sizeof(T) == 4 ? 12 : 4; }
 
 size_t fwd_smem(const Plan& p, size_t tsz) { return 2 * (size_t)p.g.nz * p.kt.npad * tsz; }
 size_t bwd_smem(const Plan& p, size_t tsz) { return (p.g.with_torque ? 3 : 1) * (size_t)p.g.nz * p.kt.cpad * tsz; }
@@ -606,7 +651,7 @@ int bvp_occupancy_blocks(const Plan& p) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 4) per_sm = 4;
+  if (per_sm > 2) per_sm = 2;  // leave room on each SM for the concurrent float kernels
   return per_sm * sms;
 }
 
@@ -630,10 +675,10 @@ int bvp_prepare(Plan& p) {
 }
 
 template <typename T>
-void launch_bvp(const Plan& p, int part, cudaStream_t s) {
+void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
   const Geometry& g = p.g;
-  const int64_t K = (int64_t)g.nkx * g.ny;
-  const unsigned blocks = (unsigned)((K + kBvpThreads - 1) / kBvpThreads);
+  const int64_t total = (int64_t)w * g.ny;
+  const unsigned blocks = (unsigned)((total + kBvpThreads - 1) / kBvpThreads);
   constexpr int NB = fwd_nb<T>(), CB = bwd_cb<T>();
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
   cplx<T>* kbuf = reinterpret_cast<cplx<T>*>(p.kt.kbuf);
@@ -641,7 +686,7 @@ void launch_bvp(const Plan& p, int part, cudaStream_t s) {
   if (part == 0) {
     fwd_kernel<T, NB><<<blocks, kBvpThreads, p.kt.fwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, p.kt.fwd_smem > 0,
-        grid, kbuf, p.zrange);
+        grid, kbuf, p.zrange, kx0, w);
   } else if (part == 1) {
     const size_t N = (size_t)g.nz;
     const size_t slots = (size_t)p.bvp_blocks * kBvpThreads;
@@ -650,16 +695,16 @@ void launch_bvp(const Plan& p, int part, cudaStream_t s) {
     double* fr = reinterpret_cast<double*>(base + 3 * N * slots * sizeof(cplx<double>));
     cplx<T>* pws = reinterpret_cast<cplx<T>*>(base + 3 * N * slots * (sizeof(cplx<double>) + sizeof(double)));
     solve_kernel<T><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT), kbuf,
-                                                         kaux, pws, sw, fr);
+                                                         kaux, pws, sw, fr, kx0, w);
   } else if (g.with_torque) {
     bwd_kernel<T, CB, true><<<blocks, kBvpThreads, p.kt.bwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ict), reinterpret_cast<const T*>(p.kt.icdt),
         reinterpret_cast<const T*>(p.kt.sdt), reinterpret_cast<const T*>(p.tab.zeta), p.kt.cpad, p.kt.bwd_smem > 0, kbuf,
-        kaux, grid, p.zrange);
+        kaux, grid, p.zrange, kx0, w);
   } else {
     bwd_kernel<T, CB, false><<<blocks, kBvpThreads, p.kt.bwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ict), nullptr, nullptr, reinterpret_cast<const T*>(p.tab.zeta), p.kt.cpad,
-        p.kt.bwd_smem > 0, kbuf, kaux, grid, p.zrange);
+        p.kt.bwd_smem > 0, kbuf, kaux, grid, p.zrange, kx0, w);
   }
 }
 
@@ -669,7 +714,7 @@ template int bvp_occupancy_blocks<float>(const Plan&);
 template int bvp_occupancy_blocks<double>(const Plan&);
 template int bvp_prepare<float>(Plan&);
 template int bvp_prepare<double>(Plan&);
-template void launch_bvp<float>(const Plan&, int, cudaStream_t);
-template void launch_bvp<double>(const Plan&, int, cudaStream_t);
+template void launch_bvp<float>(const Plan&, int, int, int, cudaStream_t);
+template void launch_bvp<double>(const Plan&, int, int, int, cudaStream_t);
 
 }  // namespace dps

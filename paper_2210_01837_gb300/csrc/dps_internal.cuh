@@ -38,6 +38,8 @@ constexpr int kSpreadThreads = kTileX * kTileY;
 constexpr int kMaxFftRadices = 24;
 constexpr int kMaxM = 12;           // largest ES support in cells
 constexpr int kBvpThreads = 128;    // threads (wavenumbers) per block in the per-k solver
+constexpr int kMaxChunks = 16;      // column chunks of the wavenumber-space pipeline
+constexpr int kMaxTimed = 8 + 5 * kMaxChunks;  // timed launches per apply
 
 // FFT factorisation (radices applied in order, Stockham autosort)
 struct FftPlan {
@@ -123,10 +125,17 @@ struct Plan {
   double* stage_in;     // [max_n][9]
   double* stage_out;    // [max_n][6]
   int64_t device_bytes;
-  // per-stage timing (dpstokes_enable_timing)
+  // wavenumber-space pipeline: column chunks on three streams (fork/join by events)
+  int nchunks;
+  int chunk_x0[kMaxChunks + 1];
+  cudaStream_t side[2];
+  cudaEvent_t ev_fork, ev_f[kMaxChunks], ev_s[kMaxChunks], ev_b[kMaxChunks];
+  // per-stage timing (dpstokes_enable_timing): a start/end event pair per launch, summed per stage
   int timing;
   int timed_apply;
-  cudaEvent_t ev[DPS_NUM_STAGES + 1];
+  int nev;
+  int ev_stage[kMaxTimed];
+  cudaEvent_t ev0[kMaxTimed], ev1[kMaxTimed];
 };
 
 // status bits written by kernels
@@ -139,8 +148,10 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s);
 template <typename T> void launch_spread(const Plan& p, cudaStream_t s);
 template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s);
 template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
-template <typename T> void launch_fft_cols(const Plan& p, int dir, cudaStream_t s);
-template <typename T> void launch_bvp(const Plan& p, int part, cudaStream_t s);  // 0 fwd, 1 solve, 2 bwd
+template <typename T> void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s);
+template <typename T> int fft_col_width(const Plan& p);
+// part 0 Chebyshev forward, 1 FP64 solve, 2 backward; columns [kx0, kx0 + w) of every ky
+template <typename T> void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s);
 template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);

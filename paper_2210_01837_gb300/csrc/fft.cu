@@ -304,15 +304,15 @@ __global__ void row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict
 
 template <typename T, int DIR>
 __global__ void col_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ grid,
-                           const int* __restrict__ zrange, int lcw) {
+                           const int* __restrict__ zrange, int lcw, int kxs, int kxe) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int cw = 1 << lcw;
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* b1 = b0 + pad16(g.ny * cw);
   const int c = blockIdx.y, f = blockIdx.z;
   if (!plane_live(zrange, c)) return;
-  const int kx0 = blockIdx.x * cw;
-  const int ncols = min(cw, g.nkx - kx0);
+  const int kx0 = kxs + blockIdx.x * cw;
+  const int ncols = min(cw, kxe - kx0);
   cplx<T>* base = grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
   const int tot = g.ny << lcw;
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
@@ -367,24 +367,29 @@ void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_fft_cols(const Plan& p, int dir, cudaStream_t s) {
+void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   const int lcw = col_lwidth<T>(p);
   const int cw = 1 << lcw;
-  dim3 gc((g.nkx + cw - 1) / cw, g.nz, g.nfields);
+  dim3 gc((kxe - kxs + cw - 1) / cw, g.nz, g.nfields);
   const size_t sm = 2 * padded_bytes(g.ny << lcw, sizeof(cplx<T>));
   if (dir < 0)
-    col_kernel<T, -1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw);
+    col_kernel<T, -1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw, kxs, kxe);
   else
-    col_kernel<T, +1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw);
+    col_kernel<T, +1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw, kxs, kxe);
 }
 
 template int fft_smem_ok<float>(const Plan&);
 template int fft_smem_ok<double>(const Plan&);
 template void launch_fft_rows<float>(const Plan&, int, cudaStream_t);
 template void launch_fft_rows<double>(const Plan&, int, cudaStream_t);
-template void launch_fft_cols<float>(const Plan&, int, cudaStream_t);
-template void launch_fft_cols<double>(const Plan&, int, cudaStream_t);
+template void launch_fft_cols<float>(const Plan&, int, int, int, cudaStream_t);
+template void launch_fft_cols<double>(const Plan&, int, int, int, cudaStream_t);
+
+template <typename T>
+int fft_col_width(const Plan& p) { return 1 << col_lwidth<T>(p); }
+template int fft_col_width<float>(const Plan&);
+template int fft_col_width<double>(const Plan&);
 
 }  // namespace dps

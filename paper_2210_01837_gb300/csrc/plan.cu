@@ -110,8 +110,18 @@ __global__ void apply_init_kernel(int* zrange, int nz, int* bin_count, int nbins
 
 void free_plan(Plan* p) {
   if (!p) return;
-  for (int i = 0; i <= DPS_NUM_STAGES; ++i)
-    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  for (int i = 0; i < kMaxTimed; ++i) {
+    if (p->ev0[i]) cudaEventDestroy(p->ev0[i]);
+    if (p->ev1[i]) cudaEventDestroy(p->ev1[i]);
+  }
+  for (int j = 0; j < kMaxChunks; ++j) {
+    if (p->ev_f[j]) cudaEventDestroy(p->ev_f[j]);
+    if (p->ev_s[j]) cudaEventDestroy(p->ev_s[j]);
+    if (p->ev_b[j]) cudaEventDestroy(p->ev_b[j]);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  for (int i = 0; i < 2; ++i)
+    if (p->side[i]) cudaStreamDestroy(p->side[i]);
   void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->kt.ct, p->kt.dct,
                   p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
                   p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
@@ -264,6 +274,22 @@ dps_status allocate(Plan* p) {
   if (!alloc((void**)&p->stage_in, nmax * 9 * sizeof(double))) return DPS_ERR_OOM;
   if (!alloc((void**)&p->stage_out, nmax * 6 * sizeof(double))) return DPS_ERR_OOM;
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
+  // column chunks of the wavenumber-space pipeline (multiples of 32 columns, ~192 wide)
+  const int nkx = g.nkx;
+  int J = (nkx + 191) / 192;
+  J = std::max(1, std::min(J, 8));
+  if (nkx < 64) J = 1;
+  p->nchunks = J;
+  for (int j = 0; j < J; ++j) p->chunk_x0[j] = (int)((int64_t)j * nkx / J) / 32 * 32;
+  p->chunk_x0[J] = nkx;
+  for (int i = 0; i < 2; ++i)
+    if (cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) != cudaSuccess) return DPS_ERR_CUDA;
+  if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
+  for (int j = 0; j < J; ++j) {
+    if (cudaEventCreateWithFlags(&p->ev_f[j], cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&p->ev_s[j], cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&p->ev_b[j], cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
+  }
   return DPS_OK;
 }
 
@@ -272,40 +298,58 @@ void enqueue(Plan& p, int64_t n, const double* pos, const double* F, const doubl
              cudaStream_t s, int last_stage) {
   const int nbins = p.g.nbx * p.g.nby;
   const bool tm = p.timing != 0 && last_stage >= 6;
-  int e = 0;
-  auto mark = [&]() {
-    if (tm) cudaEventRecord(p.ev[e++], s);
+  p.nev = 0;
+  // bracket one launch with a timed event pair on the stream it runs on
+  auto timed = [&](int stage, cudaStream_t st, auto&& launch) {
+    const int i = p.nev;
+    if (tm && i < kMaxTimed) cudaEventRecord(p.ev0[i], st);
+    launch();
+    if (tm && i < kMaxTimed) {
+      cudaEventRecord(p.ev1[i], st);
+      p.ev_stage[i] = stage;
+      p.nev = i + 1;
+    }
   };
-  mark();
-  apply_init_kernel<<<std::min(1024, (nbins + 255) / 256 + 1), 256, 0, s>>>(p.zrange, p.g.nz, p.bin_count, nbins);
-  mark();
-  launch_records<T>(p, n, pos, F, Tq, s);
-  mark();
+  timed(0, s, [&] {
+    apply_init_kernel<<<std::min(1024, (nbins + 255) / 256 + 1), 256, 0, s>>>(p.zrange, p.g.nz, p.bin_count, nbins);
+  });
+  timed(1, s, [&] { launch_records<T>(p, n, pos, F, Tq, s); });
   if (last_stage <= 1) return;
-  launch_bins(p, n, s);
-  mark();
-  launch_spread<T>(p, s);
-  mark();
+  timed(2, s, [&] { launch_bins(p, n, s); });
+  timed(3, s, [&] { launch_spread<T>(p, s); });
   if (last_stage <= 2) return;
-  launch_fft_rows<T>(p, -1, s);
-  mark();
-  launch_fft_cols<T>(p, -1, s);
-  mark();
-  if (last_stage <= 3) return;
-  launch_bvp<T>(p, 0, s);
-  mark();
-  launch_bvp<T>(p, 1, s);
-  mark();
-  launch_bvp<T>(p, 2, s);
-  mark();
-  if (last_stage <= 4) return;
-  launch_fft_cols<T>(p, +1, s);
-  mark();
-  launch_fft_rows<T>(p, +1, s);
-  mark();
+  timed(4, s, [&] { launch_fft_rows<T>(p, -1, s); });
+  if (last_stage <= 3) {
+    launch_fft_cols<T>(p, -1, 0, p.g.nkx, s);
+    return;
+  }
+  // wavenumber space, column chunks: y-FFT + Chebyshev forward on s, FP64 solve on side[0],
+  // backward + inverse y-FFT on side[1]; the FP64-bound solve of one chunk overlaps the float and
+  // memory-bound work of its neighbours
+  cudaStream_t ss = p.side[0], sb = p.side[1];
+  cudaEventRecord(p.ev_fork, s);
+  cudaStreamWaitEvent(ss, p.ev_fork, 0);
+  cudaStreamWaitEvent(sb, p.ev_fork, 0);
+  const bool inverse = last_stage >= 5;
+  for (int j = 0; j < p.nchunks; ++j) {
+    const int x0 = p.chunk_x0[j], x1 = p.chunk_x0[j + 1];
+    timed(5, s, [&] { launch_fft_cols<T>(p, -1, x0, x1, s); });
+    timed(6, s, [&] { launch_bvp<T>(p, 0, x0, x1 - x0, s); });
+    cudaEventRecord(p.ev_f[j], s);
+    cudaStreamWaitEvent(ss, p.ev_f[j], 0);
+    timed(7, ss, [&] { launch_bvp<T>(p, 1, x0, x1 - x0, ss); });
+    cudaEventRecord(p.ev_s[j], ss);
+    cudaStreamWaitEvent(sb, p.ev_s[j], 0);
+    timed(8, sb, [&] { launch_bvp<T>(p, 2, x0, x1 - x0, sb); });
+    if (inverse) timed(9, sb, [&] { launch_fft_cols<T>(p, +1, x0, x1, sb); });
+    cudaEventRecord(p.ev_b[j], sb);
+  }
+  cudaStreamWaitEvent(s, p.ev_b[p.nchunks - 1], 0);
+  cudaStreamWaitEvent(s, p.ev_s[p.nchunks - 1], 0);
+  if (!inverse) return;
+  timed(10, s, [&] { launch_fft_rows<T>(p, +1, s); });
   if (last_stage <= 5) return;
-  launch_interp<T>(p, n, U, W, s);
-  mark();
+  timed(11, s, [&] { launch_interp<T>(p, n, U, W, s); });
   if (tm) p.timed_apply = 1;
 }
 
@@ -500,15 +544,19 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   out->h = p->g.h;
   out->alpha_M = p->g.kM.alpha;
   out->alpha_D = p->g.with_torque ? p->g.kD.alpha : 0.0;
+  out->launches_per_apply = 7 + 5 * p->nchunks;
+  out->nchunks = p->nchunks;
   return DPS_OK;
 }
 
 dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p) return DPS_ERR_INVALID_ARG;
-  if (enable && !p->ev[0]) {
-    for (int i = 0; i <= DPS_NUM_STAGES; ++i)
-      if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return DPS_ERR_CUDA;
+  if (enable && !p->ev0[0]) {
+    for (int i = 0; i < dps::kMaxTimed; ++i) {
+      if (cudaEventCreate(&p->ev0[i]) != cudaSuccess) return DPS_ERR_CUDA;
+      if (cudaEventCreate(&p->ev1[i]) != cudaSuccess) return DPS_ERR_CUDA;
+    }
   }
   p->timing = enable ? 1 : 0;
   p->timed_apply = 0;
@@ -518,13 +566,15 @@ dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable) {
 dps_status dpstokes_stage_times(dps_plan_t plan, double* ms_out, int32_t capacity, int32_t* count) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || !ms_out || capacity < 0 || !p->timing || !p->timed_apply) return DPS_ERR_INVALID_ARG;
-  if (cudaEventSynchronize(p->ev[DPS_NUM_STAGES]) != cudaSuccess) return DPS_ERR_CUDA;
-  const int m = std::min<int>(capacity, DPS_NUM_STAGES);
-  for (int i = 0; i < m; ++i) {
+  double acc[DPS_NUM_STAGES] = {0.0};
+  for (int i = 0; i < p->nev; ++i) {
+    if (cudaEventSynchronize(p->ev1[i]) != cudaSuccess) return DPS_ERR_CUDA;
     float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]) != cudaSuccess) return DPS_ERR_CUDA;
-    ms_out[i] = ms;
+    if (cudaEventElapsedTime(&ms, p->ev0[i], p->ev1[i]) != cudaSuccess) return DPS_ERR_CUDA;
+    acc[p->ev_stage[i]] += ms;
   }
+  const int m = std::min<int>(capacity, DPS_NUM_STAGES);
+  for (int i = 0; i < m; ++i) ms_out[i] = acc[i];
   if (count) *count = m;
   return DPS_OK;
 }
