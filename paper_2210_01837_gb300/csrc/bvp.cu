@@ -269,20 +269,28 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
   const double kx = ki.kx, ky = ki.ky, kk = ki.kk, kap = kk * kk;
   const T tkx = (T)kx, tky = (T)ky, tsH = (T)sH, tie = (T)inv_eta;
 
+  // Every sweep below loads the inputs of its next row before the FP64 recurrence of the current
+  // row, so the memory latency of the workspace overlaps the dependent DFMA chain.
+  const cplx<T> zT = mk<T>((T)0, (T)0);
   // ---- pressure: (D^2 - k^2) p = i kx f + i ky g + D h, DtN rows with zero data ----------------
   cplx<double> ptop = mk<double>(0, 0), pbot = mk<double>(0, 0);
   for (int par = 0; par < 2; ++par) {
     const int nlast = ((N - 1 - par) & 1) ? N - 2 : N - 1;
     cplx<double> s_next = mk<double>(0, 0), gacc = mk<double>(0, 0);
     double t_next = 0.0, bfold = 0.0;
-    cplx<T> dh_next = mk<T>((T)0, (T)0);  // derivative recurrence of h over the opposite parity
+    cplx<T> dh_next = zT;  // derivative recurrence of h over the opposite parity
+    cplx<T> fc = KB(0, nlast), gc = KB(1, nlast), hc = (nlast + 1 < N) ? KB(2, nlast + 1) : zT;
     for (int n = nlast; n >= par; n -= 2) {
-      const cplx<T> f = KB(0, n), gg = KB(1, n);
-      cplx<T> dh = dh_next;
-      if (n + 1 < N) dh = dh + scl(KB(2, n + 1), (T)(2 * (n + 1)));
+      cplx<T> fn = zT, gn = zT, hn = zT;
+      if (n - 2 >= par) {
+        fn = KB(0, n - 2);
+        gn = KB(1, n - 2);
+        hn = KB(2, n - 1);
+      }
+      cplx<T> dh = dh_next + scl(hc, (T)(2 * (n + 1)));
       dh_next = dh;
       if (n == 0) dh = scl(dh, (T)0.5);
-      const cplx<T> rt = mk<T>(-tkx * f.y - tky * gg.y + tsH * dh.x, tkx * f.x + tky * gg.x + tsH * dh.y);
+      const cplx<T> rt = mk<T>(-tkx * fc.y - tky * gc.y + tsH * dh.x, tkx * fc.x + tky * gc.x + tsH * dh.y);
       const cplx<double> r = wid(rt);
       const double U = -kap * bu[n];
       const double bcur = (n == nlast) ? (sH * bP[n] + kk * bQ[n]) : bfold;
@@ -310,13 +318,21 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
         FR(2, n) = bcur;
         // ascending substitution; y = B B c + a in the transform precision
         cplx<double> cm = c0;
-        cplx<T> tcm2 = mk<T>((T)0, (T)0), tcm = nar<T>(c0);
+        cplx<T> tcm2 = zT, tcm = nar<T>(c0);
         cplx<double> sp = scl(c0, bQ[par]);
         const cplx<T> ta = nar<T>(a);
+        cplx<double> sc = (par + 2 <= nlast) ? SW(0, par + 2) : mk<double>(0, 0);
+        double tc = (par + 2 <= nlast) ? FR(1, par + 2) : 0.0;
         for (int m = par + 2; m <= nlast + 2; m += 2) {
-          cplx<T> tnew = mk<T>((T)0, (T)0);
+          cplx<double> sn = mk<double>(0, 0);
+          double tn = 0.0;
+          if (m + 2 <= nlast) {
+            sn = SW(0, m + 2);
+            tn = FR(1, m + 2);
+          }
+          cplx<T> tnew = zT;
           if (m <= nlast) {
-            const cplx<double> cnew = SW(0, m) - scl(cm, FR(1, m));
+            const cplx<double> cnew = sc - scl(cm, tc);
             sp = sp + scl(cnew, bQ[m]);
             cm = cnew;
             tnew = nar<T>(cnew);
@@ -328,11 +344,16 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
           PW(q) = y;
           tcm2 = tcm;
           tcm = tnew;
+          sc = sn;
+          tc = tn;
         }
         const double sgn = par ? -1.0 : 1.0;
         ptop = ptop + sp + a;
         pbot = pbot + scl(sp + a, sgn);
       }
+      fc = fn;
+      gc = gn;
+      hc = hn;
     }
   }
 
@@ -357,22 +378,34 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
       s_next[f] = mk<double>(0, 0);
       gacc[f] = par ? scl(gt[f] + gb[f], 0.5) : scl(gt[f] - gb[f], 0.5);
     }
-    cplx<T> dp_next = mk<T>((T)0, (T)0);
+    cplx<T> dp_next = zT;
+    // current-row inputs, loaded one row ahead
+    cplx<T> pc1 = (nlast + 1 < N) ? PW(nlast + 1) : zT, pc0 = PW(nlast);
+    cplx<T> f0c = KB(0, nlast), f1c = KB(1, nlast), f2c = KB(2, nlast);
+    double rhoc = FR(0, nlast), bc = FR(2, nlast);
     for (int n = nlast; n >= par; n -= 2) {
-      cplx<T> dp = dp_next;
-      if (n + 1 < N) dp = dp + scl(PW(n + 1), (T)(2 * (n + 1)));
+      cplx<T> pn1 = zT, pn0 = zT, f0n = zT, f1n = zT, f2n = zT;
+      double rhon = 0.0, bn = 0.0;
+      if (n - 2 >= par) {
+        pn1 = PW(n - 1);
+        pn0 = PW(n - 2);
+        f0n = KB(0, n - 2);
+        f1n = KB(1, n - 2);
+        f2n = KB(2, n - 2);
+        rhon = FR(0, n - 2);
+        bn = FR(2, n - 2);
+      }
+      cplx<T> dp = dp_next + scl(pc1, (T)(2 * (n + 1)));
       dp_next = dp;
       if (n == 0) dp = scl(dp, (T)0.5);
-      const cplx<T> pn = PW(n);
-      const cplx<T> f0 = KB(0, n), f1 = KB(1, n), f2 = KB(2, n);
       cplx<double> r[3];
-      r[0] = wid(scl(scl(mul_i(pn), tkx) - f0, tie));
-      r[1] = wid(scl(scl(mul_i(pn), tky) - f1, tie));
-      r[2] = wid(scl(scl(dp, tsH) - f2, tie));
+      r[0] = wid(scl(scl(mul_i(pc0), tkx) - f0c, tie));
+      r[1] = wid(scl(scl(mul_i(pc0), tky) - f1c, tie));
+      r[2] = wid(scl(scl(dp, tsH) - f2c, tie));
       const double U = -kap * bu[n];
-      const double bcur = FR(2, n);
+      const double bcur = bc;
       if (n > par) {
-        const double rho = FR(0, n);
+        const double rho = rhoc;
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
           const cplx<double> s = scl(r[f] - scl(s_next[f], U), rho);
@@ -381,39 +414,74 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
           s_next[f] = s;
         }
       } else {
-        const double Dp = FR(0, n);
+        const double Dp = rhoc;
         const double beta_a = (par == 0) ? kk : (sH + kk);
         const double idet = 1.0 / (Dp * beta_a + kap * bcur);
         const double sgn = par ? -1.0 : 1.0;
+        cplx<double> cm[3];
+        cplx<T> tcm2[3], tcm[3];
+        cplx<double> sp[3];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
           const cplx<double> rhs = r[f] - scl(s_next[f], U);
           const cplx<double> c0 = scl(scl(rhs, beta_a) + scl(gacc[f], kap), idet);
           const cplx<double> a = scl(scl(gacc[f], Dp) - scl(rhs, bcur), idet);
-          cplx<double> cm = c0;
-          cplx<T> tcm2 = mk<T>((T)0, (T)0), tcm = nar<T>(c0);
-          cplx<double> sp = scl(c0, bQ[par]);
-          const cplx<T> ta = nar<T>(a);
-          for (int m = par + 2; m <= nlast + 2; m += 2) {
-            cplx<T> tnew = mk<T>((T)0, (T)0);
+          cm[f] = c0;
+          tcm[f] = nar<T>(c0);
+          tcm2[f] = zT;
+          sp[f] = scl(c0, bQ[par]);
+          vtop[f] = vtop[f] + a;
+          vbot[f] = vbot[f] + scl(a, sgn);
+          gacc[f] = a;  // reuse: a_par of this field
+        }
+        // ascending substitution for the three fields together
+        cplx<double> sc[3];
+        double tc = (par + 2 <= nlast) ? FR(1, par + 2) : 0.0;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) sc[f] = (par + 2 <= nlast) ? SW(f, par + 2) : mk<double>(0, 0);
+        for (int m = par + 2; m <= nlast + 2; m += 2) {
+          cplx<double> sn[3];
+          double tn = 0.0;
+#pragma unroll
+          for (int f = 0; f < 3; ++f) sn[f] = mk<double>(0, 0);
+          if (m + 2 <= nlast) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) sn[f] = SW(f, m + 2);
+            tn = FR(1, m + 2);
+          }
+          const int q = m - 2;
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            cplx<T> tnew = zT;
             if (m <= nlast) {
-              const cplx<double> cnew = SW(f, m) - scl(cm, FR(1, m));
-              sp = sp + scl(cnew, bQ[m]);
-              cm = cnew;
+              const cplx<double> cnew = sc[f] - scl(cm[f], tc);
+              sp[f] = sp[f] + scl(cnew, bQ[m]);
+              cm[f] = cnew;
               tnew = nar<T>(cnew);
             }
-            const int q = m - 2;
-            cplx<T> y = scl(tcm, td[q]) + scl(tnew, tu[q]);
-            if (q >= 2) y = y + scl(tcm2, tl[q]);
-            if (q == par) y = y + ta;
+            cplx<T> y = scl(tcm[f], td[q]) + scl(tnew, tu[q]);
+            if (q >= 2) y = y + scl(tcm2[f], tl[q]);
+            if (q == par) y = y + nar<T>(gacc[f]);
             KB(f, q) = y;
-            tcm2 = tcm;
-            tcm = tnew;
+            tcm2[f] = tcm[f];
+            tcm[f] = tnew;
+            sc[f] = sn[f];
           }
-          vtop[f] = vtop[f] + sp + a;
-          vbot[f] = vbot[f] + scl(sp + a, sgn);
+          tc = tn;
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          vtop[f] = vtop[f] + sp[f];
+          vbot[f] = vbot[f] + scl(sp[f], sgn);
         }
       }
+      pc1 = pn1;
+      pc0 = pn0;
+      f0c = f0n;
+      f1c = f1n;
+      f2c = f2n;
+      rhoc = rhon;
+      bc = bn;
     }
   }
 
@@ -651,7 +719,7 @@ int bvp_occupancy_blocks(const Plan& p) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;  // leave room on each SM for the concurrent float kernels
+  if (per_sm > 4) per_sm = 4;
   return per_sm * sms;
 }
 

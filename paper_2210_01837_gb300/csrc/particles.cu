@@ -208,11 +208,47 @@ __device__ __forceinline__ bool cyc_overlap(int a, int len_a, int b, int len_b, 
 }
 
 constexpr int kCandCap = 2048;
+constexpr int kStage = 128;  // candidate records staged in shared memory at a time
+
+// Accumulate one batch of staged candidate records into the thread's node column, planes
+// [zb, zb + ZC).  Records live in shared memory (`srec`, `nb` of them, `rw` words each).
+template <typename T, int NF, int ZC>
+__device__ __forceinline__ void spread_batch(const Geometry& g, const uint32_t* srec, int nb, int rw, int gx, int gy,
+                                             int zb, T (&acc)[ZC][NF]) {
+  const int stride = 2 * g.pxc + g.lzc;
+  for (int i = 0; i < nb; ++i) {
+    const uint32_t* r = srec + (size_t)i * rw;
+    const T* tv = reinterpret_cast<const T*>(r + 8);
+#pragma unroll
+    for (int K = 0; K < NF / 3; ++K) {
+      const int4 hd = reinterpret_cast<const int4*>(r)[K];
+      const int px = (K == 0) ? g.kM.px : g.kD.px;
+      int dx = gx - hd.x; if (dx < 0) dx += g.nx;
+      int dy = gy - hd.y; if (dy < 0) dy += g.ny;
+      if (dx < px && dy < px) {
+        const T* ph = tv + 6 + K * stride;
+        const T wxy = ph[dx] * ph[g.pxc + dy];
+        const T f0 = tv[3 * K], f1 = tv[3 * K + 1], f2 = tv[3 * K + 2];
+#pragma unroll
+        for (int zz = 0; zz < ZC; ++zz) {
+          const int iz = zb + zz - hd.z;
+          if (iz >= 0 && iz < hd.w) {
+            const T w = wxy * ph[2 * g.pxc + iz];
+            acc[zz][3 * K] += f0 * w;
+            acc[zz][3 * K + 1] += f1 * w;
+            acc[zz][3 * K + 2] += f2 * w;
+          }
+        }
+      }
+    }
+  }
+}
 
 template <typename T, int NF, int ZC>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
               const int* __restrict__ sorted, const int* __restrict__ zrange, T* __restrict__ grid) {
+  extern __shared__ __align__(16) uint32_t srec[];   // kStage staged records
   __shared__ int s_bins[64];
   __shared__ int s_pref[65];
   __shared__ int s_nb;
@@ -226,6 +262,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   const int gx = tx0 + (tid % kTileX), gy = ty0 + (tid / kTileX);
   const bool active = (gx < g.nx) && (gy < g.ny);
   const int tw = min(kTileX, g.nx - tx0), th = min(kTileY, g.ny - ty0);
+  const int rw = g.rec_words;
   if (tid == 0) {
     int nb = 0;
     for (int dy = -g.rby; dy <= g.rby; ++dy) {
@@ -250,7 +287,14 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   const size_t plane = (size_t)g.ny * 2 * g.pitch;          // T values per z plane (real rows)
   const size_t fstride = plane * g.nz;
   const size_t node = (size_t)gy * 2 * g.pitch + gx;
-  const int stride = 2 * g.pxc + g.lzc;
+  // copy records [i0, i0 + cnt) of the candidate list into shared memory
+  auto stage = [&](int i0, int cnt) {
+    const int words = cnt * rw;
+    for (int t = tid; t < words; t += kSpreadThreads) {
+      const int i = t / rw, w = t - i * rw;
+      srec[t] = rec[(size_t)s_cand[i0 + i] * rw + w];
+    }
+  };
   // rounds over windows of kCandCap passing candidates (one round unless the tile is crowded)
   for (int round = 0;; ++round) {
     const int win0 = round * kCandCap, win1 = win0 + kCandCap;
@@ -263,7 +307,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
         int b = 0;
         while (b + 1 < nb && s_pref[b + 1] <= e) ++b;
         j = sorted[bin_start[s_bins[b]] + (e - s_pref[b])];
-        const uint32_t* r = rec + (size_t)j * g.rec_words;
+        const uint32_t* r = rec + (size_t)j * rw;
         for (int K = 0; K < g.nkernels; ++K) {
           const int4 hd = reinterpret_cast<const int4*>(r)[K];
           const int px = (K == 0) ? g.kM.px : g.kD.px;
@@ -286,6 +330,11 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     }
     const int ncand = min(passed, win1) - win0;
     if (ncand <= 0 && round > 0) break;
+    const bool once = ncand <= kStage;
+    if (once) {
+      stage(0, max(ncand, 0));
+      __syncthreads();
+    }
     for (int zb = clo; zb <= chi; zb += ZC) {
       T acc[ZC][NF];
 #pragma unroll
@@ -296,33 +345,18 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
           if (round > 0 && active && zb + zz <= chi) v = grid[f * fstride + (size_t)(zb + zz) * plane + node];
           acc[zz][f] = v;
         }
-      if (active) {
-        for (int i = 0; i < ncand; ++i) {
-          const uint32_t* r = rec + (size_t)s_cand[i] * g.rec_words;
-          const T* tv = reinterpret_cast<const T*>(r + 8);
-#pragma unroll
-          for (int K = 0; K < NF / 3; ++K) {
-            const int4 hd = reinterpret_cast<const int4*>(r)[K];
-            const int px = (K == 0) ? g.kM.px : g.kD.px;
-            int dx = gx - hd.x; if (dx < 0) dx += g.nx;
-            int dy = gy - hd.y; if (dy < 0) dy += g.ny;
-            if (dx < px && dy < px) {
-              const T* ph = tv + 6 + K * stride;
-              const T wxy = ph[dx] * ph[g.pxc + dy];
-              const T f0 = tv[3 * K], f1 = tv[3 * K + 1], f2 = tv[3 * K + 2];
-#pragma unroll
-              for (int zz = 0; zz < ZC; ++zz) {
-                const int iz = zb + zz - hd.z;
-                if (iz >= 0 && iz < hd.w) {
-                  const T w = wxy * ph[2 * g.pxc + iz];
-                  acc[zz][3 * K] += f0 * w;
-                  acc[zz][3 * K + 1] += f1 * w;
-                  acc[zz][3 * K + 2] += f2 * w;
-                }
-              }
-            }
-          }
+      if (once) {
+        if (active) spread_batch<T, NF, ZC>(g, srec, ncand, rw, gx, gy, zb, acc);
+      } else {
+        for (int i0 = 0; i0 < ncand; i0 += kStage) {
+          const int cnt = min(kStage, ncand - i0);
+          __syncthreads();
+          stage(i0, cnt);
+          __syncthreads();
+          if (active) spread_batch<T, NF, ZC>(g, srec, cnt, rw, gx, gy, zb, acc);
         }
+      }
+      if (active) {
 #pragma unroll
         for (int zz = 0; zz < ZC; ++zz) {
           if (zb + zz <= chi) {
@@ -418,13 +452,18 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
 template <typename T>
 void launch_spread(const Plan& p, cudaStream_t s) {
   const unsigned blocks = (unsigned)(p.g.nbx * p.g.nby);
-  constexpr int ZC = sizeof(T) == 4 ? 8 : 4;
-  if (p.g.nfields == 6)
-    spread_kernel<T, 6, ZC><<<blocks, kSpreadThreads, 0, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
-                                                              reinterpret_cast<T*>(p.grid));
-  else
-    spread_kernel<T, 3, ZC><<<blocks, kSpreadThreads, 0, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
-                                                              reinterpret_cast<T*>(p.grid));
+  // z chunk: as many planes as keep the accumulators near 48 registers' worth
+  constexpr int ZC6 = sizeof(T) == 4 ? 8 : 4, ZC3 = sizeof(T) == 4 ? 12 : 6;
+  const size_t sm = (size_t)kStage * p.g.rec_words * sizeof(uint32_t);
+  if (p.g.nfields == 6) {
+    cudaFuncSetAttribute(spread_kernel<T, 6, ZC6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    spread_kernel<T, 6, ZC6><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                                reinterpret_cast<T*>(p.grid));
+  } else {
+    cudaFuncSetAttribute(spread_kernel<T, 3, ZC3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    spread_kernel<T, 3, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                                reinterpret_cast<T*>(p.grid));
+  }
 }
 
 template <typename T>

@@ -1,6 +1,7 @@
 // Host side of the library: plan construction (validation, tables, device buffers), the apply
 // pipeline (steps 1-8 of Sec. III.D enqueued on one stream) and the C ABI of include/dpstokes.h.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -276,9 +277,12 @@ dps_status allocate(Plan* p) {
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
   // column chunks of the wavenumber-space pipeline (multiples of 32 columns, ~192 wide)
   const int nkx = g.nkx;
-  int J = (nkx + 191) / 192;
-  J = std::max(1, std::min(J, 8));
-  if (nkx < 64) J = 1;
+  // one chunk: measured on GB300, co-running the FP64 solve with the float transforms slowed both
+  // (they compete for issue slots), so the stages run back to back; the chunked form is kept for
+  // DPS_CHUNKS experiments
+  int J = 1;
+  if (const char* e = getenv("DPS_CHUNKS")) J = std::max(1, std::min(atoi(e), kMaxChunks));
+  if (nkx < 64 * J) J = 1;
   p->nchunks = J;
   for (int j = 0; j < J; ++j) p->chunk_x0[j] = (int)((int64_t)j * nkx / J) / 32 * 32;
   p->chunk_x0[J] = nkx;
