@@ -31,6 +31,8 @@
 // leaving a 2x2 system for (c_par, a_par); the rows are diagonally dominant, so no pivoting.
 #include <math.h>
 
+#include <algorithm>
+
 #include "dps_internal.cuh"
 
 namespace dps {
@@ -698,6 +700,295 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tiled forms of the two transforms (N <= 128): a block owns 64 consecutive wavenumbers of the chunk
+// and computes dense products with shared-memory tiles and register blocking (4 wavenumbers x a few
+// rows per thread), so every shared load feeds several FMAs.
+// ---------------------------------------------------------------------------------------------
+constexpr int kTK = 64;     // wavenumbers per block
+template <typename T> __host__ __device__ constexpr int kCC() { return sizeof(T) == 4 ? 16 : 8; }  // planes per chunk
+
+// forward: kbuf[o][n][k] = sum_c C[n][c] a_c(k) + DC[n][c] b_c(k), n-tiles of 16*NG rows
+template <typename T, int NG>
+__global__ void __launch_bounds__(256) fwd_tiled_kernel(Geometry g, const T* __restrict__ ct, const T* __restrict__ dct,
+                                                        int npad, const cplx<T>* __restrict__ grid,
+                                                        cplx<T>* __restrict__ kbuf, const int* __restrict__ zrange,
+                                                        int kx0, int w) {
+  constexpr int NT = 16 * NG;
+  constexpr int CC = kCC<T>();
+  __shared__ __align__(16) cplx<T> sA[CC][kTK];
+  __shared__ __align__(16) cplx<T> sB[CC][kTK];
+  __shared__ __align__(16) T sC[CC][NT];
+  __shared__ __align__(16) T sD[CC][NT];
+  const int N = g.nz;
+  const int tid = threadIdx.x, kg = tid & 15, ng = tid >> 4;
+  const int64_t K = (int64_t)g.nkx * g.ny;
+  const int64_t total = (int64_t)w * g.ny;
+  const int64_t i0 = (int64_t)blockIdx.x * kTK;
+  const int clo = zrange[0], chi = zrange[1];
+  const bool tq = g.with_torque != 0;
+  // per-thread wavenumbers (for the epilogue)
+  int64_t my_k[4];
+  bool my_ok[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t it = i0 + kg * 4 + q;
+    my_ok[q] = it < total;
+    my_k[q] = my_ok[q] ? chunk_kidx(g, it, kx0, w) : 0;
+  }
+  for (int o = 0; o < 3; ++o) {
+    const bool use_b = tq && o < 2;
+    for (int n0 = 0; n0 < N; n0 += NT) {
+      cplx<T> acc[4][NG];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < NG; ++j) acc[q][j] = mk<T>((T)0, (T)0);
+      for (int c0 = clo; c0 <= chi; c0 += CC) {
+        __syncthreads();
+        for (int e = tid; e < CC * kTK; e += 256) {
+          const int cc = e / kTK, kk = e - cc * kTK;
+          const int c = c0 + cc;
+          const int64_t it = i0 + kk;
+          cplx<T> a = mk<T>((T)0, (T)0), bb = mk<T>((T)0, (T)0);
+          if (c <= chi && it < total) {
+            const int64_t kidx = chunk_kidx(g, it, kx0, w);
+            const int kxi = (int)(kidx % g.nkx), kyi = (int)(kidx / g.nkx);
+            const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
+            const T hkx = (T)(M_PI * (double)kxi / g.Lx), hky = (T)(M_PI * (double)nyv / g.Ly);  // k/2
+            a = grid[gidx(g, o, c, kyi, kxi)];
+            if (tq) {
+              if (o == 0) {
+                a = a + mul_i(scl(grid[gidx(g, 5, c, kyi, kxi)], hky));
+                bb = scl(grid[gidx(g, 4, c, kyi, kxi)], (T)-0.5);
+              } else if (o == 1) {
+                a = a - mul_i(scl(grid[gidx(g, 5, c, kyi, kxi)], hkx));
+                bb = scl(grid[gidx(g, 3, c, kyi, kxi)], (T)0.5);
+              } else {
+                a = a + mul_i(scl(grid[gidx(g, 4, c, kyi, kxi)], hkx) - scl(grid[gidx(g, 3, c, kyi, kxi)], hky));
+              }
+            }
+          }
+          sA[cc][kk] = a;
+          sB[cc][kk] = bb;
+        }
+        for (int e = tid; e < CC * NT; e += 256) {
+          const int cc = e / NT, nn = e - cc * NT;
+          const int c = c0 + cc, n = n0 + nn;
+          const bool ok = c <= chi && n < N;
+          sC[cc][nn] = ok ? ct[(size_t)c * npad + n] : (T)0;
+          sD[cc][nn] = (ok && use_b) ? dct[(size_t)c * npad + n] : (T)0;
+        }
+        __syncthreads();
+        const int ccmax = min(CC, chi - c0 + 1);
+        for (int cc = 0; cc < ccmax; ++cc) {
+          cplx<T> a[4], bv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            a[q] = sA[cc][kg * 4 + q];
+            bv[q] = sB[cc][kg * 4 + q];
+          }
+#pragma unroll
+          for (int j = 0; j < NG; ++j) {
+            const T cm = sC[cc][ng * NG + j];
+            const T dm = sD[cc][ng * NG + j];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc[q][j].x += cm * a[q].x + dm * bv[q].x;
+              acc[q][j].y += cm * a[q].y + dm * bv[q].y;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NG; ++j) {
+        const int n = n0 + ng * NG + j;
+        if (n < N) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (my_ok[q]) kbuf[((size_t)o * N + n) * K + my_k[q]] = acc[q][j];
+        }
+      }
+    }
+  }
+}
+
+// backward: per field, y_tot = y + DCT(correction node values) via E = C e, G = C g (e = e^{-k zeta},
+// g = zeta e; the top family uses the mirrored vectors), then nodes = IC y_tot and, with torques,
+// the derivative ICD y_tot; the half-curl is assembled across the three fields in the grid.
+template <typename T, bool CURL>
+__global__ void __launch_bounds__(128) bwd_tiled_kernel(Geometry g, const T* __restrict__ cmat /*[N][N] C[n][j]*/,
+                                                        const T* __restrict__ ict, const T* __restrict__ icdt, int cpad,
+                                                        const T* __restrict__ zeta_g, const cplx<T>* __restrict__ kbuf,
+                                                        const cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ grid,
+                                                        const int* __restrict__ zrange, int kx0, int w) {
+  constexpr int TK = 32;           // wavenumbers per block; thread: 4 wavenumbers x 3 planes
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = g.nz;
+  const int tid = threadIdx.x, kq = tid & 7, cg = tid >> 3;  // 8 k-groups x 16 plane-groups
+  T* sE = reinterpret_cast<T*>(smraw);                       // [N][TK]
+  T* sG = sE + N * TK;                                        // [N][TK]
+  cplx<T>* sY = reinterpret_cast<cplx<T>*>(sG + N * TK);     // [N][TK]  (e, g staged here first)
+  cplx<T>* sAmp = sY + N * TK;                                // [TK][12]
+  const int64_t K = (int64_t)g.nkx * g.ny;
+  const int64_t total = (int64_t)w * g.ny;
+  const int64_t i0 = (int64_t)blockIdx.x * TK;
+  const int clo = zrange[0], chi = zrange[1];
+  const bool corr_mode = g.mode != DPS_FREE;
+  const bool top = g.mode == DPS_SLIT;
+  const T scale = (T)(1.0 / ((double)g.nx * (double)g.ny));
+  const T H = (T)g.H;
+  // ---- correction amplitudes and e/g vectors for the block's wavenumbers ----
+  T* se = reinterpret_cast<T*>(sY);        // [N][TK]
+  T* sg = se + N * TK;                     // [N][TK]
+  for (int e = tid; e < TK * 12; e += 128) {
+    const int kk = e / 12, q = e - kk * 12;
+    const int64_t it = i0 + kk;
+    cplx<T> v = mk<T>((T)0, (T)0);
+    if (corr_mode && it < total) {
+      const int64_t kidx = chunk_kidx(g, it, kx0, w);
+      if (kidx != 0) v = kaux[(size_t)q * K + kidx];
+    }
+    sAmp[kk * 12 + q] = v;
+  }
+  if (corr_mode) {
+    for (int e = tid; e < N * TK; e += 128) {
+      const int j = e / TK, kk = e - j * TK;
+      const int64_t it = i0 + kk;
+      T ev = (T)0, gv = (T)0;
+      if (it < total) {
+        const int64_t kidx = chunk_kidx(g, it, kx0, w);
+        const int kxi = (int)(kidx % g.nkx), kyi = (int)(kidx / g.nkx);
+        const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
+        const double kx = 2.0 * M_PI * (double)kxi / g.Lx, ky = 2.0 * M_PI * (double)nyv / g.Ly;
+        const T kt = (T)sqrt(kx * kx + ky * ky);
+        const T zt = zeta_g[j];
+        ev = (sizeof(T) == 4) ? (T)expf((float)(-kt * zt)) : (T)exp((double)(-kt * zt));
+        gv = zt * ev;
+      }
+      se[e] = ev;
+      sg[e] = gv;
+    }
+    __syncthreads();
+    // E[n][k] = sum_j C[n][j] e[j][k], G likewise; thread: 4 k x ceil(N/16) n
+    for (int n = cg; n < N; n += 16) {
+      T aE[4] = {0, 0, 0, 0}, aG[4] = {0, 0, 0, 0};
+      for (int j = 0; j < N; ++j) {
+        const T cm = cmat[(size_t)n * N + j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          aE[q] += cm * se[j * TK + kq * 4 + q];
+          aG[q] += cm * sg[j * TK + kq * 4 + q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sE[n * TK + kq * 4 + q] = aE[q];
+        sG[n * TK + kq * 4 + q] = aG[q];
+      }
+    }
+  }
+  // per-thread wavenumbers
+  int64_t my_k[4];
+  bool my_ok[4];
+  T hkx[4], hky[4];
+  bool my_nyq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t it = i0 + kq * 4 + q;
+    my_ok[q] = it < total;
+    my_k[q] = my_ok[q] ? chunk_kidx(g, it, kx0, w) : 0;
+    const KInfo ki = kinfo(g, my_k[q]);
+    my_nyq[q] = ki.nyq;
+    hkx[q] = (T)(0.5 * ki.kx);
+    hky[q] = (T)(0.5 * ki.ky);
+  }
+  for (int f = 0; f < 3; ++f) {
+    __syncthreads();  // sY reuse
+    // y_tot[n][k] = y + aE E + aG G + (-1)^n (bE E + bG G)
+    for (int e = tid; e < N * TK; e += 128) {
+      const int n = e / TK, kk = e - n * TK;
+      const int64_t it = i0 + kk;
+      cplx<T> y = mk<T>((T)0, (T)0);
+      if (it < total) {
+        const int64_t kidx = chunk_kidx(g, it, kx0, w);
+        y = kbuf[((size_t)f * N + n) * K + kidx];
+        if (corr_mode) {
+          const T Ev = sE[e], Gv = sG[e];
+          const cplx<T>* am = sAmp + kk * 12 + 4 * f;
+          y = y + scl(am[0], Ev) + scl(am[1], Gv);
+          if (top) {
+            const T sgn = (n & 1) ? (T)-1 : (T)1;
+            y = y + scl(scl(am[2], Ev) + scl(am[3], Gv), sgn);
+          }
+        }
+      }
+      sY[e] = y;
+    }
+    __syncthreads();
+    const bool need_d = CURL && f < 2;
+    for (int c0 = (clo & ~3); c0 <= chi; c0 += 48) {
+      // thread planes c0 + cg*3 + {0,1,2}
+      cplx<T> acc[4][3], dac[4][3];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { acc[q][j] = mk<T>((T)0, (T)0); dac[q][j] = mk<T>((T)0, (T)0); }
+      const int cb = c0 + cg * 3;
+      if (cb <= chi && cb + 2 >= clo) {
+        for (int n = 0; n < N; ++n) {
+          cplx<T> yv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) yv[q] = sY[n * TK + kq * 4 + q];
+          const T* ir = ict + (size_t)n * cpad + cb;
+          const T* dr = icdt + (size_t)n * cpad + cb;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const T im = ir[j];
+            const T dm = need_d ? dr[j] : (T)0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc[q][j].x += im * yv[q].x; acc[q][j].y += im * yv[q].y;
+              if (need_d) { dac[q][j].x += dm * yv[q].x; dac[q][j].y += dm * yv[q].y; }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int c = cb + j;
+        if (c < clo || c > chi) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (!my_ok[q]) continue;
+          const int kxi = (int)(my_k[q] % g.nkx), kyi = (int)(my_k[q] / g.nkx);
+          if (my_nyq[q]) {
+            grid[gidx(g, f, c, kyi, kxi)] = mk<T>((T)0, (T)0);
+            if (CURL) grid[gidx(g, 3 + f, c, kyi, kxi)] = mk<T>((T)0, (T)0);
+            continue;
+          }
+          const cplx<T> v = acc[q][j];
+          grid[gidx(g, f, c, kyi, kxi)] = scl(v, scale);
+          if (CURL) {
+            // omega = 1/2 (i ky w - Dv, Du - i kx w, i kx v - i ky u), assembled field by field
+            const size_t ox = gidx(g, 3, c, kyi, kxi), oy = gidx(g, 4, c, kyi, kxi), oz = gidx(g, 5, c, kyi, kxi);
+            if (f == 0) {
+              grid[oy] = scl(dac[q][j], (T)0.5 * scale);
+              grid[oz] = scl(mul_i(v), -hky[q] * scale);
+            } else if (f == 1) {
+              grid[ox] = scl(dac[q][j], (T)-0.5 * scale);
+              grid[oz] = grid[oz] + scl(mul_i(v), hkx[q] * scale);
+            } else {
+              grid[ox] = grid[ox] + scl(mul_i(v), hky[q] * scale);
+              grid[oy] = grid[oy] - scl(mul_i(v), hkx[q] * scale);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename T> constexpr int fwd_nb() { return sizeof(T) == 4 ? 24 : 12; }
 template <typename T> constexpr int bwd_cb() { return sizeof(T) == 4 ? 12 : 4; }
 
@@ -739,6 +1030,11 @@ int bvp_prepare(Plan& p) {
   if (cudaFuncSetAttribute(bwd_kernel<T, CB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.kt.bwd_smem) !=
       cudaSuccess)
     return 0;
+  const int tsm = (int)((size_t)std::min(p.g.nz, 128) * 32 * (2 * sizeof(T) + sizeof(cplx<T>)) + 32 * 12 * sizeof(cplx<T>));
+  if (cudaFuncSetAttribute(bwd_tiled_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm) != cudaSuccess)
+    return 0;
+  if (cudaFuncSetAttribute(bwd_tiled_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm) != cudaSuccess)
+    return 0;
   return 1;
 }
 
@@ -751,7 +1047,28 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
   cplx<T>* kbuf = reinterpret_cast<cplx<T>*>(p.kt.kbuf);
   cplx<T>* kaux = reinterpret_cast<cplx<T>*>(p.kt.kaux);
-  if (part == 0) {
+  const bool tiled = g.nz <= 128;
+  if (part == 0 && tiled) {
+    const unsigned tb = (unsigned)((total + kTK - 1) / kTK);
+    fwd_tiled_kernel<T, 5><<<tb, 256, 0, s>>>(g, reinterpret_cast<const T*>(p.kt.ct),
+                                              reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, grid, kbuf, p.zrange,
+                                              kx0, w);
+  } else if (part == 2 && tiled) {
+    const unsigned tb = (unsigned)((total + 31) / 32);
+    const size_t sm = (size_t)g.nz * 32 * (2 * sizeof(T) + sizeof(cplx<T>)) + 32 * 12 * sizeof(cplx<T>);
+    if (g.with_torque)
+      bwd_tiled_kernel<T, true><<<tb, 128, sm, s>>>(g, reinterpret_cast<const T*>(p.kt.cmat),
+                                                    reinterpret_cast<const T*>(p.kt.ict),
+                                                    reinterpret_cast<const T*>(p.kt.icdt), p.kt.cpad,
+                                                    reinterpret_cast<const T*>(p.tab.zeta), kbuf, kaux, grid, p.zrange,
+                                                    kx0, w);
+    else
+      bwd_tiled_kernel<T, false><<<tb, 128, sm, s>>>(g, reinterpret_cast<const T*>(p.kt.cmat),
+                                                     reinterpret_cast<const T*>(p.kt.ict),
+                                                     reinterpret_cast<const T*>(p.kt.icdt), p.kt.cpad,
+                                                     reinterpret_cast<const T*>(p.tab.zeta), kbuf, kaux, grid, p.zrange,
+                                                     kx0, w);
+  } else if (part == 0) {
     fwd_kernel<T, NB><<<blocks, kBvpThreads, p.kt.fwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, p.kt.fwd_smem > 0,
         grid, kbuf, p.zrange, kx0, w);

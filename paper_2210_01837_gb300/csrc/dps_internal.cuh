@@ -94,6 +94,7 @@ struct KTabs {
   void* icdt;      // [N][cpad]  (2/H) IC D transposed (derivative at the nodes from coefficients)
   void* sdt;       // [N][cpad]  spectral differentiation at the nodes, transposed: sdt[j][c] = SD[c][j]
   void* bandT;     // [3][N]     l, d, u of the B B map in T
+  void* cmat;      // [N][N]     forward DCT-I C[n][j] (correction coefficients in the tiled backward)
   void* kbuf;      // [3][N][K]  Chebyshev coefficients per wavenumber (forces, then DP velocity)
   void* kaux;      // [12][K]    wall-correction amplitudes per wavenumber
   int npad, cpad;

@@ -124,7 +124,7 @@ void free_plan(Plan* p) {
   for (int i = 0; i < 2; ++i)
     if (p->side[i]) cudaStreamDestroy(p->side[i]);
   void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->kt.ct, p->kt.dct,
-                  p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
+                  p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.cmat, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
                   p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -231,6 +231,7 @@ dps_status build_tables(Plan* p) {
   if ((e = upload<T>(&p->kt.ict, ict, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload<T>(&p->kt.icdt, icdt, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload<T>(&p->kt.sdt, sdt, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload<T>(&p->kt.cmat, C, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   {
     std::vector<double> bt(3 * (size_t)N);
     for (size_t i = 0; i < 3 * (size_t)N; ++i) bt[i] = band[i];
