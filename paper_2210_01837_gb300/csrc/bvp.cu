@@ -83,8 +83,43 @@ struct KInfo {
 
 // thread i of a chunk (columns [kx0, kx0 + w), every ky) -> wavenumber column; kidx = kyi*nkx + kxi
 __device__ __forceinline__ int64_t chunk_kidx(const Geometry& g, int64_t i, int kx0, int w) {
-  const int kyi = (int)(i / w);
-  return (int64_t)kyi * g.nkx + kx0 + (int)(i - (int64_t)kyi * w);
+  const unsigned ii = (unsigned)i;  // total wavenumbers < 2^31
+  const int kyi = (int)(ii / (unsigned)w);
+  return (int64_t)kyi * g.nkx + kx0 + (int)(ii - (unsigned)kyi * (unsigned)w);
+}
+
+// per-block wavenumber table of the tiled kernels: grid column offset, kbuf index, k/2 components
+struct KTile {
+  int col[64];
+  int kid[64];
+  float hkx[64], hky[64];
+  double kk[64];
+};
+
+__device__ __forceinline__ void fill_ktile(const Geometry& g, KTile& t, int64_t i0, int64_t total, int kx0, int w,
+                                           int tk) {
+  for (int kk = threadIdx.x; kk < tk; kk += blockDim.x) {
+    const int64_t it = i0 + kk;
+    int col = -1, kid = 0;
+    double hx = 0.0, hy = 0.0;
+    if (it < total) {
+      const int64_t kidx = chunk_kidx(g, it, kx0, w);
+      const unsigned ku = (unsigned)kidx;
+      const int kyi = (int)(ku / (unsigned)g.nkx), kxi = (int)(ku - (unsigned)kyi * (unsigned)g.nkx);
+      const bool nyq = ((g.nx % 2 == 0) && kxi == g.nx / 2) || ((g.ny % 2 == 0) && kyi == g.ny / 2);
+      const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
+      col = kyi * g.pitch + kxi;
+      kid = (int)kidx;
+      hx = M_PI * (double)kxi / g.Lx;
+      hy = M_PI * (double)nyv / g.Ly;
+      if (nyq) kid = -1 - kid;  // flag Nyquist columns (negative), index recoverable
+    }
+    t.col[kk] = col;
+    t.kid[kk] = kid;
+    t.hkx[kk] = (float)hx;
+    t.hky[kk] = (float)hy;
+    t.kk[kk] = 2.0 * sqrt(hx * hx + hy * hy);
+  }
 }
 
 __device__ __forceinline__ KInfo kinfo(const Geometry& g, int64_t kidx) {
@@ -716,6 +751,7 @@ __global__ void __launch_bounds__(256) fwd_tiled_kernel(Geometry g, const T* __r
                                                         int kx0, int w) {
   constexpr int NT = 16 * NG;
   constexpr int CC = kCC<T>();
+  __shared__ KTile kt;
   __shared__ __align__(16) cplx<T> sA[CC][kTK];
   __shared__ __align__(16) cplx<T> sB[CC][kTK];
   __shared__ __align__(16) T sC[CC][NT];
@@ -727,15 +763,9 @@ __global__ void __launch_bounds__(256) fwd_tiled_kernel(Geometry g, const T* __r
   const int64_t i0 = (int64_t)blockIdx.x * kTK;
   const int clo = zrange[0], chi = zrange[1];
   const bool tq = g.with_torque != 0;
-  // per-thread wavenumbers (for the epilogue)
-  int64_t my_k[4];
-  bool my_ok[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t it = i0 + kg * 4 + q;
-    my_ok[q] = it < total;
-    my_k[q] = my_ok[q] ? chunk_kidx(g, it, kx0, w) : 0;
-  }
+  fill_ktile(g, kt, i0, total, kx0, w, kTK);
+  __syncthreads();
+  const size_t plane = (size_t)g.ny * g.pitch;
   for (int o = 0; o < 3; ++o) {
     const bool use_b = tq && o < 2;
     for (int n0 = 0; n0 < N; n0 += NT) {
@@ -749,23 +779,21 @@ __global__ void __launch_bounds__(256) fwd_tiled_kernel(Geometry g, const T* __r
         for (int e = tid; e < CC * kTK; e += 256) {
           const int cc = e / kTK, kk = e - cc * kTK;
           const int c = c0 + cc;
-          const int64_t it = i0 + kk;
+          const int col = kt.col[kk];
           cplx<T> a = mk<T>((T)0, (T)0), bb = mk<T>((T)0, (T)0);
-          if (c <= chi && it < total) {
-            const int64_t kidx = chunk_kidx(g, it, kx0, w);
-            const int kxi = (int)(kidx % g.nkx), kyi = (int)(kidx / g.nkx);
-            const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
-            const T hkx = (T)(M_PI * (double)kxi / g.Lx), hky = (T)(M_PI * (double)nyv / g.Ly);  // k/2
-            a = grid[gidx(g, o, c, kyi, kxi)];
+          if (c <= chi && col >= 0) {
+            const T hkx = (T)kt.hkx[kk], hky = (T)kt.hky[kk];  // k/2
+            auto at = [&](int f) { return grid[((size_t)f * g.nz + c) * plane + col]; };
+            a = at(o);
             if (tq) {
               if (o == 0) {
-                a = a + mul_i(scl(grid[gidx(g, 5, c, kyi, kxi)], hky));
-                bb = scl(grid[gidx(g, 4, c, kyi, kxi)], (T)-0.5);
+                a = a + mul_i(scl(at(5), hky));
+                bb = scl(at(4), (T)-0.5);
               } else if (o == 1) {
-                a = a - mul_i(scl(grid[gidx(g, 5, c, kyi, kxi)], hkx));
-                bb = scl(grid[gidx(g, 3, c, kyi, kxi)], (T)0.5);
+                a = a - mul_i(scl(at(5), hkx));
+                bb = scl(at(3), (T)0.5);
               } else {
-                a = a + mul_i(scl(grid[gidx(g, 4, c, kyi, kxi)], hkx) - scl(grid[gidx(g, 3, c, kyi, kxi)], hky));
+                a = a + mul_i(scl(at(4), hkx) - scl(at(3), hky));
               }
             }
           }
@@ -805,8 +833,13 @@ __global__ void __launch_bounds__(256) fwd_tiled_kernel(Geometry g, const T* __r
         const int n = n0 + ng * NG + j;
         if (n < N) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (my_ok[q]) kbuf[((size_t)o * N + n) * K + my_k[q]] = acc[q][j];
+          for (int q = 0; q < 4; ++q) {
+            const int kk = kg * 4 + q;
+            if (kt.col[kk] >= 0) {
+              const int kid = kt.kid[kk] >= 0 ? kt.kid[kk] : -1 - kt.kid[kk];
+              kbuf[((size_t)o * N + n) * K + kid] = acc[q][j];
+            }
+          }
         }
       }
     }
@@ -824,6 +857,7 @@ __global__ void __launch_bounds__(128) bwd_tiled_kernel(Geometry g, const T* __r
                                                         const int* __restrict__ zrange, int kx0, int w) {
   constexpr int TK = 32;           // wavenumbers per block; thread: 4 wavenumbers x 3 planes
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ KTile kt;
   const int N = g.nz;
   const int tid = threadIdx.x, kq = tid & 7, cg = tid >> 3;  // 8 k-groups x 16 plane-groups
   T* sE = reinterpret_cast<T*>(smraw);                       // [N][TK]
@@ -837,33 +871,26 @@ __global__ void __launch_bounds__(128) bwd_tiled_kernel(Geometry g, const T* __r
   const bool corr_mode = g.mode != DPS_FREE;
   const bool top = g.mode == DPS_SLIT;
   const T scale = (T)(1.0 / ((double)g.nx * (double)g.ny));
-  const T H = (T)g.H;
+  fill_ktile(g, kt, i0, total, kx0, w, TK);
+  __syncthreads();
   // ---- correction amplitudes and e/g vectors for the block's wavenumbers ----
   T* se = reinterpret_cast<T*>(sY);        // [N][TK]
   T* sg = se + N * TK;                     // [N][TK]
   for (int e = tid; e < TK * 12; e += 128) {
     const int kk = e / 12, q = e - kk * 12;
-    const int64_t it = i0 + kk;
     cplx<T> v = mk<T>((T)0, (T)0);
-    if (corr_mode && it < total) {
-      const int64_t kidx = chunk_kidx(g, it, kx0, w);
-      if (kidx != 0) v = kaux[(size_t)q * K + kidx];
-    }
+    const int kid = kt.kid[kk];
+    if (corr_mode && kt.col[kk] >= 0 && kid > 0) v = kaux[(size_t)q * K + kid];
     sAmp[kk * 12 + q] = v;
   }
   if (corr_mode) {
     for (int e = tid; e < N * TK; e += 128) {
       const int j = e / TK, kk = e - j * TK;
-      const int64_t it = i0 + kk;
       T ev = (T)0, gv = (T)0;
-      if (it < total) {
-        const int64_t kidx = chunk_kidx(g, it, kx0, w);
-        const int kxi = (int)(kidx % g.nkx), kyi = (int)(kidx / g.nkx);
-        const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
-        const double kx = 2.0 * M_PI * (double)kxi / g.Lx, ky = 2.0 * M_PI * (double)nyv / g.Ly;
-        const T kt = (T)sqrt(kx * kx + ky * ky);
+      if (kt.col[kk] >= 0) {
+        const T kt_ = (T)kt.kk[kk];
         const T zt = zeta_g[j];
-        ev = (sizeof(T) == 4) ? (T)expf((float)(-kt * zt)) : (T)exp((double)(-kt * zt));
+        ev = (sizeof(T) == 4) ? (T)expf((float)(-kt_ * zt)) : (T)exp((double)(-kt_ * zt));
         gv = zt * ev;
       }
       se[e] = ev;
@@ -888,31 +915,15 @@ __global__ void __launch_bounds__(128) bwd_tiled_kernel(Geometry g, const T* __r
       }
     }
   }
-  // per-thread wavenumbers
-  int64_t my_k[4];
-  bool my_ok[4];
-  T hkx[4], hky[4];
-  bool my_nyq[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t it = i0 + kq * 4 + q;
-    my_ok[q] = it < total;
-    my_k[q] = my_ok[q] ? chunk_kidx(g, it, kx0, w) : 0;
-    const KInfo ki = kinfo(g, my_k[q]);
-    my_nyq[q] = ki.nyq;
-    hkx[q] = (T)(0.5 * ki.kx);
-    hky[q] = (T)(0.5 * ki.ky);
-  }
+  const size_t plane = (size_t)g.ny * g.pitch;
   for (int f = 0; f < 3; ++f) {
     __syncthreads();  // sY reuse
     // y_tot[n][k] = y + aE E + aG G + (-1)^n (bE E + bG G)
     for (int e = tid; e < N * TK; e += 128) {
       const int n = e / TK, kk = e - n * TK;
-      const int64_t it = i0 + kk;
       cplx<T> y = mk<T>((T)0, (T)0);
-      if (it < total) {
-        const int64_t kidx = chunk_kidx(g, it, kx0, w);
-        y = kbuf[((size_t)f * N + n) * K + kidx];
+      if (kt.col[kk] >= 0 && kt.kid[kk] >= 0) {
+        y = kbuf[((size_t)f * N + n) * K + kt.kid[kk]];
         if (corr_mode) {
           const T Ev = sE[e], Gv = sG[e];
           const cplx<T>* am = sAmp + kk * 12 + 4 * f;
@@ -960,27 +971,31 @@ __global__ void __launch_bounds__(128) bwd_tiled_kernel(Geometry g, const T* __r
         if (c < clo || c > chi) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (!my_ok[q]) continue;
-          const int kxi = (int)(my_k[q] % g.nkx), kyi = (int)(my_k[q] / g.nkx);
-          if (my_nyq[q]) {
-            grid[gidx(g, f, c, kyi, kxi)] = mk<T>((T)0, (T)0);
-            if (CURL) grid[gidx(g, 3 + f, c, kyi, kxi)] = mk<T>((T)0, (T)0);
+          const int kk = kq * 4 + q;
+          const int col = kt.col[kk];
+          if (col < 0) continue;
+          const size_t o0 = ((size_t)f * g.nz + c) * plane + col;
+          if (kt.kid[kk] < 0) {  // Nyquist column
+            grid[o0] = mk<T>((T)0, (T)0);
+            if (CURL) grid[o0 + 3 * (size_t)g.nz * plane] = mk<T>((T)0, (T)0);
             continue;
           }
           const cplx<T> v = acc[q][j];
-          grid[gidx(g, f, c, kyi, kxi)] = scl(v, scale);
+          const T hkx = (T)kt.hkx[kk], hky = (T)kt.hky[kk];
+          grid[o0] = scl(v, scale);
           if (CURL) {
             // omega = 1/2 (i ky w - Dv, Du - i kx w, i kx v - i ky u), assembled field by field
-            const size_t ox = gidx(g, 3, c, kyi, kxi), oy = gidx(g, 4, c, kyi, kxi), oz = gidx(g, 5, c, kyi, kxi);
+            const size_t ox = ((size_t)3 * g.nz + c) * plane + col, oy = ((size_t)4 * g.nz + c) * plane + col,
+                         oz = ((size_t)5 * g.nz + c) * plane + col;
             if (f == 0) {
               grid[oy] = scl(dac[q][j], (T)0.5 * scale);
-              grid[oz] = scl(mul_i(v), -hky[q] * scale);
+              grid[oz] = scl(mul_i(v), -hky * scale);
             } else if (f == 1) {
               grid[ox] = scl(dac[q][j], (T)-0.5 * scale);
-              grid[oz] = grid[oz] + scl(mul_i(v), hkx[q] * scale);
+              grid[oz] = grid[oz] + scl(mul_i(v), hkx * scale);
             } else {
-              grid[ox] = grid[ox] + scl(mul_i(v), hky[q] * scale);
-              grid[oy] = grid[oy] - scl(mul_i(v), hkx[q] * scale);
+              grid[ox] = grid[ox] + scl(mul_i(v), hky * scale);
+              grid[oy] = grid[oy] - scl(mul_i(v), hkx * scale);
             }
           }
         }
