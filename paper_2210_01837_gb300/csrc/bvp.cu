@@ -92,7 +92,7 @@ __device__ __forceinline__ int64_t chunk_kidx(const Geometry& g, int64_t i, int 
 struct KTile {
   int col[64];
   int kid[64];
-  float hkx[64], hky[64];
+  double hkx[64], hky[64];
   double kk[64];
 };
 
@@ -116,8 +116,8 @@ __device__ __forceinline__ void fill_ktile(const Geometry& g, KTile& t, int64_t 
     }
     t.col[kk] = col;
     t.kid[kk] = kid;
-    t.hkx[kk] = (float)hx;
-    t.hky[kk] = (float)hy;
+    t.hkx[kk] = hx;
+    t.hky[kk] = hy;
     t.kk[kk] = 2.0 * sqrt(hx * hx + hy * hy);
   }
 }
