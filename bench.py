@@ -201,9 +201,9 @@ def main():
     ap.add_argument("--div", type=int, default=1, help="shrink the workload by div^2 in area (testing only)")
     args = ap.parse_args()
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2210_01837_gb300.replicas import Collective, rank_env, replica_seed_offset, whole_job_rate
+    env = rank_env()
+    rank, world, local = env.rank, env.world, env.local
 
     if args.impl == "reference":
         run_reference(args, rank)
@@ -222,7 +222,7 @@ def main():
     binding.load()
 
     div = args.div
-    params, pos, F, T = rollers_1m(n=(1 << 20) // (div * div), nxy=3072 // div, L=2048.0 / div, seed_offset=3 + rank)
+    params, pos, F, T = rollers_1m(n=(1 << 20) // (div * div), nxy=3072 // div, L=2048.0 / div, seed_offset=replica_seed_offset(rank))
     n = len(pos)
     dev = torch.device("cuda", local)
     tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -231,16 +231,8 @@ def main():
     W = torch.empty_like(U)
     stream = torch.cuda.current_stream(dev)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    coll = Collective(dist, dev)
+    barrier, max_over_ranks = coll.barrier, coll.max
 
     def time_plan(plan, steps, warmup, stage_log=None):
         for _ in range(warmup):
@@ -277,7 +269,7 @@ def main():
     clocks = sampler.stop()
     t_mixed = max_over_ranks(t_mixed)
     ms_step = t_mixed / args.steps * 1e3
-    value = world * args.steps / t_mixed
+    value = whole_job_rate(world, args.steps, t_mixed)
     U_mixed = U.clone()
     W_mixed = W.clone()
 
@@ -317,7 +309,7 @@ def main():
     for _ in range(e2e_steps):
         plan.apply_host(h_pos, h_F, h_T, h_U, h_W)
     t_e2e = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * e2e_steps / t_e2e, "unit": "products/s", "h2d_bytes_per_step": 3 * h_pos.nbytes,
+    e2e = {"value": whole_job_rate(world, e2e_steps, t_e2e), "unit": "products/s", "h2d_bytes_per_step": 3 * h_pos.nbytes,
            "d2h_bytes_per_step": 2 * h_U.nbytes, "steps": e2e_steps}
     plan.close()
     del plan
@@ -328,7 +320,7 @@ def main():
         plan64 = binding.Plan.from_params(params, with_torque=True, precision="fp64", max_n=n)
         t64 = max_over_ranks(time_plan(plan64, args.fp64_steps, 1))
         d = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-        fp64 = {"value": world * args.fp64_steps / t64, "unit": "products/s",
+        fp64 = {"value": whole_job_rate(world, args.fp64_steps, t64), "unit": "products/s",
                 "ms_per_step": t64 / args.fp64_steps * 1e3, "steps": args.fp64_steps,
                 "mixed_speedup": (world * args.steps / t_mixed) / (world * args.fp64_steps / t64),
                 "mixed_vs_fp64_rel_l2": {"U": d(U_mixed, U), "Omega": d(W_mixed, W)}}
