@@ -736,272 +736,309 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
 }
 
 // ---------------------------------------------------------------------------------------------
-// Tiled forms of the two transforms (N <= 128): a block owns 64 consecutive wavenumbers of the chunk
-// and computes dense products with shared-memory tiles and register blocking (4 wavenumbers x a few
-// rows per thread), so every shared load feeds several FMAs.
+// Lane-per-wavenumber forms of the two transforms (N <= 128).  A block owns 32 consecutive
+// wavenumbers of the chunk, one per lane, and its warps split the output rows in groups of PG
+// (Chebyshev index n forward, occupied plane backward).  The per-wavenumber operands sit in shared
+// memory and are read one value per lane; the table rows sit beside them and are read as warp-wide
+// broadcasts, so every shared load feeds PG or more FMAs and no table is read from global memory
+// inside the contraction loops.
 // ---------------------------------------------------------------------------------------------
-constexpr int kTK = 64;     // wavenumbers per block
-template <typename T> __host__ __device__ constexpr int kCC() { return sizeof(T) == 4 ? 16 : 8; }  // planes per chunk
+constexpr int kLaneK = 32;
+template <typename T> __host__ __device__ constexpr int fwd_pg() { return sizeof(T) == 4 ? 12 : 6; }
+template <typename T> __host__ __device__ constexpr int bwd_pg() { return sizeof(T) == 4 ? 8 : 4; }
+template <typename T> __host__ __device__ constexpr int bwd_warps() { return sizeof(T) == 4 ? 5 : 10; }
 
-// forward: kbuf[o][n][k] = sum_c C[n][c] a_c(k) + DC[n][c] b_c(k), n-tiles of 16*NG rows
-template <typename T, int NG>
-__global__ void __launch_bounds__(256) fwd_tiled_kernel(Geometry g, const T* __restrict__ ct, const T* __restrict__ dct,
-                                                        int npad, const cplx<T>* __restrict__ grid,
-                                                        cplx<T>* __restrict__ kbuf, const int* __restrict__ zrange,
-                                                        int kx0, int w) {
-  constexpr int NT = 16 * NG;
-  constexpr int CC = kCC<T>();
+// PG consecutive shared-memory table values (16-byte aligned) into registers
+// (PG a multiple of 4 for float, of 2 for double)
+template <int PG>
+__device__ __forceinline__ void ld_row(const float* p, float (&o)[PG]) {
+  static_assert(PG % 4 == 0, "float rows load as float4");
+#pragma unroll
+  for (int q = 0; q < PG; q += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p + q);
+    o[q] = v.x; o[q + 1] = v.y; o[q + 2] = v.z; o[q + 3] = v.w;
+  }
+}
+template <int PG>
+__device__ __forceinline__ void ld_row(const double* p, double (&o)[PG]) {
+  static_assert(PG % 2 == 0, "double rows load as double2");
+#pragma unroll
+  for (int q = 0; q < PG; q += 2) {
+    const double2 v = *reinterpret_cast<const double2*>(p + q);
+    o[q] = v.x; o[q + 1] = v.y;
+  }
+}
+
+// forward: kbuf[o][n][k] = sum_c C[n][c] a_o(c, k) + DC[n][c] b_o(c, k) over the occupied planes, with
+// a_o = f_o + (1/2)(i k x tau)_o and the derivative terms of the half-curl b_x = -tau_y/2, b_y = tau_x/2
+template <typename T> __host__ __device__ constexpr int fwd_max_threads() { return sizeof(T) == 4 ? 384 : 512; }
+
+template <typename T, int PG, bool TQ>
+__global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry g, const T* __restrict__ ct,
+                                                                        const T* __restrict__ dct, int npad,
+                                                                        const cplx<T>* __restrict__ grid,
+                                                                        cplx<T>* __restrict__ kbuf,
+                                                                        const int* __restrict__ zrange, int kx0, int w,
+                                                                        int cz) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ KTile kt;
-  __shared__ __align__(16) cplx<T> sA[CC][kTK];
-  __shared__ __align__(16) cplx<T> sB[CC][kTK];
-  __shared__ __align__(16) T sC[CC][NT];
-  __shared__ __align__(16) T sD[CC][NT];
+  constexpr int NF = TQ ? 6 : 3;  // staged fields per (plane, wavenumber); the first 3 (5) become a (a, b)
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int nthreads = blockDim.x;
+  const int NP = (nthreads >> 5) * PG;  // rows covered by the block (>= N)
   const int N = g.nz;
-  const int tid = threadIdx.x, kg = tid & 15, ng = tid >> 4;
+  cplx<T>* sV = reinterpret_cast<cplx<T>*>(smraw);               // [cz][NF][32]
+  T* sM = reinterpret_cast<T*>(sV + (size_t)cz * NF * kLaneK);  // [cz][2][NP]
   const int64_t K = (int64_t)g.nkx * g.ny;
-  const int64_t total = (int64_t)w * g.ny;
-  const int64_t i0 = (int64_t)blockIdx.x * kTK;
-  const int clo = zrange[0], chi = zrange[1];
-  const bool tq = g.with_torque != 0;
-  fill_ktile(g, kt, i0, total, kx0, w, kTK);
+  fill_ktile(g, kt, (int64_t)blockIdx.x * kLaneK, (int64_t)w * g.ny, kx0, w, kLaneK);
   __syncthreads();
+  const int clo = zrange[0], chi = zrange[1];
   const size_t plane = (size_t)g.ny * g.pitch;
-  for (int o = 0; o < 3; ++o) {
-    const bool use_b = tq && o < 2;
-    for (int n0 = 0; n0 < N; n0 += NT) {
-      cplx<T> acc[4][NG];
+  cplx<T> acc[3][PG];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+  for (int o = 0; o < 3; ++o)
 #pragma unroll
-        for (int j = 0; j < NG; ++j) acc[q][j] = mk<T>((T)0, (T)0);
-      for (int c0 = clo; c0 <= chi; c0 += CC) {
-        __syncthreads();
-        for (int e = tid; e < CC * kTK; e += 256) {
-          const int cc = e / kTK, kk = e - cc * kTK;
-          const int c = c0 + cc;
-          const int col = kt.col[kk];
-          cplx<T> a = mk<T>((T)0, (T)0), bb = mk<T>((T)0, (T)0);
-          if (c <= chi && col >= 0) {
-            const T hkx = (T)kt.hkx[kk], hky = (T)kt.hky[kk];  // k/2
-            auto at = [&](int f) { return grid[((size_t)f * g.nz + c) * plane + col]; };
-            a = at(o);
-            if (tq) {
-              if (o == 0) {
-                a = a + mul_i(scl(at(5), hky));
-                bb = scl(at(4), (T)-0.5);
-              } else if (o == 1) {
-                a = a - mul_i(scl(at(5), hkx));
-                bb = scl(at(3), (T)0.5);
-              } else {
-                a = a + mul_i(scl(at(4), hkx) - scl(at(3), hky));
-              }
-            }
-          }
-          sA[cc][kk] = a;
-          sB[cc][kk] = bb;
-        }
-        for (int e = tid; e < CC * NT; e += 256) {
-          const int cc = e / NT, nn = e - cc * NT;
-          const int c = c0 + cc, n = n0 + nn;
-          const bool ok = c <= chi && n < N;
-          sC[cc][nn] = ok ? ct[(size_t)c * npad + n] : (T)0;
-          sD[cc][nn] = (ok && use_b) ? dct[(size_t)c * npad + n] : (T)0;
-        }
-        __syncthreads();
-        const int ccmax = min(CC, chi - c0 + 1);
-        for (int cc = 0; cc < ccmax; ++cc) {
-          cplx<T> a[4], bv[4];
+    for (int p = 0; p < PG; ++p) acc[o][p] = mk<T>((T)0, (T)0);
+  for (int c0 = clo; c0 <= chi; c0 += cz) {
+    const int nc = min(cz, chi - c0 + 1);
+    __syncthreads();  // the previous chunk has been consumed
+    // stage the field values and the table rows of this chunk (asynchronous copies)
+    for (int e = threadIdx.x; e < nc * NF * kLaneK; e += nthreads) {
+      const int l = e & 31, r = e >> 5;
+      const int cl = r / NF, f = r - cl * NF;
+      const int col = kt.col[l];
+      if (col >= 0) async_elem(sV + e, grid + ((size_t)f * g.nz + c0 + cl) * plane + col);
+      else sV[e] = mk<T>((T)0, (T)0);
+    }
+    const int mrow = (TQ ? 2 : 1) * NP;
+    for (int e = threadIdx.x; e < nc * mrow; e += nthreads) {
+      const int cl = e / mrow, r = e - cl * mrow;
+      const int m = r >= NP ? 1 : 0, n = r - m * NP;
+      T* dst = sM + (size_t)cl * 2 * NP + r;
+      if (n < N) async_elem(dst, (m ? dct : ct) + (size_t)(c0 + cl) * npad + n);
+      else *dst = (T)0;
+    }
+    cp_commit();
+    cp_wait_all();
+    __syncthreads();
+    if (TQ) {
+      // a_o = f_o + (1/2)(i k x tau)_o in slots 0..2, b_x = -tau_y/2, b_y = tau_x/2 in slots 3, 4
+      for (int e = threadIdx.x; e < nc * kLaneK; e += nthreads) {
+        const int cl = e >> 5, l = e & 31;
+        cplx<T>* v = sV + (size_t)cl * NF * kLaneK + l;
+        const T hkx = (T)kt.hkx[l], hky = (T)kt.hky[l];  // k/2
+        const cplx<T> tx = v[3 * kLaneK], ty = v[4 * kLaneK], tz = v[5 * kLaneK];
+        v[0] = v[0] + mul_i(scl(tz, hky));
+        v[kLaneK] = v[kLaneK] - mul_i(scl(tz, hkx));
+        v[2 * kLaneK] = v[2 * kLaneK] + mul_i(scl(ty, hkx) - scl(tx, hky));
+        v[3 * kLaneK] = scl(ty, (T)-0.5);
+        v[4 * kLaneK] = scl(tx, (T)0.5);
+      }
+      __syncthreads();
+    }
+    for (int cl = 0; cl < nc; ++cl) {
+      const cplx<T>* vr = sV + (size_t)cl * NF * kLaneK + lane;
+      const cplx<T> a0 = vr[0], a1 = vr[kLaneK], a2 = vr[2 * kLaneK];
+      T cm[PG];
+      ld_row<PG>(sM + (size_t)cl * 2 * NP + wi * PG, cm);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            a[q] = sA[cc][kg * 4 + q];
-            bv[q] = sB[cc][kg * 4 + q];
-          }
+      for (int p = 0; p < PG; ++p) {
+        acc[0][p].x += cm[p] * a0.x; acc[0][p].y += cm[p] * a0.y;
+        acc[1][p].x += cm[p] * a1.x; acc[1][p].y += cm[p] * a1.y;
+        acc[2][p].x += cm[p] * a2.x; acc[2][p].y += cm[p] * a2.y;
+      }
+      if (TQ) {
+        const cplx<T> b0 = vr[3 * kLaneK], b1 = vr[4 * kLaneK];
+        T dm[PG];
+        ld_row<PG>(sM + (size_t)cl * 2 * NP + NP + wi * PG, dm);
 #pragma unroll
-          for (int j = 0; j < NG; ++j) {
-            const T cm = sC[cc][ng * NG + j];
-            const T dm = sD[cc][ng * NG + j];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              acc[q][j].x += cm * a[q].x + dm * bv[q].x;
-              acc[q][j].y += cm * a[q].y + dm * bv[q].y;
-            }
-          }
+        for (int p = 0; p < PG; ++p) {
+          acc[0][p].x += dm[p] * b0.x; acc[0][p].y += dm[p] * b0.y;
+          acc[1][p].x += dm[p] * b1.x; acc[1][p].y += dm[p] * b1.y;
         }
       }
+    }
+  }
+  if (kt.col[lane] >= 0) {
+    const int kid = kt.kid[lane] >= 0 ? kt.kid[lane] : -1 - kt.kid[lane];
 #pragma unroll
-      for (int j = 0; j < NG; ++j) {
-        const int n = n0 + ng * NG + j;
-        if (n < N) {
+    for (int p = 0; p < PG; ++p) {
+      const int n = wi * PG + p;
+      if (n < N) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int kk = kg * 4 + q;
-            if (kt.col[kk] >= 0) {
-              const int kid = kt.kid[kk] >= 0 ? kt.kid[kk] : -1 - kt.kid[kk];
-              kbuf[((size_t)o * N + n) * K + kid] = acc[q][j];
-            }
-          }
-        }
+        for (int o = 0; o < 3; ++o) kbuf[((size_t)o * N + n) * K + kid] = acc[o][p];
       }
     }
   }
 }
 
-// backward: per field, y_tot = y + DCT(correction node values) via E = C e, G = C g (e = e^{-k zeta},
-// g = zeta e; the top family uses the mirrored vectors), then nodes = IC y_tot and, with torques,
-// the derivative ICD y_tot; the half-curl is assembled across the three fields in the grid.
-template <typename T, bool CURL>
-__global__ void __launch_bounds__(128) bwd_tiled_kernel(Geometry g, const T* __restrict__ cmat /*[N][N] C[n][j]*/,
-                                                        const T* __restrict__ ict, const T* __restrict__ icdt, int cpad,
-                                                        const T* __restrict__ zeta_g, const cplx<T>* __restrict__ kbuf,
+// backward: node values on the occupied planes, u_f(z_c) = sum_n IC[c][n] y_f[n] + corr_f(z_c), with
+// corr_f = (cE + cG zeta) e^{-k zeta} (+ (tE + tG xi) e^{-k xi} between two walls); with torques the
+// half-curl (Eq. 11) from ICD y and the spectral derivative SD corr of the correction node values.
+// CORR: 0 no wall, 1 bottom wall, 2 both walls.
+template <typename T, int PG, bool CURL, int CORR>
+__global__ void __launch_bounds__(32 * bwd_warps<T>(), sizeof(T) == 4 ? 2 : 1) bwd_lane_kernel(Geometry g, const T* __restrict__ ict,
+                                                        const T* __restrict__ icdt, const T* __restrict__ sdt,
+                                                        int cpad, const T* __restrict__ zeta_g,
+                                                        const cplx<T>* __restrict__ kbuf,
                                                         const cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ grid,
                                                         const int* __restrict__ zrange, int kx0, int w) {
-  constexpr int TK = 32;           // wavenumbers per block; thread: 4 wavenumbers x 3 planes
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ KTile kt;
+  constexpr bool DE = CURL && CORR > 0;              // derivative of the correction
+  constexpr int NT = CURL ? (CORR > 0 ? 3 : 2) : 1;  // staged tables: IC, ICD, SD
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int nthreads = blockDim.x;
+  const int CZ = (nthreads >> 5) * PG;  // planes per chunk
   const int N = g.nz;
-  const int tid = threadIdx.x, kq = tid & 7, cg = tid >> 3;  // 8 k-groups x 16 plane-groups
-  T* sE = reinterpret_cast<T*>(smraw);                       // [N][TK]
-  T* sG = sE + N * TK;                                        // [N][TK]
-  cplx<T>* sY = reinterpret_cast<cplx<T>*>(sG + N * TK);     // [N][TK]  (e, g staged here first)
-  cplx<T>* sAmp = sY + N * TK;                                // [TK][12]
+  const int N4 = (N + 3) & ~3;
+  cplx<T>* sY = reinterpret_cast<cplx<T>*>(smraw);                     // [3][N][32]
+  cplx<T>* sAmp = sY + (size_t)3 * N * kLaneK;                         // [12][32]
+  T* sE = reinterpret_cast<T*>(sAmp + (CORR ? 12 * kLaneK : 0));      // [N][32] e^{-k zeta_j}
+  T* sZ = sE + (CORR ? (size_t)N * kLaneK : 0);                        // [N4] zeta_j
+  T* sM = sZ + (CORR ? N4 : 0);                                        // [N][NT][CZ]
   const int64_t K = (int64_t)g.nkx * g.ny;
-  const int64_t total = (int64_t)w * g.ny;
-  const int64_t i0 = (int64_t)blockIdx.x * TK;
-  const int clo = zrange[0], chi = zrange[1];
-  const bool corr_mode = g.mode != DPS_FREE;
-  const bool top = g.mode == DPS_SLIT;
-  const T scale = (T)(1.0 / ((double)g.nx * (double)g.ny));
-  fill_ktile(g, kt, i0, total, kx0, w, TK);
+  fill_ktile(g, kt, (int64_t)blockIdx.x * kLaneK, (int64_t)w * g.ny, kx0, w, kLaneK);
   __syncthreads();
-  // ---- correction amplitudes and e/g vectors for the block's wavenumbers ----
-  T* se = reinterpret_cast<T*>(sY);        // [N][TK]
-  T* sg = se + N * TK;                     // [N][TK]
-  for (int e = tid; e < TK * 12; e += 128) {
-    const int kk = e / 12, q = e - kk * 12;
-    cplx<T> v = mk<T>((T)0, (T)0);
-    const int kid = kt.kid[kk];
-    if (corr_mode && kt.col[kk] >= 0 && kid > 0) v = kaux[(size_t)q * K + kid];
-    sAmp[kk * 12 + q] = v;
+  for (int e = threadIdx.x; e < 3 * N * kLaneK; e += nthreads) {
+    const int l = e & 31, fn = e >> 5;
+    const int kid = kt.kid[l];
+    if (kt.col[l] >= 0 && kid >= 0) async_elem(sY + e, kbuf + (size_t)fn * K + kid);
+    else sY[e] = mk<T>((T)0, (T)0);
   }
-  if (corr_mode) {
-    for (int e = tid; e < N * TK; e += 128) {
-      const int j = e / TK, kk = e - j * TK;
-      T ev = (T)0, gv = (T)0;
-      if (kt.col[kk] >= 0) {
-        const T kt_ = (T)kt.kk[kk];
-        const T zt = zeta_g[j];
-        ev = (sizeof(T) == 4) ? (T)expf((float)(-kt_ * zt)) : (T)exp((double)(-kt_ * zt));
-        gv = zt * ev;
-      }
-      se[e] = ev;
-      sg[e] = gv;
+  if (CORR) {
+    for (int e = threadIdx.x; e < 12 * kLaneK; e += nthreads) {
+      const int l = e & 31, q = e >> 5;
+      const int kid = kt.kid[l];
+      if (kt.col[l] >= 0 && kid > 0) async_elem(sAmp + e, kaux + (size_t)q * K + kid);
+      else sAmp[e] = mk<T>((T)0, (T)0);
     }
-    __syncthreads();
-    // E[n][k] = sum_j C[n][j] e[j][k], G likewise; thread: 4 k x ceil(N/16) n
-    for (int n = cg; n < N; n += 16) {
-      T aE[4] = {0, 0, 0, 0}, aG[4] = {0, 0, 0, 0};
-      for (int j = 0; j < N; ++j) {
-        const T cm = cmat[(size_t)n * N + j];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          aE[q] += cm * se[j * TK + kq * 4 + q];
-          aG[q] += cm * sg[j * TK + kq * 4 + q];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        sE[n * TK + kq * 4 + q] = aE[q];
-        sG[n * TK + kq * 4 + q] = aG[q];
-      }
+    for (int e = threadIdx.x; e < N * kLaneK; e += nthreads) {
+      const int l = e & 31, j = e >> 5;
+      const T kz = (T)kt.kk[l] * zeta_g[j];
+      sE[e] = (kt.col[l] >= 0) ? ((sizeof(T) == 4) ? (T)expf((float)-kz) : (T)exp((double)-kz)) : (T)0;
     }
+    for (int j = threadIdx.x; j < N4; j += nthreads) sZ[j] = j < N ? zeta_g[j] : (T)0;
   }
+  const int clo = zrange[0], chi = zrange[1];
   const size_t plane = (size_t)g.ny * g.pitch;
-  for (int f = 0; f < 3; ++f) {
-    __syncthreads();  // sY reuse
-    // y_tot[n][k] = y + aE E + aG G + (-1)^n (bE E + bG G)
-    for (int e = tid; e < N * TK; e += 128) {
-      const int n = e / TK, kk = e - n * TK;
-      cplx<T> y = mk<T>((T)0, (T)0);
-      if (kt.col[kk] >= 0 && kt.kid[kk] >= 0) {
-        y = kbuf[((size_t)f * N + n) * K + kt.kid[kk]];
-        if (corr_mode) {
-          const T Ev = sE[e], Gv = sG[e];
-          const cplx<T>* am = sAmp + kk * 12 + 4 * f;
-          y = y + scl(am[0], Ev) + scl(am[1], Gv);
-          if (top) {
-            const T sgn = (n & 1) ? (T)-1 : (T)1;
-            y = y + scl(scl(am[2], Ev) + scl(am[3], Gv), sgn);
-          }
-        }
-      }
-      sY[e] = y;
+  const size_t fstride = (size_t)g.nz * plane;
+  const T scale = (T)(1.0 / ((double)g.nx * (double)g.ny));
+  const int col = kt.col[lane];
+  const int kidl = kt.kid[lane];
+  const T hkx = (T)kt.hkx[lane], hky = (T)kt.hky[lane];
+  cp_commit();
+  for (int c0 = clo; c0 <= chi; c0 += CZ) {
+    __syncthreads();  // previous chunk consumed
+    for (int e = threadIdx.x; e < N * NT * CZ; e += nthreads) {
+      const int n = e / (NT * CZ), r = e - n * (NT * CZ);
+      const int m = r / CZ, cl = r - m * CZ;
+      const int c = c0 + cl;
+      const T* tab = m == 0 ? ict : (m == 1 ? icdt : sdt);
+      if (c <= chi) async_elem(sM + e, tab + (size_t)n * cpad + c);
+      else sM[e] = (T)0;
     }
+    cp_commit();
+    cp_wait_all();  // (the first chunk also completes the staging of y and the amplitudes)
     __syncthreads();
-    const bool need_d = CURL && f < 2;
-    for (int c0 = (clo & ~3); c0 <= chi; c0 += 48) {
-      // thread planes c0 + cg*3 + {0,1,2}
-      cplx<T> acc[4][3], dac[4][3];
+    const int cw = c0 + wi * PG;  // first plane of this warp
+    if (cw > chi) continue;
+    cplx<T> au[PG], av[PG], aw[PG], du[PG], dv[PG];
+    T dE[PG], dG[PG], dEt[PG], dGt[PG];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+    for (int p = 0; p < PG; ++p) {
+      au[p] = av[p] = aw[p] = du[p] = dv[p] = mk<T>((T)0, (T)0);
+      dE[p] = dG[p] = dEt[p] = dGt[p] = (T)0;
+    }
+    for (int n = 0; n < N; ++n) {
+      const cplx<T> yu = sY[(size_t)n * kLaneK + lane];
+      const cplx<T> yv = sY[(size_t)(N + n) * kLaneK + lane];
+      const cplx<T> yw = sY[(size_t)(2 * N + n) * kLaneK + lane];
+      const T* mr = sM + (size_t)n * NT * CZ + wi * PG;
+      T ic[PG];
+      ld_row<PG>(mr, ic);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) { acc[q][j] = mk<T>((T)0, (T)0); dac[q][j] = mk<T>((T)0, (T)0); }
-      const int cb = c0 + cg * 3;
-      if (cb <= chi && cb + 2 >= clo) {
-        for (int n = 0; n < N; ++n) {
-          cplx<T> yv[4];
+      for (int p = 0; p < PG; ++p) {
+        au[p].x += ic[p] * yu.x; au[p].y += ic[p] * yu.y;
+        av[p].x += ic[p] * yv.x; av[p].y += ic[p] * yv.y;
+        aw[p].x += ic[p] * yw.x; aw[p].y += ic[p] * yw.y;
+      }
+      if (CURL) {
+        T id[PG];
+        ld_row<PG>(mr + CZ, id);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) yv[q] = sY[n * TK + kq * 4 + q];
-          const T* ir = ict + (size_t)n * cpad + cb;
-          const T* dr = icdt + (size_t)n * cpad + cb;
+        for (int p = 0; p < PG; ++p) {
+          du[p].x += id[p] * yu.x; du[p].y += id[p] * yu.y;
+          dv[p].x += id[p] * yv.x; dv[p].y += id[p] * yv.y;
+        }
+      }
+      if (DE) {
+        const T en = sE[(size_t)n * kLaneK + lane], gn = sZ[n] * en;
+        T sd[PG];
+        ld_row<PG>(mr + 2 * CZ, sd);
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            const T im = ir[j];
-            const T dm = need_d ? dr[j] : (T)0;
+        for (int p = 0; p < PG; ++p) {
+          dE[p] += sd[p] * en;
+          dG[p] += sd[p] * gn;
+        }
+        if (CORR == 2) {
+          const T et = sE[(size_t)(N - 1 - n) * kLaneK + lane], gt = sZ[N - 1 - n] * et;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              acc[q][j].x += im * yv[q].x; acc[q][j].y += im * yv[q].y;
-              if (need_d) { dac[q][j].x += dm * yv[q].x; dac[q][j].y += dm * yv[q].y; }
-            }
+          for (int p = 0; p < PG; ++p) {
+            dEt[p] += sd[p] * et;
+            dGt[p] += sd[p] * gt;
           }
         }
       }
+    }
+    if (col < 0) continue;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int c = cb + j;
-        if (c < clo || c > chi) continue;
+    for (int p = 0; p < PG; ++p) {
+      const int c = cw + p;
+      if (c > chi) break;
+      const size_t o0 = (size_t)c * plane + col;
+      if (kidl < 0) {  // Nyquist column
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int kk = kq * 4 + q;
-          const int col = kt.col[kk];
-          if (col < 0) continue;
-          const size_t o0 = ((size_t)f * g.nz + c) * plane + col;
-          if (kt.kid[kk] < 0) {  // Nyquist column
-            grid[o0] = mk<T>((T)0, (T)0);
-            if (CURL) grid[o0 + 3 * (size_t)g.nz * plane] = mk<T>((T)0, (T)0);
-            continue;
-          }
-          const cplx<T> v = acc[q][j];
-          const T hkx = (T)kt.hkx[kk], hky = (T)kt.hky[kk];
-          grid[o0] = scl(v, scale);
-          if (CURL) {
-            // omega = 1/2 (i ky w - Dv, Du - i kx w, i kx v - i ky u), assembled field by field
-            const size_t ox = ((size_t)3 * g.nz + c) * plane + col, oy = ((size_t)4 * g.nz + c) * plane + col,
-                         oz = ((size_t)5 * g.nz + c) * plane + col;
-            if (f == 0) {
-              grid[oy] = scl(dac[q][j], (T)0.5 * scale);
-              grid[oz] = scl(mul_i(v), -hky * scale);
-            } else if (f == 1) {
-              grid[ox] = scl(dac[q][j], (T)-0.5 * scale);
-              grid[oz] = grid[oz] + scl(mul_i(v), hkx * scale);
-            } else {
-              grid[ox] = grid[ox] + scl(mul_i(v), hky * scale);
-              grid[oy] = grid[oy] - scl(mul_i(v), hkx * scale);
-            }
+        for (int f = 0; f < (CURL ? 6 : 3); ++f) grid[o0 + f * fstride] = mk<T>((T)0, (T)0);
+        continue;
+      }
+      cplx<T> u = au[p], v = av[p], wv = aw[p], Du = du[p], Dv = dv[p];
+      if (CORR) {
+        const T zc = sZ[c], ec = sE[(size_t)c * kLaneK + lane];
+        auto amp = [&](int q) { return sAmp[q * kLaneK + lane]; };
+        u = u + scl(amp(0) + scl(amp(1), zc), ec);
+        v = v + scl(amp(4) + scl(amp(5), zc), ec);
+        wv = wv + scl(amp(8) + scl(amp(9), zc), ec);
+        if (CORR == 2) {
+          const T xc = sZ[N - 1 - c], et = sE[(size_t)(N - 1 - c) * kLaneK + lane];
+          u = u + scl(amp(2) + scl(amp(3), xc), et);
+          v = v + scl(amp(6) + scl(amp(7), xc), et);
+          wv = wv + scl(amp(10) + scl(amp(11), xc), et);
+        }
+        if (DE) {
+          Du = Du + scl(amp(0), dE[p]) + scl(amp(1), dG[p]);
+          Dv = Dv + scl(amp(4), dE[p]) + scl(amp(5), dG[p]);
+          if (CORR == 2) {
+            Du = Du + scl(amp(2), dEt[p]) + scl(amp(3), dGt[p]);
+            Dv = Dv + scl(amp(6), dEt[p]) + scl(amp(7), dGt[p]);
           }
         }
+      }
+      grid[o0] = scl(u, scale);
+      grid[o0 + fstride] = scl(v, scale);
+      grid[o0 + 2 * fstride] = scl(wv, scale);
+      if (CURL) {
+        // omega = 1/2 (i ky w - Dv, Du - i kx w, i kx v - i ky u)
+        const cplx<T> ox = scl(mul_i(wv), hky) - scl(Dv, (T)0.5);
+        const cplx<T> oy = scl(Du, (T)0.5) - scl(mul_i(wv), hkx);
+        const cplx<T> oz = scl(mul_i(v), hkx) - scl(mul_i(u), hky);
+        grid[o0 + 3 * fstride] = scl(ox, scale);
+        grid[o0 + 4 * fstride] = scl(oy, scale);
+        grid[o0 + 5 * fstride] = scl(oz, scale);
       }
     }
   }
+  cp_wait_all();  // no copy outlives the block when no plane is occupied
 }
 
 template <typename T> constexpr int fwd_nb() { return sizeof(T) == 4 ? 24 : 12; }
@@ -1009,6 +1046,56 @@ template <typename T> constexpr int bwd_cb() { return sizeof(T) == 4 ? 12 : 4; }
 
 size_t fwd_smem(const Plan& p, size_t tsz) { return 2 * (size_t)p.g.nz * p.kt.npad * tsz; }
 size_t bwd_smem(const Plan& p, size_t tsz) { return (p.g.with_torque ? 3 : 1) * (size_t)p.g.nz * p.kt.cpad * tsz; }
+
+// launch shape of the lane-per-wavenumber forward transform; threads = 0 when it does not apply
+struct LaneCfg {
+  int threads = 0, cz = 0;
+  size_t smem = 0;
+};
+constexpr size_t kFwdLaneSmem = 80 * 1024;   // two blocks per SM
+constexpr size_t kBwdLaneSmem = 200 * 1024;  // largest backward stage
+
+template <typename T>
+LaneCfg fwd_lane_cfg(const Geometry& g) {
+  LaneCfg c;
+  constexpr int PG = fwd_pg<T>();
+  const int nw = (g.nz + PG - 1) / PG;
+  if (g.nz > 128 || 32 * nw > fwd_max_threads<T>()) return c;
+  const int nf = g.with_torque ? 6 : 3;
+  const size_t per_plane = (size_t)nf * kLaneK * sizeof(cplx<T>) + (size_t)2 * nw * PG * sizeof(T);
+  c.threads = 32 * nw;
+  c.cz = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.nz, kFwdLaneSmem / per_plane));
+  c.smem = per_plane * c.cz;
+  return c;
+}
+
+template <typename T>
+size_t bwd_lane_smem(const Geometry& g) {
+  const size_t N = (size_t)g.nz, N4 = (N + 3) & ~(size_t)3;
+  const bool corr = g.mode != DPS_FREE;
+  const int nt = g.with_torque ? (corr ? 3 : 2) : 1;
+  const size_t cz = (size_t)bwd_warps<T>() * bwd_pg<T>();
+  size_t b = 3 * N * kLaneK * sizeof(cplx<T>) + N * nt * cz * sizeof(T);
+  if (corr) b += 12 * kLaneK * sizeof(cplx<T>) + N * kLaneK * sizeof(T) + N4 * sizeof(T);
+  return (g.nz <= 128 && b <= kBwdLaneSmem) ? b : 0;
+}
+
+template <typename T, bool CURL, int CORR>
+void launch_bwd_lane(const Plan& p, int kx0, int w, cudaStream_t s) {
+  const Geometry& g = p.g;
+  const unsigned blocks = (unsigned)(((int64_t)w * g.ny + kLaneK - 1) / kLaneK);
+  bwd_lane_kernel<T, bwd_pg<T>(), CURL, CORR><<<blocks, 32 * bwd_warps<T>(), bwd_lane_smem<T>(g), s>>>(
+      g, reinterpret_cast<const T*>(p.kt.ict), reinterpret_cast<const T*>(p.kt.icdt),
+      reinterpret_cast<const T*>(p.kt.sdt), p.kt.cpad, reinterpret_cast<const T*>(p.tab.zeta),
+      reinterpret_cast<const cplx<T>*>(p.kt.kbuf), reinterpret_cast<const cplx<T>*>(p.kt.kaux),
+      reinterpret_cast<cplx<T>*>(p.grid), p.zrange, kx0, w);
+}
+
+template <typename T, bool CURL, int CORR>
+bool set_bwd_lane_smem(size_t bytes) {
+  return cudaFuncSetAttribute(bwd_lane_kernel<T, bwd_pg<T>(), CURL, CORR>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
 
 }  // namespace
 
@@ -1031,7 +1118,7 @@ int bvp_occupancy_blocks(const Plan& p) {
 
 template <typename T>
 int bvp_prepare(Plan& p) {
-  // shared-memory staging of the transform tables when they fit
+  // shared-memory staging of the transform tables of the per-thread fallbacks when they fit
   const size_t fs = fwd_smem(p, sizeof(T)), bs = bwd_smem(p, sizeof(T));
   p.kt.fwd_smem = fs <= 160 * 1024 ? (int)fs : 0;
   p.kt.bwd_smem = bs <= 160 * 1024 ? (int)bs : 0;
@@ -1045,11 +1132,22 @@ int bvp_prepare(Plan& p) {
   if (cudaFuncSetAttribute(bwd_kernel<T, CB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.kt.bwd_smem) !=
       cudaSuccess)
     return 0;
-  const int tsm = (int)((size_t)std::min(p.g.nz, 128) * 32 * (2 * sizeof(T) + sizeof(cplx<T>)) + 32 * 12 * sizeof(cplx<T>));
-  if (cudaFuncSetAttribute(bwd_tiled_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm) != cudaSuccess)
-    return 0;
-  if (cudaFuncSetAttribute(bwd_tiled_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm) != cudaSuccess)
-    return 0;
+  const LaneCfg fc = fwd_lane_cfg<T>(p.g);
+  if (fc.threads > 0) {
+    constexpr int PG = fwd_pg<T>();
+    if (cudaFuncSetAttribute(fwd_lane_kernel<T, PG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fc.smem) != cudaSuccess ||
+        cudaFuncSetAttribute(fwd_lane_kernel<T, PG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fc.smem) != cudaSuccess)
+      return 0;
+  }
+  const size_t bl = bwd_lane_smem<T>(p.g);
+  if (bl > 0) {
+    if (!set_bwd_lane_smem<T, true, 0>(bl) || !set_bwd_lane_smem<T, true, 1>(bl) ||
+        !set_bwd_lane_smem<T, true, 2>(bl) || !set_bwd_lane_smem<T, false, 0>(bl) ||
+        !set_bwd_lane_smem<T, false, 1>(bl) || !set_bwd_lane_smem<T, false, 2>(bl))
+      return 0;
+  }
   return 1;
 }
 
@@ -1062,27 +1160,29 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
   cplx<T>* kbuf = reinterpret_cast<cplx<T>*>(p.kt.kbuf);
   cplx<T>* kaux = reinterpret_cast<cplx<T>*>(p.kt.kaux);
-  const bool tiled = g.nz <= 128;
-  if (part == 0 && tiled) {
-    const unsigned tb = (unsigned)((total + kTK - 1) / kTK);
-    fwd_tiled_kernel<T, 5><<<tb, 256, 0, s>>>(g, reinterpret_cast<const T*>(p.kt.ct),
-                                              reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, grid, kbuf, p.zrange,
-                                              kx0, w);
-  } else if (part == 2 && tiled) {
-    const unsigned tb = (unsigned)((total + 31) / 32);
-    const size_t sm = (size_t)g.nz * 32 * (2 * sizeof(T) + sizeof(cplx<T>)) + 32 * 12 * sizeof(cplx<T>);
+  const LaneCfg fc = fwd_lane_cfg<T>(g);
+  if (part == 0 && fc.threads > 0) {
+    const unsigned lb = (unsigned)((total + kLaneK - 1) / kLaneK);
+    constexpr int PG = fwd_pg<T>();
     if (g.with_torque)
-      bwd_tiled_kernel<T, true><<<tb, 128, sm, s>>>(g, reinterpret_cast<const T*>(p.kt.cmat),
-                                                    reinterpret_cast<const T*>(p.kt.ict),
-                                                    reinterpret_cast<const T*>(p.kt.icdt), p.kt.cpad,
-                                                    reinterpret_cast<const T*>(p.tab.zeta), kbuf, kaux, grid, p.zrange,
-                                                    kx0, w);
+      fwd_lane_kernel<T, PG, true><<<lb, fc.threads, fc.smem, s>>>(
+          g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, grid, kbuf,
+          p.zrange, kx0, w, fc.cz);
     else
-      bwd_tiled_kernel<T, false><<<tb, 128, sm, s>>>(g, reinterpret_cast<const T*>(p.kt.cmat),
-                                                     reinterpret_cast<const T*>(p.kt.ict),
-                                                     reinterpret_cast<const T*>(p.kt.icdt), p.kt.cpad,
-                                                     reinterpret_cast<const T*>(p.tab.zeta), kbuf, kaux, grid, p.zrange,
-                                                     kx0, w);
+      fwd_lane_kernel<T, PG, false><<<lb, fc.threads, fc.smem, s>>>(
+          g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, grid, kbuf,
+          p.zrange, kx0, w, fc.cz);
+  } else if (part == 2 && bwd_lane_smem<T>(g) > 0) {
+    const int corr = g.mode == DPS_FREE ? 0 : (g.mode == DPS_SLIT ? 2 : 1);
+    if (g.with_torque) {
+      if (corr == 0) launch_bwd_lane<T, true, 0>(p, kx0, w, s);
+      else if (corr == 1) launch_bwd_lane<T, true, 1>(p, kx0, w, s);
+      else launch_bwd_lane<T, true, 2>(p, kx0, w, s);
+    } else {
+      if (corr == 0) launch_bwd_lane<T, false, 0>(p, kx0, w, s);
+      else if (corr == 1) launch_bwd_lane<T, false, 1>(p, kx0, w, s);
+      else launch_bwd_lane<T, false, 2>(p, kx0, w, s);
+    }
   } else if (part == 0) {
     fwd_kernel<T, NB><<<blocks, kBvpThreads, p.kt.fwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, p.kt.fwd_smem > 0,

@@ -121,6 +121,7 @@ struct Plan {
   int* status;          // [1] device status bits
   void* ws;             // per-slot workspace of the per-k solver
   int bvp_blocks;       // persistent grid size of the per-k solver
+  int fft_grid[4];      // resident grids of the persistent FFT passes: rows fwd/inv, columns fwd/inv
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)
   double* stage_in;     // [max_n][9]
@@ -139,6 +140,33 @@ struct Plan {
   cudaEvent_t ev0[kMaxTimed], ev1[kMaxTimed];
 };
 
+// ---------------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async): the issuing thread continues at once and
+// cp_wait_all() later waits for its own copies (a __syncthreads() then publishes them), so a block
+// can keep many copies in flight without holding registers for them.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// one naturally aligned element of 4, 8 or 16 bytes
+template <typename E>
+__device__ __forceinline__ void async_elem(E* s, const E* g) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8 || sizeof(E) == 16, "cp.async sizes");
+  if (sizeof(E) == 16) cp_async16(s, g);
+  else if (sizeof(E) == 8) cp_async8(s, g);
+  else cp_async4(s, g);
+}
+
 // status bits written by kernels
 enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4 };
 
@@ -156,6 +184,6 @@ template <typename T> void launch_bvp(const Plan& p, int part, int kx0, int w, c
 template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
-template <typename T> int fft_smem_ok(const Plan& p);
+template <typename T> int fft_smem_ok(Plan& p);
 
 }  // namespace dps

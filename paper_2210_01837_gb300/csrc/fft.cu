@@ -5,14 +5,19 @@
 //
 // Layout of one field/plane: ny rows; each row holds nx reals in real space and nx/2+1 complex
 // values (pitch >= nx/2+1 complex) in x-Fourier space, in place.
-//   * row pass:    one block transforms two real rows packed as one complex sequence
-//                  (z = r0 + i r1), then separates the two half spectra; inverse likewise.
-//   * column pass: one block transforms `cw` adjacent x-wavenumber columns along y.
+//   * row pass:    a unit is two real rows packed as one complex sequence (z = r0 + i r1), whose
+//                  transform is then split into the two half spectra; inverse likewise.
+//   * column pass: a unit is `cw` adjacent x-wavenumber columns of one plane, transformed along y.
+// Both passes run persistent blocks (as many as fit on the GPU) that walk the units of the live
+// planes; a block stages its next unit in shared memory with cp.async while it transforms the
+// current one, so HBM traffic overlaps the shared-memory butterflies.
 // Each 1D transform is a self-sorting (Stockham) mixed-radix FFT in shared memory written from the
 // textbook formulation: stage s with radix R and span Ns multiplies input j + r n/R by
 // W_{Ns R}^{(j mod Ns) r}, applies an R-point DFT, and stores to (j / Ns) Ns R + (j mod Ns) + r Ns.
 // Radices 8, 4, 2 (hand-written butterflies) and 3, 5, 7 (direct DFT with exact constants).
 // Twiddles W_n^t = exp(-2 pi i t/n) come from a table built in double precision on the host.
+#include <algorithm>
+
 #include "dps_internal.cuh"
 
 namespace dps {
@@ -240,117 +245,242 @@ __device__ cplx<T>* fft_smem(cplx<T>* b0, cplx<T>* b1, const FftPlan& fp, int lb
   return in;
 }
 
-__device__ __forceinline__ bool plane_live(const int* zrange, int c) { return c >= zrange[0] && c <= zrange[1]; }
+// `bytes` (a multiple of 4) from a 16-byte aligned global address to a 16-byte aligned shared one
+__device__ __forceinline__ void async_bytes(void* s, const void* g, int bytes) {
+  const int n16 = bytes >> 4;
+  char* sc = reinterpret_cast<char*>(s);
+  const char* gc = reinterpret_cast<const char*>(g);
+  for (int i = threadIdx.x; i < n16; i += blockDim.x) cp_async16(sc + 16 * i, gc + 16 * i);
+  for (int i = 4 * n16 + threadIdx.x; i < (bytes >> 2); i += blockDim.x) cp_async4(sc + 4 * i, gc + 4 * i);
+}
 
+// Work units of the persistent transforms: (field, live plane, unit within the plane), unit fastest.
+struct UnitMap {
+  int clo, nlive, per_plane;
+  long long total;
+  __device__ UnitMap(const Geometry& g, const int* zrange, int per) {
+    clo = zrange[0];
+    nlive = max(0, zrange[1] - clo + 1);
+    per_plane = per;
+    total = (long long)g.nfields * nlive * per;
+  }
+  __device__ void at(long long u, int& f, int& c, int& j) const {
+    j = (int)(u % per_plane);
+    const long long r = u / per_plane;
+    c = clo + (int)(r % nlive);
+    f = (int)(r / nlive);
+  }
+};
+
+// real rows rounded up so that the second staged row stays 16-byte aligned
+__host__ __device__ __forceinline__ int staged_len(int n) { return (n + 3) & ~3; }
+
+// Row pass, forward: a unit is two real rows y0 = 2j, y1 = 2j + 1, packed as z = r0 + i r1.
 template <typename T>
-__global__ void row_r2c_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, T* __restrict__ grid,
-                               const int* __restrict__ zrange) {
+__global__ void __launch_bounds__(256, 2) row_r2c_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                      T* __restrict__ grid, const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* b1 = b0 + pad16(g.nx);
-  const int c = blockIdx.y, f = blockIdx.z;
-  if (!plane_live(zrange, c)) return;
-  const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
-  const bool has1 = y1 < g.ny;
+  const int nx = g.nx, nxr = staged_len(nx);
+  T* raw = reinterpret_cast<T*>(smraw);  // [2][nxr]
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(raw + 2 * nxr);
+  cplx<T>* b1 = b0 + pad16(nx) + 1;
+  const UnitMap um(g, zrange, (g.ny + 1) / 2);
   const size_t rowlen = (size_t)2 * g.pitch;
-  T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + y0) * rowlen;
-  T* row1 = row0 + rowlen;
-  for (int a = threadIdx.x; a < g.nx; a += blockDim.x) b0[pad16(a)] = mk<T>(row0[a], has1 ? row1[a] : (T)0);
-  __syncthreads();
-  const cplx<T>* res = fft_smem<T, -1>(b0, b1, fp, 0, tw);
-  cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
-  cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row1);
-  const T half = (T)0.5;
-  for (int k = threadIdx.x; k <= g.nx / 2; k += blockDim.x) {
-    const cplx<T> zk = res[pad16(k)];
-    const cplx<T> zm = conjg(res[pad16(k == 0 ? 0 : g.nx - k)]);
-    c0[k] = scl(zk + zm, half);
-    if (has1) {
-      const cplx<T> d = zk - zm;  // (zk - conj z_{-k}) / (2i)
-      c1[k] = mk<T>(half * d.y, -half * d.x);
+  auto row0_of = [&](long long u, bool& has1) {
+    int f, c, j;
+    um.at(u, f, c, j);
+    has1 = 2 * j + 1 < g.ny;
+    return grid + ((size_t)(f * g.nz + c) * g.ny + 2 * j) * rowlen;
+  };
+  auto issue = [&](long long u) {
+    bool has1;
+    const T* r0 = row0_of(u, has1);
+    async_bytes(raw, r0, nx * (int)sizeof(T));
+    if (has1) async_bytes(raw + nxr, r0 + rowlen, nx * (int)sizeof(T));
+    cp_commit();
+  };
+  long long u = blockIdx.x;
+  if (u < um.total) issue(u);
+  for (; u < um.total; u += gridDim.x) {
+    bool has1;
+    T* row0 = row0_of(u, has1);
+    cp_wait_all();
+    __syncthreads();  // staged rows visible; previous unit's epilogue done with b0/b1
+    for (int a = threadIdx.x; a < nx; a += blockDim.x) b0[pad16(a)] = mk<T>(raw[a], has1 ? raw[nxr + a] : (T)0);
+    __syncthreads();
+    if (u + gridDim.x < um.total) issue(u + gridDim.x);
+    const cplx<T>* res = fft_smem<T, -1>(b0, b1, fp, 0, tw);
+    cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
+    cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row0 + rowlen);
+    const T half = (T)0.5;
+    for (int k = threadIdx.x; k <= nx / 2; k += blockDim.x) {
+      const cplx<T> zk = res[pad16(k)];
+      const cplx<T> zm = conjg(res[pad16(k == 0 ? 0 : nx - k)]);
+      c0[k] = scl(zk + zm, half);
+      if (has1) {
+        const cplx<T> d = zk - zm;  // (zk - conj z_{-k}) / (2i)
+        c1[k] = mk<T>(half * d.y, -half * d.x);
+      }
     }
   }
 }
 
+// Row pass, inverse: two half spectra -> z with z_k = X0_k + i X1_k (Hermitian extension), one FFT.
 template <typename T>
-__global__ void row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, T* __restrict__ grid,
-                               const int* __restrict__ zrange) {
+__global__ void __launch_bounds__(256, 2) row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                      T* __restrict__ grid, const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* b1 = b0 + pad16(g.nx);
-  const int c = blockIdx.y, f = blockIdx.z;
-  if (!plane_live(zrange, c)) return;
-  const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
-  const bool has1 = y1 < g.ny;
+  const int nx = g.nx, nh = nx / 2 + 1, nhr = (nh + 1) & ~1;
+  cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [2][nhr]
+  cplx<T>* b0 = raw + 2 * nhr;
+  cplx<T>* b1 = b0 + pad16(nx) + 1;
+  const UnitMap um(g, zrange, (g.ny + 1) / 2);
   const size_t rowlen = (size_t)2 * g.pitch;
-  T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + y0) * rowlen;
-  T* row1 = row0 + rowlen;
-  const cplx<T>* c0 = reinterpret_cast<const cplx<T>*>(row0);
-  const cplx<T>* c1 = reinterpret_cast<const cplx<T>*>(row1);
-  for (int k = threadIdx.x; k <= g.nx / 2; k += blockDim.x) {
-    const cplx<T> x0 = c0[k];
-    const cplx<T> x1 = has1 ? c1[k] : mk<T>((T)0, (T)0);
-    b0[pad16(k)] = x0 + mul_i(x1);
-    if (k > 0 && k < g.nx - k) b0[pad16(g.nx - k)] = conjg(x0) + mul_i(conjg(x1));
-  }
-  __syncthreads();
-  const cplx<T>* res = fft_smem<T, +1>(b0, b1, fp, 0, tw);
-  for (int a = threadIdx.x; a < g.nx; a += blockDim.x) {
-    const cplx<T> v = res[pad16(a)];
-    row0[a] = v.x;
-    if (has1) row1[a] = v.y;
+  auto row0_of = [&](long long u, bool& has1) {
+    int f, c, j;
+    um.at(u, f, c, j);
+    has1 = 2 * j + 1 < g.ny;
+    return grid + ((size_t)(f * g.nz + c) * g.ny + 2 * j) * rowlen;
+  };
+  auto issue = [&](long long u) {
+    bool has1;
+    const T* r0 = row0_of(u, has1);
+    async_bytes(raw, r0, nh * (int)sizeof(cplx<T>));
+    if (has1) async_bytes(raw + nhr, r0 + rowlen, nh * (int)sizeof(cplx<T>));
+    cp_commit();
+  };
+  long long u = blockIdx.x;
+  if (u < um.total) issue(u);
+  for (; u < um.total; u += gridDim.x) {
+    bool has1;
+    T* row0 = row0_of(u, has1);
+    T* row1 = row0 + rowlen;
+    cp_wait_all();
+    __syncthreads();
+    for (int k = threadIdx.x; k < nh; k += blockDim.x) {
+      const cplx<T> x0 = raw[k];
+      const cplx<T> x1 = has1 ? raw[nhr + k] : mk<T>((T)0, (T)0);
+      b0[pad16(k)] = x0 + mul_i(x1);
+      if (k > 0 && k < nx - k) b0[pad16(nx - k)] = conjg(x0) + mul_i(conjg(x1));
+    }
+    __syncthreads();
+    if (u + gridDim.x < um.total) issue(u + gridDim.x);
+    const cplx<T>* res = fft_smem<T, +1>(b0, b1, fp, 0, tw);
+    for (int a = threadIdx.x; a < nx; a += blockDim.x) {
+      const cplx<T> v = res[pad16(a)];
+      row0[a] = v.x;
+      if (has1) row1[a] = v.y;
+    }
   }
 }
 
+// Column pass: a unit is cw adjacent x-wavenumber columns [kx0, kx0 + cw) of one plane, along y.
 template <typename T, int DIR>
-__global__ void col_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ grid,
-                           const int* __restrict__ zrange, int lcw, int kxs, int kxe) {
+__global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                  cplx<T>* __restrict__ grid, const int* __restrict__ zrange, int lcw,
+                                                  int kxs, int kxe) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int cw = 1 << lcw;
-  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* b1 = b0 + pad16(g.ny * cw);
-  const int c = blockIdx.y, f = blockIdx.z;
-  if (!plane_live(zrange, c)) return;
-  const int kx0 = kxs + blockIdx.x * cw;
-  const int ncols = min(cw, kxe - kx0);
-  cplx<T>* base = grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
   const int tot = g.ny << lcw;
-  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int y = t >> lcw, b = t & (cw - 1);
-    b0[pad16(t)] = (b < ncols) ? base[(size_t)y * g.pitch + b] : mk<T>((T)0, (T)0);
-  }
-  __syncthreads();
-  const cplx<T>* res = fft_smem<T, DIR>(b0, b1, fp, lcw, tw);
-  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int y = t >> lcw, b = t & (cw - 1);
-    if (b < ncols) base[(size_t)y * g.pitch + b] = res[pad16(t)];
+  cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [ny][cw]
+  cplx<T>* b0 = raw + tot;
+  cplx<T>* b1 = b0 + pad16(tot) + 1;
+  const UnitMap um(g, zrange, (kxe - kxs + cw - 1) >> lcw);
+  auto base_of = [&](long long u, int& ncols) {
+    int f, c, j;
+    um.at(u, f, c, j);
+    const int kx0 = kxs + (j << lcw);
+    ncols = min(cw, kxe - kx0);
+    return grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
+  };
+  auto issue = [&](long long u) {
+    int ncols;
+    const cplx<T>* base = base_of(u, ncols);
+    const bool wide = ncols == cw && (cw * sizeof(cplx<T>)) % 16 == 0 &&
+                      (reinterpret_cast<size_t>(base) & 15) == 0;
+    if (wide) {
+      const int per = (cw * (int)sizeof(cplx<T>)) >> 4;  // 16-byte pieces per row
+      for (int t = threadIdx.x; t < g.ny * per; t += blockDim.x) {
+        const int y = t / per, q = t - y * per;
+        cp_async16(reinterpret_cast<char*>(raw + (y << lcw)) + 16 * q,
+                   reinterpret_cast<const char*>(base + (size_t)y * g.pitch) + 16 * q);
+      }
+    } else {
+      for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int y = t >> lcw, b = t & (cw - 1);
+        if (b < ncols) async_elem(raw + t, base + (size_t)y * g.pitch + b);
+      }
+    }
+    cp_commit();
+  };
+  long long u = blockIdx.x;
+  if (u < um.total) issue(u);
+  for (; u < um.total; u += gridDim.x) {
+    int ncols;
+    cplx<T>* base = base_of(u, ncols);
+    cp_wait_all();
+    __syncthreads();
+    for (int t = threadIdx.x; t < tot; t += blockDim.x)
+      b0[pad16(t)] = ((t & (cw - 1)) < ncols) ? raw[t] : mk<T>((T)0, (T)0);
+    __syncthreads();
+    if (u + gridDim.x < um.total) issue(u + gridDim.x);
+    const cplx<T>* res = fft_smem<T, DIR>(b0, b1, fp, lcw, tw);
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int y = t >> lcw, b = t & (cw - 1);
+      if (b < ncols) base[(size_t)y * g.pitch + b] = res[pad16(t)];
+    }
   }
 }
 
 size_t padded_bytes(int n, size_t esz) { return (size_t)(n + (n >> 4) + 1) * esz; }
 
-// log2 of the column block: widest power of two (at most 8) whose two padded buffers leave room for
-// two blocks per SM (100 KB each), else one block (200 KB)
+template <typename T>
+size_t row_r2c_smem(const Geometry& g) {
+  return (size_t)2 * staged_len(g.nx) * sizeof(T) + 2 * padded_bytes(g.nx, sizeof(cplx<T>));
+}
+template <typename T>
+size_t row_c2r_smem(const Geometry& g) {
+  return (size_t)2 * ((g.nx / 2 + 2) & ~1) * sizeof(cplx<T>) + 2 * padded_bytes(g.nx, sizeof(cplx<T>));
+}
+template <typename T>
+size_t col_smem(const Geometry& g, int l) {
+  return (size_t)(g.ny << l) * sizeof(cplx<T>) + 2 * padded_bytes(g.ny << l, sizeof(cplx<T>));
+}
+
+// log2 of the column block: the widest (at most 8 columns) whose staged and working buffers fit in
+// 200 KB of shared memory
 template <typename T>
 int col_lwidth(const Plan& p) {
   for (int l = 3; l > 0; --l)
-    if (2 * padded_bytes(p.g.ny << l, sizeof(cplx<T>)) <= 100 * 1024) return l;
-  for (int l = 3; l > 0; --l)
-    if (2 * padded_bytes(p.g.ny << l, sizeof(cplx<T>)) <= 200 * 1024) return l;
+    if (col_smem<T>(p.g, l) <= 200 * 1024) return l;
   return 0;
+}
+
+template <typename KernelT>
+int resident_grid(KernelT kernel, int threads, size_t smem, int device) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return std::max(1, per_sm) * std::max(1, sms);
 }
 
 }  // namespace
 
 template <typename T>
-int fft_smem_ok(const Plan& p) {
-  const size_t row = 2 * padded_bytes(p.g.nx, sizeof(cplx<T>));
-  const size_t col = 2 * padded_bytes(p.g.ny << col_lwidth<T>(p), sizeof(cplx<T>));
-  if (row > 220 * 1024 || col > 220 * 1024) return 0;
-  cudaFuncSetAttribute(row_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row);
-  cudaFuncSetAttribute(row_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row);
-  cudaFuncSetAttribute(col_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col);
-  cudaFuncSetAttribute(col_kernel<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col);
+int fft_smem_ok(Plan& p) {
+  const size_t r2c = row_r2c_smem<T>(p.g), c2r = row_c2r_smem<T>(p.g);
+  const int lcw = col_lwidth<T>(p);
+  const size_t col = col_smem<T>(p.g, lcw);
+  if (r2c > 220 * 1024 || c2r > 220 * 1024 || col > 220 * 1024) return 0;
+  if (cudaFuncSetAttribute(row_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r2c) != cudaSuccess ||
+      cudaFuncSetAttribute(row_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c2r) != cudaSuccess ||
+      cudaFuncSetAttribute(col_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col) != cudaSuccess ||
+      cudaFuncSetAttribute(col_kernel<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col) != cudaSuccess)
+    return 0;
+  p.fft_grid[0] = resident_grid(row_r2c_kernel<T>, 256, r2c, p.device);
+  p.fft_grid[1] = resident_grid(row_c2r_kernel<T>, 256, c2r, p.device);
+  p.fft_grid[2] = resident_grid(col_kernel<T, -1>, 512, col, p.device);
+  p.fft_grid[3] = resident_grid(col_kernel<T, +1>, 512, col, p.device);
   return 1;
 }
 
@@ -358,12 +488,12 @@ template <typename T>
 void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
-  dim3 gr((g.ny + 1) / 2, g.nz, g.nfields);
-  const size_t sm = 2 * padded_bytes(g.nx, sizeof(cplx<T>));
   if (dir < 0)
-    row_r2c_kernel<T><<<gr, 256, sm, s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
+    row_r2c_kernel<T><<<p.fft_grid[0], 256, row_r2c_smem<T>(g), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid),
+                                                                       p.zrange);
   else
-    row_c2r_kernel<T><<<gr, 256, sm, s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid), p.zrange);
+    row_c2r_kernel<T><<<p.fft_grid[1], 256, row_c2r_smem<T>(g), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid),
+                                                                       p.zrange);
 }
 
 template <typename T>
@@ -371,17 +501,17 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   const int lcw = col_lwidth<T>(p);
-  const int cw = 1 << lcw;
-  dim3 gc((kxe - kxs + cw - 1) / cw, g.nz, g.nfields);
-  const size_t sm = 2 * padded_bytes(g.ny << lcw, sizeof(cplx<T>));
+  const size_t sm = col_smem<T>(g, lcw);
   if (dir < 0)
-    col_kernel<T, -1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw, kxs, kxe);
+    col_kernel<T, -1><<<p.fft_grid[2], 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw,
+                                                     kxs, kxe);
   else
-    col_kernel<T, +1><<<gc, 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw, kxs, kxe);
+    col_kernel<T, +1><<<p.fft_grid[3], 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw,
+                                                     kxs, kxe);
 }
 
-template int fft_smem_ok<float>(const Plan&);
-template int fft_smem_ok<double>(const Plan&);
+template int fft_smem_ok<float>(Plan&);
+template int fft_smem_ok<double>(Plan&);
 template void launch_fft_rows<float>(const Plan&, int, cudaStream_t);
 template void launch_fft_rows<double>(const Plan&, int, cudaStream_t);
 template void launch_fft_cols<float>(const Plan&, int, int, int, cudaStream_t);
