@@ -585,7 +585,7 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBvpThreads) solve_kernel(Geometry g, const double* __restrict__ band,
+__global__ void __launch_bounds__(kBvpThreads, 3) solve_kernel(Geometry g, const double* __restrict__ band,
                                                             const T* __restrict__ bandT, cplx<T>* __restrict__ kbuf,
                                                             cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ pws,
                                                             cplx<double>* __restrict__ sw, double* __restrict__ fr,
