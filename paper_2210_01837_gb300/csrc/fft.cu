@@ -9,8 +9,10 @@
 //                  transform is then split into the two half spectra; inverse likewise.
 //   * column pass: a unit is `cw` adjacent x-wavenumber columns of one plane, transformed along y.
 // Both passes run persistent blocks (as many as fit on the GPU) that walk the units of the live
-// planes; a block stages its next unit in shared memory with cp.async while it transforms the
-// current one, so HBM traffic overlaps the shared-memory butterflies.
+// planes.  A block stages a unit in shared memory with cp.async; the first stage reads the staged
+// values directly, after which the staging buffer takes the next unit's copies while the later
+// stages alternate between two padded work buffers, so HBM traffic overlaps the butterflies and
+// each unit crosses shared memory 2 S + 2 times for S stages.
 // Each 1D transform is a self-sorting (Stockham) mixed-radix FFT in shared memory written from the
 // textbook formulation: stage s with radix R and span Ns multiplies input j + r n/R by
 // W_{Ns R}^{(j mod Ns) r}, applies an R-point DFT, and stores to (j / Ns) Ns R + (j mod Ns) + r Ns.
@@ -181,35 +183,83 @@ template <typename T, int DIR> struct Dft<T, 7, DIR> {
   static __device__ __forceinline__ void run(cplx<T>* v) { dft_direct<T, 7, DIR>(v); }
 };
 
+// 12-point DFT as 4 x 3: x[3 a + b] -> X[c + 4 d]; inner DFT4 over a, twiddle W12^(b c), outer DFT3 over b
+template <typename T, int DIR> struct Dft<T, 12, DIR> {
+  static __device__ __forceinline__ void run(cplx<T>* v) {
+    const T h = (T)0.5, s3 = (T)0.86602540378443865, sg = (T)DIR;  // cos/sin of 30 and 60 degrees
+    cplx<T> y[3][4];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      cplx<T> w[4] = {v[b], v[3 + b], v[6 + b], v[9 + b]};
+      Dft<T, 4, DIR>::run(w);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y[b][c] = w[c];
+    }
+    // W12^m = (cos(2 pi m / 12), DIR sin(2 pi m / 12)) for m = b c
+    y[1][1] = y[1][1] * mk<T>(s3, sg * h);
+    y[1][2] = y[1][2] * mk<T>(h, sg * s3);
+    y[1][3] = rot_quarter<T, DIR>(y[1][3]);
+    y[2][1] = y[2][1] * mk<T>(h, sg * s3);
+    y[2][2] = y[2][2] * mk<T>(-h, sg * s3);
+    y[2][3] = mk<T>(-y[2][3].x, -y[2][3].y);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      cplx<T> w[3] = {y[0][c], y[1][c], y[2][c]};
+      Dft<T, 3, DIR>::run(w);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[c + 4 * d] = w[d];
+    }
+  }
+};
+
 // Shared-memory index with one pad element per 16: breaks the power-of-two strides of the
 // Stockham writes across bank groups.
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
-// One Stockham stage over `batch` interleaved sequences (element e of sequence b at e*batch + b,
-// batch a power of two given by its log).  Division by the span Ns uses a multiply-high with a
-// per-stage magic number (exact for indices below 2^20).
+// A transform of n points over 2^lbatch interleaved sequences runs on about n 2^lbatch / kFftPer
+// threads (whole warps), so a radix-R stage gives each thread about kFftPer / R butterflies.
+constexpr int kFftPer = 12;
+
+// First Stockham stage (span 1, no twiddles): butterfly (jj, b) reads elements jj + r n/R of
+// sequence b through `in(flat index)` and writes X to buf[(jj R + r) 2^lbatch + b] (padded).
+template <typename T, int R, int DIR, class In>
+__device__ __forceinline__ void stage_first(cplx<T>* __restrict__ buf, int n, int lbatch, const In& in) {
+  const int nr = n / R;
+  const int total = nr << lbatch;
+  const int bmask = (1 << lbatch) - 1;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int b = t & bmask, jj = t >> lbatch;
+    cplx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in(((jj + r * nr) << lbatch) + b);
+    Dft<T, R, DIR>::run(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad16(((jj * R + r) << lbatch) + b)] = v[r];
+  }
+}
+
+// Later stage (span Ns), out of place: stage s multiplies input j + r n/R by W_{Ns R}^{(j mod Ns) r},
+// applies an R-point DFT and stores to (j / Ns) Ns R + (j mod Ns) + r Ns; the division by Ns is a
+// multiply-high with a per-stage magic number (exact below 2^20).
 template <typename T, int R, int DIR>
 __device__ __forceinline__ void stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int n, int Ns,
                                       unsigned long long magic, int lbatch, const cplx<T>* __restrict__ tw) {
   const int nr = n / R;
-  const int batch = 1 << lbatch;
   const int total = nr << lbatch;
+  const int bmask = (1 << lbatch) - 1;
   const int tstep = n / (Ns * R);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int b = t & (batch - 1);
-    const int jj = t >> lbatch;
+    const int b = t & bmask, jj = t >> lbatch;
     const int q = (int)(((unsigned long long)jj * magic) >> 40);
     const int k = jj - q * Ns;
     cplx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[pad16(((jj + r * nr) << lbatch) + b)];
-    if (Ns > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        cplx<T> w = tw[k * r * tstep];
-        if (DIR > 0) w.y = -w.y;
-        v[r] = v[r] * w;
-      }
+    for (int r = 1; r < R; ++r) {
+      cplx<T> w = tw[k * r * tstep];
+      if (DIR > 0) w.y = -w.y;
+      v[r] = v[r] * w;
     }
     Dft<T, R, DIR>::run(v);
     const int base = q * Ns * R + k;
@@ -218,17 +268,33 @@ __device__ __forceinline__ void stage(const cplx<T>* __restrict__ in, cplx<T>* _
   }
 }
 
-// Full transform; returns the buffer that holds the result.
+template <typename T, int DIR, class In>
+__device__ __forceinline__ void fft_first(cplx<T>* buf, const FftPlan& fp, int lbatch, const In& in) {
+  switch (fp.radix[0]) {
+    case 16: stage_first<T, 16, DIR>(buf, fp.n, lbatch, in); break;
+    case 12: stage_first<T, 12, DIR>(buf, fp.n, lbatch, in); break;
+    case 8: stage_first<T, 8, DIR>(buf, fp.n, lbatch, in); break;
+    case 4: stage_first<T, 4, DIR>(buf, fp.n, lbatch, in); break;
+    case 2: stage_first<T, 2, DIR>(buf, fp.n, lbatch, in); break;
+    case 3: stage_first<T, 3, DIR>(buf, fp.n, lbatch, in); break;
+    case 5: stage_first<T, 5, DIR>(buf, fp.n, lbatch, in); break;
+    default: stage_first<T, 7, DIR>(buf, fp.n, lbatch, in); break;
+  }
+}
+
+// stages 1 .. nstages-1, alternating between the two work buffers (each ends with a block
+// barrier); returns the buffer that holds the transform
 template <typename T, int DIR>
-__device__ cplx<T>* fft_smem(cplx<T>* b0, cplx<T>* b1, const FftPlan& fp, int lbatch, const cplx<T>* tw) {
-  int Ns = 1;
+__device__ cplx<T>* fft_rest(cplx<T>* b0, cplx<T>* b1, const FftPlan& fp, int lbatch, const cplx<T>* tw) {
+  int Ns = fp.radix[0];
   cplx<T>* in = b0;
   cplx<T>* out = b1;
-  for (int s = 0; s < fp.nstages; ++s) {
+  for (int s = 1; s < fp.nstages; ++s) {
     const int R = fp.radix[s];
     const unsigned long long mg = fp.magic[s];
     switch (R) {
       case 16: stage<T, 16, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
+      case 12: stage<T, 12, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
       case 8: stage<T, 8, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
       case 4: stage<T, 4, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
       case 2: stage<T, 2, DIR>(in, out, fp.n, Ns, mg, lbatch, tw); break;
@@ -277,11 +343,11 @@ __host__ __device__ __forceinline__ int staged_len(int n) { return (n + 3) & ~3;
 
 // Row pass, forward: a unit is two real rows y0 = 2j, y1 = 2j + 1, packed as z = r0 + i r1.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) row_r2c_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
-                                                      T* __restrict__ grid, const int* __restrict__ zrange) {
+__global__ void __launch_bounds__(512, 1) row_r2c_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                         T* __restrict__ grid, const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nx = g.nx, nxr = staged_len(nx);
-  T* raw = reinterpret_cast<T*>(smraw);  // [2][nxr]
+  T* raw = reinterpret_cast<T*>(smraw);  // [2][nxr] staged rows
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(raw + 2 * nxr);
   cplx<T>* b1 = b0 + pad16(nx) + 1;
   const UnitMap um(g, zrange, (g.ny + 1) / 2);
@@ -305,17 +371,17 @@ __global__ void __launch_bounds__(256, 2) row_r2c_kernel(Geometry g, FftPlan fp,
     bool has1;
     T* row0 = row0_of(u, has1);
     cp_wait_all();
-    __syncthreads();  // staged rows visible; previous unit's epilogue done with b0/b1
-    for (int a = threadIdx.x; a < nx; a += blockDim.x) b0[pad16(a)] = mk<T>(raw[a], has1 ? raw[nxr + a] : (T)0);
-    __syncthreads();
+    __syncthreads();  // staged rows visible; the previous unit's epilogue is done with buf
+    fft_first<T, -1>(b0, fp, 0, [&](int e) { return mk<T>(raw[e], has1 ? raw[nxr + e] : (T)0); });
+    __syncthreads();  // staging buffer consumed
     if (u + gridDim.x < um.total) issue(u + gridDim.x);
-    const cplx<T>* res = fft_smem<T, -1>(b0, b1, fp, 0, tw);
+    const cplx<T>* buf = fft_rest<T, -1>(b0, b1, fp, 0, tw);
     cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
     cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row0 + rowlen);
     const T half = (T)0.5;
     for (int k = threadIdx.x; k <= nx / 2; k += blockDim.x) {
-      const cplx<T> zk = res[pad16(k)];
-      const cplx<T> zm = conjg(res[pad16(k == 0 ? 0 : nx - k)]);
+      const cplx<T> zk = buf[pad16(k)];
+      const cplx<T> zm = conjg(buf[pad16(k == 0 ? 0 : nx - k)]);
       c0[k] = scl(zk + zm, half);
       if (has1) {
         const cplx<T> d = zk - zm;  // (zk - conj z_{-k}) / (2i)
@@ -327,11 +393,11 @@ __global__ void __launch_bounds__(256, 2) row_r2c_kernel(Geometry g, FftPlan fp,
 
 // Row pass, inverse: two half spectra -> z with z_k = X0_k + i X1_k (Hermitian extension), one FFT.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
-                                                      T* __restrict__ grid, const int* __restrict__ zrange) {
+__global__ void __launch_bounds__(512, 1) row_c2r_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                         T* __restrict__ grid, const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nx = g.nx, nh = nx / 2 + 1, nhr = (nh + 1) & ~1;
-  cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [2][nhr]
+  cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [2][nhr] staged half spectra
   cplx<T>* b0 = raw + 2 * nhr;
   cplx<T>* b1 = b0 + pad16(nx) + 1;
   const UnitMap um(g, zrange, (g.ny + 1) / 2);
@@ -357,17 +423,18 @@ __global__ void __launch_bounds__(256, 2) row_c2r_kernel(Geometry g, FftPlan fp,
     T* row1 = row0 + rowlen;
     cp_wait_all();
     __syncthreads();
-    for (int k = threadIdx.x; k < nh; k += blockDim.x) {
+    fft_first<T, +1>(b0, fp, 0, [&](int e) {
+      const bool lo = e <= nx / 2;
+      const int k = lo ? e : nx - e;
       const cplx<T> x0 = raw[k];
       const cplx<T> x1 = has1 ? raw[nhr + k] : mk<T>((T)0, (T)0);
-      b0[pad16(k)] = x0 + mul_i(x1);
-      if (k > 0 && k < nx - k) b0[pad16(nx - k)] = conjg(x0) + mul_i(conjg(x1));
-    }
+      return lo ? x0 + mul_i(x1) : conjg(x0) + mul_i(conjg(x1));
+    });
     __syncthreads();
     if (u + gridDim.x < um.total) issue(u + gridDim.x);
-    const cplx<T>* res = fft_smem<T, +1>(b0, b1, fp, 0, tw);
+    const cplx<T>* buf = fft_rest<T, +1>(b0, b1, fp, 0, tw);
     for (int a = threadIdx.x; a < nx; a += blockDim.x) {
-      const cplx<T> v = res[pad16(a)];
+      const cplx<T> v = buf[pad16(a)];
       row0[a] = v.x;
       if (has1) row1[a] = v.y;
     }
@@ -377,12 +444,12 @@ __global__ void __launch_bounds__(256, 2) row_c2r_kernel(Geometry g, FftPlan fp,
 // Column pass: a unit is cw adjacent x-wavenumber columns [kx0, kx0 + cw) of one plane, along y.
 template <typename T, int DIR>
 __global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
-                                                  cplx<T>* __restrict__ grid, const int* __restrict__ zrange, int lcw,
-                                                  int kxs, int kxe) {
+                                                     cplx<T>* __restrict__ grid, const int* __restrict__ zrange,
+                                                     int lcw, int kxs, int kxe) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int cw = 1 << lcw;
   const int tot = g.ny << lcw;
-  cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [ny][cw]
+  cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [ny][cw] staged columns
   cplx<T>* b0 = raw + tot;
   cplx<T>* b1 = b0 + pad16(tot) + 1;
   const UnitMap um(g, zrange, (kxe - kxs + cw - 1) >> lcw);
@@ -420,14 +487,13 @@ __global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, con
     cplx<T>* base = base_of(u, ncols);
     cp_wait_all();
     __syncthreads();
-    for (int t = threadIdx.x; t < tot; t += blockDim.x)
-      b0[pad16(t)] = ((t & (cw - 1)) < ncols) ? raw[t] : mk<T>((T)0, (T)0);
+    fft_first<T, DIR>(b0, fp, lcw, [&](int t) { return ((t & (cw - 1)) < ncols) ? raw[t] : mk<T>((T)0, (T)0); });
     __syncthreads();
     if (u + gridDim.x < um.total) issue(u + gridDim.x);
-    const cplx<T>* res = fft_smem<T, DIR>(b0, b1, fp, lcw, tw);
+    const cplx<T>* buf = fft_rest<T, DIR>(b0, b1, fp, lcw, tw);
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
       const int y = t >> lcw, b = t & (cw - 1);
-      if (b < ncols) base[(size_t)y * g.pitch + b] = res[pad16(t)];
+      if (b < ncols) base[(size_t)y * g.pitch + b] = buf[pad16(t)];
     }
   }
 }
@@ -447,12 +513,17 @@ size_t col_smem(const Geometry& g, int l) {
   return (size_t)(g.ny << l) * sizeof(cplx<T>) + 2 * padded_bytes(g.ny << l, sizeof(cplx<T>));
 }
 
-// log2 of the column block: the widest (at most 8 columns) whose staged and working buffers fit in
-// 200 KB of shared memory
+constexpr int kFftMaxThreads = 512;
+
+// threads for a transform of `points` values: at most kFftPer per thread, whole warps
+int fft_threads(int points) { return std::max(32, (points + kFftPer * 32 - 1) / (kFftPer * 32) * 32); }
+
+// log2 of the column block: the widest (at most 8 columns) within the thread limit whose staging
+// and work buffers fit in 160 KB of shared memory
 template <typename T>
 int col_lwidth(const Plan& p) {
   for (int l = 3; l > 0; --l)
-    if (col_smem<T>(p.g, l) <= 200 * 1024) return l;
+    if (fft_threads(p.g.ny << l) <= kFftMaxThreads && col_smem<T>(p.g, l) <= 160 * 1024) return l;
   return 0;
 }
 
@@ -471,16 +542,18 @@ int fft_smem_ok(Plan& p) {
   const size_t r2c = row_r2c_smem<T>(p.g), c2r = row_c2r_smem<T>(p.g);
   const int lcw = col_lwidth<T>(p);
   const size_t col = col_smem<T>(p.g, lcw);
+  const int trow = fft_threads(p.g.nx), tcol = fft_threads(p.g.ny << lcw);
+  if (trow > kFftMaxThreads || tcol > kFftMaxThreads) return 0;
   if (r2c > 220 * 1024 || c2r > 220 * 1024 || col > 220 * 1024) return 0;
   if (cudaFuncSetAttribute(row_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r2c) != cudaSuccess ||
       cudaFuncSetAttribute(row_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c2r) != cudaSuccess ||
       cudaFuncSetAttribute(col_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col) != cudaSuccess ||
       cudaFuncSetAttribute(col_kernel<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col) != cudaSuccess)
     return 0;
-  p.fft_grid[0] = resident_grid(row_r2c_kernel<T>, 256, r2c, p.device);
-  p.fft_grid[1] = resident_grid(row_c2r_kernel<T>, 256, c2r, p.device);
-  p.fft_grid[2] = resident_grid(col_kernel<T, -1>, 512, col, p.device);
-  p.fft_grid[3] = resident_grid(col_kernel<T, +1>, 512, col, p.device);
+  p.fft_grid[0] = resident_grid(row_r2c_kernel<T>, trow, r2c, p.device);
+  p.fft_grid[1] = resident_grid(row_c2r_kernel<T>, trow, c2r, p.device);
+  p.fft_grid[2] = resident_grid(col_kernel<T, -1>, tcol, col, p.device);
+  p.fft_grid[3] = resident_grid(col_kernel<T, +1>, tcol, col, p.device);
   return 1;
 }
 
@@ -488,12 +561,13 @@ template <typename T>
 void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
+  const int th = fft_threads(g.nx);
   if (dir < 0)
-    row_r2c_kernel<T><<<p.fft_grid[0], 256, row_r2c_smem<T>(g), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid),
-                                                                       p.zrange);
+    row_r2c_kernel<T><<<p.fft_grid[0], th, row_r2c_smem<T>(g), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid),
+                                                                      p.zrange);
   else
-    row_c2r_kernel<T><<<p.fft_grid[1], 256, row_c2r_smem<T>(g), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid),
-                                                                       p.zrange);
+    row_c2r_kernel<T><<<p.fft_grid[1], th, row_c2r_smem<T>(g), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid),
+                                                                      p.zrange);
 }
 
 template <typename T>
@@ -502,12 +576,13 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   const int lcw = col_lwidth<T>(p);
   const size_t sm = col_smem<T>(g, lcw);
+  const int th = fft_threads(g.ny << lcw);
   if (dir < 0)
-    col_kernel<T, -1><<<p.fft_grid[2], 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw,
-                                                     kxs, kxe);
+    col_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw,
+                                                    kxs, kxe);
   else
-    col_kernel<T, +1><<<p.fft_grid[3], 512, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw,
-                                                     kxs, kxe);
+    col_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, twy, reinterpret_cast<cplx<T>*>(p.grid), p.zrange, lcw,
+                                                    kxs, kxe);
 }
 
 template int fft_smem_ok<float>(Plan&);

@@ -10,10 +10,9 @@
 // with the wall images folded in).  Spreading and interpolation both read these records, so the
 // two operators use bit-identical weights (they are adjoint under the quadrature).
 //
-// Spreading: one block owns a 32 x 8 tile of xy nodes over all occupied Chebyshev planes,
-// collects the particles whose support touches the tile from the surrounding bins, scatters them
-// into a shared-memory accumulator (shared atomics) and writes every node of its tile exactly once
-// with plain stores (no global atomics, no zero-fill pass).
+// Spreading is a gather: one block owns a 32 x 8 tile of xy nodes over all occupied Chebyshev
+// planes, collects the particles whose support touches the tile from the surrounding bins, and
+// writes every node of its tile exactly once with plain stores (no atomics, no zero-fill pass).
 // Interpolation is a warp per particle: lane groups walk the x run of each (z, y) row of the
 // support, so every row is read as one contiguous segment.
 #include <math.h>
@@ -209,66 +208,47 @@ __device__ __forceinline__ bool cyc_overlap(int a, int len_a, int b, int len_b, 
 }
 
 constexpr int kCandCap = 2048;
-constexpr int kStage = 128;   // candidate records staged in shared memory at a time
-constexpr int kAccRow = 33;   // accumulator row stride: the 4 planes of one atomic hit distinct banks
+constexpr int kStage = 128;  // candidate records staged in shared memory at a time
 
-// Scatter one batch of staged candidate records into the block's accumulator tile, planes
-// [zb, ze).  Warp w takes candidates w, w + 8, ...; its lanes cover XL x offsets of the support times
-// 32 / XL planes, so the lanes of one atomic add touch distinct nodes of one support row.
-template <typename T, int NF, int ZC, int XL>
-__device__ __forceinline__ void scatter_batch(const Geometry& g, const uint32_t* __restrict__ srec, int nrec,
-                                              int rw, int tx0, int ty0, int tw, int th, int zb, int ze,
-                                              T* __restrict__ acc) {
-  constexpr int ZL = 32 / XL;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ix = lane % XL, izo = lane / XL;
+// Accumulate one batch of staged candidate records into the thread's node column, planes
+// [zb, zb + ZC).  Records live in shared memory (`srec`, `nb` of them, `rw` words each).
+template <typename T, int NF, int ZC>
+__device__ __forceinline__ void spread_batch(const Geometry& g, const uint32_t* srec, int nb, int rw, int gx, int gy,
+                                             int zb, T (&acc)[ZC][NF]) {
   const int stride = 2 * g.pxc + g.lzc;
-  for (int i = warp; i < nrec; i += kSpreadThreads / 32) {
+  for (int i = 0; i < nb; ++i) {
     const uint32_t* r = srec + (size_t)i * rw;
     const T* tv = reinterpret_cast<const T*>(r + 8);
 #pragma unroll
     for (int K = 0; K < NF / 3; ++K) {
       const int4 hd = reinterpret_cast<const int4*>(r)[K];
-      const int cs = max(hd.z, zb), ce = min(hd.z + hd.w, ze);
-      if (cs >= ce) continue;
       const int px = (K == 0) ? g.kM.px : g.kD.px;
-      int dxs = hd.x - tx0; if (dxs < 0) dxs += g.nx;
-      int dys = hd.y - ty0; if (dys < 0) dys += g.ny;
-      int lx = dxs + ix; if (lx >= g.nx) lx -= g.nx;
-      const bool vx = ix < px && lx < tw;
-      const T* ph = tv + 6 + K * stride;
-      const T wx = vx ? ph[ix] : (T)0;
-      const T f0 = tv[3 * K], f1 = tv[3 * K + 1], f2 = tv[3 * K + 2];
-      for (int iy = 0; iy < px; ++iy) {
-        int ly = dys + iy; if (ly >= g.ny) ly -= g.ny;
-        if (ly >= th) continue;  // row outside the tile (uniform over the warp)
-        const T wxy = wx * ph[g.pxc + iy];
-        const T g0 = f0 * wxy, g1 = f1 * wxy, g2 = f2 * wxy;
-        if (!vx) continue;
-        for (int c = cs + izo; c < ce; c += ZL) {
-          const T wz = ph[2 * g.pxc + (c - hd.z)];
-          T* a = acc + ((size_t)((3 * K) * ZC + (c - zb)) * kTileY + ly) * kAccRow + lx;
-          constexpr size_t fs = (size_t)ZC * kTileY * kAccRow;  // field stride of the accumulator
-          atomicAdd(a, g0 * wz);
-          atomicAdd(a + fs, g1 * wz);
-          atomicAdd(a + 2 * fs, g2 * wz);
+      int dx = gx - hd.x; if (dx < 0) dx += g.nx;
+      int dy = gy - hd.y; if (dy < 0) dy += g.ny;
+      if (dx < px && dy < px) {
+        const T* ph = tv + 6 + K * stride;
+        const T wxy = ph[dx] * ph[g.pxc + dy];
+        const T f0 = tv[3 * K], f1 = tv[3 * K + 1], f2 = tv[3 * K + 2];
+#pragma unroll
+        for (int zz = 0; zz < ZC; ++zz) {
+          const int iz = zb + zz - hd.z;
+          if (iz >= 0 && iz < hd.w) {
+            const T w = wxy * ph[2 * g.pxc + iz];
+            acc[zz][3 * K] += f0 * w;
+            acc[zz][3 * K + 1] += f1 * w;
+            acc[zz][3 * K + 2] += f2 * w;
+          }
         }
       }
     }
   }
 }
 
-// Spreading: one block per 32 x 8 tile of xy nodes (a bin) over all occupied planes.  It collects
-// the particles whose support touches the tile from the surrounding bins, then, per chunk of ZC
-// planes, scatters their weighted forces and torques into a shared-memory accumulator and writes
-// every node of the tile exactly once with plain stores (no global atomics, no zero-fill pass).
-template <typename T, int NF, int ZC, int XL>
+template <typename T, int NF, int ZC>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
               const int* __restrict__ sorted, const int* __restrict__ zrange, T* __restrict__ grid) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* acc = reinterpret_cast<T*>(smraw);                                         // [NF][ZC][8][kAccRow]
-  uint32_t* srec = reinterpret_cast<uint32_t*>(acc + (size_t)NF * ZC * kTileY * kAccRow);  // kStage records
+  extern __shared__ __align__(16) uint32_t srec[];   // kStage staged records
   __shared__ int s_bins[64];
   __shared__ int s_pref[65];
   __shared__ int s_nb;
@@ -279,6 +259,8 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   const int bx = blockIdx.x % g.nbx, by = blockIdx.x / g.nbx;
   const int tx0 = bx * kTileX, ty0 = by * kTileY;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gx = tx0 + (tid % kTileX), gy = ty0 + (tid / kTileX);
+  const bool active = (gx < g.nx) && (gy < g.ny);
   const int tw = min(kTileX, g.nx - tx0), th = min(kTileY, g.ny - ty0);
   const int rw = g.rec_words;
   if (tid == 0) {
@@ -292,22 +274,23 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
       }
     }
     s_nb = nb;
-    int run = 0;
+    int acc = 0;
     for (int i = 0; i < nb; ++i) {
-      s_pref[i] = run;
-      run += bin_start[s_bins[i] + 1] - bin_start[s_bins[i]];
+      s_pref[i] = acc;
+      acc += bin_start[s_bins[i] + 1] - bin_start[s_bins[i]];
     }
-    s_pref[nb] = run;
+    s_pref[nb] = acc;
   }
   __syncthreads();
   const int nb = s_nb;
   const int total = s_pref[nb];
-  const size_t plane = (size_t)g.ny * 2 * g.pitch;  // T values per z plane (real rows)
+  const size_t plane = (size_t)g.ny * 2 * g.pitch;          // T values per z plane (real rows)
   const size_t fstride = plane * g.nz;
-  constexpr int kAccN = NF * ZC * kTileY * kAccRow;
-  // copy records [i0, i0 + cnt) of the candidate list into shared memory (16-byte pieces)
+  const size_t node = (size_t)gy * 2 * g.pitch + gx;
+  // copy records [i0, i0 + cnt) of the candidate list into shared memory (16-byte pieces; records
+  // are 16-byte aligned), all copies in flight at once
   auto stage = [&](int i0, int cnt) {
-    const int q = rw >> 2;  // 16-byte pieces per record (records are 16-byte aligned)
+    const int q = rw >> 2;
     for (int t = tid; t < cnt * q; t += kSpreadThreads) {
       const int i = t / q, w = t - i * q;
       cp_async16(srec + (size_t)i * rw + 4 * w, rec + (size_t)s_cand[i0 + i] * rw + 4 * w);
@@ -356,42 +339,35 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
       __syncthreads();
     }
     for (int zb = clo; zb <= chi; zb += ZC) {
-      const int ze = min(zb + ZC, chi + 1);
-      // accumulator: zero, or the values written by the previous round
-      for (int e = tid; e < kAccN; e += kSpreadThreads) {
-        T v = (T)0;
-        if (round > 0) {
-          const int lx = e % kAccRow, rr = e / kAccRow;
-          const int ly = rr % kTileY, fz = rr / kTileY;
-          const int cz = fz % ZC, f = fz / ZC;
-          if (lx < tw && ly < th && zb + cz < ze)
-            v = grid[f * fstride + (size_t)(zb + cz) * plane + (size_t)(ty0 + ly) * 2 * g.pitch + tx0 + lx];
+      T acc[ZC][NF];
+#pragma unroll
+      for (int zz = 0; zz < ZC; ++zz)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          T v = (T)0;
+          if (round > 0 && active && zb + zz <= chi) v = grid[f * fstride + (size_t)(zb + zz) * plane + node];
+          acc[zz][f] = v;
         }
-        acc[e] = v;
-      }
-      __syncthreads();
       if (once) {
-        scatter_batch<T, NF, ZC, XL>(g, srec, ncand, rw, tx0, ty0, tw, th, zb, ze, acc);
+        if (active) spread_batch<T, NF, ZC>(g, srec, ncand, rw, gx, gy, zb, acc);
       } else {
         for (int i0 = 0; i0 < ncand; i0 += kStage) {
           const int cnt = min(kStage, ncand - i0);
           __syncthreads();
           stage(i0, cnt);
           __syncthreads();
-          scatter_batch<T, NF, ZC, XL>(g, srec, cnt, rw, tx0, ty0, tw, th, zb, ze, acc);
+          if (active) spread_batch<T, NF, ZC>(g, srec, cnt, rw, gx, gy, zb, acc);
         }
       }
-      __syncthreads();
-      // write the tile: rows of 32 contiguous nodes
-      for (int e = tid; e < NF * ZC * kTileY * kTileX; e += kSpreadThreads) {
-        const int lx = e % kTileX, rr = e / kTileX;
-        const int ly = rr % kTileY, fz = rr / kTileY;
-        const int cz = fz % ZC, f = fz / ZC;
-        if (lx < tw && ly < th && zb + cz < ze)
-          grid[f * fstride + (size_t)(zb + cz) * plane + (size_t)(ty0 + ly) * 2 * g.pitch + tx0 + lx] =
-              acc[((size_t)fz * kTileY + ly) * kAccRow + lx];
+      if (active) {
+#pragma unroll
+        for (int zz = 0; zz < ZC; ++zz) {
+          if (zb + zz <= chi) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) grid[f * fstride + (size_t)(zb + zz) * plane + node] = acc[zz][f];
+          }
+        }
       }
-      __syncthreads();
     }
     if (passed <= win1) break;
     __syncthreads();
@@ -496,26 +472,20 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
   }
 }
 
-template <typename T, int NF, int ZC, int XL>
-void spread_launch(const Plan& p, cudaStream_t s) {
-  const unsigned blocks = (unsigned)(p.g.nbx * p.g.nby);
-  const size_t sm = (size_t)NF * ZC * kTileY * kAccRow * sizeof(T) + (size_t)kStage * p.g.rec_words * sizeof(uint32_t);
-  cudaFuncSetAttribute(spread_kernel<T, NF, ZC, XL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  spread_kernel<T, NF, ZC, XL><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
-                                                                  reinterpret_cast<T*>(p.grid));
-}
-
 template <typename T>
 void launch_spread(const Plan& p, cudaStream_t s) {
-  // chunk of planes held in shared memory: 8 (float) or 4 (double) with six fields
-  constexpr int ZC6 = sizeof(T) == 4 ? 8 : 4, ZC3 = sizeof(T) == 4 ? 16 : 8;
-  const bool narrow = p.g.pxc <= 8;
+  const unsigned blocks = (unsigned)(p.g.nbx * p.g.nby);
+  // z chunk: as many planes as keep the accumulators near 48 registers' worth
+  constexpr int ZC6 = sizeof(T) == 4 ? 8 : 4, ZC3 = sizeof(T) == 4 ? 12 : 6;
+  const size_t sm = (size_t)kStage * p.g.rec_words * sizeof(uint32_t);
   if (p.g.nfields == 6) {
-    if (narrow) spread_launch<T, 6, ZC6, 8>(p, s);
-    else spread_launch<T, 6, ZC6, 16>(p, s);
+    cudaFuncSetAttribute(spread_kernel<T, 6, ZC6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    spread_kernel<T, 6, ZC6><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                                reinterpret_cast<T*>(p.grid));
   } else {
-    if (narrow) spread_launch<T, 3, ZC3, 8>(p, s);
-    else spread_launch<T, 3, ZC3, 16>(p, s);
+    cudaFuncSetAttribute(spread_kernel<T, 3, ZC3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    spread_kernel<T, 3, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                                reinterpret_cast<T*>(p.grid));
   }
 }
 

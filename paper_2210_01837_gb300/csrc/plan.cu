@@ -63,6 +63,7 @@ bool fft_plan(int n, FftPlan& fp) {
   fp.nstages = 0;
   int m = n;
   while (m % 16 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 16; m /= 16; }
+  while (m % 12 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 12; m /= 12; }
   while (m % 8 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 8; m /= 8; }
   while (m % 4 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 4; m /= 4; }
   while (m % 2 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 2; m /= 2; }
