@@ -64,7 +64,7 @@ typedef enum {
 } dps_status;
 
 typedef struct {
-  int32_t nx, ny;  /* xy grid; nx, ny >= 8 and 2,3,5,7-smooth                                   */
+  int32_t nx, ny;  /* xy grid; 8 <= nx, ny <= 6144, 2,3,5,7-smooth                              */
   int32_t nz;      /* Chebyshev nodes on [zmin, zmax] including both ends, 5 <= nz <= 257      */
 } dps_grid;
 
@@ -88,10 +88,10 @@ dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zm
                                 int32_t wall_mode, const dps_grid* grid,
                                 const dps_kernel_params* kp);
 
-/* One mobility product, enqueued on `stream` (a cudaStream_t, NULL for the legacy stream).  The
- * wavenumber-space stages fork onto two plan-owned streams and join back to `stream` before the
- * apply's last kernels, so all of an apply's work is ordered after earlier work on `stream` and
- * before later work on it.
+/* One mobility product, enqueued on `stream` (a cudaStream_t, NULL for the legacy stream).  All of
+ * an apply's work is ordered after earlier work on `stream` and before later work on it (when the
+ * wavenumber-space stages run in several column chunks, DPS_CHUNKS in the environment at plan
+ * creation, they fork onto two plan-owned streams and join back before the apply's last kernels).
  * positions, forces: device [n][3]; torques: device [n][3] or NULL; out_vel: device [n][3];
  * out_angvel: device [n][3] or NULL.  torques and out_angvel must both be NULL for a plan built
  * without torques and both non-NULL for one built with torques.  0 <= n <= max_n.  Outputs are
@@ -170,6 +170,91 @@ dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin, double zma
                                    const double* positions, const double* forces,
                                    const double* torques, double* out_grid, int64_t ldx,
                                    void* stream);
+
+/* ---- Batched applies ----------------------------------------------------------------------
+ * No counterpart in the paper: independent products (different plans, sizes and wall modes) run
+ * concurrently, each exactly as dpstokes_apply would compute it. */
+typedef struct {
+  dps_plan_t plan;
+  int64_t n;
+  const double* positions;  /* device [n][3], as in dpstokes_apply                               */
+  const double* forces;     /* device [n][3]                                                      */
+  const double* torques;    /* device [n][3] or NULL (must match the plan)                        */
+  double* out_vel;          /* device [n][3]                                                      */
+  double* out_angvel;       /* device [n][3] or NULL (must match the plan)                        */
+  int32_t* status;          /* device int32 or NULL: receives the request's dps_status from the
+                               device checks (what dpstokes_status would return), and the plan's
+                               status word is cleared                                            */
+} dps_request;
+
+/* Enqueue `count` requests after the work already on `stream` and before later work on it.  The
+ * requests run concurrently on a pool of 8 library-owned streams (created on the device's first
+ * batch, or by dpstokes_batch_prepare); requests that name the same plan run in the order given.
+ * Every argument check of dpstokes_apply is made for every request before anything is enqueued
+ * (DPS_ERR_INVALID_ARG, nothing enqueued).  Asynchronous, no allocation, no host
+ * synchronisation: a batch may be captured into a CUDA graph (call dpstokes_batch_prepare before
+ * the capture) and the graph replayed; the plans then must stay alive while it is in use. */
+dps_status dpstokes_apply_batch(const dps_request* reqs, int32_t count, void* stream);
+
+/* Create the current device's batch stream pool now (idempotent). */
+dps_status dpstokes_batch_prepare(void);
+
+/* ---- Serving ------------------------------------------------------------------------------
+ * No counterpart in the paper.  A server owns a worker thread, `slots` streams and a cache of
+ * plans keyed by every plan parameter.  Submitted requests wait in arrival order; the worker
+ * admits the oldest one whenever a slot is free and its plan is available: an idle cached plan
+ * with the same key, or a new plan if the memory budget allows, after evicting least-recently-used
+ * idle plans (an eviction frees device memory, which synchronises the device).  A request that can
+ * never fit the budget completes with DPS_ERR_OOM.  Each admitted request copies its inputs from
+ * host memory, runs the product and copies the outputs back on its slot's stream, so requests
+ * overlap on the device.  Results are those of dpstokes_apply_host on a plan with the same
+ * parameters. */
+typedef struct dps_server_s* dps_server_t;
+
+typedef struct {
+  double Lx, Ly, zmin, zmax;  /* plan parameters, as in dpstokes_plan_create                      */
+  int32_t wall_mode;
+  dps_grid grid;
+  dps_kernel_params kp;       /* kp.max_n is part of the plan key; 0 <= n <= kp.max_n             */
+  int64_t n;
+  const double* positions;    /* HOST [n][3] (pinned memory copies fastest); read after admission */
+  const double* forces;       /* HOST [n][3]                                                      */
+  const double* torques;      /* HOST [n][3] or NULL (must match kp.with_torque)                  */
+  double* out_vel;            /* HOST [n][3], written before the request completes                */
+  double* out_angvel;         /* HOST [n][3] or NULL                                              */
+} dps_serve_request;
+
+typedef struct {
+  int32_t status;             /* dps_status of the request                                         */
+  double t_submit;            /* steady-clock seconds: submission, admission, completion seen by  */
+  double t_start;             /* the worker (completion is polled every ~20 microseconds)        */
+  double t_done;
+} dps_serve_result;
+
+typedef struct {
+  int64_t queued, running;    /* requests waiting / on a slot                                      */
+  int64_t plans_resident, plans_created, plans_evicted;
+  int64_t bytes_resident;     /* device bytes held by cached plans                                 */
+} dps_server_stats;
+
+/* memory_budget_bytes > 0 bounds the plans' device memory; 1 <= slots <= 64.  The server works on
+ * the device current at creation. */
+dps_status dpstokes_server_create(dps_server_t* out, int64_t memory_budget_bytes, int32_t slots);
+
+/* Queue a request (the descriptor is copied; the host buffers must stay valid until the request's
+ * dpstokes_server_wait returns).  *ticket identifies it.  DPS_ERR_INVALID_ARG for n outside
+ * [0, kp.max_n] or after destroy has begun; parameter errors are reported by the result. */
+dps_status dpstokes_server_submit(dps_server_t server, const dps_serve_request* req, int64_t* ticket);
+
+/* Wait up to timeout_s seconds for a ticket; DPS_ERR_TIMEOUT if it has not completed (it keeps
+ * running), DPS_ERR_INVALID_ARG for an unknown or already collected ticket. */
+dps_status dpstokes_server_wait(dps_server_t server, int64_t ticket, double timeout_s,
+                                dps_serve_result* result);
+
+dps_status dpstokes_server_stats(dps_server_t server, dps_server_stats* out);
+
+/* Finish every queued and running request, then free the slots and all cached plans. */
+void dpstokes_server_destroy(dps_server_t server);
 
 /* Diagnostics for tests: run the apply pipeline on `stream` up to and including stage
  * `last_stage` (1 = particle records, 2 = spread, 3 = forward xy FFT, 4 = per-k solve,

@@ -37,6 +37,31 @@ class dps_plan_info(ctypes.Structure):
                 ("nchunks", ctypes.c_int32)]
 
 
+class dps_request(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("n", ctypes.c_int64), ("positions", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p), ("torques", ctypes.c_void_p), ("out_vel", ctypes.c_void_p),
+                ("out_angvel", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+class dps_serve_request(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("zmin", ctypes.c_double),
+                ("zmax", ctypes.c_double), ("wall_mode", ctypes.c_int32), ("grid", dps_grid),
+                ("kp", dps_kernel_params), ("n", ctypes.c_int64), ("positions", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p), ("torques", ctypes.c_void_p), ("out_vel", ctypes.c_void_p),
+                ("out_angvel", ctypes.c_void_p)]
+
+
+class dps_serve_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class dps_server_stats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("plans_resident", ctypes.c_int64),
+                ("plans_created", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
+                ("bytes_resident", ctypes.c_int64)]
+
+
 class DpsError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -78,6 +103,13 @@ def load(path=None):
                                            ctypes.POINTER(dps_kernel_params), _I64, _P, _P, _P, _P, _I64, _P]),
         "dpstokes_debug_run": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, _I32]),
         "dpstokes_debug_copy": (_I32, [_P, _I32, _P, _I64, _P]),
+        "dpstokes_apply_batch": (_I32, [ctypes.POINTER(dps_request), _I32, _P]),
+        "dpstokes_batch_prepare": (_I32, []),
+        "dpstokes_server_create": (_I32, [ctypes.POINTER(_P), _I64, _I32]),
+        "dpstokes_server_submit": (_I32, [_P, ctypes.POINTER(dps_serve_request), ctypes.POINTER(_I64)]),
+        "dpstokes_server_wait": (_I32, [_P, _I64, _D, ctypes.POINTER(dps_serve_result)]),
+        "dpstokes_server_stats": (_I32, [_P, ctypes.POINTER(dps_server_stats)]),
+        "dpstokes_server_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -154,6 +186,46 @@ def dpstokes_debug_run(plan, n, positions, forces, torques, out_vel, out_angvel,
 
 def dpstokes_debug_copy(plan, which, dst, dst_bytes, stream):
     return load().dpstokes_debug_copy(plan, which, dst, dst_bytes, stream)
+
+
+def dpstokes_apply_batch(reqs, stream):
+    """reqs: a ctypes array of dps_request."""
+    return load().dpstokes_apply_batch(reqs, len(reqs), stream)
+
+
+def dpstokes_batch_prepare():
+    return load().dpstokes_batch_prepare()
+
+
+def dpstokes_server_create(memory_budget_bytes, slots):
+    """Returns (status, handle)."""
+    h = _P()
+    st = load().dpstokes_server_create(ctypes.byref(h), int(memory_budget_bytes), int(slots))
+    return st, h
+
+
+def dpstokes_server_submit(server, req):
+    """Returns (status, ticket)."""
+    t = _I64(-1)
+    st = load().dpstokes_server_submit(server, ctypes.byref(req), ctypes.byref(t))
+    return st, t.value
+
+
+def dpstokes_server_wait(server, ticket, timeout_s):
+    """Returns (status, dps_serve_result)."""
+    r = dps_serve_result()
+    st = load().dpstokes_server_wait(server, int(ticket), float(timeout_s), ctypes.byref(r))
+    return st, r
+
+
+def dpstokes_server_stats(server):
+    s = dps_server_stats()
+    st = load().dpstokes_server_stats(server, ctypes.byref(s))
+    return st, s
+
+
+def dpstokes_server_destroy(server):
+    load().dpstokes_server_destroy(server)
 
 
 # ---- convenience wrapper --------------------------------------------------------------------
@@ -262,6 +334,80 @@ class Plan:
         if getattr(self, "handle", None):
             dpstokes_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def apply_batch(items, stream=None, status=None):
+    """items: list of (Plan, pos, F, T, U, W) with CUDA tensors; status: optional CUDA int32 tensor
+    [len(items)] that receives each request's device status."""
+    arr = (dps_request * len(items))()
+    for i, (plan, pos, F, T, U, W) in enumerate(items):
+        arr[i].plan = plan.handle.value if isinstance(plan.handle, ctypes.c_void_p) else plan.handle
+        arr[i].n = pos.shape[0]
+        arr[i].positions, arr[i].forces, arr[i].torques = _ptr(pos), _ptr(F), _ptr(T)
+        arr[i].out_vel, arr[i].out_angvel = _ptr(U), _ptr(W)
+        arr[i].status = (status.data_ptr() + 4 * i) if status is not None else None
+    st = dpstokes_apply_batch(arr, _stream(stream))
+    if st != DPS_OK:
+        raise DpsError(st, "dpstokes_apply_batch")
+
+
+class Server:
+    """Request server: host arrays in and out, plans cached under a device-memory budget."""
+
+    def __init__(self, memory_budget_bytes, slots=8):
+        st, h = dpstokes_server_create(memory_budget_bytes, slots)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, params, with_torque, precision, max_n, pos, F, T=None, U=None, W=None):
+        """params: dict as in Plan.from_params; pos/F/T host float64 [n, 3] (kept alive until wait).
+        Returns a ticket; outputs land in U (and W)."""
+        n = pos.shape[0]
+        U = np.empty((n, 3)) if U is None else U
+        W = (np.empty((n, 3)) if W is None else W) if with_torque else None
+        r = dps_serve_request()
+        r.Lx, r.Ly, r.zmin, r.zmax = (float(params[k]) for k in ("Lx", "Ly", "zmin", "zmax"))
+        r.wall_mode = MODES[params["mode"]]
+        r.grid = dps_grid(int(params["nx"]), int(params["ny"]), int(params["nz"]))
+        r.kp = dps_kernel_params(int(params["m_M"]), float(params["beta_M"]), int(params.get("m_D", 0) or 0),
+                                 float(params.get("beta_D", 0.0) or 0.0), float(params.get("eta", 1.0)),
+                                 1 if with_torque else 0, PRECISIONS[precision], int(max_n))
+        r.n = n
+        r.positions, r.forces, r.torques = _ptr(pos), _ptr(F), _ptr(T)
+        r.out_vel, r.out_angvel = _ptr(U), _ptr(W)
+        st, t = dpstokes_server_submit(self.handle, r)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_server_submit")
+        self._keep[t] = (pos, F, T, U, W)
+        return t
+
+    def wait(self, ticket, timeout_s=600.0):
+        """Returns (dps_serve_result, U, W)."""
+        st, r = dpstokes_server_wait(self.handle, ticket, timeout_s)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_server_wait")
+        _, _, _, U, W = self._keep.pop(ticket)
+        return r, U, W
+
+    def stats(self):
+        st, s = dpstokes_server_stats(self.handle)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_server_stats")
+        return {k: getattr(s, k) for k, _ in dps_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dpstokes_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -175,6 +175,7 @@ template <typename T> void launch_records(const Plan& p, int64_t n, const double
                                           const double* Tq, cudaStream_t s);
 void launch_bins(const Plan& p, int64_t n, cudaStream_t s);
 template <typename T> void launch_spread(const Plan& p, cudaStream_t s);
+template <typename T> int spread_prepare(const Plan& p);
 template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s);
 template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s);
@@ -185,5 +186,11 @@ template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
+
+// host-side validation of an apply's arguments, and the stream-ordered product itself
+dps_status check_apply_args(const Plan* p, int64_t n, const double* pos, const double* F, const double* Tq,
+                            const double* U, const double* W, bool need_out = true);
+dps_status run(Plan* p, int64_t n, const double* pos, const double* F, const double* Tq, double* U, double* W,
+               cudaStream_t s, int last_stage);
 
 }  // namespace dps

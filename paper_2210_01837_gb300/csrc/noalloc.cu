@@ -185,6 +185,7 @@ extern "C" dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin,
     return DPS_ERR_CUDA;
   const int blocks = std::min(1024, std::max(nz, nbins) / 256 + 1);
   noalloc_init_kernel<<<blocks, 256, 0, s>>>(p.tab.zc, nz, zmin, g.H, p.zrange, p.status, p.bin_count, nbins);
+  if (!spread_prepare<double>(p)) return DPS_ERR_CUDA;
   launch_records<double>(p, n, positions, forces, torques, s);
   launch_bins(p, n, s);
   launch_spread<double>(p, s);

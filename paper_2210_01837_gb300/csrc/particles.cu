@@ -472,21 +472,36 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
   }
 }
 
+constexpr int kZC6F = 8, kZC6D = 4, kZC3F = 12, kZC3D = 6;  // z chunk: accumulators near 48 registers
+
+template <typename T>
+size_t spread_smem(const Plan& p) {
+  return (size_t)kStage * p.g.rec_words * sizeof(uint32_t);
+}
+
+// shared-memory limit of the spreading kernels, set once per plan (not at launch, so that applies
+// can be captured into graphs)
+template <typename T>
+int spread_prepare(const Plan& p) {
+  const int sm = (int)spread_smem<T>(p);
+  constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
+  return cudaFuncSetAttribute(spread_kernel<T, 6, ZC6>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(spread_kernel<T, 3, ZC3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) ==
+             cudaSuccess;
+}
+
 template <typename T>
 void launch_spread(const Plan& p, cudaStream_t s) {
   const unsigned blocks = (unsigned)(p.g.nbx * p.g.nby);
-  // z chunk: as many planes as keep the accumulators near 48 registers' worth
-  constexpr int ZC6 = sizeof(T) == 4 ? 8 : 4, ZC3 = sizeof(T) == 4 ? 12 : 6;
-  const size_t sm = (size_t)kStage * p.g.rec_words * sizeof(uint32_t);
-  if (p.g.nfields == 6) {
-    cudaFuncSetAttribute(spread_kernel<T, 6, ZC6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
+  const size_t sm = spread_smem<T>(p);
+  if (p.g.nfields == 6)
     spread_kernel<T, 6, ZC6><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
                                                                 reinterpret_cast<T*>(p.grid));
-  } else {
-    cudaFuncSetAttribute(spread_kernel<T, 3, ZC3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  else
     spread_kernel<T, 3, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
                                                                 reinterpret_cast<T*>(p.grid));
-  }
 }
 
 template <typename T>
@@ -508,6 +523,8 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
 template void launch_records<float>(const Plan&, int64_t, const double*, const double*, const double*, cudaStream_t);
 template void launch_records<double>(const Plan&, int64_t, const double*, const double*, const double*, cudaStream_t);
 template void launch_spread<float>(const Plan&, cudaStream_t);
+template int spread_prepare<float>(const Plan&);
+template int spread_prepare<double>(const Plan&);
 template void launch_spread<double>(const Plan&, cudaStream_t);
 template void launch_interp<float>(const Plan&, int64_t, double*, double*, cudaStream_t);
 template void launch_interp<double>(const Plan&, int64_t, double*, double*, cudaStream_t);

@@ -277,6 +277,7 @@ dps_status allocate(Plan* p) {
   if (!alloc((void**)&p->stage_in, nmax * 9 * sizeof(double))) return DPS_ERR_OOM;
   if (!alloc((void**)&p->stage_out, nmax * 6 * sizeof(double))) return DPS_ERR_OOM;
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
+  if (!spread_prepare<T>(*p)) return DPS_ERR_CUDA;
   // column chunks of the wavenumber-space pipeline (multiples of 32 columns, ~192 wide)
   const int nkx = g.nkx;
   // one chunk: measured on GB300, co-running the FP64 solve with the float transforms slowed both
@@ -359,8 +360,10 @@ void enqueue(Plan& p, int64_t n, const double* pos, const double* F, const doubl
   if (tm) p.timed_apply = 1;
 }
 
+}  // namespace
+
 dps_status check_apply_args(const Plan* p, int64_t n, const double* pos, const double* F, const double* Tq,
-                            const double* U, const double* W, bool need_out = true) {
+                            const double* U, const double* W, bool need_out) {
   if (!p || n < 0 || n > p->max_n) return DPS_ERR_INVALID_ARG;
   if (n > 0 && (!pos || !F || (need_out && !U))) return DPS_ERR_INVALID_ARG;
   if (p->g.with_torque) {
@@ -385,7 +388,6 @@ dps_status run(Plan* p, int64_t n, const double* pos, const double* F, const dou
   return e == cudaSuccess ? DPS_OK : DPS_ERR_CUDA;
 }
 
-}  // namespace
 }  // namespace dps
 
 using dps::Plan;
@@ -479,7 +481,9 @@ dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zm
   dps_status st = (p->precision == DPS_MIXED) ? dps::build_tables<float>(p) : dps::build_tables<double>(p);
   if (st == DPS_OK) st = (p->precision == DPS_MIXED) ? dps::allocate<float>(p) : dps::allocate<double>(p);
   if (st != DPS_OK) { dps::free_plan(p); cudaGetLastError(); return st; }
-  if (cudaDeviceSynchronize() != cudaSuccess) { dps::free_plan(p); cudaGetLastError(); return DPS_ERR_CUDA; }
+  // the uploads and clears ran on the legacy stream; waiting for it leaves work on non-blocking
+  // streams (other plans' applies, the serving slots) running
+  if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) { dps::free_plan(p); cudaGetLastError(); return DPS_ERR_CUDA; }
   *out = reinterpret_cast<dps_plan_t>(p);
   return DPS_OK;
 }

@@ -79,3 +79,50 @@ def test_null_plan_rejected(lib):
     st, _ = binding.dpstokes_plan_info(None)
     assert st == binding.DPS_ERR_INVALID_ARG
     binding.dpstokes_destroy(None)
+
+
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    """sizeof/offsetof of every ABI struct from gcc against the ctypes mirrors."""
+    from paper_2210_01837_gb300 import binding
+    fields = {
+        "dps_grid": ["nz"], "dps_kernel_params": ["beta_M", "m_D", "beta_D", "eta", "with_torque", "precision", "max_n"],
+        "dps_plan_info": ["nkx", "h", "alpha_D", "launches_per_apply", "nchunks"],
+        "dps_request": ["n", "positions", "torques", "out_angvel", "status"],
+        "dps_serve_request": ["wall_mode", "grid", "kp", "n", "positions", "out_angvel"],
+        "dps_serve_result": ["t_submit", "t_done"], "dps_server_stats": ["running", "bytes_resident"],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dpstokes.h"', "int main(void) {"]
+    for s, fs in fields.items():
+        lines.append(f'  printf("{s} %zu\\n", sizeof({s}));')
+        for f in fs:
+            lines.append(f'  printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for s, fs in fields.items():
+        cls = getattr(binding, s)
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for f in fs:
+            assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"
+
+
+def test_batch_and_server_reject_invalid_arguments_on_host(lib):
+    from paper_2210_01837_gb300 import binding
+    assert lib.dpstokes_apply_batch(None, -1, None) == binding.DPS_ERR_INVALID_ARG
+    assert lib.dpstokes_apply_batch(None, 2, None) == binding.DPS_ERR_INVALID_ARG
+    reqs = (binding.dps_request * 1)()  # NULL plan
+    assert binding.dpstokes_apply_batch(reqs, None) == binding.DPS_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert lib.dpstokes_server_create(ctypes.byref(h), 0, 4) == binding.DPS_ERR_INVALID_ARG
+    assert lib.dpstokes_server_create(ctypes.byref(h), 1 << 30, 0) == binding.DPS_ERR_INVALID_ARG
+    assert lib.dpstokes_server_create(None, 1 << 30, 4) == binding.DPS_ERR_INVALID_ARG
+    t = ctypes.c_int64()
+    assert lib.dpstokes_server_submit(None, None, ctypes.byref(t)) == binding.DPS_ERR_INVALID_ARG
+    r = binding.dps_serve_result()
+    assert lib.dpstokes_server_wait(None, 0, 0.0, ctypes.byref(r)) == binding.DPS_ERR_INVALID_ARG
+    lib.dpstokes_server_destroy(None)
