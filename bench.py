@@ -189,6 +189,147 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------------------------------------
+# batched and served products (independent systems of uneven size)
+# ---------------------------------------------------------------------------------------------
+def batch_leg(binding, torch, dev, count, steps, warmup):
+    """Products/s of `count` uneven systems: one after another on one stream, as one batched apply,
+    and as a replayed CUDA graph of that batch."""
+    from paper_2210_01837_gb300.workloads import batch_systems
+    systems = batch_systems(count=count)
+    t0 = time.perf_counter()
+    plans, items = [], []
+    for params, pos, F, T in systems:
+        plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=len(pos))
+        tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        U = torch.empty((len(pos), 3), dtype=torch.float64, device=dev)
+        plans.append(plan)
+        items.append((plan, tdev(pos), tdev(F), tdev(T), U, torch.empty_like(U)))
+    t_plans = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, k):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3 / k
+
+    def sequential():
+        for plan, pos, F, T, U, W in items:
+            plan.apply(pos, F, T, U, W)
+
+    def batched():
+        binding.apply_batch(items)
+
+    t_seq = timed(sequential, steps)
+    t_bat = timed(batched, steps)
+    binding.dpstokes_batch_prepare()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batched()
+    t_graph = timed(graph.replay, steps)
+    for plan in plans:
+        plan.check()
+    del graph
+    particles = sum(len(s[1]) for s in systems)
+    out = {"workload": f"batch_systems: first {count} of the 256 uneven systems (N log-uniform 100..50000, "
+                       f"half bottom wall / half slit, nz in 33/65/97), forces+torques, mixed",
+           "systems": count, "particles": particles, "plan_create_s": round(t_plans, 2),
+           "sequential_products_per_s": count / t_seq, "batched_products_per_s": count / t_bat,
+           "graph_products_per_s": count / t_graph, "batched_vs_sequential": t_seq / t_bat,
+           "ms_per_batch": {"sequential": t_seq * 1e3, "batched": t_bat * 1e3, "graph": t_graph * 1e3}}
+    for plan in plans:
+        plan.close()
+    return out, systems
+
+
+def fp64_unbatched_leg(binding, torch, dev, systems, count):
+    """Products/s of the FP64 path, one system after another on one stream (the unbatched baseline
+    of the served numbers)."""
+    sub = systems[:count]
+    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    total = 0.0
+    for params, pos, F, T in sub:
+        plan = binding.Plan.from_params(params, with_torque=True, precision="fp64", max_n=len(pos))
+        args = (tdev(pos), tdev(F), tdev(T))
+        plan.apply(*args)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan.apply(*args)
+        torch.cuda.synchronize(dev)
+        total += time.perf_counter() - t0
+        plan.check()
+        plan.close()
+    return {"systems": count, "products_per_s": count / total}
+
+
+def served_leg(binding, torch, systems, rate, duration, slots=8, budget=120e9, seed=20221009):
+    """Poisson arrivals of requests drawn uniformly from `systems` (host inputs in pinned memory) at
+    `rate` per second for `duration` seconds; latency = completion - submission."""
+    import queue as _queue
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    inputs = [(params, pin(pos), pin(F), pin(T)) for params, pos, F, T in systems]
+    nmax = max(len(s[1]) for s in systems)
+    ring = 128  # output buffers in flight
+    outs = [(torch.empty((nmax, 3), dtype=torch.float64).pin_memory().numpy(),
+             torch.empty((nmax, 3), dtype=torch.float64).pin_memory().numpy()) for _ in range(ring)]
+    srv = binding.Server(int(budget), slots=slots)
+    # plans of the population resident before the clock starts
+    warm = []
+    for i, (params, pos, F, T) in enumerate(inputs):
+        n = len(pos)
+        warm.append(srv.submit(params, True, "mixed", n, pos, F, T, outs[i % ring][0][:n], outs[i % ring][1][:n]))
+    for t in warm:
+        r, _, _ = srv.wait(t)
+        if r.status != 0:
+            raise RuntimeError(f"served warm-up request failed: {r.status}")
+    rng = np.random.default_rng(seed)
+    n_req = max(1, int(rate * duration))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    picks = rng.integers(0, len(inputs), n_req)
+    tickets = _queue.Queue()
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            params, pos, F, T = inputs[picks[i]]
+            n = len(pos)
+            U, W = outs[i % ring]
+            tickets.put(srv.submit(params, True, "mixed", n, pos, F, T, U[:n], W[:n]))
+        tickets.put(None)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, first, last, bad = [], None, None, 0
+    while True:
+        t = tickets.get()
+        if t is None:
+            break
+        r, _, _ = srv.wait(t, timeout_s=600.0)
+        bad += r.status != 0
+        lat.append(r.t_done - r.t_submit)
+        first = r.t_submit if first is None else min(first, r.t_submit)
+        last = r.t_done if last is None else max(last, r.t_done)
+    th.join()
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat) * 1e3
+    return {"rate_req_per_s": rate, "duration_s": duration, "requests": n_req, "failed": int(bad),
+            "throughput_req_per_s": n_req / (last - first), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "slots": slots,
+            "budget_gb": budget / 1e9, "plans_resident": stats["plans_resident"],
+            "plans_evicted": stats["plans_evicted"]}
+
+
+# ---------------------------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,6 +341,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--div", type=int, default=1, help="shrink the workload by div^2 in area (testing only)")
     ap.add_argument("--nz", type=int, default=0, help="Chebyshev nodes in z (profiling only; default 65)")
+    ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched/served legs (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="duration of the served leg")
     args = ap.parse_args()
 
     from paper_2210_01837_gb300.replicas import Collective, rank_env, replica_seed_offset, whole_job_rate
@@ -329,6 +472,17 @@ def main():
                 "mixed_vs_fp64_rel_l2": {"U": d(U_mixed, U), "Omega": d(W_mixed, W)}}
         plan64.close()
 
+    # ---- batched and served products (independent systems of uneven size) --------------------
+    batch = served = fp64_unbatched = None
+    if args.batch_systems > 0:
+        batch, systems = batch_leg(binding, torch, dev, args.batch_systems, max(1, min(args.steps, 5)), 2)
+        capacity = batch["batched_products_per_s"]
+        served = served_leg(binding, torch, systems, rate=min(2000.0, 0.8 * capacity), duration=args.serve_seconds)
+        served["rate_basis"] = "0.8 x the batched capacity of the same population (2000/s is above capacity)"
+        fp64_unbatched = fp64_unbatched_leg(binding, torch, dev, systems, min(16, len(systems)))
+        served["fp64_unbatched_products_per_s"] = fp64_unbatched["products_per_s"]
+        served["fp64_unbatched_systems"] = fp64_unbatched["systems"]
+
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -342,7 +496,8 @@ def main():
                           "parallelism": "replicas" if world > 1 else "1 GPU"},
                "particles_per_s": value * n, "fp64": fp64, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                "stage_roofline": stage_roof, "roofline": roofline, "e2e": e2e,
-               "gpu_launches": launches_per_apply * args.steps, "clocks": clocks}
+               "gpu_launches": launches_per_apply * args.steps, "clocks": clocks,
+               "batch": batch, "served": served}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

@@ -1093,8 +1093,7 @@ void launch_bwd_lane(const Plan& p, int kx0, int w, cudaStream_t s) {
 
 template <typename T, bool CURL, int CORR>
 bool set_bwd_lane_smem(size_t bytes) {
-  return cudaFuncSetAttribute(bwd_lane_kernel<T, bwd_pg<T>(), CURL, CORR>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+  return bytes == 0 || allow_smem(bwd_lane_kernel<T, bwd_pg<T>(), CURL, CORR>);
 }
 
 }  // namespace
@@ -1123,23 +1122,12 @@ int bvp_prepare(Plan& p) {
   p.kt.fwd_smem = fs <= 160 * 1024 ? (int)fs : 0;
   p.kt.bwd_smem = bs <= 160 * 1024 ? (int)bs : 0;
   constexpr int NB = fwd_nb<T>(), CB = bwd_cb<T>();
-  if (cudaFuncSetAttribute(fwd_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.kt.fwd_smem) !=
-      cudaSuccess)
-    return 0;
-  if (cudaFuncSetAttribute(bwd_kernel<T, CB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.kt.bwd_smem) !=
-      cudaSuccess)
-    return 0;
-  if (cudaFuncSetAttribute(bwd_kernel<T, CB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.kt.bwd_smem) !=
-      cudaSuccess)
+  if (!allow_smem(fwd_kernel<T, NB>) || !allow_smem(bwd_kernel<T, CB, true>) || !allow_smem(bwd_kernel<T, CB, false>))
     return 0;
   const LaneCfg fc = fwd_lane_cfg<T>(p.g);
   if (fc.threads > 0) {
     constexpr int PG = fwd_pg<T>();
-    if (cudaFuncSetAttribute(fwd_lane_kernel<T, PG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fc.smem) != cudaSuccess ||
-        cudaFuncSetAttribute(fwd_lane_kernel<T, PG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fc.smem) != cudaSuccess)
-      return 0;
+    if (!allow_smem(fwd_lane_kernel<T, PG, true>) || !allow_smem(fwd_lane_kernel<T, PG, false>)) return 0;
   }
   const size_t bl = bwd_lane_smem<T>(p.g);
   if (bl > 0) {

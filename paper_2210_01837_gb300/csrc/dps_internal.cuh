@@ -167,6 +167,21 @@ __device__ __forceinline__ void async_elem(E* s, const E* g) {
   else cp_async4(s, g);
 }
 
+// The largest dynamic shared memory a kernel may be launched with is an attribute of the kernel,
+// shared by every plan in the process.  Raising it once to what the device allows (minus the
+// kernel's static shared memory) lets plans of different sizes coexist; the bytes each launch asks
+// for still decide occupancy.
+template <typename K>
+inline bool allow_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes) == cudaSuccess;
+}
+
 // status bits written by kernels
 enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4 };
 

@@ -545,10 +545,8 @@ int fft_smem_ok(Plan& p) {
   const int trow = fft_threads(p.g.nx), tcol = fft_threads(p.g.ny << lcw);
   if (trow > kFftMaxThreads || tcol > kFftMaxThreads) return 0;
   if (r2c > 220 * 1024 || c2r > 220 * 1024 || col > 220 * 1024) return 0;
-  if (cudaFuncSetAttribute(row_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r2c) != cudaSuccess ||
-      cudaFuncSetAttribute(row_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c2r) != cudaSuccess ||
-      cudaFuncSetAttribute(col_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col) != cudaSuccess ||
-      cudaFuncSetAttribute(col_kernel<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col) != cudaSuccess)
+  if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
+      !allow_smem(col_kernel<T, +1>))
     return 0;
   p.fft_grid[0] = resident_grid(row_r2c_kernel<T>, trow, r2c, p.device);
   p.fft_grid[1] = resident_grid(row_c2r_kernel<T>, trow, c2r, p.device);

@@ -479,16 +479,13 @@ size_t spread_smem(const Plan& p) {
   return (size_t)kStage * p.g.rec_words * sizeof(uint32_t);
 }
 
-// shared-memory limit of the spreading kernels, set once per plan (not at launch, so that applies
-// can be captured into graphs)
+// dynamic shared-memory limit of the spreading kernels, raised at plan creation (never at launch,
+// so that applies can be captured into graphs)
 template <typename T>
 int spread_prepare(const Plan& p) {
-  const int sm = (int)spread_smem<T>(p);
+  (void)p;
   constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
-  return cudaFuncSetAttribute(spread_kernel<T, 6, ZC6>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(spread_kernel<T, 3, ZC3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) ==
-             cudaSuccess;
+  return allow_smem(spread_kernel<T, 6, ZC6>) && allow_smem(spread_kernel<T, 3, ZC3>);
 }
 
 template <typename T>

@@ -13,7 +13,13 @@ by seeded random draws because the paper's configurations are not available:
                     max(|N(1.6, 0.3)|, 1.05), force (0, 0, -1) (gravity) and torque (0, 1, 0)
                     on every particle; grid 3072^2 x 65, h = 2/3, m = 5 with Table I betas.
 
-Seeds are 20221004 + the workload's index (1, 2, 3).
+* ``batch_systems`` - independent systems of uneven size for batched and served products: N
+                    log-uniform on [100, 50000], box side 4 sqrt(N), xy grid the 7-smooth size
+                    nearest L / 0.6, nz drawn from {33, 65, 97}; bottom wall z in [0, 12] with
+                    heights U[1.2, 10], slit z in [0, 20] with U[1.2, 18.8], open z in [0, 20]
+                    with U[2, 18]; forces and torques N(0,1); m = 5 with Table I betas.
+
+Seeds are 20221004 + the workload's index (1, 2, 3, 4).
 """
 
 import numpy as np
@@ -86,3 +92,44 @@ def random_particles(params, n, seed, torques=True, margin=None):
     F = rng.standard_normal((n, 3))
     T = rng.standard_normal((n, 3)) if torques else None
     return pos, F, T
+
+
+def smooth7_sizes(limit):
+    """All 2,3,5,7-smooth integers in [8, limit]."""
+    out = []
+    for a in range(0, 20):
+        for b in range(0, 13):
+            for c in range(0, 9):
+                for d in range(0, 7):
+                    v = 2 ** a * 3 ** b * 5 ** c * 7 ** d
+                    if 8 <= v <= limit:
+                        out.append(v)
+    return sorted(set(out))
+
+
+_DOMAINS = {"bottom_wall": (12.0, 1.2, 10.0), "slit": (20.0, 1.2, 18.8), "free": (20.0, 2.0, 18.0)}
+
+
+def batch_systems(count=256, seed_offset=4, modes=("bottom_wall", "slit"), n_range=(100, 50000), nz_set=(33, 65, 97)):
+    """Independent systems of uneven size: a list of (params, pos, F, T).  Modes alternate over
+    `modes` (half bottom wall, half slit by default)."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    sizes = np.array(smooth7_sizes(8192))
+    out = []
+    m = 5
+    for i in range(count):
+        mode = modes[i % len(modes)]
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        L = 4.0 * np.sqrt(n)
+        nxy = int(sizes[np.argmin(np.abs(sizes - L / 0.6))])
+        nz = int(rng.choice(nz_set))
+        zmax, zlo, zhi = _DOMAINS[mode]
+        x, y = _uniform_xy(rng, n, L)
+        z = rng.uniform(zlo, zhi, n)
+        pos = np.stack([x, y, z], axis=1)
+        F = rng.standard_normal((n, 3))
+        T = rng.standard_normal((n, 3))
+        params = dict(Lx=L, Ly=L, zmin=0.0, zmax=zmax, mode=mode, nx=nxy, ny=nxy, nz=nz,
+                      m_M=m, beta_M=m * _T1_M5[1], m_D=m, beta_D=m * _T1_M5[2], eta=1.0)
+        out.append((params, pos, F, T))
+    return out
