@@ -72,6 +72,15 @@ def algorithmic(params, n, zocc, tsize, rec_bytes):
     }
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return int(json.load(f)[kernel]["bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def occupied_planes(params, pos, alpha):
     """Chebyshev planes within alpha of some particle or of its wall image (the planes the
     library transforms); computed here only to size the algorithmic byte counts."""
@@ -435,7 +444,9 @@ def main():
     if dom == "solve":
         roofline = {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves)", "achieved": round(solve_tflops, 4),
                     "peak": round(FP64_NOMINAL_TFLOPS, 3), "unit": "TFLOP/s",
-                    "frac": round(solve_tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                    "frac": round(solve_tflops / FP64_NOMINAL_TFLOPS, 4),
+                    "traffic": measured_traffic("solve_kernel<float>") if div == 1 and not args.nz else None,
+                    "traffic_source": "profiles/traffic.json (ncu dram bytes, scaled by wavenumbers)",
                     "peak_kind": "FP64 nominal from unit counts x max clock"}
     else:
         gbs = work[dom] / (stages[dom] * 1e-3) / 1e9

@@ -785,7 +785,8 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
   constexpr int NF = TQ ? 6 : 3;  // staged fields per (plane, wavenumber); the first 3 (5) become a (a, b)
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int nthreads = blockDim.x;
-  const int NP = (nthreads >> 5) * PG;  // rows covered by the block (>= N)
+  const int nwarps = nthreads >> 5;
+  const int NP = nwarps * PG;  // rows covered by the block (>= N)
   const int N = g.nz;
   cplx<T>* sV = reinterpret_cast<cplx<T>*>(smraw);               // [cz][NF][32]
   T* sM = reinterpret_cast<T*>(sV + (size_t)cz * NF * kLaneK);  // [cz][2][NP]
@@ -803,20 +804,28 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
     const int nc = min(cz, chi - c0 + 1);
     __syncthreads();  // the previous chunk has been consumed
     // stage the field values and the table rows of this chunk (asynchronous copies)
-    for (int e = threadIdx.x; e < nc * NF * kLaneK; e += nthreads) {
-      const int l = e & 31, r = e >> 5;
-      const int cl = r / NF, f = r - cl * NF;
-      const int col = kt.col[l];
-      if (col >= 0) async_elem(sV + e, grid + ((size_t)f * g.nz + c0 + cl) * plane + col);
-      else sV[e] = mk<T>((T)0, (T)0);
+    // warps stride over (plane, field) rows and lanes over wavenumbers: no divisions
+    {
+      const int col = kt.col[lane];
+      for (int r = wi; r < nc * NF; r += nwarps) {
+        const int cl = r / NF, f = r - cl * NF;  // NF is a compile-time constant
+        cplx<T>* dst = sV + (size_t)r * kLaneK + lane;
+        if (col >= 0) async_elem(dst, grid + ((size_t)f * g.nz + c0 + cl) * plane + col);
+        else *dst = mk<T>((T)0, (T)0);
+      }
     }
-    const int mrow = (TQ ? 2 : 1) * NP;
-    for (int e = threadIdx.x; e < nc * mrow; e += nthreads) {
-      const int cl = e / mrow, r = e - cl * mrow;
-      const int m = r >= NP ? 1 : 0, n = r - m * NP;
-      T* dst = sM + (size_t)cl * 2 * NP + r;
-      if (n < N) async_elem(dst, (m ? dct : ct) + (size_t)(c0 + cl) * npad + n);
-      else *dst = (T)0;
+    for (int cl = wi; cl < nc; cl += nwarps) {
+      const T* crow = ct + (size_t)(c0 + cl) * npad;
+      const T* drow = dct + (size_t)(c0 + cl) * npad;
+      T* dst = sM + (size_t)cl * 2 * NP;
+      for (int n = lane; n < NP; n += 32) {
+        if (n < N) async_elem(dst + n, crow + n);
+        else dst[n] = (T)0;
+        if (TQ) {
+          if (n < N) async_elem(dst + NP + n, drow + n);
+          else dst[NP + n] = (T)0;
+        }
+      }
     }
     cp_commit();
     cp_wait_all();
@@ -889,7 +898,8 @@ __global__ void __launch_bounds__(32 * bwd_warps<T>(), sizeof(T) == 4 ? 2 : 1) b
   constexpr int NT = CURL ? (CORR > 0 ? 3 : 2) : 1;  // staged tables: IC, ICD, SD
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int nthreads = blockDim.x;
-  const int CZ = (nthreads >> 5) * PG;  // planes per chunk
+  constexpr int NW = bwd_warps<T>();
+  constexpr int CZ = NW * PG;  // planes per chunk (the block has NW warps)
   const int N = g.nz;
   const int N4 = (N + 3) & ~3;
   cplx<T>* sY = reinterpret_cast<cplx<T>*>(smraw);                     // [3][N][32]
@@ -930,13 +940,17 @@ __global__ void __launch_bounds__(32 * bwd_warps<T>(), sizeof(T) == 4 ? 2 : 1) b
   cp_commit();
   for (int c0 = clo; c0 <= chi; c0 += CZ) {
     __syncthreads();  // previous chunk consumed
-    for (int e = threadIdx.x; e < N * NT * CZ; e += nthreads) {
-      const int n = e / (NT * CZ), r = e - n * (NT * CZ);
-      const int m = r / CZ, cl = r - m * CZ;
-      const int c = c0 + cl;
-      const T* tab = m == 0 ? ict : (m == 1 ? icdt : sdt);
-      if (c <= chi) async_elem(sM + e, tab + (size_t)n * cpad + c);
-      else sM[e] = (T)0;
+    // warps stride over coefficient rows, lanes over the chunk's planes: no divisions
+    for (int n = wi; n < N; n += NW) {
+#pragma unroll
+      for (int m = 0; m < NT; ++m) {
+        const T* tab = (m == 0 ? ict : (m == 1 ? icdt : sdt)) + (size_t)n * cpad + c0;
+        T* dst = sM + ((size_t)n * NT + m) * CZ;
+        for (int cl = lane; cl < CZ; cl += 32) {
+          if (c0 + cl <= chi) async_elem(dst + cl, tab + cl);
+          else dst[cl] = (T)0;
+        }
+      }
     }
     cp_commit();
     cp_wait_all();  // (the first chunk also completes the staging of y and the amplitudes)

@@ -182,6 +182,18 @@ inline bool allow_smem(K kernel) {
                               optin - (int)fa.sharedSizeBytes) == cudaSuccess;
 }
 
+// float -> double with integer operations only (a conversion instruction would occupy the FP64
+// pipe, which this GPU has little of); exact for normal numbers, infinities and NaNs; float
+// subnormals become zero.
+__device__ __forceinline__ double widen_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  const unsigned m = b & 0x7fffffu;
+  const unsigned de = (e == 0xffu) ? 0x7ffu : e + 896u;
+  return __hiloint2double((int)((b & 0x80000000u) | (de << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // status bits written by kernels
 enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4 };
 

@@ -377,8 +377,8 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
 // Interpolation, a warp per particle (bin order, so neighbouring warps reuse grid lines in cache):
 // the warp splits into NG = 32 / LR groups of LR >= px lanes; a group walks whole x runs of the
 // support rows (iz, iy), lane lx reading node x = hd.x + lx.  Rows are decoded with a multiply-shift
-// (exact for rows < 2^16 / px) and U rows are gathered before they are accumulated, so each lane
-// keeps 3 U loads in flight.
+// (exact for rows < 2^16 / px) and UR rows are gathered before they are accumulated, so each lane
+// keeps 3 UR loads in flight.
 template <typename T, int LR>
 __global__ void __launch_bounds__(256) interp_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec,
                                                      const T* __restrict__ grid, const T* __restrict__ wz,
@@ -443,9 +443,16 @@ __global__ void __launch_bounds__(256) interp_kernel(Geometry g, int64_t n, cons
     }
     double* out = (K == 0) ? U : W;
     if (lane == 0) {
-      out[3 * j] = h2 * (double)a0;
-      out[3 * j + 1] = h2 * (double)a1;
-      out[3 * j + 2] = h2 * (double)a2;
+      if (sizeof(T) == 4) {  // float path: scale in float, widen on the integer pipe
+        const float h2f = (float)h2;
+        out[3 * j] = widen_bits((float)a0 * h2f);
+        out[3 * j + 1] = widen_bits((float)a1 * h2f);
+        out[3 * j + 2] = widen_bits((float)a2 * h2f);
+      } else {
+        out[3 * j] = h2 * (double)a0;
+        out[3 * j + 1] = h2 * (double)a1;
+        out[3 * j + 2] = h2 * (double)a2;
+      }
     }
   }
 }
