@@ -884,9 +884,13 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
 // backward: node values on the occupied planes, u_f(z_c) = sum_n IC[c][n] y_f[n] + corr_f(z_c), with
 // corr_f = (cE + cG zeta) e^{-k zeta} (+ (tE + tG xi) e^{-k xi} between two walls); with torques the
 // half-curl (Eq. 11) from ICD y and the spectral derivative SD corr of the correction node values.
-// CORR: 0 no wall, 1 bottom wall, 2 both walls.
+// CORR: 0 no wall, 1 bottom wall, 2 both walls.  The coefficients y and the table rows stream
+// through shared memory in chunks of kBwdRows rows, double-buffered with cp.async, so the copies of
+// chunk q + 1 overlap the contraction over chunk q.
+constexpr int kBwdRows = 16;
+
 template <typename T, int PG, bool CURL, int CORR>
-__global__ void __launch_bounds__(32 * bwd_warps<T>(), sizeof(T) == 4 ? 2 : 1) bwd_lane_kernel(Geometry g, const T* __restrict__ ict,
+__global__ void __launch_bounds__(32 * bwd_warps<T>(), sizeof(T) == 4 ? 3 : 1) bwd_lane_kernel(Geometry g, const T* __restrict__ ict,
                                                         const T* __restrict__ icdt, const T* __restrict__ sdt,
                                                         int cpad, const T* __restrict__ zeta_g,
                                                         const cplx<T>* __restrict__ kbuf,
@@ -896,67 +900,72 @@ __global__ void __launch_bounds__(32 * bwd_warps<T>(), sizeof(T) == 4 ? 2 : 1) b
   __shared__ KTile kt;
   constexpr bool DE = CURL && CORR > 0;              // derivative of the correction
   constexpr int NT = CURL ? (CORR > 0 ? 3 : 2) : 1;  // staged tables: IC, ICD, SD
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const int nthreads = blockDim.x;
   constexpr int NW = bwd_warps<T>();
-  constexpr int CZ = NW * PG;  // planes per chunk (the block has NW warps)
+  constexpr int CZ = NW * PG;  // planes per plane chunk (the block has NW warps)
+  constexpr int RC = kBwdRows;
+  constexpr int SLOT_Y = 3 * RC * kLaneK;  // complex values of y per slot  [3][RC][32]
+  constexpr int SLOT_M = RC * NT * CZ;     // table values per slot        [RC][NT][CZ]
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int N = g.nz;
   const int N4 = (N + 3) & ~3;
-  cplx<T>* sY = reinterpret_cast<cplx<T>*>(smraw);                     // [3][N][32]
-  cplx<T>* sAmp = sY + (size_t)3 * N * kLaneK;                         // [12][32]
-  T* sE = reinterpret_cast<T*>(sAmp + (CORR ? 12 * kLaneK : 0));      // [N][32] e^{-k zeta_j}
-  T* sZ = sE + (CORR ? (size_t)N * kLaneK : 0);                        // [N4] zeta_j
-  T* sM = sZ + (CORR ? N4 : 0);                                        // [N][NT][CZ]
+  cplx<T>* sAmp = reinterpret_cast<cplx<T>*>(smraw);                                  // [12][32]
+  cplx<T>* sYs = sAmp + (CORR ? 12 * kLaneK : 0);                                     // [2][SLOT_Y]
+  T* sMs = reinterpret_cast<T*>(sYs + 2 * SLOT_Y);                                    // [2][SLOT_M]
+  T* sE = sMs + 2 * SLOT_M;                                                            // [N][32] e^{-k zeta_j}
+  T* sZ = sE + (CORR ? (size_t)N * kLaneK : 0);                                        // [N4] zeta_j
   const int64_t K = (int64_t)g.nkx * g.ny;
   fill_ktile(g, kt, (int64_t)blockIdx.x * kLaneK, (int64_t)w * g.ny, kx0, w, kLaneK);
   __syncthreads();
-  for (int e = threadIdx.x; e < 3 * N * kLaneK; e += nthreads) {
-    const int l = e & 31, fn = e >> 5;
-    const int kid = kt.kid[l];
-    if (kt.col[l] >= 0 && kid >= 0) async_elem(sY + e, kbuf + (size_t)fn * K + kid);
-    else sY[e] = mk<T>((T)0, (T)0);
-  }
+  const int col = kt.col[lane];
+  const int kidl = kt.kid[lane];
   if (CORR) {
-    for (int e = threadIdx.x; e < 12 * kLaneK; e += nthreads) {
-      const int l = e & 31, q = e >> 5;
-      const int kid = kt.kid[l];
-      if (kt.col[l] >= 0 && kid > 0) async_elem(sAmp + e, kaux + (size_t)q * K + kid);
-      else sAmp[e] = mk<T>((T)0, (T)0);
+    for (int q = wi; q < 12; q += NW) {
+      cplx<T>* dst = sAmp + q * kLaneK + lane;
+      if (col >= 0 && kidl > 0) async_elem(dst, kaux + (size_t)q * K + kidl);
+      else *dst = mk<T>((T)0, (T)0);
     }
-    for (int e = threadIdx.x; e < N * kLaneK; e += nthreads) {
-      const int l = e & 31, j = e >> 5;
-      const T kz = (T)kt.kk[l] * zeta_g[j];
-      sE[e] = (kt.col[l] >= 0) ? ((sizeof(T) == 4) ? (T)expf((float)-kz) : (T)exp((double)-kz)) : (T)0;
+    const T kk = (T)kt.kk[lane];
+    for (int j = wi; j < N; j += NW) {
+      const T kz = kk * zeta_g[j];
+      sE[j * kLaneK + lane] = (col >= 0) ? ((sizeof(T) == 4) ? (T)expf((float)-kz) : (T)exp((double)-kz)) : (T)0;
     }
-    for (int j = threadIdx.x; j < N4; j += nthreads) sZ[j] = j < N ? zeta_g[j] : (T)0;
+    for (int j = threadIdx.x; j < N4; j += blockDim.x) sZ[j] = j < N ? zeta_g[j] : (T)0;
   }
+  cp_commit();  // the amplitudes form their own group
   const int clo = zrange[0], chi = zrange[1];
   const size_t plane = (size_t)g.ny * g.pitch;
   const size_t fstride = (size_t)g.nz * plane;
   const T scale = (T)(1.0 / ((double)g.nx * (double)g.ny));
-  const int col = kt.col[lane];
-  const int kidl = kt.kid[lane];
   const T hkx = (T)kt.hkx[lane], hky = (T)kt.hky[lane];
-  cp_commit();
-  for (int c0 = clo; c0 <= chi; c0 += CZ) {
-    __syncthreads();  // previous chunk consumed
-    // warps stride over coefficient rows, lanes over the chunk's planes: no divisions
-    for (int n = wi; n < N; n += NW) {
+  const int nq = (N + RC - 1) / RC;
+  // copies of row chunk q (rows q RC .. q RC + RC - 1) for the plane chunk starting at c0
+  auto stage = [&](int q, int c0) {
+    cplx<T>* dY = sYs + (q & 1) * SLOT_Y;
+    T* dM = sMs + (q & 1) * SLOT_M;
+    const int n0 = q * RC;
+    for (int r = wi; r < 3 * RC; r += NW) {
+      const int f = r / RC, nn = r - f * RC;  // RC is a compile-time constant
+      const int n = n0 + nn;
+      cplx<T>* dst = dY + r * kLaneK + lane;
+      if (n < N && col >= 0 && kidl >= 0) async_elem(dst, kbuf + ((size_t)f * N + n) * K + kidl);
+      else *dst = mk<T>((T)0, (T)0);
+    }
+    for (int nn = wi; nn < RC; nn += NW) {
+      const int n = n0 + nn;
 #pragma unroll
       for (int m = 0; m < NT; ++m) {
         const T* tab = (m == 0 ? ict : (m == 1 ? icdt : sdt)) + (size_t)n * cpad + c0;
-        T* dst = sM + ((size_t)n * NT + m) * CZ;
+        T* dst = dM + (nn * NT + m) * CZ;
         for (int cl = lane; cl < CZ; cl += 32) {
-          if (c0 + cl <= chi) async_elem(dst + cl, tab + cl);
+          if (n < N && c0 + cl <= chi) async_elem(dst + cl, tab + cl);
           else dst[cl] = (T)0;
         }
       }
     }
     cp_commit();
-    cp_wait_all();  // (the first chunk also completes the staging of y and the amplitudes)
-    __syncthreads();
+  };
+  for (int c0 = clo; c0 <= chi; c0 += CZ) {
     const int cw = c0 + wi * PG;  // first plane of this warp
-    if (cw > chi) continue;
     cplx<T> au[PG], av[PG], aw[PG], du[PG], dv[PG];
     T dE[PG], dG[PG], dEt[PG], dGt[PG];
 #pragma unroll
@@ -964,48 +973,66 @@ __global__ void __launch_bounds__(32 * bwd_warps<T>(), sizeof(T) == 4 ? 2 : 1) b
       au[p] = av[p] = aw[p] = du[p] = dv[p] = mk<T>((T)0, (T)0);
       dE[p] = dG[p] = dEt[p] = dGt[p] = (T)0;
     }
-    for (int n = 0; n < N; ++n) {
-      const cplx<T> yu = sY[(size_t)n * kLaneK + lane];
-      const cplx<T> yv = sY[(size_t)(N + n) * kLaneK + lane];
-      const cplx<T> yw = sY[(size_t)(2 * N + n) * kLaneK + lane];
-      const T* mr = sM + (size_t)n * NT * CZ + wi * PG;
-      T ic[PG];
-      ld_row<PG>(mr, ic);
-#pragma unroll
-      for (int p = 0; p < PG; ++p) {
-        au[p].x += ic[p] * yu.x; au[p].y += ic[p] * yu.y;
-        av[p].x += ic[p] * yv.x; av[p].y += ic[p] * yv.y;
-        aw[p].x += ic[p] * yw.x; aw[p].y += ic[p] * yw.y;
+    __syncthreads();  // the previous plane chunk has finished with both slots
+    stage(0, c0);
+    for (int q = 0; q < nq; ++q) {
+      if (q + 1 < nq) {
+        stage(q + 1, c0);
+        cp_wait_but_newest();
+      } else {
+        cp_wait_all();
       }
-      if (CURL) {
-        T id[PG];
-        ld_row<PG>(mr + CZ, id);
-#pragma unroll
-        for (int p = 0; p < PG; ++p) {
-          du[p].x += id[p] * yu.x; du[p].y += id[p] * yu.y;
-          dv[p].x += id[p] * yv.x; dv[p].y += id[p] * yv.y;
-        }
-      }
-      if (DE) {
-        const T en = sE[(size_t)n * kLaneK + lane], gn = sZ[n] * en;
-        T sd[PG];
-        ld_row<PG>(mr + 2 * CZ, sd);
-#pragma unroll
-        for (int p = 0; p < PG; ++p) {
-          dE[p] += sd[p] * en;
-          dG[p] += sd[p] * gn;
-        }
-        if (CORR == 2) {
-          const T et = sE[(size_t)(N - 1 - n) * kLaneK + lane], gt = sZ[N - 1 - n] * et;
+      __syncthreads();  // chunk q (and the amplitudes, node exponentials) visible
+      const cplx<T>* Y = sYs + (q & 1) * SLOT_Y;
+      const T* Mq = sMs + (q & 1) * SLOT_M;
+      const int nend = min(RC, N - q * RC);
+      if (cw <= chi) {
+        for (int nn = 0; nn < nend; ++nn) {
+          const int n = q * RC + nn;
+          const cplx<T> yu = Y[(0 * RC + nn) * kLaneK + lane];
+          const cplx<T> yv = Y[(1 * RC + nn) * kLaneK + lane];
+          const cplx<T> yw = Y[(2 * RC + nn) * kLaneK + lane];
+          const T* mr = Mq + nn * NT * CZ + wi * PG;
+          T ic[PG];
+          ld_row<PG>(mr, ic);
 #pragma unroll
           for (int p = 0; p < PG; ++p) {
-            dEt[p] += sd[p] * et;
-            dGt[p] += sd[p] * gt;
+            au[p].x += ic[p] * yu.x; au[p].y += ic[p] * yu.y;
+            av[p].x += ic[p] * yv.x; av[p].y += ic[p] * yv.y;
+            aw[p].x += ic[p] * yw.x; aw[p].y += ic[p] * yw.y;
+          }
+          if (CURL) {
+            T id[PG];
+            ld_row<PG>(mr + CZ, id);
+#pragma unroll
+            for (int p = 0; p < PG; ++p) {
+              du[p].x += id[p] * yu.x; du[p].y += id[p] * yu.y;
+              dv[p].x += id[p] * yv.x; dv[p].y += id[p] * yv.y;
+            }
+          }
+          if (DE) {
+            const T en = sE[(size_t)n * kLaneK + lane], gn = sZ[n] * en;
+            T sd[PG];
+            ld_row<PG>(mr + 2 * CZ, sd);
+#pragma unroll
+            for (int p = 0; p < PG; ++p) {
+              dE[p] += sd[p] * en;
+              dG[p] += sd[p] * gn;
+            }
+            if (CORR == 2) {
+              const T et = sE[(size_t)(N - 1 - n) * kLaneK + lane], gt = sZ[N - 1 - n] * et;
+#pragma unroll
+              for (int p = 0; p < PG; ++p) {
+                dEt[p] += sd[p] * et;
+                dGt[p] += sd[p] * gt;
+              }
+            }
           }
         }
       }
+      __syncthreads();  // slot q & 1 may be refilled by the next iteration's copies
     }
-    if (col < 0) continue;
+    if (col < 0 || cw > chi) continue;
 #pragma unroll
     for (int p = 0; p < PG; ++p) {
       const int c = cw + p;
@@ -1087,9 +1114,9 @@ template <typename T>
 size_t bwd_lane_smem(const Geometry& g) {
   const size_t N = (size_t)g.nz, N4 = (N + 3) & ~(size_t)3;
   const bool corr = g.mode != DPS_FREE;
-  const int nt = g.with_torque ? (corr ? 3 : 2) : 1;
+  const size_t nt = g.with_torque ? (corr ? 3 : 2) : 1;
   const size_t cz = (size_t)bwd_warps<T>() * bwd_pg<T>();
-  size_t b = 3 * N * kLaneK * sizeof(cplx<T>) + N * nt * cz * sizeof(T);
+  size_t b = 2 * (3 * (size_t)kBwdRows * kLaneK * sizeof(cplx<T>) + (size_t)kBwdRows * nt * cz * sizeof(T));
   if (corr) b += 12 * kLaneK * sizeof(cplx<T>) + N * kLaneK * sizeof(T) + N4 * sizeof(T);
   return (g.nz <= 128 && b <= kBwdLaneSmem) ? b : 0;
 }

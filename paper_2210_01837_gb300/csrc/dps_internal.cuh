@@ -157,6 +157,8 @@ __device__ __forceinline__ void cp_async4(void* s, const void* g) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// wait until at most the newest committed group of this thread is still in flight
+__device__ __forceinline__ void cp_wait_but_newest() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // one naturally aligned element of 4, 8 or 16 bytes
 template <typename E>
