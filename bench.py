@@ -200,21 +200,14 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------------------------------------
 # batched and served products (independent systems of uneven size)
 # ---------------------------------------------------------------------------------------------
-def batch_leg(binding, torch, dev, count, steps, warmup):
-    """Products/s of `count` uneven systems: one after another on one stream, as one batched apply,
-    and as a replayed CUDA graph of that batch."""
+def batch_leg(binding, torch, dev, count, steps, warmup, wave=64):
+    """Products/s of `count` uneven systems, run in waves of `wave` systems (all plans of a wave
+    resident): one after another on one stream, as one batched apply per wave, and as a replayed
+    CUDA graph of each wave's batch.  Returns the summary and the first wave's systems."""
     from paper_2210_01837_gb300.workloads import batch_systems
     systems = batch_systems(count=count)
-    t0 = time.perf_counter()
-    plans, items = [], []
-    for params, pos, F, T in systems:
-        plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=len(pos))
-        tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-        U = torch.empty((len(pos), 3), dtype=torch.float64, device=dev)
-        plans.append(plan)
-        items.append((plan, tdev(pos), tdev(F), tdev(T), U, torch.empty_like(U)))
-    t_plans = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
+    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
     def timed(fn, k):
         for _ in range(warmup):
@@ -228,33 +221,70 @@ def batch_leg(binding, torch, dev, count, steps, warmup):
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / 1e3 / k
 
-    def sequential():
-        for plan, pos, F, T, U, W in items:
-            plan.apply(pos, F, T, U, W)
-
-    def batched():
-        binding.apply_batch(items)
-
-    t_seq = timed(sequential, steps)
-    t_bat = timed(batched, steps)
     binding.dpstokes_batch_prepare()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        batched()
-    t_graph = timed(graph.replay, steps)
-    for plan in plans:
-        plan.check()
-    del graph
+    t_seq = t_bat = t_graph = t_plans = 0.0
+    waves = 0
+    for w0 in range(0, count, wave):
+        chunk = systems[w0:w0 + wave]
+        t0 = time.perf_counter()
+        plans, items = [], []
+        for params, pos, F, T in chunk:
+            plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=len(pos))
+            U = torch.empty((len(pos), 3), dtype=torch.float64, device=dev)
+            plans.append(plan)
+            items.append((plan, tdev(pos), tdev(F), tdev(T), U, torch.empty_like(U)))
+        t_plans += time.perf_counter() - t0
+
+        def sequential():
+            for plan, pos, F, T, U, W in items:
+                plan.apply(pos, F, T, U, W)
+
+        def batched():
+            binding.apply_batch(items)
+
+        t_seq += timed(sequential, steps)
+        t_bat += timed(batched, steps)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            batched()
+        t_graph += timed(graph.replay, steps)
+        for plan in plans:
+            plan.check()
+        del graph, items
+        for plan in plans:
+            plan.close()
+        torch.cuda.synchronize(dev)
+        waves += 1
     particles = sum(len(s[1]) for s in systems)
-    out = {"workload": f"batch_systems: first {count} of the 256 uneven systems (N log-uniform 100..50000, "
-                       f"half bottom wall / half slit, nz in 33/65/97), forces+torques, mixed",
-           "systems": count, "particles": particles, "plan_create_s": round(t_plans, 2),
+    out = {"workload": f"batch_systems: {count} uneven systems (N log-uniform 100..50000, half bottom wall / "
+                       f"half slit, nz in 33/65/97), forces+torques, mixed; {waves} waves of <= {wave} resident plans",
+           "systems": count, "particles": particles, "waves": waves, "plan_create_s": round(t_plans, 2),
            "sequential_products_per_s": count / t_seq, "batched_products_per_s": count / t_bat,
            "graph_products_per_s": count / t_graph, "batched_vs_sequential": t_seq / t_bat,
            "ms_per_batch": {"sequential": t_seq * 1e3, "batched": t_bat * 1e3, "graph": t_graph * 1e3}}
+    return out, systems[:wave]
+
+
+def served_capacity(binding, torch, dev, systems):
+    """Requests/s of the served population when every system runs once per batched apply."""
+    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    plans, items = [], []
+    for params, pos, F, T in systems:
+        plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=len(pos))
+        U = torch.empty((len(pos), 3), dtype=torch.float64, device=dev)
+        plans.append(plan)
+        items.append((plan, tdev(pos), tdev(F), tdev(T), U, torch.empty_like(U)))
+    binding.apply_batch(items)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        binding.apply_batch(items)
+    torch.cuda.synchronize(dev)
+    t = (time.perf_counter() - t0) / 2
+    del items
     for plan in plans:
         plan.close()
-    return out, systems
+    return len(systems) / t
 
 
 def fp64_unbatched_leg(binding, torch, dev, systems, count):
@@ -350,7 +380,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--div", type=int, default=1, help="shrink the workload by div^2 in area (testing only)")
     ap.add_argument("--nz", type=int, default=0, help="Chebyshev nodes in z (profiling only; default 65)")
-    ap.add_argument("--batch-systems", type=int, default=64, help="systems in the batched/served legs (0: skip)")
+    ap.add_argument("--batch-systems", type=int, default=256, help="systems in the batched leg (0: skip batched and served legs)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="duration of the served leg")
     args = ap.parse_args()
 
@@ -410,7 +441,10 @@ def main():
 
     # ---- mixed precision (headline) --------------------------------------------------------
     plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=n)
+    tuned_ms = plan.autotune(d_pos, d_F, d_T, U, W) if not args.no_tune else None
     info = plan.info()
+    tuned = {"autotune_ms": tuned_ms, "fft_col_width": info.fft_col_width, "solve_blocks": info.solve_blocks,
+             "wavenumber_chunks": info.nchunks}
     launches_per_apply = info.launches_per_apply
     plan.enable_timing(True)
     uuid = None
@@ -486,10 +520,12 @@ def main():
     # ---- batched and served products (independent systems of uneven size) --------------------
     batch = served = fp64_unbatched = None
     if args.batch_systems > 0:
-        batch, systems = batch_leg(binding, torch, dev, args.batch_systems, max(1, min(args.steps, 5)), 2)
-        capacity = batch["batched_products_per_s"]
+        batch, systems = batch_leg(binding, torch, dev, args.batch_systems, max(1, min(args.steps, 3)), 1)
+        capacity = served_capacity(binding, torch, dev, systems)
         served = served_leg(binding, torch, systems, rate=min(2000.0, 0.8 * capacity), duration=args.serve_seconds)
-        served["rate_basis"] = "0.8 x the batched capacity of the same population (2000/s is above capacity)"
+        served["population"] = f"the first {len(systems)} batch systems, requests drawn uniformly"
+        served["capacity_req_per_s"] = capacity
+        served["rate_basis"] = "0.8 x the batched capacity of the population (2000/s is above capacity)"
         fp64_unbatched = fp64_unbatched_leg(binding, torch, dev, systems, min(16, len(systems)))
         served["fp64_unbatched_products_per_s"] = fp64_unbatched["products_per_s"]
         served["fp64_unbatched_systems"] = fp64_unbatched["systems"]
@@ -504,6 +540,7 @@ def main():
                           "box": f"{params['Lx']:g}x{params['Ly']:g}x[0,8]",
                           "kernels": "ES m=5, beta_M=6.525, beta_D=11.16 (Table I)", "precision": "mixed",
                           "occupied_planes": zocc, "l2": "working set >> L2 (no flush needed)",
+                          "launch_shapes": tuned,
                           "parallelism": "replicas" if world > 1 else "1 GPU"},
                "particles_per_s": value * n, "fp64": fp64, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                "stage_roofline": stage_roof, "roofline": roofline, "e2e": e2e,

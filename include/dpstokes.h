@@ -127,8 +127,23 @@ typedef struct {
   double alpha_M, alpha_D;  /* kernel supports                                                  */
   int32_t launches_per_apply; /* kernels one apply launches                                       */
   int32_t nchunks;          /* column chunks of the wavenumber-space pipeline                     */
+  int32_t fft_col_width;    /* x-wavenumber columns per block of the y-FFT pass                   */
+  int32_t solve_blocks;     /* persistent blocks of the FP64 per-wavenumber solve                 */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
+
+/* Autotuner (no counterpart in the paper).  Times the plan's applies on the given particles (same
+ * arguments and rules as dpstokes_apply) over a small set of launch shapes, one knob at a time:
+ * the column width of the y-FFT pass (1, 2, 4, 8 within the shared-memory and thread limits), the
+ * persistent grid of the FP64 solve (1-4 blocks per SM within the allocated workspace) and the
+ * column chunks of the wavenumber-space pipeline (1, 2, 4); a candidate replaces the current shape
+ * when it is at least 2 % faster.  The plan keeps the chosen shapes (dpstokes_plan_info reports
+ * them); results do not depend on them beyond summation order.  Synchronises `stream`; on return the
+ * outputs hold the product computed with the chosen shapes and *best_ms (if not NULL) its time.
+ * Returns the device status of the applies. */
+dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
+                                  const double* torques, double* out_vel, double* out_angvel, void* stream,
+                                  double* best_ms);
 
 /* Per-stage timing.  With timing enabled, every apply brackets each kernel launch with a pair of
  * CUDA events on the stream that launch runs on (the wavenumber-space stages run in column chunks

@@ -34,7 +34,7 @@ class dps_plan_info(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("nkx", ctypes.c_int32), ("pitch", ctypes.c_int32),
                 ("nfields", ctypes.c_int32), ("record_words", ctypes.c_int32), ("h", ctypes.c_double),
                 ("alpha_M", ctypes.c_double), ("alpha_D", ctypes.c_double), ("launches_per_apply", ctypes.c_int32),
-                ("nchunks", ctypes.c_int32)]
+                ("nchunks", ctypes.c_int32), ("fft_col_width", ctypes.c_int32), ("solve_blocks", ctypes.c_int32)]
 
 
 class dps_request(ctypes.Structure):
@@ -103,6 +103,7 @@ def load(path=None):
                                            ctypes.POINTER(dps_kernel_params), _I64, _P, _P, _P, _P, _I64, _P]),
         "dpstokes_debug_run": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, _I32]),
         "dpstokes_debug_copy": (_I32, [_P, _I32, _P, _I64, _P]),
+        "dpstokes_plan_autotune": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
         "dpstokes_apply_batch": (_I32, [ctypes.POINTER(dps_request), _I32, _P]),
         "dpstokes_batch_prepare": (_I32, []),
         "dpstokes_server_create": (_I32, [ctypes.POINTER(_P), _I64, _I32]),
@@ -186,6 +187,14 @@ def dpstokes_debug_run(plan, n, positions, forces, torques, out_vel, out_angvel,
 
 def dpstokes_debug_copy(plan, which, dst, dst_bytes, stream):
     return load().dpstokes_debug_copy(plan, which, dst, dst_bytes, stream)
+
+
+def dpstokes_plan_autotune(plan, n, positions, forces, torques, out_vel, out_angvel, stream):
+    """Returns (status, best milliseconds)."""
+    ms = ctypes.c_double(0.0)
+    st = load().dpstokes_plan_autotune(plan, n, positions, forces, torques, out_vel, out_angvel, stream,
+                                       ctypes.byref(ms))
+    return st, ms.value
 
 
 def dpstokes_apply_batch(reqs, stream):
@@ -288,6 +297,19 @@ class Plan:
         if check:
             self.check(stream)
         return U, (W if self.with_torque else None)
+
+    def autotune(self, pos, F, T=None, U=None, W=None, stream=None):
+        """Pick launch shapes by timing applies on these particles; returns the best time in ms."""
+        import torch
+        n = pos.shape[0]
+        U = torch.empty((n, 3), dtype=torch.float64, device=pos.device) if U is None else U
+        if self.with_torque and W is None:
+            W = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+        st, ms = dpstokes_plan_autotune(self.handle, n, _ptr(pos), _ptr(F), _ptr(T), _ptr(U),
+                                        _ptr(W) if self.with_torque else None, _stream(stream))
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_plan_autotune")
+        return ms
 
     def apply_host(self, pos, F, T=None, U=None, W=None, stream=None):
         """Host (numpy float64, preferably pinned) arrays in and out; synchronises."""

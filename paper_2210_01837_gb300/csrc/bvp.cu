@@ -241,14 +241,18 @@ struct SolveWs {
   int slots;
 };
 
-template <typename T>
-__device__ void solve_one(const Geometry& g, const double* __restrict__ band, const T* __restrict__ bandT,
+// FACT: factorise the banded systems while sweeping the pressure right-hand side and keep the
+// factorisation in the slot's workspace; without FACT, reuse the factorisation left there by the
+// previous call on the same slot, which must have had the same |k| (the partner -ky of a pair).
+// Returns whether the slot now holds a factorisation.
+template <typename T, bool FACT>
+__device__ __noinline__ bool solve_one(const Geometry& g, const double* __restrict__ band, const T* __restrict__ bandT,
                           cplx<T>* __restrict__ kbuf, cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ pws,
                           cplx<double>* __restrict__ sw, double* __restrict__ fr, int slots, int slot, int64_t kidx,
                           int64_t K) {
   const int N = g.nz;
   const KInfo ki = kinfo(g, kidx);
-  if (ki.nyq) return;
+  if (ki.nyq) return false;
   auto KB = [&](int f, int n) -> cplx<T>& { return kbuf[((size_t)f * N + n) * K + kidx]; };
   auto SW = [&](int f, int n) -> cplx<double>& { return sw[((size_t)f * N + n) * slots + slot]; };
   auto FR = [&](int f, int n) -> double& { return fr[((size_t)f * N + n) * slots + slot]; };
@@ -300,7 +304,7 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
       }
     }
     for (int q = 0; q < 12; ++q) AUX(q) = mk<T>((T)0, (T)0);
-    return;
+    return false;
   }
 
   const double kx = ki.kx, ky = ki.ky, kk = ki.kk, kap = kk * kk;
@@ -317,12 +321,18 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
     double t_next = 0.0, bfold = 0.0;
     cplx<T> dh_next = zT;  // derivative recurrence of h over the opposite parity
     cplx<T> fc = KB(0, nlast), gc = KB(1, nlast), hc = (nlast + 1 < N) ? KB(2, nlast + 1) : zT;
+    double rhoc = FACT ? 0.0 : FR(0, nlast), bcc = FACT ? 0.0 : FR(2, nlast);  // stored factorisation
     for (int n = nlast; n >= par; n -= 2) {
       cplx<T> fn = zT, gn = zT, hn = zT;
+      double rhon = 0.0, bcn = 0.0;
       if (n - 2 >= par) {
         fn = KB(0, n - 2);
         gn = KB(1, n - 2);
         hn = KB(2, n - 1);
+        if (!FACT) {
+          rhon = FR(0, n - 2);
+          bcn = FR(2, n - 2);
+        }
       }
       cplx<T> dh = dh_next + scl(hc, (T)(2 * (n + 1)));
       dh_next = dh;
@@ -330,29 +340,36 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
       const cplx<T> rt = mk<T>(-tkx * fc.y - tky * gc.y + tsH * dh.x, tkx * fc.x + tky * gc.x + tsH * dh.y);
       const cplx<double> r = wid(rt);
       const double U = -kap * bu[n];
-      const double bcur = (n == nlast) ? (sH * bP[n] + kk * bQ[n]) : bfold;
+      const double bcur = FACT ? ((n == nlast) ? (sH * bP[n] + kk * bQ[n]) : bfold) : bcc;
       if (n > par) {
-        const double rho = 1.0 / ((sig - kap * bd[n]) - U * t_next);
-        const double t = rho * (-kap * bl[n]);
+        double rho;
+        if (FACT) {
+          rho = 1.0 / ((sig - kap * bd[n]) - U * t_next);
+          const double t = rho * (-kap * bl[n]);
+          FR(0, n) = rho;
+          FR(1, n) = t;
+          FR(2, n) = bcur;
+          bfold = (sH * bP[n - 2] + kk * bQ[n - 2]) - bcur * t;
+          t_next = t;
+        } else {
+          rho = rhoc;
+        }
         const cplx<double> s = scl(r - scl(s_next, U), rho);
-        FR(0, n) = rho;
-        FR(1, n) = t;
-        FR(2, n) = bcur;
         SW(0, n) = s;
         gacc = gacc - scl(s, bcur);
-        bfold = (sH * bP[n - 2] + kk * bQ[n - 2]) - bcur * t;
         s_next = s;
-        t_next = t;
       } else {
         // row `par`: D' c - kappa a = r - U s_{par+2};  boundary row: beta_a a + bcur c = g'
-        const double Dp = (sig - kap * bd[n]) - U * t_next;
+        const double Dp = FACT ? (sig - kap * bd[n]) - U * t_next : rhoc;
         const double beta_a = (par == 0) ? kk : (sH + kk);
         const cplx<double> rhs = r - scl(s_next, U);
         const double idet = 1.0 / (Dp * beta_a + kap * bcur);
         const cplx<double> c0 = scl(scl(rhs, beta_a) + scl(gacc, kap), idet);
         const cplx<double> a = scl(scl(gacc, Dp) - scl(rhs, bcur), idet);
-        FR(0, n) = Dp;
-        FR(2, n) = bcur;
+        if (FACT) {
+          FR(0, n) = Dp;
+          FR(2, n) = bcur;
+        }
         // ascending substitution; y = B B c + a in the transform precision
         cplx<double> cm = c0;
         cplx<T> tcm2 = zT, tcm = nar<T>(c0);
@@ -391,6 +408,8 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
       fc = fn;
       gc = gn;
       hc = hn;
+      rhoc = rhon;
+      bcc = bcn;
     }
   }
 
@@ -582,6 +601,7 @@ __device__ void solve_one(const Geometry& g, const double* __restrict__ band, co
     AUX(4 * f + 2) = nar<T>(tE[f]);
     AUX(4 * f + 3) = nar<T>(tG[f]);
   }
+  return true;
 }
 
 template <typename T>
@@ -591,11 +611,22 @@ __global__ void __launch_bounds__(kBvpThreads, 3) solve_kernel(Geometry g, const
                                                             cplx<double>* __restrict__ sw, double* __restrict__ fr,
                                                             int kx0, int w) {
   const int64_t K = (int64_t)g.nkx * g.ny;
-  const int64_t total = (int64_t)w * g.ny;
+  const int rows = g.ny / 2 + 1;  // ky rows 0 .. ny/2; row j > 0 pairs with ny - j unless 2 j = ny
+  const int64_t total = (int64_t)w * rows;
   const int slots = gridDim.x * blockDim.x;
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int64_t i = slot; i < total; i += slots)
-    solve_one<T>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, chunk_kidx(g, i, kx0, w), K);
+  for (int64_t i = slot; i < total; i += slots) {
+    const unsigned ii = (unsigned)i;
+    const int kyi = (int)(ii / (unsigned)w);
+    const int kxi = kx0 + (int)(ii - (unsigned)kyi * (unsigned)w);
+    const int64_t k1 = (int64_t)kyi * g.nkx + kxi;
+    const bool factored = solve_one<T, true>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k1, K);
+    if (kyi > 0 && 2 * kyi != g.ny && factored) {
+      // the partner -ky has the same |k| and therefore the same banded systems
+      const int64_t k2 = (int64_t)(g.ny - kyi) * g.nkx + kxi;
+      solve_one<T, false>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k2, K);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------

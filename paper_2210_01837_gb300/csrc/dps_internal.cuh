@@ -122,6 +122,8 @@ struct Plan {
   void* ws;             // per-slot workspace of the per-k solver
   int bvp_blocks;       // persistent grid size of the per-k solver
   int fft_grid[4];      // resident grids of the persistent FFT passes: rows fwd/inv, columns fwd/inv
+  int col_lcw;          // log2 of the column block of the y-FFT pass (default rule or autotuned)
+  int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)
   double* stage_in;     // [max_n][9]
@@ -215,6 +217,7 @@ template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
+template <typename T> int fft_set_col_width(Plan& p, int lcw);  // 0 if the width does not fit
 
 // host-side validation of an apply's arguments, and the stream-ordered product itself
 dps_status check_apply_args(const Plan* p, int64_t n, const double* pos, const double* F, const double* Tq,

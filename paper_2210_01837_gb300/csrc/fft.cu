@@ -538,21 +538,29 @@ int resident_grid(KernelT kernel, int threads, size_t smem, int device) {
 }  // namespace
 
 template <typename T>
+int fft_set_col_width(Plan& p, int lcw) {
+  if (lcw < 0 || lcw > 3) return 0;
+  const size_t col = col_smem<T>(p.g, lcw);
+  const int tcol = fft_threads(p.g.ny << lcw);
+  if (tcol > kFftMaxThreads || col > 220 * 1024) return 0;
+  p.col_lcw = lcw;
+  p.fft_grid[2] = resident_grid(col_kernel<T, -1>, tcol, col, p.device);
+  p.fft_grid[3] = resident_grid(col_kernel<T, +1>, tcol, col, p.device);
+  return 1;
+}
+
+template <typename T>
 int fft_smem_ok(Plan& p) {
   const size_t r2c = row_r2c_smem<T>(p.g), c2r = row_c2r_smem<T>(p.g);
-  const int lcw = col_lwidth<T>(p);
-  const size_t col = col_smem<T>(p.g, lcw);
-  const int trow = fft_threads(p.g.nx), tcol = fft_threads(p.g.ny << lcw);
-  if (trow > kFftMaxThreads || tcol > kFftMaxThreads) return 0;
-  if (r2c > 220 * 1024 || c2r > 220 * 1024 || col > 220 * 1024) return 0;
+  const int trow = fft_threads(p.g.nx);
+  if (trow > kFftMaxThreads) return 0;
+  if (r2c > 220 * 1024 || c2r > 220 * 1024) return 0;
   if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
       !allow_smem(col_kernel<T, +1>))
     return 0;
   p.fft_grid[0] = resident_grid(row_r2c_kernel<T>, trow, r2c, p.device);
   p.fft_grid[1] = resident_grid(row_c2r_kernel<T>, trow, c2r, p.device);
-  p.fft_grid[2] = resident_grid(col_kernel<T, -1>, tcol, col, p.device);
-  p.fft_grid[3] = resident_grid(col_kernel<T, +1>, tcol, col, p.device);
-  return 1;
+  return fft_set_col_width<T>(p, col_lwidth<T>(p));
 }
 
 template <typename T>
@@ -572,7 +580,7 @@ template <typename T>
 void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
-  const int lcw = col_lwidth<T>(p);
+  const int lcw = p.col_lcw;
   const size_t sm = col_smem<T>(g, lcw);
   const int th = fft_threads(g.ny << lcw);
   if (dir < 0)
@@ -585,13 +593,15 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
 
 template int fft_smem_ok<float>(Plan&);
 template int fft_smem_ok<double>(Plan&);
+template int fft_set_col_width<float>(Plan&, int);
+template int fft_set_col_width<double>(Plan&, int);
 template void launch_fft_rows<float>(const Plan&, int, cudaStream_t);
 template void launch_fft_rows<double>(const Plan&, int, cudaStream_t);
 template void launch_fft_cols<float>(const Plan&, int, int, int, cudaStream_t);
 template void launch_fft_cols<double>(const Plan&, int, int, int, cudaStream_t);
 
 template <typename T>
-int fft_col_width(const Plan& p) { return 1 << col_lwidth<T>(p); }
+int fft_col_width(const Plan& p) { return 1 << p.col_lcw; }
 template int fft_col_width<float>(const Plan&);
 template int fft_col_width<double>(const Plan&);
 

@@ -200,6 +200,27 @@ __global__ void bin_scatter_kernel(int64_t n, const int* __restrict__ bin_of, in
   sorted[p] = (int)j;
 }
 
+// Particles of one bin in increasing index order (the scatter's atomics leave the order open), so
+// the spread sums in the same order on every apply: results repeat bit for bit.  One thread per bin,
+// insertion sort; bins above kSortedBinMax particles keep the scatter's order.
+constexpr int kSortedBinMax = 256;
+
+__global__ void bin_sort_kernel(const int* __restrict__ start, int* __restrict__ sorted, int nbins) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const int s0 = start[b], s1 = start[b + 1];
+  if (s1 - s0 < 2 || s1 - s0 > kSortedBinMax) return;
+  for (int i = s0 + 1; i < s1; ++i) {
+    const int v = sorted[i];
+    int j = i - 1;
+    while (j >= s0 && sorted[j] > v) {
+      sorted[j + 1] = sorted[j];
+      --j;
+    }
+    sorted[j + 1] = v;
+  }
+}
+
 // does the cyclic node interval [a, a+len_a) intersect [b, b+len_b) (mod n)?
 __device__ __forceinline__ bool cyc_overlap(int a, int len_a, int b, int len_b, int n) {
   int d1 = b - a; if (d1 < 0) d1 += n;
@@ -476,6 +497,7 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
     const int threads = 256;
     bin_scatter_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(n, p.bin_of, p.bin_cursor,
                                                                                   p.sorted);
+    bin_sort_kernel<<<(unsigned)((nbins + 127) / 128), 128, 0, s>>>(p.bin_start, p.sorted, nbins);
   }
 }
 

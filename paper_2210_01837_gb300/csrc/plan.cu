@@ -244,6 +244,16 @@ dps_status build_tables(Plan* p) {
   return DPS_OK;
 }
 
+// column chunks of the wavenumber-space pipeline: multiples of 32 columns; false if too narrow
+bool set_chunks(Plan& p, int J) {
+  const int nkx = p.g.nkx;
+  if (J < 1 || J > kMaxChunks || (J > 1 && nkx < 64 * J)) return false;
+  p.nchunks = J;
+  for (int j = 0; j < J; ++j) p.chunk_x0[j] = (int)((int64_t)j * nkx / J) / 32 * 32;
+  p.chunk_x0[J] = nkx;
+  return true;
+}
+
 template <typename T>
 dps_status allocate(Plan* p) {
   Geometry& g = p->g;
@@ -269,6 +279,7 @@ dps_status allocate(Plan* p) {
   const int64_t K = (int64_t)g.nkx * g.ny;
   const int64_t need_blocks = (K + kBvpThreads - 1) / kBvpThreads;
   if (p->bvp_blocks > need_blocks) p->bvp_blocks = (int)std::max<int64_t>(1, need_blocks);
+  p->bvp_blocks_max = p->bvp_blocks;
   p->ws_bytes = (int64_t)p->bvp_blocks * kBvpThreads * (int64_t)bvp_slot_bytes<T>(*p);
   if (!alloc(&p->ws, (size_t)p->ws_bytes)) return DPS_ERR_OOM;
   if (!alloc(&p->kt.kbuf, 3 * (size_t)g.nz * (size_t)K * sizeof(cplx<T>))) return DPS_ERR_OOM;
@@ -279,20 +290,16 @@ dps_status allocate(Plan* p) {
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
   if (!spread_prepare<T>(*p)) return DPS_ERR_CUDA;
   // column chunks of the wavenumber-space pipeline (multiples of 32 columns, ~192 wide)
-  const int nkx = g.nkx;
-  // one chunk: measured on GB300, co-running the FP64 solve with the float transforms slowed both
-  // (they compete for issue slots), so the stages run back to back; the chunked form is kept for
-  // DPS_CHUNKS experiments
+  // one chunk by default: measured on GB300, co-running the FP64 solve with the float transforms
+  // slowed both (they compete for issue slots); DPS_CHUNKS in the environment or the autotuner may
+  // choose more
   int J = 1;
   if (const char* e = getenv("DPS_CHUNKS")) J = std::max(1, std::min(atoi(e), kMaxChunks));
-  if (nkx < 64 * J) J = 1;
-  p->nchunks = J;
-  for (int j = 0; j < J; ++j) p->chunk_x0[j] = (int)((int64_t)j * nkx / J) / 32 * 32;
-  p->chunk_x0[J] = nkx;
+  if (!set_chunks(*p, J)) set_chunks(*p, 1);
   for (int i = 0; i < 2; ++i)
     if (cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) != cudaSuccess) return DPS_ERR_CUDA;
   if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
-  for (int j = 0; j < J; ++j) {
+  for (int j = 0; j < kMaxChunks; ++j) {  // events for every chunk count the autotuner may pick
     if (cudaEventCreateWithFlags(&p->ev_f[j], cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
     if (cudaEventCreateWithFlags(&p->ev_s[j], cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
     if (cudaEventCreateWithFlags(&p->ev_b[j], cudaEventDisableTiming) != cudaSuccess) return DPS_ERR_CUDA;
@@ -554,9 +561,80 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   out->h = p->g.h;
   out->alpha_M = p->g.kM.alpha;
   out->alpha_D = p->g.with_torque ? p->g.kD.alpha : 0.0;
-  out->launches_per_apply = 7 + 5 * p->nchunks;
+  out->launches_per_apply = 8 + 5 * p->nchunks;
   out->nchunks = p->nchunks;
+  out->fft_col_width = 1 << p->col_lcw;
+  out->solve_blocks = p->bvp_blocks;
   return DPS_OK;
+}
+
+dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
+                                  const double* torques, double* out_vel, double* out_angvel, void* stream,
+                                  double* best_ms) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  dps_status st = dps::check_apply_args(p, n, positions, forces, torques, out_vel, out_angvel);
+  if (st != DPS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return DPS_ERR_CUDA;
+  // mean time of two applies after one untimed apply
+  auto measure = [&](double* ms) -> dps_status {
+    dps_status r = dps::run(p, n, positions, forces, torques, out_vel, out_angvel, s, 99);
+    if (r != DPS_OK) return r;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < 2 && r == DPS_OK; ++i) r = dps::run(p, n, positions, forces, torques, out_vel, out_angvel, s, 99);
+    cudaEventRecord(e1, s);
+    if (r != DPS_OK) return r;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return DPS_ERR_CUDA;
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, e0, e1) != cudaSuccess) return DPS_ERR_CUDA;
+    *ms = 0.5 * f;
+    return DPS_OK;
+  };
+  const bool mixed = p->precision == DPS_MIXED;
+  auto set_width = [&](int l) { return mixed ? dps::fft_set_col_width<float>(*p, l) : dps::fft_set_col_width<double>(*p, l); };
+  double best = 0.0, t = 0.0;
+  st = measure(&best);
+  // keep a candidate only when it is clearly (2 %) faster than the incumbent
+  auto better = [&](double cand) { return cand < 0.98 * best; };
+  // 1. column block of the y-FFT pass
+  int best_l = p->col_lcw;
+  for (int l = 0; l <= 3 && st == DPS_OK; ++l) {
+    if (l == best_l || !set_width(l)) continue;
+    st = measure(&t);
+    if (st == DPS_OK && better(t)) { best = t; best_l = l; }
+  }
+  set_width(best_l);
+  // 2. persistent grid of the FP64 solve (blocks per SM, within the allocated workspace)
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  int best_b = p->bvp_blocks;
+  for (int per = 1; per <= 4 && st == DPS_OK; ++per) {
+    const int b = std::min(per * sms, p->bvp_blocks_max);
+    if (b == best_b) continue;
+    p->bvp_blocks = b;
+    st = measure(&t);
+    if (st == DPS_OK && better(t)) { best = t; best_b = b; }
+  }
+  p->bvp_blocks = best_b;
+  // 3. column chunks of the wavenumber-space pipeline (the FP64 solve of one chunk overlaps the
+  //    float transforms of its neighbours)
+  int best_j = p->nchunks;
+  for (int j : {1, 2, 4}) {
+    if (st != DPS_OK) break;
+    if (j == best_j || !dps::set_chunks(*p, j)) continue;
+    st = measure(&t);
+    if (st == DPS_OK && better(t)) { best = t; best_j = j; }
+  }
+  dps::set_chunks(*p, best_j);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DPS_OK) return st;
+  // leave the outputs holding the product with the chosen shapes
+  st = dps::run(p, n, positions, forces, torques, out_vel, out_angvel, s, 99);
+  if (st != DPS_OK) return st;
+  if (best_ms) *best_ms = best;
+  return dpstokes_status(plan, stream);
 }
 
 dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable) {

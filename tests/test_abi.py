@@ -86,7 +86,7 @@ def test_struct_layout_matches_the_c_compiler(tmp_path):
     from paper_2210_01837_gb300 import binding
     fields = {
         "dps_grid": ["nz"], "dps_kernel_params": ["beta_M", "m_D", "beta_D", "eta", "with_torque", "precision", "max_n"],
-        "dps_plan_info": ["nkx", "h", "alpha_D", "launches_per_apply", "nchunks"],
+        "dps_plan_info": ["nkx", "h", "alpha_D", "launches_per_apply", "nchunks", "fft_col_width", "solve_blocks"],
         "dps_request": ["n", "positions", "torques", "out_angvel", "status"],
         "dps_serve_request": ["wall_mode", "grid", "kp", "n", "positions", "out_angvel"],
         "dps_serve_result": ["t_submit", "t_done"], "dps_server_stats": ["running", "bytes_resident"],

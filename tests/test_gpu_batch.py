@@ -1,8 +1,8 @@
 """Batched applies and the request server against single applies of the same problems.
 
 Each result of a batch or of the server must be the product of dpstokes_apply for that problem,
-within the alone-vs-in-mix bars (1e-12 relative L2 in FP64, 1e-6 mixed): the only freedom is the
-order in which particles of one bin are summed, which binning by atomics leaves open."""
+within the alone-vs-in-mix bars (1e-12 relative L2 in FP64, 1e-6 mixed).  (Bins are sorted by
+particle index, so in practice the results repeat bit for bit.)"""
 
 import numpy as np
 import pytest
