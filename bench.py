@@ -68,7 +68,10 @@ def algorithmic(params, n, zocc, tsize, rec_bytes):
         "fft_y_inv": 2 * cpx,
         "fft_x_inv": cpx + real,
         "interp": real + n * rec_bytes + n * 6 * 8,
-        "solve_fp64_flops": K * 134 * nz,
+        # FP64 flops per wavenumber and Chebyshev row: 8 real right-hand sides x (elimination 3,
+        # boundary fold 2, back substitution 2, boundary value 2), 2 for the U coefficients of the two
+        # passes, and the factorisation (13) shared by the +ky/-ky pair; the B B map runs in float
+        "solve_fp64_flops": K * nz * (8 * 9 + 2 + 13 / 2),
     }
 
 
