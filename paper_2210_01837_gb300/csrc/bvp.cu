@@ -801,7 +801,8 @@ __device__ __forceinline__ void ld_row(const double* p, double (&o)[PG]) {
 }
 
 // forward: kbuf[o][n][k] = sum_c C[n][c] a_o(c, k) + DC[n][c] b_o(c, k) over the occupied planes, with
-// a_o = f_o + (1/2)(i k x tau)_o and the derivative terms of the half-curl b_x = -tau_y/2, b_y = tau_x/2
+// a_o = f_o + (1/2)(i k x tau)_o and the derivative terms of the half-curl b_x = -tau_y/2, b_y = tau_x/2.
+// The planes stream through two shared-memory slots of cz planes (cp.async, double-buffered).
 template <typename T> __host__ __device__ constexpr int fwd_max_threads() { return sizeof(T) == 4 ? 384 : 512; }
 
 template <typename T, int PG, bool TQ>
@@ -819,31 +820,32 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
   const int nwarps = nthreads >> 5;
   const int NP = nwarps * PG;  // rows covered by the block (>= N)
   const int N = g.nz;
-  cplx<T>* sV = reinterpret_cast<cplx<T>*>(smraw);               // [cz][NF][32]
-  T* sM = reinterpret_cast<T*>(sV + (size_t)cz * NF * kLaneK);  // [cz][2][NP]
+  // two slots of cz planes each: field values [cz][NF][32] and table rows [cz][2][NP]
+  const int slotV = cz * NF * kLaneK, slotM = cz * 2 * NP;
+  cplx<T>* sVs = reinterpret_cast<cplx<T>*>(smraw);
+  T* sMs = reinterpret_cast<T*>(sVs + 2 * (size_t)slotV);
   const int64_t K = (int64_t)g.nkx * g.ny;
   fill_ktile(g, kt, (int64_t)blockIdx.x * kLaneK, (int64_t)w * g.ny, kx0, w, kLaneK);
   __syncthreads();
   const int clo = zrange[0], chi = zrange[1];
   const size_t plane = (size_t)g.ny * g.pitch;
+  const int col = kt.col[lane];
   cplx<T> acc[3][PG];
 #pragma unroll
   for (int o = 0; o < 3; ++o)
 #pragma unroll
     for (int p = 0; p < PG; ++p) acc[o][p] = mk<T>((T)0, (T)0);
-  for (int c0 = clo; c0 <= chi; c0 += cz) {
-    const int nc = min(cz, chi - c0 + 1);
-    __syncthreads();  // the previous chunk has been consumed
-    // stage the field values and the table rows of this chunk (asynchronous copies)
-    // warps stride over (plane, field) rows and lanes over wavenumbers: no divisions
-    {
-      const int col = kt.col[lane];
-      for (int r = wi; r < nc * NF; r += nwarps) {
-        const int cl = r / NF, f = r - cl * NF;  // NF is a compile-time constant
-        cplx<T>* dst = sV + (size_t)r * kLaneK + lane;
-        if (col >= 0) async_elem(dst, grid + ((size_t)f * g.nz + c0 + cl) * plane + col);
-        else *dst = mk<T>((T)0, (T)0);
-      }
+  const int nq = chi >= clo ? (chi - clo + cz) / cz : 0;  // plane chunks
+  // copies of plane chunk q into slot q & 1 (warps stride over rows, lanes over wavenumbers)
+  auto stage = [&](int q) {
+    const int c0 = clo + q * cz, nc = min(cz, chi - c0 + 1);
+    cplx<T>* sV = sVs + (q & 1) * (size_t)slotV;
+    T* sM = sMs + (q & 1) * (size_t)slotM;
+    for (int r = wi; r < nc * NF; r += nwarps) {
+      const int cl = r / NF, f = r - cl * NF;  // NF is a compile-time constant
+      cplx<T>* dst = sV + (size_t)r * kLaneK + lane;
+      if (col >= 0) async_elem(dst, grid + ((size_t)f * g.nz + c0 + cl) * plane + col);
+      else *dst = mk<T>((T)0, (T)0);
     }
     for (int cl = wi; cl < nc; cl += nwarps) {
       const T* crow = ct + (size_t)(c0 + cl) * npad;
@@ -859,14 +861,24 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
       }
     }
     cp_commit();
-    cp_wait_all();
-    __syncthreads();
+  };
+  if (nq > 0) stage(0);
+  for (int q = 0; q < nq; ++q) {
+    if (q + 1 < nq) {
+      stage(q + 1);
+      cp_wait_but_newest();
+    } else {
+      cp_wait_all();
+    }
+    __syncthreads();  // chunk q visible
+    const int nc = min(cz, chi - (clo + q * cz) + 1);
+    cplx<T>* sV = sVs + (q & 1) * (size_t)slotV;
+    const T* sM = sMs + (q & 1) * (size_t)slotM;
     if (TQ) {
       // a_o = f_o + (1/2)(i k x tau)_o in slots 0..2, b_x = -tau_y/2, b_y = tau_x/2 in slots 3, 4
-      for (int e = threadIdx.x; e < nc * kLaneK; e += nthreads) {
-        const int cl = e >> 5, l = e & 31;
-        cplx<T>* v = sV + (size_t)cl * NF * kLaneK + l;
-        const T hkx = (T)kt.hkx[l], hky = (T)kt.hky[l];  // k/2
+      for (int cl = wi; cl < nc; cl += nwarps) {
+        cplx<T>* v = sV + (size_t)cl * NF * kLaneK + lane;
+        const T hkx = (T)kt.hkx[lane], hky = (T)kt.hky[lane];  // k/2
         const cplx<T> tx = v[3 * kLaneK], ty = v[4 * kLaneK], tz = v[5 * kLaneK];
         v[0] = v[0] + mul_i(scl(tz, hky));
         v[kLaneK] = v[kLaneK] - mul_i(scl(tz, hkx));
@@ -898,8 +910,9 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
         }
       }
     }
+    __syncthreads();  // slot q & 1 may be refilled by the next iteration's copies
   }
-  if (kt.col[lane] >= 0) {
+  if (col >= 0) {
     const int kid = kt.kid[lane] >= 0 ? kt.kid[lane] : -1 - kt.kid[lane];
 #pragma unroll
     for (int p = 0; p < PG; ++p) {
@@ -1124,7 +1137,7 @@ struct LaneCfg {
   int threads = 0, cz = 0;
   size_t smem = 0;
 };
-constexpr size_t kFwdLaneSmem = 80 * 1024;   // two blocks per SM
+constexpr int kFwdPlanes = 8;                // planes per double-buffered chunk of the forward transform
 constexpr size_t kBwdLaneSmem = 200 * 1024;  // largest backward stage
 
 template <typename T>
@@ -1136,8 +1149,8 @@ LaneCfg fwd_lane_cfg(const Geometry& g) {
   const int nf = g.with_torque ? 6 : 3;
   const size_t per_plane = (size_t)nf * kLaneK * sizeof(cplx<T>) + (size_t)2 * nw * PG * sizeof(T);
   c.threads = 32 * nw;
-  c.cz = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.nz, kFwdLaneSmem / per_plane));
-  c.smem = per_plane * c.cz;
+  c.cz = std::min(g.nz, kFwdPlanes);      // planes per pipelined chunk
+  c.smem = 2 * per_plane * (size_t)c.cz;  // two slots
   return c;
 }
 

@@ -231,35 +231,69 @@ __device__ __forceinline__ bool cyc_overlap(int a, int len_a, int b, int len_b, 
 constexpr int kCandCap = 2048;
 constexpr int kStage = 128;  // candidate records staged in shared memory at a time
 
-// Accumulate one batch of staged candidate records into the thread's node column, planes
-// [zb, zb + ZC).  Records live in shared memory (`srec`, `nb` of them, `rw` words each).
-template <typename T, int NF, int ZC>
-__device__ __forceinline__ void spread_batch(const Geometry& g, const uint32_t* srec, int nb, int rw, int gx, int gy,
-                                             int zb, T (&acc)[ZC][NF]) {
+// Per warp (one tile row gy), the staged candidates whose support rows include gy, one list per
+// kernel (monopole / dipole), built with warp ballots; the z-chunk loops then walk only these.
+template <int NF>
+__device__ __forceinline__ void build_row_lists(const Geometry& g, const uint32_t* srec, int nrec, int rw, int gy,
+                                                int* wl0, int* wl1, int& n0, int& n1) {
+  const int lane = threadIdx.x & 31;
+  n0 = n1 = 0;
+  for (int base = 0; base < nrec; base += 32) {
+    const int i = base + lane;
+    bool h0 = false, h1 = false;
+    if (i < nrec) {
+      const int4* hd = reinterpret_cast<const int4*>(srec + (size_t)i * rw);
+      const int4 a = hd[0];
+      int dy = gy - a.y;
+      if (dy < 0) dy += g.ny;
+      h0 = a.w > 0 && dy < g.kM.px;
+      if (NF == 6) {
+        const int4 b = hd[1];
+        int dy1 = gy - b.y;
+        if (dy1 < 0) dy1 += g.ny;
+        h1 = b.w > 0 && dy1 < g.kD.px;
+      }
+    }
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned m0 = __ballot_sync(0xffffffffu, h0);
+    if (h0) wl0[n0 + __popc(m0 & below)] = i;
+    n0 += __popc(m0);
+    if (NF == 6) {
+      const unsigned m1 = __ballot_sync(0xffffffffu, h1);
+      if (h1) wl1[n1 + __popc(m1 & below)] = i;
+      n1 += __popc(m1);
+    }
+  }
+  __syncwarp();
+}
+
+// Accumulate the listed candidates of kernel K into the thread's node column, planes [zb, zb + ZC).
+template <typename T, int NF, int ZC, int K>
+__device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl, int rw,
+                                            int gx, int gy, int zb, T (&acc)[ZC][NF]) {
   const int stride = 2 * g.pxc + g.lzc;
-  for (int i = 0; i < nb; ++i) {
-    const uint32_t* r = srec + (size_t)i * rw;
+  const int px = (K == 0) ? g.kM.px : g.kD.px;
+  for (int e = 0; e < nl; ++e) {
+    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const int4 hd = reinterpret_cast<const int4*>(r)[K];
+    if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
+    int dx = gx - hd.x;
+    if (dx < 0) dx += g.nx;
+    if (dx >= px) continue;
+    int dy = gy - hd.y;
+    if (dy < 0) dy += g.ny;
     const T* tv = reinterpret_cast<const T*>(r + 8);
+    const T* ph = tv + 6 + K * stride;
+    const T wxy = ph[dx] * ph[g.pxc + dy];
+    const T f0 = tv[3 * K], f1 = tv[3 * K + 1], f2 = tv[3 * K + 2];
 #pragma unroll
-    for (int K = 0; K < NF / 3; ++K) {
-      const int4 hd = reinterpret_cast<const int4*>(r)[K];
-      const int px = (K == 0) ? g.kM.px : g.kD.px;
-      int dx = gx - hd.x; if (dx < 0) dx += g.nx;
-      int dy = gy - hd.y; if (dy < 0) dy += g.ny;
-      if (dx < px && dy < px) {
-        const T* ph = tv + 6 + K * stride;
-        const T wxy = ph[dx] * ph[g.pxc + dy];
-        const T f0 = tv[3 * K], f1 = tv[3 * K + 1], f2 = tv[3 * K + 2];
-#pragma unroll
-        for (int zz = 0; zz < ZC; ++zz) {
-          const int iz = zb + zz - hd.z;
-          if (iz >= 0 && iz < hd.w) {
-            const T w = wxy * ph[2 * g.pxc + iz];
-            acc[zz][3 * K] += f0 * w;
-            acc[zz][3 * K + 1] += f1 * w;
-            acc[zz][3 * K + 2] += f2 * w;
-          }
-        }
+    for (int zz = 0; zz < ZC; ++zz) {
+      const int iz = zb + zz - hd.z;
+      if (iz >= 0 && iz < hd.w) {
+        const T w = wxy * ph[2 * g.pxc + iz];
+        acc[zz][3 * K] += f0 * w;
+        acc[zz][3 * K + 1] += f1 * w;
+        acc[zz][3 * K + 2] += f2 * w;
       }
     }
   }
@@ -275,6 +309,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   __shared__ int s_nb;
   __shared__ int s_cand[kCandCap];
   __shared__ int s_warp[kSpreadThreads / 32];
+  __shared__ int s_wl[kSpreadThreads / 32][2][kStage];  // per-warp row lists (monopole, dipole)
   const int clo = zrange[0], chi = zrange[1];
   if (chi < clo) return;
   const int bx = blockIdx.x % g.nbx, by = blockIdx.x / g.nbx;
@@ -355,9 +390,13 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     const int ncand = min(passed, win1) - win0;
     if (ncand <= 0 && round > 0) break;
     const bool once = ncand <= kStage;
+    int nl0 = 0, nl1 = 0;
+    int* wl0 = s_wl[warp][0];
+    int* wl1 = s_wl[warp][1];
     if (once) {
       stage(0, max(ncand, 0));
       __syncthreads();
+      build_row_lists<NF>(g, srec, max(ncand, 0), rw, gy, wl0, wl1, nl0, nl1);
     }
     for (int zb = clo; zb <= chi; zb += ZC) {
       T acc[ZC][NF];
@@ -369,16 +408,21 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
           if (round > 0 && active && zb + zz <= chi) v = grid[f * fstride + (size_t)(zb + zz) * plane + node];
           acc[zz][f] = v;
         }
-      if (once) {
-        if (active) spread_batch<T, NF, ZC>(g, srec, ncand, rw, gx, gy, zb, acc);
-      } else {
+      if (!once) {
         for (int i0 = 0; i0 < ncand; i0 += kStage) {
           const int cnt = min(kStage, ncand - i0);
           __syncthreads();
           stage(i0, cnt);
           __syncthreads();
-          if (active) spread_batch<T, NF, ZC>(g, srec, cnt, rw, gx, gy, zb, acc);
+          build_row_lists<NF>(g, srec, cnt, rw, gy, wl0, wl1, nl0, nl1);
+          if (active) {
+            spread_list<T, NF, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+            if (NF == 6) spread_list<T, NF, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+          }
         }
+      } else if (active) {
+        spread_list<T, NF, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+        if (NF == 6) spread_list<T, NF, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
       }
       if (active) {
 #pragma unroll
