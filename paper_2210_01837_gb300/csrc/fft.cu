@@ -350,6 +350,8 @@ __global__ void __launch_bounds__(512, 1) row_r2c_kernel(Geometry g, FftPlan fp,
   T* raw = reinterpret_cast<T*>(smraw);  // [2][nxr] staged rows
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(raw + 2 * nxr);
   cplx<T>* b1 = b0 + pad16(nx) + 1;
+  cplx<T>* stw = b1 + pad16(nx) + 1;  // twiddle table, staged once per (persistent) block
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) stw[i] = tw[i];
   const UnitMap um(g, zrange, (g.ny + 1) / 2);
   const size_t rowlen = (size_t)2 * g.pitch;
   auto row0_of = [&](long long u, bool& has1) {
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(512, 1) row_r2c_kernel(Geometry g, FftPlan fp,
     fft_first<T, -1>(b0, fp, 0, [&](int e) { return mk<T>(raw[e], has1 ? raw[nxr + e] : (T)0); });
     __syncthreads();  // staging buffer consumed
     if (u + gridDim.x < um.total) issue(u + gridDim.x);
-    const cplx<T>* buf = fft_rest<T, -1>(b0, b1, fp, 0, tw);
+    const cplx<T>* buf = fft_rest<T, -1>(b0, b1, fp, 0, stw);
     cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
     cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row0 + rowlen);
     const T half = (T)0.5;
@@ -400,6 +402,8 @@ __global__ void __launch_bounds__(512, 1) row_c2r_kernel(Geometry g, FftPlan fp,
   cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [2][nhr] staged half spectra
   cplx<T>* b0 = raw + 2 * nhr;
   cplx<T>* b1 = b0 + pad16(nx) + 1;
+  cplx<T>* stw = b1 + pad16(nx) + 1;  // twiddle table, staged once per (persistent) block
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) stw[i] = tw[i];
   const UnitMap um(g, zrange, (g.ny + 1) / 2);
   const size_t rowlen = (size_t)2 * g.pitch;
   auto row0_of = [&](long long u, bool& has1) {
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(512, 1) row_c2r_kernel(Geometry g, FftPlan fp,
     });
     __syncthreads();
     if (u + gridDim.x < um.total) issue(u + gridDim.x);
-    const cplx<T>* buf = fft_rest<T, +1>(b0, b1, fp, 0, tw);
+    const cplx<T>* buf = fft_rest<T, +1>(b0, b1, fp, 0, stw);
     for (int a = threadIdx.x; a < nx; a += blockDim.x) {
       const cplx<T> v = buf[pad16(a)];
       row0[a] = v.x;
@@ -452,6 +456,8 @@ __global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, con
   cplx<T>* raw = reinterpret_cast<cplx<T>*>(smraw);  // [ny][cw] staged columns
   cplx<T>* b0 = raw + tot;
   cplx<T>* b1 = b0 + pad16(tot) + 1;
+  cplx<T>* stw = b1 + pad16(tot) + 1;  // twiddle table, staged once per (persistent) block
+  for (int i = threadIdx.x; i < g.ny; i += blockDim.x) stw[i] = tw[i];
   const UnitMap um(g, zrange, (kxe - kxs + cw - 1) >> lcw);
   auto base_of = [&](long long u, int& ncols) {
     int f, c, j;
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, con
     fft_first<T, DIR>(b0, fp, lcw, [&](int t) { return ((t & (cw - 1)) < ncols) ? raw[t] : mk<T>((T)0, (T)0); });
     __syncthreads();
     if (u + gridDim.x < um.total) issue(u + gridDim.x);
-    const cplx<T>* buf = fft_rest<T, DIR>(b0, b1, fp, lcw, tw);
+    const cplx<T>* buf = fft_rest<T, DIR>(b0, b1, fp, lcw, stw);
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
       const int y = t >> lcw, b = t & (cw - 1);
       if (b < ncols) base[(size_t)y * g.pitch + b] = buf[pad16(t)];
@@ -502,15 +508,18 @@ size_t padded_bytes(int n, size_t esz) { return (size_t)(n + (n >> 4) + 1) * esz
 
 template <typename T>
 size_t row_r2c_smem(const Geometry& g) {
-  return (size_t)2 * staged_len(g.nx) * sizeof(T) + 2 * padded_bytes(g.nx, sizeof(cplx<T>));
+  return (size_t)2 * staged_len(g.nx) * sizeof(T) + 2 * padded_bytes(g.nx, sizeof(cplx<T>)) +
+         (size_t)g.nx * sizeof(cplx<T>);
 }
 template <typename T>
 size_t row_c2r_smem(const Geometry& g) {
-  return (size_t)2 * ((g.nx / 2 + 2) & ~1) * sizeof(cplx<T>) + 2 * padded_bytes(g.nx, sizeof(cplx<T>));
+  return (size_t)2 * ((g.nx / 2 + 2) & ~1) * sizeof(cplx<T>) + 2 * padded_bytes(g.nx, sizeof(cplx<T>)) +
+         (size_t)g.nx * sizeof(cplx<T>);
 }
 template <typename T>
 size_t col_smem(const Geometry& g, int l) {
-  return (size_t)(g.ny << l) * sizeof(cplx<T>) + 2 * padded_bytes(g.ny << l, sizeof(cplx<T>));
+  return (size_t)(g.ny << l) * sizeof(cplx<T>) + 2 * padded_bytes(g.ny << l, sizeof(cplx<T>)) +
+         (size_t)g.ny * sizeof(cplx<T>);
 }
 
 constexpr int kFftMaxThreads = 512;
@@ -518,12 +527,12 @@ constexpr int kFftMaxThreads = 512;
 // threads for a transform of `points` values: at most kFftPer per thread, whole warps
 int fft_threads(int points) { return std::max(32, (points + kFftPer * 32 - 1) / (kFftPer * 32) * 32); }
 
-// log2 of the column block: the widest (at most 8 columns) within the thread limit whose staging
-// and work buffers fit in 160 KB of shared memory
+// log2 of the column block: the widest (at most 8 columns) within the thread limit whose staging,
+// work and twiddle buffers fit in 190 KB of shared memory
 template <typename T>
 int col_lwidth(const Plan& p) {
   for (int l = 3; l > 0; --l)
-    if (fft_threads(p.g.ny << l) <= kFftMaxThreads && col_smem<T>(p.g, l) <= 160 * 1024) return l;
+    if (fft_threads(p.g.ny << l) <= kFftMaxThreads && col_smem<T>(p.g, l) <= 190 * 1024) return l;
   return 0;
 }
 
