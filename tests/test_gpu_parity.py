@@ -43,6 +43,9 @@ CASES = [
     ("bottom_wall", 40, 54, 17, False),
     ("slit", 72, 72, 33, False),
     ("free", 72, 72, 33, False),
+    # several spreading tiles in x and y with ragged tails, 7-smooth sizes
+    ("slit", 96, 40, 33, True),
+    ("bottom_wall", 80, 32, 25, False),
 ]
 
 
@@ -123,3 +126,20 @@ def test_apply_host_matches_device_apply():
     assert np.allclose(U1.cpu().numpy(), U2, rtol=0, atol=1e-6 * np.abs(U2).max())
     assert np.allclose(W1.cpu().numpy(), W2, rtol=0, atol=1e-6 * np.abs(W2).max())
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_crowded_bin_matches_oracle(precision):
+    """200 particles inside one 32 x 8 spreading tile: the spread takes its multi-batch path (more
+    candidates than one staged batch of records)."""
+    params = small_params("bottom_wall", nx=80, ny=32, nz=17, zmax=6.0, torque=True)
+    h = params["Lx"] / params["nx"]
+    rng = np.random.default_rng(4242)
+    n = 200
+    pos = np.stack([rng.uniform(0.0, 32 * h, n), rng.uniform(0.0, 8 * h, n), rng.uniform(0.5, 3.0, n)], axis=1)
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3))
+    U_ref, W_ref = mobility(oracle_params(params), pos, F, T)
+    U, W = gpu_mobility(params, pos, F, T, precision)
+    assert rel_l2(U, U_ref) <= TOL[precision]
+    assert rel_l2(W, W_ref) <= TOL[precision]
