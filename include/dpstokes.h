@@ -216,10 +216,11 @@ dps_status dpstokes_batch_prepare(void);
 
 /* ---- Serving ------------------------------------------------------------------------------
  * No counterpart in the paper.  A server owns a worker thread, `slots` streams and a cache of
- * plans keyed by every plan parameter.  Submitted requests wait in arrival order; the worker
- * admits the oldest one whenever a slot is free and its plan is available: an idle cached plan
- * with the same key, or a new plan if the memory budget allows, after evicting least-recently-used
- * idle plans (an eviction frees device memory, which synchronises the device).  A request that can
+ * plans keyed by every plan parameter (one plan per key).  Whenever a slot is free the worker
+ * looks at the 64 oldest queued requests and admits the oldest whose plan is cached and idle,
+ * else the oldest whose key has no plan yet, creating that plan if the memory budget allows after
+ * evicting least-recently-used idle plans (an eviction frees device memory, which synchronises
+ * the device); requests whose plan is busy wait without holding up the others.  A request that can
  * never fit the budget completes with DPS_ERR_OOM.  Each admitted request copies its inputs from
  * host memory, runs the product and copies the outputs back on its slot's stream, so requests
  * overlap on the device.  Results are those of dpstokes_apply_host on a plan with the same

@@ -7,10 +7,10 @@
 // small system leaves idle.  Nothing synchronises the host and nothing allocates, so a batch can
 // be captured into a CUDA graph and replayed.
 //
-// dps server: a worker thread admits queued requests, in arrival order, to a fixed number of
-// slots (streams) as slots and device memory free up; plans are cached by their full parameter
-// key, used by one request at a time, and evicted least-recently-used when the memory budget
-// would be exceeded.  Each request copies its host inputs in, runs the product and copies the
+// dps server: a worker thread admits queued requests to a fixed number of slots (streams) as
+// slots and device memory free up, oldest first among those whose plan is available; plans are
+// cached by their full parameter key (one plan per key), used by one request at a time, and
+// evicted least-recently-used when the memory budget would be exceeded.  Each request copies its host inputs in, runs the product and copies the
 // outputs back on its slot's stream, so requests that arrive while others run overlap with them.
 #include <string.h>
 #include <time.h>
@@ -33,6 +33,7 @@ namespace {
 // stream pool of the batched apply (one per device, created on first use)
 // ---------------------------------------------------------------------------------------------
 constexpr int kBatchStreams = 8;
+constexpr size_t kAdmitWindow = 64;  // queued requests the server's admission looks at
 constexpr int kMaxDevices = 64;
 
 struct StreamPool {
@@ -164,6 +165,12 @@ struct Server {
     return nullptr;
   }
 
+  CachedPlan* find_any(const PlanKey& k) {
+    for (CachedPlan* c : cache)
+      if (c->key == k) return c;
+    return nullptr;
+  }
+
   // evict least-recently-used idle plans until `need` more bytes fit; false if they cannot
   bool make_room(int64_t need) {
     while (used + need > budget) {
@@ -252,7 +259,10 @@ struct Server {
         progress = true;
       }
       if (progress) cv_done.notify_all();
-      // admit in arrival order while a slot is free
+      // Admission, while a slot is free, over the oldest kAdmitWindow queued requests: first the
+      // oldest whose plan is cached and idle; otherwise the oldest whose key has no plan at all
+      // (created now, after evicting idle plans if the budget needs it).  A key never holds two
+      // plans, and no request waits behind another one's busy plan.
       while (!queue.empty()) {
         Slot* free_slot = nullptr;
         bool any_busy = false;
@@ -261,20 +271,28 @@ struct Server {
           else if (!free_slot) free_slot = &sl;
         }
         if (!free_slot) break;
-        Pending q = queue.front();
-        const PlanKey k = key_of(q.r);
-        CachedPlan* cp = find_free(k);
+        const size_t window = std::min<size_t>(queue.size(), kAdmitWindow);
+        size_t pick = window;
+        CachedPlan* cp = nullptr;
+        for (size_t i = 0; i < window && !cp; ++i) {
+          cp = find_free(key_of(queue[i].r));
+          if (cp) pick = i;
+        }
         if (!cp) {
+          for (size_t i = 0; i < window; ++i)
+            if (!find_any(key_of(queue[i].r))) { pick = i; break; }
+          if (pick == window) break;  // every candidate's plan is busy: wait for a completion
+          Pending q = queue[pick];
           const int64_t need = estimate_bytes(q.r);
           if (need > budget) {  // can never fit
-            queue.pop_front();
+            queue.erase(queue.begin() + pick);
             fail(q, DPS_ERR_OOM);
             cv_done.notify_all();
             continue;
           }
           if (!make_room(need)) {
             if (any_busy) break;  // wait for running requests to release plans
-            queue.pop_front();
+            queue.erase(queue.begin() + pick);
             fail(q, DPS_ERR_OOM);
             cv_done.notify_all();
             continue;
@@ -283,13 +301,13 @@ struct Server {
           const dps_status st = dpstokes_plan_create(&plan, q.r.Lx, q.r.Ly, q.r.zmin, q.r.zmax, q.r.wall_mode,
                                                      &q.r.grid, &q.r.kp);
           if (st != DPS_OK) {
-            queue.pop_front();
+            queue.erase(queue.begin() + pick);
             fail(q, st);
             cv_done.notify_all();
             continue;
           }
           cp = new CachedPlan();
-          cp->key = k;
+          cp->key = key_of(q.r);
           cp->plan = plan;
           dps_plan_info info;
           dpstokes_plan_info(plan, &info);
@@ -298,7 +316,8 @@ struct Server {
           cache.push_back(cp);
           ++created;
         }
-        queue.pop_front();
+        const Pending q = queue[pick];
+        queue.erase(queue.begin() + pick);
         cp->in_use = true;
         cp->last_use = ++clock;
         free_slot->busy = true;
