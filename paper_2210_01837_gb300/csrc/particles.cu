@@ -267,10 +267,11 @@ __device__ __forceinline__ void build_row_lists(const Geometry& g, const uint32_
   __syncwarp();
 }
 
-// Accumulate the listed candidates of kernel K into the thread's node column, planes [zb, zb + ZC).
-template <typename T, int NF, int ZC, int K>
+// Accumulate the listed candidates of kernel K into the thread's node column (the three fields of
+// that kernel), planes [zb, zb + ZC).
+template <typename T, int ZC, int K>
 __device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl, int rw,
-                                            int gx, int gy, int zb, T (&acc)[ZC][NF]) {
+                                            int gx, int gy, int zb, T (&acc)[ZC][3]) {
   const int stride = 2 * g.pxc + g.lzc;
   const int px = (K == 0) ? g.kM.px : g.kD.px;
   for (int e = 0; e < nl; ++e) {
@@ -291,9 +292,9 @@ __device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* s
       const int iz = zb + zz - hd.z;
       if (iz >= 0 && iz < hd.w) {
         const T w = wxy * ph[2 * g.pxc + iz];
-        acc[zz][3 * K] += f0 * w;
-        acc[zz][3 * K + 1] += f1 * w;
-        acc[zz][3 * K + 2] += f2 * w;
+        acc[zz][0] += f0 * w;
+        acc[zz][1] += f1 * w;
+        acc[zz][2] += f2 * w;
       }
     }
   }
@@ -398,38 +399,44 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
       __syncthreads();
       build_row_lists<NF>(g, srec, max(ncand, 0), rw, gy, wl0, wl1, nl0, nl1);
     }
-    for (int zb = clo; zb <= chi; zb += ZC) {
-      T acc[ZC][NF];
+    // one pass per kernel (monopole: force fields, dipole: torque fields), ZC planes at a time
 #pragma unroll
-      for (int zz = 0; zz < ZC; ++zz)
+    for (int K = 0; K < NF / 3; ++K) {
+      const int* wl = K == 0 ? wl0 : wl1;
+      for (int zb = clo; zb <= chi; zb += ZC) {
+        T acc[ZC][3];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          T v = (T)0;
-          if (round > 0 && active && zb + zz <= chi) v = grid[f * fstride + (size_t)(zb + zz) * plane + node];
-          acc[zz][f] = v;
-        }
-      if (!once) {
-        for (int i0 = 0; i0 < ncand; i0 += kStage) {
-          const int cnt = min(kStage, ncand - i0);
-          __syncthreads();
-          stage(i0, cnt);
-          __syncthreads();
-          build_row_lists<NF>(g, srec, cnt, rw, gy, wl0, wl1, nl0, nl1);
-          if (active) {
-            spread_list<T, NF, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
-            if (NF == 6) spread_list<T, NF, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+        for (int zz = 0; zz < ZC; ++zz)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            T v = (T)0;
+            if (round > 0 && active && zb + zz <= chi)
+              v = grid[(3 * K + f) * fstride + (size_t)(zb + zz) * plane + node];
+            acc[zz][f] = v;
           }
+        if (!once) {
+          for (int i0 = 0; i0 < ncand; i0 += kStage) {
+            const int cnt = min(kStage, ncand - i0);
+            __syncthreads();
+            stage(i0, cnt);
+            __syncthreads();
+            build_row_lists<NF>(g, srec, cnt, rw, gy, wl0, wl1, nl0, nl1);
+            if (active) {
+              if (K == 0) spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+              else spread_list<T, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+            }
+          }
+        } else if (active) {
+          if (K == 0) spread_list<T, ZC, 0>(g, srec, wl, nl0, rw, gx, gy, zb, acc);
+          else spread_list<T, ZC, 1>(g, srec, wl, nl1, rw, gx, gy, zb, acc);
         }
-      } else if (active) {
-        spread_list<T, NF, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
-        if (NF == 6) spread_list<T, NF, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
-      }
-      if (active) {
+        if (active) {
 #pragma unroll
-        for (int zz = 0; zz < ZC; ++zz) {
-          if (zb + zz <= chi) {
+          for (int zz = 0; zz < ZC; ++zz) {
+            if (zb + zz <= chi) {
 #pragma unroll
-            for (int f = 0; f < NF; ++f) grid[f * fstride + (size_t)(zb + zz) * plane + node] = acc[zz][f];
+              for (int f = 0; f < 3; ++f) grid[(3 * K + f) * fstride + (size_t)(zb + zz) * plane + node] = acc[zz][f];
+            }
           }
         }
       }
@@ -545,7 +552,7 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
   }
 }
 
-constexpr int kZC6F = 8, kZC6D = 4, kZC3F = 12, kZC3D = 6;  // z chunk: accumulators near 48 registers
+constexpr int kZC6F = 16, kZC6D = 8, kZC3F = 16, kZC3D = 8;  // z chunk of a pass: 3 fields x ZC accumulators
 
 template <typename T>
 size_t spread_smem(const Plan& p) {
