@@ -46,6 +46,9 @@ CASES = [
     # several spreading tiles in x and y with ragged tails, 7-smooth sizes
     ("slit", 96, 40, 33, True),
     ("bottom_wall", 80, 32, 25, False),
+    # odd sizes: radix-5 and radix-7 butterflies, half spectra without a Nyquist column or row
+    ("bottom_wall", 45, 35, 17, True),
+    ("slit", 63, 50, 25, False),
 ]
 
 

@@ -54,3 +54,18 @@ def test_image_only_near_wall():
     free_near = kernel.z_envelope(zc, 1.0, 1.5, 10.2, FREE, 0.0, 12.0)
     img = kernel.es(zc + 1.0, 1.5, 10.2)
     assert np.allclose(near, free_near - img, atol=1e-16)
+
+
+def test_kernel_tables_match_the_printed_tables():
+    """The oracle's Table I/II constants are the paper's printed values (tests/golden fixture)."""
+    import os
+    from oracle import table1, table2
+    path = os.path.join(os.path.dirname(__file__), "golden", "es_kernel_tables.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 5
+    for t, m, rh, bm, bd, _, _ in rows:
+        m = int(m)
+        if t == "I":
+            assert table1(m) == (float(rh), float(bm), float(bd))
+        else:
+            assert table2(m) == (float(rh), float(bm))
