@@ -49,6 +49,7 @@ CASES = [
     # odd sizes: radix-5 and radix-7 butterflies, half spectra without a Nyquist column or row
     ("bottom_wall", 45, 35, 17, True),
     ("slit", 63, 50, 25, False),
+    ("free", 64, 40, 17, False),  # 64 = 16 * 4: a radix-4 stage
 ]
 
 
