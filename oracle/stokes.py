@@ -10,6 +10,10 @@ Follows the eight steps of Sec. III.D in order, one wavenumber block at a time:
   6. correction node values -> Chebyshev coefficients (DCT-I), added to the DP coefficients;
   7. curl in Fourier-Chebyshev space, inverse DCT-I and inverse xy FFT;
   8. interpolation (transfer.interpolate).
+With torque_route='kernel_derivative' (the second torque route of Sec. III.D) step 1 adds the
+half-curl of the dipole envelope to the force density instead of spreading a torque field, step 7
+transforms the velocity only, and step 8 returns Omega with the envelope gradient
+(transfer.spread_curl, transfer.interpolate_curl).
 
 Readings where the paper is silent or ambiguous (each one is shared with the GPU path by
 construction of its own code, never by shared code):
@@ -26,7 +30,7 @@ import numpy as np
 
 from . import bvp, cheb
 from .params import BOTTOM_WALL, FREE, SLIT
-from .transfer import interpolate, spread
+from .transfer import interpolate, interpolate_curl, spread, spread_curl
 
 
 def wavenumbers(p):
@@ -273,22 +277,36 @@ def wrap_positions(p, pos):
     return pos
 
 
-def mobility(p, pos, F, T=None, return_grids=False):
+TORQUE_ROUTES = ("spectral_curl", "kernel_derivative")
+
+
+def mobility(p, pos, F, T=None, return_grids=False, torque_route="spectral_curl"):
     """The mobility product [U; Omega] = M [F; T] of Eq. 58 by steps 1-8 of Sec. III.D.
 
-    pos, F, T: (N, 3).  Returns U (N, 3) and Omega (N, 3) (None when T is None)."""
+    torque_route selects one of the two ways Sec. III.D gives for torques: 'spectral_curl' spreads
+    tau Delta^W_D and takes the half-curl of the torque field and of the velocity in
+    Fourier-Chebyshev space; 'kernel_derivative' spreads (1/2) grad Delta^W_D x tau with the force
+    density and interpolates Omega with the envelope gradient, so only the three velocity fields are
+    transformed.  pos, F, T: (N, 3).  Returns U (N, 3) and Omega (N, 3) (None when T is None)."""
+    if torque_route not in TORQUE_ROUTES:
+        raise ValueError(f"unknown torque route {torque_route!r}")
     pos = wrap_positions(p, pos)
     fgrid = spread(p, pos, F, "M")
+    derivative = T is not None and torque_route == "kernel_derivative"
+    if derivative:
+        fgrid = fgrid + spread_curl(p, pos, T)
     fcoef = to_spectral(p, fgrid[None] if fgrid.ndim == 3 else fgrid)
     tcoef = None
-    if T is not None:
+    if T is not None and not derivative:
         tgrid = spread(p, pos, T, "D")
         tcoef = to_spectral(p, tgrid)
-    vcoef, ocoef = solve_spectral(p, fcoef, tcoef, want_curl=T is not None)
+    vcoef, ocoef = solve_spectral(p, fcoef, tcoef, want_curl=T is not None and not derivative)
     ugrid = to_nodes(p, vcoef)
     U = interpolate(p, pos, ugrid, "M")
     Om = None
-    if T is not None:
+    if derivative:
+        Om = interpolate_curl(p, pos, ugrid)
+    elif T is not None:
         ogrid = to_nodes(p, ocoef)
         Om = interpolate(p, pos, ogrid, "D")
     if return_grids:
