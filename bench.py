@@ -51,10 +51,12 @@ def peaks():
 # ---------------------------------------------------------------------------------------------
 # algorithmic work per stage (bytes that must cross HBM once; FP64 flops of the banded solves)
 # ---------------------------------------------------------------------------------------------
-def algorithmic(params, n, zocc, tsize, rec_bytes):
+def algorithmic(params, n, zocc, tsize, rec_bytes, fields=6):
+    """fields: grid fields spread and transformed (6 with the spectral-curl torque route, 3 with
+    the kernel-derivative route, whose interpolation still returns U and Omega)."""
     nx, ny, nz = params["nx"], params["ny"], params["nz"]
     nkx = nx // 2 + 1
-    F = 6
+    F = fields
     real = F * zocc * ny * nx * tsize
     cpx = F * zocc * ny * nkx * 2 * tsize
     K = nkx * ny
@@ -386,6 +388,7 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=256, help="systems in the batched leg (0: skip batched and served legs)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="duration of the served leg")
+    ap.add_argument("--no-deriv", action="store_true", help="skip the kernel-derivative torque-route leg")
     args = ap.parse_args()
 
     from paper_2210_01837_gb300.replicas import Collective, rank_env, replica_seed_offset, whole_job_rate
@@ -508,6 +511,36 @@ def main():
     plan.close()
     del plan
 
+    # ---- the kernel-derivative torque route (second route of Sec. III.D), same workload --------
+    deriv = None
+    if not args.no_deriv:
+        plan_d = binding.Plan.from_params(params, with_torque="kernel_derivative", precision="mixed", max_n=n)
+        tuned_d_ms = plan_d.autotune(d_pos, d_F, d_T, U, W) if not args.no_tune else None
+        info_d = plan_d.info()
+        plan_d.enable_timing(True)
+        log_d = []
+        t_d = max_over_ranks(time_plan(plan_d, args.steps, args.warmup, log_d))
+        plan_d.enable_timing(False)
+        st_d = {k: float(np.mean([s_[k] for s_ in log_d])) for k in log_d[0]}
+        work_d = algorithmic(params, n, zocc, 4, info_d.record_words * 4, fields=3)
+        roof_d = {}
+        for k, ms in st_d.items():
+            if k in work_d:
+                gbs = work_d[k] / (ms * 1e-3) / 1e9
+                roof_d[k] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3)}
+        rl2 = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        value_d = whole_job_rate(world, args.steps, t_d)
+        deriv = {"value": value_d, "unit": "products/s", "ms_per_step": t_d / args.steps * 1e3,
+                 "speedup_vs_spectral_curl": value_d / value, "nfields": info_d.nfields,
+                 "gpu_launches": info_d.launches_per_apply * args.steps,
+                 "launch_shapes": {"autotune_ms": tuned_d_ms, "fft_col_width": info_d.fft_col_width,
+                                   "solve_blocks": info_d.solve_blocks, "wavenumber_chunks": info_d.nchunks},
+                 "stages_ms": {k: round(v, 4) for k, v in st_d.items()}, "stage_roofline": roof_d,
+                 "vs_spectral_curl_rel_l2": {"U": rl2(U, U_mixed), "Omega": rl2(W, W_mixed)},
+                 "note": "same workload and precision; the two routes differ by the kernel sampling error at m = 5"}
+        plan_d.close()
+        del plan_d
+
     # ---- all-FP64 path on the same GPU -------------------------------------------------------
     fp64 = None
     if not args.no_fp64:
@@ -548,7 +581,7 @@ def main():
                "particles_per_s": value * n, "fp64": fp64, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                "stage_roofline": stage_roof, "roofline": roofline, "e2e": e2e,
                "gpu_launches": launches_per_apply * args.steps, "clocks": clocks,
-               "batch": batch, "served": served}
+               "batch": batch, "served": served, "kernel_derivative_route": deriv}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

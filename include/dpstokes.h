@@ -52,6 +52,23 @@ typedef enum {
                      in double                                                                   */
 } dps_precision;
 
+/* how torques enter (the two routes of Sec. III.D, the paragraph after the algorithm) */
+typedef enum {
+  DPS_TORQUE_NONE = 0,              /* forces only                                                */
+  DPS_TORQUE_SPECTRAL_CURL = 1,     /* spread the torque field tau Delta^W_D, add its half-curl in
+                                       Fourier-Chebyshev space, and transform the half-curl of the
+                                       velocity back for the angular velocities: 6 fields are
+                                       spread and transformed each way (the paper's GPU route)     */
+  DPS_TORQUE_KERNEL_DERIVATIVE = 2  /* spread (1/2) grad Delta^W_D x tau with the force density and
+                                       interpolate Omega_j = (1/2) h^2 sum w_c u x grad Delta^W_D:
+                                       3 fields each way.  The kernel derivative is zero beyond the
+                                       point where |phi'| is smallest before the support edge
+                                       (beta v sqrt(1 - v) = 1, v = (t/alpha)^2, larger root); the z
+                                       derivative is the exact one of the imaged envelope.  Needs
+                                       beta_D > 3 sqrt(3) / 2.  Both routes approximate the same
+                                       operator; they differ by the kernel sampling error          */
+} dps_torque_route;
+
 typedef enum {
   DPS_OK = 0,
   DPS_ERR_INVALID_ARG = -1,   /* bad sizes or parameters, inconsistent pointer combination      */
@@ -74,7 +91,9 @@ typedef struct {
   int32_t m_D;     /* dipole support (used only with torques)                                  */
   double beta_D;   /* dipole shape parameter                                                    */
   double eta;      /* viscosity (Eq. 4), > 0                                                    */
-  int32_t with_torque;  /* 1: applies take torques and return angular velocities             */
+  int32_t with_torque;  /* dps_torque_route: 0 forces only; 1 or 2: applies take torques and
+                           return angular velocities, by the spectral curl (1) or by kernel
+                           derivatives (2)                                                     */
   int32_t precision;    /* dps_precision                                                       */
   int64_t max_n;        /* largest particle count an apply may pass                           */
 } dps_kernel_params;
@@ -82,7 +101,8 @@ typedef struct {
 /* Build a plan: validates the box, grid and kernels, builds the Chebyshev/quadrature/transform
  * tables and allocates every device buffer an apply needs (no allocation happens in apply).
  * Host-detectable errors: non-positive sizes, h_x != h_y, nz out of range, a non-smooth xy size,
- * m out of range or its envelope wider than half the box, a slit narrower than 2 alpha.
+ * m out of range or its envelope wider than half the box, a slit narrower than 2 alpha, an
+ * unknown torque route, beta_D <= 3 sqrt(3) / 2 with the kernel-derivative route.
  * The current CUDA device at the call is the plan's device.  *out is NULL on error. */
 dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zmin, double zmax,
                                 int32_t wall_mode, const dps_grid* grid,
@@ -121,7 +141,8 @@ typedef struct {
   int64_t device_bytes;     /* device memory owned by the plan                                  */
   int32_t nkx;              /* nx/2 + 1 stored wavenumbers in x                                 */
   int32_t pitch;            /* complex elements per stored grid row                             */
-  int32_t nfields;          /* 3 (forces) or 6 (forces and torques)                            */
+  int32_t nfields;          /* fields spread and transformed: 6 for the spectral-curl torque
+                               route, else 3                                                   */
   int32_t record_words;     /* 32-bit words per particle kernel record                          */
   double h;                 /* grid spacing                                                     */
   double alpha_M, alpha_D;  /* kernel supports                                                  */
@@ -167,9 +188,11 @@ dps_status dpstokes_stage_times(dps_plan_t plan, double* ms_out, int32_t capacit
  * Sec. III.D, in double precision) using only a scratch array of fixed size, 64 MiB, compiled into
  * the library as device memory; every GPU that loads the library holds that array until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
- *   - out_grid: caller-owned device buffer of nfields * nz * ny * ldx doubles (nfields = 3, or 6
- *     with torques: force fields, then torque fields), laid out [field][c][y][x] with row stride
- *     ldx (even, >= nx); it is zeroed and then receives the spread node values.
+ *   - out_grid: caller-owned device buffer of nfields * nz * ny * ldx doubles (nfields = 6 with
+ *     the spectral-curl torque route: force fields, then torque fields; else 3: the force
+ *     density, plus the half-curl of the torque envelopes with the kernel-derivative route), laid
+ *     out [field][c][y][x] with row stride ldx (even, >= nx); it is zeroed and then receives the
+ *     spread node values.
  *   - The other arguments mean what they mean in dpstokes_plan_create / dpstokes_apply;
  *     kp->precision, kp->eta and kp->max_n are ignored.
  *   - Returns DPS_ERR_INVALID_ARG when the problem needs more scratch than the fixed array holds

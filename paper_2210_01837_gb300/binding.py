@@ -14,6 +14,19 @@ from . import build as _build
 
 MODES = {"free": 0, "bottom_wall": 1, "slit": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+# dps_torque_route; with_torque also takes False (none) and True (the spectral curl)
+TORQUE_ROUTES = {"none": 0, "spectral_curl": 1, "kernel_derivative": 2}
+
+
+def torque_route(with_torque):
+    """dps_torque_route code of a with_torque argument: a bool, a route name or the code itself."""
+    if isinstance(with_torque, str):
+        return TORQUE_ROUTES[with_torque]
+    if isinstance(with_torque, bool) or with_torque in (0, 1):
+        return 1 if with_torque else 0
+    if with_torque == 2:
+        return 2
+    raise ValueError(f"unknown torque route {with_torque!r}")
 STATUS = {0: "DPS_OK", -1: "DPS_ERR_INVALID_ARG", -2: "DPS_ERR_OUT_OF_DOMAIN", -3: "DPS_ERR_OOM",
           -4: "DPS_ERR_CUDA", -5: "DPS_ERR_TIMEOUT", -6: "DPS_ERR_NONFINITE"}
 DPS_OK, DPS_ERR_INVALID_ARG, DPS_ERR_OUT_OF_DOMAIN, DPS_ERR_OOM = 0, -1, -2, -3
@@ -260,12 +273,13 @@ class Plan:
 
     def __init__(self, Lx, Ly, zmin, zmax, mode, nx, ny, nz, m_M, beta_M, m_D=0, beta_D=0.0, eta=1.0,
                  with_torque=False, precision="mixed", max_n=1):
-        self.with_torque = bool(with_torque)
+        self.route = torque_route(with_torque)
+        self.with_torque = self.route != 0
         self.precision = precision
         self.max_n = int(max_n)
         grid = dps_grid(int(nx), int(ny), int(nz))
         kp = dps_kernel_params(int(m_M), float(beta_M), int(m_D), float(beta_D), float(eta),
-                               1 if with_torque else 0, PRECISIONS[precision], int(max_n))
+                               self.route, PRECISIONS[precision], int(max_n))
         st, h = dpstokes_plan_create(float(Lx), float(Ly), float(zmin), float(zmax), MODES[mode], grid, kp)
         if st != DPS_OK:
             raise DpsError(st, "dpstokes_plan_create")
@@ -393,15 +407,16 @@ class Server:
         """params: dict as in Plan.from_params; pos/F/T host float64 [n, 3] (kept alive until wait).
         Returns a ticket; outputs land in U (and W)."""
         n = pos.shape[0]
+        route = torque_route(with_torque)
         U = np.empty((n, 3)) if U is None else U
-        W = (np.empty((n, 3)) if W is None else W) if with_torque else None
+        W = (np.empty((n, 3)) if W is None else W) if route else None
         r = dps_serve_request()
         r.Lx, r.Ly, r.zmin, r.zmax = (float(params[k]) for k in ("Lx", "Ly", "zmin", "zmax"))
         r.wall_mode = MODES[params["mode"]]
         r.grid = dps_grid(int(params["nx"]), int(params["ny"]), int(params["nz"]))
         r.kp = dps_kernel_params(int(params["m_M"]), float(params["beta_M"]), int(params.get("m_D", 0) or 0),
                                  float(params.get("beta_D", 0.0) or 0.0), float(params.get("eta", 1.0)),
-                                 1 if with_torque else 0, PRECISIONS[precision], int(max_n))
+                                 route, PRECISIONS[precision], int(max_n))
         r.n = n
         r.positions, r.forces, r.torques = _ptr(pos), _ptr(F), _ptr(T)
         r.out_vel, r.out_angvel = _ptr(U), _ptr(W)

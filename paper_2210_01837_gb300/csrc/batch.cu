@@ -146,7 +146,9 @@ struct Server {
     const int64_t ts = r.kp.precision == DPS_MIXED ? 4 : 8;
     const int64_t nx = r.grid.nx, ny = r.grid.ny, nz = r.grid.nz;
     const int64_t nkx = nx / 2 + 1, pitch = (nkx + 31) / 32 * 32, K = nkx * ny;
-    const int64_t nf = r.kp.with_torque ? 6 : 3, nk = r.kp.with_torque ? 2 : 1;
+    const int route = r.kp.with_torque;  // record slabs: M, plus D, plus D' for the derivative route
+    const int64_t nf = route == DPS_TORQUE_SPECTRAL_CURL ? 6 : 3;
+    const int64_t nk = route == DPS_TORQUE_NONE ? 1 : (route == DPS_TORQUE_KERNEL_DERIVATIVE ? 3 : 2);
     const int64_t nmax = std::max<int64_t>(r.kp.max_n, 1);
     const int64_t rec = 4 * (8 + (6 + nk * (2 * (kMaxM + 1) + nz)) * ts / 4 + 3);
     const int64_t nbins = ((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY);

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kBvpThreads) fwd_kernel(Geometry g, const T* _
   if (ki.nyq) return;
   const int clo = zrange[0], chi = zrange[1];
   const T hkx = (T)(0.5 * ki.kx), hky = (T)(0.5 * ki.ky);
-  const bool tq = g.with_torque != 0;
+  const bool tq = g.spectral_curl != 0;
   for (int o = 0; o < 3; ++o) {
     const bool use_b = tq && o < 2;
     for (int n0 = 0; n0 < N; n0 += NB) {
@@ -1130,7 +1130,7 @@ template <typename T> constexpr int fwd_nb() { return sizeof(T) == 4 ? 24 : 12; 
 template <typename T> constexpr int bwd_cb() { return sizeof(T) == 4 ? 12 : 4; }
 
 size_t fwd_smem(const Plan& p, size_t tsz) { return 2 * (size_t)p.g.nz * p.kt.npad * tsz; }
-size_t bwd_smem(const Plan& p, size_t tsz) { return (p.g.with_torque ? 3 : 1) * (size_t)p.g.nz * p.kt.cpad * tsz; }
+size_t bwd_smem(const Plan& p, size_t tsz) { return (p.g.spectral_curl ? 3 : 1) * (size_t)p.g.nz * p.kt.cpad * tsz; }
 
 // launch shape of the lane-per-wavenumber forward transform; threads = 0 when it does not apply
 struct LaneCfg {
@@ -1146,7 +1146,7 @@ LaneCfg fwd_lane_cfg(const Geometry& g) {
   constexpr int PG = fwd_pg<T>();
   const int nw = (g.nz + PG - 1) / PG;
   if (g.nz > 128 || 32 * nw > fwd_max_threads<T>()) return c;
-  const int nf = g.with_torque ? 6 : 3;
+  const int nf = g.spectral_curl ? 6 : 3;
   const size_t per_plane = (size_t)nf * kLaneK * sizeof(cplx<T>) + (size_t)2 * nw * PG * sizeof(T);
   c.threads = 32 * nw;
   c.cz = std::min(g.nz, kFwdPlanes);      // planes per pipelined chunk
@@ -1158,7 +1158,7 @@ template <typename T>
 size_t bwd_lane_smem(const Geometry& g) {
   const size_t N = (size_t)g.nz, N4 = (N + 3) & ~(size_t)3;
   const bool corr = g.mode != DPS_FREE;
-  const size_t nt = g.with_torque ? (corr ? 3 : 2) : 1;
+  const size_t nt = g.spectral_curl ? (corr ? 3 : 2) : 1;
   const size_t cz = (size_t)bwd_warps<T>() * bwd_pg<T>();
   size_t b = 2 * (3 * (size_t)kBwdRows * kLaneK * sizeof(cplx<T>) + (size_t)kBwdRows * nt * cz * sizeof(T));
   if (corr) b += 12 * kLaneK * sizeof(cplx<T>) + N * kLaneK * sizeof(T) + N4 * sizeof(T);
@@ -1237,7 +1237,7 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
   if (part == 0 && fc.threads > 0) {
     const unsigned lb = (unsigned)((total + kLaneK - 1) / kLaneK);
     constexpr int PG = fwd_pg<T>();
-    if (g.with_torque)
+    if (g.spectral_curl)
       fwd_lane_kernel<T, PG, true><<<lb, fc.threads, fc.smem, s>>>(
           g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, grid, kbuf,
           p.zrange, kx0, w, fc.cz);
@@ -1247,7 +1247,7 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
           p.zrange, kx0, w, fc.cz);
   } else if (part == 2 && bwd_lane_smem<T>(g) > 0) {
     const int corr = g.mode == DPS_FREE ? 0 : (g.mode == DPS_SLIT ? 2 : 1);
-    if (g.with_torque) {
+    if (g.spectral_curl) {
       if (corr == 0) launch_bwd_lane<T, true, 0>(p, kx0, w, s);
       else if (corr == 1) launch_bwd_lane<T, true, 1>(p, kx0, w, s);
       else launch_bwd_lane<T, true, 2>(p, kx0, w, s);
@@ -1269,7 +1269,7 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
     cplx<T>* pws = reinterpret_cast<cplx<T>*>(base + 3 * N * slots * (sizeof(cplx<double>) + sizeof(double)));
     solve_kernel<T><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT), kbuf,
                                                          kaux, pws, sw, fr, kx0, w);
-  } else if (g.with_torque) {
+  } else if (g.spectral_curl) {
     bwd_kernel<T, CB, true><<<blocks, kBvpThreads, p.kt.bwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ict), reinterpret_cast<const T*>(p.kt.icdt),
         reinterpret_cast<const T*>(p.kt.sdt), reinterpret_cast<const T*>(p.tab.zeta), p.kt.cpad, p.kt.bwd_smem > 0, kbuf,

@@ -54,6 +54,7 @@ struct EsKernel {
   double alpha;     // support half width
   double beta;      // shape
   double inv_norm;  // 1 / integral of exp(beta (sqrt(1-(t/alpha)^2) - 1)) over [-alpha, alpha]
+  double cut;       // derivative kernel: phi'(t) = 0 for |t| > cut (kernel-derivative torque route)
   int px;           // x/y node slots per particle (m + 1)
 };
 
@@ -65,15 +66,20 @@ struct Geometry {
   int nx, ny, nz;
   int nkx;           // nx/2 + 1
   int pitch;         // complex elements per stored row (>= nkx); real rows hold 2*pitch values
-  int nfields;       // 3 or 6
-  int with_torque;
+  int nfields;       // fields spread and transformed: 6 (spectral-curl torques) or 3
+  int with_torque;   // applies take torques and return angular velocities
+  int spectral_curl; // torque fields are spread; the half-curl is taken in Fourier-Chebyshev space
+  int torque_deriv;  // the half-curl of the dipole envelope is spread with the forces; Omega by
+                     // interpolation with the envelope gradient
   int nbx, nby;      // bins (spread tiles) in x and y
   int rbx, rby;      // bin radius searched around a tile
   EsKernel kM, kD;
   int pxc;           // x/y slots in a particle record (max over kernels)
   int lzc;           // z slots in a particle record
   int rec_words;     // 32-bit words per particle record
-  int nkernels;      // 1 (M) or 2 (M and D)
+  int nkernels;      // 1 (M) or 2 (M and D): record heads
+  int nslabs;        // value slabs per record: one per kernel, plus the dipole derivative slab
+  int stage_cap;     // particle records the spreading kernel stages in shared memory at a time
 };
 
 // Device tables owned by the plan
@@ -201,12 +207,20 @@ __device__ __forceinline__ double widen_bits(float f) {
 // status bits written by kernels
 enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4 };
 
+// host side of the particle stage: the ES normalisation (Eq. 54), the truncation point of the
+// derivative kernel, and the particle-side geometry (kernels, record layout, bins) shared by plans
+// and the allocation-free spread; g must hold the box, grid and wall mode.  tsize: 32-bit words
+// per stored value (1 float, 2 double).
+double es_norm(double alpha, double beta);
+double es_deriv_cut(double alpha, double beta);
+dps_status particle_geometry(Geometry& g, const dps_kernel_params* kp, int tsize);
+
 // launchers (stream-ordered, no host sync)
 template <typename T> void launch_records(const Plan& p, int64_t n, const double* pos, const double* F,
                                           const double* Tq, cudaStream_t s);
 void launch_bins(const Plan& p, int64_t n, cudaStream_t s);
 template <typename T> void launch_spread(const Plan& p, cudaStream_t s);
-template <typename T> int spread_prepare(const Plan& p);
+template <typename T> int spread_prepare(Plan& p);  // 1 ready, 0 CUDA error, -1 records too large
 template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s);
 template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s);

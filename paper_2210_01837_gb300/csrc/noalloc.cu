@@ -36,32 +36,6 @@ dps_status scratch_address(int dev, unsigned char** out) {
   return DPS_OK;
 }
 
-// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
-double es_norm_noalloc(double alpha, double beta) {
-  const int n = 128;
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) {
-    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
-    double dp = 0.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int k = 2; k <= n; ++k) {
-        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (fabs(dz) < 1e-16) break;
-    }
-    const double w = 2.0 / ((1.0 - z * z) * dp * dp);
-    const double th = 0.5 * M_PI * z;
-    s += w * exp(beta * (cos(th) - 1.0)) * cos(th);
-  }
-  return alpha * 0.5 * M_PI * s;
-}
-
 __global__ void noalloc_init_kernel(double* zc, int nz, double zmin, double H, int* zrange, int* status,
                                     int* bin_count, int nbins) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,10 +72,6 @@ extern "C" dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin,
   const bool torque = kp->with_torque != 0;
   if (n > 0 && (!positions || !forces || (torque && !torques))) return DPS_ERR_INVALID_ARG;
   if (!torque && torques) return DPS_ERR_INVALID_ARG;
-  auto bad_kernel = [&](int m, double beta) {
-    return m < 2 || m > kMaxM || !(beta > 0) || !isfinite(beta) || m + 1 > nx / 2 || m + 1 > ny / 2;
-  };
-  if (bad_kernel(kp->m_M, kp->beta_M) || (torque && bad_kernel(kp->m_D, kp->beta_D))) return DPS_ERR_INVALID_ARG;
 
   // geometry of the spreading stage, double precision, caller's row stride
   Plan p;
@@ -111,39 +81,7 @@ extern "C" dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin,
   g.h = hx; g.inv_h = 1.0 / hx; g.eta = 1.0; g.mode = wall_mode;
   g.nx = nx; g.ny = ny; g.nz = nz; g.nkx = nx / 2 + 1;
   g.pitch = (int)(ldx / 2);  // the spreading kernel writes rows of 2 * pitch values
-  g.with_torque = torque ? 1 : 0;
-  g.nfields = torque ? 6 : 3;
-  g.nkernels = torque ? 2 : 1;
-  auto setk = [&](EsKernel& k, int m, double beta) {
-    k.alpha = 0.5 * m * hx;
-    k.beta = beta;
-    k.inv_norm = 1.0 / es_norm_noalloc(k.alpha, beta);
-    k.px = m + 1;
-  };
-  setk(g.kM, kp->m_M, kp->beta_M);
-  if (torque) setk(g.kD, kp->m_D, kp->beta_D); else g.kD = g.kM;
-  const double amax = std::max(g.kM.alpha, torque ? g.kD.alpha : 0.0);
-  if (wall_mode == DPS_SLIT && g.H < 2.0 * amax) return DPS_ERR_INVALID_ARG;
-  if (wall_mode == DPS_FREE && g.H <= 2.0 * amax) return DPS_ERR_INVALID_ARG;
-  g.pxc = std::max(g.kM.px, torque ? g.kD.px : 0);
-  int best = 0;
-  for (int c = 0; c < nz; ++c) {
-    const double zc0 = zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / (nz - 1)));
-    int cnt = 0;
-    for (int q = 0; q < nz; ++q) {
-      const double zq = zmin + 0.5 * g.H * (1.0 + cos(M_PI * q / (nz - 1)));
-      if (zq <= zc0 && zq >= zc0 - 2.0 * amax * (1.0 + 1e-9) - 1e-12 * g.H) ++cnt;
-    }
-    best = std::max(best, cnt);
-  }
-  g.lzc = std::min(nz, best + 2);
-  const int tvals = 6 + g.nkernels * (2 * g.pxc + g.lzc);
-  g.rec_words = (8 + tvals * 2 + 3) / 4 * 4;
-  g.nbx = (nx + kTileX - 1) / kTileX;
-  g.nby = (ny + kTileY - 1) / kTileY;
-  g.rbx = (g.pxc + kTileX - 1) / kTileX + ((nx % kTileX) ? 1 : 0);
-  g.rby = (g.pxc + kTileY - 1) / kTileY + ((ny % kTileY) ? 1 : 0);
-  if ((2 * g.rbx + 1) * (2 * g.rby + 1) > 64) return DPS_ERR_INVALID_ARG;
+  if (particle_geometry(g, kp, 2) != DPS_OK) return DPS_ERR_INVALID_ARG;
 
   // carve the scratch: node table, plane range, status, bins, particle records
   const int nbins = g.nbx * g.nby;
@@ -185,7 +123,9 @@ extern "C" dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin,
     return DPS_ERR_CUDA;
   const int blocks = std::min(1024, std::max(nz, nbins) / 256 + 1);
   noalloc_init_kernel<<<blocks, 256, 0, s>>>(p.tab.zc, nz, zmin, g.H, p.zrange, p.status, p.bin_count, nbins);
-  if (!spread_prepare<double>(p)) return DPS_ERR_CUDA;
+  const int sp = spread_prepare<double>(p);
+  if (sp < 0) return DPS_ERR_INVALID_ARG;
+  if (sp == 0) return DPS_ERR_CUDA;
   launch_records<double>(p, n, positions, forces, torques, s);
   launch_bins(p, n, s);
   launch_spread<double>(p, s);

@@ -15,7 +15,15 @@
 // writes every node of its tile exactly once with plain stores (no atomics, no zero-fill pass).
 // Interpolation is a warp per particle: lane groups walk the x run of each (z, y) row of the
 // support, so every row is read as one contiguous segment.
+//
+// Torques take one of the two routes of Sec. III.D.  Spectral curl: the torque envelopes are spread
+// as three more fields (the half-curl is formed in Fourier-Chebyshev space).  Kernel derivative:
+// the records also hold the truncated derivative phi' of the dipole kernel in x, y and (imaged) z,
+// the spread adds (1/2) grad Delta_D x tau to the force density, and interpolation returns
+// Omega_j = (1/2) h^2 sum_g w_c u(x_g) x grad Delta_D(x_g - r_j).
 #include <math.h>
+
+#include <algorithm>
 
 #include "dps_internal.cuh"
 
@@ -41,6 +49,28 @@ __device__ __forceinline__ float es_eval_f(double t, const EsKernel& k) {
 template <typename T> __device__ __forceinline__ T es_t(double t, const EsKernel& k);
 template <> __device__ __forceinline__ double es_t<double>(double t, const EsKernel& k) { return es_eval(t, k); }
 template <> __device__ __forceinline__ float es_t<float>(double t, const EsKernel& k) { return es_eval_f(t, k); }
+
+// derivative of the ES kernel, phi'(t) = -beta t / (alpha^2 sqrt(1 - (t/alpha)^2)) phi(t), zero for
+// |t| > cut (the point where |phi'| is smallest before it blows up at the support edge)
+__device__ __forceinline__ double esd_eval(double t, const EsKernel& k) {
+  if (fabs(t) > k.cut) return 0.0;
+  const double r = t / k.alpha;
+  const double s = sqrt(1.0 - r * r);
+  return -k.beta * r / (k.alpha * s) * exp(k.beta * (s - 1.0)) * k.inv_norm;
+}
+
+__device__ __forceinline__ float esd_eval_f(double t, const EsKernel& k) {
+  // the truncation is decided in double, as on the double path: a node cut on one side and kept on
+  // the other would change a result by |phi'(cut)|, far above float rounding
+  if (fabs(t) > k.cut) return 0.0f;
+  const float r = (float)t * (float)(1.0 / k.alpha);
+  const float s = sqrtf(fmaxf(0.0f, 1.0f - r * r));
+  return -(float)(k.beta / k.alpha) * r / s * expf((float)k.beta * (s - 1.0f)) * (float)k.inv_norm;
+}
+
+template <typename T> __device__ __forceinline__ T esd_t(double t, const EsKernel& k);
+template <> __device__ __forceinline__ double esd_t<double>(double t, const EsKernel& k) { return esd_eval(t, k); }
+template <> __device__ __forceinline__ float esd_t<float>(double t, const EsKernel& k) { return esd_eval_f(t, k); }
 
 __device__ __forceinline__ int wrap_idx(int i, int n) {
   i %= n;
@@ -100,9 +130,10 @@ __global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__
     if (yw >= g.Ly) yw -= g.Ly;
     if (yw < 0.0) yw = 0.0;
   }
+  const double tscale = g.torque_deriv ? 0.5 : 1.0;  // the derivative route stores tau / 2
   for (int i = 0; i < 3; ++i) {
     tv[i] = ok ? (T)f[i] : (T)0;
-    tv[3 + i] = ok ? (T)tq[i] : (T)0;
+    tv[3 + i] = ok ? (T)(tscale * tq[i]) : (T)0;
   }
   int cmin = g.nz, cmax = -1;
   const int stride = 2 * g.pxc + g.lzc;
@@ -142,12 +173,33 @@ __global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__
         }
         ph[2 * g.pxc + i] = v;
       }
+      if (K == 1 && g.torque_deriv) {
+        // derivative slab: phi' in x and y, and d/dz of the imaged z factor (the exact derivative
+        // of the negatively imaged envelope)
+        T* pd = tv + 6 + 2 * stride;
+        for (int i = 0; i < g.pxc; ++i) {
+          pd[i] = (i < k.px) ? esd_t<T>((double)(ax + i) * g.h - xw, k) : (T)0;
+          pd[g.pxc + i] = (i < k.px) ? esd_t<T>((double)(ay + i) * g.h - yw, k) : (T)0;
+        }
+        for (int i = 0; i < g.lzc; ++i) {
+          T v = (T)0;
+          if (i < cnt) {
+            const double zz = zc[c0 + i];
+            T acc = esd_t<T>(zz - z, k);
+            if (bottom_img) acc -= esd_t<T>(zz - (2.0 * g.zmin - z), k);
+            if (top_img) acc -= esd_t<T>(zz - (2.0 * g.zmax - z), k);
+            v = acc;
+          }
+          pd[2 * g.pxc + i] = v;
+        }
+      }
       if (cnt > 0) {
         cmin = min(cmin, c0);
         cmax = max(cmax, c0 + cnt - 1);
       }
     } else {
-      for (int i = 0; i < stride; ++i) ph[i] = (T)0;
+      const int nv = (K == 1 && g.torque_deriv) ? 2 * stride : stride;  // slab K (and the derivatives)
+      for (int i = 0; i < nv; ++i) ph[i] = (T)0;
     }
     reinterpret_cast<int4*>(r)[K] = hd;
   }
@@ -232,8 +284,9 @@ constexpr int kCandCap = 2048;
 constexpr int kStage = 128;  // candidate records staged in shared memory at a time
 
 // Per warp (one tile row gy), the staged candidates whose support rows include gy, one list per
-// kernel (monopole / dipole), built with warp ballots; the z-chunk loops then walk only these.
-template <int NF>
+// kernel (monopole / dipole, the latter when TWO), built with warp ballots; the z-chunk loops then
+// walk only these.
+template <bool TWO>
 __device__ __forceinline__ void build_row_lists(const Geometry& g, const uint32_t* srec, int nrec, int rw, int gy,
                                                 int* wl0, int* wl1, int& n0, int& n1) {
   const int lane = threadIdx.x & 31;
@@ -247,7 +300,7 @@ __device__ __forceinline__ void build_row_lists(const Geometry& g, const uint32_
       int dy = gy - a.y;
       if (dy < 0) dy += g.ny;
       h0 = a.w > 0 && dy < g.kM.px;
-      if (NF == 6) {
+      if (TWO) {
         const int4 b = hd[1];
         int dy1 = gy - b.y;
         if (dy1 < 0) dy1 += g.ny;
@@ -258,7 +311,7 @@ __device__ __forceinline__ void build_row_lists(const Geometry& g, const uint32_
     const unsigned m0 = __ballot_sync(0xffffffffu, h0);
     if (h0) wl0[n0 + __popc(m0 & below)] = i;
     n0 += __popc(m0);
-    if (NF == 6) {
+    if (TWO) {
       const unsigned m1 = __ballot_sync(0xffffffffu, h1);
       if (h1) wl1[n1 + __popc(m1 & below)] = i;
       n1 += __popc(m1);
@@ -300,11 +353,54 @@ __device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* s
   }
 }
 
-template <typename T, int NF, int ZC>
+// Kernel-derivative torque route: accumulate the listed candidates' half-curl sources
+// (1/2) grad Delta_D x tau into the thread's node column (the three force-density fields), planes
+// [zb, zb + ZC).  The records hold tau / 2.  With gx = phi'x phiy phiz, gy = phix phi'y phiz and
+// gz = phix phiy phi'z, grad Delta x tau = (gy tz - gz ty, gz tx - gx tz, gx ty - gy tx).
+template <typename T, int ZC>
+__device__ __forceinline__ void spread_curl_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl,
+                                                 int rw, int gx, int gy, int zb, T (&acc)[ZC][3]) {
+  const int stride = 2 * g.pxc + g.lzc;
+  const int px = g.kD.px;
+  for (int e = 0; e < nl; ++e) {
+    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const int4 hd = reinterpret_cast<const int4*>(r)[1];
+    if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
+    int dx = gx - hd.x;
+    if (dx < 0) dx += g.nx;
+    if (dx >= px) continue;
+    int dy = gy - hd.y;
+    if (dy < 0) dy += g.ny;
+    const T* tv = reinterpret_cast<const T*>(r + 8);
+    const T* ph = tv + 6 + stride;      // dipole phi
+    const T* pd = tv + 6 + 2 * stride;  // dipole phi'
+    const T fx = ph[dx], fy = ph[g.pxc + dy];
+    const T wxy = fx * fy, bx = pd[dx] * fy, by = fx * pd[g.pxc + dy];
+    const T tx = tv[3], ty = tv[4], tz = tv[5];
+    const T a0 = by * tz, b0 = -wxy * ty;    // field 0: a0 phiz + b0 phi'z
+    const T a1 = -bx * tz, b1 = wxy * tx;    // field 1: a1 phiz + b1 phi'z
+    const T a2 = bx * ty - by * tx;          // field 2: a2 phiz
+#pragma unroll
+    for (int zz = 0; zz < ZC; ++zz) {
+      const int iz = zb + zz - hd.z;
+      if (iz >= 0 && iz < hd.w) {
+        const T pz = ph[2 * g.pxc + iz], dz = pd[2 * g.pxc + iz];
+        acc[zz][0] += a0 * pz + b0 * dz;
+        acc[zz][1] += a1 * pz + b1 * dz;
+        acc[zz][2] += a2 * pz;
+      }
+    }
+  }
+}
+
+// MODE 0: forces only (3 fields); 1: spectral-curl torques (force fields, then torque fields, one
+// pass each); 2: kernel-derivative torques (the force density and the half-curl sources in one pass
+// over the 3 fields).
+template <typename T, int MODE, int ZC>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
               const int* __restrict__ sorted, const int* __restrict__ zrange, T* __restrict__ grid) {
-  extern __shared__ __align__(16) uint32_t srec[];   // kStage staged records
+  extern __shared__ __align__(16) uint32_t srec[];   // g.stage_cap (<= kStage) staged records
   __shared__ int s_bins[64];
   __shared__ int s_pref[65];
   __shared__ int s_nb;
@@ -390,19 +486,31 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     }
     const int ncand = min(passed, win1) - win0;
     if (ncand <= 0 && round > 0) break;
-    const bool once = ncand <= kStage;
+    constexpr bool TWO = MODE != 0;
+    const bool once = ncand <= g.stage_cap;
     int nl0 = 0, nl1 = 0;
     int* wl0 = s_wl[warp][0];
     int* wl1 = s_wl[warp][1];
     if (once) {
       stage(0, max(ncand, 0));
       __syncthreads();
-      build_row_lists<NF>(g, srec, max(ncand, 0), rw, gy, wl0, wl1, nl0, nl1);
+      build_row_lists<TWO>(g, srec, max(ncand, 0), rw, gy, wl0, wl1, nl0, nl1);
     }
-    // one pass per kernel (monopole: force fields, dipole: torque fields), ZC planes at a time
+    // the candidates of list set (wl0, wl1) into the accumulators of pass K
+    auto apply = [&](int K, T (&acc)[ZC][3], int zb) {
+      if (MODE == 2) {
+        spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+        spread_curl_list<T, ZC>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+      } else if (K == 0) {
+        spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+      } else {
+        spread_list<T, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+      }
+    };
+    // one pass per field triple (spectral curl: force fields, then torque fields), ZC planes at a time
+    constexpr int NPASS = MODE == 1 ? 2 : 1;
 #pragma unroll
-    for (int K = 0; K < NF / 3; ++K) {
-      const int* wl = K == 0 ? wl0 : wl1;
+    for (int K = 0; K < NPASS; ++K) {
       for (int zb = clo; zb <= chi; zb += ZC) {
         T acc[ZC][3];
 #pragma unroll
@@ -415,20 +523,16 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
             acc[zz][f] = v;
           }
         if (!once) {
-          for (int i0 = 0; i0 < ncand; i0 += kStage) {
-            const int cnt = min(kStage, ncand - i0);
+          for (int i0 = 0; i0 < ncand; i0 += g.stage_cap) {
+            const int cnt = min(g.stage_cap, ncand - i0);
             __syncthreads();
             stage(i0, cnt);
             __syncthreads();
-            build_row_lists<NF>(g, srec, cnt, rw, gy, wl0, wl1, nl0, nl1);
-            if (active) {
-              if (K == 0) spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
-              else spread_list<T, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
-            }
+            build_row_lists<TWO>(g, srec, cnt, rw, gy, wl0, wl1, nl0, nl1);
+            if (active) apply(K, acc, zb);
           }
         } else if (active) {
-          if (K == 0) spread_list<T, ZC, 0>(g, srec, wl, nl0, rw, gx, gy, zb, acc);
-          else spread_list<T, ZC, 1>(g, srec, wl, nl1, rw, gx, gy, zb, acc);
+          apply(K, acc, zb);
         }
         if (active) {
 #pragma unroll
@@ -529,7 +633,220 @@ __global__ void __launch_bounds__(256) interp_kernel(Geometry g, int64_t n, cons
   }
 }
 
+// Kernel-derivative torque route: U_j = h^2 sum w_c u Delta_M and
+// Omega_j = (1/2) h^2 sum w_c u x grad Delta_D (records hold the dipole phi and phi' slabs), a warp
+// per particle with the row walk of interp_kernel.  FUSED (monopole and dipole supports coincide,
+// m_M = m_D): one walk reads each velocity node once for both outputs; otherwise U is gathered over
+// the monopole support first and Omega over the dipole support.
+template <typename T, int LR, bool FUSED>
+__global__ void __launch_bounds__(256) interp_curl_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec,
+                                                          const T* __restrict__ grid, const T* __restrict__ wz,
+                                                          const int* __restrict__ order, double* __restrict__ U,
+                                                          double* __restrict__ W) {
+  constexpr int NG = 32 / LR;
+  constexpr int UR = 4;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int64_t j = order[i];
+  const uint32_t* r = rec + (size_t)j * g.rec_words;
+  const T* tv = reinterpret_cast<const T*>(r + 8);
+  const int lx = lane % LR, grp = lane / LR;
+  const size_t rowlen = (size_t)2 * g.pitch;
+  const size_t plane = (size_t)g.ny * rowlen;
+  const size_t fstride = plane * g.nz;
+  const int stride = 2 * g.pxc + g.lzc;
+  const T* pm = tv + 6;               // monopole phi
+  const T* ph = tv + 6 + stride;      // dipole phi
+  const T* pd = tv + 6 + 2 * stride;  // dipole phi'
+  T a0 = 0, a1 = 0, a2 = 0;           // U sums
+  T o0 = 0, o1 = 0, o2 = 0;           // Omega sums (without the factor 1/2)
+  // walk K = 0: U over the monopole support (FUSED: skipped, done by the dipole walk);
+  // K = 1: Omega over the dipole support
+  for (int K = FUSED ? 1 : 0; K < 2; ++K) {
+    const int4 hd = reinterpret_cast<const int4*>(r)[K];
+    const int px = (K == 0) ? g.kM.px : g.kD.px;
+    const bool vx = grp < NG && lx < px;
+    int xi = hd.x + lx;
+    if (xi >= g.nx) xi -= g.nx;
+    const bool wantU = K == 0 || FUSED, wantW = K == 1;
+    const T mx = (vx && wantU) ? pm[lx] : (T)0;
+    const T fx = (vx && wantW) ? ph[lx] : (T)0, dxv = (vx && wantW) ? pd[lx] : (T)0;
+    const unsigned magic = (65536u + (unsigned)px - 1u) / (unsigned)px;  // ceil(2^16 / px)
+    const int rows = hd.w * px;
+    const T* gbase = grid + xi;
+    for (int r0 = grp; r0 < rows; r0 += NG * UR) {
+      T v0[UR], v1[UR], v2[UR], wm[UR], gxv[UR], gyv[UR], gzv[UR];
+#pragma unroll
+      for (int u = 0; u < UR; ++u) {
+        const int rr = r0 + u * NG;
+        v0[u] = v1[u] = v2[u] = wm[u] = gxv[u] = gyv[u] = gzv[u] = (T)0;
+        if (vx && rr < rows) {
+          const int iz = (int)(((unsigned)rr * magic) >> 16), iy = rr - iz * px;
+          const int c = hd.z + iz;
+          int yi = hd.y + iy;
+          if (yi >= g.ny) yi -= g.ny;
+          const T w = wz[c];
+          if (wantU) wm[u] = pm[2 * g.pxc + iz] * w * pm[g.pxc + iy] * mx;
+          if (wantW) {
+            const T pz = ph[2 * g.pxc + iz] * w, dz = pd[2 * g.pxc + iz] * w;
+            const T fy = ph[g.pxc + iy], dyv = pd[g.pxc + iy];
+            gxv[u] = dxv * fy * pz;
+            gyv[u] = fx * dyv * pz;
+            gzv[u] = fx * fy * dz;
+          }
+          const T* gp = gbase + (size_t)c * plane + (size_t)yi * rowlen;
+          v0[u] = gp[0];
+          v1[u] = gp[fstride];
+          v2[u] = gp[2 * fstride];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UR; ++u) {
+        if (wantU) {
+          a0 += v0[u] * wm[u];
+          a1 += v1[u] * wm[u];
+          a2 += v2[u] * wm[u];
+        }
+        if (wantW) {  // u x grad Delta
+          o0 += v1[u] * gzv[u] - v2[u] * gyv[u];
+          o1 += v2[u] * gxv[u] - v0[u] * gzv[u];
+          o2 += v0[u] * gyv[u] - v1[u] * gxv[u];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    o0 += __shfl_xor_sync(0xffffffffu, o0, off);
+    o1 += __shfl_xor_sync(0xffffffffu, o1, off);
+    o2 += __shfl_xor_sync(0xffffffffu, o2, off);
+  }
+  if (lane == 0) {
+    const double h2 = g.h * g.h;
+    if (sizeof(T) == 4) {  // float path: scale in float, widen on the integer pipe
+      const float h2f = (float)h2, hh = (float)(0.5 * h2);
+      U[3 * j] = widen_bits((float)a0 * h2f);
+      U[3 * j + 1] = widen_bits((float)a1 * h2f);
+      U[3 * j + 2] = widen_bits((float)a2 * h2f);
+      W[3 * j] = widen_bits((float)o0 * hh);
+      W[3 * j + 1] = widen_bits((float)o1 * hh);
+      W[3 * j + 2] = widen_bits((float)o2 * hh);
+    } else {
+      U[3 * j] = h2 * (double)a0;
+      U[3 * j + 1] = h2 * (double)a1;
+      U[3 * j + 2] = h2 * (double)a2;
+      W[3 * j] = 0.5 * h2 * (double)o0;
+      W[3 * j + 1] = 0.5 * h2 * (double)o1;
+      W[3 * j + 2] = 0.5 * h2 * (double)o2;
+    }
+  }
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// host side: kernel constants and the particle-side geometry
+// ---------------------------------------------------------------------------------------------
+
+// Integral of exp(beta (sqrt(1 - (t/alpha)^2) - 1)) over [-alpha, alpha] (the normalisation of
+// Eq. 54), by 128-point Gauss-Legendre quadrature after t = alpha sin(theta), which leaves the
+// smooth integrand alpha exp(beta (cos(theta) - 1)) cos(theta).  Nodes by Newton iteration on the
+// Legendre three-term recurrence; no heap use (the allocation-free spread calls this too).
+double es_norm(double alpha, double beta) {
+  const int n = 128;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);  // P_n'(z) from P_n = p1, P_{n-1} = p0
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    const double w = 2.0 / ((1.0 - z * z) * dp * dp);
+    const double th = 0.5 * M_PI * z;
+    s += w * exp(beta * (cos(th) - 1.0)) * cos(th);
+  }
+  return alpha * 0.5 * M_PI * s;
+}
+
+// Truncation point of the derivative kernel: with v = (t/alpha)^2, |phi'| is stationary where
+// beta v sqrt(1 - v) = 1.  The left side rises from 0 to 2/(3 sqrt 3) at v = 2/3 and falls to 0 at
+// v = 1, so for beta > 3 sqrt(3)/2 the larger root, in (2/3, 1), is the minimum of |phi'| before
+// it blows up at the support edge.  Bisection; -1 when there is no interior minimum.
+double es_deriv_cut(double alpha, double beta) {
+  if (!(beta * (2.0 / 3.0) * sqrt(1.0 / 3.0) > 1.0)) return -1.0;
+  double lo = 2.0 / 3.0, hi = 1.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-17; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (beta * mid * sqrt(1.0 - mid) - 1.0 > 0.0) lo = mid; else hi = mid;
+  }
+  return alpha * sqrt(0.5 * (lo + hi));
+}
+
+dps_status particle_geometry(Geometry& g, const dps_kernel_params* kp, int tsize) {
+  const int route = kp->with_torque;
+  if (route < DPS_TORQUE_NONE || route > DPS_TORQUE_KERNEL_DERIVATIVE) return DPS_ERR_INVALID_ARG;
+  const bool torque = route != DPS_TORQUE_NONE;
+  auto bad_kernel = [&](int m, double beta) {
+    return m < 2 || m > kMaxM || !(beta > 0) || !isfinite(beta) || m + 1 > g.nx / 2 || m + 1 > g.ny / 2;
+  };
+  if (bad_kernel(kp->m_M, kp->beta_M) || (torque && bad_kernel(kp->m_D, kp->beta_D))) return DPS_ERR_INVALID_ARG;
+  g.with_torque = torque ? 1 : 0;
+  g.spectral_curl = route == DPS_TORQUE_SPECTRAL_CURL ? 1 : 0;
+  g.torque_deriv = route == DPS_TORQUE_KERNEL_DERIVATIVE ? 1 : 0;
+  g.nfields = g.spectral_curl ? 6 : 3;
+  g.nkernels = torque ? 2 : 1;
+  g.nslabs = g.nkernels + g.torque_deriv;
+  auto setk = [&](EsKernel& k, int m, double beta) {
+    k.alpha = 0.5 * m * g.h;
+    k.beta = beta;
+    k.inv_norm = 1.0 / es_norm(k.alpha, beta);
+    k.cut = 0.0;
+    k.px = m + 1;
+  };
+  setk(g.kM, kp->m_M, kp->beta_M);
+  if (torque) setk(g.kD, kp->m_D, kp->beta_D); else g.kD = g.kM;
+  if (g.torque_deriv) {
+    g.kD.cut = es_deriv_cut(g.kD.alpha, g.kD.beta);
+    if (!(g.kD.cut > 0.0)) return DPS_ERR_INVALID_ARG;
+  }
+  const double amax = std::max(g.kM.alpha, torque ? g.kD.alpha : 0.0);
+  if (g.mode == DPS_SLIT && g.H < 2.0 * amax) return DPS_ERR_INVALID_ARG;
+  if (g.mode == DPS_FREE && g.H <= 2.0 * amax) return DPS_ERR_INVALID_ARG;
+  g.pxc = std::max(g.kM.px, torque ? g.kD.px : 0);
+  // z slots: most Chebyshev nodes inside any closed window of length 2 alpha (plus margin)
+  int best = 0;
+  for (int c = 0; c < g.nz; ++c) {
+    const double zc0 = g.zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / (g.nz - 1)));
+    int cnt = 0;
+    for (int q = 0; q < g.nz; ++q) {
+      const double zq = g.zmin + 0.5 * g.H * (1.0 + cos(M_PI * q / (g.nz - 1)));
+      if (zq <= zc0 && zq >= zc0 - 2.0 * amax * (1.0 + 1e-9) - 1e-12 * g.H) ++cnt;
+    }
+    best = std::max(best, cnt);
+  }
+  g.lzc = std::min(g.nz, best + 2);
+  const int tvals = 6 + g.nslabs * (2 * g.pxc + g.lzc);
+  g.rec_words = (8 + tvals * tsize + 3) / 4 * 4;
+  g.nbx = (g.nx + kTileX - 1) / kTileX;
+  g.nby = (g.ny + kTileY - 1) / kTileY;
+  g.rbx = (g.pxc + kTileX - 1) / kTileX + ((g.nx % kTileX) ? 1 : 0);
+  g.rby = (g.pxc + kTileY - 1) / kTileY + ((g.ny % kTileY) ? 1 : 0);
+  if ((2 * g.rbx + 1) * (2 * g.rby + 1) > 64) return DPS_ERR_INVALID_ARG;
+  return DPS_OK;
+}
 
 template <typename T>
 void launch_records(const Plan& p, int64_t n, const double* pos, const double* F, const double* Tq,
@@ -556,16 +873,28 @@ constexpr int kZC6F = 16, kZC6D = 8, kZC3F = 16, kZC3D = 8;  // z chunk of a pas
 
 template <typename T>
 size_t spread_smem(const Plan& p) {
-  return (size_t)kStage * p.g.rec_words * sizeof(uint32_t);
+  return (size_t)p.g.stage_cap * p.g.rec_words * sizeof(uint32_t);
 }
 
 // dynamic shared-memory limit of the spreading kernels, raised at plan creation (never at launch,
-// so that applies can be captured into graphs)
+// so that applies can be captured into graphs), and the records staged at a time: kStage, or fewer
+// when that many large records (wide kernels, many z slots, three slabs) would not fit.
+// 1: ready; 0: a CUDA call failed; -1: not even one record fits.
 template <typename T>
-int spread_prepare(const Plan& p) {
-  (void)p;
+int spread_prepare(Plan& p) {
   constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
-  return allow_smem(spread_kernel<T, 6, ZC6>) && allow_smem(spread_kernel<T, 3, ZC3>);
+  if (!(allow_smem(spread_kernel<T, 1, ZC6>) && allow_smem(spread_kernel<T, 0, ZC3>) &&
+        allow_smem(spread_kernel<T, 2, ZC3>)))
+    return 0;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;  // the three modes declare the same static shared arrays
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, spread_kernel<T, 1, ZC6>) != cudaSuccess)
+    return 0;
+  const long cap = ((long)optin - (long)fa.sharedSizeBytes) / ((long)p.g.rec_words * (long)sizeof(uint32_t));
+  p.g.stage_cap = (int)std::min<long>(kStage, cap);
+  return p.g.stage_cap >= 1 ? 1 : -1;
 }
 
 template <typename T>
@@ -573,12 +902,13 @@ void launch_spread(const Plan& p, cudaStream_t s) {
   const unsigned blocks = (unsigned)(p.g.nbx * p.g.nby);
   constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
   const size_t sm = spread_smem<T>(p);
-  if (p.g.nfields == 6)
-    spread_kernel<T, 6, ZC6><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
-                                                                reinterpret_cast<T*>(p.grid));
+  T* grid = reinterpret_cast<T*>(p.grid);
+  if (p.g.spectral_curl)
+    spread_kernel<T, 1, ZC6><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
+  else if (p.g.torque_deriv)
+    spread_kernel<T, 2, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
   else
-    spread_kernel<T, 3, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
-                                                                reinterpret_cast<T*>(p.grid));
+    spread_kernel<T, 0, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
 }
 
 template <typename T>
@@ -589,6 +919,20 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
   const T* grid = reinterpret_cast<const T*>(p.grid);
   const T* wz = reinterpret_cast<const T*>(p.tab.wz);
   // lanes per x run: the narrowest group that holds a support row
+  if (p.g.torque_deriv) {
+    const bool fused = p.g.kM.px == p.g.kD.px;  // equal m: identical supports (alpha = m h / 2)
+    if (p.g.pxc <= 6) {
+      if (fused) interp_curl_kernel<T, 6, true><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+      else interp_curl_kernel<T, 6, false><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+    } else if (p.g.pxc <= 8) {
+      if (fused) interp_curl_kernel<T, 8, true><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+      else interp_curl_kernel<T, 8, false><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+    } else {
+      if (fused) interp_curl_kernel<T, 16, true><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+      else interp_curl_kernel<T, 16, false><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+    }
+    return;
+  }
   if (p.g.pxc <= 6)
     interp_kernel<T, 6><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
   else if (p.g.pxc <= 8)
@@ -600,8 +944,8 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
 template void launch_records<float>(const Plan&, int64_t, const double*, const double*, const double*, cudaStream_t);
 template void launch_records<double>(const Plan&, int64_t, const double*, const double*, const double*, cudaStream_t);
 template void launch_spread<float>(const Plan&, cudaStream_t);
-template int spread_prepare<float>(const Plan&);
-template int spread_prepare<double>(const Plan&);
+template int spread_prepare<float>(Plan&);
+template int spread_prepare<double>(Plan&);
 template void launch_spread<double>(const Plan&, cudaStream_t);
 template void launch_interp<float>(const Plan&, int64_t, double*, double*, cudaStream_t);
 template void launch_interp<double>(const Plan&, int64_t, double*, double*, cudaStream_t);

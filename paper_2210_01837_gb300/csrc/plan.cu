@@ -13,44 +13,6 @@
 namespace dps {
 namespace {
 
-// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n (three-term recurrence).
-void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(n, 0.0);
-  w.assign(n, 0.0);
-  for (int i = 0; i < (n + 1) / 2; ++i) {
-    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
-    double dp = 0.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int k = 2; k <= n; ++k) {
-        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      // p1 = P_n(z), p0 = P_{n-1}(z)
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (fabs(dz) < 1e-16) break;
-    }
-    x[i] = -z;
-    x[n - 1 - i] = z;
-    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
-  }
-}
-
-// integral of exp(beta (sqrt(1 - (t/alpha)^2) - 1)) over [-alpha, alpha]; t = alpha sin(theta)
-double es_norm(double alpha, double beta) {
-  std::vector<double> x, w;
-  gauss_legendre(128, x, w);
-  double s = 0.0;
-  for (size_t i = 0; i < x.size(); ++i) {
-    const double th = 0.5 * M_PI * x[i];
-    s += w[i] * exp(beta * (cos(th) - 1.0)) * cos(th);
-  }
-  return alpha * 0.5 * M_PI * s;
-}
-
 bool smooth_7(int n) {
   if (n < 1) return false;
   for (int p : {2, 3, 5, 7})
@@ -288,7 +250,9 @@ dps_status allocate(Plan* p) {
   if (!alloc((void**)&p->stage_in, nmax * 9 * sizeof(double))) return DPS_ERR_OOM;
   if (!alloc((void**)&p->stage_out, nmax * 6 * sizeof(double))) return DPS_ERR_OOM;
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
-  if (!spread_prepare<T>(*p)) return DPS_ERR_CUDA;
+  const int sp = spread_prepare<T>(*p);
+  if (sp < 0) return DPS_ERR_INVALID_ARG;
+  if (sp == 0) return DPS_ERR_CUDA;
   // column chunks of the wavenumber-space pipeline (multiples of 32 columns, ~192 wide)
   // one chunk by default: measured on GB300, co-running the FP64 solve with the float transforms
   // slowed both (they compete for issue slots); DPS_CHUNKS in the environment or the autotuner may
@@ -429,12 +393,15 @@ dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zm
   if (kp->precision != DPS_FP64 && kp->precision != DPS_MIXED) return DPS_ERR_INVALID_ARG;
   if (kp->max_n < 0 || kp->max_n > (int64_t)1 << 30) return DPS_ERR_INVALID_ARG;
   if (!(kp->eta > 0) || !isfinite(kp->eta)) return DPS_ERR_INVALID_ARG;
-  const bool torque = kp->with_torque != 0;
-  auto bad_kernel = [&](int m, double beta) {
-    return m < 2 || m > dps::kMaxM || !(beta > 0) || !isfinite(beta) || m + 1 > nx / 2 || m + 1 > ny / 2;
-  };
-  if (bad_kernel(kp->m_M, kp->beta_M)) return DPS_ERR_INVALID_ARG;
-  if (torque && bad_kernel(kp->m_D, kp->beta_D)) return DPS_ERR_INVALID_ARG;
+  dps::Geometry g;
+  memset(&g, 0, sizeof(g));
+  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin;
+  g.h = hx; g.inv_h = 1.0 / hx; g.eta = kp->eta; g.mode = wall_mode;
+  g.nx = nx; g.ny = ny; g.nz = nz; g.nkx = nx / 2 + 1;
+  g.pitch = (g.nkx + 31) / 32 * 32;
+  // kernels, torque route, particle records and bins
+  const int tsize = (kp->precision == DPS_FP64) ? 2 : 1;  // 32-bit words per stored value
+  if (dps::particle_geometry(g, kp, tsize) != DPS_OK) return DPS_ERR_INVALID_ARG;
 
   Plan* p = new (std::nothrow) Plan();
   if (!p) return DPS_ERR_OOM;
@@ -442,48 +409,7 @@ dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zm
   cudaGetDevice(&p->device);
   p->precision = kp->precision;
   p->max_n = kp->max_n;
-  dps::Geometry& g = p->g;
-  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin;
-  g.h = hx; g.inv_h = 1.0 / hx; g.eta = kp->eta; g.mode = wall_mode;
-  g.nx = nx; g.ny = ny; g.nz = nz; g.nkx = nx / 2 + 1;
-  g.pitch = (g.nkx + 31) / 32 * 32;
-  g.with_torque = torque ? 1 : 0;
-  g.nfields = torque ? 6 : 3;
-  g.nkernels = torque ? 2 : 1;
-  auto setk = [&](dps::EsKernel& k, int m, double beta) {
-    k.alpha = 0.5 * m * hx;
-    k.beta = beta;
-    k.inv_norm = 1.0 / dps::es_norm(k.alpha, beta);
-    k.px = m + 1;
-  };
-  setk(g.kM, kp->m_M, kp->beta_M);
-  if (torque) setk(g.kD, kp->m_D, kp->beta_D); else g.kD = g.kM;
-  const double amax = std::max(g.kM.alpha, torque ? g.kD.alpha : 0.0);
-  if (wall_mode == DPS_SLIT && g.H < 2.0 * amax) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
-  if (wall_mode == DPS_FREE && g.H <= 2.0 * amax) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
-  g.pxc = std::max(g.kM.px, torque ? g.kD.px : 0);
-  // z slots: most Chebyshev nodes inside any closed window of length 2 alpha (plus margin)
-  {
-    int best = 0;
-    for (int c = 0; c < nz; ++c) {
-      const double zc0 = zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / (nz - 1)));
-      int cnt = 0;
-      for (int q = 0; q < nz; ++q) {
-        const double zq = zmin + 0.5 * g.H * (1.0 + cos(M_PI * q / (nz - 1)));
-        if (zq <= zc0 && zq >= zc0 - 2.0 * amax * (1.0 + 1e-9) - 1e-12 * g.H) ++cnt;
-      }
-      best = std::max(best, cnt);
-    }
-    g.lzc = std::min(nz, best + 2);
-  }
-  const int tsize = (p->precision == DPS_FP64) ? 2 : 1;  // 32-bit words per stored value
-  const int tvals = 6 + g.nkernels * (2 * g.pxc + g.lzc);
-  g.rec_words = (8 + tvals * tsize + 3) / 4 * 4;
-  g.nbx = (nx + dps::kTileX - 1) / dps::kTileX;
-  g.nby = (ny + dps::kTileY - 1) / dps::kTileY;
-  g.rbx = (g.pxc + dps::kTileX - 1) / dps::kTileX + ((nx % dps::kTileX) ? 1 : 0);
-  g.rby = (g.pxc + dps::kTileY - 1) / dps::kTileY + ((ny % dps::kTileY) ? 1 : 0);
-  if ((2 * g.rbx + 1) * (2 * g.rby + 1) > 64) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
+  p->g = g;
   if (!dps::fft_plan(nx, p->fx) || !dps::fft_plan(ny, p->fy)) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
   dps_status st = (p->precision == DPS_MIXED) ? dps::build_tables<float>(p) : dps::build_tables<double>(p);
   if (st == DPS_OK) st = (p->precision == DPS_MIXED) ? dps::allocate<float>(p) : dps::allocate<double>(p);

@@ -31,11 +31,11 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
-def gpu_mobility(params, pos, F, T, precision, plan=None):
+def gpu_mobility(params, pos, F, T, precision, plan=None, route="spectral_curl"):
     import torch
     close = plan is None
     if plan is None:
-        plan = binding.Plan.from_params(params, with_torque=T is not None, precision=precision,
+        plan = binding.Plan.from_params(params, with_torque=route if T is not None else False, precision=precision,
                                         max_n=max(1, len(pos)))
     U, W = plan.apply(to_dev(pos), to_dev(F), None if T is None else to_dev(T), check=True)
     torch.cuda.synchronize()

@@ -64,6 +64,9 @@ def _create(**over):
     dict(nx=7), dict(nx=11 * 8), dict(nz=4), dict(nz=300), dict(Ly=65.0), dict(zmax=-1.0), dict(mode=3),
     dict(m_M=1), dict(m_M=13), dict(beta_M=0.0), dict(eta=0.0), dict(precision=2), dict(max_n=-1),
     dict(with_torque=1, m_D=0), dict(mode=2, zmax=1.0), dict(Lx=float("nan")),
+    dict(with_torque=3, m_D=6, beta_D=13.3), dict(with_torque=-1),
+    # the kernel-derivative route needs beta_D > 3 sqrt(3) / 2 (an interior minimum of |phi'|)
+    dict(with_torque=2, m_D=6, beta_D=2.5),
 ])
 def test_invalid_plan_arguments_rejected_on_host(lib, over):
     from paper_2210_01837_gb300 import binding

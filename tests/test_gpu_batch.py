@@ -16,25 +16,26 @@ pytestmark = pytest.mark.gpu
 
 BAR = {"fp64": 1e-12, "mixed": 1e-6}
 
-# (mode, nx, ny, nz, torque, precision, n, seed)
+# (mode, nx, ny, nz, torque route (False: forces only, True: spectral curl), precision, n, seed)
 PROBLEMS = [
     ("bottom_wall", 48, 48, 33, True, "fp64", 120, 11),
     ("slit", 40, 56, 25, False, "mixed", 200, 12),
     ("free", 54, 36, 17, True, "mixed", 80, 13),
     ("bottom_wall", 72, 40, 33, False, "fp64", 150, 14),
     ("slit", 36, 36, 33, True, "mixed", 60, 15),
+    ("bottom_wall", 40, 48, 25, "kernel_derivative", "mixed", 90, 16),
 ]
 
 
 def _problem(mode, nx, ny, nz, torque, precision, n, seed):
-    params = small_params(mode, nx=nx, ny=ny, nz=nz, zmax=8.0 if mode != "slit" else 6.0, torque=torque)
-    pos, F, T = random_particles(params, n, seed, torques=torque)
+    params = small_params(mode, nx=nx, ny=ny, nz=nz, zmax=8.0 if mode != "slit" else 6.0, torque=bool(torque))
+    pos, F, T = random_particles(params, n, seed, torques=bool(torque))
     return params, pos, F, T if torque else None
 
 
-def _alone(params, pos, F, T, precision, sizes=None):
+def _alone(params, pos, F, T, precision, route, sizes=None):
     import torch
-    plan = binding.Plan.from_params(params, with_torque=T is not None, precision=precision, max_n=len(pos))
+    plan = binding.Plan.from_params(params, with_torque=route, precision=precision, max_n=len(pos))
     U, W = plan.apply(to_dev(pos), to_dev(F), None if T is None else to_dev(T), check=True)
     torch.cuda.synchronize()
     out = (U.cpu().numpy(), None if W is None else W.cpu().numpy())
@@ -53,10 +54,10 @@ def _check(got, want, precision):
 def test_batch_matches_single_applies_and_reports_status():
     import torch
     probs = [_problem(*p) for p in PROBLEMS]
-    alone = [_alone(pa, pos, F, T, p[5]) for p, (pa, pos, F, T) in zip(PROBLEMS, probs)]
+    alone = [_alone(pa, pos, F, T, p[5], p[4]) for p, (pa, pos, F, T) in zip(PROBLEMS, probs)]
     plans, items, outs = [], [], []
     for p, (pa, pos, F, T) in zip(PROBLEMS, probs):
-        plan = binding.Plan.from_params(pa, with_torque=T is not None, precision=p[5], max_n=len(pos))
+        plan = binding.Plan.from_params(pa, with_torque=p[4], precision=p[5], max_n=len(pos))
         plans.append(plan)
         U = torch.empty((len(pos), 3), dtype=torch.float64, device="cuda")
         W = torch.empty_like(U) if T is not None else None
@@ -85,9 +86,9 @@ def test_batch_same_plan_twice_runs_in_order():
     import torch
     pa, pos, F, T = _problem(*PROBLEMS[0])
     plan = binding.Plan.from_params(pa, with_torque=True, precision="fp64", max_n=len(pos))
-    want1 = _alone(pa, pos, F, T, "fp64")
+    want1 = _alone(pa, pos, F, T, "fp64", True)
     F2 = -2.0 * F
-    want2 = _alone(pa, pos, F2, T, "fp64")
+    want2 = _alone(pa, pos, F2, T, "fp64", True)
     U1, W1, U2, W2 = (torch.empty((len(pos), 3), dtype=torch.float64, device="cuda") for _ in range(4))
     binding.apply_batch([(plan, to_dev(pos), to_dev(F), to_dev(T), U1, W1),
                          (plan, to_dev(pos), to_dev(F2), to_dev(T), U2, W2)])
@@ -103,7 +104,7 @@ def test_batch_captured_in_a_cuda_graph_and_replayed():
     binding.dpstokes_batch_prepare()
     plans, items, outs, ins = [], [], [], []
     for p, (pa, pos, F, T) in zip(PROBLEMS[:3], probs):
-        plan = binding.Plan.from_params(pa, with_torque=T is not None, precision=p[5], max_n=len(pos))
+        plan = binding.Plan.from_params(pa, with_torque=p[4], precision=p[5], max_n=len(pos))
         plans.append(plan)
         dpos, dF, dT = to_dev(pos), to_dev(F), None if T is None else to_dev(T)
         U = torch.empty((len(pos), 3), dtype=torch.float64, device="cuda")
@@ -128,7 +129,7 @@ def test_batch_captured_in_a_cuda_graph_and_replayed():
         graph.replay()
         torch.cuda.synchronize()
         for p, (pa, pos, F, T), (U, W) in zip(PROBLEMS[:3], probs, outs):
-            want = _alone(pa, pos, scale * F, T, p[5])
+            want = _alone(pa, pos, scale * F, T, p[5], p[4])
             _check((U.cpu().numpy(), None if W is None else W.cpu().numpy()), want, p[5])
     del graph
     for plan in plans:
@@ -144,7 +145,7 @@ def _pinned(a):
 def test_server_results_equal_single_applies_and_evicts_under_budget():
     probs = [_problem(*p) for p in PROBLEMS]
     sizes = []
-    alone = [_alone(pa, pos, F, T, p[5], sizes) for p, (pa, pos, F, T) in zip(PROBLEMS, probs)]
+    alone = [_alone(pa, pos, F, T, p[5], p[4], sizes) for p, (pa, pos, F, T) in zip(PROBLEMS, probs)]
     # budget for about two of these plans at a time: every request still completes, plans are
     # evicted and recreated, and the results do not depend on what ran beside them
     budget = int(2.5 * max(sizes))
@@ -152,7 +153,7 @@ def test_server_results_equal_single_applies_and_evicts_under_budget():
     tickets = []
     for rep in range(3):
         for k, (p, (pa, pos, F, T)) in enumerate(zip(PROBLEMS, probs)):
-            t = srv.submit(pa, with_torque=T is not None, precision=p[5], max_n=len(pos), pos=_pinned(pos),
+            t = srv.submit(pa, with_torque=p[4], precision=p[5], max_n=len(pos), pos=_pinned(pos),
                            F=_pinned(F), T=None if T is None else _pinned(T))
             tickets.append((k, t))
     for k, t in tickets:

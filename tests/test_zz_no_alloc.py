@@ -28,13 +28,14 @@ def _lib():
     binding.load()
 
 
-def _noalloc(params, pos, F, T, ldx):
+def _noalloc(params, pos, F, T, ldx, route):
     import torch
-    nf = 6 if T is not None else 3
+    code = binding.torque_route(route)
+    nf = 6 if code == 1 else 3
     out = torch.full((nf, params["nz"], params["ny"], ldx), float("nan"), dtype=torch.float64, device="cuda")
     grid = binding.dps_grid(params["nx"], params["ny"], params["nz"])
     kp = binding.dps_kernel_params(params["m_M"], params["beta_M"], params["m_D"], params["beta_D"], 1.0,
-                                   1 if T is not None else 0, binding.PRECISIONS["fp64"], len(pos))
+                                   code, binding.PRECISIONS["fp64"], len(pos))
     d_pos, d_F = to_dev(pos), to_dev(F)
     d_T = to_dev(T) if T is not None else None
     st = binding.dpstokes_spread_noalloc(params["Lx"], params["Ly"], params["zmin"], params["zmax"],
@@ -46,17 +47,19 @@ def _noalloc(params, pos, F, T, ldx):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode,torque", [("slit", True), ("bottom_wall", False)])
-def test_noalloc_spread_matches_plan_spread_twice(mode, torque):
+@pytest.mark.parametrize("mode,route", [("slit", "spectral_curl"), ("bottom_wall", "none"),
+                                        ("bottom_wall", "kernel_derivative")])
+def test_noalloc_spread_matches_plan_spread_twice(mode, route):
+    torque = route != "none"
     params = small_params(mode, nx=72, ny=40, nz=33, torque=torque)
-    plan = binding.Plan.from_params(params, with_torque=torque, precision="fp64", max_n=64)
+    plan = binding.Plan.from_params(params, with_torque=route, precision="fp64", max_n=64)
     ldx = 2 * plan.info().pitch
     for call, seed in enumerate((21, 22)):
         pos, F, T = random_particles(params, 40 + 7 * call, seed=seed, torques=torque)
         plan.debug_run(to_dev(pos), to_dev(F), to_dev(T) if torque else None, last_stage=2)
         ref, _ = read_grid(plan, params, "fp64")
         clo, chi = zrange(plan)
-        got = _noalloc(params, pos, F, T, ldx)
+        got = _noalloc(params, pos, F, T, ldx, route)
         assert not np.isnan(got).any()
         nx = params["nx"]
         want = ref[:, clo:chi + 1, :, :nx]
