@@ -389,6 +389,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="duration of the served leg")
     ap.add_argument("--no-deriv", action="store_true", help="skip the kernel-derivative torque-route leg")
+    ap.add_argument("--no-lanczos", action="store_true", help="skip the Brownian-increment (Lanczos) leg")
     args = ap.parse_args()
 
     from paper_2210_01837_gb300.replicas import Collective, rank_env, replica_seed_offset, whole_job_rate
@@ -541,6 +542,38 @@ def main():
         plan_d.close()
         del plan_d
 
+    # ---- Brownian increments g = M^{1/2} W by Lanczos (Sec. IV.C) on the paper's layer ---------
+    lanczos = None
+    if not args.no_lanczos:
+        from paper_2210_01837_gb300.workloads import lanczos_layer
+        reps = max(1, 8 // div)
+        lp, lpos, lW = lanczos_layer(reps, seed_offset=5 + rank)
+        lplan = binding.Plan.from_params(lp, with_torque=False, precision="mixed", max_n=len(lpos))
+        lz = binding.Lanczos(lplan, max_iter=40)
+        d_lpos, d_lW = tdev(lpos), tdev(lW.ravel())
+        for _ in range(2):
+            g_l, it_l, hist_l = lz.sample(d_lpos, d_lW, tol=1e-3)
+        k_l = max(1, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(k_l):
+            g_l, it_l, hist_l = lz.sample(d_lpos, d_lW, tol=1e-3)
+        torch.cuda.synchronize(dev)
+        t_l = max_over_ranks(time.perf_counter() - t0)
+        lplan.enable_timing(True)
+        lplan.apply(d_lpos, tdev(lW), None)
+        t_prod = sum(lplan.stage_times().values())
+        lplan.enable_timing(False)
+        lanczos = {"value": whole_job_rate(world, k_l, t_l), "unit": "samples/s", "ms_per_sample": t_l / k_l * 1e3,
+                   "iterations": it_l, "eps_history": [float(f"{e:.3e}") for e in hist_l], "tol": 1e-3,
+                   "n": len(lpos), "product_kernel_ms": round(t_prod, 4),
+                   "workload": f"lanczos_layer reps={reps}: {len(lpos)} non-overlapping spheres in two layers above "
+                               f"one wall, H = 7.5 R_h, grid {lp['nx']}^2 x {lp['nz']}, m = 4, forces only, mixed",
+                   "timing": "host clock around whole samples (one synchronisation per iteration)"}
+        lz.close()
+        lplan.close()
+
     # ---- all-FP64 path on the same GPU -------------------------------------------------------
     fp64 = None
     if not args.no_fp64:
@@ -581,7 +614,7 @@ def main():
                "particles_per_s": value * n, "fp64": fp64, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                "stage_roofline": stage_roof, "roofline": roofline, "e2e": e2e,
                "gpu_launches": launches_per_apply * args.steps, "clocks": clocks,
-               "batch": batch, "served": served, "kernel_derivative_route": deriv}
+               "batch": batch, "served": served, "kernel_derivative_route": deriv, "lanczos": lanczos}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

@@ -295,6 +295,39 @@ dps_status dpstokes_server_stats(dps_server_t server, dps_server_stats* out);
 /* Finish every queued and running request, then free the slots and all cached plans. */
 void dpstokes_server_destroy(dps_server_t server);
 
+/* ---- Brownian increments ------------------------------------------------------------------
+ * g = M^{1/2} w by the Lanczos process in the Krylov subspace of the mobility (Sec. IV.C), with the
+ * plan's product as the operator.  Vectors have dimension d = 3n for a plan without torques
+ * (layout [n][3]) and d = 6n with torques ([n][3] force part, then [n][3] torque part; the result
+ * likewise: velocities, then angular velocities).  Each iteration applies the product once and
+ * re-orthogonalises against the whole basis (two classical Gram-Schmidt passes); the host forms
+ * T_j^{1/2} e_1 of the tridiagonal Lanczos matrix (Jacobi eigendecomposition; eigenvalues below
+ * zero take a zero root) and eps_j = ||g_j - g_{j-1}|| / ||g_{j-1}||.  The process stops at the
+ * first j >= 2 with eps_j <= tol, when the Krylov space is exhausted (beta_j = 0), or after
+ * max_iter products. */
+typedef struct dps_lanczos_s* dps_lanczos_t;
+
+/* Basis storage for up to max_iter vectors of dimension 6 max_n (or 3 max_n) of `plan` on the
+ * plan's device; 2 <= max_iter <= 128.  The plan must outlive the handle. */
+dps_status dpstokes_lanczos_create(dps_lanczos_t* out, dps_plan_t plan, int32_t max_iter);
+
+/* positions: device [n][3]; w, g: device [d] (w is the caller's i.i.d. standard normal vector and
+ * is not modified; g receives the increment); 0 <= n <= max_n; tol >= 0.  iters, eps (NULL or host
+ * scalars): products applied and the last eps_j (0 before the second iteration); eps_hist (NULL or
+ * host array of max_iter doubles): eps_2, eps_3, ... .  Runs on `stream` and synchronises it once
+ * per iteration (not graph-capturable); returns the device status of the products (as
+ * dpstokes_status) or a host error.  The handle's buffers serve one call at a time. */
+dps_status dpstokes_lanczos_sample(dps_lanczos_t lz, int64_t n, const double* positions, const double* w,
+                                   double* g, double tol, int32_t* iters, double* eps, double* eps_hist,
+                                   void* stream);
+
+void dpstokes_lanczos_destroy(dps_lanczos_t lz);
+
+/* Host utility (no GPU): y = T^{1/2} e_1 for the symmetric tridiagonal T with diagonal alpha[j] and
+ * off-diagonal beta[j-1] (beta may be NULL for j = 1), 1 <= j <= 128; the step the sampler takes on
+ * the host each iteration. */
+dps_status dpstokes_tridiag_sqrt_e1(int32_t j, const double* alpha, const double* beta, double* y);
+
 /* Diagnostics for tests: run the apply pipeline on `stream` up to and including stage
  * `last_stage` (1 = particle records, 2 = spread, 3 = forward xy FFT, 4 = per-k solve,
  * 5 = inverse xy FFT, 6 = interpolation; the outputs may be NULL below stage 6) and copy plan buffer `which` (0 = grid/spectrum,

@@ -124,6 +124,11 @@ def load(path=None):
         "dpstokes_server_wait": (_I32, [_P, _I64, _D, ctypes.POINTER(dps_serve_result)]),
         "dpstokes_server_stats": (_I32, [_P, ctypes.POINTER(dps_server_stats)]),
         "dpstokes_server_destroy": (None, [_P]),
+        "dpstokes_lanczos_create": (_I32, [ctypes.POINTER(_P), _P, _I32]),
+        "dpstokes_lanczos_sample": (_I32, [_P, _I64, _P, _P, _P, _D, ctypes.POINTER(_I32), ctypes.POINTER(_D),
+                                           ctypes.POINTER(_D), _P]),
+        "dpstokes_lanczos_destroy": (None, [_P]),
+        "dpstokes_tridiag_sqrt_e1": (_I32, [_I32, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -451,3 +456,64 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---- Brownian increments (Lanczos) -----------------------------------------------------------
+def dpstokes_lanczos_create(plan, max_iter):
+    h = _P()
+    st = load().dpstokes_lanczos_create(ctypes.byref(h), plan, int(max_iter))
+    return st, h
+
+
+def dpstokes_lanczos_sample(lz, n, positions, w, g, tol, stream, max_iter):
+    """Returns (status, iterations, last eps, eps history as a list)."""
+    it = _I32(0)
+    eps = _D(0.0)
+    hist = (_D * max(1, int(max_iter)))()
+    st = load().dpstokes_lanczos_sample(lz, int(n), positions, w, g, float(tol), ctypes.byref(it), ctypes.byref(eps),
+                                        hist, stream)
+    return st, it.value, eps.value, [hist[i] for i in range(max(0, it.value - 1))]
+
+
+def dpstokes_lanczos_destroy(lz):
+    load().dpstokes_lanczos_destroy(lz)
+
+
+def dpstokes_tridiag_sqrt_e1(alpha, beta):
+    """y = T^{1/2} e_1 of the symmetric tridiagonal (alpha, beta), computed by the library (host)."""
+    j = len(alpha)
+    a = (_D * j)(*[float(x) for x in alpha])
+    b = (_D * max(1, j - 1))(*[float(x) for x in beta[: j - 1]] if j > 1 else [0.0])
+    y = (_D * j)()
+    st = load().dpstokes_tridiag_sqrt_e1(j, a, b, y)
+    return st, [y[i] for i in range(j)]
+
+
+class Lanczos:
+    """Brownian increments g ~ M^{1/2} w with a plan's mobility product as the operator."""
+
+    def __init__(self, plan, max_iter=32):
+        st, h = dpstokes_lanczos_create(plan.handle, max_iter)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_lanczos_create")
+        self.handle = h
+        self.plan = plan
+        self.max_iter = int(max_iter)
+
+    def sample(self, pos, w, g=None, tol=1e-3, stream=None):
+        """pos: CUDA float64 [n, 3]; w: CUDA float64 of 3n (or 6n with torques) values.  Returns
+        (g, iterations, eps history)."""
+        import torch
+        n = pos.shape[0]
+        if g is None:
+            g = torch.empty_like(w)
+        st, it, _, hist = dpstokes_lanczos_sample(self.handle, n, _ptr(pos), _ptr(w), _ptr(g), tol, _stream(stream),
+                                                  self.max_iter)
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_lanczos_sample")
+        return g, it, hist
+
+    def close(self):
+        if self.handle:
+            dpstokes_lanczos_destroy(self.handle)
+            self.handle = None

@@ -56,6 +56,9 @@ struct EsKernel {
   double inv_norm;  // 1 / integral of exp(beta (sqrt(1-(t/alpha)^2) - 1)) over [-alpha, alpha]
   double cut;       // derivative kernel: phi'(t) = 0 for |t| > cut (kernel-derivative torque route)
   int px;           // x/y node slots per particle (m + 1)
+  // float copies for the float evaluations (a division or conversion in double at every
+  // evaluation would occupy the FP64 pipe): 1/alpha, beta, 1/Z, beta/alpha
+  float inv_alpha_f, beta_f, inv_norm_f, beta_over_alpha_f;
 };
 
 // Everything a kernel needs to know about the problem (passed by value)
@@ -80,6 +83,8 @@ struct Geometry {
   int nkernels;      // 1 (M) or 2 (M and D): record heads
   int nslabs;        // value slabs per record: one per kernel, plus the dipole derivative slab
   int stage_cap;     // particle records the spreading kernel stages in shared memory at a time
+  int rec_threads;   // threads per block of the record kernel when it stages records in shared
+                     // memory (0: direct writes)
 };
 
 // Device tables owned by the plan

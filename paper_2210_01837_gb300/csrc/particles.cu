@@ -40,10 +40,10 @@ __device__ __forceinline__ double es_eval(double t, const EsKernel& k) {
 __device__ __forceinline__ float es_eval_f(double t, const EsKernel& k) {
   // the offset t is formed in double by the caller (a difference of nearby large numbers); the
   // rest runs in float (a division or a conversion in double occupies the scarce FP64 pipe)
-  const float r = (float)t * (float)(1.0 / k.alpha);
+  const float r = (float)t * k.inv_alpha_f;
   if (fabsf(r) > 1.0f) return 0.0f;
   const float q = fmaxf(0.0f, 1.0f - r * r);
-  return expf((float)k.beta * (sqrtf(q) - 1.0f)) * (float)k.inv_norm;
+  return expf(k.beta_f * (sqrtf(q) - 1.0f)) * k.inv_norm_f;
 }
 
 template <typename T> __device__ __forceinline__ T es_t(double t, const EsKernel& k);
@@ -63,9 +63,9 @@ __device__ __forceinline__ float esd_eval_f(double t, const EsKernel& k) {
   // the truncation is decided in double, as on the double path: a node cut on one side and kept on
   // the other would change a result by |phi'(cut)|, far above float rounding
   if (fabs(t) > k.cut) return 0.0f;
-  const float r = (float)t * (float)(1.0 / k.alpha);
+  const float r = (float)t * k.inv_alpha_f;
   const float s = sqrtf(fmaxf(0.0f, 1.0f - r * r));
-  return -(float)(k.beta / k.alpha) * r / s * expf((float)k.beta * (s - 1.0f)) * (float)k.inv_norm;
+  return -k.beta_over_alpha_f * r / s * expf(k.beta_f * (s - 1.0f)) * k.inv_norm_f;
 }
 
 template <typename T> __device__ __forceinline__ T esd_t(double t, const EsKernel& k);
@@ -94,15 +94,21 @@ __device__ __forceinline__ int count_above(const double* zc, int nz, double v) {
   return lo;
 }
 
-template <typename T>
+// One thread per particle.  STAGED: the block's records are built in shared memory and then
+// copied to their contiguous place in global memory with 16-byte stores (a thread writing its own
+// record directly would make every warp store touch 32 different sectors).
+template <typename T, bool STAGED>
 __global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__ pos,
                                const double* __restrict__ F, const double* __restrict__ Tq,
                                const double* __restrict__ zc, uint32_t* __restrict__ rec,
                                int* __restrict__ bin_of, int* __restrict__ bin_count,
                                int* __restrict__ zrange, int* __restrict__ status) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  uint32_t* r = rec + (size_t)j * g.rec_words;
+  extern __shared__ __align__(16) uint32_t srec_out[];
+  const int64_t j0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t j = j0 + threadIdx.x;
+  if (!STAGED && j >= n) return;
+  if (j < n) {
+  uint32_t* r = STAGED ? srec_out + (size_t)threadIdx.x * g.rec_words : rec + (size_t)j * g.rec_words;
   T* tv = reinterpret_cast<T*>(r + 8);
   double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
   double f[3] = {F[3 * j], F[3 * j + 1], F[3 * j + 2]};
@@ -215,6 +221,16 @@ __global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__
   if (cmax >= 0) {
     atomicMin(&zrange[0], cmin);
     atomicMax(&zrange[1], cmax);
+  }
+  }  // j < n
+  if (STAGED) {
+    __syncthreads();
+    const int64_t left = n - j0;
+    const int cnt = left < (int64_t)blockDim.x ? (int)left : (int)blockDim.x;
+    const int q = cnt * (g.rec_words / 4);  // 16-byte pieces (rec_words is a multiple of 4)
+    const uint4* src = reinterpret_cast<const uint4*>(srec_out);
+    uint4* dst = reinterpret_cast<uint4*>(rec + (size_t)j0 * g.rec_words);
+    for (int t = threadIdx.x; t < q; t += blockDim.x) dst[t] = src[t];
   }
 }
 
@@ -393,9 +409,50 @@ __device__ __forceinline__ void spread_curl_list(const Geometry& g, const uint32
   }
 }
 
+// Kernel-derivative route with coinciding supports (m_M = m_D, so both record heads are equal): each
+// listed candidate adds F Delta_M and (1/2) grad Delta_D x tau in one walk.
+template <typename T, int ZC>
+__device__ __forceinline__ void spread_fused_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl,
+                                                  int rw, int gx, int gy, int zb, T (&acc)[ZC][3]) {
+  const int stride = 2 * g.pxc + g.lzc;
+  const int px = g.kM.px;
+  for (int e = 0; e < nl; ++e) {
+    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const int4 hd = reinterpret_cast<const int4*>(r)[0];
+    if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
+    int dx = gx - hd.x;
+    if (dx < 0) dx += g.nx;
+    if (dx >= px) continue;
+    int dy = gy - hd.y;
+    if (dy < 0) dy += g.ny;
+    const T* tv = reinterpret_cast<const T*>(r + 8);
+    const T* pm = tv + 6;               // monopole phi
+    const T* ph = tv + 6 + stride;      // dipole phi
+    const T* pd = tv + 6 + 2 * stride;  // dipole phi'
+    const T mxy = pm[dx] * pm[g.pxc + dy];
+    const T fm0 = tv[0] * mxy, fm1 = tv[1] * mxy, fm2 = tv[2] * mxy;
+    const T fx = ph[dx], fy = ph[g.pxc + dy];
+    const T wxy = fx * fy, bx = pd[dx] * fy, by = fx * pd[g.pxc + dy];
+    const T tx = tv[3], ty = tv[4], tz = tv[5];
+    const T a0 = by * tz, b0 = -wxy * ty;
+    const T a1 = -bx * tz, b1 = wxy * tx;
+    const T a2 = bx * ty - by * tx;
+#pragma unroll
+    for (int zz = 0; zz < ZC; ++zz) {
+      const int iz = zb + zz - hd.z;
+      if (iz >= 0 && iz < hd.w) {
+        const T mz = pm[2 * g.pxc + iz], pz = ph[2 * g.pxc + iz], dz = pd[2 * g.pxc + iz];
+        acc[zz][0] += fm0 * mz + a0 * pz + b0 * dz;
+        acc[zz][1] += fm1 * mz + a1 * pz + b1 * dz;
+        acc[zz][2] += fm2 * mz + a2 * pz;
+      }
+    }
+  }
+}
+
 // MODE 0: forces only (3 fields); 1: spectral-curl torques (force fields, then torque fields, one
 // pass each); 2: kernel-derivative torques (the force density and the half-curl sources in one pass
-// over the 3 fields).
+// over the 3 fields); 3: as 2 with coinciding supports (one list, one walk per candidate).
 template <typename T, int MODE, int ZC>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
@@ -486,7 +543,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     }
     const int ncand = min(passed, win1) - win0;
     if (ncand <= 0 && round > 0) break;
-    constexpr bool TWO = MODE != 0;
+    constexpr bool TWO = MODE == 1 || MODE == 2;
     const bool once = ncand <= g.stage_cap;
     int nl0 = 0, nl1 = 0;
     int* wl0 = s_wl[warp][0];
@@ -498,7 +555,9 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     }
     // the candidates of list set (wl0, wl1) into the accumulators of pass K
     auto apply = [&](int K, T (&acc)[ZC][3], int zb) {
-      if (MODE == 2) {
+      if (MODE == 3) {
+        spread_fused_list<T, ZC>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+      } else if (MODE == 2) {
         spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
         spread_curl_list<T, ZC>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
       } else if (K == 0) {
@@ -815,6 +874,10 @@ dps_status particle_geometry(Geometry& g, const dps_kernel_params* kp, int tsize
     k.inv_norm = 1.0 / es_norm(k.alpha, beta);
     k.cut = 0.0;
     k.px = m + 1;
+    k.inv_alpha_f = (float)(1.0 / k.alpha);
+    k.beta_f = (float)beta;
+    k.inv_norm_f = (float)k.inv_norm;
+    k.beta_over_alpha_f = (float)(beta / k.alpha);
   };
   setk(g.kM, kp->m_M, kp->beta_M);
   if (torque) setk(g.kD, kp->m_D, kp->beta_D); else g.kD = g.kM;
@@ -852,10 +915,14 @@ template <typename T>
 void launch_records(const Plan& p, int64_t n, const double* pos, const double* F, const double* Tq,
                     cudaStream_t s) {
   if (n <= 0) return;
-  const int threads = 128;
+  const int threads = p.g.rec_threads > 0 ? p.g.rec_threads : 128;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  records_kernel<T><<<blocks, threads, 0, s>>>(p.g, n, pos, F, Tq, p.tab.zc, p.records, p.bin_of,
-                                               p.bin_count, p.zrange, p.status);
+  if (p.g.rec_threads > 0)
+    records_kernel<T, true><<<blocks, threads, (size_t)threads * p.g.rec_words * sizeof(uint32_t), s>>>(
+        p.g, n, pos, F, Tq, p.tab.zc, p.records, p.bin_of, p.bin_count, p.zrange, p.status);
+  else
+    records_kernel<T, false><<<blocks, threads, 0, s>>>(p.g, n, pos, F, Tq, p.tab.zc, p.records, p.bin_of,
+                                                        p.bin_count, p.zrange, p.status);
 }
 
 void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
@@ -884,7 +951,7 @@ template <typename T>
 int spread_prepare(Plan& p) {
   constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
   if (!(allow_smem(spread_kernel<T, 1, ZC6>) && allow_smem(spread_kernel<T, 0, ZC3>) &&
-        allow_smem(spread_kernel<T, 2, ZC3>)))
+        allow_smem(spread_kernel<T, 2, ZC3>) && allow_smem(spread_kernel<T, 3, ZC3>)))
     return 0;
   int dev = 0, optin = 0;
   cudaFuncAttributes fa;  // the three modes declare the same static shared arrays
@@ -892,8 +959,15 @@ int spread_prepare(Plan& p) {
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
       cudaFuncGetAttributes(&fa, spread_kernel<T, 1, ZC6>) != cudaSuccess)
     return 0;
-  const long cap = ((long)optin - (long)fa.sharedSizeBytes) / ((long)p.g.rec_words * (long)sizeof(uint32_t));
+  const long rb = (long)p.g.rec_words * (long)sizeof(uint32_t);
+  const long cap = ((long)optin - (long)fa.sharedSizeBytes) / rb;
   p.g.stage_cap = (int)std::min<long>(kStage, cap);
+  // records built in shared memory by blocks of 128, 64 or 32 threads when that many fit in
+  // 96 KB (two blocks per SM), else written directly
+  if (!allow_smem(records_kernel<T, true>)) return 0;
+  p.g.rec_threads = 0;
+  for (int t : {128, 64, 32})
+    if ((long)t * rb <= 96 * 1024) { p.g.rec_threads = t; break; }
   return p.g.stage_cap >= 1 ? 1 : -1;
 }
 
@@ -905,6 +979,8 @@ void launch_spread(const Plan& p, cudaStream_t s) {
   T* grid = reinterpret_cast<T*>(p.grid);
   if (p.g.spectral_curl)
     spread_kernel<T, 1, ZC6><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
+  else if (p.g.torque_deriv && p.g.kM.px == p.g.kD.px)  // equal m: the two supports coincide
+    spread_kernel<T, 3, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
   else if (p.g.torque_deriv)
     spread_kernel<T, 2, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
   else

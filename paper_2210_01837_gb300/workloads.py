@@ -19,7 +19,14 @@ by seeded random draws because the paper's configurations are not available:
                     heights U[1.2, 10], slit z in [0, 20] with U[1.2, 18.8], open z in [0, 20]
                     with U[2, 18]; forces and torques N(0,1); m = 5 with Table I betas.
 
-Seeds are 20221004 + the workload's index (1, 2, 3, 4).
+* ``lanczos_layer`` - the Lanczos-convergence suspension of Sec. IV.C: a base cell of 2048
+                    non-overlapping spheres (random sequential addition, centre distance >= 2 R_h)
+                    in L = 128.8 R_h (area fraction 0.39) tiled r x r times in xy (N = 2048 r^2),
+                    two layers of heights (half near 1.1 R_h, half near 2.2 R_h: the bimodal
+                    profile of the scaling test, drawn here), box height H = 7.5 R_h, forces only,
+                    Table III monopole grid (150 r)^2 x 19, m = 4, beta = 1.87 m; R_h = 1.
+
+Seeds are 20221004 + the workload's index (1, 2, 3, 4, 5).
 """
 
 import numpy as np
@@ -133,3 +140,43 @@ def batch_systems(count=256, seed_offset=4, modes=("bottom_wall", "slit"), n_ran
                       m_M=m, beta_M=m * _T1_M5[1], m_D=m, beta_D=m * _T1_M5[2], eta=1.0)
         out.append((params, pos, F, T))
     return out
+
+
+def _rsa_layer(rng, n, L, heights, dmin, max_tries=200000):
+    """n spheres placed one at a time at a uniform xy position (periodic box of side L) and a height
+    drawn by heights(rng), rejected while closer than dmin to one already placed (random
+    sequential addition: no overlaps, as in a suspension with steric repulsion)."""
+    pos = np.empty((n, 3))
+    k = 0
+    for _ in range(max_tries):
+        p = np.array([rng.uniform(0.0, L), rng.uniform(0.0, L), heights(rng)])
+        if k:
+            d = pos[:k] - p
+            d[:, :2] -= L * np.round(d[:, :2] / L)
+            if np.min(np.einsum("ij,ij->i", d, d)) < dmin * dmin:
+                continue
+        pos[k] = p
+        k += 1
+        if k == n:
+            return pos
+    raise RuntimeError("random sequential addition did not place every particle")
+
+
+def lanczos_layer(reps=1, mode="bottom_wall", seed_offset=5):
+    """Particle layer of the Lanczos convergence test, tiled reps x reps times in xy; returns
+    (params, pos, W) with W the i.i.d. standard normal vector [N][3]."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    L0, n0, H = 128.8, 2048, 7.5
+
+    def heights(r):  # two layers
+        return r.normal(1.1, 0.05) if r.uniform() < 0.5 else r.normal(2.2, 0.1)
+
+    base = _rsa_layer(rng, n0, L0, heights, 2.0)
+    base[:, 2] = np.clip(base[:, 2], 1.0, 3.0)
+    tiles = [base + np.array([i * L0, j * L0, 0.0]) for j in range(reps) for i in range(reps)]
+    pos = np.concatenate(tiles)
+    L = reps * L0
+    params = dict(Lx=L, Ly=L, zmin=0.0, zmax=H, mode=mode, nx=150 * reps, ny=150 * reps, nz=19, m_M=4,
+                  beta_M=4 * 1.87, m_D=0, beta_D=0.0, eta=1.0)
+    W = rng.standard_normal((len(pos), 3))
+    return params, pos, W

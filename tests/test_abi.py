@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -129,3 +130,31 @@ def test_batch_and_server_reject_invalid_arguments_on_host(lib):
     r = binding.dps_serve_result()
     assert lib.dpstokes_server_wait(None, 0, 0.0, ctypes.byref(r)) == binding.DPS_ERR_INVALID_ARG
     lib.dpstokes_server_destroy(None)
+
+
+def test_tridiagonal_square_root_on_the_host_matches_the_oracle(lib):
+    # the Lanczos sampler's host step (Jacobi eigendecomposition) against the oracle's eigh route
+    from oracle.lanczos import sqrt_tridiagonal_e1
+    from paper_2210_01837_gb300 import binding
+    rng = np.random.default_rng(12)
+    for j in (1, 2, 5, 17, 64):
+        a = rng.uniform(1.0, 4.0, j)
+        b = rng.uniform(-1.0, 1.0, max(j - 1, 0))
+        st, y = binding.dpstokes_tridiag_sqrt_e1(a, b)
+        assert st == binding.DPS_OK
+        assert np.allclose(y, sqrt_tridiagonal_e1(a, b), rtol=0, atol=1e-12)
+    # an indefinite T: eigenvalues below zero take a zero root on both sides
+    a = np.array([1.0, -2.0, 0.5])
+    b = np.array([0.7, 0.3])
+    st, y = binding.dpstokes_tridiag_sqrt_e1(a, b)
+    assert np.allclose(y, sqrt_tridiagonal_e1(a, b), rtol=0, atol=1e-12)
+
+
+def test_lanczos_entry_points_reject_invalid_arguments_on_host(lib):
+    from paper_2210_01837_gb300 import binding
+    st, h = binding.dpstokes_lanczos_create(None, 8)
+    assert st == binding.DPS_ERR_INVALID_ARG and not h.value
+    st, _, _, _ = binding.dpstokes_lanczos_sample(None, 4, None, None, None, 1e-3, None, 8)
+    assert st == binding.DPS_ERR_INVALID_ARG
+    assert binding.dpstokes_tridiag_sqrt_e1([], [])[0] == binding.DPS_ERR_INVALID_ARG
+    binding.dpstokes_lanczos_destroy(None)
