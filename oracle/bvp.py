@@ -14,8 +14,10 @@ zero mode).  The paper defers the discretisation to Greengard's spectral-integra
 * Two boundary rows on the truncated y, using T_n(+-1) = (+-1)^n and T_n'(+-1) = (+-1)^(n+1) n^2:
   - 'dtn'  : (2/H) y_s(+1) + k y(+1) = g_top,  (2/H) y_s(-1) - k y(-1) = g_bot
              (the Dirichlet-to-Neumann rows of Eqs. 17, 22, 24);
-  - 'bw0'  : y(-1) = g_bot, (2/H) y_s(+1) = g_top   (Eq. 52, zero mode above one wall);
-  - 'sc0'  : y(-1) = g_bot, y(+1) = g_top          (Eq. A12 with zero slip lengths).
+  - 'bw0'  : y(-1) - l0 (2/H) y_s(-1) = g_bot, (2/H) y_s(+1) = g_top   (Eq. 52, zero mode above
+             one wall; the Robin bottom row with slip length l0 follows Eq. A12);
+  - 'sc0'  : y(-1) - l0 (2/H) y_s(-1) = g_bot, y(+1) + lH (2/H) y_s(+1) = g_top   (Eq. A12).
+  slip = (l0, lH), zero by default (no-slip walls).
 
 The oracle assembles the full dense (N+2) x (N+2) real matrix and solves it by LU
 (numpy.linalg.solve); the matrix is real because it depends on k only through k and k^2.
@@ -51,7 +53,7 @@ def _endpoint_rows(N):
     return val_top, val_bot, der_top, der_bot
 
 
-def assemble(k, N, H, bc):
+def assemble(k, N, H, bc, slip=(0.0, 0.0)):
     """Dense BVP matrices for an array of wavenumber magnitudes k (shape (K,)): (K, N+2, N+2)."""
     k = np.atleast_1d(np.asarray(k, dtype=float))
     Y = y_map(N)
@@ -66,16 +68,16 @@ def assemble(k, N, H, bc):
         A[:, N + 1, :] = s * (db @ Y)[None] - k[:, None] * (vb @ Y)[None]
     elif bc == "bw0":
         A[:, N, :] = s * (dt @ Y)[None]
-        A[:, N + 1, :] = (vb @ Y)[None]
+        A[:, N + 1, :] = ((vb - slip[0] * s * db) @ Y)[None]
     elif bc == "sc0":
-        A[:, N, :] = (vt @ Y)[None]
-        A[:, N + 1, :] = (vb @ Y)[None]
+        A[:, N, :] = ((vt + slip[1] * s * dt) @ Y)[None]
+        A[:, N + 1, :] = ((vb - slip[0] * s * db) @ Y)[None]
     else:
         raise ValueError(bc)
     return A, Y
 
 
-def solve(k, H, r, g_top, g_bot, bc):
+def solve(k, H, r, g_top, g_bot, bc, slip=(0.0, 0.0)):
     """Solve (D^2 - k^2) y = r with the boundary rows `bc` for many wavenumbers at once.
 
     k: (K,) magnitudes; r: (K, R, N) complex Chebyshev coefficients of R right-hand sides;
@@ -83,7 +85,7 @@ def solve(k, H, r, g_top, g_bot, bc):
     """
     r = np.asarray(r, dtype=complex)
     K, R, N = r.shape
-    A, Y = assemble(k, N, H, bc)
+    A, Y = assemble(k, N, H, bc, slip)
     rhs = np.zeros((K, N + 2, 2 * R))
     rhs[:, :N, :R] = np.transpose(r.real, (0, 2, 1))
     rhs[:, :N, R:] = np.transpose(r.imag, (0, 2, 1))

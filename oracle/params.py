@@ -37,6 +37,10 @@ class Params:
     m_M, beta_M / m_D, beta_D : ES support width in grid cells and shape parameter of the
             monopole / dipole kernels (Sec. III.E, Eq. 54); alpha = m*h/2.
     eta   : viscosity (Eq. 4).
+    slip_bottom, slip_top : slip lengths l0 at zmin and lH at zmax (Appendix A, Eq. A1); 0 is a
+            no-slip wall.  The bottom-wall geometry takes l0 only; the open geometry neither.
+    uw_bottom, uw_top : uniform tangential wall velocities (u^W, v^W) at zmin and zmax (Eq. A1;
+            the paper allows any smooth u^W(x, y), only uniform ones are modelled here).
     """
 
     Lx: float
@@ -52,6 +56,10 @@ class Params:
     m_D: int = 0
     beta_D: float = 0.0
     eta: float = 1.0
+    slip_bottom: float = 0.0
+    slip_top: float = 0.0
+    uw_bottom: tuple = (0.0, 0.0)
+    uw_top: tuple = (0.0, 0.0)
 
     def __post_init__(self):
         if self.mode not in MODES:
@@ -62,6 +70,14 @@ class Params:
             raise ValueError("the grid spacing must be the same in x and y")
         if not self.zmax > self.zmin:
             raise ValueError("zmax must exceed zmin")
+        if not (self.slip_bottom >= 0.0 and self.slip_top >= 0.0):
+            raise ValueError("slip lengths must be non-negative")
+        top_wall = self.mode == SLIT
+        bottom_wall = self.mode in (BOTTOM_WALL, SLIT)
+        if not bottom_wall and (self.slip_bottom or any(self.uw_bottom)):
+            raise ValueError("no bottom wall to carry slip or a wall velocity")
+        if not top_wall and (self.slip_top or any(self.uw_top)):
+            raise ValueError("no top wall to carry slip or a wall velocity")
 
     @property
     def h(self):

@@ -112,7 +112,11 @@ def dp_solve(p, f, g, hz, kx, ky):
 
 def correction_bw(p, u0, v0, w0, kx, ky):
     """Step 4, bottom wall: Eqs. 41-44 evaluated at the nodes, zeta = z - zmin.
-    u0, v0, w0: (K,) wall data (minus the DP velocity at the wall).  Returns (3, K, N) node values."""
+    u0, v0, w0: (K,) wall data (minus the DP velocity at the wall, plus l0 times its z derivative
+    for the tangential parts).  With a slip length the solution is correction_bw_slip.
+    Returns (3, K, N) node values."""
+    if p.slip_bottom:
+        return correction_bw_slip(p, u0, v0, w0, kx, ky)
     k = np.hypot(kx, ky)[:, None]
     kxc = kx[:, None]
     kyc = ky[:, None]
@@ -128,10 +132,45 @@ def correction_bw(p, u0, v0, w0, kx, ky):
     return np.stack([uc, vc, wc])
 
 
+def correction_bw_slip(p, u0, v0, w0, kx, ky, return_coefficients=False):
+    """Step 4, bottom wall with slip length l0: the slit construction of Appendix A restricted to
+    the family that decays away from the wall (the growing one is excluded by boundedness as
+    z -> infinity): unknowns C0, Cx, Cy, Cz of Eqs. A5-A6 from the bottom rows of Eq. A8 (Robin
+    rows for u and v, w = w0) and the continuity row at the wall (Eq. A10), dense LU per k."""
+    eta, l0 = p.eta, p.slip_bottom
+    k = np.hypot(kx, ky)
+    K = k.size
+    ikx, iky = 1j * kx, 1j * ky
+    A = np.zeros((K, 4, 4), dtype=complex)
+    # unknown order: C0, Cx, Cy, Cz
+    A[:, 0, 0] = ikx * l0 / (2 * eta * k)
+    A[:, 0, 1] = 1.0 + k * l0
+    A[:, 1, 0] = iky * l0 / (2 * eta * k)
+    A[:, 1, 2] = 1.0 + k * l0
+    A[:, 2, 3] = 1.0
+    A[:, 3, 0] = 1.0 / (2 * eta)
+    A[:, 3, 1] = ikx
+    A[:, 3, 2] = iky
+    A[:, 3, 3] = -k
+    rhs = np.stack([u0, v0, w0, np.zeros_like(u0)], axis=1)
+    x = np.linalg.solve(A, rhs[:, :, None])[:, :, 0]
+    C0, Cx, Cy, Cz = (x[:, i][:, None] for i in range(4))
+    zeta = (cheb.nodes_z(p.nz, p.zmin, p.zmax) - p.zmin)[None, :]
+    kc = k[:, None]
+    Eb = np.exp(-kc * zeta)
+    uc = -(C0 * ikx[:, None] / (2 * eta * kc)) * zeta * Eb + Cx * Eb
+    vc = -(C0 * iky[:, None] / (2 * eta * kc)) * zeta * Eb + Cy * Eb
+    wc = (C0 / (2 * eta)) * zeta * Eb + Cz * Eb
+    if return_coefficients:
+        return np.stack([uc, vc, wc]), x.T
+    return np.stack([uc, vc, wc])
+
+
 def correction_sc(p, bot, top, kx, ky, return_coefficients=False):
-    """Step 4, slit channel: the 8 equations A8 and A10 with zero slip lengths, in the rescaled
-    basis (top family multiplied by e^{kH}), solved by dense LU per k; then Eqs. A5-A6 at the
-    nodes.  bot = (u0, v0, w0), top = (uH, vH, wH), each (K,).  Returns (3, K, N) node values."""
+    """Step 4, slit channel: the 8 equations A8 and A10 with slip lengths l0, lH (zero: no-slip),
+    in the rescaled basis (top family multiplied by e^{kH}), solved by dense LU per k; then
+    Eqs. A5-A6 at the nodes.  bot = (u0, v0, w0), top = (uH, vH, wH), each (K,).  Returns (3, K, N)
+    node values."""
     eta = p.eta
     H = p.H
     k = np.hypot(kx, ky)
@@ -139,22 +178,23 @@ def correction_sc(p, bot, top, kx, ky, return_coefficients=False):
     E = np.exp(-k * H)
     ikx = 1j * kx
     iky = 1j * ky
+    l0, lH = p.slip_bottom, p.slip_top
     A = np.zeros((K, 8, 8), dtype=complex)
     # unknown order: C0, D0, Cx, Dx, Cy, Dy, Cz, Dz  (D's rescaled by e^{kH})
-    A[:, 0, 2] = 1.0
-    A[:, 0, 3] = E
-    A[:, 1, 4] = 1.0
-    A[:, 1, 5] = E
+    # bottom Robin rows (Eq. A8, first line, for u and v) and w = w0
+    for row, ik, c, d in ((0, ikx, 2, 3), (1, iky, 4, 5)):
+        A[:, row, 0] = ik * l0 / (2 * eta * k)
+        A[:, row, 1] = -ik * l0 * E / (2 * eta * k)
+        A[:, row, c] = 1.0 + k * l0
+        A[:, row, d] = E * (1.0 - k * l0)
     A[:, 2, 6] = 1.0
     A[:, 2, 7] = E
-    A[:, 3, 0] = -ikx * H * E / (2 * eta * k)
-    A[:, 3, 1] = ikx * H / (2 * eta * k)
-    A[:, 3, 2] = E
-    A[:, 3, 3] = 1.0
-    A[:, 4, 0] = -iky * H * E / (2 * eta * k)
-    A[:, 4, 1] = iky * H / (2 * eta * k)
-    A[:, 4, 4] = E
-    A[:, 4, 5] = 1.0
+    # top Robin rows (Eq. A8, third line) and w = wH
+    for row, ik, c, d in ((3, ikx, 2, 3), (4, iky, 4, 5)):
+        A[:, row, 0] = ik * H * E / (2 * eta * k) * (k * lH - lH / H - 1.0)
+        A[:, row, 1] = ik * H / (2 * eta * k) * (k * lH + lH / H + 1.0)
+        A[:, row, c] = E * (1.0 - k * lH)
+        A[:, row, d] = 1.0 + k * lH
     A[:, 5, 0] = H * E / (2 * eta)
     A[:, 5, 1] = H / (2 * eta)
     A[:, 5, 6] = E
@@ -195,17 +235,21 @@ def correction_sc(p, bot, top, kx, ky, return_coefficients=False):
 
 
 def zero_mode(p, f0, g0):
-    """Step 5: k = 0.  w = 0; d^2u/dz^2 = -f/eta with u(zmin) = 0 and du/dz(zmax) = 0 above one
-    wall (Eqs. 51-52), u(zmin) = u(zmax) = 0 in the slit (Eq. A12, zero slip), and u = 0 in the
-    open geometry.  f0, g0: (N,) coefficients.  Returns (u, v, w) coefficients."""
+    """Step 5: k = 0.  w = 0; d^2u/dz^2 = -f/eta with, above one wall, u - l0 du/dz = u^W at zmin
+    and du/dz = 0 at zmax (Eqs. 51-52 with the Robin bottom row of Eq. A12), in the slit
+    u - l0 du/dz = u^W_0 at zmin and u + lH du/dz = u^W_H at zmax (Eq. A12), and u = 0 in the open
+    geometry.  The k = 0 coefficient of a uniform wall velocity is Nx Ny u^W (the forward transform
+    is unnormalised).  f0, g0: (N,) coefficients.  Returns (u, v, w) coefficients."""
     N = f0.shape[-1]
     if p.mode == FREE:
         z = np.zeros(N, dtype=complex)
         return z, z.copy(), z.copy()
     bc = "bw0" if p.mode == BOTTOM_WALL else "sc0"
     r = np.stack([-f0 / p.eta, -g0 / p.eta])[None]
-    zero = np.zeros((1, 2), dtype=complex)
-    y = bvp.solve(np.zeros(1), p.H, r, zero, zero, bc)[0]
+    scale = p.nx * p.ny
+    g_bot = scale * np.array([p.uw_bottom], dtype=complex)
+    g_top = scale * np.array([p.uw_top], dtype=complex) if p.mode == SLIT else np.zeros((1, 2), dtype=complex)
+    y = bvp.solve(np.zeros(1), p.H, r, g_top, g_bot, bc, (p.slip_bottom, p.slip_top))[0]
     return y[0], y[1], np.zeros(N, dtype=complex)
 
 
@@ -238,12 +282,20 @@ def solve_spectral(p, fcoef, tcoef=None, want_curl=False, chunk=4096):
             idx = np.nonzero(act)[0]
             _, u, v, w = dp_solve(p, fb[0, idx], fb[1, idx], fb[2, idx], kx[idx], ky[idx])
             if p.mode != FREE:
-                ub, vb, wb = (np.stack([u, v, w]) * ((-1.0) ** np.arange(N))).sum(axis=-1)
+                # wall data (Eq. A3): minus the DP velocity at the wall, and for the tangential
+                # parts plus l0 (bottom) or minus lH (top) times its z derivative there
+                sign = (-1.0) ** np.arange(N)
+                ub, vb, wb = (np.stack([u, v, w]) * sign).sum(axis=-1)
+                dub, dvb = (dz(p, np.stack([u, v])) * sign).sum(axis=-1)
+                l0, lH = p.slip_bottom, p.slip_top
+                bot = (-ub + l0 * dub, -vb + l0 * dvb, -wb)
                 if p.mode == BOTTOM_WALL:
-                    corr = correction_bw(p, -ub, -vb, -wb, kx[idx], ky[idx])
+                    corr = correction_bw(p, *bot, kx[idx], ky[idx])
                 else:
                     ut, vt, wt = np.stack([u, v, w]).sum(axis=-1)
-                    corr = correction_sc(p, (-ub, -vb, -wb), (-ut, -vt, -wt), kx[idx], ky[idx])
+                    dut, dvt = dz(p, np.stack([u, v])).sum(axis=-1)
+                    top = (-ut - lH * dut, -vt - lH * dvt, -wt)
+                    corr = correction_sc(p, bot, top, kx[idx], ky[idx])
                 corr_coef = np.einsum("nc,fkc->fkn", Cd, corr)
                 u = u + corr_coef[0]
                 v = v + corr_coef[1]
