@@ -108,6 +108,29 @@ dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zm
                                 int32_t wall_mode, const dps_grid* grid,
                                 const dps_kernel_params* kp);
 
+/* Wall conditions beyond no-slip stationary walls (Appendix A, Eqs. A1-A12): slip lengths and
+ * uniform tangential wall velocities.  The tangential velocity obeys u - l0 du/dz = u^W_0 at zmin
+ * and u + lH du/dz = u^W_H at zmax (the normal velocity vanishes at a wall).  Slip enters the
+ * wall data of the correction (minus the DP velocity plus or minus l times its z derivative there),
+ * the correction's boundary rows and the k = 0 rows; a wall velocity enters the k = 0 rows only,
+ * which makes the product affine in the forces.  For the bottom-wall geometry the paper prints slip
+ * for the slit only; the bottom-wall rows here are the slit's restricted to the decaying family.
+ * A very large l0 above one wall under an open top makes the k = 0 response grow with l0 (a net
+ * force has no steady state over a shear-free wall); l0 must be finite. */
+typedef struct {
+  double slip_bottom;   /* l0 >= 0 at zmin (bottom wall and slit)                                 */
+  double slip_top;      /* lH >= 0 at zmax (slit only; 0 otherwise)                                */
+  double uw_bottom[2];  /* (u, v) of the wall at zmin (bottom wall and slit)                       */
+  double uw_top[2];     /* (u, v) of the wall at zmax (slit only; 0 otherwise)                     */
+} dps_wall_params;
+
+/* dpstokes_plan_create with wall conditions; wp = NULL means no-slip stationary walls (what
+ * dpstokes_plan_create builds).  DPS_ERR_INVALID_ARG also for a negative or non-finite slip length
+ * or wall velocity, and for slip or a wall velocity on a wall the geometry does not have. */
+dps_status dpstokes_plan_create_ex(dps_plan_t* out, double Lx, double Ly, double zmin, double zmax,
+                                   int32_t wall_mode, const dps_grid* grid, const dps_kernel_params* kp,
+                                   const dps_wall_params* wp);
+
 /* One mobility product, enqueued on `stream` (a cudaStream_t, NULL for the legacy stream).  All of
  * an apply's work is ordered after earlier work on `stream` and before later work on it (when the
  * wavenumber-space stages run in several column chunks, DPS_CHUNKS in the environment at plan
@@ -261,6 +284,8 @@ typedef struct {
   const double* torques;      /* HOST [n][3] or NULL (must match kp.with_torque)                  */
   double* out_vel;            /* HOST [n][3], written before the request completes                */
   double* out_angvel;         /* HOST [n][3] or NULL                                              */
+  dps_wall_params walls;      /* wall conditions (all zero: no-slip stationary walls); part of the
+                                 plan key                                                        */
 } dps_serve_request;
 
 typedef struct {

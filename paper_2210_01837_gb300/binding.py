@@ -56,12 +56,27 @@ class dps_request(ctypes.Structure):
                 ("out_angvel", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
+class dps_wall_params(ctypes.Structure):
+    _fields_ = [("slip_bottom", ctypes.c_double), ("slip_top", ctypes.c_double),
+                ("uw_bottom", ctypes.c_double * 2), ("uw_top", ctypes.c_double * 2)]
+
+
+def wall_params(params):
+    """dps_wall_params from the optional slip_bottom, slip_top, uw_bottom, uw_top entries of params."""
+    ub = params.get("uw_bottom", (0.0, 0.0)) or (0.0, 0.0)
+    ut = params.get("uw_top", (0.0, 0.0)) or (0.0, 0.0)
+    w = dps_wall_params(float(params.get("slip_bottom", 0.0) or 0.0), float(params.get("slip_top", 0.0) or 0.0))
+    w.uw_bottom[0], w.uw_bottom[1] = float(ub[0]), float(ub[1])
+    w.uw_top[0], w.uw_top[1] = float(ut[0]), float(ut[1])
+    return w
+
+
 class dps_serve_request(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("zmin", ctypes.c_double),
                 ("zmax", ctypes.c_double), ("wall_mode", ctypes.c_int32), ("grid", dps_grid),
                 ("kp", dps_kernel_params), ("n", ctypes.c_int64), ("positions", ctypes.c_void_p),
                 ("forces", ctypes.c_void_p), ("torques", ctypes.c_void_p), ("out_vel", ctypes.c_void_p),
-                ("out_angvel", ctypes.c_void_p)]
+                ("out_angvel", ctypes.c_void_p), ("walls", dps_wall_params)]
 
 
 class dps_serve_result(ctypes.Structure):
@@ -104,6 +119,8 @@ def load(path=None):
     sig = {
         "dpstokes_plan_create": (_I32, [ctypes.POINTER(_P), _D, _D, _D, _D, _I32, ctypes.POINTER(dps_grid),
                                         ctypes.POINTER(dps_kernel_params)]),
+        "dpstokes_plan_create_ex": (_I32, [ctypes.POINTER(_P), _D, _D, _D, _D, _I32, ctypes.POINTER(dps_grid),
+                                           ctypes.POINTER(dps_kernel_params), ctypes.POINTER(dps_wall_params)]),
         "dpstokes_apply": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P]),
         "dpstokes_apply_host": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P]),
         "dpstokes_status": (_I32, [_P, _P]),
@@ -151,6 +168,14 @@ def dpstokes_plan_create(Lx, Ly, zmin, zmax, wall_mode, grid, kp):
     h = _P()
     st = load().dpstokes_plan_create(ctypes.byref(h), Lx, Ly, zmin, zmax, wall_mode, ctypes.byref(grid),
                                      ctypes.byref(kp))
+    return st, h
+
+
+def dpstokes_plan_create_ex(Lx, Ly, zmin, zmax, wall_mode, grid, kp, wp):
+    """Returns (status, handle); wp a dps_wall_params or None."""
+    h = _P()
+    st = load().dpstokes_plan_create_ex(ctypes.byref(h), Lx, Ly, zmin, zmax, wall_mode, ctypes.byref(grid),
+                                        ctypes.byref(kp), None if wp is None else ctypes.byref(wp))
     return st, h
 
 
@@ -277,7 +302,8 @@ class Plan:
     """A resident problem (box, wall mode, grid, kernels) with its device buffers."""
 
     def __init__(self, Lx, Ly, zmin, zmax, mode, nx, ny, nz, m_M, beta_M, m_D=0, beta_D=0.0, eta=1.0,
-                 with_torque=False, precision="mixed", max_n=1):
+                 with_torque=False, precision="mixed", max_n=1, slip_bottom=0.0, slip_top=0.0,
+                 uw_bottom=(0.0, 0.0), uw_top=(0.0, 0.0)):
         self.route = torque_route(with_torque)
         self.with_torque = self.route != 0
         self.precision = precision
@@ -285,7 +311,8 @@ class Plan:
         grid = dps_grid(int(nx), int(ny), int(nz))
         kp = dps_kernel_params(int(m_M), float(beta_M), int(m_D), float(beta_D), float(eta),
                                self.route, PRECISIONS[precision], int(max_n))
-        st, h = dpstokes_plan_create(float(Lx), float(Ly), float(zmin), float(zmax), MODES[mode], grid, kp)
+        wp = wall_params(dict(slip_bottom=slip_bottom, slip_top=slip_top, uw_bottom=uw_bottom, uw_top=uw_top))
+        st, h = dpstokes_plan_create_ex(float(Lx), float(Ly), float(zmin), float(zmax), MODES[mode], grid, kp, wp)
         if st != DPS_OK:
             raise DpsError(st, "dpstokes_plan_create")
         self.handle = h
@@ -293,7 +320,9 @@ class Plan:
     @classmethod
     def from_params(cls, params, with_torque, precision, max_n):
         keys = ("Lx", "Ly", "zmin", "zmax", "mode", "nx", "ny", "nz", "m_M", "beta_M", "m_D", "beta_D", "eta")
-        return cls(**{k: params[k] for k in keys}, with_torque=with_torque, precision=precision, max_n=max_n)
+        walls = {k: params[k] for k in ("slip_bottom", "slip_top", "uw_bottom", "uw_top") if k in params}
+        return cls(**{k: params[k] for k in keys}, with_torque=with_torque, precision=precision, max_n=max_n,
+                   **walls)
 
     def info(self):
         st, info = dpstokes_plan_info(self.handle)
@@ -423,6 +452,7 @@ class Server:
                                  float(params.get("beta_D", 0.0) or 0.0), float(params.get("eta", 1.0)),
                                  route, PRECISIONS[precision], int(max_n))
         r.n = n
+        r.walls = wall_params(params)
         r.positions, r.forces, r.torques = _ptr(pos), _ptr(F), _ptr(T)
         r.out_vel, r.out_angvel = _ptr(U), _ptr(W)
         st, t = dpstokes_server_submit(self.handle, r)

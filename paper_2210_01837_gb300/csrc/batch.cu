@@ -85,6 +85,7 @@ struct PlanKey {
   int32_t mode, nx, ny, nz, m_M, m_D, with_torque, precision;
   double beta_M, beta_D, eta;
   int64_t max_n;
+  dps_wall_params walls;
   bool operator==(const PlanKey& o) const { return memcmp(this, &o, sizeof(PlanKey)) == 0; }
 };
 
@@ -96,6 +97,7 @@ PlanKey key_of(const dps_serve_request& r) {
   k.m_M = r.kp.m_M; k.m_D = r.kp.with_torque ? r.kp.m_D : 0; k.with_torque = r.kp.with_torque;
   k.precision = r.kp.precision; k.beta_M = r.kp.beta_M; k.beta_D = r.kp.with_torque ? r.kp.beta_D : 0.0;
   k.eta = r.kp.eta; k.max_n = r.kp.max_n;
+  k.walls = r.walls;
   return k;
 }
 
@@ -300,8 +302,8 @@ struct Server {
             continue;
           }
           dps_plan_t plan = nullptr;
-          const dps_status st = dpstokes_plan_create(&plan, q.r.Lx, q.r.Ly, q.r.zmin, q.r.zmax, q.r.wall_mode,
-                                                     &q.r.grid, &q.r.kp);
+          const dps_status st = dpstokes_plan_create_ex(&plan, q.r.Lx, q.r.Ly, q.r.zmin, q.r.zmax, q.r.wall_mode,
+                                                        &q.r.grid, &q.r.kp, &q.r.walls);
           if (st != DPS_OK) {
             queue.erase(queue.begin() + pick);
             fail(q, st);

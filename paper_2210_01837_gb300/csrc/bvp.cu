@@ -245,7 +245,7 @@ struct SolveWs {
 // factorisation in the slot's workspace; without FACT, reuse the factorisation left there by the
 // previous call on the same slot, which must have had the same |k| (the partner -ky of a pair).
 // Returns whether the slot now holds a factorisation.
-template <typename T, bool FACT>
+template <typename T, bool FACT, bool SLIP>
 __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restrict__ band, const T* __restrict__ bandT,
                           cplx<T>* __restrict__ kbuf, cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ pws,
                           cplx<double>* __restrict__ sw, double* __restrict__ fr, int slots, int slot, int64_t kidx,
@@ -277,7 +277,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
         for (int n = 0; n < N; ++n) KB(o, n) = mk<T>((T)0, (T)0);
         continue;
       }
-      cplx<double> Sp = mk<double>(0, 0), Sm = mk<double>(0, 0), Pd = mk<double>(0, 0);
+      cplx<double> Sp = mk<double>(0, 0), Sm = mk<double>(0, 0), Pd = mk<double>(0, 0), Pm = mk<double>(0, 0);
       for (int n = 0; n < N; ++n) {
         const cplx<double> cn = scl(wid(KB(o, n)), -inv_eta / sig);
         SW(0, n) = cn;
@@ -285,9 +285,26 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
         Sp = Sp + scl(cn, bQ[n]);
         Sm = Sm + scl(cn, sgn * bQ[n]);
         Pd = Pd + scl(cn, bP[n]);
+        if (SLIP) Pm = Pm + scl(cn, sgn * bP[n]);
       }
       cplx<double> a0, a1;
-      if (g.mode == DPS_BOTTOM_WALL) {  // y(-1) = 0, y_s(+1) = 0
+      if (SLIP) {
+        // Robin rows (Eq. A12): y(-1) - l0 (2/H) y_s(-1) = g_bot and, in the slit,
+        // y(+1) + lH (2/H) y_s(+1) = g_top (above one wall: y_s(+1) = 0); y(+-1) = S+- + a0 +- a1,
+        // y_s(+1) = Pd + a1, y_s(-1) = -Pm + a1; g = Nx Ny u^W (unnormalised transform)
+        const double nxy = (double)g.nx * (double)g.ny;
+        const double al = 1.0 + g.slip0 * sH;
+        const cplx<double> Rb = mk<double>(nxy * g.uw0[o], 0.0) - Sm - scl(Pm, g.slip0 * sH);
+        if (g.mode == DPS_BOTTOM_WALL) {
+          a1 = scl(Pd, -1.0);
+          a0 = Rb + scl(a1, al);
+        } else {
+          const double be = 1.0 + g.slipH * sH;
+          const cplx<double> Rt = mk<double>(nxy * g.uwH[o], 0.0) - Sp - scl(Pd, g.slipH * sH);
+          a1 = scl(Rt - Rb, 1.0 / (al + be));
+          a0 = Rb + scl(a1, al);
+        }
+      } else if (g.mode == DPS_BOTTOM_WALL) {  // y(-1) = 0, y_s(+1) = 0
         a1 = scl(Pd, -1.0);
         a0 = a1 - Sm;
       } else {                           // y(-1) = y(+1) = 0
@@ -424,8 +441,11 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
   gt[2] = scl(ptop, 0.5 * inv_eta);
   gb[2] = scl(pbot, 0.5 * inv_eta);
   cplx<double> vtop[3], vbot[3];
+  cplx<double> dtop[2], dbot[2];  // SLIP: y_s(+-1) of the tangential DP velocities
 #pragma unroll
   for (int f = 0; f < 3; ++f) { vtop[f] = mk<double>(0, 0); vbot[f] = mk<double>(0, 0); }
+#pragma unroll
+  for (int f = 0; f < 2; ++f) { dtop[f] = mk<double>(0, 0); dbot[f] = mk<double>(0, 0); }
   for (int par = 0; par < 2; ++par) {
     const int nlast = ((N - 1 - par) & 1) ? N - 2 : N - 1;
     cplx<double> s_next[3], gacc[3];
@@ -476,7 +496,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
         const double sgn = par ? -1.0 : 1.0;
         cplx<double> cm[3];
         cplx<T> tcm2[3], tcm[3];
-        cplx<double> sp[3];
+        cplx<double> sp[3], sd[2];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
           const cplx<double> rhs = r[f] - scl(s_next[f], U);
@@ -486,6 +506,13 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
           tcm[f] = nar<T>(c0);
           tcm2[f] = zT;
           sp[f] = scl(c0, bQ[par]);
+          if (SLIP && f < 2) {
+            sd[f] = scl(c0, bP[par]);
+            if (par) {  // a1 T_1 has y_s = a1 at both ends; a0 T_0 has none
+              dtop[f] = dtop[f] + a;
+              dbot[f] = dbot[f] + a;
+            }
+          }
           vtop[f] = vtop[f] + a;
           vbot[f] = vbot[f] + scl(a, sgn);
           gacc[f] = a;  // reuse: a_par of this field
@@ -512,6 +539,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
             if (m <= nlast) {
               const cplx<double> cnew = sc[f] - scl(cm[f], tc);
               sp[f] = sp[f] + scl(cnew, bQ[m]);
+              if (SLIP && f < 2) sd[f] = sd[f] + scl(cnew, bP[m]);
               cm[f] = cnew;
               tnew = nar<T>(cnew);
             }
@@ -529,6 +557,13 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
         for (int f = 0; f < 3; ++f) {
           vtop[f] = vtop[f] + sp[f];
           vbot[f] = vbot[f] + scl(sp[f], sgn);
+        }
+        if (SLIP) {  // T_n'(-1) = (-1)^(n+1) n^2: the even part enters y_s(-1) negated
+#pragma unroll
+          for (int f = 0; f < 2; ++f) {
+            dtop[f] = dtop[f] + sd[f];
+            dbot[f] = dbot[f] + scl(sd[f], -sgn);
+          }
         }
       }
       pc1 = pn1;
@@ -549,11 +584,67 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
     const double ex = kx / kk, ey = ky / kk;
     auto Lp = [&](cplx<double> u, cplx<double> v) { return scl(u, ex) + scl(v, ey); };
     auto Tp = [&](cplx<double> u, cplx<double> v) { return scl(v, ex) - scl(u, ey); };
-    const cplx<double> u0L = scl(Lp(vbot[0], vbot[1]), -1.0), u0T = scl(Tp(vbot[0], vbot[1]), -1.0);
+    // wall data (Eq. A3): minus the DP velocity, and with slip u_DP - l0 du_DP/dz at the bottom,
+    // u_DP + lH du_DP/dz at the top for the tangential parts
+    cplx<double> eb0 = vbot[0], eb1 = vbot[1], et0 = vtop[0], et1 = vtop[1];
+    if (SLIP) {
+      eb0 = eb0 - scl(dbot[0], g.slip0 * sH);
+      eb1 = eb1 - scl(dbot[1], g.slip0 * sH);
+      et0 = et0 + scl(dtop[0], g.slipH * sH);
+      et1 = et1 + scl(dtop[1], g.slipH * sH);
+    }
+    const cplx<double> u0L = scl(Lp(eb0, eb1), -1.0), u0T = scl(Tp(eb0, eb1), -1.0);
     const cplx<double> w0 = scl(vbot[2], -1.0);
     cplx<double> AL = u0L, Az = w0, AT = u0T;
     cplx<double> BL = mk<double>(0, 0), Bz = mk<double>(0, 0), BT = mk<double>(0, 0);
-    if (g.mode == DPS_SLIT) {
+    if (SLIP && g.mode == DPS_BOTTOM_WALL) {
+      // bottom family only: Robin rows u - l0 du/dz = u0 with w(0) = w0 give
+      // AT (1 + k l0) = u0T and AL (1 + 2 k l0) + i k l0 Az = u0L
+      const double kl0 = kk * g.slip0;
+      AT = scl(u0T, 1.0 / (1.0 + kl0));
+      AL = scl(u0L - scl(mul_i(w0), kl0), 1.0 / (1.0 + 2.0 * kl0));
+    }
+    if (SLIP && g.mode == DPS_SLIT) {
+      const cplx<double> uHL = scl(Lp(et0, et1), -1.0), uHT = scl(Tp(et0, et1), -1.0);
+      const cplx<double> wH = scl(vtop[2], -1.0);
+      const double kH = kk * g.H, E = exp(-kH), E2 = E * E;
+      const double kl0 = kk * g.slip0, klH = kk * g.slipH;
+      // transverse: [1 + k l0, E (1 - k l0); E (1 - k lH), 1 + k lH] [AT; BT] = [u0T; uHT]
+      {
+        const double t11 = 1.0 + kl0, t12 = E * (1.0 - kl0), t21 = E * (1.0 - klH), t22 = 1.0 + klH;
+        const double idt = 1.0 / (t11 * t22 - t12 * t21);
+        AT = scl(scl(u0T, t22) - scl(uHT, t12), idt);
+        BT = scl(scl(uHT, t11) - scl(u0T, t21), idt);
+      }
+      // longitudinal/normal: S0 A + E N1 B = a0, SH B + E N2 A = b0 with A = (AL, Az), B = (BL, Bz),
+      // S0 = [1 + 2 k l0, i k l0; 0, 1], SH = [1 + 2 k lH, -i k lH; 0, 1],
+      // N1 = [(1 - k l0)(1 - kH) - k l0, i k (H (1 - k l0) + l0); i kH, 1 + kH],
+      // N2 = [(1 - kH)(1 - k lH) - k lH, -i k (H (1 - k lH) + lH); -i kH, 1 + kH];
+      // (S0 - E^2 N1 SH^-1 N2) A = a0 - E N1 SH^-1 b0, then B = SH^-1 (b0 - E N2 A)
+      const cplx<double> zc = mk<double>(0, 0);
+      const double sh = 1.0 / (1.0 + 2.0 * klH);
+      const cplx<double> h11 = mk<double>(sh, 0), h12 = mk<double>(0, klH * sh);  // SH^-1 = [h11 h12; 0 1]
+      const cplx<double> n11 = mk<double>((1.0 - kl0) * (1.0 - kH) - kl0, 0), n12 = mk<double>(0, kk * (g.H * (1.0 - kl0) + g.slip0));
+      const cplx<double> n21 = mk<double>(0, kH), n22 = mk<double>(1.0 + kH, 0);
+      const cplx<double> m11 = mk<double>((1.0 - kH) * (1.0 - klH) - klH, 0), m12 = mk<double>(0, -kk * (g.H * (1.0 - klH) + g.slipH));
+      const cplx<double> m21 = mk<double>(0, -kH), m22 = mk<double>(1.0 + kH, 0);
+      // P = SH^-1 N2, Q = N1 P
+      const cplx<double> p11 = h11 * m11 + h12 * m21, p12 = h11 * m12 + h12 * m22, p21 = m21, p22 = m22;
+      const cplx<double> q11 = n11 * p11 + n12 * p21, q12 = n11 * p12 + n12 * p22;
+      const cplx<double> q21 = n21 * p11 + n22 * p21, q22 = n21 * p12 + n22 * p22;
+      const cplx<double> x11 = mk<double>(1.0 + 2.0 * kl0, 0) - scl(q11, E2), x12 = mk<double>(0, kl0) - scl(q12, E2);
+      const cplx<double> x21 = zc - scl(q21, E2), x22 = mk<double>(1.0, 0) - scl(q22, E2);
+      const cplx<double> hb0 = h11 * uHL + h12 * wH, hb1 = wH;  // SH^-1 b0
+      const cplx<double> r0 = u0L - scl(n11 * hb0 + n12 * hb1, E);
+      const cplx<double> r1 = w0 - scl(n21 * hb0 + n22 * hb1, E);
+      const cplx<double> det = x11 * x22 - x12 * x21;
+      AL = cdiv(x22 * r0 - x12 * r1, det);
+      Az = cdiv(x11 * r1 - x21 * r0, det);
+      const cplx<double> e0 = uHL - scl(m11 * AL + m12 * Az, E), e1 = wH - scl(m21 * AL + m22 * Az, E);
+      BL = h11 * e0 + h12 * e1;
+      Bz = e1;
+    }
+    if (!SLIP && g.mode == DPS_SLIT) {
       const cplx<double> uHL = scl(Lp(vtop[0], vtop[1]), -1.0), uHT = scl(Tp(vtop[0], vtop[1]), -1.0);
       const cplx<double> wH = scl(vtop[2], -1.0);
       const double kH = kk * g.H;
@@ -604,7 +695,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
   return true;
 }
 
-template <typename T>
+template <typename T, bool SLIP>
 __global__ void __launch_bounds__(kBvpThreads, 3) solve_kernel(Geometry g, const double* __restrict__ band,
                                                             const T* __restrict__ bandT, cplx<T>* __restrict__ kbuf,
                                                             cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ pws,
@@ -620,11 +711,11 @@ __global__ void __launch_bounds__(kBvpThreads, 3) solve_kernel(Geometry g, const
     const int kyi = (int)(ii / (unsigned)w);
     const int kxi = kx0 + (int)(ii - (unsigned)kyi * (unsigned)w);
     const int64_t k1 = (int64_t)kyi * g.nkx + kxi;
-    const bool factored = solve_one<T, true>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k1, K);
+    const bool factored = solve_one<T, true, SLIP>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k1, K);
     if (kyi > 0 && 2 * kyi != g.ny && factored) {
       // the partner -ky has the same |k| and therefore the same banded systems
       const int64_t k2 = (int64_t)(g.ny - kyi) * g.nkx + kxi;
-      solve_one<T, false>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k2, K);
+      solve_one<T, false, SLIP>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k2, K);
     }
   }
 }
@@ -1192,7 +1283,7 @@ size_t bvp_slot_bytes(const Plan& p) {
 template <typename T>
 int bvp_occupancy_blocks(const Plan& p) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<T>, kBvpThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<T, false>, kBvpThreads, 0);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
   if (per_sm < 1) per_sm = 1;
@@ -1267,8 +1358,12 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
     cplx<double>* sw = reinterpret_cast<cplx<double>*>(base);
     double* fr = reinterpret_cast<double*>(base + 3 * N * slots * sizeof(cplx<double>));
     cplx<T>* pws = reinterpret_cast<cplx<T>*>(base + 3 * N * slots * (sizeof(cplx<double>) + sizeof(double)));
-    solve_kernel<T><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT), kbuf,
-                                                         kaux, pws, sw, fr, kx0, w);
+    if (g.slip)
+      solve_kernel<T, true><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT),
+                                                                 kbuf, kaux, pws, sw, fr, kx0, w);
+    else
+      solve_kernel<T, false><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT),
+                                                                  kbuf, kaux, pws, sw, fr, kx0, w);
   } else if (g.spectral_curl) {
     bwd_kernel<T, CB, true><<<blocks, kBvpThreads, p.kt.bwd_smem, s>>>(
         g, reinterpret_cast<const T*>(p.kt.ict), reinterpret_cast<const T*>(p.kt.icdt),

@@ -82,6 +82,11 @@ struct Geometry {
   int rec_words;     // 32-bit words per particle record
   int nkernels;      // 1 (M) or 2 (M and D): record heads
   int nslabs;        // value slabs per record: one per kernel, plus the dipole derivative slab
+  // wall conditions beyond no-slip stationary walls (Appendix A): slip lengths and uniform
+  // tangential wall velocities; slip = 1 when any of them is non-zero
+  double slip0, slipH;
+  double uw0[2], uwH[2];
+  int slip;
   int stage_cap;     // particle records the spreading kernel stages in shared memory at a time
   int rec_threads;   // threads per block of the record kernel when it stages records in shared
                      // memory (0: direct writes)

@@ -380,6 +380,11 @@ const char* dpstokes_error_string(dps_status st) {
 
 dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zmin, double zmax, int32_t wall_mode,
                                 const dps_grid* grid, const dps_kernel_params* kp) {
+  return dpstokes_plan_create_ex(out, Lx, Ly, zmin, zmax, wall_mode, grid, kp, nullptr);
+}
+
+dps_status dpstokes_plan_create_ex(dps_plan_t* out, double Lx, double Ly, double zmin, double zmax, int32_t wall_mode,
+                                   const dps_grid* grid, const dps_kernel_params* kp, const dps_wall_params* wp) {
   if (!out) return DPS_ERR_INVALID_ARG;
   *out = nullptr;
   if (!grid || !kp) return DPS_ERR_INVALID_ARG;
@@ -402,6 +407,24 @@ dps_status dpstokes_plan_create(dps_plan_t* out, double Lx, double Ly, double zm
   // kernels, torque route, particle records and bins
   const int tsize = (kp->precision == DPS_FP64) ? 2 : 1;  // 32-bit words per stored value
   if (dps::particle_geometry(g, kp, tsize) != DPS_OK) return DPS_ERR_INVALID_ARG;
+  if (wp) {
+    const double v[6] = {wp->slip_bottom, wp->slip_top, wp->uw_bottom[0], wp->uw_bottom[1], wp->uw_top[0],
+                         wp->uw_top[1]};
+    for (double x : v)
+      if (!isfinite(x)) return DPS_ERR_INVALID_ARG;
+    if (wp->slip_bottom < 0.0 || wp->slip_top < 0.0) return DPS_ERR_INVALID_ARG;
+    const bool bottom = wall_mode == DPS_BOTTOM_WALL || wall_mode == DPS_SLIT, top = wall_mode == DPS_SLIT;
+    if (!bottom && (wp->slip_bottom != 0.0 || wp->uw_bottom[0] != 0.0 || wp->uw_bottom[1] != 0.0))
+      return DPS_ERR_INVALID_ARG;
+    if (!top && (wp->slip_top != 0.0 || wp->uw_top[0] != 0.0 || wp->uw_top[1] != 0.0)) return DPS_ERR_INVALID_ARG;
+    g.slip0 = wp->slip_bottom;
+    g.slipH = wp->slip_top;
+    g.uw0[0] = wp->uw_bottom[0];
+    g.uw0[1] = wp->uw_bottom[1];
+    g.uwH[0] = wp->uw_top[0];
+    g.uwH[1] = wp->uw_top[1];
+    for (double x : v) g.slip = g.slip || x != 0.0;
+  }
 
   Plan* p = new (std::nothrow) Plan();
   if (!p) return DPS_ERR_OOM;

@@ -92,7 +92,8 @@ def test_struct_layout_matches_the_c_compiler(tmp_path):
         "dps_grid": ["nz"], "dps_kernel_params": ["beta_M", "m_D", "beta_D", "eta", "with_torque", "precision", "max_n"],
         "dps_plan_info": ["nkx", "h", "alpha_D", "launches_per_apply", "nchunks", "fft_col_width", "solve_blocks"],
         "dps_request": ["n", "positions", "torques", "out_angvel", "status"],
-        "dps_serve_request": ["wall_mode", "grid", "kp", "n", "positions", "out_angvel"],
+        "dps_serve_request": ["wall_mode", "grid", "kp", "n", "positions", "out_angvel", "walls"],
+        "dps_wall_params": ["slip_top", "uw_bottom", "uw_top"],
         "dps_serve_result": ["t_submit", "t_done"], "dps_server_stats": ["running", "bytes_resident"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dpstokes.h"', "int main(void) {"]
@@ -158,3 +159,16 @@ def test_lanczos_entry_points_reject_invalid_arguments_on_host(lib):
     assert st == binding.DPS_ERR_INVALID_ARG
     assert binding.dpstokes_tridiag_sqrt_e1([], [])[0] == binding.DPS_ERR_INVALID_ARG
     binding.dpstokes_lanczos_destroy(None)
+
+
+@pytest.mark.parametrize("mode,walls", [
+    (0, dict(slip_bottom=0.5)), (0, dict(uw_bottom=(1.0, 0.0))), (1, dict(slip_top=0.5)), (1, dict(uw_top=(0.0, 1.0))),
+    (2, dict(slip_bottom=-1.0)), (2, dict(slip_top=float("inf"))), (2, dict(uw_bottom=(float("nan"), 0.0))),
+])
+def test_invalid_wall_conditions_rejected_on_host(lib, mode, walls):
+    from paper_2210_01837_gb300 import binding
+    grid = binding.dps_grid(128, 128, 65)
+    kp = binding.dps_kernel_params(6, 10.2, 0, 0.0, 1.0, 0, 0, 100)
+    wp = binding.wall_params(walls)
+    st, h = binding.dpstokes_plan_create_ex(64.0, 64.0, 0.0, 12.0, mode, grid, kp, wp)
+    assert st == binding.DPS_ERR_INVALID_ARG and not h.value
