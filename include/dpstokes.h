@@ -348,6 +348,18 @@ dps_status dpstokes_lanczos_sample(dps_lanczos_t lz, int64_t n, const double* po
 
 void dpstokes_lanczos_destroy(dps_lanczos_t lz);
 
+/* Stochastic drift by random finite differences (Sec. IV.C, footnote: two extra solves per step):
+ * out = (1/delta) [M(q + delta/2 W) - M(q - delta/2 W)] [W; 0], whose average over a standard
+ * normal W is the divergence of the mobility with respect to the positions q (for spheres the
+ * configuration is the positions only, so the torque part of the vector multiplied is zero).
+ * positions, W: device [n][3]; out: device [n][3] (velocity part), followed by [n][3] (angular
+ * part) for a plan with torques; delta > 0 (a length; the displaced heights must stay legal, else
+ * the device status reports DPS_ERR_OUT_OF_DOMAIN).  Two products on `stream` through the plan's
+ * staging buffers (not concurrently with dpstokes_apply_host on the same plan); no host
+ * synchronisation, graph-capturable. */
+dps_status dpstokes_rfd_drift(dps_plan_t plan, int64_t n, const double* positions, const double* W,
+                              double delta, double* out, void* stream);
+
 /* Host utility (no GPU): y = T^{1/2} e_1 for the symmetric tridiagonal T with diagonal alpha[j] and
  * off-diagonal beta[j-1] (beta may be NULL for j = 1), 1 <= j <= 128; the step the sampler takes on
  * the host each iteration. */

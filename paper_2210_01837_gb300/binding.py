@@ -146,6 +146,7 @@ def load(path=None):
                                            ctypes.POINTER(_D), _P]),
         "dpstokes_lanczos_destroy": (None, [_P]),
         "dpstokes_tridiag_sqrt_e1": (_I32, [_I32, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+        "dpstokes_rfd_drift": (_I32, [_P, _I64, _P, _P, _D, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -319,10 +320,10 @@ class Plan:
 
     @classmethod
     def from_params(cls, params, with_torque, precision, max_n):
-        keys = ("Lx", "Ly", "zmin", "zmax", "mode", "nx", "ny", "nz", "m_M", "beta_M", "m_D", "beta_D", "eta")
-        walls = {k: params[k] for k in ("slip_bottom", "slip_top", "uw_bottom", "uw_top") if k in params}
-        return cls(**{k: params[k] for k in keys}, with_torque=with_torque, precision=precision, max_n=max_n,
-                   **walls)
+        keys = ("Lx", "Ly", "zmin", "zmax", "mode", "nx", "ny", "nz", "m_M", "beta_M")
+        optional = ("m_D", "beta_D", "eta", "slip_bottom", "slip_top", "uw_bottom", "uw_top")
+        return cls(**{k: params[k] for k in keys}, **{k: params[k] for k in optional if k in params},
+                   with_torque=with_torque, precision=precision, max_n=max_n)
 
     def info(self):
         st, info = dpstokes_plan_info(self.handle)
@@ -486,6 +487,24 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---- stochastic drift (random finite differences) --------------------------------------------
+def dpstokes_rfd_drift(plan, n, positions, W, delta, out, stream):
+    return load().dpstokes_rfd_drift(plan, int(n), positions, W, float(delta), out, stream)
+
+
+def rfd_drift(plan, pos, W, delta, out=None, stream=None):
+    """(1/delta)[M(q + delta/2 W) - M(q - delta/2 W)][W; 0] for a Plan; pos, W CUDA float64 [n, 3].
+    Returns a CUDA tensor [n, 3] (or [2n, 3] with torques: velocity rows, then angular rows)."""
+    import torch
+    n = pos.shape[0]
+    if out is None:
+        out = torch.empty(((2 if plan.with_torque else 1) * n, 3), dtype=torch.float64, device=pos.device)
+    st = dpstokes_rfd_drift(plan.handle, n, _ptr(pos), _ptr(W), delta, _ptr(out), _stream(stream))
+    if st != DPS_OK:
+        raise DpsError(st, "dpstokes_rfd_drift")
+    return out
 
 
 # ---- Brownian increments (Lanczos) -----------------------------------------------------------

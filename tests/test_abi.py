@@ -172,3 +172,8 @@ def test_invalid_wall_conditions_rejected_on_host(lib, mode, walls):
     wp = binding.wall_params(walls)
     st, h = binding.dpstokes_plan_create_ex(64.0, 64.0, 0.0, 12.0, mode, grid, kp, wp)
     assert st == binding.DPS_ERR_INVALID_ARG and not h.value
+
+
+def test_rfd_drift_rejects_invalid_arguments_on_host(lib):
+    from paper_2210_01837_gb300 import binding
+    assert binding.dpstokes_rfd_drift(None, 4, None, None, 1e-3, None, None) == binding.DPS_ERR_INVALID_ARG
