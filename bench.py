@@ -486,7 +486,7 @@ def main():
         roofline = {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves)", "achieved": round(solve_tflops, 4),
                     "peak": round(FP64_NOMINAL_TFLOPS, 3), "unit": "TFLOP/s",
                     "frac": round(solve_tflops / FP64_NOMINAL_TFLOPS, 4),
-                    "traffic": measured_traffic("solve_kernel<float>") if div == 1 and not args.nz else None,
+                    "traffic": measured_traffic("solve_kernel<float, 0>") if div == 1 and not args.nz else None,
                     "traffic_source": "profiles/traffic.json (ncu dram bytes, scaled by wavenumbers)",
                     "peak_kind": "FP64 nominal from unit counts x max clock"}
     else:

@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(256) interp_kernel(Geometry g, int64_t n, cons
                                                      const int* __restrict__ order, double* __restrict__ U,
                                                      double* __restrict__ W) {
   constexpr int NG = 32 / LR;
-  constexpr int UR = 8;
+  constexpr int UR = 4;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
