@@ -51,14 +51,7 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)(m << 29));
 }
 
-__device__ __forceinline__ float d2f(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned s = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-  if (e <= 0) return __uint_as_float(s);
-  if (e >= 255) return __uint_as_float(s | 0x7f800000u);
-  return __uint_as_float(s | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
-}
+__device__ __forceinline__ float d2f(double d) { return narrow_bits(d); }
 
 template <typename T> __device__ __forceinline__ double widen(T v);
 template <> __device__ __forceinline__ double widen<float>(float v) { return f2d(v); }

@@ -214,6 +214,18 @@ __device__ __forceinline__ double widen_bits(float f) {
   return __hiloint2double((int)((b & 0x80000000u) | (de << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// double -> float with integer operations only, rounding toward zero (|result| <= |d|); exact
+// exponent handling for normal floats, results below the float normal range become zero, above it
+// infinity (NaN inputs are not expected: callers check finiteness first).
+__device__ __forceinline__ float narrow_bits(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned s = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  if (e <= 0) return __uint_as_float(s);
+  if (e >= 255) return __uint_as_float(s | 0x7f800000u);
+  return __uint_as_float(s | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
 // status bits written by kernels
 enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4 };
 

@@ -39,8 +39,9 @@ __device__ __forceinline__ double es_eval(double t, const EsKernel& k) {
 
 __device__ __forceinline__ float es_eval_f(double t, const EsKernel& k) {
   // the offset t is formed in double by the caller (a difference of nearby large numbers); the
-  // rest runs in float (a division or a conversion in double occupies the scarce FP64 pipe)
-  const float r = (float)t * k.inv_alpha_f;
+  // rest runs in float, narrowed on the integer pipe toward zero (a division or a conversion in
+  // double occupies the scarce FP64 pipe; toward zero, a node inside the support stays inside)
+  const float r = narrow_bits(t) * k.inv_alpha_f;
   if (fabsf(r) > 1.0f) return 0.0f;
   const float q = fmaxf(0.0f, 1.0f - r * r);
   return expf(k.beta_f * (sqrtf(q) - 1.0f)) * k.inv_norm_f;
@@ -61,9 +62,10 @@ __device__ __forceinline__ double esd_eval(double t, const EsKernel& k) {
 
 __device__ __forceinline__ float esd_eval_f(double t, const EsKernel& k) {
   // the truncation is decided in double, as on the double path: a node cut on one side and kept on
-  // the other would change a result by |phi'(cut)|, far above float rounding
-  if (fabs(t) > k.cut) return 0.0f;
-  const float r = (float)t * k.inv_alpha_f;
+  // the other would change a result by |phi'(cut)|, far above float rounding.  The bit patterns of
+  // non-negative doubles order as the values, so the test runs on the integer pipe.
+  if ((__double_as_longlong(t) & 0x7fffffffffffffffLL) > __double_as_longlong(k.cut)) return 0.0f;
+  const float r = narrow_bits(t) * k.inv_alpha_f;
   const float s = sqrtf(fmaxf(0.0f, 1.0f - r * r));
   return -k.beta_over_alpha_f * r / s * expf(k.beta_f * (s - 1.0f)) * k.inv_norm_f;
 }
@@ -150,9 +152,15 @@ __global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__
     if (ok) {
       const int ax = first_node(xw, g.h, g.inv_h, k.alpha);
       const int ay = first_node(yw, g.h, g.inv_h, k.alpha);
-      for (int i = 0; i < g.pxc; ++i) {
-        ph[i] = (i < k.px) ? es_t<T>((double)(ax + i) * g.h - xw, k) : (T)0;
-        ph[g.pxc + i] = (i < k.px) ? es_t<T>((double)(ay + i) * g.h - yw, k) : (T)0;
+      const double tx0 = (double)ax * g.h - xw, ty0 = (double)ay * g.h - yw;  // offsets of the first nodes
+      {
+        double tx = tx0, ty = ty0;  // node offsets by running sums (one add each per slot)
+        for (int i = 0; i < g.pxc; ++i) {
+          ph[i] = (i < k.px) ? es_t<T>(tx, k) : (T)0;
+          ph[g.pxc + i] = (i < k.px) ? es_t<T>(ty, k) : (T)0;
+          tx += g.h;
+          ty += g.h;
+        }
       }
       hd.x = wrap_idx(ax, g.nx);
       hd.y = wrap_idx(ay, g.ny);
@@ -183,9 +191,12 @@ __global__ void records_kernel(Geometry g, int64_t n, const double* __restrict__
         // derivative slab: phi' in x and y, and d/dz of the imaged z factor (the exact derivative
         // of the negatively imaged envelope)
         T* pd = tv + 6 + 2 * stride;
+        double tx = tx0, ty = ty0;
         for (int i = 0; i < g.pxc; ++i) {
-          pd[i] = (i < k.px) ? esd_t<T>((double)(ax + i) * g.h - xw, k) : (T)0;
-          pd[g.pxc + i] = (i < k.px) ? esd_t<T>((double)(ay + i) * g.h - yw, k) : (T)0;
+          pd[i] = (i < k.px) ? esd_t<T>(tx, k) : (T)0;
+          pd[g.pxc + i] = (i < k.px) ? esd_t<T>(ty, k) : (T)0;
+          tx += g.h;
+          ty += g.h;
         }
         for (int i = 0; i < g.lzc; ++i) {
           T v = (T)0;
