@@ -461,9 +461,48 @@ __device__ __forceinline__ void spread_fused_list(const Geometry& g, const uint3
   }
 }
 
+// Spectral-curl route with coinciding supports (m_M = m_D): each listed candidate adds F Delta_M to
+// the force fields and tau Delta_D to the torque fields in one walk (six accumulators per plane).
+template <typename T, int ZC>
+__device__ __forceinline__ void spread_six_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl,
+                                                int rw, int gx, int gy, int zb, T (&acc)[ZC][6]) {
+  const int stride = 2 * g.pxc + g.lzc;
+  const int px = g.kM.px;
+  for (int e = 0; e < nl; ++e) {
+    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const int4 hd = reinterpret_cast<const int4*>(r)[0];
+    if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
+    int dx = gx - hd.x;
+    if (dx < 0) dx += g.nx;
+    if (dx >= px) continue;
+    int dy = gy - hd.y;
+    if (dy < 0) dy += g.ny;
+    const T* tv = reinterpret_cast<const T*>(r + 8);
+    const T* pm = tv + 6;           // monopole phi
+    const T* pd = tv + 6 + stride;  // dipole phi
+    const T mxy = pm[dx] * pm[g.pxc + dy], dxy = pd[dx] * pd[g.pxc + dy];
+    const T f0 = tv[0] * mxy, f1 = tv[1] * mxy, f2 = tv[2] * mxy;
+    const T t0 = tv[3] * dxy, t1 = tv[4] * dxy, t2 = tv[5] * dxy;
+#pragma unroll
+    for (int zz = 0; zz < ZC; ++zz) {
+      const int iz = zb + zz - hd.z;
+      if (iz >= 0 && iz < hd.w) {
+        const T mz = pm[2 * g.pxc + iz], dz = pd[2 * g.pxc + iz];
+        acc[zz][0] += f0 * mz;
+        acc[zz][1] += f1 * mz;
+        acc[zz][2] += f2 * mz;
+        acc[zz][3] += t0 * dz;
+        acc[zz][4] += t1 * dz;
+        acc[zz][5] += t2 * dz;
+      }
+    }
+  }
+}
+
 // MODE 0: forces only (3 fields); 1: spectral-curl torques (force fields, then torque fields, one
 // pass each); 2: kernel-derivative torques (the force density and the half-curl sources in one pass
-// over the 3 fields); 3: as 2 with coinciding supports (one list, one walk per candidate).
+// over the 3 fields); 3: as 2 with coinciding supports (one list, one walk per candidate); 4: as 1
+// with coinciding supports (one walk per candidate writes all six fields).
 template <typename T, int MODE, int ZC>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
@@ -555,6 +594,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     const int ncand = min(passed, win1) - win0;
     if (ncand <= 0 && round > 0) break;
     constexpr bool TWO = MODE == 1 || MODE == 2;
+    constexpr int NA = MODE == 4 ? 6 : 3;  // fields accumulated per pass
     const bool once = ncand <= g.stage_cap;
     int nl0 = 0, nl1 = 0;
     int* wl0 = s_wl[warp][0];
@@ -565,16 +605,17 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
       build_row_lists<TWO>(g, srec, max(ncand, 0), rw, gy, wl0, wl1, nl0, nl1);
     }
     // the candidates of list set (wl0, wl1) into the accumulators of pass K
-    auto apply = [&](int K, T (&acc)[ZC][3], int zb) {
-      if (MODE == 3) {
+    auto apply = [&](int K, T (&acc)[ZC][NA], int zb) {
+      if constexpr (MODE == 4) {
+        spread_six_list<T, ZC>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+      } else if constexpr (MODE == 3) {
         spread_fused_list<T, ZC>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
-      } else if (MODE == 2) {
+      } else if constexpr (MODE == 2) {
         spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
         spread_curl_list<T, ZC>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
-      } else if (K == 0) {
-        spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
       } else {
-        spread_list<T, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+        if (K == 0) spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+        else spread_list<T, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
       }
     };
     // one pass per field triple (spectral curl: force fields, then torque fields), ZC planes at a time
@@ -582,11 +623,11 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
 #pragma unroll
     for (int K = 0; K < NPASS; ++K) {
       for (int zb = clo; zb <= chi; zb += ZC) {
-        T acc[ZC][3];
+        T acc[ZC][NA];
 #pragma unroll
         for (int zz = 0; zz < ZC; ++zz)
 #pragma unroll
-          for (int f = 0; f < 3; ++f) {
+          for (int f = 0; f < NA; ++f) {
             T v = (T)0;
             if (round > 0 && active && zb + zz <= chi)
               v = grid[(3 * K + f) * fstride + (size_t)(zb + zz) * plane + node];
@@ -609,7 +650,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
           for (int zz = 0; zz < ZC; ++zz) {
             if (zb + zz <= chi) {
 #pragma unroll
-              for (int f = 0; f < 3; ++f) grid[(3 * K + f) * fstride + (size_t)(zb + zz) * plane + node] = acc[zz][f];
+              for (int f = 0; f < NA; ++f) grid[(3 * K + f) * fstride + (size_t)(zb + zz) * plane + node] = acc[zz][f];
             }
           }
         }
@@ -948,6 +989,7 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s) {
 }
 
 constexpr int kZC6F = 16, kZC6D = 8, kZC3F = 16, kZC3D = 8;  // z chunk of a pass: 3 fields x ZC accumulators
+constexpr int kZCSF = 8, kZCSD = 4;                            // six fields at once: 6 x ZC accumulators
 
 template <typename T>
 size_t spread_smem(const Plan& p) {
@@ -961,8 +1003,10 @@ size_t spread_smem(const Plan& p) {
 template <typename T>
 int spread_prepare(Plan& p) {
   constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
+  constexpr int ZCS = sizeof(T) == 4 ? kZCSF : kZCSD;
   if (!(allow_smem(spread_kernel<T, 1, ZC6>) && allow_smem(spread_kernel<T, 0, ZC3>) &&
-        allow_smem(spread_kernel<T, 2, ZC3>) && allow_smem(spread_kernel<T, 3, ZC3>)))
+        allow_smem(spread_kernel<T, 2, ZC3>) && allow_smem(spread_kernel<T, 3, ZC3>) &&
+        allow_smem(spread_kernel<T, 4, ZCS>)))
     return 0;
   int dev = 0, optin = 0;
   cudaFuncAttributes fa;  // the three modes declare the same static shared arrays
@@ -987,8 +1031,11 @@ void launch_spread(const Plan& p, cudaStream_t s) {
   const unsigned blocks = (unsigned)(p.g.nbx * p.g.nby);
   constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
   const size_t sm = spread_smem<T>(p);
+  constexpr int ZCS = sizeof(T) == 4 ? kZCSF : kZCSD;
   T* grid = reinterpret_cast<T*>(p.grid);
-  if (p.g.spectral_curl)
+  if (p.g.spectral_curl && p.g.kM.px == p.g.kD.px)  // equal m: the two supports coincide
+    spread_kernel<T, 4, ZCS><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
+  else if (p.g.spectral_curl)
     spread_kernel<T, 1, ZC6><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
   else if (p.g.torque_deriv && p.g.kM.px == p.g.kD.px)  // equal m: the two supports coincide
     spread_kernel<T, 3, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
