@@ -53,6 +53,18 @@ __device__ __forceinline__ double f2d(float f) {
 
 __device__ __forceinline__ float d2f(double d) { return narrow_bits(d); }
 
+// 1/d for the pivots of the factorisation (|d| well inside the float range) by Newton-Raphson from a
+// float seed: x0 = approximate float reciprocal of the narrowed d (relative error about 2^-22),
+// then x <- x + x (1 - d x) twice in double, which squares the error each time (2^-44, then the
+// double rounding level).  Four FP64 instructions instead of an IEEE double division; the result
+// may differ from the correctly rounded quotient in the last bit.
+__device__ __forceinline__ double recip_nr(double d) {
+  double x = widen_bits(__fdividef(1.0f, narrow_bits(d)));
+  x = fma(x, fma(-d, x, 1.0), x);
+  x = fma(x, fma(-d, x, 1.0), x);
+  return x;
+}
+
 template <typename T> __device__ __forceinline__ double widen(T v);
 template <> __device__ __forceinline__ double widen<float>(float v) { return f2d(v); }
 template <> __device__ __forceinline__ double widen<double>(double v) { return v; }
@@ -354,7 +366,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
       if (n > par) {
         double rho;
         if (FACT) {
-          rho = 1.0 / ((sig - kap * bd[n]) - U * t_next);
+          rho = recip_nr((sig - kap * bd[n]) - U * t_next);
           const double t = rho * (-kap * bl[n]);
           FR(0, n) = rho;
           FR(1, n) = t;

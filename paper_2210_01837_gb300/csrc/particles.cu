@@ -857,6 +857,100 @@ __global__ void __launch_bounds__(256) interp_curl_kernel(Geometry g, int64_t n,
   }
 }
 
+// Spectral-curl route with coinciding supports (m_M = m_D): one walk over the common support reads
+// the velocity (fields 0..2) and the half-curl (fields 3..5) of each node and returns
+// U_j = h^2 sum w_c u Delta_M and Omega_j = h^2 sum w_c omega Delta_D (the row walk of interp_kernel).
+template <typename T, int LR>
+__global__ void __launch_bounds__(256) interp_pair_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec,
+                                                          const T* __restrict__ grid, const T* __restrict__ wz,
+                                                          const int* __restrict__ order, double* __restrict__ U,
+                                                          double* __restrict__ W) {
+  constexpr int NG = 32 / LR;
+  constexpr int UR = 4;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int64_t j = order[i];
+  const uint32_t* r = rec + (size_t)j * g.rec_words;
+  const T* tv = reinterpret_cast<const T*>(r + 8);
+  const int lx = lane % LR, grp = lane / LR;
+  const size_t rowlen = (size_t)2 * g.pitch;
+  const size_t plane = (size_t)g.ny * rowlen;
+  const size_t fstride = plane * g.nz;
+  const int stride = 2 * g.pxc + g.lzc;
+  const T* pm = tv + 6;           // monopole phi
+  const T* pd = tv + 6 + stride;  // dipole phi
+  const int4 hd = reinterpret_cast<const int4*>(r)[0];
+  const int px = g.kM.px;
+  const bool vx = grp < NG && lx < px;
+  int xi = hd.x + lx;
+  if (xi >= g.nx) xi -= g.nx;
+  const T mx = vx ? pm[lx] : (T)0, dxw = vx ? pd[lx] : (T)0;
+  const unsigned magic = (65536u + (unsigned)px - 1u) / (unsigned)px;  // ceil(2^16 / px)
+  const int rows = hd.w * px;
+  const T* gbase = grid + xi;
+  T a0 = 0, a1 = 0, a2 = 0, o0 = 0, o1 = 0, o2 = 0;
+  for (int r0 = grp; r0 < rows; r0 += NG * UR) {
+    T v[6][UR], wm[UR], wd[UR];
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+      const int rr = r0 + u * NG;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) v[f][u] = (T)0;
+      wm[u] = wd[u] = (T)0;
+      if (vx && rr < rows) {
+        const int iz = (int)(((unsigned)rr * magic) >> 16), iy = rr - iz * px;
+        const int c = hd.z + iz;
+        int yi = hd.y + iy;
+        if (yi >= g.ny) yi -= g.ny;
+        const T w = wz[c];
+        wm[u] = pm[2 * g.pxc + iz] * w * pm[g.pxc + iy] * mx;
+        wd[u] = pd[2 * g.pxc + iz] * w * pd[g.pxc + iy] * dxw;
+        const T* gp = gbase + (size_t)c * plane + (size_t)yi * rowlen;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) v[f][u] = gp[f * fstride];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+      a0 += v[0][u] * wm[u];
+      a1 += v[1][u] * wm[u];
+      a2 += v[2][u] * wm[u];
+      o0 += v[3][u] * wd[u];
+      o1 += v[4][u] * wd[u];
+      o2 += v[5][u] * wd[u];
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    o0 += __shfl_xor_sync(0xffffffffu, o0, off);
+    o1 += __shfl_xor_sync(0xffffffffu, o1, off);
+    o2 += __shfl_xor_sync(0xffffffffu, o2, off);
+  }
+  if (lane == 0) {
+    const double h2 = g.h * g.h;
+    if (sizeof(T) == 4) {  // float path: scale in float, widen on the integer pipe
+      const float h2f = (float)h2;
+      U[3 * j] = widen_bits((float)a0 * h2f);
+      U[3 * j + 1] = widen_bits((float)a1 * h2f);
+      U[3 * j + 2] = widen_bits((float)a2 * h2f);
+      W[3 * j] = widen_bits((float)o0 * h2f);
+      W[3 * j + 1] = widen_bits((float)o1 * h2f);
+      W[3 * j + 2] = widen_bits((float)o2 * h2f);
+    } else {
+      U[3 * j] = h2 * (double)a0;
+      U[3 * j + 1] = h2 * (double)a1;
+      U[3 * j + 2] = h2 * (double)a2;
+      W[3 * j] = h2 * (double)o0;
+      W[3 * j + 1] = h2 * (double)o1;
+      W[3 * j + 2] = h2 * (double)o2;
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -1065,6 +1159,15 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
       if (fused) interp_curl_kernel<T, 16, true><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
       else interp_curl_kernel<T, 16, false><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
     }
+    return;
+  }
+  if (p.g.spectral_curl && p.g.kM.px == p.g.kD.px) {  // equal m: one walk for U and Omega
+    if (p.g.pxc <= 6)
+      interp_pair_kernel<T, 6><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+    else if (p.g.pxc <= 8)
+      interp_pair_kernel<T, 8><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
+    else
+      interp_pair_kernel<T, 16><<<blocks, threads, 0, s>>>(p.g, n, p.records, grid, wz, p.sorted, U, W);
     return;
   }
   if (p.g.pxc <= 6)
