@@ -24,6 +24,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "dps_internal.cuh"
 
@@ -310,6 +311,39 @@ __device__ __forceinline__ bool cyc_overlap(int a, int len_a, int b, int len_b, 
 constexpr int kCandCap = 2048;
 constexpr int kStage = 128;  // candidate records staged in shared memory at a time
 
+// Candidate e of a list: a warp-wide row list (int staged indices) or, with LANE, this lane's own
+// list of byte indices stored [e][32 lanes].
+template <bool LANE>
+__device__ __forceinline__ int list_entry(const void* wl, int e) {
+  if (LANE) return (int)static_cast<const unsigned char*>(wl)[e * 32 + (threadIdx.x & 31)];
+  return static_cast<const int*>(wl)[e];
+}
+
+constexpr int kLaneCap = 32;  // entries of a per-lane candidate list
+
+// Per lane (node column gx) of a warp, the candidates of the warp's row list whose x support covers
+// gx (record head K), as byte indices into the staged records; returns the count, which may exceed
+// kLaneCap (the caller then keeps the row list).  A candidate covers about 6 of the 32 columns, so
+// the walks over the z chunks visit about a fifth of the row list per lane.
+template <int K>
+__device__ __forceinline__ int build_lane_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl, int rw,
+                                               int gx, bool active, unsigned char* ll) {
+  const int lane = threadIdx.x & 31;
+  const int px = (K == 0) ? g.kM.px : g.kD.px;
+  int cnt = 0;
+  for (int e = 0; e < nl; ++e) {
+    const int idx = wl[e];
+    const int4 hd = reinterpret_cast<const int4*>(srec + (size_t)idx * rw)[K];
+    int dx = gx - hd.x;
+    if (dx < 0) dx += g.nx;
+    if (active && dx < px) {
+      if (cnt < kLaneCap) ll[cnt * 32 + lane] = (unsigned char)idx;
+      ++cnt;
+    }
+  }
+  return cnt;
+}
+
 // Per warp (one tile row gy), the staged candidates whose support rows include gy, one list per
 // kernel (monopole / dipole, the latter when TWO), built with warp ballots; the z-chunk loops then
 // walk only these.
@@ -349,13 +383,13 @@ __device__ __forceinline__ void build_row_lists(const Geometry& g, const uint32_
 
 // Accumulate the listed candidates of kernel K into the thread's node column (the three fields of
 // that kernel), planes [zb, zb + ZC).
-template <typename T, int ZC, int K>
-__device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl, int rw,
+template <typename T, int ZC, int K, bool LANE>
+__device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* srec, const void* wl, int nl, int rw,
                                             int gx, int gy, int zb, T (&acc)[ZC][3]) {
   const int stride = 2 * g.pxc + g.lzc;
   const int px = (K == 0) ? g.kM.px : g.kD.px;
   for (int e = 0; e < nl; ++e) {
-    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const uint32_t* r = srec + (size_t)list_entry<LANE>(wl, e) * rw;
     const int4 hd = reinterpret_cast<const int4*>(r)[K];
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
@@ -384,13 +418,13 @@ __device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* s
 // (1/2) grad Delta_D x tau into the thread's node column (the three force-density fields), planes
 // [zb, zb + ZC).  The records hold tau / 2.  With gx = phi'x phiy phiz, gy = phix phi'y phiz and
 // gz = phix phiy phi'z, grad Delta x tau = (gy tz - gz ty, gz tx - gx tz, gx ty - gy tx).
-template <typename T, int ZC>
-__device__ __forceinline__ void spread_curl_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl,
+template <typename T, int ZC, bool LANE>
+__device__ __forceinline__ void spread_curl_list(const Geometry& g, const uint32_t* srec, const void* wl, int nl,
                                                  int rw, int gx, int gy, int zb, T (&acc)[ZC][3]) {
   const int stride = 2 * g.pxc + g.lzc;
   const int px = g.kD.px;
   for (int e = 0; e < nl; ++e) {
-    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const uint32_t* r = srec + (size_t)list_entry<LANE>(wl, e) * rw;
     const int4 hd = reinterpret_cast<const int4*>(r)[1];
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
@@ -422,13 +456,13 @@ __device__ __forceinline__ void spread_curl_list(const Geometry& g, const uint32
 
 // Kernel-derivative route with coinciding supports (m_M = m_D, so both record heads are equal): each
 // listed candidate adds F Delta_M and (1/2) grad Delta_D x tau in one walk.
-template <typename T, int ZC>
-__device__ __forceinline__ void spread_fused_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl,
+template <typename T, int ZC, bool LANE>
+__device__ __forceinline__ void spread_fused_list(const Geometry& g, const uint32_t* srec, const void* wl, int nl,
                                                   int rw, int gx, int gy, int zb, T (&acc)[ZC][3]) {
   const int stride = 2 * g.pxc + g.lzc;
   const int px = g.kM.px;
   for (int e = 0; e < nl; ++e) {
-    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const uint32_t* r = srec + (size_t)list_entry<LANE>(wl, e) * rw;
     const int4 hd = reinterpret_cast<const int4*>(r)[0];
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
@@ -463,13 +497,13 @@ __device__ __forceinline__ void spread_fused_list(const Geometry& g, const uint3
 
 // Spectral-curl route with coinciding supports (m_M = m_D): each listed candidate adds F Delta_M to
 // the force fields and tau Delta_D to the torque fields in one walk (six accumulators per plane).
-template <typename T, int ZC>
-__device__ __forceinline__ void spread_six_list(const Geometry& g, const uint32_t* srec, const int* wl, int nl,
+template <typename T, int ZC, bool LANE>
+__device__ __forceinline__ void spread_six_list(const Geometry& g, const uint32_t* srec, const void* wl, int nl,
                                                 int rw, int gx, int gy, int zb, T (&acc)[ZC][6]) {
   const int stride = 2 * g.pxc + g.lzc;
   const int px = g.kM.px;
   for (int e = 0; e < nl; ++e) {
-    const uint32_t* r = srec + (size_t)wl[e] * rw;
+    const uint32_t* r = srec + (size_t)list_entry<LANE>(wl, e) * rw;
     const int4 hd = reinterpret_cast<const int4*>(r)[0];
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
@@ -514,6 +548,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   __shared__ int s_cand[kCandCap];
   __shared__ int s_warp[kSpreadThreads / 32];
   __shared__ int s_wl[kSpreadThreads / 32][2][kStage];  // per-warp row lists (monopole, dipole)
+  __shared__ unsigned char s_ll[kSpreadThreads / 32][2][kLaneCap * 32];  // per-lane lists of the row lists
   const int clo = zrange[0], chi = zrange[1];
   if (chi < clo) return;
   const int bx = blockIdx.x % g.nbx, by = blockIdx.x / g.nbx;
@@ -599,24 +634,41 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     int nl0 = 0, nl1 = 0;
     int* wl0 = s_wl[warp][0];
     int* wl1 = s_wl[warp][1];
+    unsigned char* ll0 = s_ll[warp][0];
+    unsigned char* ll1 = s_ll[warp][1];
+    int lc0 = 0, lc1 = 0;
+    bool lanes = false;  // warp-uniform: walk per-lane lists instead of the row lists
     if (once) {
       stage(0, max(ncand, 0));
       __syncthreads();
       build_row_lists<TWO>(g, srec, max(ncand, 0), rw, gy, wl0, wl1, nl0, nl1);
+      lc0 = build_lane_list<0>(g, srec, wl0, nl0, rw, gx, active, ll0);
+      if (TWO) lc1 = build_lane_list<1>(g, srec, wl1, nl1, rw, gx, active, ll1);
+      lanes = !__any_sync(0xffffffffu, lc0 > kLaneCap || lc1 > kLaneCap);
+      __syncwarp();
     }
     // the candidates of list set (wl0, wl1) into the accumulators of pass K
-    auto apply = [&](int K, T (&acc)[ZC][NA], int zb) {
+    auto walk = [&](auto lane_tag, int K, T (&acc)[ZC][NA], int zb) {
+      constexpr bool L = decltype(lane_tag)::value;
+      const void* w0 = L ? static_cast<const void*>(ll0) : static_cast<const void*>(wl0);
+      const void* w1 = L ? static_cast<const void*>(ll1) : static_cast<const void*>(wl1);
+      const int n0 = L ? lc0 : nl0, n1 = L ? lc1 : nl1;
       if constexpr (MODE == 4) {
-        spread_six_list<T, ZC>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+        spread_six_list<T, ZC, L>(g, srec, w0, n0, rw, gx, gy, zb, acc);
       } else if constexpr (MODE == 3) {
-        spread_fused_list<T, ZC>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
+        spread_fused_list<T, ZC, L>(g, srec, w0, n0, rw, gx, gy, zb, acc);
       } else if constexpr (MODE == 2) {
-        spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
-        spread_curl_list<T, ZC>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+        spread_list<T, ZC, 0, L>(g, srec, w0, n0, rw, gx, gy, zb, acc);
+        spread_curl_list<T, ZC, L>(g, srec, w1, n1, rw, gx, gy, zb, acc);
       } else {
-        if (K == 0) spread_list<T, ZC, 0>(g, srec, wl0, nl0, rw, gx, gy, zb, acc);
-        else spread_list<T, ZC, 1>(g, srec, wl1, nl1, rw, gx, gy, zb, acc);
+        if (K == 0) spread_list<T, ZC, 0, L>(g, srec, w0, n0, rw, gx, gy, zb, acc);
+        else spread_list<T, ZC, 1, L>(g, srec, w1, n1, rw, gx, gy, zb, acc);
       }
+    };
+    // the candidates of the current lists into the accumulators of pass K
+    auto apply = [&](int K, T (&acc)[ZC][NA], int zb) {
+      if (lanes) walk(std::true_type{}, K, acc, zb);
+      else walk(std::false_type{}, K, acc, zb);
     };
     // one pass per field triple (spectral curl: force fields, then torque fields), ZC planes at a time
     constexpr int NPASS = MODE == 1 ? 2 : 1;
@@ -640,7 +692,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
             stage(i0, cnt);
             __syncthreads();
             build_row_lists<TWO>(g, srec, cnt, rw, gy, wl0, wl1, nl0, nl1);
-            if (active) apply(K, acc, zb);
+            if (active) walk(std::false_type{}, K, acc, zb);
           }
         } else if (active) {
           apply(K, acc, zb);
