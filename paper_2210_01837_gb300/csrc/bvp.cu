@@ -871,7 +871,7 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
 // inside the contraction loops.
 // ---------------------------------------------------------------------------------------------
 constexpr int kLaneK = 32;
-template <typename T> __host__ __device__ constexpr int fwd_pg() { return sizeof(T) == 4 ? 12 : 6; }
+template <typename T> __host__ __device__ constexpr int fwd_pg() { return sizeof(T) == 4 ? 8 : 6; }
 template <typename T> __host__ __device__ constexpr int bwd_pg() { return sizeof(T) == 4 ? 8 : 4; }
 template <typename T> __host__ __device__ constexpr int bwd_warps() { return sizeof(T) == 4 ? 5 : 10; }
 
