@@ -802,7 +802,7 @@ __global__ void __launch_bounds__(256) interp_kernel(Geometry g, int64_t n, cons
 // m_M = m_D): one walk reads each velocity node once for both outputs; otherwise U is gathered over
 // the monopole support first and Omega over the dipole support.
 template <typename T, int LR, bool FUSED>
-__global__ void __launch_bounds__(256) interp_curl_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec,
+__global__ void __launch_bounds__(256, 4) interp_curl_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec,
                                                           const T* __restrict__ grid, const T* __restrict__ wz,
                                                           const int* __restrict__ order, double* __restrict__ U,
                                                           double* __restrict__ W) {
