@@ -270,6 +270,48 @@ def batch_leg(binding, torch, dev, count, steps, warmup, wave=64):
     return out, systems[:wave]
 
 
+def configs_leg(binding, torch, dev, steps=5, warmup=3):
+    """Time per product of the other workloads, for context: the small FP64 case (bw_small), the
+    slit with 16k particles (slit_16k, mixed and FP64), and the paper's largest force-only scaling
+    system (663,552 particles, grid 2700^2 x 19, m = 4; 370 ms per solve on a V100 in the paper)."""
+    from paper_2210_01837_gb300.workloads import bw_small, lanczos_layer, slit_16k
+    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    def ms(params, pos, F, T, precision, with_torque):
+        plan = binding.Plan.from_params(params, with_torque=with_torque, precision=precision, max_n=len(pos))
+        d_pos, d_F = tdev(pos), tdev(F)
+        d_T = tdev(T) if with_torque else None
+        U = torch.empty((len(pos), 3), dtype=torch.float64, device=dev)
+        W = torch.empty_like(U) if with_torque else None
+        for _ in range(warmup):
+            plan.apply(d_pos, d_F, d_T, U, W)
+        plan.check()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.apply(d_pos, d_F, d_T, U, W)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        plan.check()
+        plan.close()
+        return round(e0.elapsed_time(e1) / steps, 4)
+
+    out = {}
+    p, pos, F, _ = bw_small()
+    out["bw_small_fp64_ms"] = ms(p, pos, F, None, "fp64", False)
+    p, pos, F, T = slit_16k()
+    out["slit_16k_mixed_ms"] = ms(p, pos, F, T, "mixed", True)
+    out["slit_16k_fp64_ms"] = ms(p, pos, F, T, "fp64", True)
+    p, pos, W = lanczos_layer(18, H=9.1)
+    out["fig9_forces_663552_mixed_ms"] = ms(p, pos, W, None, "mixed", False)
+    out["fig9_forces_663552_fp64_ms"] = ms(p, pos, W, None, "fp64", False)
+    out["fig9_paper_v100_ms"] = 370.0
+    out["note"] = ("CUDA events per product after 3 warm-up products; the paper's 370 ms is its V100 time for the "
+                   "same-sized system (precision not stated), context only")
+    return out
+
+
 def served_capacity(binding, torch, dev, systems):
     """Requests/s of the served population when every system runs once per batched apply."""
     tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -390,6 +432,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="duration of the served leg")
     ap.add_argument("--no-deriv", action="store_true", help="skip the kernel-derivative torque-route leg")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Brownian-increment (Lanczos) leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other-configuration timings")
     args = ap.parse_args()
 
     from paper_2210_01837_gb300.replicas import Collective, rank_env, replica_seed_offset, whole_job_rate
@@ -574,6 +617,10 @@ def main():
         lz.close()
         lplan.close()
 
+    configs = None
+    if not args.no_configs and div == 1:
+        configs = configs_leg(binding, torch, dev)
+
     # ---- all-FP64 path on the same GPU -------------------------------------------------------
     fp64 = None
     if not args.no_fp64:
@@ -614,7 +661,8 @@ def main():
                "particles_per_s": value * n, "fp64": fp64, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                "stage_roofline": stage_roof, "roofline": roofline, "e2e": e2e,
                "gpu_launches": launches_per_apply * args.steps, "clocks": clocks,
-               "batch": batch, "served": served, "kernel_derivative_route": deriv, "lanczos": lanczos}
+               "batch": batch, "served": served, "kernel_derivative_route": deriv, "lanczos": lanczos,
+               "other_configs": configs}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

@@ -871,7 +871,11 @@ __global__ void __launch_bounds__(kBvpThreads) bwd_kernel(Geometry g, const T* _
 // inside the contraction loops.
 // ---------------------------------------------------------------------------------------------
 constexpr int kLaneK = 32;
+// Chebyshev rows per warp of the forward transform: 8 (float) while the block stays within the thread
+// limit (nz <= 96), else 12; the smaller split needs fewer registers (74 against 142) and fits
+// three blocks per SM
 template <typename T> __host__ __device__ constexpr int fwd_pg() { return sizeof(T) == 4 ? 8 : 6; }
+template <typename T> __host__ __device__ constexpr int fwd_pg_wide() { return sizeof(T) == 4 ? 12 : 6; }
 template <typename T> __host__ __device__ constexpr int bwd_pg() { return sizeof(T) == 4 ? 8 : 4; }
 template <typename T> __host__ __device__ constexpr int bwd_warps() { return sizeof(T) == 4 ? 5 : 10; }
 
@@ -1232,6 +1236,7 @@ size_t bwd_smem(const Plan& p, size_t tsz) { return (p.g.spectral_curl ? 3 : 1) 
 struct LaneCfg {
   int threads = 0, cz = 0;
   size_t smem = 0;
+  int pg = 0;  // forward transform: Chebyshev rows per warp (fwd_pg or fwd_pg_wide)
 };
 constexpr int kFwdPlanes = 8;                // planes per double-buffered chunk of the forward transform
 constexpr size_t kBwdLaneSmem = 200 * 1024;  // largest backward stage
@@ -1239,11 +1244,16 @@ constexpr size_t kBwdLaneSmem = 200 * 1024;  // largest backward stage
 template <typename T>
 LaneCfg fwd_lane_cfg(const Geometry& g) {
   LaneCfg c;
-  constexpr int PG = fwd_pg<T>();
-  const int nw = (g.nz + PG - 1) / PG;
+  int PG = fwd_pg<T>();
+  int nw = (g.nz + PG - 1) / PG;
+  if (32 * nw > fwd_max_threads<T>()) {
+    PG = fwd_pg_wide<T>();
+    nw = (g.nz + PG - 1) / PG;
+  }
   if (g.nz > 128 || 32 * nw > fwd_max_threads<T>()) return c;
   const int nf = g.spectral_curl ? 6 : 3;
   const size_t per_plane = (size_t)nf * kLaneK * sizeof(cplx<T>) + (size_t)2 * nw * PG * sizeof(T);
+  c.pg = PG;
   c.threads = 32 * nw;
   c.cz = std::min(g.nz, kFwdPlanes);      // planes per pipelined chunk
   c.smem = 2 * per_plane * (size_t)c.cz;  // two slots
@@ -1307,8 +1317,10 @@ int bvp_prepare(Plan& p) {
     return 0;
   const LaneCfg fc = fwd_lane_cfg<T>(p.g);
   if (fc.threads > 0) {
-    constexpr int PG = fwd_pg<T>();
-    if (!allow_smem(fwd_lane_kernel<T, PG, true>) || !allow_smem(fwd_lane_kernel<T, PG, false>)) return 0;
+    constexpr int PG = fwd_pg<T>(), PW = fwd_pg_wide<T>();
+    if (!allow_smem(fwd_lane_kernel<T, PG, true>) || !allow_smem(fwd_lane_kernel<T, PG, false>) ||
+        !allow_smem(fwd_lane_kernel<T, PW, true>) || !allow_smem(fwd_lane_kernel<T, PW, false>))
+      return 0;
   }
   const size_t bl = bwd_lane_smem<T>(p.g);
   if (bl > 0) {
@@ -1332,15 +1344,24 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
   const LaneCfg fc = fwd_lane_cfg<T>(g);
   if (part == 0 && fc.threads > 0) {
     const unsigned lb = (unsigned)((total + kLaneK - 1) / kLaneK);
-    constexpr int PG = fwd_pg<T>();
-    if (g.spectral_curl)
-      fwd_lane_kernel<T, PG, true><<<lb, fc.threads, fc.smem, s>>>(
-          g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, grid, kbuf,
-          p.zrange, kx0, w, fc.cz);
-    else
-      fwd_lane_kernel<T, PG, false><<<lb, fc.threads, fc.smem, s>>>(
-          g, reinterpret_cast<const T*>(p.kt.ct), reinterpret_cast<const T*>(p.kt.dct), p.kt.npad, grid, kbuf,
-          p.zrange, kx0, w, fc.cz);
+    constexpr int PG = fwd_pg<T>(), PW = fwd_pg_wide<T>();
+    const T* ct = reinterpret_cast<const T*>(p.kt.ct);
+    const T* dct = reinterpret_cast<const T*>(p.kt.dct);
+    if (fc.pg == PG) {
+      if (g.spectral_curl)
+        fwd_lane_kernel<T, PG, true><<<lb, fc.threads, fc.smem, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0,
+                                                                     w, fc.cz);
+      else
+        fwd_lane_kernel<T, PG, false><<<lb, fc.threads, fc.smem, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0,
+                                                                      w, fc.cz);
+    } else {
+      if (g.spectral_curl)
+        fwd_lane_kernel<T, PW, true><<<lb, fc.threads, fc.smem, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0,
+                                                                     w, fc.cz);
+      else
+        fwd_lane_kernel<T, PW, false><<<lb, fc.threads, fc.smem, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0,
+                                                                      w, fc.cz);
+    }
   } else if (part == 2 && bwd_lane_smem<T>(g) > 0) {
     const int corr = g.mode == DPS_FREE ? 0 : (g.mode == DPS_SLIT ? 2 : 1);
     if (g.spectral_curl) {

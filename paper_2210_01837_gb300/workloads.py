@@ -162,11 +162,12 @@ def _rsa_layer(rng, n, L, heights, dmin, max_tries=200000):
     raise RuntimeError("random sequential addition did not place every particle")
 
 
-def lanczos_layer(reps=1, mode="bottom_wall", seed_offset=5):
+def lanczos_layer(reps=1, mode="bottom_wall", seed_offset=5, H=7.5):
     """Particle layer of the Lanczos convergence test, tiled reps x reps times in xy; returns
-    (params, pos, W) with W the i.i.d. standard normal vector [N][3]."""
+    (params, pos, W) with W the i.i.d. standard normal vector [N][3].  H = 9.1 with reps = 18 is the
+    largest force-only system of the scaling test (663,552 particles, grid 2700^2 x 19)."""
     rng = np.random.default_rng(SEED_BASE + seed_offset)
-    L0, n0, H = 128.8, 2048, 7.5
+    L0, n0 = 128.8, 2048
 
     def heights(r):  # two layers
         return r.normal(1.1, 0.05) if r.uniform() < 0.5 else r.normal(2.2, 0.1)
