@@ -493,7 +493,9 @@ def main():
     plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=n)
     tuned_ms = plan.autotune(d_pos, d_F, d_T, U, W) if not args.no_tune else None
     info = plan.info()
-    tuned = {"autotune_ms": tuned_ms, "fft_col_width": info.fft_col_width, "solve_blocks": info.solve_blocks,
+    tuned = {"autotune_ms": tuned_ms, "fft_col_width": info.fft_col_width,
+             "fft_register_staged": {"rows": info.fft_register_rows, "cols": info.fft_register_cols},
+             "solve_blocks": info.solve_blocks,
              "wavenumber_chunks": info.nchunks}
     launches_per_apply = info.launches_per_apply
     plan.enable_timing(True)

@@ -173,12 +173,16 @@ typedef struct {
   int32_t nchunks;          /* column chunks of the wavenumber-space pipeline                     */
   int32_t fft_col_width;    /* x-wavenumber columns per block of the y-FFT pass                   */
   int32_t solve_blocks;     /* persistent blocks of the FP64 per-wavenumber solve                 */
+  int32_t fft_register_rows; /* 1: the x-FFT passes run register-staged (one butterfly per thread
+                               and stage, one shared buffer), 0: shared-memory-staged           */
+  int32_t fft_register_cols; /* the same for the y-FFT passes                                     */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 
 /* Autotuner (no counterpart in the paper).  Times the plan's applies on the given particles (same
  * arguments and rules as dpstokes_apply) over a small set of launch shapes, one knob at a time:
- * the column width of the y-FFT pass (1, 2, 4, 8 within the shared-memory and thread limits), the
+ * the column width (1, 2, 4, 8) and variant (register- or shared-memory-staged) of the y-FFT pass
+ * within the shared-memory and thread limits, the
  * persistent grid of the FP64 solve (1-4 blocks per SM within the allocated workspace) and the
  * column chunks of the wavenumber-space pipeline (1, 2, 4); a candidate replaces the current shape
  * when it is at least 2 % faster.  The plan keeps the chosen shapes (dpstokes_plan_info reports
@@ -188,6 +192,14 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* positions, const double* forces,
                                   const double* torques, double* out_vel, double* out_angvel, void* stream,
                                   double* best_ms);
+
+/* Sets the xy-FFT launch shapes by hand (no counterpart in the paper): `row_register` and
+ * `col_register` choose the register-staged (1) or shared-memory-staged (0) variant of the x- and
+ * y-FFT passes, `col_width` (1, 2, 4 or 8) the x-wavenumber columns per block of the y pass.
+ * Results do not depend on the shapes beyond summation order.  DPS_ERR_INVALID_ARG (plan
+ * unchanged) when plan is NULL, a flag is not 0 or 1, or the shape does not fit this plan's sizes
+ * within the thread and shared-memory limits; dpstokes_plan_info reports the shapes in use. */
+dps_status dpstokes_plan_set_fft(dps_plan_t plan, int32_t row_register, int32_t col_register, int32_t col_width);
 
 /* Per-stage timing.  With timing enabled, every apply brackets each kernel launch with a pair of
  * CUDA events on the stream that launch runs on (the wavenumber-space stages run in column chunks

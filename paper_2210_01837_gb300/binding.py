@@ -47,7 +47,8 @@ class dps_plan_info(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("nkx", ctypes.c_int32), ("pitch", ctypes.c_int32),
                 ("nfields", ctypes.c_int32), ("record_words", ctypes.c_int32), ("h", ctypes.c_double),
                 ("alpha_M", ctypes.c_double), ("alpha_D", ctypes.c_double), ("launches_per_apply", ctypes.c_int32),
-                ("nchunks", ctypes.c_int32), ("fft_col_width", ctypes.c_int32), ("solve_blocks", ctypes.c_int32)]
+                ("nchunks", ctypes.c_int32), ("fft_col_width", ctypes.c_int32), ("solve_blocks", ctypes.c_int32),
+                ("fft_register_rows", ctypes.c_int32), ("fft_register_cols", ctypes.c_int32)]
 
 
 class dps_request(ctypes.Structure):
@@ -133,6 +134,7 @@ def load(path=None):
                                            ctypes.POINTER(dps_kernel_params), _I64, _P, _P, _P, _P, _I64, _P]),
         "dpstokes_debug_run": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, _I32]),
         "dpstokes_debug_copy": (_I32, [_P, _I32, _P, _I64, _P]),
+        "dpstokes_plan_set_fft": (_I32, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
         "dpstokes_plan_autotune": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
         "dpstokes_apply_batch": (_I32, [ctypes.POINTER(dps_request), _I32, _P]),
         "dpstokes_batch_prepare": (_I32, []),
@@ -346,6 +348,12 @@ class Plan:
         if check:
             self.check(stream)
         return U, (W if self.with_torque else None)
+
+    def set_fft(self, row_register, col_register, col_width):
+        """Set the xy-FFT variants and column width by hand; raises if the shape does not fit."""
+        st = load().dpstokes_plan_set_fft(self.handle, int(row_register), int(col_register), int(col_width))
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_plan_set_fft")
 
     def autotune(self, pos, F, T=None, U=None, W=None, stream=None):
         """Pick launch shapes by timing applies on these particles; returns the best time in ms."""

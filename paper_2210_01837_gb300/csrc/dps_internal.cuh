@@ -139,6 +139,7 @@ struct Plan {
   int bvp_blocks;       // persistent grid size of the per-k solver
   int fft_grid[4];      // resident grids of the persistent FFT passes: rows fwd/inv, columns fwd/inv
   int col_lcw;          // log2 of the column block of the y-FFT pass (default rule or autotuned)
+  int fft_reg[2];       // FFT variant of the row and the column pass: 1 register-staged, 0 smem-staged
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)
@@ -253,7 +254,10 @@ template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
-template <typename T> int fft_set_col_width(Plan& p, int lcw);  // 0 if the width does not fit
+// column block 2^lcw of the y-FFT pass, register-staged (reg = 1) or shared-memory-staged; 0 if it does not fit
+template <typename T> int fft_set_col_width(Plan& p, int lcw, int reg);
+// x-FFT pass variant: register-staged (reg = 1) or shared-memory-staged; 0 if it does not fit
+template <typename T> int fft_set_row_variant(Plan& p, int reg);
 
 // host-side validation of an apply's arguments, and the stream-ordered product itself
 dps_status check_apply_args(const Plan* p, int64_t n, const double* pos, const double* F, const double* Tq,

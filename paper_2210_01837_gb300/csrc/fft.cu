@@ -9,10 +9,13 @@
 //                  transform is then split into the two half spectra; inverse likewise.
 //   * column pass: a unit is `cw` adjacent x-wavenumber columns of one plane, transformed along y.
 // Both passes run persistent blocks (as many as fit on the GPU) that walk the units of the live
-// planes.  A block stages a unit in shared memory with cp.async; the first stage reads the staged
-// values directly, after which the staging buffer takes the next unit's copies while the later
-// stages alternate between two padded work buffers, so HBM traffic overlaps the butterflies and
-// each unit crosses shared memory 2 S + 2 times for S stages.
+// planes, in one of two variants.  Shared-memory-staged: a block stages a unit in shared memory
+// with cp.async; the first stage reads the staged values directly, after which the staging buffer
+// takes the next unit's copies while the later stages alternate between two padded work buffers,
+// so HBM traffic overlaps the butterflies and each unit crosses shared memory 2 S + 2 times for S
+// stages.  Register-staged: one butterfly per thread and stage, updated in place in one shared
+// buffer, the first stage reading HBM and the last writing it directly (described further below).
+// The plan picks the variant per pass (default rule at fft_smem_ok, or autotuned / set by hand).
 // Each 1D transform is a self-sorting (Stockham) mixed-radix FFT in shared memory written from the
 // textbook formulation: stage s with radix R and span Ns multiplies input j + r n/R by
 // W_{Ns R}^{(j mod Ns) r}, applies an R-point DFT, and stores to (j / Ns) Ns R + (j mod Ns) + r Ns.
@@ -504,6 +507,197 @@ __global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, con
   }
 }
 
+// ---- register-staged variant ----
+// Each thread owns at most one butterfly per stage (the block has at least as many threads as the
+// stage with the most butterflies): it reads the butterfly's R inputs, applies the twiddles and the
+// R-point DFT in registers and, after a block barrier, writes the R outputs back in place, so the
+// block needs one unit-sized shared buffer instead of a staging buffer and two work buffers.  The
+// first stage reads HBM directly and (column pass and inverse row pass) the last stage writes HBM
+// directly, so a unit crosses shared memory 2 (S - 1) times for S stages and the resident blocks
+// (several per SM) hide each other's memory latency.
+
+// One stage (radix R, span Ns) over 2^lb interleaved sequences: butterfly t = (jj, b) reads
+// element jj + r n/R of sequence b through src(element, b), multiplies input r by
+// W_{Ns R}^{(jj mod Ns) r} (stages after the first), and stores X_r as element
+// (jj / Ns) Ns R + (jj mod Ns) + r Ns through dst(element, b, X_r).  With `barrier` every thread
+// has read its inputs before any thread writes (in-place update).
+template <typename T, int R, int DIR, class Src, class Dst>
+__device__ __forceinline__ void reg_stage(const FftPlan& fp, int s, int Ns, int lb, const cplx<T>* __restrict__ tw,
+                                          const Src& src, const Dst& dst, bool barrier) {
+  const int n = fp.n, nr = n / R, total = nr << lb;
+  const int t = threadIdx.x;
+  const bool act = t < total;
+  const int b = t & ((1 << lb) - 1), jj = t >> lb;
+  cplx<T> v[R];  // initialised: an array left undefined on the idle threads' path is not kept in registers
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = mk<T>((T)0, (T)0);
+  int ob = jj * R;
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src(jj + r * nr, b);
+    if (s > 0) {
+      const int q = (int)(((unsigned long long)jj * fp.magic[s]) >> 40);
+      const int k = jj - q * Ns;
+      const int tstep = n / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = tw[k * r * tstep];
+        if (DIR > 0) w.y = -w.y;
+        v[r] = v[r] * w;
+      }
+      ob = q * Ns * R + k;
+    }
+    Dft<T, R, DIR>::run(v);
+  }
+  if (barrier) __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst(ob + r * Ns, b, v[r]);
+  }
+}
+
+template <typename T, int DIR, class Src, class Dst>
+__device__ __forceinline__ void reg_stage_any(const FftPlan& fp, int s, int Ns, int lb, const cplx<T>* tw,
+                                              const Src& src, const Dst& dst, bool barrier) {
+  switch (fp.radix[s]) {
+    case 16: reg_stage<T, 16, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 12: reg_stage<T, 12, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 8: reg_stage<T, 8, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 4: reg_stage<T, 4, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 2: reg_stage<T, 2, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 3: reg_stage<T, 3, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 5: reg_stage<T, 5, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    default: reg_stage<T, 7, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+  }
+}
+
+// A whole transform: src (HBM) -> stages in the shared buffer -> dst.  The first barrier also
+// orders this unit's first shared writes after the previous unit's last shared reads.  With
+// DST_SMEM the last stage writes the shared buffer too (followed by a barrier), for an epilogue.
+template <typename T, int DIR, bool DST_SMEM, class Src, class Dst>
+__device__ __forceinline__ void reg_fft(cplx<T>* buf, const FftPlan& fp, int lb, const cplx<T>* tw, const Src& gsrc,
+                                        const Dst& gdst) {
+  auto ssrc = [&](int e, int b) { return buf[pad16((e << lb) + b)]; };
+  auto sdst = [&](int e, int b, cplx<T> v) { buf[pad16((e << lb) + b)] = v; };
+  const int S = fp.nstages;
+  if (S == 1) {
+    // in place in HBM as well (the column pass and the inverse row pass overwrite their input)
+    if (DST_SMEM) {
+      reg_stage_any<T, DIR>(fp, 0, 1, lb, tw, gsrc, sdst, true);
+      __syncthreads();
+    } else {
+      reg_stage_any<T, DIR>(fp, 0, 1, lb, tw, gsrc, gdst, true);
+    }
+    return;
+  }
+  reg_stage_any<T, DIR>(fp, 0, 1, lb, tw, gsrc, sdst, true);
+  __syncthreads();
+  int Ns = fp.radix[0];
+  for (int s = 1; s < S - 1; ++s) {
+    reg_stage_any<T, DIR>(fp, s, Ns, lb, tw, ssrc, sdst, true);
+    __syncthreads();
+    Ns *= fp.radix[s];
+  }
+  if (DST_SMEM) {
+    reg_stage_any<T, DIR>(fp, S - 1, Ns, lb, tw, ssrc, sdst, true);
+    __syncthreads();
+  } else {
+    reg_stage_any<T, DIR>(fp, S - 1, Ns, lb, tw, ssrc, gdst, false);
+  }
+}
+
+constexpr int kRegMaxThreads = 512;
+#define DPS_REG_FFT_BOUNDS __launch_bounds__(kRegMaxThreads, sizeof(T) == 4 ? 2 : 1)
+
+// Row pass, forward, register-staged: two real rows packed as z = r0 + i r1, then the half-spectrum split.
+template <typename T>
+__global__ void DPS_REG_FFT_BOUNDS row_r2c_reg_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                      T* __restrict__ grid, const int* __restrict__ zrange) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smraw);
+  const int nx = g.nx;
+  const UnitMap um(g, zrange, (g.ny + 1) / 2);
+  const size_t rowlen = (size_t)2 * g.pitch;
+  const T half = (T)0.5;
+  for (long long u = blockIdx.x; u < um.total; u += gridDim.x) {
+    int f, c, j;
+    um.at(u, f, c, j);
+    const bool has1 = 2 * j + 1 < g.ny;
+    T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + 2 * j) * rowlen;
+    const T* row1 = row0 + rowlen;
+    reg_fft<T, -1, true>(buf, fp, 0, tw, [&](int e, int) { return mk<T>(row0[e], has1 ? row1[e] : (T)0); },
+                         [](int, int, cplx<T>) {});
+    cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
+    cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row0 + rowlen);
+    for (int k = threadIdx.x; k <= nx / 2; k += blockDim.x) {
+      const cplx<T> zk = buf[pad16(k)];
+      const cplx<T> zm = conjg(buf[pad16(k == 0 ? 0 : nx - k)]);
+      c0[k] = scl(zk + zm, half);
+      if (has1) {
+        const cplx<T> d = zk - zm;  // (zk - conj z_{-k}) / (2i)
+        c1[k] = mk<T>(half * d.y, -half * d.x);
+      }
+    }
+  }
+}
+
+// Row pass, inverse, register-staged: z_k = X0_k + i X1_k over the Hermitian extension, one FFT.
+template <typename T>
+__global__ void DPS_REG_FFT_BOUNDS row_c2r_reg_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                      T* __restrict__ grid, const int* __restrict__ zrange) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smraw);
+  const int nx = g.nx;
+  const UnitMap um(g, zrange, (g.ny + 1) / 2);
+  const size_t rowlen = (size_t)2 * g.pitch;
+  for (long long u = blockIdx.x; u < um.total; u += gridDim.x) {
+    int f, c, j;
+    um.at(u, f, c, j);
+    const bool has1 = 2 * j + 1 < g.ny;
+    T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + 2 * j) * rowlen;
+    T* row1 = row0 + rowlen;
+    const cplx<T>* c0 = reinterpret_cast<const cplx<T>*>(row0);
+    const cplx<T>* c1 = reinterpret_cast<const cplx<T>*>(row1);
+    reg_fft<T, +1, false>(
+        buf, fp, 0, tw,
+        [&](int e, int) {
+          const bool lo = e <= nx / 2;
+          const int k = lo ? e : nx - e;
+          const cplx<T> x0 = c0[k];
+          const cplx<T> x1 = has1 ? c1[k] : mk<T>((T)0, (T)0);
+          return lo ? x0 + mul_i(x1) : conjg(x0) + mul_i(conjg(x1));
+        },
+        [&](int a, int, cplx<T> v) {
+          row0[a] = v.x;
+          if (has1) row1[a] = v.y;
+        });
+  }
+}
+
+// Column pass, register-staged: cw = 2^lcw adjacent x-wavenumber columns of one plane, along y.
+template <typename T, int DIR>
+__global__ void DPS_REG_FFT_BOUNDS col_reg_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                                                  cplx<T>* __restrict__ grid, const int* __restrict__ zrange, int lcw,
+                                                  int kxs, int kxe) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smraw);
+  const int cw = 1 << lcw;
+  const UnitMap um(g, zrange, (kxe - kxs + cw - 1) >> lcw);
+  for (long long u = blockIdx.x; u < um.total; u += gridDim.x) {
+    int f, c, j;
+    um.at(u, f, c, j);
+    const int kx0 = kxs + (j << lcw);
+    const int ncols = min(cw, kxe - kx0);
+    cplx<T>* base = grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
+    reg_fft<T, DIR, false>(
+        buf, fp, lcw, tw,
+        [&](int y, int b) { return b < ncols ? base[(size_t)y * g.pitch + b] : mk<T>((T)0, (T)0); },
+        [&](int y, int b, cplx<T> v) {
+          if (b < ncols) base[(size_t)y * g.pitch + b] = v;
+        });
+  }
+}
+
 size_t padded_bytes(int n, size_t esz) { return (size_t)(n + (n >> 4) + 1) * esz; }
 
 template <typename T>
@@ -544,38 +738,114 @@ int resident_grid(KernelT kernel, int threads, size_t smem, int device) {
   return std::max(1, per_sm) * std::max(1, sms);
 }
 
+// threads of the register-staged variant for `points` = n 2^lb values: one per butterfly of the
+// stage with the most butterflies, whole warps
+int reg_threads(const FftPlan& fp, int lb) {
+  int m = 0;
+  for (int s = 0; s < fp.nstages; ++s) m = std::max(m, (fp.n << lb) / fp.radix[s]);
+  return (m + 31) / 32 * 32;
+}
+
+template <typename T>
+size_t reg_smem(int points) { return padded_bytes(points, sizeof(cplx<T>)); }
+
+// the register-staged variant fits: thread limit, and the two resident blocks per SM (float) its
+// register budget was compiled for share the SM's shared memory
+template <typename T>
+bool reg_fits(const FftPlan& fp, int lb) {
+  return reg_threads(fp, lb) <= kRegMaxThreads && reg_smem<T>(fp.n << lb) <= 100 * 1024;
+}
+
 }  // namespace
 
 template <typename T>
-int fft_set_col_width(Plan& p, int lcw) {
+int fft_set_col_width(Plan& p, int lcw, int reg) {
   if (lcw < 0 || lcw > 3) return 0;
+  if (reg) {
+    if (!reg_fits<T>(p.fy, lcw)) return 0;
+    const int th = reg_threads(p.fy, lcw);
+    const size_t sm = reg_smem<T>(p.g.ny << lcw);
+    p.col_lcw = lcw;
+    p.fft_reg[1] = 1;
+    p.fft_grid[2] = resident_grid(col_reg_kernel<T, -1>, th, sm, p.device);
+    p.fft_grid[3] = resident_grid(col_reg_kernel<T, +1>, th, sm, p.device);
+    return 1;
+  }
   const size_t col = col_smem<T>(p.g, lcw);
   const int tcol = fft_threads(p.g.ny << lcw);
   if (tcol > kFftMaxThreads || col > 220 * 1024) return 0;
   p.col_lcw = lcw;
+  p.fft_reg[1] = 0;
   p.fft_grid[2] = resident_grid(col_kernel<T, -1>, tcol, col, p.device);
   p.fft_grid[3] = resident_grid(col_kernel<T, +1>, tcol, col, p.device);
   return 1;
 }
 
 template <typename T>
-int fft_smem_ok(Plan& p) {
+int fft_set_row_variant(Plan& p, int reg) {
+  if (reg) {
+    if (!reg_fits<T>(p.fx, 0)) return 0;
+    const int th = reg_threads(p.fx, 0);
+    const size_t sm = reg_smem<T>(p.g.nx);
+    p.fft_reg[0] = 1;
+    p.fft_grid[0] = resident_grid(row_r2c_reg_kernel<T>, th, sm, p.device);
+    p.fft_grid[1] = resident_grid(row_c2r_reg_kernel<T>, th, sm, p.device);
+    return 1;
+  }
   const size_t r2c = row_r2c_smem<T>(p.g), c2r = row_c2r_smem<T>(p.g);
   const int trow = fft_threads(p.g.nx);
-  if (trow > kFftMaxThreads) return 0;
-  if (r2c > 220 * 1024 || c2r > 220 * 1024) return 0;
-  if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
-      !allow_smem(col_kernel<T, +1>))
-    return 0;
+  if (trow > kFftMaxThreads || r2c > 220 * 1024 || c2r > 220 * 1024) return 0;
+  p.fft_reg[0] = 0;
   p.fft_grid[0] = resident_grid(row_r2c_kernel<T>, trow, r2c, p.device);
   p.fft_grid[1] = resident_grid(row_c2r_kernel<T>, trow, c2r, p.device);
-  return fft_set_col_width<T>(p, col_lwidth<T>(p));
+  return 1;
+}
+
+// Default shapes, from measurements on rollers and slit grids (3072^2, 768^2, 384^2): the
+// register-staged row pass only for long float rows whose stages keep at least 3/4 of the block
+// busy (3072 = 16 x 16 x 12: 10 % faster than the shared-memory-staged pass; 768 = 16 x 16 x 3 and
+// 384 = 16 x 12 x 2 leave most threads idle in the radix-16 stages and run 1.5-2.5x slower, as does
+// FP64); the column pass shared-memory-staged (the register-staged one, with its loads exposed
+// instead of prefetched, measured 1.3-1.5x slower at equal width) with the widest block that fits.
+template <typename T>
+bool reg_rows_default(const FftPlan& fp) {
+  if (sizeof(T) != 4 || fp.n < 2048 || !reg_fits<T>(fp, 0)) return false;
+  int rmin = fp.radix[0], rmax = fp.radix[0];
+  for (int s = 1; s < fp.nstages; ++s) {
+    rmin = std::min(rmin, fp.radix[s]);
+    rmax = std::max(rmax, fp.radix[s]);
+  }
+  return 3 * rmax <= 4 * rmin;
+}
+
+template <typename T>
+int fft_smem_ok(Plan& p) {
+  if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
+      !allow_smem(col_kernel<T, +1>) || !allow_smem(row_r2c_reg_kernel<T>) || !allow_smem(row_c2r_reg_kernel<T>) ||
+      !allow_smem(col_reg_kernel<T, -1>) || !allow_smem(col_reg_kernel<T, +1>))
+    return 0;
+  const bool rr = reg_rows_default<T>(p.fx);
+  if (!fft_set_row_variant<T>(p, rr ? 1 : 0) && !fft_set_row_variant<T>(p, rr ? 0 : 1)) return 0;
+  if (fft_set_col_width<T>(p, col_lwidth<T>(p), 0)) return 1;
+  for (int l = 3; l >= 0; --l)
+    if (fft_set_col_width<T>(p, l, 1)) return 1;
+  return 0;
 }
 
 template <typename T>
 void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
+  if (p.fft_reg[0]) {
+    const int th = reg_threads(p.fx, 0);
+    const size_t sm = reg_smem<T>(g.nx);
+    T* grid = reinterpret_cast<T*>(p.grid);
+    if (dir < 0)
+      row_r2c_reg_kernel<T><<<p.fft_grid[0], th, sm, s>>>(g, p.fx, twx, grid, p.zrange);
+    else
+      row_c2r_reg_kernel<T><<<p.fft_grid[1], th, sm, s>>>(g, p.fx, twx, grid, p.zrange);
+    return;
+  }
   const int th = fft_threads(g.nx);
   if (dir < 0)
     row_r2c_kernel<T><<<p.fft_grid[0], th, row_r2c_smem<T>(g), s>>>(g, p.fx, twx, reinterpret_cast<T*>(p.grid),
@@ -590,6 +860,16 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   const int lcw = p.col_lcw;
+  cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
+  if (p.fft_reg[1]) {
+    const int th = reg_threads(p.fy, lcw);
+    const size_t sm = reg_smem<T>(g.ny << lcw);
+    if (dir < 0)
+      col_reg_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+    else
+      col_reg_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+    return;
+  }
   const size_t sm = col_smem<T>(g, lcw);
   const int th = fft_threads(g.ny << lcw);
   if (dir < 0)
@@ -602,8 +882,10 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
 
 template int fft_smem_ok<float>(Plan&);
 template int fft_smem_ok<double>(Plan&);
-template int fft_set_col_width<float>(Plan&, int);
-template int fft_set_col_width<double>(Plan&, int);
+template int fft_set_row_variant<float>(Plan&, int);
+template int fft_set_row_variant<double>(Plan&, int);
+template int fft_set_col_width<float>(Plan&, int, int);
+template int fft_set_col_width<double>(Plan&, int, int);
 template void launch_fft_rows<float>(const Plan&, int, cudaStream_t);
 template void launch_fft_rows<double>(const Plan&, int, cudaStream_t);
 template void launch_fft_cols<float>(const Plan&, int, int, int, cudaStream_t);

@@ -513,6 +513,8 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   out->launches_per_apply = 8 + 5 * p->nchunks;
   out->nchunks = p->nchunks;
   out->fft_col_width = 1 << p->col_lcw;
+  out->fft_register_rows = p->fft_reg[0];
+  out->fft_register_cols = p->fft_reg[1];
   out->solve_blocks = p->bvp_blocks;
   return DPS_OK;
 }
@@ -541,19 +543,22 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
     return DPS_OK;
   };
   const bool mixed = p->precision == DPS_MIXED;
-  auto set_width = [&](int l) { return mixed ? dps::fft_set_col_width<float>(*p, l) : dps::fft_set_col_width<double>(*p, l); };
+  auto set_width = [&](int l, int reg) {
+    return mixed ? dps::fft_set_col_width<float>(*p, l, reg) : dps::fft_set_col_width<double>(*p, l, reg);
+  };
   double best = 0.0, t = 0.0;
   st = measure(&best);
   // keep a candidate only when it is clearly (2 %) faster than the incumbent
   auto better = [&](double cand) { return cand < 0.98 * best; };
-  // 1. column block of the y-FFT pass
-  int best_l = p->col_lcw;
-  for (int l = 0; l <= 3 && st == DPS_OK; ++l) {
-    if (l == best_l || !set_width(l)) continue;
-    st = measure(&t);
-    if (st == DPS_OK && better(t)) { best = t; best_l = l; }
-  }
-  set_width(best_l);
+  // 1. column block and variant (register- or shared-memory-staged) of the y-FFT pass
+  int best_l = p->col_lcw, best_r = p->fft_reg[1];
+  for (int r = 1; r >= 0 && st == DPS_OK; --r)
+    for (int l = 0; l <= 3 && st == DPS_OK; ++l) {
+      if ((l == best_l && r == best_r) || !set_width(l, r)) continue;
+      st = measure(&t);
+      if (st == DPS_OK && better(t)) { best = t; best_l = l; best_r = r; }
+    }
+  set_width(best_l, best_r);
   // 2. persistent grid of the FP64 solve (blocks per SM, within the allocated workspace)
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -584,6 +589,26 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
   if (st != DPS_OK) return st;
   if (best_ms) *best_ms = best;
   return dpstokes_status(plan, stream);
+}
+
+dps_status dpstokes_plan_set_fft(dps_plan_t plan, int32_t row_register, int32_t col_register, int32_t col_width) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || (row_register != 0 && row_register != 1) || (col_register != 0 && col_register != 1))
+    return DPS_ERR_INVALID_ARG;
+  int l = -1;
+  for (int k = 0; k <= 3; ++k)
+    if (col_width == (1 << k)) l = k;
+  if (l < 0) return DPS_ERR_INVALID_ARG;
+  const bool mixed = p->precision == DPS_MIXED;
+  const int old_reg[2] = {p->fft_reg[0], p->fft_reg[1]}, old_l = p->col_lcw;
+  auto set_rows = [&](int r) { return mixed ? dps::fft_set_row_variant<float>(*p, r) : dps::fft_set_row_variant<double>(*p, r); };
+  auto set_cols = [&](int k, int r) {
+    return mixed ? dps::fft_set_col_width<float>(*p, k, r) : dps::fft_set_col_width<double>(*p, k, r);
+  };
+  if (set_rows(row_register) && set_cols(l, col_register)) return DPS_OK;
+  set_rows(old_reg[0]);
+  set_cols(old_l, old_reg[1]);
+  return DPS_ERR_INVALID_ARG;
 }
 
 dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable) {

@@ -82,6 +82,7 @@ def test_null_plan_rejected(lib):
     assert binding.dpstokes_status(None, None) == binding.DPS_ERR_INVALID_ARG
     st, _ = binding.dpstokes_plan_info(None)
     assert st == binding.DPS_ERR_INVALID_ARG
+    assert binding.load().dpstokes_plan_set_fft(None, 1, 1, 2) == binding.DPS_ERR_INVALID_ARG
     binding.dpstokes_destroy(None)
 
 
@@ -90,7 +91,8 @@ def test_struct_layout_matches_the_c_compiler(tmp_path):
     from paper_2210_01837_gb300 import binding
     fields = {
         "dps_grid": ["nz"], "dps_kernel_params": ["beta_M", "m_D", "beta_D", "eta", "with_torque", "precision", "max_n"],
-        "dps_plan_info": ["nkx", "h", "alpha_D", "launches_per_apply", "nchunks", "fft_col_width", "solve_blocks"],
+        "dps_plan_info": ["nkx", "h", "alpha_D", "launches_per_apply", "nchunks", "fft_col_width", "solve_blocks",
+                          "fft_register_cols"],
         "dps_request": ["n", "positions", "torques", "out_angvel", "status"],
         "dps_serve_request": ["wall_mode", "grid", "kp", "n", "positions", "out_angvel", "walls"],
         "dps_wall_params": ["slip_top", "uw_bottom", "uw_top"],

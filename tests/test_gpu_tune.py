@@ -31,3 +31,37 @@ def test_autotune_keeps_the_product(precision, bar):
     assert rel_l2(U1.cpu().numpy(), U0.cpu().numpy()) <= bar
     assert rel_l2(W1.cpu().numpy(), W0.cpu().numpy()) <= bar
     plan.close()
+
+
+@pytest.mark.parametrize("precision,bar", [("mixed", 1e-6), ("fp64", 1e-12)])
+@pytest.mark.parametrize("nxy", [192, 384])  # x: 16 x 12 and 16 x 12 x 2; y (nxy - 48): 16 x 3 x 3 and 16 x 3 x 7
+def test_every_fft_shape_keeps_the_product(precision, bar, nxy):
+    """Both xy-FFT variants and every column width that fits give the same product."""
+    import torch
+    params = small_params("slit", nx=nxy, ny=nxy - 48, nz=17, zmax=6.0)
+    pos, F, T = random_particles(params, 1500, 78)
+    plan = binding.Plan.from_params(params, with_torque=True, precision=precision, max_n=len(pos))
+    args = (to_dev(pos), to_dev(F), to_dev(T))
+    U0, W0 = plan.apply(*args, check=True)
+    U0, W0 = U0.cpu().numpy(), W0.cpu().numpy()
+    tried = set()
+    for rr in (0, 1):
+        for cr in (0, 1):
+            for w in (1, 2, 4, 8):
+                try:
+                    plan.set_fft(rr, cr, w)
+                except binding.DpsError:
+                    continue
+                info = plan.info()
+                assert (info.fft_register_rows, info.fft_register_cols, info.fft_col_width) == (rr, cr, w)
+                tried.add((rr, cr, w))
+                U1, W1 = plan.apply(*args, check=True)
+                torch.cuda.synchronize()
+                assert rel_l2(U1.cpu().numpy(), U0) <= bar, (rr, cr, w)
+                assert rel_l2(W1.cpu().numpy(), W0) <= bar, (rr, cr, w)
+    assert {r for r, _, _ in tried} == {0, 1} and {c for _, c, _ in tried} == {0, 1}
+    with pytest.raises(binding.DpsError):
+        plan.set_fft(2, 0, 2)
+    with pytest.raises(binding.DpsError):
+        plan.set_fft(0, 0, 3)
+    plan.close()
