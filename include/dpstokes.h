@@ -175,7 +175,8 @@ typedef struct {
   int32_t solve_blocks;     /* persistent blocks of the FP64 per-wavenumber solve                 */
   int32_t fft_register_rows; /* 1: the x-FFT passes run register-staged (one butterfly per thread
                                and stage, one shared buffer), 0: shared-memory-staged           */
-  int32_t fft_register_cols; /* the same for the y-FFT passes                                     */
+  int32_t fft_register_cols; /* the y-FFT passes: 0 shared-memory-staged, 1 register-staged,
+                               2 register-staged with prefetch                                 */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 
@@ -193,12 +194,13 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
                                   const double* torques, double* out_vel, double* out_angvel, void* stream,
                                   double* best_ms);
 
-/* Sets the xy-FFT launch shapes by hand (no counterpart in the paper): `row_register` and
- * `col_register` choose the register-staged (1) or shared-memory-staged (0) variant of the x- and
- * y-FFT passes, `col_width` (1, 2, 4 or 8) the x-wavenumber columns per block of the y pass.
- * Results do not depend on the shapes beyond summation order.  DPS_ERR_INVALID_ARG (plan
- * unchanged) when plan is NULL, a flag is not 0 or 1, or the shape does not fit this plan's sizes
- * within the thread and shared-memory limits; dpstokes_plan_info reports the shapes in use. */
+/* Sets the xy-FFT launch shapes by hand (no counterpart in the paper): `row_register` chooses the
+ * register-staged (1) or shared-memory-staged (0) variant of the x-FFT passes, `col_register` that
+ * of the y-FFT passes (0 shared-memory-staged, 1 register-staged, 2 register-staged with the next
+ * block's columns prefetched), `col_width` (1, 2, 4 or 8) the x-wavenumber columns per block of the
+ * y pass.  Results do not depend on the shapes beyond summation order.  DPS_ERR_INVALID_ARG (plan
+ * unchanged) when plan is NULL, a variant is out of range, or the shape does not fit this plan's
+ * sizes within the thread and shared-memory limits; dpstokes_plan_info reports the shapes in use. */
 dps_status dpstokes_plan_set_fft(dps_plan_t plan, int32_t row_register, int32_t col_register, int32_t col_width);
 
 /* Per-stage timing.  With timing enabled, every apply brackets each kernel launch with a pair of

@@ -139,7 +139,8 @@ struct Plan {
   int bvp_blocks;       // persistent grid size of the per-k solver
   int fft_grid[4];      // resident grids of the persistent FFT passes: rows fwd/inv, columns fwd/inv
   int col_lcw;          // log2 of the column block of the y-FFT pass (default rule or autotuned)
-  int fft_reg[2];       // FFT variant of the row and the column pass: 1 register-staged, 0 smem-staged
+  int fft_reg[2];       // FFT variant of the row and the column pass: 0 smem-staged, 1 register-staged,
+                        // 2 (columns) register-staged with cp.async prefetch
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)
@@ -254,7 +255,8 @@ template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
-// column block 2^lcw of the y-FFT pass, register-staged (reg = 1) or shared-memory-staged; 0 if it does not fit
+// column block 2^lcw and variant of the y-FFT pass (reg: 0 shared-memory-staged, 1 register-staged,
+// 2 register-staged with prefetch); 0 if it does not fit
 template <typename T> int fft_set_col_width(Plan& p, int lcw, int reg);
 // x-FFT pass variant: register-staged (reg = 1) or shared-memory-staged; 0 if it does not fit
 template <typename T> int fft_set_row_variant(Plan& p, int reg);

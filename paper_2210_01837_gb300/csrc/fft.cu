@@ -14,7 +14,8 @@
 // takes the next unit's copies while the later stages alternate between two padded work buffers,
 // so HBM traffic overlaps the butterflies and each unit crosses shared memory 2 S + 2 times for S
 // stages.  Register-staged: one butterfly per thread and stage, updated in place in one shared
-// buffer, the first stage reading HBM and the last writing it directly (described further below).
+// buffer, the first stage reading HBM and the last writing it directly (described further below);
+// for the column pass also with a second buffer that cp.async fills with the next unit.
 // The plan picks the variant per pass (default rule at fft_smem_ok, or autotuned / set by hand).
 // Each 1D transform is a self-sorting (Stockham) mixed-radix FFT in shared memory written from the
 // textbook formulation: stage s with radix R and span Ns multiplies input j + r n/R by
@@ -574,11 +575,15 @@ __device__ __forceinline__ void reg_stage_any(const FftPlan& fp, int s, int Ns, 
 // A whole transform: src (HBM) -> stages in the shared buffer -> dst.  The first barrier also
 // orders this unit's first shared writes after the previous unit's last shared reads.  With
 // DST_SMEM the last stage writes the shared buffer too (followed by a barrier), for an epilogue.
-template <typename T, int DIR, bool DST_SMEM, class Src, class Dst>
+// PW: pad elements per 16 in the shared buffer (1; 2 keeps float pairs 16-byte aligned for cp.async).
+template <int PW>
+__device__ __forceinline__ int padw(int i) { return i + PW * (i >> 4); }
+
+template <typename T, int DIR, bool DST_SMEM, int PW = 1, class Src, class Dst>
 __device__ __forceinline__ void reg_fft(cplx<T>* buf, const FftPlan& fp, int lb, const cplx<T>* tw, const Src& gsrc,
                                         const Dst& gdst) {
-  auto ssrc = [&](int e, int b) { return buf[pad16((e << lb) + b)]; };
-  auto sdst = [&](int e, int b, cplx<T> v) { buf[pad16((e << lb) + b)] = v; };
+  auto ssrc = [&](int e, int b) { return buf[padw<PW>((e << lb) + b)]; };
+  auto sdst = [&](int e, int b, cplx<T> v) { buf[padw<PW>((e << lb) + b)] = v; };
   const int S = fp.nstages;
   if (S == 1) {
     // in place in HBM as well (the column pass and the inverse row pass overwrite their input)
@@ -698,6 +703,73 @@ __global__ void DPS_REG_FFT_BOUNDS col_reg_kernel(Geometry g, FftPlan fp, const 
   }
 }
 
+// Column pass, prefetched and register-staged: two unit buffers in shared memory; while the block
+// transforms one in place (one butterfly per thread and stage, the last stage writing HBM), cp.async
+// fills the other with the next unit.  The two buffers take most of the SM's shared memory, so a
+// unit can be 4 columns x 3072 rows (a full 32-byte sector per row, half the requests of 2 columns).
+template <typename T>
+__host__ __device__ constexpr int pipe_pad() { return sizeof(cplx<T>) == 8 ? 2 : 1; }
+constexpr int kPipeMaxThreadsF = 1024, kPipeMaxThreadsD = 512;
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxThreadsD, 1)
+    col_pipe_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ grid,
+                    const int* __restrict__ zrange, int lcw, int kxs, int kxe) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int PW = pipe_pad<T>();
+  const int cw = 1 << lcw;
+  const int pts = g.ny << lcw;
+  const int blen = pts + PW * (pts >> 4) + PW;
+  cplx<T>* const buf0 = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* const buf1 = buf0 + blen;
+  const UnitMap um(g, zrange, (kxe - kxs + cw - 1) >> lcw);
+  auto base_of = [&](long long u, int& ncols) {
+    int f, c, j;
+    um.at(u, f, c, j);
+    const int kx0 = kxs + (j << lcw);
+    ncols = min(cw, kxe - kx0);
+    return grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
+  };
+  auto issue = [&](long long u, cplx<T>* dst) {
+    int ncols;
+    const cplx<T>* base = base_of(u, ncols);
+    const bool wide = ncols == cw && (cw * sizeof(cplx<T>)) % 16 == 0 && (reinterpret_cast<size_t>(base) & 15) == 0;
+    if (wide) {
+      constexpr int E = sizeof(cplx<T>) == 8 ? 2 : 1;  // elements per 16 bytes
+      const int per = cw / E;
+      for (int t = threadIdx.x; t < g.ny * per; t += blockDim.x) {
+        const int y = t / per, q = t - y * per;
+        cp_async16(dst + padw<PW>((y << lcw) + q * E), base + (size_t)y * g.pitch + q * E);
+      }
+    } else {
+      for (int t = threadIdx.x; t < pts; t += blockDim.x) {
+        const int y = t >> lcw, b = t & (cw - 1);
+        if (b < ncols) async_elem(dst + padw<PW>(t), base + (size_t)y * g.pitch + b);
+      }
+    }
+    cp_commit();
+  };
+  long long u = blockIdx.x;
+  bool odd = false;
+  if (u < um.total) issue(u, buf0);
+  for (; u < um.total; u += gridDim.x, odd = !odd) {
+    cplx<T>* const cur = odd ? buf1 : buf0;
+    cplx<T>* const nxt = odd ? buf0 : buf1;
+    int ncols;
+    cplx<T>* base = base_of(u, ncols);
+    cp_wait_all();
+    __syncthreads();  // this unit staged; every thread is done with the previous unit (in nxt)
+    if (u + gridDim.x < um.total) issue(u + gridDim.x, nxt);
+    reg_fft<T, DIR, false, PW>(
+        cur, fp, lcw, tw,
+        [&](int y, int b) { return b < ncols ? cur[padw<PW>((y << lcw) + b)] : mk<T>((T)0, (T)0); },
+        [&](int y, int b, cplx<T> v) {
+          if (b < ncols) base[(size_t)y * g.pitch + b] = v;
+        });
+  }
+  cp_wait_all();  // no copy outstanding at exit
+}
+
 size_t padded_bytes(int n, size_t esz) { return (size_t)(n + (n >> 4) + 1) * esz; }
 
 template <typename T>
@@ -759,8 +831,30 @@ bool reg_fits(const FftPlan& fp, int lb) {
 }  // namespace
 
 template <typename T>
+size_t pipe_smem(int points) {
+  constexpr int PW = pipe_pad<T>();
+  return (size_t)2 * (points + PW * (points >> 4) + PW) * sizeof(cplx<T>);
+}
+
+template <typename T>
+bool pipe_fits(const FftPlan& fp, int lb) {
+  const int maxth = sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxThreadsD;
+  return reg_threads(fp, lb) <= maxth && pipe_smem<T>(fp.n << lb) <= 224 * 1024;
+}
+
+template <typename T>
 int fft_set_col_width(Plan& p, int lcw, int reg) {
-  if (lcw < 0 || lcw > 3) return 0;
+  if (lcw < 0 || lcw > 3 || reg < 0 || reg > 2) return 0;
+  if (reg == 2) {
+    if (!pipe_fits<T>(p.fy, lcw)) return 0;
+    const int th = reg_threads(p.fy, lcw);
+    const size_t sm = pipe_smem<T>(p.g.ny << lcw);
+    p.col_lcw = lcw;
+    p.fft_reg[1] = 2;
+    p.fft_grid[2] = resident_grid(col_pipe_kernel<T, -1>, th, sm, p.device);
+    p.fft_grid[3] = resident_grid(col_pipe_kernel<T, +1>, th, sm, p.device);
+    return 1;
+  }
   if (reg) {
     if (!reg_fits<T>(p.fy, lcw)) return 0;
     const int th = reg_threads(p.fy, lcw);
@@ -805,8 +899,11 @@ int fft_set_row_variant(Plan& p, int reg) {
 // register-staged row pass only for long float rows whose stages keep at least 3/4 of the block
 // busy (3072 = 16 x 16 x 12: 10 % faster than the shared-memory-staged pass; 768 = 16 x 16 x 3 and
 // 384 = 16 x 12 x 2 leave most threads idle in the radix-16 stages and run 1.5-2.5x slower, as does
-// FP64); the column pass shared-memory-staged (the register-staged one, with its loads exposed
-// instead of prefetched, measured 1.3-1.5x slower at equal width) with the widest block that fits.
+// FP64).  Columns: the width of a block's per-row piece decides (3072 rows, mixed: 2 columns
+// shared-memory-staged 18.1 ms per pass pair, 4 columns prefetched register-staged 14.5 ms, the
+// latter at 2 columns 23.6 ms), so the prefetched register-staged pass where its two buffers fit a
+// wider block than the staged pass's three, else the staged pass at its widest; the register-staged
+// pass without prefetch (loads exposed; 1.3-1.5x slower at equal width) only by hand or autotuning.
 template <typename T>
 bool reg_rows_default(const FftPlan& fp) {
   if (sizeof(T) != 4 || fp.n < 2048 || !reg_fits<T>(fp, 0)) return false;
@@ -822,11 +919,16 @@ template <typename T>
 int fft_smem_ok(Plan& p) {
   if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
       !allow_smem(col_kernel<T, +1>) || !allow_smem(row_r2c_reg_kernel<T>) || !allow_smem(row_c2r_reg_kernel<T>) ||
-      !allow_smem(col_reg_kernel<T, -1>) || !allow_smem(col_reg_kernel<T, +1>))
+      !allow_smem(col_reg_kernel<T, -1>) || !allow_smem(col_reg_kernel<T, +1>) ||
+      !allow_smem(col_pipe_kernel<T, -1>) || !allow_smem(col_pipe_kernel<T, +1>))
     return 0;
   const bool rr = reg_rows_default<T>(p.fx);
   if (!fft_set_row_variant<T>(p, rr ? 1 : 0) && !fft_set_row_variant<T>(p, rr ? 0 : 1)) return 0;
-  if (fft_set_col_width<T>(p, col_lwidth<T>(p), 0)) return 1;
+  // columns: the prefetched register-staged pass when it fits a wider block than the staged one
+  const int ls = col_lwidth<T>(p);
+  for (int l = 3; l > ls; --l)
+    if (fft_set_col_width<T>(p, l, 2)) return 1;
+  if (fft_set_col_width<T>(p, ls, 0)) return 1;
   for (int l = 3; l >= 0; --l)
     if (fft_set_col_width<T>(p, l, 1)) return 1;
   return 0;
@@ -861,6 +963,15 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   const int lcw = p.col_lcw;
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
+  if (p.fft_reg[1] == 2) {
+    const int th = reg_threads(p.fy, lcw);
+    const size_t sm = pipe_smem<T>(g.ny << lcw);
+    if (dir < 0)
+      col_pipe_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+    else
+      col_pipe_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+    return;
+  }
   if (p.fft_reg[1]) {
     const int th = reg_threads(p.fy, lcw);
     const size_t sm = reg_smem<T>(g.ny << lcw);

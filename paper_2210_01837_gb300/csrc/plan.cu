@@ -552,7 +552,7 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
   auto better = [&](double cand) { return cand < 0.98 * best; };
   // 1. column block and variant (register- or shared-memory-staged) of the y-FFT pass
   int best_l = p->col_lcw, best_r = p->fft_reg[1];
-  for (int r = 1; r >= 0 && st == DPS_OK; --r)
+  for (int r = 2; r >= 0 && st == DPS_OK; --r)
     for (int l = 0; l <= 3 && st == DPS_OK; ++l) {
       if ((l == best_l && r == best_r) || !set_width(l, r)) continue;
       st = measure(&t);
@@ -593,7 +593,7 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
 
 dps_status dpstokes_plan_set_fft(dps_plan_t plan, int32_t row_register, int32_t col_register, int32_t col_width) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || (row_register != 0 && row_register != 1) || (col_register != 0 && col_register != 1))
+  if (!p || (row_register != 0 && row_register != 1) || col_register < 0 || col_register > 2)
     return DPS_ERR_INVALID_ARG;
   int l = -1;
   for (int k = 0; k <= 3; ++k)

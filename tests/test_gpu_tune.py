@@ -46,7 +46,7 @@ def test_every_fft_shape_keeps_the_product(precision, bar, nxy):
     U0, W0 = U0.cpu().numpy(), W0.cpu().numpy()
     tried = set()
     for rr in (0, 1):
-        for cr in (0, 1):
+        for cr in (0, 1, 2):
             for w in (1, 2, 4, 8):
                 try:
                     plan.set_fft(rr, cr, w)
@@ -59,9 +59,11 @@ def test_every_fft_shape_keeps_the_product(precision, bar, nxy):
                 torch.cuda.synchronize()
                 assert rel_l2(U1.cpu().numpy(), U0) <= bar, (rr, cr, w)
                 assert rel_l2(W1.cpu().numpy(), W0) <= bar, (rr, cr, w)
-    assert {r for r, _, _ in tried} == {0, 1} and {c for _, c, _ in tried} == {0, 1}
+    assert {r for r, _, _ in tried} == {0, 1} and {c for _, c, _ in tried} == {0, 1, 2}
     with pytest.raises(binding.DpsError):
         plan.set_fft(2, 0, 2)
+    with pytest.raises(binding.DpsError):
+        plan.set_fft(0, 3, 2)
     with pytest.raises(binding.DpsError):
         plan.set_fft(0, 0, 3)
     plan.close()
