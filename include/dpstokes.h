@@ -203,6 +203,15 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
  * sizes within the thread and shared-memory limits; dpstokes_plan_info reports the shapes in use. */
 dps_status dpstokes_plan_set_fft(dps_plan_t plan, int32_t row_register, int32_t col_register, int32_t col_width);
 
+/* Sets the wavenumber-space pipeline shape by hand (no counterpart in the paper): `solve_blocks`
+ * persistent blocks of the FP64 solve (1 .. the number the plan's workspace was sized for, which
+ * dpstokes_plan_info reports as solve_blocks right after creation) and `nchunks` column chunks
+ * (1, 2, 4 or 8, at least 64 x-wavenumbers each) whose FP64 solves run on a plan-owned stream
+ * beside the float transforms of the neighbouring chunks.  Results do not depend on the shape
+ * beyond summation order.  DPS_ERR_INVALID_ARG (plan unchanged) when plan is NULL or a value is
+ * out of range. */
+dps_status dpstokes_plan_set_pipeline(dps_plan_t plan, int32_t solve_blocks, int32_t nchunks);
+
 /* Per-stage timing.  With timing enabled, every apply brackets each kernel launch with a pair of
  * CUDA events on the stream that launch runs on (the wavenumber-space stages run in column chunks
  * on two internal streams forked from and joined back to the caller's stream, so their kernels

@@ -135,6 +135,7 @@ def load(path=None):
         "dpstokes_debug_run": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, _I32]),
         "dpstokes_debug_copy": (_I32, [_P, _I32, _P, _I64, _P]),
         "dpstokes_plan_set_fft": (_I32, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+        "dpstokes_plan_set_pipeline": (_I32, [_P, ctypes.c_int32, ctypes.c_int32]),
         "dpstokes_plan_autotune": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
         "dpstokes_apply_batch": (_I32, [ctypes.POINTER(dps_request), _I32, _P]),
         "dpstokes_batch_prepare": (_I32, []),
@@ -354,6 +355,12 @@ class Plan:
         st = load().dpstokes_plan_set_fft(self.handle, int(row_register), int(col_register), int(col_width))
         if st != DPS_OK:
             raise DpsError(st, "dpstokes_plan_set_fft")
+
+    def set_pipeline(self, solve_blocks, nchunks):
+        """Set the FP64 solve's persistent grid and the column chunks by hand; raises if out of range."""
+        st = load().dpstokes_plan_set_pipeline(self.handle, int(solve_blocks), int(nchunks))
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_plan_set_pipeline")
 
     def autotune(self, pos, F, T=None, U=None, W=None, stream=None):
         """Pick launch shapes by timing applies on these particles; returns the best time in ms."""

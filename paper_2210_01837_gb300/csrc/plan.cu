@@ -611,6 +611,19 @@ dps_status dpstokes_plan_set_fft(dps_plan_t plan, int32_t row_register, int32_t 
   return DPS_ERR_INVALID_ARG;
 }
 
+dps_status dpstokes_plan_set_pipeline(dps_plan_t plan, int32_t solve_blocks, int32_t nchunks) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || solve_blocks < 1 || solve_blocks > p->bvp_blocks_max) return DPS_ERR_INVALID_ARG;
+  if (nchunks != 1 && nchunks != 2 && nchunks != 4 && nchunks != 8) return DPS_ERR_INVALID_ARG;
+  const int old = p->nchunks;
+  if (!dps::set_chunks(*p, nchunks)) {
+    dps::set_chunks(*p, old);
+    return DPS_ERR_INVALID_ARG;
+  }
+  p->bvp_blocks = solve_blocks;
+  return DPS_OK;
+}
+
 dps_status dpstokes_enable_timing(dps_plan_t plan, int32_t enable) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p) return DPS_ERR_INVALID_ARG;

@@ -83,6 +83,7 @@ def test_null_plan_rejected(lib):
     st, _ = binding.dpstokes_plan_info(None)
     assert st == binding.DPS_ERR_INVALID_ARG
     assert binding.load().dpstokes_plan_set_fft(None, 1, 1, 2) == binding.DPS_ERR_INVALID_ARG
+    assert binding.load().dpstokes_plan_set_pipeline(None, 1, 1) == binding.DPS_ERR_INVALID_ARG
     binding.dpstokes_destroy(None)
 
 

@@ -67,3 +67,29 @@ def test_every_fft_shape_keeps_the_product(precision, bar, nxy):
     with pytest.raises(binding.DpsError):
         plan.set_fft(0, 0, 3)
     plan.close()
+
+
+@pytest.mark.parametrize("precision,bar", [("mixed", 1e-6), ("fp64", 1e-12)])
+def test_every_pipeline_shape_keeps_the_product(precision, bar):
+    """Solve grids and column chunks set by hand give the same product."""
+    import torch
+    params = small_params("bottom_wall", nx=512, ny=144, nz=33, zmax=6.0)
+    pos, F, T = random_particles(params, 2000, 79)
+    plan = binding.Plan.from_params(params, with_torque=True, precision=precision, max_n=len(pos))
+    args = (to_dev(pos), to_dev(F), to_dev(T))
+    U0, W0 = plan.apply(*args, check=True)
+    U0, W0 = U0.cpu().numpy(), W0.cpu().numpy()
+    bmax = plan.info().solve_blocks
+    for blocks in sorted({1, max(1, bmax // 3), bmax}):
+        for chunks in (1, 2, 4):
+            plan.set_pipeline(blocks, chunks)
+            info = plan.info()
+            assert (info.solve_blocks, info.nchunks) == (blocks, chunks)
+            U1, W1 = plan.apply(*args, check=True)
+            torch.cuda.synchronize()
+            assert rel_l2(U1.cpu().numpy(), U0) <= bar, (blocks, chunks)
+            assert rel_l2(W1.cpu().numpy(), W0) <= bar, (blocks, chunks)
+    for bad in ((0, 1), (bmax + 1, 1), (1, 3), (1, 8)):  # 8 chunks need 512 x-wavenumbers
+        with pytest.raises(binding.DpsError):
+            plan.set_pipeline(*bad)
+    plan.close()
