@@ -905,8 +905,13 @@ __device__ __forceinline__ void ld_row(const double* p, double (&o)[PG]) {
 // The planes stream through two shared-memory slots of cz planes (cp.async, double-buffered).
 template <typename T> __host__ __device__ constexpr int fwd_max_threads() { return sizeof(T) == 4 ? 384 : 512; }
 
-template <typename T, int PG, bool TQ>
-__global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry g, const T* __restrict__ ct,
+// MB = 3: the compact instantiation for blocks of at most 9 warps (nz <= 72 at 8 rows per warp) of
+// the six-field form, compiled for three resident blocks per SM (registers are allocated 8 per thread at a time, so
+// 76 would round up to 80 and leave room for two 9-warp blocks only).  MB = 0: the thread limit
+// alone bounds the compilation.
+constexpr int kFwdCompactThreads = 288;
+template <typename T, int PG, bool TQ, int MB = 0>
+__global__ void __launch_bounds__(MB == 3 ? kFwdCompactThreads : fwd_max_threads<T>(), MB) fwd_lane_kernel(Geometry g, const T* __restrict__ ct,
                                                                         const T* __restrict__ dct, int npad,
                                                                         const cplx<T>* __restrict__ grid,
                                                                         cplx<T>* __restrict__ kbuf,
@@ -930,6 +935,7 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
   const int clo = zrange[0], chi = zrange[1];
   const size_t plane = (size_t)g.ny * g.pitch;
   const int col = kt.col[lane];
+  const T hkx = (T)kt.hkx[lane], hky = (T)kt.hky[lane];  // k/2, narrowed once (not per plane)
   cplx<T> acc[3][PG];
 #pragma unroll
   for (int o = 0; o < 3; ++o)
@@ -978,7 +984,6 @@ __global__ void __launch_bounds__(fwd_max_threads<T>()) fwd_lane_kernel(Geometry
       // a_o = f_o + (1/2)(i k x tau)_o in slots 0..2, b_x = -tau_y/2, b_y = tau_x/2 in slots 3, 4
       for (int cl = wi; cl < nc; cl += nwarps) {
         cplx<T>* v = sV + (size_t)cl * NF * kLaneK + lane;
-        const T hkx = (T)kt.hkx[lane], hky = (T)kt.hky[lane];  // k/2
         const cplx<T> tx = v[3 * kLaneK], ty = v[4 * kLaneK], tz = v[5 * kLaneK];
         v[0] = v[0] + mul_i(scl(tz, hky));
         v[kLaneK] = v[kLaneK] - mul_i(scl(tz, hkx));
@@ -1321,6 +1326,9 @@ int bvp_prepare(Plan& p) {
     if (!allow_smem(fwd_lane_kernel<T, PG, true>) || !allow_smem(fwd_lane_kernel<T, PG, false>) ||
         !allow_smem(fwd_lane_kernel<T, PW, true>) || !allow_smem(fwd_lane_kernel<T, PW, false>))
       return 0;
+    if constexpr (sizeof(T) == 4) {
+      if (!allow_smem(fwd_lane_kernel<T, PG, true, 3>)) return 0;
+    }
   }
   const size_t bl = bwd_lane_smem<T>(p.g);
   if (bl > 0) {
@@ -1347,7 +1355,18 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
     constexpr int PG = fwd_pg<T>(), PW = fwd_pg_wide<T>();
     const T* ct = reinterpret_cast<const T*>(p.kt.ct);
     const T* dct = reinterpret_cast<const T*>(p.kt.dct);
-    if (fc.pg == PG) {
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      // the six-field (spectral-curl) form only: the three-field form fits three blocks per SM as it
+      // is (70 registers) and measured slower compact (5.20 -> 5.30 ms on rollers_1m)
+      if (fc.pg == PG && fc.threads <= kFwdCompactThreads && g.spectral_curl) {
+        fwd_lane_kernel<T, PG, true, 3><<<lb, fc.threads, fc.smem, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange,
+                                                                        kx0, w, fc.cz);
+        done = true;
+      }
+    }
+    if (done) {
+    } else if (fc.pg == PG) {
       if (g.spectral_curl)
         fwd_lane_kernel<T, PG, true><<<lb, fc.threads, fc.smem, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0,
                                                                      w, fc.cz);
