@@ -522,6 +522,54 @@ __global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, con
 // W_{Ns R}^{(jj mod Ns) r} (stages after the first), and stores X_r as element
 // (jj / Ns) Ns R + (jj mod Ns) + r Ns through dst(element, b, X_r).  With `barrier` every thread
 // has read its inputs before any thread writes (in-place update).
+// The in-place shared buffer of a register-staged transform: value i at p[i + PW (i >> 4)].
+template <int PW>
+__device__ __forceinline__ int padw(int i) { return i + PW * (i >> 4); }
+
+template <typename T, int PW>
+struct ShBuf {
+  cplx<T>* p;
+  int lb;
+};
+
+// R values e0 + r es (r < R) of sequence b: through the accessor, or, for the shared buffer, from
+// one padded base plus a padded stride when the flat stride es 2^lb is a multiple of 16 (then the
+// padding is linear in r), which saves the per-value index arithmetic.
+template <typename T, int R, class Src>
+__device__ __forceinline__ void load_all(cplx<T>* v, const Src& src, int e0, int es, int b) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = src(e0 + r * es, b);
+}
+template <typename T, int R, int PW>
+__device__ __forceinline__ void load_all(cplx<T>* v, const ShBuf<T, PW>& sb, int e0, int es, int b) {
+  const int i0 = (e0 << sb.lb) + b, S = es << sb.lb;
+  if ((S & 15) == 0) {
+    const int p0 = padw<PW>(i0), Sp = S + PW * (S >> 4);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = sb.p[p0 + r * Sp];
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = sb.p[padw<PW>(i0 + r * S)];
+  }
+}
+template <typename T, int R, class Dst>
+__device__ __forceinline__ void store_all(const cplx<T>* v, const Dst& dst, int e0, int es, int b) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) dst(e0 + r * es, b, v[r]);
+}
+template <typename T, int R, int PW>
+__device__ __forceinline__ void store_all(const cplx<T>* v, const ShBuf<T, PW>& sb, int e0, int es, int b) {
+  const int i0 = (e0 << sb.lb) + b, S = es << sb.lb;
+  if ((S & 15) == 0) {
+    const int p0 = padw<PW>(i0), Sp = S + PW * (S >> 4);
+#pragma unroll
+    for (int r = 0; r < R; ++r) sb.p[p0 + r * Sp] = v[r];
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sb.p[padw<PW>(i0 + r * S)] = v[r];
+  }
+}
+
 template <typename T, int R, int DIR, class Src, class Dst>
 __device__ __forceinline__ void reg_stage(const FftPlan& fp, int s, int Ns, int lb, const cplx<T>* __restrict__ tw,
                                           const Src& src, const Dst& dst, bool barrier) {
@@ -534,15 +582,14 @@ __device__ __forceinline__ void reg_stage(const FftPlan& fp, int s, int Ns, int 
   for (int r = 0; r < R; ++r) v[r] = mk<T>((T)0, (T)0);
   int ob = jj * R;
   if (act) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src(jj + r * nr, b);
+    load_all<T, R>(v, src, jj, nr, b);
     if (s > 0) {
       const int q = (int)(((unsigned long long)jj * fp.magic[s]) >> 40);
       const int k = jj - q * Ns;
-      const int tstep = n / (Ns * R);
+      const int kt = k * (n / (Ns * R));  // twiddle step of input r: W_{Ns R}^{k r} = W_n^{kt r}
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cplx<T> w = tw[k * r * tstep];
+        cplx<T> w = tw[kt * r];
         if (DIR > 0) w.y = -w.y;
         v[r] = v[r] * w;
       }
@@ -551,10 +598,7 @@ __device__ __forceinline__ void reg_stage(const FftPlan& fp, int s, int Ns, int 
     Dft<T, R, DIR>::run(v);
   }
   if (barrier) __syncthreads();
-  if (act) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) dst(ob + r * Ns, b, v[r]);
-  }
+  if (act) store_all<T, R>(v, dst, ob, Ns, b);
 }
 
 template <typename T, int DIR, class Src, class Dst>
@@ -576,14 +620,10 @@ __device__ __forceinline__ void reg_stage_any(const FftPlan& fp, int s, int Ns, 
 // orders this unit's first shared writes after the previous unit's last shared reads.  With
 // DST_SMEM the last stage writes the shared buffer too (followed by a barrier), for an epilogue.
 // PW: pad elements per 16 in the shared buffer (1; 2 keeps float pairs 16-byte aligned for cp.async).
-template <int PW>
-__device__ __forceinline__ int padw(int i) { return i + PW * (i >> 4); }
-
 template <typename T, int DIR, bool DST_SMEM, int PW = 1, class Src, class Dst>
 __device__ __forceinline__ void reg_fft(cplx<T>* buf, const FftPlan& fp, int lb, const cplx<T>* tw, const Src& gsrc,
                                         const Dst& gdst) {
-  auto ssrc = [&](int e, int b) { return buf[padw<PW>((e << lb) + b)]; };
-  auto sdst = [&](int e, int b, cplx<T> v) { buf[padw<PW>((e << lb) + b)] = v; };
+  const ShBuf<T, PW> ssrc{buf, lb}, sdst{buf, lb};
   const int S = fp.nstages;
   if (S == 1) {
     // in place in HBM as well (the column pass and the inverse row pass overwrite their input)
@@ -745,6 +785,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
       for (int t = threadIdx.x; t < pts; t += blockDim.x) {
         const int y = t >> lcw, b = t & (cw - 1);
         if (b < ncols) async_elem(dst + padw<PW>(t), base + (size_t)y * g.pitch + b);
+        else dst[padw<PW>(t)] = mk<T>((T)0, (T)0);  // columns past the x range transform as zeros
       }
     }
     cp_commit();
@@ -762,7 +803,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
     if (u + gridDim.x < um.total) issue(u + gridDim.x, nxt);
     reg_fft<T, DIR, false, PW>(
         cur, fp, lcw, tw,
-        [&](int y, int b) { return b < ncols ? cur[padw<PW>((y << lcw) + b)] : mk<T>((T)0, (T)0); },
+        ShBuf<T, PW>{cur, lcw},
         [&](int y, int b, cplx<T> v) {
           if (b < ncols) base[(size_t)y * g.pitch + b] = v;
         });
