@@ -159,7 +159,7 @@ struct Server {
     b += nmax * (rec + 8 + 15 * 8) + 3 * nbins * 4;                      // records, bins, staging
     b += blocks * kBvpThreads * nz * (3 * 16 + 3 * 8 + 2 * ts);          // solve workspace
     b += 3 * nz * K * 2 * ts + 12 * K * 2 * ts;                          // kbuf, kaux
-    b += 8 * nz * (nz + 32) * ts + (nx + ny) * 16 + 16 * nz * 8;         // tables
+    b += 8 * nz * (nz + 32) * ts + 3 * (nx + ny) * 16 + 16 * nz * 8;     // tables (twiddles: length n + stages <= 2 n)
     return b + b / 8 + (256 << 10);
   }
 

@@ -570,7 +570,35 @@ __device__ __forceinline__ void store_all(const cplx<T>* v, const ShBuf<T, PW>& 
   }
 }
 
-template <typename T, int R, int DIR, class Src, class Dst>
+// v[r] *= row[r] (conjugated for the inverse), r = 1 .. R-1, row = one row of a stage-twiddle
+// table (row[0] = 1); float rows of even R are 16-byte aligned and load two twiddles at a time.
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void apply_twiddles(cplx<T>* v, const cplx<T>* __restrict__ row) {
+  if (sizeof(T) == 4 && R % 2 == 0) {
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+      const float4 q = *reinterpret_cast<const float4*>(row + r);
+      cplx<T> w1 = mk<T>((T)q.z, (T)q.w);
+      if (DIR > 0) w1.y = -w1.y;
+      if (r > 0) {
+        cplx<T> w0 = mk<T>((T)q.x, (T)q.y);
+        if (DIR > 0) w0.y = -w0.y;
+        v[r] = v[r] * w0;
+      }
+      v[r + 1] = v[r + 1] * w1;
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cplx<T> w = row[r];
+      if (DIR > 0) w.y = -w.y;
+      v[r] = v[r] * w;
+    }
+  }
+}
+
+// tw: with ST the stage-twiddle table of this transform (FftPlan::toff), else the length-n table
+template <typename T, int R, int DIR, bool ST, class Src, class Dst>
 __device__ __forceinline__ void reg_stage(const FftPlan& fp, int s, int Ns, int lb, const cplx<T>* __restrict__ tw,
                                           const Src& src, const Dst& dst, bool barrier) {
   const int n = fp.n, nr = n / R, total = nr << lb;
@@ -586,12 +614,16 @@ __device__ __forceinline__ void reg_stage(const FftPlan& fp, int s, int Ns, int 
     if (s > 0) {
       const int q = (int)(((unsigned long long)jj * fp.magic[s]) >> 40);
       const int k = jj - q * Ns;
-      const int kt = k * (n / (Ns * R));  // twiddle step of input r: W_{Ns R}^{k r} = W_n^{kt r}
+      if (ST) {
+        apply_twiddles<T, R, DIR>(v, tw + fp.toff[s] + k * R);  // row k of the stage's W_{Ns R}^{k r}
+      } else {
+        const int kt = k * (n / (Ns * R));  // W_{Ns R}^{k r} = W_n^{kt r}
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        cplx<T> w = tw[kt * r];
-        if (DIR > 0) w.y = -w.y;
-        v[r] = v[r] * w;
+        for (int r = 1; r < R; ++r) {
+          cplx<T> w = tw[kt * r];
+          if (DIR > 0) w.y = -w.y;
+          v[r] = v[r] * w;
+        }
       }
       ob = q * Ns * R + k;
     }
@@ -601,18 +633,18 @@ __device__ __forceinline__ void reg_stage(const FftPlan& fp, int s, int Ns, int 
   if (act) store_all<T, R>(v, dst, ob, Ns, b);
 }
 
-template <typename T, int DIR, class Src, class Dst>
+template <typename T, int DIR, bool ST, class Src, class Dst>
 __device__ __forceinline__ void reg_stage_any(const FftPlan& fp, int s, int Ns, int lb, const cplx<T>* tw,
                                               const Src& src, const Dst& dst, bool barrier) {
   switch (fp.radix[s]) {
-    case 16: reg_stage<T, 16, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
-    case 12: reg_stage<T, 12, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
-    case 8: reg_stage<T, 8, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
-    case 4: reg_stage<T, 4, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
-    case 2: reg_stage<T, 2, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
-    case 3: reg_stage<T, 3, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
-    case 5: reg_stage<T, 5, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
-    default: reg_stage<T, 7, DIR>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 16: reg_stage<T, 16, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 12: reg_stage<T, 12, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 8: reg_stage<T, 8, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 4: reg_stage<T, 4, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 2: reg_stage<T, 2, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 3: reg_stage<T, 3, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    case 5: reg_stage<T, 5, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
+    default: reg_stage<T, 7, DIR, ST>(fp, s, Ns, lb, tw, src, dst, barrier); break;
   }
 }
 
@@ -620,7 +652,9 @@ __device__ __forceinline__ void reg_stage_any(const FftPlan& fp, int s, int Ns, 
 // orders this unit's first shared writes after the previous unit's last shared reads.  With
 // DST_SMEM the last stage writes the shared buffer too (followed by a barrier), for an epilogue.
 // PW: pad elements per 16 in the shared buffer (1; 2 keeps float pairs 16-byte aligned for cp.async).
-template <typename T, int DIR, bool DST_SMEM, int PW = 1, class Src, class Dst>
+// ST: tw is the stage-twiddle table (column passes) rather than the length-n table (row passes,
+// whose tighter register budget the row loads do not fit)
+template <typename T, int DIR, bool DST_SMEM, bool ST, int PW = 1, class Src, class Dst>
 __device__ __forceinline__ void reg_fft(cplx<T>* buf, const FftPlan& fp, int lb, const cplx<T>* tw, const Src& gsrc,
                                         const Dst& gdst) {
   const ShBuf<T, PW> ssrc{buf, lb}, sdst{buf, lb};
@@ -628,26 +662,26 @@ __device__ __forceinline__ void reg_fft(cplx<T>* buf, const FftPlan& fp, int lb,
   if (S == 1) {
     // in place in HBM as well (the column pass and the inverse row pass overwrite their input)
     if (DST_SMEM) {
-      reg_stage_any<T, DIR>(fp, 0, 1, lb, tw, gsrc, sdst, true);
+      reg_stage_any<T, DIR, ST>(fp, 0, 1, lb, tw, gsrc, sdst, true);
       __syncthreads();
     } else {
-      reg_stage_any<T, DIR>(fp, 0, 1, lb, tw, gsrc, gdst, true);
+      reg_stage_any<T, DIR, ST>(fp, 0, 1, lb, tw, gsrc, gdst, true);
     }
     return;
   }
-  reg_stage_any<T, DIR>(fp, 0, 1, lb, tw, gsrc, sdst, true);
+  reg_stage_any<T, DIR, ST>(fp, 0, 1, lb, tw, gsrc, sdst, true);
   __syncthreads();
   int Ns = fp.radix[0];
   for (int s = 1; s < S - 1; ++s) {
-    reg_stage_any<T, DIR>(fp, s, Ns, lb, tw, ssrc, sdst, true);
+    reg_stage_any<T, DIR, ST>(fp, s, Ns, lb, tw, ssrc, sdst, true);
     __syncthreads();
     Ns *= fp.radix[s];
   }
   if (DST_SMEM) {
-    reg_stage_any<T, DIR>(fp, S - 1, Ns, lb, tw, ssrc, sdst, true);
+    reg_stage_any<T, DIR, ST>(fp, S - 1, Ns, lb, tw, ssrc, sdst, true);
     __syncthreads();
   } else {
-    reg_stage_any<T, DIR>(fp, S - 1, Ns, lb, tw, ssrc, gdst, false);
+    reg_stage_any<T, DIR, ST>(fp, S - 1, Ns, lb, tw, ssrc, gdst, false);
   }
 }
 
@@ -670,7 +704,7 @@ __global__ void DPS_REG_FFT_BOUNDS row_r2c_reg_kernel(Geometry g, FftPlan fp, co
     const bool has1 = 2 * j + 1 < g.ny;
     T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + 2 * j) * rowlen;
     const T* row1 = row0 + rowlen;
-    reg_fft<T, -1, true>(buf, fp, 0, tw, [&](int e, int) { return mk<T>(row0[e], has1 ? row1[e] : (T)0); },
+    reg_fft<T, -1, true, false>(buf, fp, 0, tw, [&](int e, int) { return mk<T>(row0[e], has1 ? row1[e] : (T)0); },
                          [](int, int, cplx<T>) {});
     cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
     cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row0 + rowlen);
@@ -703,7 +737,7 @@ __global__ void DPS_REG_FFT_BOUNDS row_c2r_reg_kernel(Geometry g, FftPlan fp, co
     T* row1 = row0 + rowlen;
     const cplx<T>* c0 = reinterpret_cast<const cplx<T>*>(row0);
     const cplx<T>* c1 = reinterpret_cast<const cplx<T>*>(row1);
-    reg_fft<T, +1, false>(
+    reg_fft<T, +1, false, false>(
         buf, fp, 0, tw,
         [&](int e, int) {
           const bool lo = e <= nx / 2;
@@ -734,7 +768,7 @@ __global__ void DPS_REG_FFT_BOUNDS col_reg_kernel(Geometry g, FftPlan fp, const 
     const int kx0 = kxs + (j << lcw);
     const int ncols = min(cw, kxe - kx0);
     cplx<T>* base = grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
-    reg_fft<T, DIR, false>(
+    reg_fft<T, DIR, false, true>(
         buf, fp, lcw, tw,
         [&](int y, int b) { return b < ncols ? base[(size_t)y * g.pitch + b] : mk<T>((T)0, (T)0); },
         [&](int y, int b, cplx<T> v) {
@@ -801,7 +835,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
     cp_wait_all();
     __syncthreads();  // this unit staged; every thread is done with the previous unit (in nxt)
     if (u + gridDim.x < um.total) issue(u + gridDim.x, nxt);
-    reg_fft<T, DIR, false, PW>(
+    reg_fft<T, DIR, false, true, PW>(
         cur, fp, lcw, tw,
         ShBuf<T, PW>{cur, lcw},
         [&](int y, int b, cplx<T> v) {
@@ -1004,22 +1038,23 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const cplx<T>* twy = reinterpret_cast<const cplx<T>*>(p.tab.twy);
   const int lcw = p.col_lcw;
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
+  const cplx<T>* tsy = reinterpret_cast<const cplx<T>*>(p.tab.tsy);
   if (p.fft_reg[1] == 2) {
     const int th = reg_threads(p.fy, lcw);
     const size_t sm = pipe_smem<T>(g.ny << lcw);
     if (dir < 0)
-      col_pipe_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+      col_pipe_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
     else
-      col_pipe_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+      col_pipe_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
     return;
   }
   if (p.fft_reg[1]) {
     const int th = reg_threads(p.fy, lcw);
     const size_t sm = reg_smem<T>(g.ny << lcw);
     if (dir < 0)
-      col_reg_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+      col_reg_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
     else
-      col_reg_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, twy, grid, p.zrange, lcw, kxs, kxe);
+      col_reg_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
     return;
   }
   const size_t sm = col_smem<T>(g, lcw);

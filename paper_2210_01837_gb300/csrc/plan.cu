@@ -32,10 +32,16 @@ bool fft_plan(int n, FftPlan& fp) {
   for (int p : {3, 5, 7})
     while (m % p == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = p; m /= p; }
   unsigned long long ns = 1;
+  int off = 0;
   for (int s = 0; s < fp.nstages; ++s) {
     fp.magic[s] = (1ull << 40) / ns + 1;
+    if (s > 0) {
+      fp.toff[s] = off;
+      off += ((int)ns * fp.radix[s] + 1) & ~1;  // even offsets: float rows of even R stay 16-byte aligned
+    }
     ns *= (unsigned long long)fp.radix[s];
   }
+  fp.toff[0] = off;
   return m == 1 && n < (1 << 20);
 }
 
@@ -56,6 +62,33 @@ cudaError_t upload_twiddles(void** dst, int n, int64_t& bytes) {
     const double a = -2.0 * M_PI * (double)t / (double)n;
     h[2 * t] = (T)cos(a);
     h[2 * t + 1] = (T)sin(a);
+  }
+  cudaError_t e = cudaMalloc(dst, h.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  bytes += (int64_t)(h.size() * sizeof(T));
+  return cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Stage twiddles: for each stage s >= 1 (span Ns, radix R) the values W_{Ns R}^{k r} =
+// exp(-2 pi i k r / (Ns R)), k < Ns, r < R, row k contiguous, so a butterfly reads its R twiddles
+// from one row instead of R scattered entries of the length-n table.
+template <typename T>
+cudaError_t upload_stage_twiddles(void** dst, const FftPlan& fp, int64_t& bytes) {
+  std::vector<T> h(2 * (size_t)std::max(fp.toff[0], 1), (T)0);
+  int ns = 1;
+  for (int s = 0; s < fp.nstages; ++s) {
+    const int R = fp.radix[s];
+    if (s > 0) {
+      for (int k = 0; k < ns; ++k)
+        for (int r = 0; r < R; ++r) {
+          const long long m = ((long long)k * r) % ((long long)ns * R);  // argument reduced to [0, 1)
+          const double a = -2.0 * M_PI * (double)m / ((double)ns * R);
+          const size_t i = (size_t)fp.toff[s] + (size_t)k * R + r;
+          h[2 * i] = (T)cos(a);
+          h[2 * i + 1] = (T)sin(a);
+        }
+    }
+    ns *= R;
   }
   cudaError_t e = cudaMalloc(dst, h.size() * sizeof(T));
   if (e != cudaSuccess) return e;
@@ -86,7 +119,8 @@ void free_plan(Plan* p) {
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   for (int i = 0; i < 2; ++i)
     if (p->side[i]) cudaStreamDestroy(p->side[i]);
-  void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->kt.ct, p->kt.dct,
+  void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->tab.tsx, p->tab.tsy,
+                  p->kt.ct, p->kt.dct,
                   p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.cmat, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
                   p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
   for (void* q : ptrs)
@@ -203,6 +237,8 @@ dps_status build_tables(Plan* p) {
   if ((e = upload<T>(&p->tab.zeta, zeta, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twx, g.nx, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twy, g.ny, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload_stage_twiddles<T>(&p->tab.tsx, p->fx, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload_stage_twiddles<T>(&p->tab.tsy, p->fy, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   return DPS_OK;
 }
 
