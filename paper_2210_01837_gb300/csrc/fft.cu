@@ -523,10 +523,11 @@ __global__ void __launch_bounds__(512, 1) col_kernel(Geometry g, FftPlan fp, con
 // (jj / Ns) Ns R + (jj mod Ns) + r Ns through dst(element, b, X_r).  With `barrier` every thread
 // has read its inputs before any thread writes (in-place update).
 // The in-place shared buffer of a register-staged transform: value i at p[i + PW (i >> 4)].
-template <int PW>
-__device__ __forceinline__ int padw(int i) { return i + PW * (i >> 4); }
+template <int PW, int SH = 4>
+__device__ __forceinline__ int padw(int i) { return i + PW * (i >> SH); }
 
-template <typename T, int PW>
+// a shared transform buffer padded with PW values after every 2^SH
+template <typename T, int PW, int SH = 4>
 struct ShBuf {
   cplx<T>* p;
   int lb;
@@ -540,16 +541,16 @@ __device__ __forceinline__ void load_all(cplx<T>* v, const Src& src, int e0, int
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = src(e0 + r * es, b);
 }
-template <typename T, int R, int PW>
-__device__ __forceinline__ void load_all(cplx<T>* v, const ShBuf<T, PW>& sb, int e0, int es, int b) {
+template <typename T, int R, int PW, int SH>
+__device__ __forceinline__ void load_all(cplx<T>* v, const ShBuf<T, PW, SH>& sb, int e0, int es, int b) {
   const int i0 = (e0 << sb.lb) + b, S = es << sb.lb;
-  if ((S & 15) == 0) {
-    const int p0 = padw<PW>(i0), Sp = S + PW * (S >> 4);
+  if ((S & ((1 << SH) - 1)) == 0) {
+    const int p0 = padw<PW, SH>(i0), Sp = S + PW * (S >> SH);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = sb.p[p0 + r * Sp];
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sb.p[padw<PW>(i0 + r * S)];
+    for (int r = 0; r < R; ++r) v[r] = sb.p[padw<PW, SH>(i0 + r * S)];
   }
 }
 template <typename T, int R, class Dst>
@@ -557,16 +558,16 @@ __device__ __forceinline__ void store_all(const cplx<T>* v, const Dst& dst, int 
 #pragma unroll
   for (int r = 0; r < R; ++r) dst(e0 + r * es, b, v[r]);
 }
-template <typename T, int R, int PW>
-__device__ __forceinline__ void store_all(const cplx<T>* v, const ShBuf<T, PW>& sb, int e0, int es, int b) {
+template <typename T, int R, int PW, int SH>
+__device__ __forceinline__ void store_all(const cplx<T>* v, const ShBuf<T, PW, SH>& sb, int e0, int es, int b) {
   const int i0 = (e0 << sb.lb) + b, S = es << sb.lb;
-  if ((S & 15) == 0) {
-    const int p0 = padw<PW>(i0), Sp = S + PW * (S >> 4);
+  if ((S & ((1 << SH) - 1)) == 0) {
+    const int p0 = padw<PW, SH>(i0), Sp = S + PW * (S >> SH);
 #pragma unroll
     for (int r = 0; r < R; ++r) sb.p[p0 + r * Sp] = v[r];
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) sb.p[padw<PW>(i0 + r * S)] = v[r];
+    for (int r = 0; r < R; ++r) sb.p[padw<PW, SH>(i0 + r * S)] = v[r];
   }
 }
 
@@ -654,10 +655,10 @@ __device__ __forceinline__ void reg_stage_any(const FftPlan& fp, int s, int Ns, 
 // PW: pad elements per 16 in the shared buffer (1; 2 keeps float pairs 16-byte aligned for cp.async).
 // ST: tw is the stage-twiddle table (column passes) rather than the length-n table (row passes,
 // whose tighter register budget the row loads do not fit)
-template <typename T, int DIR, bool DST_SMEM, bool ST, int PW = 1, class Src, class Dst>
+template <typename T, int DIR, bool DST_SMEM, bool ST, int PW = 1, int SH = 4, class Src, class Dst>
 __device__ __forceinline__ void reg_fft(cplx<T>* buf, const FftPlan& fp, int lb, const cplx<T>* tw, const Src& gsrc,
                                         const Dst& gdst) {
-  const ShBuf<T, PW> ssrc{buf, lb}, sdst{buf, lb};
+  const ShBuf<T, PW, SH> ssrc{buf, lb}, sdst{buf, lb};
   const int S = fp.nstages;
   if (S == 1) {
     // in place in HBM as well (the column pass and the inverse row pass overwrite their input)
@@ -781,8 +782,13 @@ __global__ void DPS_REG_FFT_BOUNDS col_reg_kernel(Geometry g, FftPlan fp, const 
 // transforms one in place (one butterfly per thread and stage, the last stage writing HBM), cp.async
 // fills the other with the next unit.  The two buffers take most of the SM's shared memory, so a
 // unit can be 4 columns x 3072 rows (a full 32-byte sector per row, half the requests of 2 columns).
+// padding of the unit buffers: float, 2 values per 32 (pairs stay 16-byte aligned for cp.async, and
+// the first stage's stores, 64 values apart across a warp, spread over the banks 2-way instead of
+// 4-way with 2 per 16); double, 1 per 16
 template <typename T>
 __host__ __device__ constexpr int pipe_pad() { return sizeof(cplx<T>) == 8 ? 2 : 1; }
+template <typename T>
+__host__ __device__ constexpr int pipe_pad_shift() { return sizeof(cplx<T>) == 8 ? 5 : 4; }
 constexpr int kPipeMaxThreadsF = 1024, kPipeMaxThreadsD = 512;
 
 template <typename T, int DIR>
@@ -790,10 +796,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
     col_pipe_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ grid,
                     const int* __restrict__ zrange, int lcw, int kxs, int kxe) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int PW = pipe_pad<T>();
+  constexpr int PW = pipe_pad<T>(), SH = pipe_pad_shift<T>();
   const int cw = 1 << lcw;
   const int pts = g.ny << lcw;
-  const int blen = pts + PW * (pts >> 4) + PW;
+  const int blen = pts + PW * (pts >> SH) + PW;
   cplx<T>* const buf0 = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* const buf1 = buf0 + blen;
   const UnitMap um(g, zrange, (kxe - kxs + cw - 1) >> lcw);
@@ -813,13 +819,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
       const int per = cw / E;
       for (int t = threadIdx.x; t < g.ny * per; t += blockDim.x) {
         const int y = t / per, q = t - y * per;
-        cp_async16(dst + padw<PW>((y << lcw) + q * E), base + (size_t)y * g.pitch + q * E);
+        cp_async16(dst + padw<PW, SH>((y << lcw) + q * E), base + (size_t)y * g.pitch + q * E);
       }
     } else {
       for (int t = threadIdx.x; t < pts; t += blockDim.x) {
         const int y = t >> lcw, b = t & (cw - 1);
-        if (b < ncols) async_elem(dst + padw<PW>(t), base + (size_t)y * g.pitch + b);
-        else dst[padw<PW>(t)] = mk<T>((T)0, (T)0);  // columns past the x range transform as zeros
+        if (b < ncols) async_elem(dst + padw<PW, SH>(t), base + (size_t)y * g.pitch + b);
+        else dst[padw<PW, SH>(t)] = mk<T>((T)0, (T)0);  // columns past the x range transform as zeros
       }
     }
     cp_commit();
@@ -835,9 +841,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
     cp_wait_all();
     __syncthreads();  // this unit staged; every thread is done with the previous unit (in nxt)
     if (u + gridDim.x < um.total) issue(u + gridDim.x, nxt);
-    reg_fft<T, DIR, false, true, PW>(
+    reg_fft<T, DIR, false, true, PW, SH>(
         cur, fp, lcw, tw,
-        ShBuf<T, PW>{cur, lcw},
+        ShBuf<T, PW, SH>{cur, lcw},
         [&](int y, int b, cplx<T> v) {
           if (b < ncols) base[(size_t)y * g.pitch + b] = v;
         });
@@ -907,8 +913,8 @@ bool reg_fits(const FftPlan& fp, int lb) {
 
 template <typename T>
 size_t pipe_smem(int points) {
-  constexpr int PW = pipe_pad<T>();
-  return (size_t)2 * (points + PW * (points >> 4) + PW) * sizeof(cplx<T>);
+  constexpr int PW = pipe_pad<T>(), SH = pipe_pad_shift<T>();
+  return (size_t)2 * (points + PW * (points >> SH) + PW) * sizeof(cplx<T>);
 }
 
 template <typename T>
