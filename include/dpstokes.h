@@ -76,7 +76,8 @@ typedef enum {
                                  boundary (footnote to step 1 of Sec. III.D)                     */
   DPS_ERR_OOM = -3,           /* device allocation failed in dpstokes_plan_create               */
   DPS_ERR_CUDA = -4,          /* a CUDA runtime call failed                                      */
-  DPS_ERR_TIMEOUT = -5,       /* reserved for bounded device waits                               */
+  DPS_ERR_TIMEOUT = -5,       /* a bounded wait gave up: a device copy did not complete in about a
+                                 second (TMA column pass), or a server ticket within its timeout */
   DPS_ERR_NONFINITE = -6      /* a non-finite position, force or torque                          */
 } dps_status;
 
@@ -176,7 +177,7 @@ typedef struct {
   int32_t fft_register_rows; /* 1: the x-FFT passes run register-staged (one butterfly per thread
                                and stage, one shared buffer), 0: shared-memory-staged           */
   int32_t fft_register_cols; /* the y-FFT passes: 0 shared-memory-staged, 1 register-staged,
-                               2 register-staged with prefetch                                 */
+                               2 register-staged with cp.async prefetch, 3 with TMA prefetch   */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 
@@ -197,7 +198,8 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
 /* Sets the xy-FFT launch shapes by hand (no counterpart in the paper): `row_register` chooses the
  * register-staged (1) or shared-memory-staged (0) variant of the x-FFT passes, `col_register` that
  * of the y-FFT passes (0 shared-memory-staged, 1 register-staged, 2 register-staged with the next
- * block's columns prefetched), `col_width` (1, 2, 4 or 8) the x-wavenumber columns per block of the
+ * block's columns prefetched by cp.async, 3 the same prefetched by TMA box loads), `col_width` (1, 2,
+ * 4 or 8) the x-wavenumber columns per block of the
  * y pass.  Results do not depend on the shapes beyond summation order.  DPS_ERR_INVALID_ARG (plan
  * unchanged) when plan is NULL, a variant is out of range, or the shape does not fit this plan's
  * sizes within the thread and shared-memory limits; dpstokes_plan_info reports the shapes in use. */

@@ -144,7 +144,10 @@ struct Plan {
   int fft_grid[4];      // resident grids of the persistent FFT passes: rows fwd/inv, columns fwd/inv
   int col_lcw;          // log2 of the column block of the y-FFT pass (default rule or autotuned)
   int fft_reg[2];       // FFT variant of the row and the column pass: 0 smem-staged, 1 register-staged,
-                        // 2 (columns) register-staged with cp.async prefetch
+                        // 2 (columns) register-staged with cp.async prefetch, 3 (columns) the same with
+                        // TMA box loads
+  alignas(64) unsigned char col_tmap[128];  // CUtensorMap of the grid for the TMA column pass
+  int col_tma_rows;     // rows per TMA box of that pass
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)
@@ -233,7 +236,7 @@ __device__ __forceinline__ float narrow_bits(double d) {
 }
 
 // status bits written by kernels
-enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4 };
+enum : int { kStatNonfinite = 1, kStatDomain = 2, kStatInternal = 4, kStatTimeout = 8 };
 
 // host side of the particle stage: the ES normalisation (Eq. 54), the truncation point of the
 // derivative kernel, and the particle-side geometry (kernels, record layout, bins) shared by plans
@@ -260,7 +263,7 @@ template <typename T> int bvp_prepare(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
 // column block 2^lcw and variant of the y-FFT pass (reg: 0 shared-memory-staged, 1 register-staged,
-// 2 register-staged with prefetch); 0 if it does not fit
+// 2 register-staged with cp.async prefetch, 3 register-staged with TMA prefetch); 0 if it does not fit
 template <typename T> int fft_set_col_width(Plan& p, int lcw, int reg);
 // x-FFT pass variant: register-staged (reg = 1) or shared-memory-staged; 0 if it does not fit
 template <typename T> int fft_set_row_variant(Plan& p, int reg);

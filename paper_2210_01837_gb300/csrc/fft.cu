@@ -22,6 +22,9 @@
 // W_{Ns R}^{(j mod Ns) r}, applies an R-point DFT, and stores to (j / Ns) Ns R + (j mod Ns) + r Ns.
 // Radices 8, 4, 2 (hand-written butterflies) and 3, 5, 7 (direct DFT with exact constants).
 // Twiddles W_n^t = exp(-2 pi i t/n) come from a table built in double precision on the host.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "dps_internal.cuh"
@@ -851,6 +854,110 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
   cp_wait_all();  // no copy outstanding at exit
 }
 
+// ---- TMA-staged column pass ----
+// As col_pipe_kernel, but the next unit arrives by TMA: one thread arms the buffer's mbarrier with
+// the unit's byte count and issues ny / bh box loads (2 cw reals x bh rows each) of the grid's
+// tensor map into the buffer, densely ([y][b]); the first FFT stage reads that dense layout and its
+// in-place writes (after the stage's barrier) use the padded one.  Every wait is bounded (about a
+// second): on expiry the block records kStatTimeout, waits (bounded again) for its copies in flight
+// and leaves.
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity to complete; false after about 2^31 cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// unit buffer length in values: the padded layout, rounded up to 128 bytes (TMA destinations)
+template <typename T>
+__host__ __device__ __forceinline__ int tma_buf_len(int points) {
+  const int n = points + pipe_pad<T>() * (points >> pipe_pad_shift<T>()) + pipe_pad<T>();
+  const int q = 128 / (int)sizeof(cplx<T>);
+  return (n + q - 1) / q * q;
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxThreadsD, 1)
+    col_tma_kernel(const __grid_constant__ CUtensorMap tmap, Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
+                   cplx<T>* __restrict__ grid, const int* __restrict__ zrange, int* __restrict__ status, int lcw,
+                   int kxs, int kxe, int bh) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  constexpr int PW = pipe_pad<T>(), SH = pipe_pad_shift<T>();
+  const int cw = 1 << lcw;
+  const int pts = g.ny << lcw;
+  const int blen = tma_buf_len<T>(pts);
+  cplx<T>* const buf0 = reinterpret_cast<cplx<T>*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~(uintptr_t)127);
+  cplx<T>* const buf1 = buf0 + blen;
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(buf1 + blen);
+  const UnitMap um(g, zrange, (kxe - kxs + cw - 1) >> lcw);
+  const unsigned bytes = (unsigned)pts * (unsigned)sizeof(cplx<T>);
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](long long u, int w) {  // thread 0
+    int f, c, j;
+    um.at(u, f, c, j);
+    const int kx0 = kxs + (j << lcw);
+    const int y0 = (f * g.nz + c) * g.ny;
+    cplx<T>* dst = w ? buf1 : buf0;
+    // the buffer's last contents were written by the generic proxy (the previous unit's stages)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&bars[w], bytes);
+    for (int r0 = 0; r0 < g.ny; r0 += bh) tma_load_2d(dst + (r0 << lcw), &tmap, 2 * kx0, y0 + r0, &bars[w]);
+  };
+  unsigned phase = 0;  // bit w: parity of the next completion of barrier w
+  long long u = blockIdx.x;
+  if (u < um.total && threadIdx.x == 0) issue(u, 0);
+  for (int w = 0; u < um.total; u += gridDim.x, w ^= 1) {
+    cplx<T>* const cur = w ? buf1 : buf0;
+    const bool ok = mbar_wait(&bars[w], (phase >> w) & 1u);
+    phase ^= 1u << w;
+    // also: every thread is done with the previous unit (the other buffer)
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(status, kStatTimeout);
+        mbar_wait(&bars[w], ((phase >> w) & 1u) ^ 1u);  // give this unit's copies a second chance to land
+      }
+      return;
+    }
+    if (u + gridDim.x < um.total && threadIdx.x == 0) issue(u + gridDim.x, w ^ 1);
+    int f, c, j;
+    um.at(u, f, c, j);
+    const int kx0 = kxs + (j << lcw);
+    const int ncols = min(cw, kxe - kx0);
+    cplx<T>* base = grid + (size_t)(f * g.nz + c) * g.ny * g.pitch + kx0;
+    reg_fft<T, DIR, false, true, PW, SH>(cur, fp, lcw, tw, ShBuf<T, 0, SH>{cur, lcw},
+                                         [&](int y, int b, cplx<T> v) {
+                                           if (b < ncols) base[(size_t)y * g.pitch + b] = v;
+                                         });
+  }
+}
+
 size_t padded_bytes(int n, size_t esz) { return (size_t)(n + (n >> 4) + 1) * esz; }
 
 template <typename T>
@@ -924,8 +1031,57 @@ bool pipe_fits(const FftPlan& fp, int lb) {
 }
 
 template <typename T>
+size_t tma_smem(int points) { return 128 + (size_t)2 * tma_buf_len<T>(points) * sizeof(cplx<T>) + 16; }
+
+// rows per TMA box: the largest divisor of ny up to 256 whose boxes keep 128-byte alignment in the
+// unit buffer; 0 if there is none
+template <typename T>
+int tma_box_rows(int ny, int lcw) {
+  for (int h = std::min(ny, 256); h >= 1; --h)
+    if (ny % h == 0 && ((size_t)h * (1u << lcw) * sizeof(cplx<T>)) % 128 == 0) return h;
+  return 0;
+}
+
+// the grid as a rank-2 tensor of reals (2 pitch per row, nfields nz ny rows) with boxes of
+// 2^lcw complex columns x bh rows; false when the driver entry point or the encoding is refused
+template <typename T>
+bool encode_col_tmap(Plan& p, int lcw, int bh) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr)
+    return false;
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const Geometry& g = p.g;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * g.pitch, (cuuint64_t)g.nfields * g.nz * g.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * g.pitch * sizeof(T)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2u << lcw), (cuuint32_t)bh};
+  const cuuint32_t estr[2] = {1, 1};
+  CUtensorMap* map = reinterpret_cast<CUtensorMap*>(p.col_tmap);
+  return encode(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, p.grid,
+                dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
 int fft_set_col_width(Plan& p, int lcw, int reg) {
-  if (lcw < 0 || lcw > 3 || reg < 0 || reg > 2) return 0;
+  if (lcw < 0 || lcw > 3 || reg < 0 || reg > 3) return 0;
+  if (reg == 3) {
+    const int maxth = sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxThreadsD;
+    const int th = reg_threads(p.fy, lcw);
+    const size_t sm = tma_smem<T>(p.g.ny << lcw);
+    const int bh = tma_box_rows<T>(p.g.ny, lcw);
+    // box rows of 16-byte multiples; a block never reads past the padded row (pitch is a multiple
+    // of 32 columns and a block starts at a multiple of its width)
+    if (th > maxth || sm > 224 * 1024 || bh == 0 || ((2u << lcw) * sizeof(T)) % 16 != 0) return 0;
+    if (!encode_col_tmap<T>(p, lcw, bh)) return 0;
+    p.col_lcw = lcw;
+    p.fft_reg[1] = 3;
+    p.col_tma_rows = bh;
+    p.fft_grid[2] = resident_grid(col_tma_kernel<T, -1>, th, sm, p.device);
+    p.fft_grid[3] = resident_grid(col_tma_kernel<T, +1>, th, sm, p.device);
+    return 1;
+  }
   if (reg == 2) {
     if (!pipe_fits<T>(p.fy, lcw)) return 0;
     const int th = reg_threads(p.fy, lcw);
@@ -1001,14 +1157,16 @@ int fft_smem_ok(Plan& p) {
   if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
       !allow_smem(col_kernel<T, +1>) || !allow_smem(row_r2c_reg_kernel<T>) || !allow_smem(row_c2r_reg_kernel<T>) ||
       !allow_smem(col_reg_kernel<T, -1>) || !allow_smem(col_reg_kernel<T, +1>) ||
-      !allow_smem(col_pipe_kernel<T, -1>) || !allow_smem(col_pipe_kernel<T, +1>))
+      !allow_smem(col_pipe_kernel<T, -1>) || !allow_smem(col_pipe_kernel<T, +1>) ||
+      !allow_smem(col_tma_kernel<T, -1>) || !allow_smem(col_tma_kernel<T, +1>))
     return 0;
   const bool rr = reg_rows_default<T>(p.fx);
   if (!fft_set_row_variant<T>(p, rr ? 1 : 0) && !fft_set_row_variant<T>(p, rr ? 0 : 1)) return 0;
-  // columns: the prefetched register-staged pass when it fits a wider block than the staged one
+  // columns: the prefetched register-staged pass when it fits a wider block than the staged one,
+  // prefetched by TMA where a box shape fits (3072^2: 12.2 -> 10.7 ms per pass pair), else cp.async
   const int ls = col_lwidth<T>(p);
   for (int l = 3; l > ls; --l)
-    if (fft_set_col_width<T>(p, l, 2)) return 1;
+    if (fft_set_col_width<T>(p, l, 3) || fft_set_col_width<T>(p, l, 2)) return 1;
   if (fft_set_col_width<T>(p, ls, 0)) return 1;
   for (int l = 3; l >= 0; --l)
     if (fft_set_col_width<T>(p, l, 1)) return 1;
@@ -1045,6 +1203,18 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   const int lcw = p.col_lcw;
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
   const cplx<T>* tsy = reinterpret_cast<const cplx<T>*>(p.tab.tsy);
+  if (p.fft_reg[1] == 3) {
+    const int th = reg_threads(p.fy, lcw);
+    const size_t sm = tma_smem<T>(g.ny << lcw);
+    const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(p.col_tmap);
+    if (dir < 0)
+      col_tma_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(map, g, p.fy, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
+                                                          p.col_tma_rows);
+    else
+      col_tma_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(map, g, p.fy, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
+                                                          p.col_tma_rows);
+    return;
+  }
   if (p.fft_reg[1] == 2) {
     const int th = reg_threads(p.fy, lcw);
     const size_t sm = pipe_smem<T>(g.ny << lcw);

@@ -525,6 +525,7 @@ dps_status dpstokes_status(dps_plan_t plan, void* stream) {
   if (v & dps::kStatNonfinite) return DPS_ERR_NONFINITE;
   if (v & dps::kStatDomain) return DPS_ERR_OUT_OF_DOMAIN;
   if (v & dps::kStatInternal) return DPS_ERR_CUDA;
+  if (v & dps::kStatTimeout) return DPS_ERR_TIMEOUT;
   return DPS_OK;
 }
 
@@ -588,7 +589,7 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
   auto better = [&](double cand) { return cand < 0.98 * best; };
   // 1. column block and variant (register- or shared-memory-staged) of the y-FFT pass
   int best_l = p->col_lcw, best_r = p->fft_reg[1];
-  for (int r = 2; r >= 0 && st == DPS_OK; --r)
+  for (int r = 3; r >= 0 && st == DPS_OK; --r)
     for (int l = 0; l <= 3 && st == DPS_OK; ++l) {
       if ((l == best_l && r == best_r) || !set_width(l, r)) continue;
       st = measure(&t);
@@ -629,7 +630,7 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
 
 dps_status dpstokes_plan_set_fft(dps_plan_t plan, int32_t row_register, int32_t col_register, int32_t col_width) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || (row_register != 0 && row_register != 1) || col_register < 0 || col_register > 2)
+  if (!p || (row_register != 0 && row_register != 1) || col_register < 0 || col_register > 3)
     return DPS_ERR_INVALID_ARG;
   int l = -1;
   for (int k = 0; k <= 3; ++k)
