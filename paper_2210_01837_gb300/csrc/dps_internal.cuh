@@ -48,7 +48,7 @@ struct FftPlan {
   int radix[kMaxFftRadices];
   unsigned long long magic[kMaxFftRadices];  // floor(2^40 / Ns) + 1 for the span Ns of each stage
   int toff[kMaxFftRadices];  // stage s >= 1: offset of its twiddles W_{Ns R}^{k r}, [k < Ns][r < R], in the
-                             // stage-twiddle table (tab.tsx / tab.tsy); total length in toff[0]
+                             // stage-twiddle table (tab.tsy, read by the column passes); total length in toff[0]
 };
 
 // Per-kernel (monopole / dipole) ES parameters on the device
@@ -102,8 +102,7 @@ struct Tables {
   double* band;    // [5][nz] doubles: l_n, d_n, u_n, P_n, Q_n of the spectral-integration operator
   void* twx;       // [nx] cplx<T>  exp(-2 pi i t / nx)
   void* twy;       // [ny] cplx<T>  exp(-2 pi i t / ny)
-  void* tsx;       // cplx<T> stage twiddles of the x transform (FftPlan::toff)
-  void* tsy;       // cplx<T> stage twiddles of the y transform
+  void* tsy;       // cplx<T> stage twiddles of the y transform (FftPlan::toff; the x passes read twx)
 };
 
 // per-wavenumber stage: transform tables (T, padded for vector loads) and buffers

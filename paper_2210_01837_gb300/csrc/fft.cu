@@ -15,13 +15,16 @@
 // so HBM traffic overlaps the butterflies and each unit crosses shared memory 2 S + 2 times for S
 // stages.  Register-staged: one butterfly per thread and stage, updated in place in one shared
 // buffer, the first stage reading HBM and the last writing it directly (described further below);
-// for the column pass also with a second buffer that cp.async fills with the next unit.
+// for the column pass also with a second buffer that receives the next unit, by cp.async or by
+// TMA box loads on an mbarrier.
 // The plan picks the variant per pass (default rule at fft_smem_ok, or autotuned / set by hand).
 // Each 1D transform is a self-sorting (Stockham) mixed-radix FFT in shared memory written from the
 // textbook formulation: stage s with radix R and span Ns multiplies input j + r n/R by
 // W_{Ns R}^{(j mod Ns) r}, applies an R-point DFT, and stores to (j / Ns) Ns R + (j mod Ns) + r Ns.
-// Radices 8, 4, 2 (hand-written butterflies) and 3, 5, 7 (direct DFT with exact constants).
-// Twiddles W_n^t = exp(-2 pi i t/n) come from a table built in double precision on the host.
+// Radices 16, 12 (as 4 x 4 and 4 x 3), 8, 4, 2 (hand-written butterflies) and 3, 5, 7 (direct DFT
+// with exact constants).  Twiddles W_n^t = exp(-2 pi i t/n) come from a table built in double
+// precision on the host; the register-staged column passes read per-stage rows W_{Ns R}^{k r}
+// instead (one contiguous row per butterfly).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 

@@ -119,7 +119,7 @@ void free_plan(Plan* p) {
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   for (int i = 0; i < 2; ++i)
     if (p->side[i]) cudaStreamDestroy(p->side[i]);
-  void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->tab.tsx, p->tab.tsy,
+  void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->tab.tsy,
                   p->kt.ct, p->kt.dct,
                   p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.cmat, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
                   p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
@@ -237,7 +237,6 @@ dps_status build_tables(Plan* p) {
   if ((e = upload<T>(&p->tab.zeta, zeta, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twx, g.nx, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twy, g.ny, bytes)) != cudaSuccess) return DPS_ERR_OOM;
-  if ((e = upload_stage_twiddles<T>(&p->tab.tsx, p->fx, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_stage_twiddles<T>(&p->tab.tsy, p->fy, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   return DPS_OK;
 }
