@@ -93,6 +93,16 @@ def test_every_pipeline_shape_keeps_the_product(precision, bar):
             torch.cuda.synchronize()
             assert rel_l2(U1.cpu().numpy(), U0) <= bar, (blocks, chunks)
             assert rel_l2(W1.cpu().numpy(), W0) <= bar, (blocks, chunks)
+    # the prefetched column passes (TMA and cp.async) over column chunks: blocks start at each
+    # chunk's first column
+    for cr in (3, 2):
+        plan.set_fft(0, cr, 4)
+        for chunks in (1, 2, 4):
+            plan.set_pipeline(bmax, chunks)
+            U1, W1 = plan.apply(*args, check=True)
+            torch.cuda.synchronize()
+            assert rel_l2(U1.cpu().numpy(), U0) <= bar, (cr, chunks)
+            assert rel_l2(W1.cpu().numpy(), W0) <= bar, (cr, chunks)
     for bad in ((0, 1), (bmax + 1, 1), (1, 3), (1, 8)):  # 8 chunks need 512 x-wavenumbers
         with pytest.raises(binding.DpsError):
             plan.set_pipeline(*bad)
