@@ -102,7 +102,7 @@ struct Tables {
   double* band;    // [5][nz] doubles: l_n, d_n, u_n, P_n, Q_n of the spectral-integration operator
   void* twx;       // [nx] cplx<T>  exp(-2 pi i t / nx)
   void* twy;       // [ny] cplx<T>  exp(-2 pi i t / ny)
-  void* tsy;       // cplx<T> stage twiddles of the y transform (FftPlan::toff; the x passes read twx)
+  void* tsy;       // cplx<T> stage twiddles of the register-staged y passes (Plan::fyr, FftPlan::toff)
 };
 
 // per-wavenumber stage: transform tables (T, padded for vector loads) and buffers
@@ -126,6 +126,7 @@ struct Plan {
   int64_t max_n;
   Geometry g;
   FftPlan fx, fy;
+  FftPlan fyr;          // y transform of the register-staged column passes (balanced factorisation)
   Tables tab;
   KTabs kt;
   // device buffers

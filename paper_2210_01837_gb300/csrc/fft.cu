@@ -1071,7 +1071,7 @@ int fft_set_col_width(Plan& p, int lcw, int reg) {
   if (lcw < 0 || lcw > 3 || reg < 0 || reg > 3) return 0;
   if (reg == 3) {
     const int maxth = sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxThreadsD;
-    const int th = reg_threads(p.fy, lcw);
+    const int th = reg_threads(p.fyr, lcw);
     const size_t sm = tma_smem<T>(p.g.ny << lcw);
     const int bh = tma_box_rows<T>(p.g.ny, lcw);
     // box rows of 16-byte multiples; a block never reads past the padded row (pitch is a multiple
@@ -1086,8 +1086,8 @@ int fft_set_col_width(Plan& p, int lcw, int reg) {
     return 1;
   }
   if (reg == 2) {
-    if (!pipe_fits<T>(p.fy, lcw)) return 0;
-    const int th = reg_threads(p.fy, lcw);
+    if (!pipe_fits<T>(p.fyr, lcw)) return 0;
+    const int th = reg_threads(p.fyr, lcw);
     const size_t sm = pipe_smem<T>(p.g.ny << lcw);
     p.col_lcw = lcw;
     p.fft_reg[1] = 2;
@@ -1096,8 +1096,8 @@ int fft_set_col_width(Plan& p, int lcw, int reg) {
     return 1;
   }
   if (reg) {
-    if (!reg_fits<T>(p.fy, lcw)) return 0;
-    const int th = reg_threads(p.fy, lcw);
+    if (!reg_fits<T>(p.fyr, lcw)) return 0;
+    const int th = reg_threads(p.fyr, lcw);
     const size_t sm = reg_smem<T>(p.g.ny << lcw);
     p.col_lcw = lcw;
     p.fft_reg[1] = 1;
@@ -1170,6 +1170,9 @@ int fft_smem_ok(Plan& p) {
   const int ls = col_lwidth<T>(p);
   for (int l = 3; l > ls; --l)
     if (fft_set_col_width<T>(p, l, 3) || fft_set_col_width<T>(p, l, 2)) return 1;
+  // at the staged pass's width, TMA on long columns (768 rows, 8 columns: 0.78 -> 0.70 ms per pass
+  // pair; 384 rows: 0.57 staged against 0.66, the units too short for the per-unit barrier work)
+  if (p.g.ny >= 512 && fft_set_col_width<T>(p, ls, 3)) return 1;
   if (fft_set_col_width<T>(p, ls, 0)) return 1;
   for (int l = 3; l >= 0; --l)
     if (fft_set_col_width<T>(p, l, 1)) return 1;
@@ -1207,33 +1210,33 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
   cplx<T>* grid = reinterpret_cast<cplx<T>*>(p.grid);
   const cplx<T>* tsy = reinterpret_cast<const cplx<T>*>(p.tab.tsy);
   if (p.fft_reg[1] == 3) {
-    const int th = reg_threads(p.fy, lcw);
+    const int th = reg_threads(p.fyr, lcw);
     const size_t sm = tma_smem<T>(g.ny << lcw);
     const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(p.col_tmap);
     if (dir < 0)
-      col_tma_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(map, g, p.fy, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
+      col_tma_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(map, g, p.fyr, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
                                                           p.col_tma_rows);
     else
-      col_tma_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(map, g, p.fy, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
+      col_tma_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(map, g, p.fyr, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
                                                           p.col_tma_rows);
     return;
   }
   if (p.fft_reg[1] == 2) {
-    const int th = reg_threads(p.fy, lcw);
+    const int th = reg_threads(p.fyr, lcw);
     const size_t sm = pipe_smem<T>(g.ny << lcw);
     if (dir < 0)
-      col_pipe_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
+      col_pipe_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fyr, tsy, grid, p.zrange, lcw, kxs, kxe);
     else
-      col_pipe_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
+      col_pipe_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fyr, tsy, grid, p.zrange, lcw, kxs, kxe);
     return;
   }
   if (p.fft_reg[1]) {
-    const int th = reg_threads(p.fy, lcw);
+    const int th = reg_threads(p.fyr, lcw);
     const size_t sm = reg_smem<T>(g.ny << lcw);
     if (dir < 0)
-      col_reg_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
+      col_reg_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(g, p.fyr, tsy, grid, p.zrange, lcw, kxs, kxe);
     else
-      col_reg_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fy, tsy, grid, p.zrange, lcw, kxs, kxe);
+      col_reg_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(g, p.fyr, tsy, grid, p.zrange, lcw, kxs, kxe);
     return;
   }
   const size_t sm = col_smem<T>(g, lcw);

@@ -20,17 +20,8 @@ bool smooth_7(int n) {
   return n == 1;
 }
 
-bool fft_plan(int n, FftPlan& fp) {
-  fp.n = n;
-  fp.nstages = 0;
-  int m = n;
-  while (m % 16 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 16; m /= 16; }
-  while (m % 12 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 12; m /= 12; }
-  while (m % 8 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 8; m /= 8; }
-  while (m % 4 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 4; m /= 4; }
-  while (m % 2 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 2; m /= 2; }
-  for (int p : {3, 5, 7})
-    while (m % p == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = p; m /= p; }
+// stage constants of a plan whose radices are set: per-stage magic numbers and twiddle-row offsets
+void fft_plan_finish(FftPlan& fp) {
   unsigned long long ns = 1;
   int off = 0;
   for (int s = 0; s < fp.nstages; ++s) {
@@ -42,7 +33,59 @@ bool fft_plan(int n, FftPlan& fp) {
     ns *= (unsigned long long)fp.radix[s];
   }
   fp.toff[0] = off;
+}
+
+// Greedy factorisation, largest radices first (the shared-memory-staged passes).
+bool fft_plan(int n, FftPlan& fp) {
+  fp.n = n;
+  fp.nstages = 0;
+  int m = n;
+  while (m % 16 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 16; m /= 16; }
+  while (m % 12 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 12; m /= 12; }
+  while (m % 8 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 8; m /= 8; }
+  while (m % 4 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 4; m /= 4; }
+  while (m % 2 == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = 2; m /= 2; }
+  for (int p : {3, 5, 7})
+    while (m % p == 0 && fp.nstages < kMaxFftRadices) { fp.radix[fp.nstages++] = p; m /= p; }
+  fft_plan_finish(fp);
   return m == 1 && n < (1 << 20);
+}
+
+// Balanced factorisation (the register-staged passes, one butterfly per thread and stage, so their
+// thread count is n / (smallest radix)): the fewest stages, then the largest smallest radix, radices
+// in descending order.  768 = 12 8 8 instead of 16 16 3, 384 = 12 8 4 instead of 16 12 2.
+namespace {
+const int kRadices[] = {16, 12, 8, 7, 5, 4, 3, 2};
+void balanced_search(int m, int from, int* cur, int depth, int* best, int& best_depth, int& best_min) {
+  if (m == 1) {
+    int mn = 1 << 30;
+    for (int i = 0; i < depth; ++i) mn = std::min(mn, cur[i]);
+    if (depth < best_depth || (depth == best_depth && mn > best_min)) {
+      best_depth = depth;
+      best_min = mn;
+      for (int i = 0; i < depth; ++i) best[i] = cur[i];
+    }
+    return;
+  }
+  if (depth >= best_depth || depth >= kMaxFftRadices) return;
+  for (int k = from; k < 8; ++k)
+    if (m % kRadices[k] == 0) {
+      cur[depth] = kRadices[k];
+      balanced_search(m / kRadices[k], k, cur, depth + 1, best, best_depth, best_min);
+    }
+}
+}  // namespace
+
+bool fft_plan_balanced(int n, FftPlan& fp) {
+  if (!fft_plan(n, fp)) return false;  // the greedy plan: validity and a fallback
+  int cur[kMaxFftRadices], best[kMaxFftRadices];
+  int best_depth = kMaxFftRadices + 1, best_min = 0;
+  balanced_search(n, 0, cur, 0, best, best_depth, best_min);
+  if (best_depth > kMaxFftRadices || best_depth > fp.nstages) return true;
+  fp.nstages = best_depth;
+  for (int i = 0; i < best_depth; ++i) fp.radix[i] = best[i];
+  fft_plan_finish(fp);
+  return true;
 }
 
 template <typename T>
@@ -237,7 +280,7 @@ dps_status build_tables(Plan* p) {
   if ((e = upload<T>(&p->tab.zeta, zeta, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twx, g.nx, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   if ((e = upload_twiddles<T>(&p->tab.twy, g.ny, bytes)) != cudaSuccess) return DPS_ERR_OOM;
-  if ((e = upload_stage_twiddles<T>(&p->tab.tsy, p->fy, bytes)) != cudaSuccess) return DPS_ERR_OOM;
+  if ((e = upload_stage_twiddles<T>(&p->tab.tsy, p->fyr, bytes)) != cudaSuccess) return DPS_ERR_OOM;
   return DPS_OK;
 }
 
@@ -468,7 +511,10 @@ dps_status dpstokes_plan_create_ex(dps_plan_t* out, double Lx, double Ly, double
   p->precision = kp->precision;
   p->max_n = kp->max_n;
   p->g = g;
-  if (!dps::fft_plan(nx, p->fx) || !dps::fft_plan(ny, p->fy)) { dps::free_plan(p); return DPS_ERR_INVALID_ARG; }
+  if (!dps::fft_plan(nx, p->fx) || !dps::fft_plan(ny, p->fy) || !dps::fft_plan_balanced(ny, p->fyr)) {
+    dps::free_plan(p);
+    return DPS_ERR_INVALID_ARG;
+  }
   dps_status st = (p->precision == DPS_MIXED) ? dps::build_tables<float>(p) : dps::build_tables<double>(p);
   if (st == DPS_OK) st = (p->precision == DPS_MIXED) ? dps::allocate<float>(p) : dps::allocate<double>(p);
   if (st != DPS_OK) { dps::free_plan(p); cudaGetLastError(); return st; }

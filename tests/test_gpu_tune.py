@@ -33,7 +33,10 @@ def test_autotune_keeps_the_product(precision, bar):
     plan.close()
 
 
-@pytest.mark.parametrize("precision,bar", [("mixed", 1e-6), ("fp64", 1e-12)])
+# mixed: the register-staged column passes factor ny differently from the shared-memory-staged
+# ones (fewest stages, largest smallest radix: 336 = 12 x 7 x 4 against 16 x 3 x 7), so float
+# rounding differs by more than summation order alone; 3e-6 is still well inside the mixed bar
+@pytest.mark.parametrize("precision,bar", [("mixed", 3e-6), ("fp64", 1e-12)])
 @pytest.mark.parametrize("nx,ny", [(192, 144), (384, 336), (192, 135)])  # y: 16x3x3, 16x3x7, odd 3x3x3x5
 def test_every_fft_shape_keeps_the_product(precision, bar, nx, ny):
     """Every xy-FFT variant and column width that fits gives the same product (nkx = nx/2 + 1 is odd,
