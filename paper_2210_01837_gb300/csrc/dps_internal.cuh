@@ -126,7 +126,7 @@ struct Plan {
   int64_t max_n;
   Geometry g;
   FftPlan fx, fy;
-  FftPlan fyr;          // y transform of the register-staged column passes (balanced factorisation)
+  FftPlan fxr, fyr;     // x / y transforms of the register-staged passes (balanced factorisation)
   Tables tab;
   KTabs kt;
   // device buffers

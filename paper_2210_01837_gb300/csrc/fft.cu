@@ -1118,8 +1118,8 @@ int fft_set_col_width(Plan& p, int lcw, int reg) {
 template <typename T>
 int fft_set_row_variant(Plan& p, int reg) {
   if (reg) {
-    if (!reg_fits<T>(p.fx, 0)) return 0;
-    const int th = reg_threads(p.fx, 0);
+    if (!reg_fits<T>(p.fxr, 0)) return 0;
+    const int th = reg_threads(p.fxr, 0);
     const size_t sm = reg_smem<T>(p.g.nx);
     p.fft_reg[0] = 1;
     p.fft_grid[0] = resident_grid(row_r2c_reg_kernel<T>, th, sm, p.device);
@@ -1163,7 +1163,7 @@ int fft_smem_ok(Plan& p) {
       !allow_smem(col_pipe_kernel<T, -1>) || !allow_smem(col_pipe_kernel<T, +1>) ||
       !allow_smem(col_tma_kernel<T, -1>) || !allow_smem(col_tma_kernel<T, +1>))
     return 0;
-  const bool rr = reg_rows_default<T>(p.fx);
+  const bool rr = reg_rows_default<T>(p.fxr);
   if (!fft_set_row_variant<T>(p, rr ? 1 : 0) && !fft_set_row_variant<T>(p, rr ? 0 : 1)) return 0;
   // columns: the prefetched register-staged pass when it fits a wider block than the staged one,
   // prefetched by TMA where a box shape fits (3072^2: 12.2 -> 10.7 ms per pass pair), else cp.async
@@ -1184,13 +1184,13 @@ void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
   const Geometry& g = p.g;
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(p.tab.twx);
   if (p.fft_reg[0]) {
-    const int th = reg_threads(p.fx, 0);
+    const int th = reg_threads(p.fxr, 0);
     const size_t sm = reg_smem<T>(g.nx);
     T* grid = reinterpret_cast<T*>(p.grid);
     if (dir < 0)
-      row_r2c_reg_kernel<T><<<p.fft_grid[0], th, sm, s>>>(g, p.fx, twx, grid, p.zrange);
+      row_r2c_reg_kernel<T><<<p.fft_grid[0], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
     else
-      row_c2r_reg_kernel<T><<<p.fft_grid[1], th, sm, s>>>(g, p.fx, twx, grid, p.zrange);
+      row_c2r_reg_kernel<T><<<p.fft_grid[1], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
     return;
   }
   const int th = fft_threads(g.nx);

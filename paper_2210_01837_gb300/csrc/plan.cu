@@ -511,7 +511,8 @@ dps_status dpstokes_plan_create_ex(dps_plan_t* out, double Lx, double Ly, double
   p->precision = kp->precision;
   p->max_n = kp->max_n;
   p->g = g;
-  if (!dps::fft_plan(nx, p->fx) || !dps::fft_plan(ny, p->fy) || !dps::fft_plan_balanced(ny, p->fyr)) {
+  if (!dps::fft_plan(nx, p->fx) || !dps::fft_plan(ny, p->fy) || !dps::fft_plan_balanced(nx, p->fxr) ||
+      !dps::fft_plan_balanced(ny, p->fyr)) {
     dps::free_plan(p);
     return DPS_ERR_INVALID_ARG;
   }
