@@ -1046,7 +1046,7 @@ int tma_box_rows(int ny, int lcw) {
 }
 
 // the grid as a rank-2 tensor of reals (2 pitch per row, nfields nz ny rows) with boxes of
-// 2^lcw complex columns x bh rows; false when the driver entry point or the encoding is refused
+// 2^lcw complex columns x bh rows; false when cuTensorMapEncodeTiled cannot be obtained or refuses it
 template <typename T>
 bool encode_col_tmap(Plan& p, int lcw, int bh) {
   void* fn = nullptr;
