@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
     col_tma_kernel(const __grid_constant__ CUtensorMap tmap, Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
                    cplx<T>* __restrict__ grid, const int* __restrict__ zrange, int* __restrict__ status, int lcw,
                    int kxs, int kxe, int bh) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];  // realigned to 128 bytes below
   constexpr int PW = pipe_pad<T>(), SH = pipe_pad_shift<T>();
   const int cw = 1 << lcw;
   const int pts = g.ny << lcw;

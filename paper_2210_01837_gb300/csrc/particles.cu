@@ -653,6 +653,8 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
       const void* w0 = L ? static_cast<const void*>(ll0) : static_cast<const void*>(wl0);
       const void* w1 = L ? static_cast<const void*>(ll1) : static_cast<const void*>(wl1);
       const int n0 = L ? lc0 : nl0, n1 = L ? lc1 : nl1;
+      (void)w1;  // the second list serves the two-pass modes only
+      (void)n1;
       if constexpr (MODE == 4) {
         spread_six_list<T, ZC, L>(g, srec, w0, n0, rw, gx, gy, zb, acc);
       } else if constexpr (MODE == 3) {
