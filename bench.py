@@ -163,41 +163,76 @@ def cpu_oracle_tile(div, seed_offset=3):
     return time.perf_counter() - t0, len(pos), params["nx"]
 
 
-def cpu_baseline(div=16):
-    """The oracle as it stands on the host, one thread, on a bounded tile; run in a child process
-    started with spawn so that no CUDA state is inherited."""
-    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "t, n, nx = bench.cpu_oracle_tile(%d); print(json.dumps([t, n, nx]))" % (ROOT, div))
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_tiles(div, procs):
+    """Wall seconds for `procs` concurrent oracle products, one per child process (each with one
+    BLAS/OpenMP thread, seed offsets 3 + i: independent tiles of the same layer), plus the tile's
+    N and grid side.  Children are fresh interpreters: no CUDA state is inherited."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    t, n, nx = json.loads(r.stdout.strip().splitlines()[-1])
+    t0 = time.perf_counter()
+    kids = []
+    for i in range(procs):
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+                "t, n, nx = bench.cpu_oracle_tile(%d, seed_offset=%d); print(json.dumps([t, n, nx]))"
+                % (ROOT, div, 3 + i))
+        kids.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                     text=True, env=env))
+    res = []
+    for k in kids:
+        out, _ = k.communicate(timeout=900)
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    return wall, res[0][1], res[0][2], [r[0] for r in res]
+
+
+def cpu_baseline(div=16):
+    """The oracle as it stands on the host's cores: one product per core on independent
+    1/div^2-area tiles of the same workload, all cores at once (the throughput reported), and one
+    product on one core; rates are extrapolated to the full product by the area ratio."""
     scale = div * div
-    return {"value": 1.0 / (t * scale), "unit": "products/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle (numpy FP64) on a 1/{scale}-area tile of the same workload (N={n}, {nx}^2x65, "
-                      f"same density, heights, h, kernels): {t:.1f} s; time x {scale} extrapolated to the full "
-                      f"product (work is linear in N and in grid nodes; the FFT log factor is ignored)"}
+    cores = host_cores()
+    wall, n, nx, per = _oracle_tiles(div, cores)
+    t1, _, _, _ = _oracle_tiles(div, 1)
+    return {"value": cores / (wall * scale), "unit": "products/s", "cores": cores, "kind": "oracle",
+            "threads_per_process": {"OMP_NUM_THREADS": 1, "OPENBLAS_NUM_THREADS": 1, "numpy.fft": 1},
+            "sample": f"oracle (numpy FP64) on {cores} concurrent 1/{scale}-area tiles of the same workload "
+                      f"(one per core; N={n}, {nx}^2x65 each, same density, heights, h, kernels): {wall:.1f} s wall "
+                      f"(per tile {min(per):.1f}-{max(per):.1f} s); products/s = cores / (wall x {scale}) (work is "
+                      f"linear in N and in grid nodes; the FFT log factor is ignored)",
+            "single_core": {"value": 1.0 / (t1 * scale), "unit": "products/s", "cores": 1,
+                            "sample": f"one tile on one core: {t1:.1f} s, time x {scale}"}}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
     div = 32
+    cores = host_cores()
     for _ in range(args.warmup):
-        cpu_oracle_tile(div)
-    times = []
+        _oracle_tiles(div, cores)
+    walls = []
     n = nx = 0
     for _ in range(args.steps):
-        t, n, nx = cpu_oracle_tile(div)
-        times.append(t)
-    t = float(np.mean(times)) * div * div
+        wall, n, nx, _ = _oracle_tiles(div, cores)
+        walls.append(wall)
+    # each step: one oracle product per core on independent 1/div^2-area tiles, all at once
+    t = float(np.mean(walls)) * div * div / cores
     value = 1.0 / t
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "rollers_1m: N=1048576 above one wall, 3072^2x65, m=5 Table I",
-                      "sample": f"1/{div * div}-area tile per step (N={n}, {nx}^2x65), extrapolated"},
-           "cpu_baseline": {"value": value, "unit": "products/s", "cores": 1, "kind": "oracle",
-                            "sample": f"1/{div * div}-area tile of the roller workload per step, time x {div * div}"},
+                      "sample": f"{cores} concurrent 1/{div * div}-area tiles per step (N={n}, {nx}^2x65 each), "
+                                f"extrapolated"},
+           "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
+                            "sample": f"one 1/{div * div}-area tile of the roller workload per core per step, all "
+                                      f"cores at once; products/s = cores / (wall x {div * div})"},
            "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -334,29 +369,42 @@ def served_capacity(binding, torch, dev, systems):
     return len(systems) / t
 
 
-def fp64_unbatched_leg(binding, torch, dev, systems, count):
-    """Products/s of the FP64 path, one system after another on one stream (the unbatched baseline
-    of the served numbers)."""
-    sub = systems[:count]
-    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    total = 0.0
-    for params, pos, F, T in sub:
-        plan = binding.Plan.from_params(params, with_torque=True, precision="fp64", max_n=len(pos))
-        args = (tdev(pos), tdev(F), tdev(T))
-        plan.apply(*args)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        plan.apply(*args)
-        torch.cuda.synchronize(dev)
-        total += time.perf_counter() - t0
-        plan.check()
-        plan.close()
-    return {"systems": count, "products_per_s": count / total}
+def fp64_unbatched_leg(binding, torch, systems, count, budget=120e9, seed=20221010):
+    """The unbatched FP64 path: `count` requests drawn from the population, each submitted when
+    the previous one has completed to a one-slot server running the all-FP64 product (plans
+    resident, host inputs and outputs pinned); per-request latency (submission to completion, no
+    queueing) and the products/s this gives."""
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    rng = np.random.default_rng(seed)
+    picks = rng.integers(0, len(systems), count)
+    srv = binding.Server(int(budget), slots=1)
+    lat = []
+    t_all = 0.0
+    for rep in range(2):  # first pass creates the plans
+        for i in (picks if rep else np.unique(picks)):
+            params, pos, F, T = systems[i]
+            n = len(pos)
+            U = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+            W = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+            t = srv.submit(params, True, "fp64", n, pin(pos), pin(F), pin(T), U, W)
+            r, _, _ = srv.wait(t)
+            if r.status != 0:
+                raise RuntimeError(f"FP64 request failed: {r.status}")
+            if rep:
+                lat.append(r.t_done - r.t_submit)
+    srv.close()
+    lat = np.array(lat) * 1e3
+    return {"requests": count, "products_per_s": 1e3 * count / lat.sum(), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "how": "one-slot server, FP64 plans resident, each request submitted after the previous completed"}
 
 
-def served_leg(binding, torch, systems, rate, duration, slots=8, budget=120e9, seed=20221009):
+def served_leg(binding, torch, systems, rate, duration, slots=8, budget=120e9, seed=20221009, max_queued=64,
+               precision="mixed"):
     """Poisson arrivals of requests drawn uniformly from `systems` (host inputs in pinned memory) at
-    `rate` per second for `duration` seconds; latency = completion - submission."""
+    `rate` per second for `duration` seconds; latency = completion - submission of the accepted
+    requests.  At most `max_queued` requests wait for admission; a submission that finds the
+    queue full is refused (load shedding) and counted."""
     import queue as _queue
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     inputs = [(params, pin(pos), pin(F), pin(T)) for params, pos, F, T in systems]
@@ -366,14 +414,14 @@ def served_leg(binding, torch, systems, rate, duration, slots=8, budget=120e9, s
              torch.empty((nmax, 3), dtype=torch.float64).pin_memory().numpy()) for _ in range(ring)]
     srv = binding.Server(int(budget), slots=slots)
     # plans of the population resident before the clock starts
-    warm = []
     for i, (params, pos, F, T) in enumerate(inputs):
         n = len(pos)
-        warm.append(srv.submit(params, True, "mixed", n, pos, F, T, outs[i % ring][0][:n], outs[i % ring][1][:n]))
-    for t in warm:
+        t = srv.submit(params, True, precision, n, pos, F, T, outs[i % ring][0][:n], outs[i % ring][1][:n])
         r, _, _ = srv.wait(t)
         if r.status != 0:
             raise RuntimeError(f"served warm-up request failed: {r.status}")
+    if max_queued:
+        binding.dpstokes_server_set_queue_limit(srv.handle, max_queued)
     rng = np.random.default_rng(seed)
     n_req = max(1, int(rate * duration))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
@@ -389,8 +437,14 @@ def served_leg(binding, torch, systems, rate, duration, slots=8, budget=120e9, s
             params, pos, F, T = inputs[picks[i]]
             n = len(pos)
             U, W = outs[i % ring]
-            tickets.put(srv.submit(params, True, "mixed", n, pos, F, T, U[:n], W[:n]))
+            t = srv.submit(params, True, precision, n, pos, F, T, U[:n], W[:n])
+            if t is None:
+                refused[0] += 1
+            else:
+                tickets.put(t)
         tickets.put(None)
+
+    refused = [0]
 
     th = threading.Thread(target=submitter)
     th.start()
@@ -408,9 +462,13 @@ def served_leg(binding, torch, systems, rate, duration, slots=8, budget=120e9, s
     stats = srv.stats()
     srv.close()
     lat = np.array(lat) * 1e3
-    return {"rate_req_per_s": rate, "duration_s": duration, "requests": n_req, "failed": int(bad),
-            "throughput_req_per_s": n_req / (last - first), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "slots": slots,
+    done = len(lat)
+    return {"offered_req_per_s": rate, "duration_s": duration, "requests": n_req, "accepted": done,
+            "refused": refused[0], "failed": int(bad), "precision": precision,
+            "throughput_req_per_s": done / (last - first) if done else 0.0,
+            "p50_ms": float(np.percentile(lat, 50)) if done else None,
+            "p99_ms": float(np.percentile(lat, 99)) if done else None,
+            "mean_ms": float(lat.mean()) if done else None, "slots": slots, "max_queued": max_queued,
             "budget_gb": budget / 1e9, "plans_resident": stats["plans_resident"],
             "plans_evicted": stats["plans_evicted"]}
 
@@ -429,7 +487,9 @@ def main():
     ap.add_argument("--nz", type=int, default=0, help="Chebyshev nodes in z (profiling only; default 65)")
     ap.add_argument("--batch-systems", type=int, default=256, help="systems in the batched leg (0: skip batched and served legs)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
-    ap.add_argument("--serve-seconds", type=float, default=5.0, help="duration of the served leg")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="duration of each served leg (0: skip serving); the configuration asks for 60")
+    ap.add_argument("--serve-population", type=int, default=64, help="systems in the served population")
     ap.add_argument("--no-deriv", action="store_true", help="skip the kernel-derivative torque-route leg")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Brownian-increment (Lanczos) leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the other-configuration timings")
@@ -470,7 +530,9 @@ def main():
     coll = Collective(dist, dev)
     barrier, max_over_ranks = coll.barrier, coll.max
 
-    def time_plan(plan, steps, warmup, stage_log=None):
+    def time_plan(plan, steps, warmup):
+        """Seconds for `steps` back-to-back applies (CUDA events on the launching stream, no
+        per-stage events and no host synchronisation inside the timed region)."""
         for _ in range(warmup):
             plan.apply(d_pos, d_F, d_T, U, W)
         plan.check()
@@ -481,13 +543,23 @@ def main():
         e0.record(stream)
         for _ in range(steps):
             plan.apply(d_pos, d_F, d_T, U, W)
-            if stage_log is not None:
-                stage_log.append(plan.stage_times())
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
         plan.check()
         return e0.elapsed_time(e1) / 1e3
+
+    def stage_pass(plan, steps):
+        """Per-stage milliseconds (mean over `steps` applies), from per-launch event pairs in a
+        separate pass after the headline timing."""
+        plan.enable_timing(True)
+        log = []
+        for _ in range(steps):
+            plan.apply(d_pos, d_F, d_T, U, W)
+            log.append(plan.stage_times())
+        plan.enable_timing(False)
+        plan.check()
+        return {k: float(np.mean([s_[k] for s_ in log])) for k in log[0]}
 
     # ---- mixed precision (headline) --------------------------------------------------------
     plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=n)
@@ -498,15 +570,13 @@ def main():
              "solve_blocks": info.solve_blocks,
              "wavenumber_chunks": info.nchunks}
     launches_per_apply = info.launches_per_apply
-    plan.enable_timing(True)
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         uuid = None
     sampler = ClockSampler(uuid=uuid, index=local)
-    stage_log = []
-    t_mixed = time_plan(plan, args.steps, args.warmup, stage_log)
+    t_mixed = time_plan(plan, args.steps, args.warmup)
     clocks = sampler.stop()
     t_mixed = max_over_ranks(t_mixed)
     ms_step = t_mixed / args.steps * 1e3
@@ -514,7 +584,7 @@ def main():
     U_mixed = U.clone()
     W_mixed = W.clone()
 
-    stages = {k: float(np.mean([s[k] for s in stage_log])) for k in stage_log[0]}
+    stages = stage_pass(plan, max(3, min(args.steps, 10)))
     zocc = occupied_planes(params, pos, info.alpha_M)
     hbm, peak_kind = peaks()
     work = algorithmic(params, n, zocc, 4, info.record_words * 4)
@@ -538,7 +608,7 @@ def main():
         gbs = work[dom] / (stages[dom] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(gbs / hbm, 4), "traffic": None, "peak_kind": peak_kind}
-    plan.enable_timing(False)
+    roofline["timing"] = "stage events from a separate pass after the headline timing"
 
     # ---- end to end through the public API with host buffers -------------------------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -563,11 +633,8 @@ def main():
         plan_d = binding.Plan.from_params(params, with_torque="kernel_derivative", precision="mixed", max_n=n)
         tuned_d_ms = plan_d.autotune(d_pos, d_F, d_T, U, W) if not args.no_tune else None
         info_d = plan_d.info()
-        plan_d.enable_timing(True)
-        log_d = []
-        t_d = max_over_ranks(time_plan(plan_d, args.steps, args.warmup, log_d))
-        plan_d.enable_timing(False)
-        st_d = {k: float(np.mean([s_[k] for s_ in log_d])) for k in log_d[0]}
+        t_d = max_over_ranks(time_plan(plan_d, args.steps, args.warmup))
+        st_d = stage_pass(plan_d, max(3, min(args.steps, 10)))
         work_d = algorithmic(params, n, zocc, 4, info_d.record_words * 4, fields=3)
         roof_d = {}
         for k, ms in st_d.items():
@@ -636,17 +703,25 @@ def main():
         plan64.close()
 
     # ---- batched and served products (independent systems of uneven size) --------------------
-    batch = served = fp64_unbatched = None
+    batch = served = None
     if args.batch_systems > 0:
-        batch, systems = batch_leg(binding, torch, dev, args.batch_systems, max(1, min(args.steps, 3)), 1)
-        capacity = served_capacity(binding, torch, dev, systems)
-        served = served_leg(binding, torch, systems, rate=min(2000.0, 0.8 * capacity), duration=args.serve_seconds)
-        served["population"] = f"the first {len(systems)} batch systems, requests drawn uniformly"
-        served["capacity_req_per_s"] = capacity
-        served["rate_basis"] = "0.8 x the batched capacity of the population (2000/s is above capacity)"
-        fp64_unbatched = fp64_unbatched_leg(binding, torch, dev, systems, min(16, len(systems)))
-        served["fp64_unbatched_products_per_s"] = fp64_unbatched["products_per_s"]
-        served["fp64_unbatched_systems"] = fp64_unbatched["systems"]
+        batch, _ = batch_leg(binding, torch, dev, args.batch_systems, max(1, min(args.steps, 3)), 1)
+    if args.serve_seconds > 0:
+        from paper_2210_01837_gb300.workloads import serving_systems
+        population = serving_systems(count=args.serve_population)
+        capacity = served_capacity(binding, torch, dev, population)
+        legs = {}
+        for name, rate in (("half_capacity", 0.5 * capacity), ("0.8_capacity", 0.8 * capacity),
+                           ("specified_2000", 2000.0)):
+            legs[name] = served_leg(binding, torch, population, rate=rate, duration=args.serve_seconds)
+        served = {"population": f"serving_systems: {len(population)} systems drawn from the configuration-4 size "
+                                f"distribution, wall mode cycling over free / bottom wall / slit, forces + torques, "
+                                f"mixed; requests drawn uniformly from them",
+                  "capacity_req_per_s": capacity,
+                  "capacity_how": "the whole population as one batched apply, twice; population / time",
+                  "legs": legs,
+                  "fp64_unbatched": fp64_unbatched_leg(binding, torch, population, min(32, len(population)))}
+        served["p99_ms"] = legs["0.8_capacity"]["p99_ms"]
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,

@@ -78,7 +78,8 @@ typedef enum {
   DPS_ERR_CUDA = -4,          /* a CUDA runtime call failed                                      */
   DPS_ERR_TIMEOUT = -5,       /* a bounded wait gave up: a device copy did not complete in about a
                                  second (TMA column pass), or a server ticket within its timeout */
-  DPS_ERR_NONFINITE = -6      /* a non-finite position, force or torque                          */
+  DPS_ERR_NONFINITE = -6,     /* a non-finite position, force or torque                          */
+  DPS_ERR_BUSY = -7           /* a server's queue is at its limit: the request was not accepted   */
 } dps_status;
 
 typedef struct {
@@ -232,8 +233,8 @@ dps_status dpstokes_stage_times(dps_plan_t plan, double* ms_out, int32_t capacit
  * Some callers cannot call cudaMalloc: a host application whose memory manager owns every byte of
  * device memory and hands out nothing outside its own pool, or a latency-critical loop that cannot
  * afford the implicit device synchronisation of an allocation.  This entry point runs the library's
- * spreading stage (particle envelope records, binning and the tile-gather spread of step 1 of
- * Sec. III.D, in double precision) using only a scratch array of fixed size, 64 MiB, compiled into
+ * spreading stage (particle envelope records, binning and the tile-gather spread, in double
+ * precision, on the same node heights as a plan) using only a scratch array of fixed size, 64 MiB, compiled into
  * the library as device memory; every GPU that loads the library holds that array until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
  *   - out_grid: caller-owned device buffer of nfields * nz * ny * ldx doubles (nfields = 6 with
@@ -279,7 +280,9 @@ typedef struct {
  * Every argument check of dpstokes_apply is made for every request before anything is enqueued
  * (DPS_ERR_INVALID_ARG, nothing enqueued).  Asynchronous, no allocation, no host
  * synchronisation: a batch may be captured into a CUDA graph (call dpstokes_batch_prepare before
- * the capture) and the graph replayed; the plans then must stay alive while it is in use. */
+ * the capture) and the graph replayed; the plans then must stay alive while it is in use.  Calls
+ * from several host threads are serialised while they enqueue (a per-device lock); a plan must
+ * still be used by one product at a time. */
 dps_status dpstokes_apply_batch(const dps_request* reqs, int32_t count, void* stream);
 
 /* Create the current device's batch stream pool now (idempotent). */
@@ -294,8 +297,11 @@ dps_status dpstokes_batch_prepare(void);
  * the device); requests whose plan is busy wait without holding up the others.  A request that can
  * never fit the budget completes with DPS_ERR_OOM.  Each admitted request copies its inputs from
  * host memory, runs the product and copies the outputs back on its slot's stream, so requests
- * overlap on the device.  Results are those of dpstokes_apply_host on a plan with the same
- * parameters. */
+ * overlap on the device.  Outputs in page-locked memory receive the device-to-host copy
+ * directly; pageable outputs are copied through a pinned staging buffer of the slot and then into
+ * the caller's arrays by the worker when the request retires (a direct copy into pageable memory
+ * would hold the worker until that product finished).  Results are those of dpstokes_apply_host
+ * on a plan with the same parameters.  Submissions may come from any number of host threads. */
 typedef struct dps_server_s* dps_server_t;
 
 typedef struct {
@@ -324,15 +330,22 @@ typedef struct {
   int64_t queued, running;    /* requests waiting / on a slot                                      */
   int64_t plans_resident, plans_created, plans_evicted;
   int64_t bytes_resident;     /* device bytes held by cached plans                                 */
+  int64_t rejected;           /* submissions refused with DPS_ERR_BUSY (queue at its limit)        */
 } dps_server_stats;
 
 /* memory_budget_bytes > 0 bounds the plans' device memory; 1 <= slots <= 64.  The server works on
  * the device current at creation. */
 dps_status dpstokes_server_create(dps_server_t* out, int64_t memory_budget_bytes, int32_t slots);
 
+/* Load shedding: at most max_queued requests wait for admission (0, the default: no limit).  A
+ * submission that finds the queue full is refused at once with DPS_ERR_BUSY (no ticket), so under
+ * an offered load above the server's capacity the accepted requests keep a bounded latency. */
+dps_status dpstokes_server_set_queue_limit(dps_server_t server, int64_t max_queued);
+
 /* Queue a request (the descriptor is copied; the host buffers must stay valid until the request's
  * dpstokes_server_wait returns).  *ticket identifies it.  DPS_ERR_INVALID_ARG for n outside
- * [0, kp.max_n] or after destroy has begun; parameter errors are reported by the result. */
+ * [0, kp.max_n] or after destroy has begun; DPS_ERR_BUSY when the queue is at its limit;
+ * parameter errors are reported by the result. */
 dps_status dpstokes_server_submit(dps_server_t server, const dps_serve_request* req, int64_t* ticket);
 
 /* Wait up to timeout_s seconds for a ticket; DPS_ERR_TIMEOUT if it has not completed (it keeps

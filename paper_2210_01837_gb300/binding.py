@@ -28,9 +28,9 @@ def torque_route(with_torque):
         return 2
     raise ValueError(f"unknown torque route {with_torque!r}")
 STATUS = {0: "DPS_OK", -1: "DPS_ERR_INVALID_ARG", -2: "DPS_ERR_OUT_OF_DOMAIN", -3: "DPS_ERR_OOM",
-          -4: "DPS_ERR_CUDA", -5: "DPS_ERR_TIMEOUT", -6: "DPS_ERR_NONFINITE"}
+          -4: "DPS_ERR_CUDA", -5: "DPS_ERR_TIMEOUT", -6: "DPS_ERR_NONFINITE", -7: "DPS_ERR_BUSY"}
 DPS_OK, DPS_ERR_INVALID_ARG, DPS_ERR_OUT_OF_DOMAIN, DPS_ERR_OOM = 0, -1, -2, -3
-DPS_ERR_CUDA, DPS_ERR_TIMEOUT, DPS_ERR_NONFINITE = -4, -5, -6
+DPS_ERR_CUDA, DPS_ERR_TIMEOUT, DPS_ERR_NONFINITE, DPS_ERR_BUSY = -4, -5, -6, -7
 
 
 class dps_grid(ctypes.Structure):
@@ -88,7 +88,7 @@ class dps_serve_result(ctypes.Structure):
 class dps_server_stats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("plans_resident", ctypes.c_int64),
                 ("plans_created", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
-                ("bytes_resident", ctypes.c_int64)]
+                ("bytes_resident", ctypes.c_int64), ("rejected", ctypes.c_int64)]
 
 
 class DpsError(RuntimeError):
@@ -143,6 +143,7 @@ def load(path=None):
         "dpstokes_server_submit": (_I32, [_P, ctypes.POINTER(dps_serve_request), ctypes.POINTER(_I64)]),
         "dpstokes_server_wait": (_I32, [_P, _I64, _D, ctypes.POINTER(dps_serve_result)]),
         "dpstokes_server_stats": (_I32, [_P, ctypes.POINTER(dps_server_stats)]),
+        "dpstokes_server_set_queue_limit": (_I32, [_P, _I64]),
         "dpstokes_server_destroy": (None, [_P]),
         "dpstokes_lanczos_create": (_I32, [ctypes.POINTER(_P), _P, _I32]),
         "dpstokes_lanczos_sample": (_I32, [_P, _I64, _P, _P, _P, _D, ctypes.POINTER(_I32), ctypes.POINTER(_D),
@@ -278,6 +279,10 @@ def dpstokes_server_stats(server):
     s = dps_server_stats()
     st = load().dpstokes_server_stats(server, ctypes.byref(s))
     return st, s
+
+
+def dpstokes_server_set_queue_limit(server, max_queued):
+    return load().dpstokes_server_set_queue_limit(server, int(max_queued))
 
 
 def dpstokes_server_destroy(server):
@@ -446,16 +451,20 @@ def apply_batch(items, stream=None, status=None):
 class Server:
     """Request server: host arrays in and out, plans cached under a device-memory budget."""
 
-    def __init__(self, memory_budget_bytes, slots=8):
+    def __init__(self, memory_budget_bytes, slots=8, max_queued=0):
         st, h = dpstokes_server_create(memory_budget_bytes, slots)
         if st != DPS_OK:
             raise DpsError(st, "dpstokes_server_create")
         self.handle = h
         self._keep = {}
+        if max_queued:
+            st = dpstokes_server_set_queue_limit(h, max_queued)
+            if st != DPS_OK:
+                raise DpsError(st, "dpstokes_server_set_queue_limit")
 
     def submit(self, params, with_torque, precision, max_n, pos, F, T=None, U=None, W=None):
         """params: dict as in Plan.from_params; pos/F/T host float64 [n, 3] (kept alive until wait).
-        Returns a ticket; outputs land in U (and W)."""
+        Returns a ticket (None when a queue limit refused the request); outputs land in U (and W)."""
         n = pos.shape[0]
         route = torque_route(with_torque)
         U = np.empty((n, 3)) if U is None else U
@@ -472,6 +481,8 @@ class Server:
         r.positions, r.forces, r.torques = _ptr(pos), _ptr(F), _ptr(T)
         r.out_vel, r.out_angvel = _ptr(U), _ptr(W)
         st, t = dpstokes_server_submit(self.handle, r)
+        if st == DPS_ERR_BUSY:
+            return None  # queue at its limit: not accepted
         if st != DPS_OK:
             raise DpsError(st, "dpstokes_server_submit")
         self._keep[t] = (pos, F, T, U, W)

@@ -37,6 +37,7 @@ constexpr size_t kAdmitWindow = 64;  // queued requests the server's admission l
 constexpr int kMaxDevices = 64;
 
 struct StreamPool {
+  std::mutex enqueue;  // one batch at a time records and waits on the pool's fork/join events
   bool ready = false;
   cudaStream_t s[kBatchStreams];
   cudaEvent_t fork;
@@ -123,7 +124,26 @@ struct Slot {
   int64_t ticket = -1;
   CachedPlan* cp = nullptr;
   double t_submit = 0, t_start = 0;
+  // pinned staging of the outputs when the caller's buffers are pageable (a device-to-host copy
+  // into pageable memory would block the worker until the product finished); copied into the
+  // caller's buffers when the slot retires
+  double* h_out = nullptr;
+  size_t h_cap = 0;  // doubles
+  double* user_U = nullptr;
+  double* user_W = nullptr;
+  size_t out_bytes = 0;
+  bool staged = false;
 };
+
+// page-locked (or device-accessible) host memory: copies to it are asynchronous
+bool copies_async_to(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged;
+}
 
 }  // namespace
 
@@ -140,7 +160,8 @@ struct Server {
   bool stop = false;
   int64_t next_ticket = 0;
   uint64_t clock = 0;
-  int64_t created = 0, evicted = 0;
+  int64_t created = 0, evicted = 0, rejected = 0;
+  int64_t max_queued = 0;  // 0: unbounded queue
 
   // plan sizing before creation, following the plan's own allocations: grid, particle records and
   // bins, solve workspace, spectra, staging buffers and tables (an upper bound, plus 1/8)
@@ -192,6 +213,13 @@ struct Server {
   }
 
   void finish(Slot& sl, dps_status st) {
+    if (sl.staged) {  // the slot's copies have completed (its event or a stream synchronisation)
+      if (st == DPS_OK) {
+        memcpy(sl.user_U, sl.h_out, sl.out_bytes);
+        if (sl.user_W) memcpy(sl.user_W, sl.h_out + sl.out_bytes / sizeof(double), sl.out_bytes);
+      }
+      sl.staged = false;
+    }
     dps_serve_result res;
     res.status = st;
     res.t_submit = sl.t_submit;
@@ -232,8 +260,27 @@ struct Server {
     st = run(p, r.n, dpos, dF, dT, dU, dW, s, 99);
     if (st != DPS_OK) return st;
     if (r.n > 0) {
-      if (cudaMemcpyAsync(r.out_vel, dU, b, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DPS_ERR_CUDA;
-      if (dW && cudaMemcpyAsync(r.out_angvel, dW, b, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DPS_ERR_CUDA;
+      double* oU = r.out_vel;
+      double* oW = r.out_angvel;
+      if (!copies_async_to(r.out_vel) || (dW && !copies_async_to(r.out_angvel))) {
+        const size_t need = 6 * (size_t)r.n;  // the slot is idle: nothing uses its staging buffer
+        if (sl.h_cap < need) {
+          const size_t cap = std::max<size_t>(need, 2 * sl.h_cap);
+          if (sl.h_out) cudaFreeHost(sl.h_out);
+          sl.h_out = nullptr;
+          sl.h_cap = 0;
+          if (cudaMallocHost((void**)&sl.h_out, cap * sizeof(double)) != cudaSuccess) return DPS_ERR_OOM;
+          sl.h_cap = cap;
+        }
+        oU = sl.h_out;
+        oW = dW ? sl.h_out + 3 * (size_t)r.n : nullptr;
+        sl.user_U = r.out_vel;
+        sl.user_W = dW ? r.out_angvel : nullptr;
+        sl.out_bytes = b;
+        sl.staged = true;
+      }
+      if (cudaMemcpyAsync(oU, dU, b, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DPS_ERR_CUDA;
+      if (dW && cudaMemcpyAsync(oW, dW, b, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DPS_ERR_CUDA;
     }
     if (cudaMemcpyAsync(sl.h_status, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return DPS_ERR_CUDA;
@@ -366,6 +413,9 @@ dps_status dpstokes_apply_batch(const dps_request* reqs, int32_t count, void* st
   dps_status st = pool_for_device(&pool);
   if (st != DPS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  // batches from several host threads enqueue one after another: each one's fork record and waits
+  // and its join records and waits must not interleave with another's on the shared events
+  std::lock_guard<std::mutex> guard(pool->enqueue);
   // requests of one plan share a stream (they use the plan's buffers in turn)
   std::vector<int> lane(count, -1);
   std::vector<dps_plan_t> owner(kBatchStreams, nullptr);
@@ -438,6 +488,10 @@ dps_status dpstokes_server_submit(dps_server_t server, const dps_serve_request* 
   {
     std::lock_guard<std::mutex> lock(sv->mu);
     if (sv->stop) return DPS_ERR_INVALID_ARG;
+    if (sv->max_queued > 0 && (int64_t)sv->queue.size() >= sv->max_queued) {
+      ++sv->rejected;
+      return DPS_ERR_BUSY;
+    }
     Pending q;
     q.r = *req;
     q.ticket = sv->next_ticket++;
@@ -481,6 +535,16 @@ dps_status dpstokes_server_stats(dps_server_t server, dps_server_stats* out) {
   out->plans_created = sv->created;
   out->plans_evicted = sv->evicted;
   out->bytes_resident = sv->used;
+  out->rejected = sv->rejected;
+  return DPS_OK;
+}
+
+dps_status dpstokes_server_set_queue_limit(dps_server_t server, int64_t max_queued) {
+  using namespace dps;
+  Server* sv = reinterpret_cast<Server*>(server);
+  if (!sv || max_queued < 0) return DPS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  sv->max_queued = max_queued;
   return DPS_OK;
 }
 
@@ -499,6 +563,7 @@ void dpstokes_server_destroy(dps_server_t server) {
     cudaStreamDestroy(sl.s);
     cudaEventDestroy(sl.done);
     cudaFreeHost(sl.h_status);
+    if (sl.h_out) cudaFreeHost(sl.h_out);
   }
   for (CachedPlan* c : sv->cache) {
     dpstokes_destroy(c->plan);

@@ -36,10 +36,16 @@ dps_status scratch_address(int dev, unsigned char** out) {
   return DPS_OK;
 }
 
-__global__ void noalloc_init_kernel(double* zc, int nz, double zmin, double H, int* zrange, int* status,
+// Chebyshev node heights, computed on the host by the same expression as a plan's table and passed
+// by value (2 KB of kernel parameters), so both paths place every envelope on identical nodes.
+struct NodeTable {
+  double z[257];
+};
+
+__global__ void noalloc_init_kernel(double* zc, const NodeTable nodes, int nz, int* zrange, int* status,
                                     int* bin_count, int nbins) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nz) zc[i] = zmin + 0.5 * H * (1.0 + cos(M_PI * (double)i / (double)(nz - 1)));
+  if (i < nz) zc[i] = nodes.z[i];
   if (i == 0) {
     zrange[0] = nz;
     zrange[1] = -1;
@@ -122,7 +128,9 @@ extern "C" dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin,
   if (cudaMemsetAsync(out_grid, 0, (size_t)g.nfields * nz * ny * (size_t)ldx * sizeof(double), s) != cudaSuccess)
     return DPS_ERR_CUDA;
   const int blocks = std::min(1024, std::max(nz, nbins) / 256 + 1);
-  noalloc_init_kernel<<<blocks, 256, 0, s>>>(p.tab.zc, nz, zmin, g.H, p.zrange, p.status, p.bin_count, nbins);
+  NodeTable nodes;
+  for (int c = 0; c < nz; ++c) nodes.z[c] = zmin + 0.5 * g.H * (1.0 + cos(M_PI * c / (nz - 1)));
+  noalloc_init_kernel<<<blocks, 256, 0, s>>>(p.tab.zc, nodes, nz, p.zrange, p.status, p.bin_count, nbins);
   const int sp = spread_prepare<double>(p);
   if (sp < 0) return DPS_ERR_INVALID_ARG;
   if (sp == 0) return DPS_ERR_CUDA;

@@ -452,6 +452,7 @@ const char* dpstokes_error_string(dps_status st) {
     case DPS_ERR_CUDA: return "CUDA runtime error";
     case DPS_ERR_TIMEOUT: return "bounded device wait expired";
     case DPS_ERR_NONFINITE: return "non-finite input";
+    case DPS_ERR_BUSY: return "server queue at its limit: request not accepted";
   }
   return "unknown status";
 }

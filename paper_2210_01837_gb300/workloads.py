@@ -19,6 +19,10 @@ by seeded random draws because the paper's configurations are not available:
                     heights U[1.2, 10], slit z in [0, 20] with U[1.2, 18.8], open z in [0, 20]
                     with U[2, 18]; forces and torques N(0,1); m = 5 with Table I betas.
 
+* ``serving_systems`` - the served population: systems drawn like ``batch_systems`` with the wall
+                    mode cycling over open, bottom wall and slit (uniform over the three); requests
+                    are drawn uniformly from the population so that plans stay resident.
+
 * ``lanczos_layer`` - the Lanczos-convergence suspension of Sec. IV.C: a base cell of 2048
                     non-overlapping spheres (random sequential addition, centre distance >= 2 R_h)
                     in L = 128.8 R_h (area fraction 0.39) tiled r x r times in xy (N = 2048 r^2),
@@ -26,7 +30,7 @@ by seeded random draws because the paper's configurations are not available:
                     profile of the scaling test, drawn here), box height H = 7.5 R_h, forces only,
                     Table III monopole grid (150 r)^2 x 19, m = 4, beta = 1.87 m; R_h = 1.
 
-Seeds are 20221004 + the workload's index (1, 2, 3, 4, 5).
+Seeds are 20221004 + the workload's index (1, 2, 3, 4, 5; 6 for the served population).
 """
 
 import numpy as np
@@ -140,6 +144,12 @@ def batch_systems(count=256, seed_offset=4, modes=("bottom_wall", "slit"), n_ran
                       m_M=m, beta_M=m * _T1_M5[1], m_D=m, beta_D=m * _T1_M5[2], eta=1.0)
         out.append((params, pos, F, T))
     return out
+
+
+def serving_systems(count=64, seed_offset=6):
+    """The served population: (params, pos, F, T) systems of the batch size distribution, wall mode
+    free, bottom wall, slit in turn."""
+    return batch_systems(count=count, seed_offset=seed_offset, modes=("free", "bottom_wall", "slit"))
 
 
 def _rsa_layer(rng, n, L, heights, dmin, max_tries=200000):

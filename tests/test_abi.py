@@ -133,6 +133,7 @@ def test_batch_and_server_reject_invalid_arguments_on_host(lib):
     assert lib.dpstokes_server_submit(None, None, ctypes.byref(t)) == binding.DPS_ERR_INVALID_ARG
     r = binding.dps_serve_result()
     assert lib.dpstokes_server_wait(None, 0, 0.0, ctypes.byref(r)) == binding.DPS_ERR_INVALID_ARG
+    assert lib.dpstokes_server_set_queue_limit(None, 4) == binding.DPS_ERR_INVALID_ARG
     lib.dpstokes_server_destroy(None)
 
 

@@ -177,3 +177,63 @@ def test_server_rejects_a_request_that_can_never_fit():
     r, _, _ = srv.wait(t, timeout_s=60.0)
     assert r.status == binding.DPS_ERR_OOM
     srv.close()
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_server_overlaps_requests_with_pinned_or_pageable_outputs(pinned):
+    """Two requests of different plans, both cached, submitted together: the second is admitted and
+    enqueued while the first product still runs (a direct device-to-host copy into pageable output
+    arrays would hold the worker until the first product finished, which would delay the second
+    admission by a whole product), and both results equal single applies."""
+    from paper_2210_01837_gb300.workloads import slit_16k
+    reqs = []
+    for nz in (97, 65):
+        pa, pos, F, T = slit_16k(n=4096, nz=nz)
+        reqs.append((pa, pos, F, T, _alone(pa, pos, F, T, "fp64", True)))
+    srv = binding.Server(memory_budget_bytes=64 << 30, slots=4)
+
+    def submit(pa, pos, F, T):
+        n = len(pos)
+        U = _pinned(np.zeros((n, 3))) if pinned else np.zeros((n, 3))
+        W = _pinned(np.zeros((n, 3))) if pinned else np.zeros((n, 3))
+        return srv.submit(pa, with_torque=True, precision="fp64", max_n=n, pos=_pinned(pos), F=_pinned(F),
+                          T=_pinned(T), U=U, W=W)
+
+    for _ in range(2):  # plans created and resident before the measured round
+        for t in [submit(*r[:4]) for r in reqs]:
+            assert srv.wait(t, timeout_s=300.0)[0].status == binding.DPS_OK
+    tickets = [submit(*r[:4]) for r in reqs]
+    res = [srv.wait(t, timeout_s=300.0) for t in tickets]
+    for (r, U, W), req in zip(res, reqs):
+        assert r.status == binding.DPS_OK
+        _check((U, W), req[4], "fp64")
+    (ra, _, _), (rb, _, _) = res
+    assert rb.t_start < ra.t_done and ra.t_start < rb.t_done
+    assert rb.t_start - ra.t_start < 0.25 * (ra.t_done - ra.t_start), (ra.t_start, ra.t_done, rb.t_start)
+    srv.close()
+
+
+def test_server_queue_limit_refuses_and_still_serves():
+    """With a queue limit, submissions that find the queue full are refused at once (no ticket)
+    and counted; every accepted request completes with the single-apply result."""
+    probs = [_problem(*p) for p in PROBLEMS[:2]]
+    alone = [_alone(pa, pos, F, T, p[5], p[4]) for p, (pa, pos, F, T) in zip(PROBLEMS[:2], probs)]
+    srv = binding.Server(memory_budget_bytes=8 << 30, slots=1, max_queued=2)
+    accepted, refused = [], 0
+    for rep in range(12):
+        k = rep % 2
+        pa, pos, F, T = probs[k]
+        t = srv.submit(pa, with_torque=PROBLEMS[k][4], precision=PROBLEMS[k][5], max_n=len(pos), pos=_pinned(pos),
+                       F=_pinned(F), T=None if T is None else _pinned(T))
+        if t is None:
+            refused += 1
+        else:
+            accepted.append((k, t))
+    for k, t in accepted:
+        r, U, W = srv.wait(t, timeout_s=300.0)
+        assert r.status == binding.DPS_OK
+        _check((U, W), alone[k], PROBLEMS[k][5])
+    stats = srv.stats()
+    assert refused >= 1 and stats["rejected"] == refused
+    assert len(accepted) + refused == 12
+    srv.close()

@@ -139,6 +139,27 @@ def test_grand_mobility_symmetric_positive_definite(mode):
     assert np.min(np.linalg.eigvalsh(0.5 * (M + M.T))) > 0.0
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", ["bottom_wall", "slit"])
+def test_grand_mobility_symmetric_to_five_digits(mode):
+    # Sec. IV.A reports mu^rt_xy = mu^tr_yx to well within five digits.  What keeps the Table I
+    # kernels above that level at Nz = 65 is the jump of the ES kernel at the edge of its support
+    # (e^{-beta}/Z, about 3e-4 for beta = 8), which the Chebyshev quadrature integrates to first
+    # order only.  With beta = 18 the jump is 1.5e-8 and the discrete grand mobility is symmetric to
+    # 4e-7, so a mistake that breaks symmetry (a transposed operand, a wrong sign in a curl or
+    # coupling term) shows far above the 1e-5 bar.
+    p = Params(Lx=20.0, Ly=20.0, zmin=0.0, zmax=10.0, mode=mode, nx=40, ny=40, nz=65, m_M=6,
+               beta_M=18.0, m_D=6, beta_D=18.0)
+    pos = np.array([[4.1, 5.3, 2.6], [7.2, 4.4, 3.9]])
+    M = _grand_mobility(p, pos)
+    assert np.linalg.norm(M - M.T) / np.linalg.norm(M) <= 1e-5
+    if mode == "bottom_wall":
+        # the element the paper quotes, particle 0: U_y from T_x against Omega_x from F_y
+        tr, rt = M[1, 6], M[6, 1]
+        assert abs(tr - rt) <= 1e-5 * abs(tr)
+    assert np.min(np.linalg.eigvalsh(0.5 * (M + M.T))) > 0.0
+
+
 def test_slit_midplane_reflection():
     p = _small("slit")
     pos, F, T = _particles(p, 3, 15, 0.5, 9.5)
