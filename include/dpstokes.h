@@ -179,8 +179,19 @@ typedef struct {
                                and stage, one shared buffer), 0: shared-memory-staged           */
   int32_t fft_register_cols; /* the y-FFT passes: 0 shared-memory-staged, 1 register-staged,
                                2 register-staged with cp.async prefetch, 3 with TMA prefetch   */
+  int32_t interp_variant;   /* interpolation (step 8): 1 tile gather (forces only, or spectral-curl
+                               torques with m_M = m_D), 0 a warp per particle                    */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
+
+/* Interpolation variant by hand (no counterpart in the paper): 1 the tile gather, the transpose of
+ * the spread (a block per 32 x 8 tile of node columns reads each column once and adds its share of
+ * every covering particle's sums to a per-tile slot; a second kernel adds a particle's slots in a
+ * fixed order), 0 a warp per particle gathering its support rows.  Both compute the same sums up to
+ * summation order.  DPS_ERR_INVALID_ARG for 1 where the tile gather does not apply (the
+ * kernel-derivative torque route, or m_M != m_D with torques).  The warp-per-particle gather is
+ * the default; the autotuner tries the tile gather where it applies. */
+dps_status dpstokes_plan_set_interp(dps_plan_t plan, int32_t variant);
 
 /* Autotuner (no counterpart in the paper).  Times the plan's applies on the given particles (same
  * arguments and rules as dpstokes_apply) over a small set of launch shapes, one knob at a time:

@@ -48,7 +48,8 @@ class dps_plan_info(ctypes.Structure):
                 ("nfields", ctypes.c_int32), ("record_words", ctypes.c_int32), ("h", ctypes.c_double),
                 ("alpha_M", ctypes.c_double), ("alpha_D", ctypes.c_double), ("launches_per_apply", ctypes.c_int32),
                 ("nchunks", ctypes.c_int32), ("fft_col_width", ctypes.c_int32), ("solve_blocks", ctypes.c_int32),
-                ("fft_register_rows", ctypes.c_int32), ("fft_register_cols", ctypes.c_int32)]
+                ("fft_register_rows", ctypes.c_int32), ("fft_register_cols", ctypes.c_int32),
+                ("interp_variant", ctypes.c_int32)]
 
 
 class dps_request(ctypes.Structure):
@@ -136,6 +137,7 @@ def load(path=None):
         "dpstokes_debug_copy": (_I32, [_P, _I32, _P, _I64, _P]),
         "dpstokes_plan_set_fft": (_I32, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
         "dpstokes_plan_set_pipeline": (_I32, [_P, ctypes.c_int32, ctypes.c_int32]),
+        "dpstokes_plan_set_interp": (_I32, [_P, ctypes.c_int32]),
         "dpstokes_plan_autotune": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
         "dpstokes_apply_batch": (_I32, [ctypes.POINTER(dps_request), _I32, _P]),
         "dpstokes_batch_prepare": (_I32, []),
@@ -360,6 +362,11 @@ class Plan:
         st = load().dpstokes_plan_set_fft(self.handle, int(row_register), int(col_register), int(col_width))
         if st != DPS_OK:
             raise DpsError(st, "dpstokes_plan_set_fft")
+
+    def set_interp(self, variant):
+        st = load().dpstokes_plan_set_interp(self.handle, int(variant))
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_plan_set_interp")
 
     def set_pipeline(self, solve_blocks, nchunks):
         """Set the FP64 solve's persistent grid and the column chunks by hand; raises if out of range."""

@@ -180,6 +180,18 @@ struct Server {
     b += nmax * (rec + 8 + 15 * 8) + 3 * nbins * 4;                      // records, bins, staging
     b += blocks * kBvpThreads * nz * (3 * 16 + 3 * 8 + 2 * ts);          // solve workspace
     b += 3 * nz * K * 2 * ts + 12 * K * 2 * ts;                          // kbuf, kaux
+    b += nkx * (ny / 2 + 1) * nz * 4 * 8;                                // factorisation table (FP64)
+    // partial sums of the tile-gather interpolation (forces only, or equal supports with the
+    // spectral curl): slots of the tiles a support can overlap x fields x particles
+    const int64_t ifields = route == DPS_TORQUE_NONE ? 3
+                          : (route == DPS_TORQUE_SPECTRAL_CURL && r.kp.m_M == r.kp.m_D ? 6 : 0);
+    if (ifields) {
+      const int64_t px = r.kp.m_M + 1;
+      const int64_t nbx = (nx + kTileX - 1) / kTileX, nby = (ny + kTileY - 1) / kTileY;
+      const int64_t sxn = std::min<int64_t>(nbx, (px - 1) / kTileX + 2 + (nx % kTileX ? 1 : 0));
+      const int64_t syn = std::min<int64_t>(nby, (px - 1) / kTileY + 2 + (ny % kTileY ? 1 : 0));
+      b += sxn * syn * ifields * nmax * ts;
+    }
     b += 8 * nz * (nz + 32) * ts + 3 * (nx + ny) * 16 + 16 * nz * 8;     // tables (twiddles: length n + stages <= 2 n)
     return b + b / 8 + (256 << 10);
   }

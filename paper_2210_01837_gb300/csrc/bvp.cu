@@ -246,6 +246,208 @@ struct SolveWs {
   int slots;
 };
 
+// k = 0 (Sec. III.C, Eqs. 47-52; Appendix A, Eq. A12): w = 0; sigma c_n = -f_n/eta with the
+// Dirichlet / Neumann (Robin with slip) rows on the truncated series; no pressure (not needed).
+// The sweep values of the slot's workspace hold the scaled right-hand side meanwhile.
+template <typename T, bool SLIP>
+__device__ __noinline__ void zero_mode(const Geometry& g, const double* __restrict__ band, const T* __restrict__ bandT,
+                                       cplx<T>* __restrict__ kbuf, cplx<T>* __restrict__ kaux,
+                                       cplx<double>* __restrict__ sw, int slots, int slot, int64_t kidx, int64_t K) {
+  const int N = g.nz;
+  auto KB = [&](int f, int n) -> cplx<T>& { return kbuf[((size_t)f * N + n) * K + kidx]; };
+  auto SW = [&](int f, int n) -> cplx<double>& { return sw[((size_t)f * N + n) * slots + slot]; };
+  auto AUX = [&](int q) -> cplx<T>& { return kaux[(size_t)q * K + kidx]; };
+  const double* bl = band;
+  const double* bd = band + N;
+  const double* bu = band + 2 * N;
+  const double* bP = band + 3 * N;
+  const double* bQ = band + 4 * N;
+  (void)bandT;
+  const double sH = 2.0 / g.H;
+  const double sig = sH * sH;
+  const double inv_eta = 1.0 / g.eta;
+  for (int o = 0; o < 3; ++o) {
+    if (g.mode == DPS_FREE || o == 2) {
+      for (int n = 0; n < N; ++n) KB(o, n) = mk<T>((T)0, (T)0);
+      continue;
+    }
+    cplx<double> Sp = mk<double>(0, 0), Sm = mk<double>(0, 0), Pd = mk<double>(0, 0), Pm = mk<double>(0, 0);
+    for (int n = 0; n < N; ++n) {
+      const cplx<double> cn = scl(wid(KB(o, n)), -inv_eta / sig);
+      SW(0, n) = cn;
+      const double sgn = (n & 1) ? -1.0 : 1.0;
+      Sp = Sp + scl(cn, bQ[n]);
+      Sm = Sm + scl(cn, sgn * bQ[n]);
+      Pd = Pd + scl(cn, bP[n]);
+      if (SLIP) Pm = Pm + scl(cn, sgn * bP[n]);
+    }
+    cplx<double> a0, a1;
+    if (SLIP) {
+      // Robin rows (Eq. A12): y(-1) - l0 (2/H) y_s(-1) = g_bot and, in the slit,
+      // y(+1) + lH (2/H) y_s(+1) = g_top (above one wall: y_s(+1) = 0); y(+-1) = S+- + a0 +- a1,
+      // y_s(+1) = Pd + a1, y_s(-1) = -Pm + a1; g = Nx Ny u^W (unnormalised transform)
+      const double nxy = (double)g.nx * (double)g.ny;
+      const double al = 1.0 + g.slip0 * sH;
+      const cplx<double> Rb = mk<double>(nxy * g.uw0[o], 0.0) - Sm - scl(Pm, g.slip0 * sH);
+      if (g.mode == DPS_BOTTOM_WALL) {
+        a1 = scl(Pd, -1.0);
+        a0 = Rb + scl(a1, al);
+      } else {
+        const double be = 1.0 + g.slipH * sH;
+        const cplx<double> Rt = mk<double>(nxy * g.uwH[o], 0.0) - Sp - scl(Pd, g.slipH * sH);
+        a1 = scl(Rt - Rb, 1.0 / (al + be));
+        a0 = Rb + scl(a1, al);
+      }
+    } else if (g.mode == DPS_BOTTOM_WALL) {  // y(-1) = 0, y_s(+1) = 0
+      a1 = scl(Pd, -1.0);
+      a0 = a1 - Sm;
+    } else {                           // y(-1) = y(+1) = 0
+      a0 = scl(Sp + Sm, -0.5);
+      a1 = scl(Sp - Sm, -0.5);
+    }
+    for (int n = 0; n < N; ++n) {
+      cplx<double> y = scl(SW(0, n), bd[n]);
+      if (n >= 2) y = y + scl(SW(0, n - 2), bl[n]);
+      if (n + 2 < N) y = y + scl(SW(0, n + 2), bu[n]);
+      if (n == 0) y = y + a0;
+      if (n == 1) y = y + a1;
+      KB(o, n) = nar<T>(y);
+    }
+  }
+  for (int q = 0; q < 12; ++q) AUX(q) = mk<T>((T)0, (T)0);
+}
+
+// Wall-correction amplitudes (FP64 boundary rows) from the DP velocity at the walls (vtop, vbot)
+// and, with slip, its z derivatives there: bottom wall Eqs. 41-44, slit Eqs. A4-A10 in closed
+// form (reading B3), slip lengths and wall velocities Eqs. A3, A8.  Written to kaux as the
+// node-value coefficients (cE + cG zeta) e^{-k zeta} + (tE + tG xi) e^{-k xi} per field.
+template <typename T, bool SLIP>
+__device__ __forceinline__ void wall_amplitudes(const Geometry& g, double kx, double ky, double kk,
+                                                const cplx<double> (&vtop)[3], const cplx<double> (&vbot)[3],
+                                                const cplx<double> (&dtop)[2], const cplx<double> (&dbot)[2],
+                                                cplx<T>* __restrict__ kaux, int64_t kidx, int64_t K) {
+  auto AUX = [&](int q) -> cplx<T>& { return kaux[(size_t)q * K + kidx]; };
+  const double sH = 2.0 / g.H;
+  (void)dtop;
+  (void)dbot;
+  (void)sH;
+  cplx<double> cE[3], cG[3], tE[3], tG[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) { cE[f] = cG[f] = tE[f] = tG[f] = mk<double>(0, 0); }
+  if (g.mode != DPS_FREE) {
+    const double ex = kx / kk, ey = ky / kk;
+    auto Lp = [&](cplx<double> u, cplx<double> v) { return scl(u, ex) + scl(v, ey); };
+    auto Tp = [&](cplx<double> u, cplx<double> v) { return scl(v, ex) - scl(u, ey); };
+    // wall data (Eq. A3): minus the DP velocity, and with slip u_DP - l0 du_DP/dz at the bottom,
+    // u_DP + lH du_DP/dz at the top for the tangential parts
+    cplx<double> eb0 = vbot[0], eb1 = vbot[1], et0 = vtop[0], et1 = vtop[1];
+    if (SLIP) {
+      eb0 = eb0 - scl(dbot[0], g.slip0 * sH);
+      eb1 = eb1 - scl(dbot[1], g.slip0 * sH);
+      et0 = et0 + scl(dtop[0], g.slipH * sH);
+      et1 = et1 + scl(dtop[1], g.slipH * sH);
+    }
+    const cplx<double> u0L = scl(Lp(eb0, eb1), -1.0), u0T = scl(Tp(eb0, eb1), -1.0);
+    const cplx<double> w0 = scl(vbot[2], -1.0);
+    cplx<double> AL = u0L, Az = w0, AT = u0T;
+    cplx<double> BL = mk<double>(0, 0), Bz = mk<double>(0, 0), BT = mk<double>(0, 0);
+    if (SLIP && g.mode == DPS_BOTTOM_WALL) {
+      // bottom family only: Robin rows u - l0 du/dz = u0 with w(0) = w0 give
+      // AT (1 + k l0) = u0T and AL (1 + 2 k l0) + i k l0 Az = u0L
+      const double kl0 = kk * g.slip0;
+      AT = scl(u0T, 1.0 / (1.0 + kl0));
+      AL = scl(u0L - scl(mul_i(w0), kl0), 1.0 / (1.0 + 2.0 * kl0));
+    }
+    if (SLIP && g.mode == DPS_SLIT) {
+      const cplx<double> uHL = scl(Lp(et0, et1), -1.0), uHT = scl(Tp(et0, et1), -1.0);
+      const cplx<double> wH = scl(vtop[2], -1.0);
+      const double kH = kk * g.H, E = exp(-kH), E2 = E * E;
+      const double kl0 = kk * g.slip0, klH = kk * g.slipH;
+      // transverse: [1 + k l0, E (1 - k l0); E (1 - k lH), 1 + k lH] [AT; BT] = [u0T; uHT]
+      {
+        const double t11 = 1.0 + kl0, t12 = E * (1.0 - kl0), t21 = E * (1.0 - klH), t22 = 1.0 + klH;
+        const double idt = 1.0 / (t11 * t22 - t12 * t21);
+        AT = scl(scl(u0T, t22) - scl(uHT, t12), idt);
+        BT = scl(scl(uHT, t11) - scl(u0T, t21), idt);
+      }
+      // longitudinal/normal: S0 A + E N1 B = a0, SH B + E N2 A = b0 with A = (AL, Az), B = (BL, Bz),
+      // S0 = [1 + 2 k l0, i k l0; 0, 1], SH = [1 + 2 k lH, -i k lH; 0, 1],
+      // N1 = [(1 - k l0)(1 - kH) - k l0, i k (H (1 - k l0) + l0); i kH, 1 + kH],
+      // N2 = [(1 - kH)(1 - k lH) - k lH, -i k (H (1 - k lH) + lH); -i kH, 1 + kH];
+      // (S0 - E^2 N1 SH^-1 N2) A = a0 - E N1 SH^-1 b0, then B = SH^-1 (b0 - E N2 A)
+      const cplx<double> zc = mk<double>(0, 0);
+      const double sh = 1.0 / (1.0 + 2.0 * klH);
+      const cplx<double> h11 = mk<double>(sh, 0), h12 = mk<double>(0, klH * sh);  // SH^-1 = [h11 h12; 0 1]
+      const cplx<double> n11 = mk<double>((1.0 - kl0) * (1.0 - kH) - kl0, 0), n12 = mk<double>(0, kk * (g.H * (1.0 - kl0) + g.slip0));
+      const cplx<double> n21 = mk<double>(0, kH), n22 = mk<double>(1.0 + kH, 0);
+      const cplx<double> m11 = mk<double>((1.0 - kH) * (1.0 - klH) - klH, 0), m12 = mk<double>(0, -kk * (g.H * (1.0 - klH) + g.slipH));
+      const cplx<double> m21 = mk<double>(0, -kH), m22 = mk<double>(1.0 + kH, 0);
+      // P = SH^-1 N2, Q = N1 P
+      const cplx<double> p11 = h11 * m11 + h12 * m21, p12 = h11 * m12 + h12 * m22, p21 = m21, p22 = m22;
+      const cplx<double> q11 = n11 * p11 + n12 * p21, q12 = n11 * p12 + n12 * p22;
+      const cplx<double> q21 = n21 * p11 + n22 * p21, q22 = n21 * p12 + n22 * p22;
+      const cplx<double> x11 = mk<double>(1.0 + 2.0 * kl0, 0) - scl(q11, E2), x12 = mk<double>(0, kl0) - scl(q12, E2);
+      const cplx<double> x21 = zc - scl(q21, E2), x22 = mk<double>(1.0, 0) - scl(q22, E2);
+      const cplx<double> hb0 = h11 * uHL + h12 * wH, hb1 = wH;  // SH^-1 b0
+      const cplx<double> r0 = u0L - scl(n11 * hb0 + n12 * hb1, E);
+      const cplx<double> r1 = w0 - scl(n21 * hb0 + n22 * hb1, E);
+      const cplx<double> det = x11 * x22 - x12 * x21;
+      AL = cdiv(x22 * r0 - x12 * r1, det);
+      Az = cdiv(x11 * r1 - x21 * r0, det);
+      const cplx<double> e0 = uHL - scl(m11 * AL + m12 * Az, E), e1 = wH - scl(m21 * AL + m22 * Az, E);
+      BL = h11 * e0 + h12 * e1;
+      Bz = e1;
+    }
+    if (!SLIP && g.mode == DPS_SLIT) {
+      const cplx<double> uHL = scl(Lp(vtop[0], vtop[1]), -1.0), uHT = scl(Tp(vtop[0], vtop[1]), -1.0);
+      const cplx<double> wH = scl(vtop[2], -1.0);
+      const double kH = kk * g.H;
+      const double E = exp(-kH);
+      const double E2 = E * E;
+      // transverse: [1 E; E 1] [AT; BT] = [u0T; uHT]
+      AT = scl(u0T - scl(uHT, E), 1.0 / (1.0 - E2));
+      BT = scl(uHT - scl(u0T, E), 1.0 / (1.0 - E2));
+      // longitudinal/normal: A = a0 - E M1 B, B = b0 - E M2 A  =>  (I - E^2 M1 M2) A = a0 - E M1 b0,
+      // M1 = [[1-kH, i kH], [i kH, 1+kH]], M2 = [[1-kH, -i kH], [-i kH, 1+kH]]
+      const double k2H2 = kH * kH;
+      const cplx<double> m11 = mk<double>(1.0 - E2 * (1.0 - 2.0 * kH + 2.0 * k2H2), 0.0);
+      const cplx<double> m12 = mk<double>(0.0, -E2 * 2.0 * k2H2);
+      const cplx<double> m21 = mk<double>(0.0, E2 * 2.0 * k2H2);
+      const cplx<double> m22 = mk<double>(1.0 - E2 * (1.0 + 2.0 * kH + 2.0 * k2H2), 0.0);
+      const cplx<double> M1b_L = scl(uHL, 1.0 - kH) + scl(mul_i(wH), kH);
+      const cplx<double> M1b_z = scl(mul_i(uHL), kH) + scl(wH, 1.0 + kH);
+      const cplx<double> rL = u0L - scl(M1b_L, E);
+      const cplx<double> rz = w0 - scl(M1b_z, E);
+      const cplx<double> det = m11 * m22 - m12 * m21;
+      AL = cdiv(m22 * rL - m12 * rz, det);
+      Az = cdiv(m11 * rz - m21 * rL, det);
+      const cplx<double> M2a_L = scl(AL, 1.0 - kH) - scl(mul_i(Az), kH);
+      const cplx<double> M2a_z = scl(mul_i(AL), -kH) + scl(Az, 1.0 + kH);
+      BL = uHL - scl(M2a_L, E);
+      Bz = wH - scl(M2a_z, E);
+    }
+    // pressure amplitudes over 2 eta: bottom k (Az - i AL), top -k (Bz + i BL)
+    const cplx<double> pib = scl(Az - mul_i(AL), kk);
+    const cplx<double> pit = scl(Bz + mul_i(BL), -kk);
+    // u_L = (AL - i pib zeta) e^{-k zeta} + (BL - i pit xi) e^{-k xi};  u_T = AT e^{-k zeta} + BT e^{-k xi}
+    // w   = (Az + pib zeta) e^{-k zeta} + (Bz - pit xi) e^{-k xi}
+    const cplx<double> gbL = scl(mul_i(pib), -1.0), gtL = scl(mul_i(pit), -1.0);
+    cE[0] = scl(AL, ex) - scl(AT, ey);  cG[0] = scl(gbL, ex);
+    tE[0] = scl(BL, ex) - scl(BT, ey);  tG[0] = scl(gtL, ex);
+    cE[1] = scl(AL, ey) + scl(AT, ex);  cG[1] = scl(gbL, ey);
+    tE[1] = scl(BL, ey) + scl(BT, ex);  tG[1] = scl(gtL, ey);
+    cE[2] = Az;                          cG[2] = pib;
+    tE[2] = Bz;                          tG[2] = scl(pit, -1.0);
+  }
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    AUX(4 * f + 0) = nar<T>(cE[f]);
+    AUX(4 * f + 1) = nar<T>(cG[f]);
+    AUX(4 * f + 2) = nar<T>(tE[f]);
+    AUX(4 * f + 3) = nar<T>(tG[f]);
+  }
+}
+
 // FACT: factorise the banded systems while sweeping the pressure right-hand side and keep the
 // factorisation in the slot's workspace; without FACT, reuse the factorisation left there by the
 // previous call on the same slot, which must have had the same |k| (the partner -ky of a pair).
@@ -276,56 +478,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
   const double inv_eta = 1.0 / g.eta;
 
   if (ki.zero) {
-    // ---- k = 0: w = 0; sigma c_n = -f_n/eta with Dirichlet/Neumann rows (Eqs. 51-52, A12) ----
-    for (int o = 0; o < 3; ++o) {
-      if (g.mode == DPS_FREE || o == 2) {
-        for (int n = 0; n < N; ++n) KB(o, n) = mk<T>((T)0, (T)0);
-        continue;
-      }
-      cplx<double> Sp = mk<double>(0, 0), Sm = mk<double>(0, 0), Pd = mk<double>(0, 0), Pm = mk<double>(0, 0);
-      for (int n = 0; n < N; ++n) {
-        const cplx<double> cn = scl(wid(KB(o, n)), -inv_eta / sig);
-        SW(0, n) = cn;
-        const double sgn = (n & 1) ? -1.0 : 1.0;
-        Sp = Sp + scl(cn, bQ[n]);
-        Sm = Sm + scl(cn, sgn * bQ[n]);
-        Pd = Pd + scl(cn, bP[n]);
-        if (SLIP) Pm = Pm + scl(cn, sgn * bP[n]);
-      }
-      cplx<double> a0, a1;
-      if (SLIP) {
-        // Robin rows (Eq. A12): y(-1) - l0 (2/H) y_s(-1) = g_bot and, in the slit,
-        // y(+1) + lH (2/H) y_s(+1) = g_top (above one wall: y_s(+1) = 0); y(+-1) = S+- + a0 +- a1,
-        // y_s(+1) = Pd + a1, y_s(-1) = -Pm + a1; g = Nx Ny u^W (unnormalised transform)
-        const double nxy = (double)g.nx * (double)g.ny;
-        const double al = 1.0 + g.slip0 * sH;
-        const cplx<double> Rb = mk<double>(nxy * g.uw0[o], 0.0) - Sm - scl(Pm, g.slip0 * sH);
-        if (g.mode == DPS_BOTTOM_WALL) {
-          a1 = scl(Pd, -1.0);
-          a0 = Rb + scl(a1, al);
-        } else {
-          const double be = 1.0 + g.slipH * sH;
-          const cplx<double> Rt = mk<double>(nxy * g.uwH[o], 0.0) - Sp - scl(Pd, g.slipH * sH);
-          a1 = scl(Rt - Rb, 1.0 / (al + be));
-          a0 = Rb + scl(a1, al);
-        }
-      } else if (g.mode == DPS_BOTTOM_WALL) {  // y(-1) = 0, y_s(+1) = 0
-        a1 = scl(Pd, -1.0);
-        a0 = a1 - Sm;
-      } else {                           // y(-1) = y(+1) = 0
-        a0 = scl(Sp + Sm, -0.5);
-        a1 = scl(Sp - Sm, -0.5);
-      }
-      for (int n = 0; n < N; ++n) {
-        cplx<double> y = scl(SW(0, n), bd[n]);
-        if (n >= 2) y = y + scl(SW(0, n - 2), bl[n]);
-        if (n + 2 < N) y = y + scl(SW(0, n + 2), bu[n]);
-        if (n == 0) y = y + a0;
-        if (n == 1) y = y + a1;
-        KB(o, n) = nar<T>(y);
-      }
-    }
-    for (int q = 0; q < 12; ++q) AUX(q) = mk<T>((T)0, (T)0);
+    zero_mode<T, SLIP>(g, band, bandT, kbuf, kaux, sw, slots, slot, kidx, K);
     return false;
   }
 
@@ -581,122 +734,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
     }
   }
 
-  // ---- wall-correction amplitudes (FP64 boundary rows) -------------------------------------------
-  cplx<double> cE[3], cG[3], tE[3], tG[3];
-#pragma unroll
-  for (int f = 0; f < 3; ++f) { cE[f] = cG[f] = tE[f] = tG[f] = mk<double>(0, 0); }
-  if (g.mode != DPS_FREE) {
-    const double ex = kx / kk, ey = ky / kk;
-    auto Lp = [&](cplx<double> u, cplx<double> v) { return scl(u, ex) + scl(v, ey); };
-    auto Tp = [&](cplx<double> u, cplx<double> v) { return scl(v, ex) - scl(u, ey); };
-    // wall data (Eq. A3): minus the DP velocity, and with slip u_DP - l0 du_DP/dz at the bottom,
-    // u_DP + lH du_DP/dz at the top for the tangential parts
-    cplx<double> eb0 = vbot[0], eb1 = vbot[1], et0 = vtop[0], et1 = vtop[1];
-    if (SLIP) {
-      eb0 = eb0 - scl(dbot[0], g.slip0 * sH);
-      eb1 = eb1 - scl(dbot[1], g.slip0 * sH);
-      et0 = et0 + scl(dtop[0], g.slipH * sH);
-      et1 = et1 + scl(dtop[1], g.slipH * sH);
-    }
-    const cplx<double> u0L = scl(Lp(eb0, eb1), -1.0), u0T = scl(Tp(eb0, eb1), -1.0);
-    const cplx<double> w0 = scl(vbot[2], -1.0);
-    cplx<double> AL = u0L, Az = w0, AT = u0T;
-    cplx<double> BL = mk<double>(0, 0), Bz = mk<double>(0, 0), BT = mk<double>(0, 0);
-    if (SLIP && g.mode == DPS_BOTTOM_WALL) {
-      // bottom family only: Robin rows u - l0 du/dz = u0 with w(0) = w0 give
-      // AT (1 + k l0) = u0T and AL (1 + 2 k l0) + i k l0 Az = u0L
-      const double kl0 = kk * g.slip0;
-      AT = scl(u0T, 1.0 / (1.0 + kl0));
-      AL = scl(u0L - scl(mul_i(w0), kl0), 1.0 / (1.0 + 2.0 * kl0));
-    }
-    if (SLIP && g.mode == DPS_SLIT) {
-      const cplx<double> uHL = scl(Lp(et0, et1), -1.0), uHT = scl(Tp(et0, et1), -1.0);
-      const cplx<double> wH = scl(vtop[2], -1.0);
-      const double kH = kk * g.H, E = exp(-kH), E2 = E * E;
-      const double kl0 = kk * g.slip0, klH = kk * g.slipH;
-      // transverse: [1 + k l0, E (1 - k l0); E (1 - k lH), 1 + k lH] [AT; BT] = [u0T; uHT]
-      {
-        const double t11 = 1.0 + kl0, t12 = E * (1.0 - kl0), t21 = E * (1.0 - klH), t22 = 1.0 + klH;
-        const double idt = 1.0 / (t11 * t22 - t12 * t21);
-        AT = scl(scl(u0T, t22) - scl(uHT, t12), idt);
-        BT = scl(scl(uHT, t11) - scl(u0T, t21), idt);
-      }
-      // longitudinal/normal: S0 A + E N1 B = a0, SH B + E N2 A = b0 with A = (AL, Az), B = (BL, Bz),
-      // S0 = [1 + 2 k l0, i k l0; 0, 1], SH = [1 + 2 k lH, -i k lH; 0, 1],
-      // N1 = [(1 - k l0)(1 - kH) - k l0, i k (H (1 - k l0) + l0); i kH, 1 + kH],
-      // N2 = [(1 - kH)(1 - k lH) - k lH, -i k (H (1 - k lH) + lH); -i kH, 1 + kH];
-      // (S0 - E^2 N1 SH^-1 N2) A = a0 - E N1 SH^-1 b0, then B = SH^-1 (b0 - E N2 A)
-      const cplx<double> zc = mk<double>(0, 0);
-      const double sh = 1.0 / (1.0 + 2.0 * klH);
-      const cplx<double> h11 = mk<double>(sh, 0), h12 = mk<double>(0, klH * sh);  // SH^-1 = [h11 h12; 0 1]
-      const cplx<double> n11 = mk<double>((1.0 - kl0) * (1.0 - kH) - kl0, 0), n12 = mk<double>(0, kk * (g.H * (1.0 - kl0) + g.slip0));
-      const cplx<double> n21 = mk<double>(0, kH), n22 = mk<double>(1.0 + kH, 0);
-      const cplx<double> m11 = mk<double>((1.0 - kH) * (1.0 - klH) - klH, 0), m12 = mk<double>(0, -kk * (g.H * (1.0 - klH) + g.slipH));
-      const cplx<double> m21 = mk<double>(0, -kH), m22 = mk<double>(1.0 + kH, 0);
-      // P = SH^-1 N2, Q = N1 P
-      const cplx<double> p11 = h11 * m11 + h12 * m21, p12 = h11 * m12 + h12 * m22, p21 = m21, p22 = m22;
-      const cplx<double> q11 = n11 * p11 + n12 * p21, q12 = n11 * p12 + n12 * p22;
-      const cplx<double> q21 = n21 * p11 + n22 * p21, q22 = n21 * p12 + n22 * p22;
-      const cplx<double> x11 = mk<double>(1.0 + 2.0 * kl0, 0) - scl(q11, E2), x12 = mk<double>(0, kl0) - scl(q12, E2);
-      const cplx<double> x21 = zc - scl(q21, E2), x22 = mk<double>(1.0, 0) - scl(q22, E2);
-      const cplx<double> hb0 = h11 * uHL + h12 * wH, hb1 = wH;  // SH^-1 b0
-      const cplx<double> r0 = u0L - scl(n11 * hb0 + n12 * hb1, E);
-      const cplx<double> r1 = w0 - scl(n21 * hb0 + n22 * hb1, E);
-      const cplx<double> det = x11 * x22 - x12 * x21;
-      AL = cdiv(x22 * r0 - x12 * r1, det);
-      Az = cdiv(x11 * r1 - x21 * r0, det);
-      const cplx<double> e0 = uHL - scl(m11 * AL + m12 * Az, E), e1 = wH - scl(m21 * AL + m22 * Az, E);
-      BL = h11 * e0 + h12 * e1;
-      Bz = e1;
-    }
-    if (!SLIP && g.mode == DPS_SLIT) {
-      const cplx<double> uHL = scl(Lp(vtop[0], vtop[1]), -1.0), uHT = scl(Tp(vtop[0], vtop[1]), -1.0);
-      const cplx<double> wH = scl(vtop[2], -1.0);
-      const double kH = kk * g.H;
-      const double E = exp(-kH);
-      const double E2 = E * E;
-      // transverse: [1 E; E 1] [AT; BT] = [u0T; uHT]
-      AT = scl(u0T - scl(uHT, E), 1.0 / (1.0 - E2));
-      BT = scl(uHT - scl(u0T, E), 1.0 / (1.0 - E2));
-      // longitudinal/normal: A = a0 - E M1 B, B = b0 - E M2 A  =>  (I - E^2 M1 M2) A = a0 - E M1 b0,
-      // M1 = [[1-kH, i kH], [i kH, 1+kH]], M2 = [[1-kH, -i kH], [-i kH, 1+kH]]
-      const double k2H2 = kH * kH;
-      const cplx<double> m11 = mk<double>(1.0 - E2 * (1.0 - 2.0 * kH + 2.0 * k2H2), 0.0);
-      const cplx<double> m12 = mk<double>(0.0, -E2 * 2.0 * k2H2);
-      const cplx<double> m21 = mk<double>(0.0, E2 * 2.0 * k2H2);
-      const cplx<double> m22 = mk<double>(1.0 - E2 * (1.0 + 2.0 * kH + 2.0 * k2H2), 0.0);
-      const cplx<double> M1b_L = scl(uHL, 1.0 - kH) + scl(mul_i(wH), kH);
-      const cplx<double> M1b_z = scl(mul_i(uHL), kH) + scl(wH, 1.0 + kH);
-      const cplx<double> rL = u0L - scl(M1b_L, E);
-      const cplx<double> rz = w0 - scl(M1b_z, E);
-      const cplx<double> det = m11 * m22 - m12 * m21;
-      AL = cdiv(m22 * rL - m12 * rz, det);
-      Az = cdiv(m11 * rz - m21 * rL, det);
-      const cplx<double> M2a_L = scl(AL, 1.0 - kH) - scl(mul_i(Az), kH);
-      const cplx<double> M2a_z = scl(mul_i(AL), -kH) + scl(Az, 1.0 + kH);
-      BL = uHL - scl(M2a_L, E);
-      Bz = wH - scl(M2a_z, E);
-    }
-    // pressure amplitudes over 2 eta: bottom k (Az - i AL), top -k (Bz + i BL)
-    const cplx<double> pib = scl(Az - mul_i(AL), kk);
-    const cplx<double> pit = scl(Bz + mul_i(BL), -kk);
-    // u_L = (AL - i pib zeta) e^{-k zeta} + (BL - i pit xi) e^{-k xi};  u_T = AT e^{-k zeta} + BT e^{-k xi}
-    // w   = (Az + pib zeta) e^{-k zeta} + (Bz - pit xi) e^{-k xi}
-    const cplx<double> gbL = scl(mul_i(pib), -1.0), gtL = scl(mul_i(pit), -1.0);
-    cE[0] = scl(AL, ex) - scl(AT, ey);  cG[0] = scl(gbL, ex);
-    tE[0] = scl(BL, ex) - scl(BT, ey);  tG[0] = scl(gtL, ex);
-    cE[1] = scl(AL, ey) + scl(AT, ex);  cG[1] = scl(gbL, ey);
-    tE[1] = scl(BL, ey) + scl(BT, ex);  tG[1] = scl(gtL, ey);
-    cE[2] = Az;                          cG[2] = pib;
-    tE[2] = Bz;                          tG[2] = scl(pit, -1.0);
-  }
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    AUX(4 * f + 0) = nar<T>(cE[f]);
-    AUX(4 * f + 1) = nar<T>(cG[f]);
-    AUX(4 * f + 2) = nar<T>(tE[f]);
-    AUX(4 * f + 3) = nar<T>(tG[f]);
-  }
+  wall_amplitudes<T, SLIP>(g, kx, ky, kk, vtop, vbot, dtop, dbot, kaux, kidx, K);
   return true;
 }
 
@@ -723,6 +761,342 @@ __global__ void __launch_bounds__(kBvpThreads, 3) solve_kernel(Geometry g, const
       solve_one<T, false, SLIP>(g, band, bandT, kbuf, kaux, pws, sw, fr, slots, slot, k2, K);
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 solve from a plan-time factorisation table.  The banded systems of a wavenumber depend on
+// |k| only, so their elimination coefficients are computed once per (kx, |ky|) when the plan is
+// created (factor_kernel) and read by every product.  Each row's pivot reciprocal rho_n scales
+// that row's right-hand side where the right-hand side is formed (in the transform precision, as
+// the right-hand side itself), so the FP64 sweep of a row is s_n = r'_n - V_n s_{n+2},
+// V_n = rho_n U_n: one DFMA per real right-hand side instead of a DFMA and a DMUL.
+//
+// Table fac[(n * 4 + q) * KP + kp], kp = |kyi| nkx + kxi, KP = nkx (ny/2 + 1); row n of parity
+// par = n & 1:
+//   n > par:  q0 V_n = U_n rho_n   q1 t_n   q2 b_n (folded boundary coefficient)   q3 rho_n
+//   n = par:  q0 U_n               q1 D'    q2 b_n                                  q3 1/(D' beta_a + k^2 b_n)
+// with U_n = -k^2 u_n, rho_n = 1/((sigma - k^2 d_n) - U_n t_{n+2}), t_n = -k^2 l_n rho_n, and the
+// DtN boundary rows folded as in solve_one.
+// ---------------------------------------------------------------------------------------------
+__global__ void factor_kernel(Geometry g, const double* __restrict__ band, double* __restrict__ fac, int64_t KP) {
+  const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kp >= KP) return;
+  const int N = g.nz;
+  const int kxi = (int)(kp % g.nkx), kyi = (int)(kp / g.nkx);
+  const double* bl = band;
+  const double* bd = band + N;
+  const double* bu = band + 2 * N;
+  const double* bP = band + 3 * N;
+  const double* bQ = band + 4 * N;
+  const double kx = 2.0 * M_PI * (double)kxi / g.Lx, ky = 2.0 * M_PI * (double)kyi / g.Ly;
+  const double kk = sqrt(kx * kx + ky * ky), kap = kk * kk;
+  const double sH = 2.0 / g.H, sig = sH * sH;
+  auto F = [&](int n, int q) -> double& { return fac[((size_t)n * 4 + q) * KP + kp]; };
+  for (int par = 0; par < 2; ++par) {
+    const int nlast = ((N - 1 - par) & 1) ? N - 2 : N - 1;
+    double t_next = 0.0, bfold = 0.0;
+    for (int n = nlast; n >= par; n -= 2) {
+      const double U = -kap * bu[n];
+      const double bcur = (n == nlast) ? (sH * bP[n] + kk * bQ[n]) : bfold;
+      if (n > par) {
+        const double rho = 1.0 / ((sig - kap * bd[n]) - U * t_next);
+        const double t = rho * (-kap * bl[n]);
+        F(n, 0) = U * rho;
+        F(n, 1) = t;
+        F(n, 2) = bcur;
+        F(n, 3) = rho;
+        bfold = (sH * bP[n - 2] + kk * bQ[n - 2]) - bcur * t;
+        t_next = t;
+      } else {
+        const double Dp = (sig - kap * bd[n]) - U * t_next;
+        const double beta_a = (par == 0) ? kk : (sH + kk);
+        F(n, 0) = U;
+        F(n, 1) = Dp;
+        F(n, 2) = bcur;
+        F(n, 3) = (kk > 0.0) ? 1.0 / (Dp * beta_a + kap * bcur) : 0.0;  // k = 0 takes zero_mode
+      }
+    }
+  }
+}
+
+// r rho in the transform precision (the right-hand side's own precision), widened exactly
+template <typename T> __device__ __forceinline__ cplx<double> prescale(cplx<T> r, double rho);
+template <> __device__ __forceinline__ cplx<double> prescale<float>(cplx<float> r, double rho) {
+  const float rf = narrow_bits(rho);
+  return mk<double>(f2d(r.x * rf), f2d(r.y * rf));
+}
+template <> __device__ __forceinline__ cplx<double> prescale<double>(cplx<double> r, double rho) {
+  return mk<double>(r.x * rho, r.y * rho);
+}
+
+template <typename T, bool SLIP>
+__device__ __noinline__ void solve_tab(const Geometry& g, const double* __restrict__ band, const T* __restrict__ bandT,
+                                       const double* __restrict__ fac, int64_t KP, cplx<T>* __restrict__ kbuf,
+                                       cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ pws,
+                                       cplx<double>* __restrict__ sw, int slots, int slot, int64_t kidx, int64_t K) {
+  const int N = g.nz;
+  const KInfo ki = kinfo(g, kidx);
+  if (ki.nyq) return;
+  if (ki.zero) {
+    zero_mode<T, SLIP>(g, band, bandT, kbuf, kaux, sw, slots, slot, kidx, K);
+    return;
+  }
+  const int64_t kp = (int64_t)((2 * ki.kyi <= g.ny) ? ki.kyi : g.ny - ki.kyi) * g.nkx + ki.kxi;
+  auto KB = [&](int f, int n) -> cplx<T>& { return kbuf[((size_t)f * N + n) * K + kidx]; };
+  auto SW = [&](int f, int n) -> cplx<double>& { return sw[((size_t)f * N + n) * slots + slot]; };
+  auto PW = [&](int n) -> cplx<T>& { return pws[(size_t)n * slots + slot]; };
+  auto FAC = [&](int n, int q) -> double { return fac[((size_t)n * 4 + q) * KP + kp]; };
+  const double* bP = band + 3 * N;
+  const double* bQ = band + 4 * N;
+  const T* tl = bandT;
+  const T* td = bandT + N;
+  const T* tu = bandT + 2 * N;
+  const double sH = 2.0 / g.H;
+  const double inv_eta = 1.0 / g.eta;
+  const double kx = ki.kx, ky = ki.ky, kk = ki.kk, kap = kk * kk;
+  const T tkx = (T)kx, tky = (T)ky, tsH = (T)sH, tie = (T)inv_eta;
+  const cplx<T> zT = mk<T>((T)0, (T)0);
+
+  // ---- pressure: (D^2 - k^2) p = i kx f + i ky g + D h, DtN rows with zero data ----------------
+  cplx<double> ptop = mk<double>(0, 0), pbot = mk<double>(0, 0);
+  for (int par = 0; par < 2; ++par) {
+    const int nlast = ((N - 1 - par) & 1) ? N - 2 : N - 1;
+    cplx<double> s_next = mk<double>(0, 0), gacc = mk<double>(0, 0);
+    cplx<T> dh_next = zT;  // derivative recurrence of h over the opposite parity
+    cplx<T> fc = KB(0, nlast), gc = KB(1, nlast), hc = (nlast + 1 < N) ? KB(2, nlast + 1) : zT;
+    double vc = FAC(nlast, 0), bc = FAC(nlast, 2), rc = FAC(nlast, 3);
+    for (int n = nlast; n >= par; n -= 2) {
+      cplx<T> fn = zT, gn = zT, hn = zT;
+      double vn = 0.0, bn = 0.0, rn = 0.0;
+      if (n - 2 >= par) {  // next row's inputs before this row's FP64 recurrence
+        fn = KB(0, n - 2);
+        gn = KB(1, n - 2);
+        hn = KB(2, n - 1);
+        vn = FAC(n - 2, 0);
+        bn = FAC(n - 2, 2);
+        rn = FAC(n - 2, 3);
+      }
+      cplx<T> dh = dh_next + scl(hc, (T)(2 * (n + 1)));
+      dh_next = dh;
+      if (n == 0) dh = scl(dh, (T)0.5);
+      const cplx<T> rt = mk<T>(-tkx * fc.y - tky * gc.y + tsH * dh.x, tkx * fc.x + tky * gc.x + tsH * dh.y);
+      if (n > par) {
+        const cplx<double> r = prescale<T>(rt, rc);
+        const cplx<double> sv = mk<double>(fma(-vc, s_next.x, r.x), fma(-vc, s_next.y, r.y));
+        SW(0, n) = sv;
+        gacc = gacc - scl(sv, bc);
+        s_next = sv;
+      } else {
+        // row `par`: D' c - kappa a = r - U s_{par+2};  boundary row: beta_a a + b c = g'
+        const double U = vc, Dp = FAC(n, 1), idet = rc;
+        const double beta_a = (par == 0) ? kk : (sH + kk);
+        const cplx<double> rhs = wid(rt) - scl(s_next, U);
+        const cplx<double> c0 = scl(scl(rhs, beta_a) + scl(gacc, kap), idet);
+        const cplx<double> a = scl(scl(gacc, Dp) - scl(rhs, bc), idet);
+        // ascending substitution; y = B B c + a in the transform precision
+        cplx<double> cm = c0;
+        cplx<T> tcm2 = zT, tcm = nar<T>(c0);
+        cplx<double> sp = scl(c0, bQ[par]);
+        const cplx<T> ta = nar<T>(a);
+        cplx<double> sc = (par + 2 <= nlast) ? SW(0, par + 2) : mk<double>(0, 0);
+        double tc = (par + 2 <= nlast) ? FAC(par + 2, 1) : 0.0;
+        for (int m = par + 2; m <= nlast + 2; m += 2) {
+          cplx<double> sn = mk<double>(0, 0);
+          double tn = 0.0;
+          if (m + 2 <= nlast) {
+            sn = SW(0, m + 2);
+            tn = FAC(m + 2, 1);
+          }
+          cplx<T> tnew = zT;
+          if (m <= nlast) {
+            const cplx<double> cnew = mk<double>(fma(-tc, cm.x, sc.x), fma(-tc, cm.y, sc.y));
+            sp = sp + scl(cnew, bQ[m]);
+            cm = cnew;
+            tnew = nar<T>(cnew);
+          }
+          const int q = m - 2;
+          cplx<T> y = scl(tcm, td[q]) + scl(tnew, tu[q]);
+          if (q >= 2) y = y + scl(tcm2, tl[q]);
+          if (q == par) y = y + ta;
+          PW(q) = y;
+          tcm2 = tcm;
+          tcm = tnew;
+          sc = sn;
+          tc = tn;
+        }
+        const double sgn = par ? -1.0 : 1.0;
+        ptop = ptop + sp + a;
+        pbot = pbot + scl(sp + a, sgn);
+      }
+      fc = fn;
+      gc = gn;
+      hc = hn;
+      vc = vn;
+      bc = bn;
+      rc = rn;
+    }
+  }
+
+  // ---- velocity: three right-hand sides sharing the factorisation -------------------------------
+  const cplx<double> ik_top = scl(ptop, 1.0 / (2.0 * kk * g.eta));
+  const cplx<double> ik_bot = scl(pbot, 1.0 / (2.0 * kk * g.eta));
+  cplx<double> gt[3], gb[3];
+  gt[0] = scl(mul_i(ik_top), -kx);
+  gb[0] = scl(mul_i(ik_bot), kx);
+  gt[1] = scl(mul_i(ik_top), -ky);
+  gb[1] = scl(mul_i(ik_bot), ky);
+  gt[2] = scl(ptop, 0.5 * inv_eta);
+  gb[2] = scl(pbot, 0.5 * inv_eta);
+  cplx<double> vtop[3], vbot[3];
+  cplx<double> dtop[2], dbot[2];  // SLIP: y_s(+-1) of the tangential DP velocities
+#pragma unroll
+  for (int f = 0; f < 3; ++f) { vtop[f] = mk<double>(0, 0); vbot[f] = mk<double>(0, 0); }
+#pragma unroll
+  for (int f = 0; f < 2; ++f) { dtop[f] = mk<double>(0, 0); dbot[f] = mk<double>(0, 0); }
+  for (int par = 0; par < 2; ++par) {
+    const int nlast = ((N - 1 - par) & 1) ? N - 2 : N - 1;
+    cplx<double> s_next[3], gacc[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      s_next[f] = mk<double>(0, 0);
+      gacc[f] = par ? scl(gt[f] + gb[f], 0.5) : scl(gt[f] - gb[f], 0.5);
+    }
+    cplx<T> dp_next = zT;
+    cplx<T> pc1 = (nlast + 1 < N) ? PW(nlast + 1) : zT, pc0 = PW(nlast);
+    cplx<T> f0c = KB(0, nlast), f1c = KB(1, nlast), f2c = KB(2, nlast);
+    double vc = FAC(nlast, 0), bc = FAC(nlast, 2), rc = FAC(nlast, 3);
+    for (int n = nlast; n >= par; n -= 2) {
+      cplx<T> pn1 = zT, pn0 = zT, f0n = zT, f1n = zT, f2n = zT;
+      double vn = 0.0, bn = 0.0, rn = 0.0;
+      if (n - 2 >= par) {
+        pn1 = PW(n - 1);
+        pn0 = PW(n - 2);
+        f0n = KB(0, n - 2);
+        f1n = KB(1, n - 2);
+        f2n = KB(2, n - 2);
+        vn = FAC(n - 2, 0);
+        bn = FAC(n - 2, 2);
+        rn = FAC(n - 2, 3);
+      }
+      cplx<T> dp = dp_next + scl(pc1, (T)(2 * (n + 1)));
+      dp_next = dp;
+      if (n == 0) dp = scl(dp, (T)0.5);
+      cplx<T> rt[3];
+      rt[0] = scl(scl(mul_i(pc0), tkx) - f0c, tie);
+      rt[1] = scl(scl(mul_i(pc0), tky) - f1c, tie);
+      rt[2] = scl(scl(dp, tsH) - f2c, tie);
+      if (n > par) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          const cplx<double> r = prescale<T>(rt[f], rc);
+          const cplx<double> sv = mk<double>(fma(-vc, s_next[f].x, r.x), fma(-vc, s_next[f].y, r.y));
+          SW(f, n) = sv;
+          gacc[f] = gacc[f] - scl(sv, bc);
+          s_next[f] = sv;
+        }
+      } else {
+        const double U = vc, Dp = FAC(n, 1), idet = rc;
+        const double beta_a = (par == 0) ? kk : (sH + kk);
+        const double sgn = par ? -1.0 : 1.0;
+        cplx<double> cm[3];
+        cplx<T> tcm2[3], tcm[3];
+        cplx<double> sp[3], sd[2];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          const cplx<double> rhs = wid(rt[f]) - scl(s_next[f], U);
+          const cplx<double> c0 = scl(scl(rhs, beta_a) + scl(gacc[f], kap), idet);
+          const cplx<double> a = scl(scl(gacc[f], Dp) - scl(rhs, bc), idet);
+          cm[f] = c0;
+          tcm[f] = nar<T>(c0);
+          tcm2[f] = zT;
+          sp[f] = scl(c0, bQ[par]);
+          if (SLIP && f < 2) {
+            sd[f] = scl(c0, bP[par]);
+            if (par) {  // a1 T_1 has y_s = a1 at both ends; a0 T_0 has none
+              dtop[f] = dtop[f] + a;
+              dbot[f] = dbot[f] + a;
+            }
+          }
+          vtop[f] = vtop[f] + a;
+          vbot[f] = vbot[f] + scl(a, sgn);
+          gacc[f] = a;  // reuse: a_par of this field
+        }
+        // ascending substitution for the three fields together
+        cplx<double> sc[3];
+        double tc = (par + 2 <= nlast) ? FAC(par + 2, 1) : 0.0;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) sc[f] = (par + 2 <= nlast) ? SW(f, par + 2) : mk<double>(0, 0);
+        for (int m = par + 2; m <= nlast + 2; m += 2) {
+          cplx<double> sn[3];
+          double tn = 0.0;
+#pragma unroll
+          for (int f = 0; f < 3; ++f) sn[f] = mk<double>(0, 0);
+          if (m + 2 <= nlast) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) sn[f] = SW(f, m + 2);
+            tn = FAC(m + 2, 1);
+          }
+          const int q = m - 2;
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            cplx<T> tnew = zT;
+            if (m <= nlast) {
+              const cplx<double> cnew = mk<double>(fma(-tc, cm[f].x, sc[f].x), fma(-tc, cm[f].y, sc[f].y));
+              sp[f] = sp[f] + scl(cnew, bQ[m]);
+              if (SLIP && f < 2) sd[f] = sd[f] + scl(cnew, bP[m]);
+              cm[f] = cnew;
+              tnew = nar<T>(cnew);
+            }
+            cplx<T> y = scl(tcm[f], td[q]) + scl(tnew, tu[q]);
+            if (q >= 2) y = y + scl(tcm2[f], tl[q]);
+            if (q == par) y = y + nar<T>(gacc[f]);
+            KB(f, q) = y;
+            tcm2[f] = tcm[f];
+            tcm[f] = tnew;
+            sc[f] = sn[f];
+          }
+          tc = tn;
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          vtop[f] = vtop[f] + sp[f];
+          vbot[f] = vbot[f] + scl(sp[f], sgn);
+        }
+        if (SLIP) {  // T_n'(-1) = (-1)^(n+1) n^2: the even part enters y_s(-1) negated
+#pragma unroll
+          for (int f = 0; f < 2; ++f) {
+            dtop[f] = dtop[f] + sd[f];
+            dbot[f] = dbot[f] + scl(sd[f], -sgn);
+          }
+        }
+      }
+      pc1 = pn1;
+      pc0 = pn0;
+      f0c = f0n;
+      f1c = f1n;
+      f2c = f2n;
+      vc = vn;
+      bc = bn;
+      rc = rn;
+    }
+  }
+  wall_amplitudes<T, SLIP>(g, kx, ky, kk, vtop, vbot, dtop, dbot, kaux, kidx, K);
+}
+
+// one thread per wavenumber of the chunk (persistent grid)
+template <typename T, bool SLIP>
+__global__ void __launch_bounds__(kBvpThreads, 3) solve_tab_kernel(Geometry g, const double* __restrict__ band,
+                                                                const T* __restrict__ bandT,
+                                                                const double* __restrict__ fac, int64_t KP,
+                                                                cplx<T>* __restrict__ kbuf, cplx<T>* __restrict__ kaux,
+                                                                cplx<T>* __restrict__ pws, cplx<double>* __restrict__ sw,
+                                                                int kx0, int w) {
+  const int64_t K = (int64_t)g.nkx * g.ny;
+  const int64_t total = (int64_t)w * g.ny;
+  const int slots = gridDim.x * blockDim.x;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = slot; i < total; i += slots)
+    solve_tab<T, SLIP>(g, band, bandT, fac, KP, kbuf, kaux, pws, sw, slots, slot, chunk_kidx(g, i, kx0, w), K);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1403,7 +1777,14 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
     cplx<double>* sw = reinterpret_cast<cplx<double>*>(base);
     double* fr = reinterpret_cast<double*>(base + 3 * N * slots * sizeof(cplx<double>));
     cplx<T>* pws = reinterpret_cast<cplx<T>*>(base + 3 * N * slots * (sizeof(cplx<double>) + sizeof(double)));
-    if (g.slip)
+    const T* bandT = reinterpret_cast<const T*>(p.kt.bandT);
+    if (p.kt.fac && g.slip)
+      solve_tab_kernel<T, true><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, bandT, p.kt.fac, p.kt.KP, kbuf, kaux,
+                                                                    pws, sw, kx0, w);
+    else if (p.kt.fac)
+      solve_tab_kernel<T, false><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, bandT, p.kt.fac, p.kt.KP, kbuf,
+                                                                     kaux, pws, sw, kx0, w);
+    else if (g.slip)
       solve_kernel<T, true><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT),
                                                                  kbuf, kaux, pws, sw, fr, kx0, w);
     else
@@ -1419,6 +1800,22 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
         g, reinterpret_cast<const T*>(p.kt.ict), nullptr, nullptr, reinterpret_cast<const T*>(p.tab.zeta), p.kt.cpad,
         p.kt.bwd_smem > 0, kbuf, kaux, grid, p.zrange, kx0, w);
   }
+}
+
+dps_status bvp_factor_table(Plan& p) {
+  const Geometry& g = p.g;
+  const int64_t KP = (int64_t)g.nkx * (g.ny / 2 + 1);
+  const size_t bytes = (size_t)KP * g.nz * 4 * sizeof(double);
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return DPS_ERR_OOM;
+  }
+  p.kt.fac = reinterpret_cast<double*>(q);
+  p.kt.KP = KP;
+  p.device_bytes += (int64_t)bytes;
+  factor_kernel<<<(unsigned)((KP + 127) / 128), 128>>>(g, p.tab.band, p.kt.fac, KP);
+  return cudaGetLastError() == cudaSuccess ? DPS_OK : DPS_ERR_CUDA;
 }
 
 template size_t bvp_slot_bytes<float>(const Plan&);

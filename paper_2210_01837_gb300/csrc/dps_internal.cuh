@@ -116,6 +116,8 @@ struct KTabs {
   void* cmat;      // [N][N]     forward DCT-I C[n][j] (correction coefficients in the tiled backward)
   void* kbuf;      // [3][N][K]  Chebyshev coefficients per wavenumber (forces, then DP velocity)
   void* kaux;      // [12][K]    wall-correction amplitudes per wavenumber
+  double* fac;     // [N][4][KP] factorisation of the banded systems per (kx, |ky|) (FP64), or null
+  int64_t KP;      // nkx (ny/2 + 1)
   int npad, cpad;
   int fwd_smem, bwd_smem;
 };
@@ -149,6 +151,8 @@ struct Plan {
   alignas(64) unsigned char col_tmap[128];  // CUtensorMap of the grid for the TMA column pass
   int col_tma_rows;     // rows per TMA box of that pass
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
+  int interp_tile;      // interpolation variant: 1 tile gather (where it applies), 0 warp per particle
+  void* ipart;          // partial sums of the tile-gather interpolation [slot][field][max_n] T
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)
   double* stage_in;     // [max_n][9]
@@ -253,6 +257,10 @@ void launch_bins(const Plan& p, int64_t n, cudaStream_t s);
 template <typename T> void launch_spread(const Plan& p, cudaStream_t s);
 template <typename T> int spread_prepare(Plan& p);  // 1 ready, 0 CUDA error, -1 records too large
 template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s);
+// the tile-gather interpolation: fields it sums for this geometry (0: it does not apply) and the
+// values of its partial-sum buffer for max_n particles
+int interp_tile_fields(const Geometry& g);
+size_t interp_tile_values(const Geometry& g, int64_t max_n);
 template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s);
 template <typename T> int fft_col_width(const Plan& p);
@@ -260,6 +268,9 @@ template <typename T> int fft_col_width(const Plan& p);
 template <typename T> void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s);
 template <typename T> int bvp_occupancy_blocks(const Plan& p);
 template <typename T> int bvp_prepare(Plan& p);
+// the factorisation table of the FP64 solve (allocated and filled at plan creation); DPS_ERR_OOM
+// leaves the plan on the factorise-as-you-go solve
+dps_status bvp_factor_table(Plan& p);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
 // column block 2^lcw and variant of the y-FFT pass (reg: 0 shared-memory-staged, 1 register-staged,

@@ -533,6 +533,78 @@ __device__ __forceinline__ void spread_six_list(const Geometry& g, const uint32_
   }
 }
 
+// Bins searched around tile (bx, by) (the rbx x rby neighbourhood, each bin once) and the prefix
+// sums of their particle counts; thread 0 fills them, the caller synchronises.
+struct TileBins {
+  int bins[64];
+  int pref[65];
+  int nb;
+};
+
+__device__ __forceinline__ void tile_bins(const Geometry& g, const int* __restrict__ bin_start, int bx, int by,
+                                          TileBins& tb) {
+  int nb = 0;
+  for (int dy = -g.rby; dy <= g.rby; ++dy) {
+    for (int dx = -g.rbx; dx <= g.rbx; ++dx) {
+      const int b = wrap_idx(by + dy, g.nby) * g.nbx + wrap_idx(bx + dx, g.nbx);
+      bool dup = false;
+      for (int i = 0; i < nb; ++i) dup = dup || (tb.bins[i] == b);
+      if (!dup && nb < 64) tb.bins[nb++] = b;
+    }
+  }
+  tb.nb = nb;
+  int acc = 0;
+  for (int i = 0; i < nb; ++i) {
+    tb.pref[i] = acc;
+    acc += bin_start[tb.bins[i] + 1] - bin_start[tb.bins[i]];
+  }
+  tb.pref[nb] = acc;
+}
+
+// One window of the tile's candidates: the particles of the searched bins (in bin order, each bin's
+// particles in index order) whose support overlaps the tile for some record head; those of rank
+// [win0, win0 + kCandCap) among them go to cand[rank - win0].  Returns the number of candidates of
+// all windows.  Every thread of the block (kSpreadThreads) calls it.
+__device__ __forceinline__ int tile_candidates(const Geometry& g, const uint32_t* __restrict__ rec,
+                                               const int* __restrict__ bin_start, const int* __restrict__ sorted,
+                                               const TileBins& tb, int tx0, int ty0, int tw, int th, int win0,
+                                               int* cand, int* s_warp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rw = g.rec_words;
+  const int nb = tb.nb, total = tb.pref[nb];
+  const int win1 = win0 + kCandCap;
+  int passed = 0;  // passing candidates seen so far (uniform)
+  for (int e0 = 0; e0 < total; e0 += kSpreadThreads) {
+    const int e = e0 + tid;
+    bool pass = false;
+    int j = 0;
+    if (e < total) {
+      int b = 0;
+      while (b + 1 < nb && tb.pref[b + 1] <= e) ++b;
+      j = sorted[bin_start[tb.bins[b]] + (e - tb.pref[b])];
+      const uint32_t* r = rec + (size_t)j * rw;
+      for (int K = 0; K < g.nkernels; ++K) {
+        const int4 hd = reinterpret_cast<const int4*>(r)[K];
+        const int px = (K == 0) ? g.kM.px : g.kD.px;
+        if (hd.w > 0 && cyc_overlap(hd.x, px, tx0, tw, g.nx) && cyc_overlap(hd.y, px, ty0, th, g.ny)) pass = true;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    int woff = 0, btot = 0;
+    for (int w = 0; w < kSpreadThreads / 32; ++w) {
+      if (w < warp) woff += s_warp[w];
+      btot += s_warp[w];
+    }
+    const int rank = passed + woff + __popc(m & ((1u << lane) - 1u));
+    if (pass && rank >= win0 && rank < win1) cand[rank - win0] = j;
+    passed += btot;
+    __syncthreads();
+  }
+  return passed;
+}
+
 // MODE 0: forces only (3 fields); 1: spectral-curl torques (force fields, then torque fields, one
 // pass each); 2: kernel-derivative torques (the force density and the half-curl sources in one pass
 // over the 3 fields); 3: as 2 with coinciding supports (one list, one walk per candidate); 4: as 1
@@ -542,9 +614,7 @@ __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
               const int* __restrict__ sorted, const int* __restrict__ zrange, T* __restrict__ grid) {
   extern __shared__ __align__(16) uint32_t srec[];   // g.stage_cap (<= kStage) staged records
-  __shared__ int s_bins[64];
-  __shared__ int s_pref[65];
-  __shared__ int s_nb;
+  __shared__ TileBins s_tb;
   __shared__ int s_cand[kCandCap];
   __shared__ int s_warp[kSpreadThreads / 32];
   __shared__ int s_wl[kSpreadThreads / 32][2][kStage];  // per-warp row lists (monopole, dipole)
@@ -558,27 +628,9 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   const bool active = (gx < g.nx) && (gy < g.ny);
   const int tw = min(kTileX, g.nx - tx0), th = min(kTileY, g.ny - ty0);
   const int rw = g.rec_words;
-  if (tid == 0) {
-    int nb = 0;
-    for (int dy = -g.rby; dy <= g.rby; ++dy) {
-      for (int dx = -g.rbx; dx <= g.rbx; ++dx) {
-        const int b = wrap_idx(by + dy, g.nby) * g.nbx + wrap_idx(bx + dx, g.nbx);
-        bool dup = false;
-        for (int i = 0; i < nb; ++i) dup = dup || (s_bins[i] == b);
-        if (!dup && nb < 64) s_bins[nb++] = b;
-      }
-    }
-    s_nb = nb;
-    int acc = 0;
-    for (int i = 0; i < nb; ++i) {
-      s_pref[i] = acc;
-      acc += bin_start[s_bins[i] + 1] - bin_start[s_bins[i]];
-    }
-    s_pref[nb] = acc;
-  }
+  if (tid == 0) tile_bins(g, bin_start, bx, by, s_tb);
   __syncthreads();
-  const int nb = s_nb;
-  const int total = s_pref[nb];
+  (void)lane;
   const size_t plane = (size_t)g.ny * 2 * g.pitch;          // T values per z plane (real rows)
   const size_t fstride = plane * g.nz;
   const size_t node = (size_t)gy * 2 * g.pitch + gx;
@@ -596,36 +648,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   // rounds over windows of kCandCap passing candidates (one round unless the tile is crowded)
   for (int round = 0;; ++round) {
     const int win0 = round * kCandCap, win1 = win0 + kCandCap;
-    int passed = 0;  // passing candidates seen so far (uniform)
-    for (int e0 = 0; e0 < total; e0 += kSpreadThreads) {
-      const int e = e0 + tid;
-      bool pass = false;
-      int j = 0;
-      if (e < total) {
-        int b = 0;
-        while (b + 1 < nb && s_pref[b + 1] <= e) ++b;
-        j = sorted[bin_start[s_bins[b]] + (e - s_pref[b])];
-        const uint32_t* r = rec + (size_t)j * rw;
-        for (int K = 0; K < g.nkernels; ++K) {
-          const int4 hd = reinterpret_cast<const int4*>(r)[K];
-          const int px = (K == 0) ? g.kM.px : g.kD.px;
-          if (hd.w > 0 && cyc_overlap(hd.x, px, tx0, tw, g.nx) && cyc_overlap(hd.y, px, ty0, th, g.ny))
-            pass = true;
-        }
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, pass);
-      if (lane == 0) s_warp[warp] = __popc(m);
-      __syncthreads();
-      int woff = 0, btot = 0;
-      for (int w = 0; w < kSpreadThreads / 32; ++w) {
-        if (w < warp) woff += s_warp[w];
-        btot += s_warp[w];
-      }
-      const int rank = passed + woff + __popc(m & ((1u << lane) - 1u));
-      if (pass && rank >= win0 && rank < win1) s_cand[rank - win0] = j;
-      passed += btot;
-      __syncthreads();
-    }
+    const int passed = tile_candidates(g, rec, bin_start, sorted, s_tb, tx0, ty0, tw, th, win0, s_cand, s_warp);
     const int ncand = min(passed, win1) - win0;
     if (ncand <= 0 && round > 0) break;
     constexpr bool TWO = MODE == 1 || MODE == 2;
@@ -712,6 +735,235 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     }
     if (passed <= win1) break;
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Interpolation as a tile gather, the transpose of the spread: a block owns a 32 x 8 tile of node
+// columns and the candidates of the surrounding bins (the spread's lists).  Each thread reads its
+// column of the occupied planes once, ZC planes at a time (coalesced rows, weighted by the
+// Clenshaw-Curtis weights as loaded), and for every listed candidate whose support covers the column
+// adds sum_z u(z) phi_z(z) times phi_x phi_y into that candidate's shared accumulators.  A
+// particle's support overlaps at most sxn x syn tiles; each tile writes its share into the slot
+// ((bx - bx0) mod nbx, (by - by0) mod nby) of a partial-sum buffer [slot][field][n] (bx0, by0: the
+// tiles of the support's first node), and interp_finish_kernel adds the slots of the tiles that
+// overlap the support in a fixed order.  Within a tile the columns' shares meet in shared-memory
+// float atomics, whose order varies: repeated products agree to rounding, not bit for bit (the
+// warp-per-particle kernels below sum in a fixed order).
+// MODE 0: U from fields 0..2 (monopole); MODE 4: U and Omega from fields 0..5 with coinciding
+// supports (spectral-curl torque route, m_M = m_D).
+// ---------------------------------------------------------------------------------------------
+// z sums of one staged candidate over the planes [zb, zb + ZC) of its support: a[f] += sum_z u phi_z
+// (monopole profile for fields 0..2, dipole profile for 3..5)
+template <typename T, int ZC, int NF>
+__device__ __forceinline__ void interp_zsum(const Geometry& g, const uint32_t* r, int zb, const T (&u)[ZC][NF],
+                                            T (&a)[NF]) {
+  const int4 hd = reinterpret_cast<const int4*>(r)[0];
+  if (hd.z + hd.w <= zb || hd.z >= zb + ZC) return;  // no plane of this chunk
+  const int stride = 2 * g.pxc + g.lzc;
+  const T* pm = reinterpret_cast<const T*>(r + 8) + 6;  // monopole phi
+  const T* pd = pm + stride;                            // dipole phi (six fields)
+#pragma unroll
+  for (int zz = 0; zz < ZC; ++zz) {
+    const int iz = zb + zz - hd.z;
+    if (iz >= 0 && iz < hd.w) {
+      const T mz = pm[2 * g.pxc + iz];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) a[f] += u[zz][f] * mz;
+      if (NF == 6) {
+        const T dz = pd[2 * g.pxc + iz];
+#pragma unroll
+        for (int f = 3; f < NF; ++f) a[f] += u[zz][f] * dz;
+      }
+    }
+  }
+}
+
+// a[f] times the candidate's x y weights at column (gx, gy), added to its shared accumulators;
+// false (nothing added) when the column is outside its x support
+template <typename T, int NF>
+__device__ __forceinline__ bool interp_commit(const Geometry& g, const uint32_t* r, int gx, int gy, const T (&a)[NF],
+                                              T* acc) {
+  const int4 hd = reinterpret_cast<const int4*>(r)[0];
+  const int px = g.kM.px;
+  int dx = gx - hd.x;
+  if (dx < 0) dx += g.nx;
+  if (dx >= px) return false;
+  int dy = gy - hd.y;
+  if (dy < 0) dy += g.ny;
+  const T* pm = reinterpret_cast<const T*>(r + 8) + 6;
+  const T mxy = pm[dx] * pm[g.pxc + dy];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) atomicAdd(&acc[f], a[f] * mxy);
+  if (NF == 6) {
+    const T* pd = pm + 2 * g.pxc + g.lzc;
+    const T dxy = pd[dx] * pd[g.pxc + dy];
+#pragma unroll
+    for (int f = 3; f < NF; ++f) atomicAdd(&acc[f], a[f] * dxy);
+  }
+  return true;
+}
+
+// lane-list entries whose z sums a thread keeps in registers across the z chunks (one set of
+// shared atomics per entry at the end instead of one per chunk)
+constexpr int kInterpRegEntries = 6;
+
+template <typename T, int MODE, int ZC>
+__global__ void __launch_bounds__(kSpreadThreads)
+interp_tile_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
+                   const int* __restrict__ sorted, const int* __restrict__ zrange, const T* __restrict__ grid,
+                   const T* __restrict__ wz, T* __restrict__ part, int64_t n, int sxn, int syn,
+                   int* __restrict__ status) {
+  constexpr int NF = MODE == 4 ? 6 : 3;
+  extern __shared__ __align__(16) uint32_t srec[];   // g.stage_cap (<= kStage) staged records
+  __shared__ TileBins s_tb;
+  __shared__ int s_cand[kCandCap];
+  __shared__ int s_warp[kSpreadThreads / 32];
+  __shared__ int s_wl[kSpreadThreads / 32][2][kStage];
+  __shared__ unsigned char s_ll[kSpreadThreads / 32][2][kLaneCap * 32];
+  __shared__ T s_acc[kStage][NF];  // this tile's share of each staged candidate's sums
+  const int clo = zrange[0], chi = zrange[1];
+  if (chi < clo) return;
+  const int bx = blockIdx.x % g.nbx, by = blockIdx.x / g.nbx;
+  const int tx0 = bx * kTileX, ty0 = by * kTileY;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int gx = tx0 + (tid % kTileX), gy = ty0 + (tid / kTileX);
+  const bool active = (gx < g.nx) && (gy < g.ny);
+  const int tw = min(kTileX, g.nx - tx0), th = min(kTileY, g.ny - ty0);
+  const int rw = g.rec_words;
+  if (tid == 0) tile_bins(g, bin_start, bx, by, s_tb);
+  __syncthreads();
+  const size_t plane = (size_t)g.ny * 2 * g.pitch;
+  const size_t fstride = plane * g.nz;
+  const size_t node = (size_t)gy * 2 * g.pitch + gx;
+  int* wl0 = s_wl[warp][0];
+  int* wl1 = s_wl[warp][1];
+  unsigned char* ll0 = s_ll[warp][0];
+  for (int round = 0;; ++round) {
+    const int win0 = round * kCandCap, win1 = win0 + kCandCap;
+    const int passed = tile_candidates(g, rec, bin_start, sorted, s_tb, tx0, ty0, tw, th, win0, s_cand, s_warp);
+    const int ncand = min(passed, win1) - win0;
+    if (ncand <= 0) break;
+    for (int i0 = 0; i0 < ncand; i0 += g.stage_cap) {
+      const int cnt = min(g.stage_cap, ncand - i0);
+      __syncthreads();  // the previous batch has finished with the staged records and sums
+      {
+        const int q = rw >> 2;
+        for (int t = tid; t < cnt * q; t += kSpreadThreads) {
+          const int i = t / q, w = t - i * q;
+          cp_async16(srec + (size_t)i * rw + 4 * w, rec + (size_t)s_cand[i0 + i] * rw + 4 * w);
+        }
+        cp_commit();
+      }
+      for (int t = tid; t < cnt * NF; t += kSpreadThreads) s_acc[t / NF][t % NF] = (T)0;
+      cp_wait_all();
+      __syncthreads();
+      int nl0 = 0, nl1 = 0;
+      build_row_lists<false>(g, srec, cnt, rw, gy, wl0, wl1, nl0, nl1);
+      const int lc0 = build_lane_list<0>(g, srec, wl0, nl0, rw, gx, active, ll0);
+      const bool lanes = !__any_sync(0xffffffffu, lc0 > kLaneCap);
+      __syncwarp();
+      constexpr int E = kInterpRegEntries;
+      T racc[E][NF];  // z sums of the first E lane-list entries, across all chunks
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) racc[e][f] = (T)0;
+      for (int zb = clo; zb <= chi; zb += ZC) {
+        T u[ZC][NF];
+#pragma unroll
+        for (int zz = 0; zz < ZC; ++zz) {
+          const bool in = active && zb + zz <= chi;
+          const T w = in ? wz[zb + zz] : (T)0;
+#pragma unroll
+          for (int f = 0; f < NF; ++f) u[zz][f] = in ? grid[f * fstride + (size_t)(zb + zz) * plane + node] * w : (T)0;
+        }
+        if (!active) continue;
+        if (lanes) {
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            if (e < lc0) interp_zsum<T, ZC, NF>(g, srec + (size_t)list_entry<true>(ll0, e) * rw, zb, u, racc[e]);
+          for (int e = E; e < lc0; ++e) {  // further entries: shared atomics per chunk
+            const int idx = list_entry<true>(ll0, e);
+            T a[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) a[f] = (T)0;
+            interp_zsum<T, ZC, NF>(g, srec + (size_t)idx * rw, zb, u, a);
+            interp_commit<T, NF>(g, srec + (size_t)idx * rw, gx, gy, a, s_acc[idx]);
+          }
+        } else {  // the warp's row list (a lane list overflowed): shared atomics per chunk
+          for (int e = 0; e < nl0; ++e) {
+            const int idx = list_entry<false>(wl0, e);
+            T a[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) a[f] = (T)0;
+            interp_zsum<T, ZC, NF>(g, srec + (size_t)idx * rw, zb, u, a);
+            interp_commit<T, NF>(g, srec + (size_t)idx * rw, gx, gy, a, s_acc[idx]);
+          }
+        }
+      }
+      if (active && lanes) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (e < lc0) {
+            const int idx = list_entry<true>(ll0, e);
+            interp_commit<T, NF>(g, srec + (size_t)idx * rw, gx, gy, racc[e], s_acc[idx]);
+          }
+      }
+      __syncthreads();
+      for (int i = tid; i < cnt; i += kSpreadThreads) {
+        const int4 hd = reinterpret_cast<const int4*>(srec + (size_t)i * rw)[0];
+        int sx = bx - hd.x / kTileX, sy = by - hd.y / kTileY;
+        if (sx < 0) sx += g.nbx;
+        if (sy < 0) sy += g.nby;
+        if (sx >= sxn || sy >= syn) {
+          atomicOr(status, kStatInternal);
+          continue;
+        }
+        const int64_t j = s_cand[i0 + i];
+        T* dst = part + (size_t)(sy * sxn + sx) * NF * n + j;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dst[(size_t)f * n] = s_acc[i][f];
+      }
+    }
+    if (passed <= win1) break;
+    __syncthreads();
+  }
+}
+
+// U (and Omega) of each particle: the partial sums of the tiles that overlap its support (the
+// candidate test of the tile kernels), added in slot order and scaled by h^2.
+template <typename T, int MODE>
+__global__ void interp_finish_kernel(Geometry g, int64_t n, const uint32_t* __restrict__ rec, const T* __restrict__ part,
+                                     int sxn, int syn, double* __restrict__ U, double* __restrict__ W) {
+  constexpr int NF = MODE == 4 ? 6 : 3;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int4 hd = reinterpret_cast<const int4*>(rec + (size_t)j * g.rec_words)[0];
+  T a[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) a[f] = (T)0;
+  if (hd.w > 0) {
+    const int px = g.kM.px;
+    const int bx0 = hd.x / kTileX, by0 = hd.y / kTileY;
+    for (int sy = 0; sy < syn; ++sy) {
+      const int by = (by0 + sy) % g.nby, ty0 = by * kTileY;
+      if (!cyc_overlap(hd.y, px, ty0, min(kTileY, g.ny - ty0), g.ny)) continue;
+      for (int sx = 0; sx < sxn; ++sx) {
+        const int bx = (bx0 + sx) % g.nbx, tx0 = bx * kTileX;
+        if (!cyc_overlap(hd.x, px, tx0, min(kTileX, g.nx - tx0), g.nx)) continue;
+        const T* src = part + (size_t)(sy * sxn + sx) * NF * n + j;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a[f] += src[(size_t)f * n];
+      }
+    }
+  }
+  const double h2 = g.h * g.h;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    double* out = f < 3 ? U + 3 * j + f : W + 3 * j + (f - 3);
+    if (sizeof(T) == 4) *out = widen_bits((float)a[f] * (float)h2);  // float path: widen on the integer pipe
+    else *out = h2 * (double)a[f];
   }
 }
 
@@ -1148,22 +1400,28 @@ size_t spread_smem(const Plan& p) {
 // so that applies can be captured into graphs), and the records staged at a time: kStage, or fewer
 // when that many large records (wide kernels, many z slots, three slabs) would not fit.
 // 1: ready; 0: a CUDA call failed; -1: not even one record fits.
+constexpr int kZCIF6 = 4, kZCID6 = 2, kZCIF3 = 8, kZCID3 = 4;  // z chunk of the tile interpolation
+
 template <typename T>
 int spread_prepare(Plan& p) {
   constexpr int ZC6 = sizeof(T) == 4 ? kZC6F : kZC6D, ZC3 = sizeof(T) == 4 ? kZC3F : kZC3D;
   constexpr int ZCS = sizeof(T) == 4 ? kZCSF : kZCSD;
+  constexpr int ZI6 = sizeof(T) == 4 ? kZCIF6 : kZCID6, ZI3 = sizeof(T) == 4 ? kZCIF3 : kZCID3;
   if (!(allow_smem(spread_kernel<T, 1, ZC6>) && allow_smem(spread_kernel<T, 0, ZC3>) &&
         allow_smem(spread_kernel<T, 2, ZC3>) && allow_smem(spread_kernel<T, 3, ZC3>) &&
-        allow_smem(spread_kernel<T, 4, ZCS>)))
+        allow_smem(spread_kernel<T, 4, ZCS>) && allow_smem(interp_tile_kernel<T, 4, ZI6>) &&
+        allow_smem(interp_tile_kernel<T, 0, ZI3>)))
     return 0;
   int dev = 0, optin = 0;
-  cudaFuncAttributes fa;  // the three modes declare the same static shared arrays
+  cudaFuncAttributes fa, fi;  // the spread modes declare the same static shared arrays; the tile
+                              // interpolation adds its sums
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-      cudaFuncGetAttributes(&fa, spread_kernel<T, 1, ZC6>) != cudaSuccess)
+      cudaFuncGetAttributes(&fa, spread_kernel<T, 1, ZC6>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fi, interp_tile_kernel<T, 4, ZI6>) != cudaSuccess)
     return 0;
   const long rb = (long)p.g.rec_words * (long)sizeof(uint32_t);
-  const long cap = ((long)optin - (long)fa.sharedSizeBytes) / rb;
+  const long cap = ((long)optin - (long)std::max(fa.sharedSizeBytes, fi.sharedSizeBytes)) / rb;
   p.g.stage_cap = (int)std::min<long>(kStage, cap);
   // records built in shared memory by blocks of 128, 64 or 32 threads when that many fit in
   // 96 KB (two blocks per SM), else written directly
@@ -1193,6 +1451,29 @@ void launch_spread(const Plan& p, cudaStream_t s) {
     spread_kernel<T, 0, ZC3><<<blocks, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange, grid);
 }
 
+// the tile-gather interpolation applies: forces only, or spectral-curl torques with coinciding
+// supports; returns the fields it sums (0: not applicable)
+int interp_tile_fields(const Geometry& g) {
+  if (g.torque_deriv) return 0;
+  if (g.spectral_curl) return g.kM.px == g.kD.px ? 6 : 0;
+  return 3;
+}
+
+// tiles a support can overlap in x and y (a partial last tile can add one) and the partial-sum
+// buffer of the tile-gather interpolation, in values of the transform precision
+void interp_tile_slots(const Geometry& g, int& sxn, int& syn) {
+  sxn = std::min(g.nbx, (g.kM.px - 1) / kTileX + 2 + ((g.nx % kTileX) ? 1 : 0));
+  syn = std::min(g.nby, (g.kM.px - 1) / kTileY + 2 + ((g.ny % kTileY) ? 1 : 0));
+}
+
+size_t interp_tile_values(const Geometry& g, int64_t max_n) {
+  const int nf = interp_tile_fields(g);
+  if (nf == 0) return 0;
+  int sxn, syn;
+  interp_tile_slots(g, sxn, syn);
+  return (size_t)sxn * syn * nf * (size_t)std::max<int64_t>(max_n, 1);
+}
+
 template <typename T>
 void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t s) {
   if (n <= 0) return;
@@ -1200,6 +1481,27 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
   const unsigned blocks = (unsigned)((n * 32 + threads - 1) / threads);
   const T* grid = reinterpret_cast<const T*>(p.grid);
   const T* wz = reinterpret_cast<const T*>(p.tab.wz);
+  const int nf = interp_tile_fields(p.g);
+  if (p.interp_tile && nf > 0 && p.ipart) {
+    int sxn, syn;
+    interp_tile_slots(p.g, sxn, syn);
+    T* part = reinterpret_cast<T*>(p.ipart);
+    const unsigned tiles = (unsigned)(p.g.nbx * p.g.nby);
+    const size_t sm = spread_smem<T>(p);
+    const unsigned fb = (unsigned)((n + 255) / 256);
+    if (nf == 6) {
+      constexpr int ZI = sizeof(T) == 4 ? kZCIF6 : kZCID6;
+      interp_tile_kernel<T, 4, ZI><<<tiles, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                                     grid, wz, part, n, sxn, syn, p.status);
+      interp_finish_kernel<T, 4><<<fb, 256, 0, s>>>(p.g, n, p.records, part, sxn, syn, U, W);
+    } else {
+      constexpr int ZI = sizeof(T) == 4 ? kZCIF3 : kZCID3;
+      interp_tile_kernel<T, 0, ZI><<<tiles, kSpreadThreads, sm, s>>>(p.g, p.records, p.bin_start, p.sorted, p.zrange,
+                                                                     grid, wz, part, n, sxn, syn, p.status);
+      interp_finish_kernel<T, 0><<<fb, 256, 0, s>>>(p.g, n, p.records, part, sxn, syn, U, W);
+    }
+    return;
+  }
   // lanes per x run: the narrowest group that holds a support row
   if (p.g.torque_deriv) {
     const bool fused = p.g.kM.px == p.g.kD.px;  // equal m: identical supports (alpha = m h / 2)

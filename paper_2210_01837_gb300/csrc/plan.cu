@@ -165,7 +165,8 @@ void free_plan(Plan* p) {
   void* ptrs[] = {p->tab.zc, p->tab.wz, p->tab.zeta, p->tab.band, p->tab.twx, p->tab.twy, p->tab.tsy,
                   p->kt.ct, p->kt.dct,
                   p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.cmat, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
-                  p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out};
+                  p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out, p->ipart,
+                  p->kt.fac};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -325,6 +326,22 @@ dps_status allocate(Plan* p) {
   if (!alloc(&p->kt.kbuf, 3 * (size_t)g.nz * (size_t)K * sizeof(cplx<T>))) return DPS_ERR_OOM;
   if (!alloc(&p->kt.kaux, 12 * (size_t)K * sizeof(cplx<T>))) return DPS_ERR_OOM;
   if (!bvp_prepare<T>(*p)) return DPS_ERR_INVALID_ARG;
+  // factorisation table of the FP64 solve (per (kx, |ky|), filled on the legacy stream): without
+  // the memory for it the solve factorises as it goes; DPS_SOLVE_TABLE=0 chooses that by hand
+  {
+    const char* e = getenv("DPS_SOLVE_TABLE");
+    if (!(e && atoi(e) == 0)) {
+      const dps_status ft = bvp_factor_table(*p);
+      if (ft == DPS_ERR_CUDA) return ft;
+    }
+  }
+  // the tile-gather interpolation's partial sums (where it applies); the warp-per-particle gather
+  // stays the default (on the 1M-roller workload 9.7 against 8.5 ms), the autotuner tries both
+  if (const size_t iv = interp_tile_values(g, p->max_n)) {
+    if (!alloc(&p->ipart, iv * sizeof(T))) return DPS_ERR_OOM;
+  }
+  p->interp_tile = 0;
+  if (const char* e = getenv("DPS_INTERP_TILE")) p->interp_tile = p->ipart && atoi(e) != 0;
   if (!alloc((void**)&p->stage_in, nmax * 9 * sizeof(double))) return DPS_ERR_OOM;
   if (!alloc((void**)&p->stage_out, nmax * 6 * sizeof(double))) return DPS_ERR_OOM;
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
@@ -594,12 +611,23 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   out->h = p->g.h;
   out->alpha_M = p->g.kM.alpha;
   out->alpha_D = p->g.with_torque ? p->g.kD.alpha : 0.0;
-  out->launches_per_apply = 8 + 5 * p->nchunks;
+  // init, records, 3 binning, spread, x pass, 5 per column chunk, x pass, interpolation (+ its
+  // finishing kernel for the tile gather)
+  out->launches_per_apply = 9 + 5 * p->nchunks + ((p->interp_tile && p->ipart) ? 1 : 0);
   out->nchunks = p->nchunks;
   out->fft_col_width = 1 << p->col_lcw;
   out->fft_register_rows = p->fft_reg[0];
   out->fft_register_cols = p->fft_reg[1];
   out->solve_blocks = p->bvp_blocks;
+  out->interp_variant = p->interp_tile;
+  return DPS_OK;
+}
+
+dps_status dpstokes_plan_set_interp(dps_plan_t plan, int32_t variant) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || (variant != 0 && variant != 1)) return DPS_ERR_INVALID_ARG;
+  if (variant == 1 && !p->ipart) return DPS_ERR_INVALID_ARG;
+  p->interp_tile = variant;
   return DPS_OK;
 }
 
@@ -665,6 +693,14 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
     if (st == DPS_OK && better(t)) { best = t; best_j = j; }
   }
   dps::set_chunks(*p, best_j);
+  // 4. interpolation variant (tile gather or warp per particle), where both apply
+  if (p->ipart && st == DPS_OK) {
+    const int inc = p->interp_tile;
+    p->interp_tile = 1 - inc;
+    st = measure(&t);
+    if (!(st == DPS_OK && better(t))) p->interp_tile = inc;
+    else best = t;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != DPS_OK) return st;

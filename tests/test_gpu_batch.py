@@ -2,7 +2,8 @@
 
 Each result of a batch or of the server must be the product of dpstokes_apply for that problem,
 within the alone-vs-in-mix bars (1e-12 relative L2 in FP64, 1e-6 mixed).  (Bins are sorted by
-particle index, so in practice the results repeat bit for bit.)"""
+particle index, so the spread repeats bit for bit; the tile-gather interpolation adds shares with
+shared-memory float atomics, whose order can vary.)"""
 
 import numpy as np
 import pytest

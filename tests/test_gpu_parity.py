@@ -147,3 +147,20 @@ def test_crowded_bin_matches_oracle(precision):
     U, W = gpu_mobility(params, pos, F, T, precision)
     assert rel_l2(U, U_ref) <= TOL[precision]
     assert rel_l2(W, W_ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["bottom_wall", "slit", "free"])
+def test_factorise_as_you_go_solve_matches_oracle(mode, precision, monkeypatch):
+    """The FP64 solve without its plan-time factorisation table (the path a plan takes when the
+    table does not fit in memory; DPS_SOLVE_TABLE=0 chooses it by hand)."""
+    params = small_params(mode, nx=54, ny=40, nz=33, torque=True)
+    pos, F, T = random_particles(params, 30, seed=61)
+    U_ref, W_ref = mobility(oracle_params(params), pos, F, T)
+    monkeypatch.setenv("DPS_SOLVE_TABLE", "0")
+    plan = binding.Plan.from_params(params, with_torque=True, precision=precision, max_n=len(pos))
+    monkeypatch.delenv("DPS_SOLVE_TABLE")
+    U, W = gpu_mobility(params, pos, F, T, precision, plan=plan)
+    plan.close()
+    assert rel_l2(U, U_ref) <= TOL[precision]
+    assert rel_l2(W, W_ref) <= TOL[precision]
