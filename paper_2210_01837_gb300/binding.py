@@ -49,7 +49,7 @@ class dps_plan_info(ctypes.Structure):
                 ("alpha_M", ctypes.c_double), ("alpha_D", ctypes.c_double), ("launches_per_apply", ctypes.c_int32),
                 ("nchunks", ctypes.c_int32), ("fft_col_width", ctypes.c_int32), ("solve_blocks", ctypes.c_int32),
                 ("fft_register_rows", ctypes.c_int32), ("fft_register_cols", ctypes.c_int32),
-                ("interp_variant", ctypes.c_int32)]
+                ("interp_variant", ctypes.c_int32), ("cheb_tensor_cores", ctypes.c_int32)]
 
 
 class dps_request(ctypes.Structure):

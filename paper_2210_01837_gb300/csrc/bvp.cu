@@ -1724,7 +1724,9 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
   cplx<T>* kbuf = reinterpret_cast<cplx<T>*>(p.kt.kbuf);
   cplx<T>* kaux = reinterpret_cast<cplx<T>*>(p.kt.kaux);
   const LaneCfg fc = fwd_lane_cfg<T>(g);
-  if (part == 0 && fc.threads > 0) {
+  if (part == 0 && sizeof(T) == 4 && p.cheb_tc) {
+    launch_cheb_fwd_tc(p, kx0, w, s);
+  } else if (part == 0 && fc.threads > 0) {
     const unsigned lb = (unsigned)((total + kLaneK - 1) / kLaneK);
     constexpr int PG = fwd_pg<T>(), PW = fwd_pg_wide<T>();
     const T* ct = reinterpret_cast<const T*>(p.kt.ct);

@@ -152,6 +152,8 @@ struct Plan {
   int col_tma_rows;     // rows per TMA box of that pass
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
   int interp_tile;      // interpolation variant: 1 tile gather (where it applies), 0 warp per particle
+  int cheb_tc;          // forward Chebyshev transform on the tensor cores (tcgen05, mixed precision)
+  int cheb_tc_grid;     // persistent blocks of that kernel
   void* ipart;          // partial sums of the tile-gather interpolation [slot][field][max_n] T
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)
@@ -271,6 +273,11 @@ template <typename T> int bvp_prepare(Plan& p);
 // the factorisation table of the FP64 solve (allocated and filled at plan creation); DPS_ERR_OOM
 // leaves the plan on the factorise-as-you-go solve
 dps_status bvp_factor_table(Plan& p);
+// the tensor-core forward Chebyshev transform: readiness (sets cheb_tc where it applies; 0 on a CUDA
+// error), its launcher, and its accumulator width (nz rounded up to 16)
+int cheb_tc_prepare(Plan& p);
+void launch_cheb_fwd_tc(const Plan& p, int kx0, int w, cudaStream_t s);
+int cheb_tc_np(const Geometry& g);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
 // column block 2^lcw and variant of the y-FFT pass (reg: 0 shared-memory-staged, 1 register-staged,

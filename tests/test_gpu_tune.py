@@ -11,7 +11,10 @@ from gpu_helpers import rel_l2, small_params, to_dev
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,bar", [("mixed", 1e-6), ("fp64", 1e-12)])
+# mixed: besides launch shapes the autotuner picks the interpolation variant (tile gather or warp
+# per particle), a different summation of the same float products; 3e-6, as for the FFT variants
+# below, is still well inside the mixed bar of 1e-5
+@pytest.mark.parametrize("precision,bar", [("mixed", 3e-6), ("fp64", 1e-12)])
 def test_autotune_keeps_the_product(precision, bar):
     import torch
     params = small_params("slit", nx=192, ny=160, nz=33, zmax=6.0)

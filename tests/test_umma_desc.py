@@ -1,0 +1,98 @@
+"""Host checks of the tensor-core operand descriptor encoders (csrc/umma_desc.h), compiled with the
+host C++ compiler: every field sits at the bit position of the PTX ISA's tcgen05 descriptor tables
+(shared-memory matrix descriptor; instruction descriptor of .kind::tf32), and the K-major core-matrix
+layout used for the operand tiles is a bijection onto the tile with 128-byte core matrices."""
+
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "paper_2210_01837_gb300", "csrc", "umma_desc.h")
+
+PROGRAM = r"""
+#include <stdio.h>
+#include <initializer_list>
+#include "umma_desc.h"
+int main() {
+  using namespace dps::umma;
+  const unsigned a[][3] = {{0x0, 16, 16}, {0x1230, 2048, 128}, {0x3FFF0, 1280, 128}, {0x4560, 0x3FFF0, 0x10}};
+  for (auto& v : a) printf("S %u %u %u %llu\n", v[0], v[1], v[2], (unsigned long long)smem_desc(v[0], v[1], v[2]));
+  const unsigned mn[][2] = {{128, 80}, {128, 112}, {128, 48}, {64, 16}, {128, 256}};
+  for (auto& v : mn) printf("I %u %u %u\n", v[0], v[1], idesc_tf32(v[0], v[1]));
+  for (unsigned rows : {128u, 80u}) {
+    for (unsigned r = 0; r < rows; ++r)
+      for (unsigned k = 0; k < 8; ++k) printf("O %u %u %u %u\n", rows, r, k, kmajor_offset(r, k));
+  }
+  printf("L %u %u\n", kLbo, kSbo);
+  return 0;
+}
+"""
+
+
+def _field(v, lo, width):
+    return (v >> lo) & ((1 << width) - 1)
+
+
+@pytest.fixture(scope="module")
+def encodings(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    d = tmp_path_factory.mktemp("umma")
+    src = d / "t.cpp"
+    src.write_text(PROGRAM)
+    exe = d / "t"
+    subprocess.run([cxx, "-std=c++17", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    rows = [l.split() for l in out if l]
+    return rows
+
+
+def test_shared_memory_descriptor_fields(encodings):
+    for r in (r for r in encodings if r[0] == "S"):
+        addr, lbo, sbo, d = map(int, r[1:])
+        assert _field(d, 0, 14) == (addr >> 4) & 0x3FFF
+        assert _field(d, 14, 2) == 0
+        assert _field(d, 16, 14) == (lbo >> 4) & 0x3FFF
+        assert _field(d, 30, 2) == 0
+        assert _field(d, 32, 14) == (sbo >> 4) & 0x3FFF
+        assert _field(d, 46, 2) == 1          # tcgen05 descriptor version
+        assert _field(d, 48, 1) == 0
+        assert _field(d, 49, 3) == 0          # base offset
+        assert _field(d, 52, 1) == 0          # relative leading-dimension offsets
+        assert _field(d, 53, 8) == 0
+        assert _field(d, 61, 3) == 0          # no swizzle
+
+
+def test_instruction_descriptor_fields(encodings):
+    for r in (r for r in encodings if r[0] == "I"):
+        m, n, d = map(int, r[1:])
+        assert _field(d, 0, 4) == 0           # dense, no saturation
+        assert _field(d, 4, 2) == 1           # D: f32
+        assert _field(d, 6, 1) == 0
+        assert _field(d, 7, 3) == 2           # A: tf32
+        assert _field(d, 10, 3) == 2          # B: tf32
+        assert _field(d, 13, 4) == 0          # no negation, both K-major
+        assert _field(d, 17, 6) == n >> 3
+        assert _field(d, 23, 1) == 0
+        assert _field(d, 24, 5) == m >> 4
+        assert _field(d, 29, 3) == 0
+
+
+def test_kmajor_layout_is_a_bijection_of_core_matrices(encodings):
+    lbo, sbo = next(tuple(map(int, r[1:])) for r in encodings if r[0] == "L")
+    for rows in (128, 80):
+        offs = {(int(r[2]), int(r[3])): int(r[4]) for r in encodings if r[0] == "O" and int(r[1]) == rows}
+        assert len(offs) == rows * 8
+        vals = sorted(offs.values())
+        assert vals == list(range(0, rows * 32, 4))       # every 4-byte slot of the tile once
+        for (row, k), o in offs.items():
+            # core matrix (8 rows x 16 bytes, 128 contiguous bytes) at the descriptor's strides:
+            # the leading-dimension offset along K, the stride-dimension offset along the rows
+            base = (k // 4) * lbo + (row // 8) * sbo
+            assert o == base + (row % 8) * 16 + (k % 4) * 4
+        # the descriptor's addresses stay inside the tile even with the two offsets exchanged
+        assert (rows // 8 - 1) * lbo + 1 * sbo + 127 < rows * 32
