@@ -181,8 +181,10 @@ typedef struct {
                                2 register-staged with cp.async prefetch, 3 with TMA prefetch   */
   int32_t interp_variant;   /* interpolation (step 8): 1 tile gather (forces only, or spectral-curl
                                torques with m_M = m_D), 0 a warp per particle                    */
-  int32_t cheb_tensor_cores; /* 1: the forward Chebyshev transform runs on the tensor cores
-                               (tcgen05, tf32 three-product split; mixed precision, nz <= 128)   */
+  int32_t cheb_tensor_cores; /* Chebyshev transforms on the tensor cores (tcgen05, tf32
+                               three-product split; mixed precision, nz <= 128): bit 0 the
+                               forward transform, bit 1 the backward transform (spectral-curl
+                               torques, nz <= 96)                                               */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 

@@ -1757,6 +1757,8 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
         fwd_lane_kernel<T, PW, false><<<lb, fc.threads, fc.smem, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0,
                                                                       w, fc.cz);
     }
+  } else if (part == 2 && sizeof(T) == 4 && p.cheb_tc_bwd) {
+    launch_cheb_bwd_tc(p, kx0, w, s);
   } else if (part == 2 && bwd_lane_smem<T>(g) > 0) {
     const int corr = g.mode == DPS_FREE ? 0 : (g.mode == DPS_SLIT ? 2 : 1);
     if (g.spectral_curl) {

@@ -1,26 +1,41 @@
-// Forward Chebyshev transform (step 2 of Sec. III.D, z part, with the half-curl source of the
-// torque route) on the 5th-generation tensor cores.
+// Chebyshev transforms of the per-wavenumber stage on the 5th-generation tensor cores (mixed
+// precision): the forward DCT-I with the half-curl source of the torque route (step 2 of
+// Sec. III.D, z part) and the backward step (steps 6-7, z part): inverse DCT-I of the DP
+// velocity, the wall correction at the nodes, and the half-curl of Eq. 11.
 //
-// Per wavenumber k the transform is a contraction over the occupied planes c:
-//   out_o[n] = sum_c C[n][c] a_o(c) + DC[n][c] b_o(c),   o = 0, 1, 2,
-// with a_o = f_o + (1/2)(i k x tau)_o, b_x = -tau_y/2, b_y = tau_x/2, b_z = 0 (C the DCT-I,
-// DC = (2/H) D C).  Real and imaginary parts contract independently, so a block takes 64
-// wavenumbers as the M = 128 rows of a GEMM (row 2j + p: wavenumber j, part p), the planes as K
-// and the Chebyshev index n as N (padded to Np, a multiple of 16):
-//   D_o[128 x Np] += A_o[128 x 8] B[8 x Np] per chunk of 8 planes (tcgen05.mma .kind::tf32, the
-// accumulators of the three outputs side by side in tensor memory).  Float accuracy from tf32
-// operands by the three-product split: x = x_hi + x_lo with x_hi = tf32(x), x_lo = tf32(x - x_hi),
-// and A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo is 2^-22 relative).
+// Both are contractions per wavenumber over one index, with real tables, applied to the real and
+// imaginary parts independently.  A block takes 64 wavenumbers as the M = 128 rows of a GEMM (row
+// 2j + p: wavenumber j, part p) and runs tcgen05.mma .kind::tf32 over K steps of 8, accumulating
+// in tensor memory.  Float accuracy from tf32 operands by the three-product split
+// x = x_hi + x_lo, x_hi = tf32(x), x_lo = tf32(x - x_hi):  A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (the dropped A_lo B_lo is 2^-22 relative).
 //
-// A block is persistent over 64-wavenumber tiles.  The CUDA cores build each plane chunk's
-// operands (grid values with the curl terms; table rows of C and DC), split them, and store them
-// in the K-major core-matrix layout into one of two shared-memory stages; one thread issues the
-// chunk's MMAs and commits them to that stage's mbarrier, and the other threads go on building the
-// next chunk in the other stage.  After the last chunk the accumulators are read with tcgen05.ld
-// and written to kbuf[o][n][k] (a warp's 32 lanes hold 16 wavenumbers' real and imaginary parts,
-// contiguous in kbuf).  Every mbarrier wait is bounded (about a second); on expiry the block
-// records DPS_ERR_TIMEOUT in the status word, waits once more (bounded) for its issued MMAs,
-// frees its tensor memory and leaves.
+//   forward   K = occupied planes c, N = Chebyshev index n (nz rounded up to 16):
+//             out_o = C a_o + DC b_o, a_o = f_o + (1/2)(i k x tau)_o, b_x = -tau_y/2, b_y = tau_x/2
+//             (DC = (2/H) D C); three accumulators.
+//   backward  N = occupied planes (their count rounded up to 16), K = the Chebyshev index n, then
+//             (with walls) the node index j:  u_f = IC y_f (f = u, v, w),
+//             du = ICD y_u + SD corr_u, dv = ICD y_v + SD corr_v, where corr_f(z_j) is the wall
+//             correction at node j (bottom family (cE + cG zeta) e^{-k zeta}, top family
+//             (tE + tG xi) e^{-k xi}) and SD = ICD C its spectral derivative (reading B2); five
+//             accumulators.  The epilogue adds corr_f at the output nodes, forms
+//             omega = (1/2)(i ky w - dv, du - i kx w, i kx v - i ky u) and scales by 1/(Nx Ny).
+//
+// The block is persistent over 64-wavenumber tiles and warp-specialised:
+//   warps 0-7   producers: load the K step's operands from global memory (one step ahead in
+//               registers), split them and store them in the K-major core-matrix layout of one of
+//               kStages shared-memory stages; arrive on the stage's `full` barrier;
+//   warp 12     MMA issuer: waits for a full stage (and, at a tile's first step, for a free
+//               accumulator set), issues the step's MMAs, commits them to the stage's `empty`
+//               barrier and, after a tile's last step, to the accumulator set's `full` barrier;
+//   warps 8-11  epilogue: wait for a full accumulator set, read it with tcgen05.ld (warp w reads
+//               TMEM lanes 32 (w mod 4) ...), write the results, arrive on the set's `empty`
+//               barrier.
+// Two accumulator sets when their columns fit twice in 512, so a tile's epilogue overlaps the
+// next tile's MMAs.  Every barrier wait is bounded (about a second); on expiry the waiting thread
+// records DPS_ERR_TIMEOUT in the status word and raises a block-wide stop flag, every role leaves
+// its loop, the MMA warp waits once more (bounded) for its last commit, and the tensor memory is
+// freed before the block exits.
 #include <math.h>
 
 #include <algorithm>
@@ -31,11 +46,15 @@
 namespace dps {
 namespace {
 
-constexpr int kTcThreads = 256;
 constexpr int kTcRows = 128;   // MMA M: 64 wavenumbers x (re, im)
-constexpr int kTcK = 8;        // planes per K step (8 tf32 = 32 bytes per operand row)
+constexpr int kTcK = 8;        // K step (8 tf32 = 32 bytes per operand row)
 constexpr int kTcWave = 64;    // wavenumbers per tile
-constexpr long long kWaitCycles = 1ll << 31;  // bounded waits: about one second at 2 GHz
+constexpr int kProducers = 256;
+constexpr int kTcThreads = 416;  // 8 producer warps, 4 epilogue warps, 1 MMA warp
+constexpr int kEpiWarp0 = 8, kMmaWarp = 12;
+constexpr int kStages = 4;
+constexpr uint32_t kATile = kTcRows * kTcK * 4;  // 4096 bytes: one A operand of one K step
+constexpr long long kWaitCycles = 1ll << 31;     // bounded waits: about one second at 2 GHz
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -45,35 +64,45 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// four K-consecutive values of one operand row, split into the hi tile and the lo tile that
+// follows it `lo_delta` bytes later
+__device__ __forceinline__ void split_store(unsigned char* hi_tile, uint32_t lo_delta, uint32_t off, float a, float b,
+                                            float c, float d) {
+  const float4 h = make_float4(tf32_rna(a), tf32_rna(b), tf32_rna(c), tf32_rna(d));
+  const float4 l = make_float4(tf32_rna(a - h.x), tf32_rna(b - h.y), tf32_rna(c - h.z), tf32_rna(d - h.w));
+  *reinterpret_cast<float4*>(hi_tile + off) = h;
+  *reinterpret_cast<float4*>(hi_tile + lo_delta + off) = l;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
 }
 
-// wait until the phase of the given parity has completed; false after kWaitCycles
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// wait for the completion of the phase of the given parity; false after kWaitCycles or once the
+// block's stop flag is raised
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* stop) {
   const long long t0 = clock64();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(saddr(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_test(bar, parity)) return true;
+    if (*stop) return false;
     if (clock64() - t0 > kWaitCycles) return false;
   }
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(dst)), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -89,6 +118,16 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       : "memory");
 }
 
+// D += A_hi B_hi + A_hi B_lo + A_lo B_hi (A's lo tile follows its hi tile by one A tile, B's by
+// b_lo_delta)
+__device__ __forceinline__ void mma3(uint32_t d, uint32_t a_hi, uint32_t b_hi, uint32_t b_lo_delta, uint32_t idesc,
+                                     uint32_t accumulate) {
+  using namespace umma;
+  mma_tf32(d, smem_desc(a_hi, kLbo, kSbo), smem_desc(b_hi, kLbo, kSbo), idesc, accumulate);
+  mma_tf32(d, smem_desc(a_hi, kLbo, kSbo), smem_desc(b_hi + b_lo_delta, kLbo, kSbo), idesc, 1u);
+  mma_tf32(d, smem_desc(a_hi + kATile, kLbo, kSbo), smem_desc(b_hi, kLbo, kSbo), idesc, 1u);
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
                : "memory");
@@ -97,325 +136,604 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 // 8 consecutive 32-bit columns of this thread's tensor-memory lane
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(taddr)
-      : "memory");
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
-  hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-  lo = make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z), tf32_rna(v.w - hi.w));
+// wavenumber of tile position j: stored column (-1 past the end), kbuf index, k/2 components, |k|
+struct TileK {
+  int col;
+  int kid;
+  float hkx, hky, kk;
+};
+
+__device__ __forceinline__ TileK tile_k(const Geometry& g, int64_t tile, int j, int kx0, int w) {
+  TileK t;
+  t.col = -1;
+  t.kid = 0;
+  t.hkx = t.hky = t.kk = 0.f;
+  const int64_t it = tile * kTcWave + j;
+  if (it < (int64_t)w * g.ny) {
+    const unsigned ii = (unsigned)it;
+    const int kyi = (int)(ii / (unsigned)w);
+    const int kxi = kx0 + (int)(ii - (unsigned)kyi * (unsigned)w);
+    const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
+    t.col = kyi * g.pitch + kxi;
+    t.kid = kyi * g.nkx + kxi;
+    t.hkx = (float)(M_PI * (double)kxi / g.Lx);
+    t.hky = (float)(M_PI * (double)nyv / g.Ly);
+    t.kk = 2.0f * sqrtf(t.hkx * t.hkx + t.hky * t.hky);
+  }
+  return t;
 }
 
-// shared-memory stage: A tiles [NQ][hi, lo][128 rows x 8], B tiles [NT][hi, lo][Np rows x 8]
-struct TcStage {
-  static constexpr uint32_t kATile = kTcRows * kTcK * 4;  // 4096 bytes
-  __host__ __device__ static uint32_t bytes(int nq, int nt, int np) {
-    return (uint32_t)(2 * nq * kATile + 2 * nt * np * kTcK * 4);
+__device__ __forceinline__ bool is_nyquist(const Geometry& g, int kid) {
+  const int kyi = kid / g.nkx, kxi = kid - kyi * g.nkx;
+  return ((g.nx % 2 == 0) && kxi == g.nx / 2) || ((g.ny % 2 == 0) && kyi == g.ny / 2);
+}
+
+// ---------------------------------------------------------------------------------------------
+// forward transform
+// ---------------------------------------------------------------------------------------------
+template <bool CURL>
+struct FwdSpec {
+  static constexpr bool kForward = true;
+  static constexpr int NQ = CURL ? 5 : 3;  // A operands: a0, b0, a1, b1, a2 (forces only: a0, a1, a2)
+  static constexpr int NT = CURL ? 2 : 1;  // B operands: C (and DC)
+  static constexpr int NACC = 3;
+  static constexpr int NR = CURL ? 4 : 2;  // grid fields a producer thread reads per plane
+  struct Args {
+    const float* ct;   // [c][npad] C[n][c]
+    const float* dct;  // [c][npad] DC[n][c]
+    int npad;
+    const cplx<float>* grid;
+    cplx<float>* kbuf;
+  };
+  __host__ __device__ static uint32_t stage_bytes(int nmax) { return (uint32_t)(2 * NQ * kATile + 2 * NT * nmax * kTcK * 4); }
+  struct Raw {
+    cplx<float> v[4][NR];
+  };
+  // K steps of a tile: the occupied planes in groups of 8
+  __device__ static int nks(const Geometry&, int clo, int chi) { return chi >= clo ? (chi - clo + kTcK) / kTcK : 0; }
+  // producer thread (j, grp, half): wavenumber j, planes 4 grp .. 4 grp + 3 of the step; half 0
+  // reads fx, fy, ty, tz (forces only: fx, fy), half 1 reads fz, tx, ty (fz)
+  __device__ static void load(const Geometry& g, const Args& a, int clo, int chi, int ks, const TileK& tk, Raw& r) {
+    const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
+    const size_t plane = (size_t)g.ny * g.pitch, fstride = (size_t)g.nz * plane;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int c = clo + ks * kTcK + 4 * grp + cc;
+      const bool in = tk.col >= 0 && c <= chi;
+      const cplx<float>* p = a.grid + (size_t)(in ? c : 0) * plane + (in ? tk.col : 0);
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const int f = CURL ? (half == 0 ? (q < 2 ? q : q + 2) : (q < 3 ? q + 2 : 4)) : (half == 0 ? q : 2);
+        const bool want = in && (half == 0 || q < (CURL ? 3 : 1));
+        r.v[cc][q] = want ? p[(size_t)f * fstride] : mk<float>(0.f, 0.f);
+      }
+    }
+  }
+  __device__ static void store(const Geometry& g, const Args& a, int clo, int chi, int ks, const TileK& tk,
+                               const Raw& r, unsigned char* st, int np) {
+    const int tid = threadIdx.x, j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;
+    const float hkx = tk.hkx, hky = tk.hky;
+    float re[3][4], im[3][4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      if (CURL) {
+        if (half == 0) {
+          const cplx<float> fx = r.v[cc][0], fy = r.v[cc][1], ty = r.v[cc][2], tz = r.v[cc][3];
+          // a0 = fx + i ky/2 tz, b0 = -ty/2, a1 = fy - i kx/2 tz
+          re[0][cc] = fx.x - hky * tz.y;  im[0][cc] = fx.y + hky * tz.x;
+          re[1][cc] = -0.5f * ty.x;       im[1][cc] = -0.5f * ty.y;
+          re[2][cc] = fy.x + hkx * tz.y;  im[2][cc] = fy.y - hkx * tz.x;
+        } else {
+          const cplx<float> fz = r.v[cc][0], tx = r.v[cc][1], ty = r.v[cc][2];
+          // b1 = tx/2, a2 = fz + i (kx/2 ty - ky/2 tx)
+          const float sx = hkx * ty.x - hky * tx.x, sy = hkx * ty.y - hky * tx.y;
+          re[0][cc] = 0.5f * tx.x;  im[0][cc] = 0.5f * tx.y;
+          re[1][cc] = fz.x - sy;    im[1][cc] = fz.y + sx;
+          re[2][cc] = 0.f;          im[2][cc] = 0.f;
+        }
+      } else {
+        re[0][cc] = r.v[cc][0].x;  im[0][cc] = r.v[cc][0].y;
+        re[1][cc] = r.v[cc][1].x;  im[1][cc] = r.v[cc][1].y;
+        re[2][cc] = 0.f;           im[2][cc] = 0.f;
+      }
+    }
+    const int nb = CURL ? (half == 0 ? 3 : 2) : (half == 0 ? 2 : 1);
+    const int first = half == 0 ? 0 : (CURL ? 3 : 2);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (u >= nb) break;
+      unsigned char* ahi = st + (size_t)(2 * (first + u)) * kATile;
+      split_store(ahi, kATile, umma::kmajor_offset((uint32_t)(2 * j), (uint32_t)(4 * grp)), re[u][0], re[u][1],
+                  re[u][2], re[u][3]);
+      split_store(ahi, kATile, umma::kmajor_offset((uint32_t)(2 * j + 1), (uint32_t)(4 * grp)), im[u][0], im[u][1],
+                  im[u][2], im[u][3]);
+    }
+    // B: C[n][c] (and DC[n][c]) for the step's planes, n < np
+    const uint32_t btile = (uint32_t)np * kTcK * 4;
+    for (int item = tid; item < np * 2 * NT; item += kProducers) {
+      const int n = item % np, gq = (item / np) & 1, tab = item / (2 * np);
+      const float* src = tab == 0 ? a.ct : a.dct;
+      float x[4];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = clo + ks * kTcK + 4 * gq + cc;
+        x[cc] = (n < g.nz && c <= chi) ? src[(size_t)c * a.npad + n] : 0.f;
+      }
+      unsigned char* bt = st + (size_t)2 * NQ * kATile + (size_t)(2 * tab) * btile;
+      split_store(bt, btile, umma::kmajor_offset((uint32_t)n, (uint32_t)(4 * gq)), x[0], x[1], x[2], x[3]);
+    }
+  }
+  __device__ static void mma(const Geometry&, uint32_t sbase, uint32_t tacc, int ks, int np, uint32_t idesc) {
+    const uint32_t btile = (uint32_t)np * kTcK * 4;
+    const uint32_t bbase = sbase + 2 * NQ * kATile;
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      const uint32_t d = tacc + (uint32_t)(o * np);
+      const int qa = CURL ? 2 * o : o;
+      mma3(d, sbase + (uint32_t)(2 * qa) * kATile, bbase, btile, idesc, ks > 0 ? 1u : 0u);
+      if (CURL && o < 2) mma3(d, sbase + (uint32_t)(2 * (2 * o + 1)) * kATile, bbase + 2 * btile, btile, idesc, 1u);
+    }
+  }
+  // epilogue thread: TMEM lane `row` (wavenumber row >> 1, part row & 1); out_o[n] -> kbuf (zeros
+  // when no plane is occupied)
+  __device__ static void epilogue(const Geometry& g, const Args& a, uint32_t tlane, int row, const TileK& tk, int np,
+                                  int, int, bool any) {
+    const int64_t K = (int64_t)g.nkx * g.ny;
+    const int N = g.nz, part = row & 1;
+    float* kb = reinterpret_cast<float*>(a.kbuf) + 2 * (size_t)tk.kid + part;
+    const size_t nstride = 2 * (size_t)K;
+    for (int o = 0; o < 3; ++o) {
+      for (int n0 = 0; n0 < np; n0 += 8) {
+        float v[8];
+        if (any) tmem_ld8(tlane + (uint32_t)(o * np + n0), v);
+        if (tk.col < 0) continue;
+        float* dst = kb + ((size_t)o * N + n0) * nstride;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (n0 + t < N) dst[(size_t)t * nstride] = any ? v[t] : 0.f;
+      }
+    }
   }
 };
 
-// thread i of a chunk (columns [kx0, kx0 + w), every ky) -> wavenumber index kyi * nkx + kxi
-__device__ __forceinline__ int64_t tc_kidx(const Geometry& g, int64_t i, int kx0, int w) {
-  const unsigned ii = (unsigned)i;
-  const int kyi = (int)(ii / (unsigned)w);
-  return (int64_t)kyi * g.nkx + kx0 + (int)(ii - (unsigned)kyi * (unsigned)w);
-}
-
-template <bool CURL>
-__global__ void __launch_bounds__(kTcThreads, 2) cheb_fwd_tc_kernel(Geometry g, const float* __restrict__ ct,
-                                                                    const float* __restrict__ dct, int npad,
-                                                                    const cplx<float>* __restrict__ grid,
-                                                                    cplx<float>* __restrict__ kbuf,
-                                                                    const int* __restrict__ zrange, int kx0, int w,
-                                                                    int np, int tcols, int* __restrict__ status) {
-  constexpr int NQ = CURL ? 5 : 3;  // A operands per chunk: a0, b0, a1, b1, a2 (forces only: a0, a1, a2)
-  constexpr int NT = CURL ? 2 : 1;  // B operands: C (and DC)
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ uint32_t s_tmem;
-  __shared__ int s_col[kTcWave], s_kid[kTcWave];
-  __shared__ float s_hkx[kTcWave], s_hky[kTcWave];
-  __shared__ int s_fail;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int N = g.nz;
-  const int clo = zrange[0], chi = zrange[1];
-  const int64_t K = (int64_t)g.nkx * g.ny;
-  const int64_t total = (int64_t)w * g.ny;
-  const int64_t ntiles = (total + kTcWave - 1) / kTcWave;
-  const uint32_t stage_bytes = TcStage::bytes(NQ, NT, np);
-  const uint32_t btile = (uint32_t)np * kTcK * 4;
-  unsigned char* stage0 = smraw;
-  const size_t plane = (size_t)g.ny * g.pitch;
-  const size_t fstride = (size_t)g.nz * plane;
-  const uint32_t idesc = umma::idesc_tf32(kTcRows, (uint32_t)np);
-  if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    s_fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) tmem_alloc(&s_tmem, (uint32_t)tcols);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = s_tmem;
-  unsigned uses[2] = {0, 0};  // completed-or-issued commits per stage (uniform across the block)
-  const int nchunks = chi >= clo ? (chi - clo + kTcK) / kTcK : 0;
-  bool ok = true;
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    if (tid < kTcWave) {
-      const int64_t it = tile * kTcWave + tid;
-      int col = -1, kid = 0;
-      float hx = 0.f, hy = 0.f;
-      if (it < total) {
-        const int64_t kidx = tc_kidx(g, it, kx0, w);
-        const unsigned ku = (unsigned)kidx;
-        const int kyi = (int)(ku / (unsigned)g.nkx), kxi = (int)(ku - (unsigned)kyi * (unsigned)g.nkx);
-        const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
-        col = kyi * g.pitch + kxi;
-        kid = (int)kidx;
-        hx = (float)(M_PI * (double)kxi / g.Lx);
-        hy = (float)(M_PI * (double)nyv / g.Ly);
-      }
-      s_col[tid] = col;
-      s_kid[tid] = kid;
-      s_hkx[tid] = hx;
-      s_hky[tid] = hy;
-    }
-    __syncthreads();
-    // thread (j, grp, half): wavenumber j, planes 4 grp .. 4 grp + 3 of each chunk; half 0 builds
-    // a0, b0, a1 (forces only: a0, a1), half 1 builds b1, a2 (forces only: a2).  The grid values of
-    // chunk q + 1 are loaded into registers before chunk q's operands are stored, so their latency
-    // overlaps the barrier and the MMA issue.
-    const int j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;
-    const int jcol = s_col[j];
-    const float hkx = s_hkx[j], hky = s_hky[j];
-    constexpr int NR = CURL ? 4 : 2;  // grid fields read per plane by this thread
-    cplx<float> raw[4][NR];
-    auto load = [&](int q) {
-      const int c0 = clo + q * kTcK;
+// ---------------------------------------------------------------------------------------------
+// backward transform
+// ---------------------------------------------------------------------------------------------
+template <int CORR>  // 0 no wall, 1 bottom wall, 2 both walls
+struct BwdSpec {
+  static constexpr bool kForward = false;
+  static constexpr int NQ = 3;  // A operands of a coefficient step: y_u, y_v, y_w (node step: corr_u, corr_v)
+  static constexpr int NT = 2;  // B operands: IC, ICD (node step: SD)
+  static constexpr int NACC = 5;
+  struct Args {
+    const float* ict;   // [n][cpad] IC[c][n]
+    const float* icdt;  // [n][cpad] ICD[c][n]
+    const float* sdt;   // [j][cpad] SD[c][j]
+    int cpad;
+    const float* zeta;  // [nz] z_c - zmin
+    const cplx<float>* kbuf;
+    const cplx<float>* kaux;
+    cplx<float>* grid;
+  };
+  __host__ __device__ static uint32_t stage_bytes(int nmax) { return (uint32_t)(2 * NQ * kATile + 2 * NT * nmax * kTcK * 4); }
+  struct Raw {
+    cplx<float> v[4][2];
+  };
+  __device__ static int ncoef(const Geometry& g) { return (g.nz + kTcK - 1) / kTcK; }
+  __device__ static int nks(const Geometry& g, int, int) { return ncoef(g) * (CORR ? 2 : 1); }
+  // producer thread (j, grp, half): wavenumber j, indices 4 grp .. 4 grp + 3 of the step.
+  // coefficient step: half 0 reads y_u, y_v, half 1 y_w; node step: the amplitudes cE, cG (tE, tG)
+  // of corr_u (half 0) or corr_v (half 1)
+  __device__ static void load(const Geometry& g, const Args& a, int, int, int ks, const TileK& tk, Raw& r) {
+    const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int64_t K = (int64_t)g.nkx * g.ny;
+    const int N = g.nz;
+    const bool ok = tk.col >= 0;
+    if (ks < ncoef(g)) {
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
-        const int c = c0 + 4 * grp + cc;
-        const bool in = jcol >= 0 && c <= chi;
-        const cplx<float>* p = grid + (size_t)c * plane + (in ? jcol : 0);
+        const int n = ks * kTcK + 4 * grp + cc;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          // half 0 reads fx, fy, ty, tz (forces only: fx, fy); half 1 reads fz, tx, ty (fz)
-          const int f = CURL ? (half == 0 ? (r < 2 ? r : r + 2) : (r < 3 ? r + 2 : 4)) : (half == 0 ? r : 2);
-          raw[cc][r] = in && (half == 0 || r < (CURL ? 3 : 1)) ? p[(size_t)f * fstride] : mk<float>(0.f, 0.f);
+        for (int q = 0; q < 2; ++q) {
+          const int f = half == 0 ? q : 2;
+          const bool want = ok && n < N && (half == 0 || q == 0);
+          r.v[cc][q] = want ? a.kbuf[((size_t)f * N + n) * K + tk.kid] : mk<float>(0.f, 0.f);
         }
       }
-    };
-    if (nchunks > 0) load(0);
-    for (int q = 0; q < nchunks; ++q) {
-      const int sb = q & 1;
-      unsigned char* st = stage0 + sb * stage_bytes;
-      // the MMAs that last read this stage must have completed
-      if (uses[sb] > 0 && !mbar_wait(&s_bar[sb], (uses[sb] - 1) & 1)) {
-        if (tid == 0) s_fail = 1;
+    } else {
+      const int f = half;  // u or v
+      const bool amp = ok && tk.kid > 0 && !is_nyquist(g, tk.kid);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool want = amp && (q < 2 || CORR == 2);
+        r.v[q][0] = want ? a.kaux[(size_t)(4 * f + q) * K + tk.kid] : mk<float>(0.f, 0.f);
+        r.v[q][1] = mk<float>(0.f, 0.f);
       }
-      __syncthreads();
-      if (s_fail) { ok = false; break; }
-      const int c0 = clo + q * kTcK;
-      {
-        float re[3][4], im[3][4];
+    }
+  }
+  __device__ static void store(const Geometry& g, const Args& a, int clo, int chi, int ks, const TileK& tk,
+                               const Raw& r, unsigned char* st, int nq) {
+    const int tid = threadIdx.x, j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int N = g.nz;
+    const uint32_t orow = umma::kmajor_offset((uint32_t)(2 * j), (uint32_t)(4 * grp));
+    const uint32_t orow1 = umma::kmajor_offset((uint32_t)(2 * j + 1), (uint32_t)(4 * grp));
+    const int nc = ncoef(g);
+    const uint32_t btile = (uint32_t)nq * kTcK * 4;
+    unsigned char* bbase = st + (size_t)2 * NQ * kATile;
+    if (ks < nc) {
+      // A: y_u, y_v (half 0) or y_w (half 1): operands 0, 1, 2
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          if (CURL) {
-            if (half == 0) {
-              const cplx<float> fx = raw[cc][0], fy = raw[cc][1], ty = raw[cc][2], tz = raw[cc][3];
-              // a0 = fx + i ky/2 tz, b0 = -ty/2, a1 = fy - i kx/2 tz
-              re[0][cc] = fx.x - hky * tz.y;  im[0][cc] = fx.y + hky * tz.x;
-              re[1][cc] = -0.5f * ty.x;       im[1][cc] = -0.5f * ty.y;
-              re[2][cc] = fy.x + hkx * tz.y;  im[2][cc] = fy.y - hkx * tz.x;
-            } else {
-              const cplx<float> fz = raw[cc][0], tx = raw[cc][1], ty = raw[cc][2];
-              // b1 = tx/2, a2 = fz + i (kx/2 ty - ky/2 tx)
-              const float sx = hkx * ty.x - hky * tx.x, sy = hkx * ty.y - hky * tx.y;
-              re[0][cc] = 0.5f * tx.x;        im[0][cc] = 0.5f * tx.y;
-              re[1][cc] = fz.x - sy;          im[1][cc] = fz.y + sx;
-              re[2][cc] = 0.f;                im[2][cc] = 0.f;
-            }
-          } else {
-            re[0][cc] = raw[cc][0].x;  im[0][cc] = raw[cc][0].y;
-            re[1][cc] = raw[cc][1].x;  im[1][cc] = raw[cc][1].y;
-            re[2][cc] = 0.f;           im[2][cc] = 0.f;
-          }
-        }
-        if (q + 1 < nchunks) load(q + 1);
-        // operand index of each built quantity
-        const int nb = CURL ? (half == 0 ? 3 : 2) : (half == 0 ? 2 : 1);
-        const int first = half == 0 ? 0 : (CURL ? 3 : 2);
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          if (u >= nb) break;
-          const int qi = first + u;
-          unsigned char* ahi = st + (size_t)(2 * qi) * TcStage::kATile;
-          unsigned char* alo = ahi + TcStage::kATile;
-#pragma unroll
-          for (int pp = 0; pp < 2; ++pp) {
-            const uint32_t off = umma::kmajor_offset((uint32_t)(2 * j + pp), (uint32_t)(4 * grp));
-            const float(&x)[4] = pp ? im[u] : re[u];
-            float4 hi, lo;
-            split4(make_float4(x[0], x[1], x[2], x[3]), hi, lo);
-            *reinterpret_cast<float4*>(ahi + off) = hi;
-            *reinterpret_cast<float4*>(alo + off) = lo;
-          }
-        }
+      for (int q = 0; q < 2; ++q) {
+        if (half == 1 && q == 1) break;
+        unsigned char* ahi = st + (size_t)(2 * (half == 0 ? q : 2)) * kATile;
+        split_store(ahi, kATile, orow, r.v[0][q].x, r.v[1][q].x, r.v[2][q].x, r.v[3][q].x);
+        split_store(ahi, kATile, orow1, r.v[0][q].y, r.v[1][q].y, r.v[2][q].y, r.v[3][q].y);
       }
-      // ---- B: thread (n, group, table): C[n][c] (and DC[n][c]) for four planes
-      for (int item = tid; item < np * 2 * NT; item += kTcThreads) {
-        const int n = item % np, grp = (item / np) & 1, tab = item / (2 * np);
-        const float* src = tab == 0 ? ct : dct;
+      // B: IC[c][n], ICD[c][n] for the occupied planes c = clo + p, p < nq
+      for (int item = tid; item < nq * 2 * 2; item += kProducers) {
+        const int p = item % nq, gq = (item / nq) & 1, tab = item / (2 * nq);
+        const float* src = tab == 0 ? a.ict : a.icdt;
+        const int c = clo + p;
         float x[4];
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          const int c = c0 + 4 * grp + cc;
-          x[cc] = (n < N && c <= chi) ? src[(size_t)c * npad + n] : 0.f;
+          const int n = ks * kTcK + 4 * gq + cc;
+          x[cc] = (c <= chi && n < N) ? src[(size_t)n * a.cpad + c] : 0.f;
         }
-        float4 hi, lo;
-        split4(make_float4(x[0], x[1], x[2], x[3]), hi, lo);
-        unsigned char* bt = st + (size_t)2 * NQ * TcStage::kATile + (size_t)(2 * tab) * btile;
-        const uint32_t off = umma::kmajor_offset((uint32_t)n, (uint32_t)(4 * grp));
-        *reinterpret_cast<float4*>(bt + off) = hi;
-        *reinterpret_cast<float4*>(bt + btile + off) = lo;
+        split_store(bbase + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)p, (uint32_t)(4 * gq)),
+                    x[0], x[1], x[2], x[3]);
       }
-      proxy_fence();  // the generic-proxy stores above, before the tensor core's reads
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t sbase = saddr(st);
-        const uint32_t bbase = sbase + 2 * NQ * TcStage::kATile;
-        auto adesc = [&](int qi, int lohi) {
-          return umma::smem_desc(sbase + (uint32_t)(2 * qi + lohi) * TcStage::kATile, umma::kLbo, umma::kSbo);
-        };
-        auto bdesc = [&](int tab, int lohi) {
-          return umma::smem_desc(bbase + (uint32_t)(2 * tab + lohi) * btile, umma::kLbo, umma::kSbo);
-        };
-        // D_o += A_hi B_hi + A_hi B_lo + A_lo B_hi, for the a terms with C and the b terms with DC
-        for (int o = 0; o < 3; ++o) {
-          const uint32_t d = tmem + (uint32_t)(o * np);
-          const int qa = CURL ? 2 * o : o;             // a_o operand
-          const bool hasb = CURL && o < 2;
-          const int qb = 2 * o + 1;                    // b_o operand
-          uint32_t acc = q > 0 ? 1u : 0u;
-          mma_tf32(d, adesc(qa, 0), bdesc(0, 0), idesc, acc);
-          mma_tf32(d, adesc(qa, 0), bdesc(0, 1), idesc, 1u);
-          mma_tf32(d, adesc(qa, 1), bdesc(0, 0), idesc, 1u);
-          if (hasb) {
-            mma_tf32(d, adesc(qb, 0), bdesc(1, 0), idesc, 1u);
-            mma_tf32(d, adesc(qb, 0), bdesc(1, 1), idesc, 1u);
-            mma_tf32(d, adesc(qb, 1), bdesc(1, 0), idesc, 1u);
-          }
-        }
-        mma_commit(&s_bar[sb]);
-      }
-      ++uses[sb];
-    }
-    if (!ok) break;
-    // all of the tile's MMAs: the last commit covers every earlier one of the issuing thread
-    if (nchunks > 0) {
-      const int sb = (nchunks - 1) & 1;
-      if (!mbar_wait(&s_bar[sb], (uses[sb] - 1) & 1)) {
-        if (tid == 0) s_fail = 1;
-      }
-    }
-    __syncthreads();
-    if (s_fail) { ok = false; break; }
-    tc_fence_after();
-    // ---- epilogue: warp w reads its lane quarter (rows 32 (w & 3) ...), half of the 3 Np columns:
-    // half 0 from (o, n) = (0, 0), half 1 from (1, Np/2) (Np and 3 Np/2 are multiples of 8)
-    {
-      const int sp = warp & 3, hf = warp >> 2;
-      const int row = 32 * sp + lane;
-      const int jr = row >> 1, part = row & 1;
-      const int col = s_col[jr];
-      const size_t kid = (size_t)s_kid[jr];
-      const int ncol = 3 * np, cbeg = hf * (ncol / 2), cend = hf ? ncol : ncol / 2;
-      float* kb = reinterpret_cast<float*>(kbuf) + 2 * kid + part;
-      const size_t nstride = 2 * (size_t)K;  // floats from coefficient n to n + 1
-      int o = hf, n = hf ? np / 2 : 0;
-      for (int c8 = cbeg; c8 < cend; c8 += 8) {
-        float v[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)c8, v);
-        if (col >= 0) {
-          float* dst = kb + ((size_t)o * N + n) * nstride;
+    } else {
+      // A: corr_u (half 0) or corr_v (half 1) at the step's nodes: operands 0, 1
+      const int j0 = (ks - nc) * kTcK + 4 * grp;
+      float cr[4], ci[4];
 #pragma unroll
-          for (int t = 0; t < 8; ++t)
-            if (n + t < N) dst[(size_t)t * nstride] = nchunks > 0 ? v[t] : 0.f;
+      for (int cc = 0; cc < 4; ++cc) {
+        const int jn = j0 + cc;
+        cr[cc] = ci[cc] = 0.f;
+        if (jn < N) {
+          const float z = a.zeta[jn];
+          const float eb = expf(-tk.kk * z);
+          float vx = (r.v[0][0].x + r.v[1][0].x * z) * eb, vy = (r.v[0][0].y + r.v[1][0].y * z) * eb;
+          if (CORR == 2) {
+            const float xi = a.zeta[N - 1 - jn];
+            const float et = expf(-tk.kk * xi);
+            vx += (r.v[2][0].x + r.v[3][0].x * xi) * et;
+            vy += (r.v[2][0].y + r.v[3][0].y * xi) * et;
+          }
+          cr[cc] = vx;
+          ci[cc] = vy;
         }
-        n += 8;
-        if (n >= np) { n -= np; ++o; }
+      }
+      unsigned char* ahi = st + (size_t)(2 * half) * kATile;
+      split_store(ahi, kATile, orow, cr[0], cr[1], cr[2], cr[3]);
+      split_store(ahi, kATile, orow1, ci[0], ci[1], ci[2], ci[3]);
+      // B: SD[c][j] for the occupied planes
+      for (int item = tid; item < nq * 2; item += kProducers) {
+        const int p = item % nq, gq = item / nq;
+        const int c = clo + p;
+        float x[4];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int jn = (ks - nc) * kTcK + 4 * gq + cc;
+          x[cc] = (c <= chi && jn < N) ? a.sdt[(size_t)jn * a.cpad + c] : 0.f;
+        }
+        split_store(bbase, btile, umma::kmajor_offset((uint32_t)p, (uint32_t)(4 * gq)), x[0], x[1], x[2], x[3]);
       }
     }
-    tc_fence_before();
-    __syncthreads();  // the accumulators are read before the next tile's first MMA overwrites them
   }
-  if (!ok) {
-    if (tid == 0) atomicOr(status, kStatTimeout);
-    // one more bounded wait for the MMAs already issued, before the tensor memory is freed
-    for (int sb = 0; sb < 2; ++sb)
-      if (uses[sb] > 0) mbar_wait(&s_bar[sb], (uses[sb] - 1) & 1);
+  __device__ static void mma(const Geometry& g, uint32_t sbase, uint32_t tacc, int ks, int nq, uint32_t idesc) {
+    const uint32_t btile = (uint32_t)nq * kTcK * 4;
+    const uint32_t bbase = sbase + 2 * NQ * kATile;
+    const uint32_t acc = ks > 0 ? 1u : 0u;
+    const uint32_t au = sbase, av = sbase + 2 * kATile, aw = sbase + 4 * kATile;
+    if (ks < ncoef(g)) {
+      mma3(tacc + 0 * nq, au, bbase, btile, idesc, acc);              // u  = IC y_u
+      mma3(tacc + 1 * nq, av, bbase, btile, idesc, acc);              // v  = IC y_v
+      mma3(tacc + 2 * nq, aw, bbase, btile, idesc, acc);              // w  = IC y_w
+      mma3(tacc + 3 * nq, au, bbase + 2 * btile, btile, idesc, acc);  // du = ICD y_u
+      mma3(tacc + 4 * nq, av, bbase + 2 * btile, btile, idesc, acc);  // dv = ICD y_v
+    } else {
+      mma3(tacc + 3 * nq, au, bbase, btile, idesc, 1u);               // du += SD corr_u
+      mma3(tacc + 4 * nq, av, bbase, btile, idesc, 1u);               // dv += SD corr_v
+    }
+  }
+  // epilogue thread: TMEM lane `row` = (wavenumber row >> 1, part row & 1); lanes 2j and 2j + 1 pair
+  // up for the products with i
+  __device__ static void epilogue(const Geometry& g, const Args& a, uint32_t tlane, int row, const TileK& tk, int nq,
+                                  int clo, int chi, bool) {
+    const int64_t K = (int64_t)g.nkx * g.ny;
+    const int part = row & 1;
+    const int N = g.nz;
+    const bool nyq = tk.col >= 0 && is_nyquist(g, tk.kid);
+    const bool corr = CORR > 0 && tk.col >= 0 && tk.kid > 0 && !nyq;
+    // this part of the correction amplitudes of u, v, w: bottom (E, G), top (E, G)
+    float am[3][4];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float v = 0.f;
+        if (corr && (q < 2 || CORR == 2)) {
+          const cplx<float> c = a.kaux[(size_t)(4 * f + q) * K + tk.kid];
+          v = part ? c.y : c.x;
+        }
+        am[f][q] = v;
+      }
+    const float scale = (float)(1.0 / ((double)g.nx * (double)g.ny));
+    const size_t plane = (size_t)g.ny * g.pitch, fstride = (size_t)g.nz * plane;
+    float* gr = reinterpret_cast<float*>(a.grid);
+    const float sgn = part ? 1.f : -1.f;  // (i x) of this part: re -> -x.im, im -> +x.re
+    for (int p0 = 0; p0 < nq; p0 += 8) {
+      float u[8], v[8], w[8], du[8], dv[8];
+      tmem_ld8(tlane + (uint32_t)(0 * nq + p0), u);
+      tmem_ld8(tlane + (uint32_t)(1 * nq + p0), v);
+      tmem_ld8(tlane + (uint32_t)(2 * nq + p0), w);
+      tmem_ld8(tlane + (uint32_t)(3 * nq + p0), du);
+      tmem_ld8(tlane + (uint32_t)(4 * nq + p0), dv);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int c = clo + p0 + t;
+        if (corr && c <= chi) {
+          const float z = a.zeta[c];
+          const float eb = expf(-tk.kk * z);
+          float et = 0.f, xi = 0.f;
+          if (CORR == 2) {
+            xi = a.zeta[N - 1 - c];
+            et = expf(-tk.kk * xi);
+          }
+          u[t] += (am[0][0] + am[0][1] * z) * eb + (CORR == 2 ? (am[0][2] + am[0][3] * xi) * et : 0.f);
+          v[t] += (am[1][0] + am[1][1] * z) * eb + (CORR == 2 ? (am[1][2] + am[1][3] * xi) * et : 0.f);
+          w[t] += (am[2][0] + am[2][1] * z) * eb + (CORR == 2 ? (am[2][2] + am[2][3] * xi) * et : 0.f);
+        }
+        // the other part of u, v, w (partner lane)
+        const float uo = __shfl_xor_sync(0xffffffffu, u[t], 1);
+        const float vo = __shfl_xor_sync(0xffffffffu, v[t], 1);
+        const float wo = __shfl_xor_sync(0xffffffffu, w[t], 1);
+        // omega = 1/2 (i ky w - dv, du - i kx w, i kx v - i ky u); (i x) of this part = sgn x(other)
+        const float iw = sgn * wo, iv = sgn * vo, iu = sgn * uo;
+        const float ox = tk.hky * iw - 0.5f * dv[t];
+        const float oy = 0.5f * du[t] - tk.hkx * iw;
+        const float oz = tk.hkx * iv - tk.hky * iu;
+        if (tk.col >= 0 && c <= chi) {
+          const size_t o0 = ((size_t)c * plane + tk.col) * 2 + part;
+          const float s = nyq ? 0.f : scale;
+          gr[o0] = u[t] * s;
+          gr[o0 + 2 * fstride] = v[t] * s;
+          gr[o0 + 4 * fstride] = w[t] * s;
+          gr[o0 + 6 * fstride] = ox * s;
+          gr[o0 + 8 * fstride] = oy * s;
+          gr[o0 + 10 * fstride] = oz * s;
+        }
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// the pipeline
+// ---------------------------------------------------------------------------------------------
+struct TcShared {
+  uint64_t full[kStages], empty[kStages];
+  uint64_t acc_full[2], acc_empty[2];
+  uint32_t tmem;
+  int stop;
+};
+
+template <typename Spec>
+__global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, typename Spec::Args a,
+                                                                const int* __restrict__ zrange, int kx0, int w,
+                                                                int* __restrict__ status) {
+  constexpr bool FWD = Spec::kForward;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ TcShared sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int clo = zrange[0], chi = zrange[1];
+  const int64_t ntiles = ((int64_t)w * g.ny + kTcWave - 1) / kTcWave;
+  // GEMM N: forward the Chebyshev index (nz rounded up to 16); backward the occupied planes
+  const int nocc = chi >= clo ? chi - clo + 1 : 0;
+  const int nmax = (g.nz + 15) / 16 * 16;  // the stage layout is sized for this
+  const int nn = FWD ? nmax : max(16, (nocc + 15) / 16 * 16);
+  const int cols = Spec::NACC * nn;
+  const int nbuf = 2 * cols <= 512 ? 2 : 1;
+  const int need = nbuf * cols;
+  const uint32_t tcols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+  const uint32_t stage_bytes = Spec::stage_bytes(nmax);
+  const int nks = Spec::nks(g, clo, chi);
+  const uint32_t idesc = umma::idesc_tf32(kTcRows, (uint32_t)nn);
+  volatile int* stop = &sh.stop;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sh.full[s], kProducers);
+      mbar_init(&sh.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.acc_full[b], 1);
+      mbar_init(&sh.acc_empty[b], 128);
+    }
+    sh.stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&sh.tmem)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_free(tmem, (uint32_t)tcols);
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+  auto fail = [&]() {
+    if (!*stop) {
+      sh.stop = 1;
+      atomicOr(status, kStatTimeout);
+    }
+  };
+  if (warp < kEpiWarp0) {
+    // ---- producers ------------------------------------------------------------------------
+    unsigned it = 0;  // K steps produced so far
+    typename Spec::Raw raw;
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles && nks > 0) {
+      TileK tk = tile_k(g, tile, tid & 63, kx0, w);
+      Spec::load(g, a, clo, chi, 0, tk, raw);
+      for (;;) {
+        for (int ks = 0; ks < nks; ++ks, ++it) {
+          const int s = it % kStages;
+          if (!mbar_wait(&sh.empty[s], ((it / kStages) & 1) ^ 1, stop)) { fail(); break; }
+          unsigned char* st = smraw + (size_t)s * stage_bytes;
+          const typename Spec::Raw cur = raw;
+          // the next step's loads, issued before this step's stores
+          const bool last = ks + 1 == nks;
+          const int64_t ntile = last ? tile + gridDim.x : tile;
+          const TileK ntk = last ? tile_k(g, ntile, tid & 63, kx0, w) : tk;
+          if (ntile < ntiles) Spec::load(g, a, clo, chi, last ? 0 : ks + 1, ntk, raw);
+          Spec::store(g, a, clo, chi, ks, tk, cur, st, nn);
+          proxy_fence();
+          mbar_arrive(&sh.full[s]);
+          if (last) tk = ntk;
+        }
+        if (*stop) break;
+        tile += gridDim.x;
+        if (tile >= ntiles) break;
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---- MMA issuer -----------------------------------------------------------------------
+    unsigned it = 0, t = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && nks > 0 && !*stop; tile += gridDim.x, ++t) {
+      const int b = nbuf == 2 ? (int)(t & 1) : 0;
+      const unsigned use = nbuf == 2 ? t >> 1 : t;  // earlier uses of this accumulator set
+      if (!mbar_wait(&sh.acc_empty[b], (use & 1) ^ 1, stop)) { fail(); break; }
+      tc_fence_after();
+      const uint32_t tacc = tmem + (uint32_t)(b * cols);
+      bool ok = true;
+      for (int ks = 0; ks < nks; ++ks, ++it) {
+        const int s = it % kStages;
+        if (!mbar_wait(&sh.full[s], (it / kStages) & 1, stop)) { fail(); ok = false; break; }
+        tc_fence_after();
+        if (lane == 0) {
+          Spec::mma(g, saddr(smraw + (size_t)s * stage_bytes), tacc, ks, nn, idesc);
+          mma_commit(&sh.empty[s]);  // the stage is free once these MMAs have read it
+          if (ks + 1 == nks) mma_commit(&sh.acc_full[b]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+    }
+    // a stop: wait (bounded) for the MMAs already issued before the tensor memory is freed
+    if (*stop && it > 0) {
+      const unsigned last = it - 1;
+      const long long t0 = clock64();
+      while (!mbar_test(&sh.empty[last % kStages], (last / kStages) & 1) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {
+    // ---- epilogue ---------------------------------------------------------------------------
+    const int row = 32 * (warp & 3) + lane;
+    const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    unsigned t = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+      const TileK tk = tile_k(g, tile, row >> 1, kx0, w);
+      if (nks == 0) {  // forward with no occupied plane: zero coefficients
+        Spec::epilogue(g, a, tlane, row, tk, nn, clo, chi, false);
+        continue;
+      }
+      const int b = nbuf == 2 ? (int)(t & 1) : 0;
+      const unsigned use = nbuf == 2 ? t >> 1 : t;
+      if (!mbar_wait(&sh.acc_full[b], use & 1, stop)) { fail(); break; }
+      tc_fence_after();
+      Spec::epilogue(g, a, tlane + (uint32_t)(b * cols), row, tk, nn, clo, chi, true);
+      tc_fence_before();
+      mbar_arrive(&sh.acc_empty[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+  }
+}
+
+template <typename Spec>
+size_t tc_smem(const Geometry& g) {
+  return (size_t)kStages * Spec::stage_bytes((g.nz + 15) / 16 * 16) + 1024;
+}
+
+template <typename Spec>
+void launch_tc(const Plan& p, const typename Spec::Args& a, int kx0, int w, cudaStream_t s) {
+  const int64_t tiles = ((int64_t)w * p.g.ny + kTcWave - 1) / kTcWave;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, p.cheb_tc_grid));
+  cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, p.zrange, kx0, w, p.status);
 }
 
 }  // namespace
 
-// columns of the tensor-core forward transform's accumulators: three outputs of Np columns
 int cheb_tc_np(const Geometry& g) { return (g.nz + 15) / 16 * 16; }
-
-static int tc_tcols(int np) {
-  const int need = 3 * np;
-  return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
-}
-
-static size_t tc_smem(const Geometry& g, int np) {
-  const bool curl = g.spectral_curl != 0;
-  return 2 * (size_t)TcStage::bytes(curl ? 5 : 3, curl ? 2 : 1, np) + 1024;  // two stages, 1 KB alignment slack
-}
 
 int cheb_tc_prepare(Plan& p) {
   p.cheb_tc = 0;
-  const int np = cheb_tc_np(p.g);
-  if (p.precision != DPS_MIXED || p.g.nz > 128 || tc_tcols(np) > 512) return 1;
-  if (!allow_smem(cheb_fwd_tc_kernel<true>) || !allow_smem(cheb_fwd_tc_kernel<false>)) return 0;
-  int dev = 0, sms = 0, major = 0, minor = 0;
+  p.cheb_tc_bwd = 0;
+  if (p.precision != DPS_MIXED || p.g.nz > 128) return 1;
+  int dev = 0, sms = 0, major = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (major != 10) return 1;  // tcgen05: Blackwell data-centre parts only
-  p.cheb_tc_grid = sms * (tc_tcols(np) <= 256 ? 2 : 1);
-  p.cheb_tc = 1;
+  if (!allow_smem(cheb_tc_kernel<FwdSpec<true>>) || !allow_smem(cheb_tc_kernel<FwdSpec<false>>) ||
+      !allow_smem(cheb_tc_kernel<BwdSpec<0>>) || !allow_smem(cheb_tc_kernel<BwdSpec<1>>) ||
+      !allow_smem(cheb_tc_kernel<BwdSpec<2>>))
+    return 0;
+  p.cheb_tc_grid = sms;
+  if (tc_smem<FwdSpec<true>>(p.g) + 1024 <= (size_t)optin) p.cheb_tc = 1;
+  // backward: five accumulators of up to nz (rounded up to 16) columns must fit 512 columns
+  if (p.g.spectral_curl && 5 * cheb_tc_np(p.g) <= 512 && tc_smem<BwdSpec<2>>(p.g) + 1024 <= (size_t)optin)
+    p.cheb_tc_bwd = 1;
   return 1;
 }
 
 void launch_cheb_fwd_tc(const Plan& p, int kx0, int w, cudaStream_t s) {
   const Geometry& g = p.g;
-  const int np = cheb_tc_np(g);
-  const size_t sm = tc_smem(g, np);
-  const int64_t tiles = ((int64_t)w * g.ny + kTcWave - 1) / kTcWave;
-  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, p.cheb_tc_grid));
-  const float* ct = reinterpret_cast<const float*>(p.kt.ct);
-  const float* dct = reinterpret_cast<const float*>(p.kt.dct);
-  const cplx<float>* grid = reinterpret_cast<const cplx<float>*>(p.grid);
-  cplx<float>* kbuf = reinterpret_cast<cplx<float>*>(p.kt.kbuf);
-  if (g.spectral_curl)
-    cheb_fwd_tc_kernel<true><<<blocks, kTcThreads, sm, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0, w, np,
-                                                            tc_tcols(np), p.status);
+  if (g.spectral_curl) {
+    const FwdSpec<true>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
+                                p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
+                                reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
+    launch_tc<FwdSpec<true>>(p, a, kx0, w, s);
+  } else {
+    const FwdSpec<false>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
+                                 p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
+                                 reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
+    launch_tc<FwdSpec<false>>(p, a, kx0, w, s);
+  }
+}
+
+void launch_cheb_bwd_tc(const Plan& p, int kx0, int w, cudaStream_t s) {
+  const Geometry& g = p.g;
+  const float* ict = reinterpret_cast<const float*>(p.kt.ict);
+  const float* icdt = reinterpret_cast<const float*>(p.kt.icdt);
+  const float* sdt = reinterpret_cast<const float*>(p.kt.sdt);
+  const float* zeta = reinterpret_cast<const float*>(p.tab.zeta);
+  const cplx<float>* kbuf = reinterpret_cast<const cplx<float>*>(p.kt.kbuf);
+  const cplx<float>* kaux = reinterpret_cast<const cplx<float>*>(p.kt.kaux);
+  cplx<float>* grid = reinterpret_cast<cplx<float>*>(p.grid);
+  if (g.mode == DPS_FREE)
+    launch_tc<BwdSpec<0>>(p, BwdSpec<0>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, kx0, w, s);
+  else if (g.mode == DPS_BOTTOM_WALL)
+    launch_tc<BwdSpec<1>>(p, BwdSpec<1>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, kx0, w, s);
   else
-    cheb_fwd_tc_kernel<false><<<blocks, kTcThreads, sm, s>>>(g, ct, dct, p.kt.npad, grid, kbuf, p.zrange, kx0, w, np,
-                                                             tc_tcols(np), p.status);
+    launch_tc<BwdSpec<2>>(p, BwdSpec<2>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, kx0, w, s);
 }
 
 }  // namespace dps

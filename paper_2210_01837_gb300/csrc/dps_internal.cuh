@@ -153,6 +153,7 @@ struct Plan {
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
   int interp_tile;      // interpolation variant: 1 tile gather (where it applies), 0 warp per particle
   int cheb_tc;          // forward Chebyshev transform on the tensor cores (tcgen05, mixed precision)
+  int cheb_tc_bwd;      // backward Chebyshev transform on the tensor cores (spectral-curl torques)
   int cheb_tc_grid;     // persistent blocks of that kernel
   void* ipart;          // partial sums of the tile-gather interpolation [slot][field][max_n] T
   int64_t ws_bytes;
@@ -277,6 +278,7 @@ dps_status bvp_factor_table(Plan& p);
 // error), its launcher, and its accumulator width (nz rounded up to 16)
 int cheb_tc_prepare(Plan& p);
 void launch_cheb_fwd_tc(const Plan& p, int kx0, int w, cudaStream_t s);
+void launch_cheb_bwd_tc(const Plan& p, int kx0, int w, cudaStream_t s);
 int cheb_tc_np(const Geometry& g);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);

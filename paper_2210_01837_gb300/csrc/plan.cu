@@ -327,7 +327,11 @@ dps_status allocate(Plan* p) {
   if (!alloc(&p->kt.kaux, 12 * (size_t)K * sizeof(cplx<T>))) return DPS_ERR_OOM;
   if (!bvp_prepare<T>(*p)) return DPS_ERR_INVALID_ARG;
   if (!cheb_tc_prepare(*p)) return DPS_ERR_CUDA;
-  if (const char* e = getenv("DPS_CHEB_TC")) p->cheb_tc = p->cheb_tc && atoi(e) != 0;
+  if (const char* e = getenv("DPS_CHEB_TC")) {  // bit 0 forward, bit 1 backward
+    const int v = atoi(e);
+    p->cheb_tc = p->cheb_tc && (v & 1);
+    p->cheb_tc_bwd = p->cheb_tc_bwd && (v & 2);
+  }
   // factorisation table of the FP64 solve (per (kx, |ky|), filled on the legacy stream): without
   // the memory for it the solve factorises as it goes; DPS_SOLVE_TABLE=0 chooses that by hand
   {
@@ -622,7 +626,7 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   out->fft_register_cols = p->fft_reg[1];
   out->solve_blocks = p->bvp_blocks;
   out->interp_variant = p->interp_tile;
-  out->cheb_tensor_cores = p->cheb_tc;
+  out->cheb_tensor_cores = (p->cheb_tc ? 1 : 0) | (p->cheb_tc_bwd ? 2 : 0);
   return DPS_OK;
 }
 

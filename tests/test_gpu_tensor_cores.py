@@ -1,5 +1,6 @@
-"""The forward Chebyshev transform on the tensor cores (tcgen05.mma, tf32 three-product split, mixed
-precision) against the oracle and against the CUDA-core lane kernel it replaces.
+"""The Chebyshev transforms on the tensor cores (tcgen05.mma, tf32 three-product split, mixed
+precision: the forward transform, and the backward transform of the spectral-curl torque route)
+against the oracle and against the CUDA-core lane kernels they replace.
 
 Cases: every wall mode, forces only and with torques (six-field curl source), 17 to 97 Chebyshev
 nodes (accumulator widths 32 to 112 columns per output), ragged wavenumber tiles (fewer than 64
@@ -28,10 +29,12 @@ def _lib():
 
 
 def _plan(params, torque, tc, monkeypatch):
-    monkeypatch.setenv("DPS_CHEB_TC", "1" if tc else "0")
+    monkeypatch.setenv("DPS_CHEB_TC", "3" if tc else "0")
     plan = binding.Plan.from_params(params, with_torque=torque, precision="mixed", max_n=64)
     monkeypatch.delenv("DPS_CHEB_TC")
-    assert plan.info().cheb_tensor_cores == (1 if tc else 0)
+    # bit 0 forward (nz <= 128), bit 1 backward (spectral-curl torques, nz <= 96)
+    want = (1 | (2 if torque and params["nz"] <= 96 else 0)) if tc else 0
+    assert plan.info().cheb_tensor_cores == want
     return plan
 
 
@@ -68,6 +71,6 @@ def test_tensor_cores_used_by_default_in_mixed_precision_only():
     params = small_params("bottom_wall", nx=40, ny=40, nz=33, torque=True)
     mixed = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=8)
     fp64 = binding.Plan.from_params(params, with_torque=True, precision="fp64", max_n=8)
-    assert mixed.info().cheb_tensor_cores == 1 and fp64.info().cheb_tensor_cores == 0
+    assert mixed.info().cheb_tensor_cores == 3 and fp64.info().cheb_tensor_cores == 0
     mixed.close()
     fp64.close()
