@@ -22,9 +22,11 @@
 //             omega = (1/2)(i ky w - dv, du - i kx w, i kx v - i ky u) and scales by 1/(Nx Ny).
 //
 // The block is persistent over 64-wavenumber tiles and warp-specialised:
-//   warps 0-7   producers: load the K step's operands from global memory (one step ahead in
-//               registers), split them and store them in the K-major core-matrix layout of one of
-//               kStages shared-memory stages; arrive on the stage's `full` barrier;
+//   warps 0-7   producers: load each K step's values from global memory one step ahead (in
+//               registers), form and split the step's A operands and store them in the K-major
+//               core-matrix layout of one of kStages shared-memory stages, while one thread
+//               bulk-copies the step's B operands there from a per-product image (tc_bimage_kernel);
+//               arrive on the stage's `full` barrier;
 //   warp 12     MMA issuer: waits for a full stage (and, at a tile's first step, for a free
 //               accumulator set), issues the step's MMAs, commits them to the stage's `empty`
 //               barrier and, after a tile's last step, to the accumulator set's `full` barrier;
@@ -80,6 +82,18 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) global -> shared, completing on bar
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
@@ -199,7 +213,9 @@ struct FwdSpec {
     cplx<float> v[4][NR];
   };
   // K steps of a tile: the occupied planes in groups of 8
-  __device__ static int nks(const Geometry&, int clo, int chi) { return chi >= clo ? (chi - clo + kTcK) / kTcK : 0; }
+  __host__ __device__ static int nks(const Geometry&, int clo, int chi) {
+    return chi >= clo ? (chi - clo + kTcK) / kTcK : 0;
+  }
   // producer thread (j, grp, half): wavenumber j, planes 4 grp .. 4 grp + 3 of the step; half 0
   // reads fx, fy, ty, tz (forces only: fx, fy), half 1 reads fz, tx, ty (fz)
   __device__ static void load(const Geometry& g, const Args& a, int clo, int chi, int ks, const TileK& tk, Raw& r) {
@@ -257,20 +273,21 @@ struct FwdSpec {
       split_store(ahi, kATile, umma::kmajor_offset((uint32_t)(2 * j + 1), (uint32_t)(4 * grp)), im[u][0], im[u][1],
                   im[u][2], im[u][3]);
     }
-    // B: C[n][c] (and DC[n][c]) for the step's planes, n < np
-    const uint32_t btile = (uint32_t)np * kTcK * 4;
-    for (int item = tid; item < np * 2 * NT; item += kProducers) {
-      const int n = item % np, gq = (item / np) & 1, tab = item / (2 * np);
-      const float* src = tab == 0 ? a.ct : a.dct;
-      float x[4];
+  }
+  // B image of step ks, table tab (0: C, 1: DC), row n, plane group kg (4 planes): the tf32 hi/lo
+  // split of C[n][c] (DC[n][c]) for c = clo + 8 ks + 4 kg + 0..3, zero outside the occupied planes
+  __device__ static void bimage(const Geometry& g, const Args& a, int clo, int chi, int ks, int tab, int n, int kg,
+                                unsigned char* step, int np) {
+    const float* src = tab == 0 ? a.ct : a.dct;
+    float x[4];
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const int c = clo + ks * kTcK + 4 * gq + cc;
-        x[cc] = (n < g.nz && c <= chi) ? src[(size_t)c * a.npad + n] : 0.f;
-      }
-      unsigned char* bt = st + (size_t)2 * NQ * kATile + (size_t)(2 * tab) * btile;
-      split_store(bt, btile, umma::kmajor_offset((uint32_t)n, (uint32_t)(4 * gq)), x[0], x[1], x[2], x[3]);
+    for (int cc = 0; cc < 4; ++cc) {
+      const int c = clo + ks * kTcK + 4 * kg + cc;
+      x[cc] = (n < g.nz && c <= chi) ? src[(size_t)c * a.npad + n] : 0.f;
     }
+    const uint32_t btile = (uint32_t)np * kTcK * 4;
+    split_store(step + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)n, (uint32_t)(4 * kg)), x[0], x[1],
+                x[2], x[3]);
   }
   __device__ static void mma(const Geometry&, uint32_t sbase, uint32_t tacc, int ks, int np, uint32_t idesc) {
     const uint32_t btile = (uint32_t)np * kTcK * 4;
@@ -311,8 +328,8 @@ struct FwdSpec {
 template <int CORR>  // 0 no wall, 1 bottom wall, 2 both walls
 struct BwdSpec {
   static constexpr bool kForward = false;
-  static constexpr int NQ = 3;  // A operands of a coefficient step: y_u, y_v, y_w (node step: corr_u, corr_v)
-  static constexpr int NT = 2;  // B operands: IC, ICD (node step: SD)
+  static constexpr int NQ = 3;  // A operands: y_u, y_v, y_w (node steps: corr_u, corr_v, corr_w)
+  static constexpr int NT = 2;  // B operands: IC, ICD (node steps: identity, SD)
   static constexpr int NACC = 5;
   struct Args {
     const float* ict;   // [n][cpad] IC[c][n]
@@ -324,15 +341,16 @@ struct BwdSpec {
     const cplx<float>* kaux;
     cplx<float>* grid;
   };
-  __host__ __device__ static uint32_t stage_bytes(int nmax) { return (uint32_t)(2 * NQ * kATile + 2 * NT * nmax * kTcK * 4); }
+  __host__ __device__ static uint32_t stage_bytes(int nmax) {
+    return (uint32_t)(2 * NQ * kATile + 2 * NT * nmax * kTcK * 4);
+  }
+  // coefficient step: v[cc][q] = y_f[n], n = 8 ks + 4 grp + cc (half 0: f = u, v; half 1: f = w);
+  // node step: v[q][fi] = amplitude q (cE, cG, tE, tG) of field f (half 0: u, v; half 1: w)
   struct Raw {
     cplx<float> v[4][2];
   };
-  __device__ static int ncoef(const Geometry& g) { return (g.nz + kTcK - 1) / kTcK; }
-  __device__ static int nks(const Geometry& g, int, int) { return ncoef(g) * (CORR ? 2 : 1); }
-  // producer thread (j, grp, half): wavenumber j, indices 4 grp .. 4 grp + 3 of the step.
-  // coefficient step: half 0 reads y_u, y_v, half 1 y_w; node step: the amplitudes cE, cG (tE, tG)
-  // of corr_u (half 0) or corr_v (half 1)
+  __host__ __device__ static int ncoef(const Geometry& g) { return (g.nz + kTcK - 1) / kTcK; }
+  __host__ __device__ static int nks(const Geometry& g, int, int) { return ncoef(g) * (CORR ? 2 : 1); }
   __device__ static void load(const Geometry& g, const Args& a, int, int, int ks, const TileK& tk, Raw& r) {
     const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
     const int64_t K = (int64_t)g.nkx * g.ny;
@@ -350,129 +368,113 @@ struct BwdSpec {
         }
       }
     } else {
-      const int f = half;  // u or v
       const bool amp = ok && tk.kid > 0 && !is_nyquist(g, tk.kid);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const bool want = amp && (q < 2 || CORR == 2);
-        r.v[q][0] = want ? a.kaux[(size_t)(4 * f + q) * K + tk.kid] : mk<float>(0.f, 0.f);
-        r.v[q][1] = mk<float>(0.f, 0.f);
-      }
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi) {
+          const int f = half == 0 ? fi : 2;
+          const bool want = amp && (q < 2 || CORR == 2) && (half == 0 || fi == 0);
+          r.v[q][fi] = want ? a.kaux[(size_t)(4 * f + q) * K + tk.kid] : mk<float>(0.f, 0.f);
+        }
     }
   }
-  __device__ static void store(const Geometry& g, const Args& a, int clo, int chi, int ks, const TileK& tk,
-                               const Raw& r, unsigned char* st, int nq) {
+  __device__ static void store(const Geometry& g, const Args& a, int, int, int ks, const TileK& tk, const Raw& r,
+                               unsigned char* st, int) {
     const int tid = threadIdx.x, j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;
     const int N = g.nz;
     const uint32_t orow = umma::kmajor_offset((uint32_t)(2 * j), (uint32_t)(4 * grp));
     const uint32_t orow1 = umma::kmajor_offset((uint32_t)(2 * j + 1), (uint32_t)(4 * grp));
-    const int nc = ncoef(g);
-    const uint32_t btile = (uint32_t)nq * kTcK * 4;
-    unsigned char* bbase = st + (size_t)2 * NQ * kATile;
-    if (ks < nc) {
-      // A: y_u, y_v (half 0) or y_w (half 1): operands 0, 1, 2
+    float re[2][4], im[2][4];
+    if (ks < ncoef(g)) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (half == 1 && q == 1) break;
-        unsigned char* ahi = st + (size_t)(2 * (half == 0 ? q : 2)) * kATile;
-        split_store(ahi, kATile, orow, r.v[0][q].x, r.v[1][q].x, r.v[2][q].x, r.v[3][q].x);
-        split_store(ahi, kATile, orow1, r.v[0][q].y, r.v[1][q].y, r.v[2][q].y, r.v[3][q].y);
-      }
-      // B: IC[c][n], ICD[c][n] for the occupied planes c = clo + p, p < nq
-      for (int item = tid; item < nq * 2 * 2; item += kProducers) {
-        const int p = item % nq, gq = (item / nq) & 1, tab = item / (2 * nq);
-        const float* src = tab == 0 ? a.ict : a.icdt;
-        const int c = clo + p;
-        float x[4];
+      for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          const int n = ks * kTcK + 4 * gq + cc;
-          x[cc] = (c <= chi && n < N) ? src[(size_t)n * a.cpad + c] : 0.f;
+          re[q][cc] = r.v[cc][q].x;
+          im[q][cc] = r.v[cc][q].y;
         }
-        split_store(bbase + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)p, (uint32_t)(4 * gq)),
-                    x[0], x[1], x[2], x[3]);
-      }
     } else {
-      // A: corr_u (half 0) or corr_v (half 1) at the step's nodes: operands 0, 1
-      const int j0 = (ks - nc) * kTcK + 4 * grp;
-      float cr[4], ci[4];
+      // corr_f at the step's nodes: (cE + cG zeta) e^{-k zeta} (+ (tE + tG xi) e^{-k xi})
+      const int j0 = (ks - ncoef(g)) * kTcK + 4 * grp;
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int jn = j0 + cc;
-        cr[cc] = ci[cc] = 0.f;
+        float z = 0.f, eb = 0.f, xi = 0.f, et = 0.f;
         if (jn < N) {
-          const float z = a.zeta[jn];
-          const float eb = expf(-tk.kk * z);
-          float vx = (r.v[0][0].x + r.v[1][0].x * z) * eb, vy = (r.v[0][0].y + r.v[1][0].y * z) * eb;
+          z = a.zeta[jn];
+          eb = expf(-tk.kk * z);
           if (CORR == 2) {
-            const float xi = a.zeta[N - 1 - jn];
-            const float et = expf(-tk.kk * xi);
-            vx += (r.v[2][0].x + r.v[3][0].x * xi) * et;
-            vy += (r.v[2][0].y + r.v[3][0].y * xi) * et;
+            xi = a.zeta[N - 1 - jn];
+            et = expf(-tk.kk * xi);
           }
-          cr[cc] = vx;
-          ci[cc] = vy;
         }
-      }
-      unsigned char* ahi = st + (size_t)(2 * half) * kATile;
-      split_store(ahi, kATile, orow, cr[0], cr[1], cr[2], cr[3]);
-      split_store(ahi, kATile, orow1, ci[0], ci[1], ci[2], ci[3]);
-      // B: SD[c][j] for the occupied planes
-      for (int item = tid; item < nq * 2; item += kProducers) {
-        const int p = item % nq, gq = item / nq;
-        const int c = clo + p;
-        float x[4];
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const int jn = (ks - nc) * kTcK + 4 * gq + cc;
-          x[cc] = (c <= chi && jn < N) ? a.sdt[(size_t)jn * a.cpad + c] : 0.f;
+        for (int fi = 0; fi < 2; ++fi) {
+          float vx = (r.v[0][fi].x + r.v[1][fi].x * z) * eb, vy = (r.v[0][fi].y + r.v[1][fi].y * z) * eb;
+          if (CORR == 2) {
+            vx += (r.v[2][fi].x + r.v[3][fi].x * xi) * et;
+            vy += (r.v[2][fi].y + r.v[3][fi].y * xi) * et;
+          }
+          re[fi][cc] = vx;
+          im[fi][cc] = vy;
         }
-        split_store(bbase, btile, umma::kmajor_offset((uint32_t)p, (uint32_t)(4 * gq)), x[0], x[1], x[2], x[3]);
       }
+    }
+    // A operands: u, v (half 0) or w (half 1)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (half == 1 && q == 1) break;
+      unsigned char* ahi = st + (size_t)(2 * (half == 0 ? q : 2)) * kATile;
+      split_store(ahi, kATile, orow, re[q][0], re[q][1], re[q][2], re[q][3]);
+      split_store(ahi, kATile, orow1, im[q][0], im[q][1], im[q][2], im[q][3]);
     }
   }
-  __device__ static void mma(const Geometry& g, uint32_t sbase, uint32_t tacc, int ks, int nq, uint32_t idesc) {
+  // B image of step ks, table tab, row p (plane clo + p), index group kg: coefficient steps tab 0
+  // IC[c][n], tab 1 ICD[c][n]; node steps tab 0 the identity (c = j), tab 1 SD[c][j]; zero outside
+  // the occupied planes and past the last index
+  __device__ static void bimage(const Geometry& g, const Args& a, int clo, int chi, int ks, int tab, int p, int kg,
+                                unsigned char* step, int nq) {
+    const int N = g.nz, nc = ncoef(g);
+    const int c = clo + p;
+    float x[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int idx = (ks < nc ? ks : ks - nc) * kTcK + 4 * kg + cc;
+      float v = 0.f;
+      if (c <= chi && idx < N) {
+        if (ks < nc) v = (tab == 0 ? a.ict : a.icdt)[(size_t)idx * a.cpad + c];
+        else v = tab == 0 ? (idx == c ? 1.f : 0.f) : a.sdt[(size_t)idx * a.cpad + c];
+      }
+      x[cc] = v;
+    }
     const uint32_t btile = (uint32_t)nq * kTcK * 4;
-    const uint32_t bbase = sbase + 2 * NQ * kATile;
+    split_store(step + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)p, (uint32_t)(4 * kg)), x[0], x[1],
+                x[2], x[3]);
+  }
+  // every step: u, v, w += A_f B0;  du += A_u B1, dv += A_v B1
+  __device__ static void mma(const Geometry&, uint32_t sbase, uint32_t tacc, int ks, int nq, uint32_t idesc) {
+    const uint32_t btile = (uint32_t)nq * kTcK * 4;
+    const uint32_t b0 = sbase + 2 * NQ * kATile, b1 = b0 + 2 * btile;
     const uint32_t acc = ks > 0 ? 1u : 0u;
     const uint32_t au = sbase, av = sbase + 2 * kATile, aw = sbase + 4 * kATile;
-    if (ks < ncoef(g)) {
-      mma3(tacc + 0 * nq, au, bbase, btile, idesc, acc);              // u  = IC y_u
-      mma3(tacc + 1 * nq, av, bbase, btile, idesc, acc);              // v  = IC y_v
-      mma3(tacc + 2 * nq, aw, bbase, btile, idesc, acc);              // w  = IC y_w
-      mma3(tacc + 3 * nq, au, bbase + 2 * btile, btile, idesc, acc);  // du = ICD y_u
-      mma3(tacc + 4 * nq, av, bbase + 2 * btile, btile, idesc, acc);  // dv = ICD y_v
-    } else {
-      mma3(tacc + 3 * nq, au, bbase, btile, idesc, 1u);               // du += SD corr_u
-      mma3(tacc + 4 * nq, av, bbase, btile, idesc, 1u);               // dv += SD corr_v
-    }
+    mma3(tacc + 0 * nq, au, b0, btile, idesc, acc);
+    mma3(tacc + 1 * nq, av, b0, btile, idesc, acc);
+    mma3(tacc + 2 * nq, aw, b0, btile, idesc, acc);
+    mma3(tacc + 3 * nq, au, b1, btile, idesc, acc);
+    mma3(tacc + 4 * nq, av, b1, btile, idesc, acc);
   }
   // epilogue thread: TMEM lane `row` = (wavenumber row >> 1, part row & 1); lanes 2j and 2j + 1 pair
   // up for the products with i
   __device__ static void epilogue(const Geometry& g, const Args& a, uint32_t tlane, int row, const TileK& tk, int nq,
                                   int clo, int chi, bool) {
-    const int64_t K = (int64_t)g.nkx * g.ny;
     const int part = row & 1;
-    const int N = g.nz;
     const bool nyq = tk.col >= 0 && is_nyquist(g, tk.kid);
-    const bool corr = CORR > 0 && tk.col >= 0 && tk.kid > 0 && !nyq;
-    // this part of the correction amplitudes of u, v, w: bottom (E, G), top (E, G)
-    float am[3][4];
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float v = 0.f;
-        if (corr && (q < 2 || CORR == 2)) {
-          const cplx<float> c = a.kaux[(size_t)(4 * f + q) * K + tk.kid];
-          v = part ? c.y : c.x;
-        }
-        am[f][q] = v;
-      }
-    const float scale = (float)(1.0 / ((double)g.nx * (double)g.ny));
+    const float scale = nyq ? 0.f : (float)(1.0 / ((double)g.nx * (double)g.ny));
     const size_t plane = (size_t)g.ny * g.pitch, fstride = (size_t)g.nz * plane;
-    float* gr = reinterpret_cast<float*>(a.grid);
+    float* gr = reinterpret_cast<float*>(a.grid) + 2 * (size_t)(tk.col >= 0 ? tk.col : 0) + part;
     const float sgn = part ? 1.f : -1.f;  // (i x) of this part: re -> -x.im, im -> +x.re
+    const float hx = tk.hkx * scale, hy = tk.hky * scale, hs = 0.5f * scale;
     for (int p0 = 0; p0 < nq; p0 += 8) {
       float u[8], v[8], w[8], du[8], dv[8];
       tmem_ld8(tlane + (uint32_t)(0 * nq + p0), u);
@@ -483,36 +485,19 @@ struct BwdSpec {
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int c = clo + p0 + t;
-        if (corr && c <= chi) {
-          const float z = a.zeta[c];
-          const float eb = expf(-tk.kk * z);
-          float et = 0.f, xi = 0.f;
-          if (CORR == 2) {
-            xi = a.zeta[N - 1 - c];
-            et = expf(-tk.kk * xi);
-          }
-          u[t] += (am[0][0] + am[0][1] * z) * eb + (CORR == 2 ? (am[0][2] + am[0][3] * xi) * et : 0.f);
-          v[t] += (am[1][0] + am[1][1] * z) * eb + (CORR == 2 ? (am[1][2] + am[1][3] * xi) * et : 0.f);
-          w[t] += (am[2][0] + am[2][1] * z) * eb + (CORR == 2 ? (am[2][2] + am[2][3] * xi) * et : 0.f);
-        }
-        // the other part of u, v, w (partner lane)
-        const float uo = __shfl_xor_sync(0xffffffffu, u[t], 1);
-        const float vo = __shfl_xor_sync(0xffffffffu, v[t], 1);
-        const float wo = __shfl_xor_sync(0xffffffffu, w[t], 1);
-        // omega = 1/2 (i ky w - dv, du - i kx w, i kx v - i ky u); (i x) of this part = sgn x(other)
-        const float iw = sgn * wo, iv = sgn * vo, iu = sgn * uo;
-        const float ox = tk.hky * iw - 0.5f * dv[t];
-        const float oy = 0.5f * du[t] - tk.hkx * iw;
-        const float oz = tk.hkx * iv - tk.hky * iu;
+        // the other part of u, v, w (partner lane); (i x) of this part = sgn x(other part)
+        const float iu = sgn * __shfl_xor_sync(0xffffffffu, u[t], 1);
+        const float iv = sgn * __shfl_xor_sync(0xffffffffu, v[t], 1);
+        const float iw = sgn * __shfl_xor_sync(0xffffffffu, w[t], 1);
         if (tk.col >= 0 && c <= chi) {
-          const size_t o0 = ((size_t)c * plane + tk.col) * 2 + part;
-          const float s = nyq ? 0.f : scale;
-          gr[o0] = u[t] * s;
-          gr[o0 + 2 * fstride] = v[t] * s;
-          gr[o0 + 4 * fstride] = w[t] * s;
-          gr[o0 + 6 * fstride] = ox * s;
-          gr[o0 + 8 * fstride] = oy * s;
-          gr[o0 + 10 * fstride] = oz * s;
+          // omega = 1/2 (i ky w - dv, du - i kx w, i kx v - i ky u), all scaled by 1/(Nx Ny)
+          float* o = gr + 2 * (size_t)c * plane;
+          o[0] = u[t] * scale;
+          o[2 * fstride] = v[t] * scale;
+          o[4 * fstride] = w[t] * scale;
+          o[6 * fstride] = hy * iw - hs * dv[t];
+          o[8 * fstride] = hs * du[t] - hx * iw;
+          o[10 * fstride] = hx * iv - hy * iu;
         }
       }
     }
@@ -529,20 +514,46 @@ struct TcShared {
   int stop;
 };
 
+// GEMM N of a transform: forward the Chebyshev index, backward the occupied planes (their count),
+// rounded up to 16 (at least 16)
+template <typename Spec>
+__host__ __device__ inline int tc_nn(const Geometry& g, int clo, int chi) {
+  const int nmax = (g.nz + 15) / 16 * 16;
+  const int nocc = chi >= clo ? chi - clo + 1 : 0;
+  const int nq = (nocc + 15) / 16 * 16;
+  return Spec::kForward ? nmax : (nq < 16 ? 16 : nq);
+}
+
+// The B operands of every K step of a product, tf32-split and laid out as in a stage, so that the
+// pipeline copies them with one bulk copy per step: image[ks][tab][hi, lo][nn rows x 8]
+template <typename Spec>
+__global__ void tc_bimage_kernel(Geometry g, typename Spec::Args a, const int* __restrict__ zrange,
+                                 unsigned char* __restrict__ img) {
+  const int clo = zrange[0], chi = zrange[1];
+  const int nn = tc_nn<Spec>(g, clo, chi);
+  const int nks = Spec::nks(g, clo, chi);
+  const uint32_t step = (uint32_t)(2 * Spec::NT * nn * kTcK * 4);
+  const int items = nks * Spec::NT * nn * 2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items; i += gridDim.x * blockDim.x) {
+    const int kg = i & 1, r = (i >> 1) % nn, rest = (i >> 1) / nn;
+    const int tab = rest % Spec::NT, ks = rest / Spec::NT;
+    Spec::bimage(g, a, clo, chi, ks, tab, r, kg, img + (size_t)ks * step, nn);
+  }
+}
+
 template <typename Spec>
 __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, typename Spec::Args a,
+                                                                const unsigned char* __restrict__ bimg,
                                                                 const int* __restrict__ zrange, int kx0, int w,
                                                                 int* __restrict__ status) {
-  constexpr bool FWD = Spec::kForward;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ TcShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int clo = zrange[0], chi = zrange[1];
   const int64_t ntiles = ((int64_t)w * g.ny + kTcWave - 1) / kTcWave;
-  // GEMM N: forward the Chebyshev index (nz rounded up to 16); backward the occupied planes
-  const int nocc = chi >= clo ? chi - clo + 1 : 0;
   const int nmax = (g.nz + 15) / 16 * 16;  // the stage layout is sized for this
-  const int nn = FWD ? nmax : max(16, (nocc + 15) / 16 * 16);
+  const int nn = tc_nn<Spec>(g, clo, chi);
+  const uint32_t bbytes = (uint32_t)(2 * Spec::NT * nn * kTcK * 4);  // B operands of one step
   const int cols = Spec::NACC * nn;
   const int nbuf = 2 * cols <= 512 ? 2 : 1;
   const int need = nbuf * cols;
@@ -597,10 +608,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
           const bool last = ks + 1 == nks;
           const int64_t ntile = last ? tile + gridDim.x : tile;
           const TileK ntk = last ? tile_k(g, ntile, tid & 63, kx0, w) : tk;
+          // the step's B operands: one bulk copy from the image, completing on the stage barrier
+          if (tid == 0) {
+            mbar_arrive_tx(&sh.full[s], bbytes);
+            bulk_copy(st + 2 * Spec::NQ * kATile, bimg + (size_t)ks * bbytes, bbytes, &sh.full[s]);
+          }
           if (ntile < ntiles) Spec::load(g, a, clo, chi, last ? 0 : ks + 1, ntk, raw);
           Spec::store(g, a, clo, chi, ks, tk, cur, st, nn);
           proxy_fence();
-          mbar_arrive(&sh.full[s]);
+          if (tid != 0) mbar_arrive(&sh.full[s]);
           if (last) tk = ntk;
         }
         if (*stop) break;
@@ -672,15 +688,21 @@ size_t tc_smem(const Geometry& g) {
 }
 
 template <typename Spec>
-void launch_tc(const Plan& p, const typename Spec::Args& a, int kx0, int w, cudaStream_t s) {
+void launch_tc(const Plan& p, const typename Spec::Args& a, unsigned char* img, int kx0, int w, cudaStream_t s) {
   const int64_t tiles = ((int64_t)w * p.g.ny + kTcWave - 1) / kTcWave;
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, p.cheb_tc_grid));
-  cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, p.zrange, kx0, w, p.status);
+  tc_bimage_kernel<Spec><<<64, 256, 0, s>>>(p.g, a, p.zrange, img);
+  cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status);
 }
 
 }  // namespace
 
 int cheb_tc_np(const Geometry& g) { return (g.nz + 15) / 16 * 16; }
+
+size_t cheb_tc_image_bytes(const Geometry& g, bool backward) {
+  const size_t nmax = (size_t)cheb_tc_np(g), ksteps = (size_t)(g.nz + kTcK - 1) / kTcK;
+  return (backward ? 2 * ksteps : ksteps) * 2 * 2 * nmax * kTcK * 4;
+}
 
 int cheb_tc_prepare(Plan& p) {
   p.cheb_tc = 0;
@@ -710,12 +732,12 @@ void launch_cheb_fwd_tc(const Plan& p, int kx0, int w, cudaStream_t s) {
     const FwdSpec<true>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
                                 p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
                                 reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
-    launch_tc<FwdSpec<true>>(p, a, kx0, w, s);
+    launch_tc<FwdSpec<true>>(p, a, p.kt.bimg_f, kx0, w, s);
   } else {
     const FwdSpec<false>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
                                  p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
                                  reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
-    launch_tc<FwdSpec<false>>(p, a, kx0, w, s);
+    launch_tc<FwdSpec<false>>(p, a, p.kt.bimg_f, kx0, w, s);
   }
 }
 
@@ -729,11 +751,14 @@ void launch_cheb_bwd_tc(const Plan& p, int kx0, int w, cudaStream_t s) {
   const cplx<float>* kaux = reinterpret_cast<const cplx<float>*>(p.kt.kaux);
   cplx<float>* grid = reinterpret_cast<cplx<float>*>(p.grid);
   if (g.mode == DPS_FREE)
-    launch_tc<BwdSpec<0>>(p, BwdSpec<0>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, kx0, w, s);
+    launch_tc<BwdSpec<0>>(p, BwdSpec<0>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, p.kt.bimg_b, kx0, w,
+                           s);
   else if (g.mode == DPS_BOTTOM_WALL)
-    launch_tc<BwdSpec<1>>(p, BwdSpec<1>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, kx0, w, s);
+    launch_tc<BwdSpec<1>>(p, BwdSpec<1>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, p.kt.bimg_b, kx0, w,
+                           s);
   else
-    launch_tc<BwdSpec<2>>(p, BwdSpec<2>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, kx0, w, s);
+    launch_tc<BwdSpec<2>>(p, BwdSpec<2>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, p.kt.bimg_b, kx0, w,
+                           s);
 }
 
 }  // namespace dps

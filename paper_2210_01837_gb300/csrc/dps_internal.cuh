@@ -118,6 +118,8 @@ struct KTabs {
   void* kaux;      // [12][K]    wall-correction amplitudes per wavenumber
   double* fac;     // [N][4][KP] factorisation of the banded systems per (kx, |ky|) (FP64), or null
   int64_t KP;      // nkx (ny/2 + 1)
+  unsigned char* bimg_f;  // tensor-core transforms: B operands of every K step (forward, backward)
+  unsigned char* bimg_b;
   int npad, cpad;
   int fwd_smem, bwd_smem;
 };
@@ -280,6 +282,7 @@ int cheb_tc_prepare(Plan& p);
 void launch_cheb_fwd_tc(const Plan& p, int kx0, int w, cudaStream_t s);
 void launch_cheb_bwd_tc(const Plan& p, int kx0, int w, cudaStream_t s);
 int cheb_tc_np(const Geometry& g);
+size_t cheb_tc_image_bytes(const Geometry& g, bool backward);
 template <typename T> size_t bvp_slot_bytes(const Plan& p);
 template <typename T> int fft_smem_ok(Plan& p);
 // column block 2^lcw and variant of the y-FFT pass (reg: 0 shared-memory-staged, 1 register-staged,

@@ -166,7 +166,7 @@ void free_plan(Plan* p) {
                   p->kt.ct, p->kt.dct,
                   p->kt.ict, p->kt.icdt, p->kt.sdt, p->kt.bandT, p->kt.cmat, p->kt.kbuf, p->kt.kaux, p->grid, p->records, p->bin_of, p->bin_count, p->bin_start,
                   p->bin_cursor, p->sorted, p->zrange, p->status, p->ws, p->stage_in, p->stage_out, p->ipart,
-                  p->kt.fac};
+                  p->kt.fac, p->kt.bimg_f, p->kt.bimg_b};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -327,6 +327,8 @@ dps_status allocate(Plan* p) {
   if (!alloc(&p->kt.kaux, 12 * (size_t)K * sizeof(cplx<T>))) return DPS_ERR_OOM;
   if (!bvp_prepare<T>(*p)) return DPS_ERR_INVALID_ARG;
   if (!cheb_tc_prepare(*p)) return DPS_ERR_CUDA;
+  if (p->cheb_tc && !alloc((void**)&p->kt.bimg_f, cheb_tc_image_bytes(g, false))) return DPS_ERR_OOM;
+  if (p->cheb_tc_bwd && !alloc((void**)&p->kt.bimg_b, cheb_tc_image_bytes(g, true))) return DPS_ERR_OOM;
   if (const char* e = getenv("DPS_CHEB_TC")) {  // bit 0 forward, bit 1 backward
     const int v = atoi(e);
     p->cheb_tc = p->cheb_tc && (v & 1);
@@ -619,7 +621,9 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   out->alpha_D = p->g.with_torque ? p->g.kD.alpha : 0.0;
   // init, records, 3 binning, spread, x pass, 5 per column chunk, x pass, interpolation (+ its
   // finishing kernel for the tile gather)
-  out->launches_per_apply = 9 + 5 * p->nchunks + ((p->interp_tile && p->ipart) ? 1 : 0);
+  // (+ the B-operand image kernel before each tensor-core transform)
+  out->launches_per_apply = 9 + 5 * p->nchunks + ((p->interp_tile && p->ipart) ? 1 : 0) +
+                            p->nchunks * ((p->cheb_tc ? 1 : 0) + (p->cheb_tc_bwd ? 1 : 0));
   out->nchunks = p->nchunks;
   out->fft_col_width = 1 << p->col_lcw;
   out->fft_register_rows = p->fft_reg[0];
