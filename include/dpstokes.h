@@ -429,6 +429,15 @@ dps_status dpstokes_debug_run(dps_plan_t plan, int64_t n, const double* position
 dps_status dpstokes_debug_copy(dps_plan_t plan, int32_t which, void* dst, int64_t dst_bytes,
                                void* stream);
 
+/* Failure injection for tests (no counterpart in the paper).  code 1: in the next apply the forward
+ * tensor-core transform withholds its matrix multiplies and their completion signals, so the
+ * producers' bounded waits for a free operand stage run out (about a second): the kernel records
+ * DPS_ERR_TIMEOUT in the status word (read by dpstokes_status), its blocks free their tensor memory
+ * and leave, and the plan stays usable for the next apply.  The injection applies to one apply and
+ * then clears itself.  code 0 clears it.  DPS_ERR_INVALID_ARG for other codes, or for code 1 on a
+ * plan that does not use the tensor-core forward transform. */
+dps_status dpstokes_debug_inject(dps_plan_t plan, int32_t code);
+
 #ifdef __cplusplus
 }
 #endif

@@ -138,6 +138,7 @@ def load(path=None):
         "dpstokes_plan_set_fft": (_I32, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
         "dpstokes_plan_set_pipeline": (_I32, [_P, ctypes.c_int32, ctypes.c_int32]),
         "dpstokes_plan_set_interp": (_I32, [_P, ctypes.c_int32]),
+        "dpstokes_debug_inject": (_I32, [_P, ctypes.c_int32]),
         "dpstokes_plan_autotune": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
         "dpstokes_apply_batch": (_I32, [ctypes.POINTER(dps_request), _I32, _P]),
         "dpstokes_batch_prepare": (_I32, []),
@@ -362,6 +363,11 @@ class Plan:
         st = load().dpstokes_plan_set_fft(self.handle, int(row_register), int(col_register), int(col_width))
         if st != DPS_OK:
             raise DpsError(st, "dpstokes_plan_set_fft")
+
+    def debug_inject(self, code):
+        st = load().dpstokes_debug_inject(self.handle, int(code))
+        if st != DPS_OK:
+            raise DpsError(st, "dpstokes_debug_inject")
 
     def set_interp(self, variant):
         st = load().dpstokes_plan_set_interp(self.handle, int(variant))

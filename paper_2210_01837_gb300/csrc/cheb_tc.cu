@@ -545,7 +545,7 @@ template <typename Spec>
 __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, typename Spec::Args a,
                                                                 const unsigned char* __restrict__ bimg,
                                                                 const int* __restrict__ zrange, int kx0, int w,
-                                                                int* __restrict__ status) {
+                                                                int* __restrict__ status, int inject) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ TcShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -638,6 +638,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
         const int s = it % kStages;
         if (!mbar_wait(&sh.full[s], (it / kStages) & 1, stop)) { fail(); ok = false; break; }
         tc_fence_after();
+        if (inject) continue;  // failure injection: no MMAs and no completion signals
         if (lane == 0) {
           Spec::mma(g, saddr(smraw + (size_t)s * stage_bytes), tacc, ks, nn, idesc);
           mma_commit(&sh.empty[s]);  // the stage is free once these MMAs have read it
@@ -648,7 +649,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
       if (!ok) break;
     }
     // a stop: wait (bounded) for the MMAs already issued before the tensor memory is freed
-    if (*stop && it > 0) {
+    if (*stop && it > 0 && !inject) {
       const unsigned last = it - 1;
       const long long t0 = clock64();
       while (!mbar_test(&sh.empty[last % kStages], (last / kStages) & 1) && clock64() - t0 < kWaitCycles) {
@@ -688,11 +689,13 @@ size_t tc_smem(const Geometry& g) {
 }
 
 template <typename Spec>
-void launch_tc(const Plan& p, const typename Spec::Args& a, unsigned char* img, int kx0, int w, cudaStream_t s) {
+void launch_tc(const Plan& p, const typename Spec::Args& a, unsigned char* img, int kx0, int w, cudaStream_t s,
+               int inject = 0) {
   const int64_t tiles = ((int64_t)w * p.g.ny + kTcWave - 1) / kTcWave;
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, p.cheb_tc_grid));
   tc_bimage_kernel<Spec><<<64, 256, 0, s>>>(p.g, a, p.zrange, img);
-  cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status);
+  cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status,
+                                                                      inject);
 }
 
 }  // namespace
@@ -732,12 +735,12 @@ void launch_cheb_fwd_tc(const Plan& p, int kx0, int w, cudaStream_t s) {
     const FwdSpec<true>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
                                 p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
                                 reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
-    launch_tc<FwdSpec<true>>(p, a, p.kt.bimg_f, kx0, w, s);
+    launch_tc<FwdSpec<true>>(p, a, p.kt.bimg_f, kx0, w, s, p.inject);
   } else {
     const FwdSpec<false>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
                                  p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
                                  reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
-    launch_tc<FwdSpec<false>>(p, a, p.kt.bimg_f, kx0, w, s);
+    launch_tc<FwdSpec<false>>(p, a, p.kt.bimg_f, kx0, w, s, p.inject);
   }
 }
 

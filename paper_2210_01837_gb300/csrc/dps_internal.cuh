@@ -157,6 +157,7 @@ struct Plan {
   int cheb_tc;          // forward Chebyshev transform on the tensor cores (tcgen05, mixed precision)
   int cheb_tc_bwd;      // backward Chebyshev transform on the tensor cores (spectral-curl torques)
   int cheb_tc_grid;     // persistent blocks of that kernel
+  int inject;           // failure injection of the next apply (dpstokes_debug_inject)
   void* ipart;          // partial sums of the tile-gather interpolation [slot][field][max_n] T
   int64_t ws_bytes;
   // host-input staging (dpstokes_apply_host)

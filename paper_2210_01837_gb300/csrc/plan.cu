@@ -432,6 +432,7 @@ void enqueue(Plan& p, int64_t n, const double* pos, const double* F, const doubl
   if (last_stage <= 5) return;
   timed(11, s, [&] { launch_interp<T>(p, n, U, W, s); });
   if (tm) p.timed_apply = 1;
+  p.inject = 0;  // an injected failure applies to one apply
 }
 
 }  // namespace
@@ -631,6 +632,13 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   out->solve_blocks = p->bvp_blocks;
   out->interp_variant = p->interp_tile;
   out->cheb_tensor_cores = (p->cheb_tc ? 1 : 0) | (p->cheb_tc_bwd ? 2 : 0);
+  return DPS_OK;
+}
+
+dps_status dpstokes_debug_inject(dps_plan_t plan, int32_t code) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || code < 0 || code > 1 || (code == 1 && !p->cheb_tc)) return DPS_ERR_INVALID_ARG;
+  p->inject = code;
   return DPS_OK;
 }
 

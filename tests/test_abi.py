@@ -134,6 +134,8 @@ def test_batch_and_server_reject_invalid_arguments_on_host(lib):
     r = binding.dps_serve_result()
     assert lib.dpstokes_server_wait(None, 0, 0.0, ctypes.byref(r)) == binding.DPS_ERR_INVALID_ARG
     assert lib.dpstokes_server_set_queue_limit(None, 4) == binding.DPS_ERR_INVALID_ARG
+    assert lib.dpstokes_debug_inject(None, 1) == binding.DPS_ERR_INVALID_ARG
+    assert lib.dpstokes_plan_set_interp(None, 0) == binding.DPS_ERR_INVALID_ARG
     lib.dpstokes_server_destroy(None)
 
 

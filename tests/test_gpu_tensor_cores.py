@@ -74,3 +74,20 @@ def test_tensor_cores_used_by_default_in_mixed_precision_only():
     assert mixed.info().cheb_tensor_cores == 3 and fp64.info().cheb_tensor_cores == 0
     mixed.close()
     fp64.close()
+
+
+def test_bounded_wait_reports_timeout_and_the_plan_stays_usable():
+    """Failure injection: the forward tensor-core transform withholds its MMA completions, so its
+    producers' bounded waits run out (about a second); the kernel records DPS_ERR_TIMEOUT instead
+    of hanging, frees its tensor memory, and the next apply of the same plan is correct."""
+    from gpu_helpers import to_dev
+    params = small_params("bottom_wall", nx=72, ny=40, nz=33, torque=True)
+    pos, F, T = random_particles(params, 20, seed=5)
+    plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=len(pos))
+    ref = gpu_mobility(params, pos, F, T, "mixed", plan=plan)
+    plan.debug_inject(1)
+    plan.apply(to_dev(pos), to_dev(F), to_dev(T))
+    assert plan.status() == binding.DPS_ERR_TIMEOUT
+    got = gpu_mobility(params, pos, F, T, "mixed", plan=plan)
+    plan.close()
+    assert rel_l2(got[0], ref[0]) <= 1e-6 and rel_l2(got[1], ref[1]) <= 1e-6
