@@ -72,6 +72,22 @@ template <typename T> __device__ __forceinline__ T narrow(double v);
 template <> __device__ __forceinline__ float narrow<float>(double v) { return d2f(v); }
 template <> __device__ __forceinline__ double narrow<double>(double v) { return v; }
 
+// loads and stores of data touched once (evict-first in L1 and L2)
+__device__ __forceinline__ cplx<float> ld_stream(const cplx<float>* p) {
+  const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+__device__ __forceinline__ cplx<double> ld_stream(const cplx<double>* p) {
+  const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+__device__ __forceinline__ void st_stream(cplx<float>* p, cplx<float> v) {
+  __stcs(reinterpret_cast<float2*>(p), make_float2(v.x, v.y));
+}
+__device__ __forceinline__ void st_stream(cplx<double>* p, cplx<double> v) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(v.x, v.y));
+}
+
 template <typename T> __device__ __forceinline__ cplx<double> wid(cplx<T> a) { return mk<double>(widen<T>(a.x), widen<T>(a.y)); }
 template <typename T> __device__ __forceinline__ cplx<T> nar(cplx<double> a) { return mk<T>(narrow<T>(a.x), narrow<T>(a.y)); }
 
@@ -842,8 +858,14 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
     return;
   }
   const int64_t kp = (int64_t)((2 * ki.kyi <= g.ny) ? ki.kyi : g.ny - ki.kyi) * g.nkx + ki.kxi;
-  auto KB = [&](int f, int n) -> cplx<T>& { return kbuf[((size_t)f * N + n) * K + kidx]; };
-  auto SW = [&](int f, int n) -> cplx<double>& { return sw[((size_t)f * N + n) * slots + slot]; };
+  // the spectra are read once and written once: streaming loads and stores, so that they do not
+  // push the sweep values out of L2
+  auto KBL = [&](int f, int n) -> cplx<T> { return ld_stream(kbuf + ((size_t)f * N + n) * K + kidx); };
+  auto KBS = [&](int f, int n, cplx<T> v) { st_stream(kbuf + ((size_t)f * N + n) * K + kidx, v); };
+  // sweep values of one parity at a time: row n in slot n / 2, so a thread's live workspace is
+  // half of the rows (kept small enough to stay in L2 across the sweep and the substitution)
+  const int NH = (N + 1) / 2;
+  auto SW = [&](int f, int n) -> cplx<double>& { return sw[((size_t)f * NH + (n >> 1)) * slots + slot]; };
   auto PW = [&](int n) -> cplx<T>& { return pws[(size_t)n * slots + slot]; };
   auto FAC = [&](int n, int q) -> double { return fac[((size_t)n * 4 + q) * KP + kp]; };
   const double* bP = band + 3 * N;
@@ -863,15 +885,15 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
     const int nlast = ((N - 1 - par) & 1) ? N - 2 : N - 1;
     cplx<double> s_next = mk<double>(0, 0), gacc = mk<double>(0, 0);
     cplx<T> dh_next = zT;  // derivative recurrence of h over the opposite parity
-    cplx<T> fc = KB(0, nlast), gc = KB(1, nlast), hc = (nlast + 1 < N) ? KB(2, nlast + 1) : zT;
+    cplx<T> fc = KBL(0, nlast), gc = KBL(1, nlast), hc = (nlast + 1 < N) ? KBL(2, nlast + 1) : zT;
     double vc = FAC(nlast, 0), bc = FAC(nlast, 2), rc = FAC(nlast, 3);
     for (int n = nlast; n >= par; n -= 2) {
       cplx<T> fn = zT, gn = zT, hn = zT;
       double vn = 0.0, bn = 0.0, rn = 0.0;
       if (n - 2 >= par) {  // next row's inputs before this row's FP64 recurrence
-        fn = KB(0, n - 2);
-        gn = KB(1, n - 2);
-        hn = KB(2, n - 1);
+        fn = KBL(0, n - 2);
+        gn = KBL(1, n - 2);
+        hn = KBL(2, n - 1);
         vn = FAC(n - 2, 0);
         bn = FAC(n - 2, 2);
         rn = FAC(n - 2, 3);
@@ -963,7 +985,7 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
     }
     cplx<T> dp_next = zT;
     cplx<T> pc1 = (nlast + 1 < N) ? PW(nlast + 1) : zT, pc0 = PW(nlast);
-    cplx<T> f0c = KB(0, nlast), f1c = KB(1, nlast), f2c = KB(2, nlast);
+    cplx<T> f0c = KBL(0, nlast), f1c = KBL(1, nlast), f2c = KBL(2, nlast);
     double vc = FAC(nlast, 0), bc = FAC(nlast, 2), rc = FAC(nlast, 3);
     for (int n = nlast; n >= par; n -= 2) {
       cplx<T> pn1 = zT, pn0 = zT, f0n = zT, f1n = zT, f2n = zT;
@@ -971,9 +993,9 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
       if (n - 2 >= par) {
         pn1 = PW(n - 1);
         pn0 = PW(n - 2);
-        f0n = KB(0, n - 2);
-        f1n = KB(1, n - 2);
-        f2n = KB(2, n - 2);
+        f0n = KBL(0, n - 2);
+        f1n = KBL(1, n - 2);
+        f2n = KBL(2, n - 2);
         vn = FAC(n - 2, 0);
         bn = FAC(n - 2, 2);
         rn = FAC(n - 2, 3);
@@ -1050,7 +1072,7 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
             cplx<T> y = scl(tcm[f], td[q]) + scl(tnew, tu[q]);
             if (q >= 2) y = y + scl(tcm2[f], tl[q]);
             if (q == par) y = y + nar<T>(gacc[f]);
-            KB(f, q) = y;
+            KBS(f, q, y);
             tcm2[f] = tcm[f];
             tcm[f] = tnew;
             sc[f] = sn[f];
@@ -1083,6 +1105,16 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
   wall_amplitudes<T, SLIP>(g, kx, ky, kk, vtop, vbot, dtop, dbot, kaux, kidx, K);
 }
 
+// thread i of a chunk -> wavenumber, with the ky rows in the order 0, 1, ny-1, 2, ny-2, ...: the
+// two wavenumbers (kx, +-ky) that read the same factorisation-table rows run in the same pass of the
+// persistent grid, so the second read comes from L2
+__device__ __forceinline__ int64_t paired_kidx(const Geometry& g, int64_t i, int kx0, int w) {
+  const unsigned ii = (unsigned)i;
+  const int j = (int)(ii / (unsigned)w);
+  const int kyi = (j == 0) ? 0 : ((j & 1) ? (j + 1) >> 1 : g.ny - (j >> 1));
+  return (int64_t)kyi * g.nkx + kx0 + (int)(ii - (unsigned)j * (unsigned)w);
+}
+
 // one thread per wavenumber of the chunk (persistent grid)
 template <typename T, bool SLIP>
 __global__ void __launch_bounds__(kBvpThreads, 3) solve_tab_kernel(Geometry g, const double* __restrict__ band,
@@ -1096,7 +1128,7 @@ __global__ void __launch_bounds__(kBvpThreads, 3) solve_tab_kernel(Geometry g, c
   const int slots = gridDim.x * blockDim.x;
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t i = slot; i < total; i += slots)
-    solve_tab<T, SLIP>(g, band, bandT, fac, KP, kbuf, kaux, pws, sw, slots, slot, chunk_kidx(g, i, kx0, w), K);
+    solve_tab<T, SLIP>(g, band, bandT, fac, KP, kbuf, kaux, pws, sw, slots, slot, paired_kidx(g, i, kx0, w), K);
 }
 
 // ---------------------------------------------------------------------------------------------
