@@ -165,6 +165,56 @@ def cpu_oracle_tile(div, seed_offset=3):
     return time.perf_counter() - t0, len(pos), params["nx"]
 
 
+def cpu_oracle_config(name, div=1, seed=0):
+    """One oracle product of configuration `name` ("bw_small": whole; "slit_16k": a 1/div^2-area
+    tile with the same density, heights and h); returns seconds."""
+    from oracle import Params, mobility
+    from paper_2210_01837_gb300.workloads import bw_small, slit_16k
+    if name == "bw_small":
+        params, pos, F, T = bw_small()
+    else:
+        params, pos, F, T = slit_16k(n=16384 // (div * div), nxy=384 // div, L=256.0 / div, seed_offset=2 + 100 * seed)
+    t0 = time.perf_counter()
+    mobility(Params(**params), pos, F, T)
+    return time.perf_counter() - t0
+
+
+def _oracle_config_runs(name, div, procs, threads):
+    """Wall seconds of `procs` concurrent oracle products of `name`, each in a fresh interpreter
+    with `threads` BLAS/OpenMP threads, and the per-process times."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    t0 = time.perf_counter()
+    kids = []
+    for i in range(procs):
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench.cpu_oracle_config(%r, %d, %d)))" % (ROOT, name, div, i))
+        kids.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                     text=True, env=env))
+    per = [json.loads(k.communicate(timeout=1800)[0].strip().splitlines()[-1]) for k in kids]
+    return time.perf_counter() - t0, per
+
+
+def oracle_configs():
+    """The oracle on configurations 1 and 2 on the host's cores: configuration 1 whole (one process
+    with every core's BLAS threads, and one process on one core); configuration 2 as one 1/16-area
+    tile per core, all at once, and one tile on one core (times x 16: work is linear in N and in
+    grid nodes)."""
+    cores = host_cores()
+    c1_all, _ = _oracle_config_runs("bw_small", 1, 1, cores)
+    c1_one, _ = _oracle_config_runs("bw_small", 1, 1, 1)
+    div = 4
+    wall, per = _oracle_config_runs("slit_16k", div, cores, 1)
+    t1, _ = _oracle_config_runs("slit_16k", div, 1, 1)
+    return {"cores": cores,
+            "bw_small": {"wall_s_all_cores": c1_all, "wall_s_one_core": c1_one, "sample": "whole product, N=100"},
+            "slit_16k": {"products_per_s_all_cores": cores / (wall * div * div),
+                         "wall_s_one_core_extrapolated": t1 * div * div,
+                         "sample": f"{cores} concurrent 1/{div * div}-area tiles (N={16384 // (div * div)}, "
+                                   f"{384 // div}^2x97, one core each): {wall:.1f} s wall (per tile "
+                                   f"{min(per):.1f}-{max(per):.1f} s); one tile on one core {t1:.1f} s, x {div * div}"}}
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -495,6 +545,8 @@ def main():
     ap.add_argument("--no-deriv", action="store_true", help="skip the kernel-derivative torque-route leg")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Brownian-increment (Lanczos) leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the other-configuration timings")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="also time the oracle on configurations 1 and 2 on the host cores (minutes)")
     args = ap.parse_args()
 
     from paper_2210_01837_gb300.replicas import Collective, rank_env, replica_seed_offset, whole_job_rate
@@ -691,6 +743,9 @@ def main():
     configs = None
     if not args.no_configs and div == 1:
         configs = configs_leg(binding, torch, dev)
+    if args.oracle_configs and rank == 0:
+        configs = dict(configs or {})
+        configs["oracle"] = oracle_configs()
 
     # ---- all-FP64 path on the same GPU -------------------------------------------------------
     fp64 = None

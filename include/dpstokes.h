@@ -179,8 +179,8 @@ typedef struct {
                                and stage, one shared buffer), 0: shared-memory-staged           */
   int32_t fft_register_cols; /* the y-FFT passes: 0 shared-memory-staged, 1 register-staged,
                                2 register-staged with cp.async prefetch, 3 with TMA prefetch   */
-  int32_t interp_variant;   /* interpolation (step 8): 1 tile gather (forces only, or spectral-curl
-                               torques with m_M = m_D), 0 a warp per particle                    */
+  int32_t interp_variant;   /* interpolation (step 8): 0 a warp per particle, 1 tile gather,
+                               2 staged gather (see dpstokes_plan_set_interp)                    */
   int32_t cheb_tensor_cores; /* Chebyshev transforms on the tensor cores (tcgen05, tf32
                                three-product split; mixed precision, nz <= 128): bit 0 the
                                forward transform, bit 1 the backward transform (spectral-curl
@@ -188,13 +188,16 @@ typedef struct {
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 
-/* Interpolation variant by hand (no counterpart in the paper): 1 the tile gather, the transpose of
- * the spread (a block per 32 x 8 tile of node columns reads each column once and adds its share of
- * every covering particle's sums to a per-tile slot; a second kernel adds a particle's slots in a
- * fixed order), 0 a warp per particle gathering its support rows.  Both compute the same sums up to
- * summation order.  DPS_ERR_INVALID_ARG for 1 where the tile gather does not apply (the
- * kernel-derivative torque route, or m_M != m_D with torques).  The warp-per-particle gather is
- * the default; the autotuner tries the tile gather where it applies. */
+/* Interpolation variant by hand (no counterpart in the paper): 0 a warp per particle gathering its
+ * support rows from global memory; 1 the tile gather, the transpose of the spread (a block per
+ * 32 x 8 tile of node columns reads each column once and adds its share of every covering
+ * particle's sums to a per-tile slot; a second kernel adds a particle's slots in a fixed order);
+ * 2 the staged gather (a block per particle bin copies the grid region its particles' supports
+ * cover into shared memory, four planes at a time, and its warps gather their particles from
+ * there).  All compute the sums of Eqs. 10-11 up to summation order.  DPS_ERR_INVALID_ARG for 1
+ * or 2 where the variant does not apply: both need forces only or spectral-curl torques with
+ * m_M = m_D; 2 needs mixed precision and supports of at most 6 nodes (m <= 5).  The staged gather
+ * is the default where it applies, else the warp per particle; the autotuner tries the others. */
 dps_status dpstokes_plan_set_interp(dps_plan_t plan, int32_t variant);
 
 /* Autotuner (no counterpart in the paper).  Times the plan's applies on the given particles (same
@@ -429,13 +432,16 @@ dps_status dpstokes_debug_run(dps_plan_t plan, int64_t n, const double* position
 dps_status dpstokes_debug_copy(dps_plan_t plan, int32_t which, void* dst, int64_t dst_bytes,
                                void* stream);
 
-/* Failure injection for tests (no counterpart in the paper).  code 1: in the next apply the forward
- * tensor-core transform withholds its matrix multiplies and their completion signals, so the
- * producers' bounded waits for a free operand stage run out (about a second): the kernel records
- * DPS_ERR_TIMEOUT in the status word (read by dpstokes_status), its blocks free their tensor memory
- * and leave, and the plan stays usable for the next apply.  The injection applies to one apply and
- * then clears itself.  code 0 clears it.  DPS_ERR_INVALID_ARG for other codes, or for code 1 on a
- * plan that does not use the tensor-core forward transform. */
+/* Failure injection and path forcing for tests (no counterpart in the paper).  code 1: in the next
+ * apply the forward tensor-core transform withholds its matrix multiplies and their completion
+ * signals, so the producers' bounded waits for a free operand stage run out (about a second): the
+ * kernel records DPS_ERR_TIMEOUT in the status word (read by dpstokes_status), its blocks free
+ * their tensor memory and leave, and the plan stays usable for the next apply.  code 2: in the
+ * next apply every bin of the staged interpolation takes its global-memory gather (the path a bin
+ * whose region does not fit in shared memory takes).  An injection applies to one apply and then
+ * clears itself.  code 0 clears it.  DPS_ERR_INVALID_ARG for other codes, for code 1 on a plan
+ * that does not use the tensor-core forward transform, or for code 2 on a plan whose
+ * interpolation variant is not 2. */
 dps_status dpstokes_debug_inject(dps_plan_t plan, int32_t code);
 
 #ifdef __cplusplus

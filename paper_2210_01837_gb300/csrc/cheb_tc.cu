@@ -735,12 +735,12 @@ void launch_cheb_fwd_tc(const Plan& p, int kx0, int w, cudaStream_t s) {
     const FwdSpec<true>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
                                 p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
                                 reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
-    launch_tc<FwdSpec<true>>(p, a, p.kt.bimg_f, kx0, w, s, p.inject);
+    launch_tc<FwdSpec<true>>(p, a, p.kt.bimg_f, kx0, w, s, p.inject == 1 ? 1 : 0);
   } else {
     const FwdSpec<false>::Args a{reinterpret_cast<const float*>(p.kt.ct), reinterpret_cast<const float*>(p.kt.dct),
                                  p.kt.npad, reinterpret_cast<const cplx<float>*>(p.grid),
                                  reinterpret_cast<cplx<float>*>(p.kt.kbuf)};
-    launch_tc<FwdSpec<false>>(p, a, p.kt.bimg_f, kx0, w, s, p.inject);
+    launch_tc<FwdSpec<false>>(p, a, p.kt.bimg_f, kx0, w, s, p.inject == 1 ? 1 : 0);
   }
 }
 

@@ -153,7 +153,7 @@ struct Plan {
   alignas(64) unsigned char col_tmap[128];  // CUtensorMap of the grid for the TMA column pass
   int col_tma_rows;     // rows per TMA box of that pass
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
-  int interp_tile;      // interpolation variant: 1 tile gather (where it applies), 0 warp per particle
+  int interp_tile;      // interpolation variant: 0 warp per particle, 1 tile gather, 2 staged grid (where they apply)
   int cheb_tc;          // forward Chebyshev transform on the tensor cores (tcgen05, mixed precision)
   int cheb_tc_bwd;      // backward Chebyshev transform on the tensor cores (spectral-curl torques)
   int cheb_tc_grid;     // persistent blocks of that kernel
@@ -266,6 +266,9 @@ template <typename T> void launch_interp(const Plan& p, int64_t n, double* U, do
 // the tile-gather interpolation: fields it sums for this geometry (0: it does not apply) and the
 // values of its partial-sum buffer for max_n particles
 int interp_tile_fields(const Geometry& g);
+// the staged-grid interpolation (variant 2): fields it sums for this geometry and transform
+// precision (tsize 32-bit words per value), 0 where it does not apply
+int interp_stage_fields(const Geometry& g, int tsize);
 size_t interp_tile_values(const Geometry& g, int64_t max_n);
 template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s);

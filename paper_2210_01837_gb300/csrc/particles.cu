@@ -21,6 +21,7 @@
 // the records also hold the truncated derivative phi' of the dipole kernel in x, y and (imaged) z,
 // the spread adds (1/2) grad Delta_D x tau to the force density, and interpolation returns
 // Omega_j = (1/2) h^2 sum_g w_c u(x_g) x grad Delta_D(x_g - r_j).
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -1257,6 +1258,212 @@ __global__ void __launch_bounds__(256) interp_pair_kernel(Geometry g, int64_t n,
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Interpolation with the grid staged in shared memory (float, supports of at most 6 nodes): a
+// block per particle bin.  The particles of a bin (32 x 8 nodes by position) have their supports'
+// first nodes within one node of each other per 32-node run, so their supports lie in a region of
+// at most 40 x 16 node columns; the block copies that region of the occupied planes into shared
+// memory, four planes at a time (16-byte cp.async pieces of whole rows, coalesced), and each warp
+// gathers its particles from there: lane group g (6 x-lanes) takes plane g of the four, walks the 6
+// support rows of that plane and adds the 6 fields (U from fields 0..2 with the monopole weights,
+// Omega from fields 3..5 with the dipole weights; forces only: U from fields 0..2).  A warp holds
+// the sums of up to 4 particles across the chunks and reduces them over its lanes at the end.
+// Where a bin's region would not fit (it cannot with the bins' construction, but the kernel checks)
+// the block gathers from global memory instead, with the same lane walk.
+// Shared layout: [field][plane of the chunk][row][44]; rows of 44 values (11 pieces of 16 bytes)
+// and planes 712 values apart, 8 banks apart modulo 32, so that the four lane groups reading the
+// same (row, column) of four planes hit 24 distinct banks.
+// ---------------------------------------------------------------------------------------------
+constexpr int kIsPX = 6;                  // support width the staged kernel handles
+constexpr int kIsGroups = 4;              // lane groups = planes per chunk
+constexpr int kIsSX = 44;                 // staged row length (values)
+constexpr int kIsPieces = kIsSX / 4;      // 16-byte pieces per row
+constexpr int kIsRows = 16;               // staged rows per plane (8 bin rows + support + margin)
+constexpr int kIsPS = 712;                // plane stride (values): 704 rounded up to 8 mod 32
+constexpr int kIsFS = kIsGroups * kIsPS;  // field stride (values)
+constexpr int kIsSlots = 4;               // particles per warp per batch
+constexpr int kIsThreads = 256;
+static_assert(kIsPS >= kIsSX * kIsRows && kIsPS % 32 == 8 && kIsPS % 4 == 0, "staged plane layout");
+static_assert(kIsGroups * kIsPX <= 32, "lane groups");
+
+__host__ __device__ constexpr size_t interp_stage_smem(int nf) { return (size_t)nf * kIsFS * sizeof(float); }
+
+// offset of node v from t0 on a periodic axis of n nodes, in (-n/2, n/2]
+__device__ __forceinline__ int rel_node(int v, int t0, int n) {
+  int d = v - t0;
+  if (2 * d > n) d -= n;
+  else if (2 * d <= -n) d += n;
+  return d;
+}
+
+template <int NF>
+__global__ void __launch_bounds__(kIsThreads, 2)
+interp_stage_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
+                    const int* __restrict__ sorted, const float* __restrict__ grid, const float* __restrict__ wz,
+                    double* __restrict__ U, double* __restrict__ W, int force_global) {
+  constexpr int PX = kIsPX, NG = kIsGroups, ZC = kIsGroups, SX = kIsSX, FS = kIsFS, PW = kIsSlots;
+  extern __shared__ __align__(16) float sg[];  // [NF][ZC][kIsPS]
+  __shared__ int s_b[6];                       // bounds: ox min/max, oy min/max, z begin/end
+  __shared__ int s_xo[kIsSX];                  // wrapped x of each staged column
+  __shared__ int s_yo[kIsRows];                // wrapped y of each staged row, times the row length
+  const int b = blockIdx.x;
+  const int p0 = bin_start[b], cnt = bin_start[b + 1] - p0;
+  if (cnt <= 0) return;
+  const int tx0 = (b % g.nbx) * kTileX, ty0 = (b / g.nbx) * kTileY;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = lane / PX, lx = lane - grp * PX;
+  const bool lane_on = grp < NG;
+  const int rw = g.rec_words, stride = 2 * g.pxc + g.lzc, px = g.kM.px;
+  const int rowlen = 2 * g.pitch;
+  const size_t plane = (size_t)g.ny * rowlen, fstride = plane * g.nz;
+  if (tid < 6) s_b[tid] = (tid & 1) ? INT_MIN : INT_MAX;
+  __syncthreads();
+  for (int i = tid; i < cnt; i += kIsThreads) {
+    const int4 hd = *reinterpret_cast<const int4*>(rec + (size_t)sorted[p0 + i] * rw);
+    if (hd.w <= 0) continue;
+    const int ox = rel_node(hd.x, tx0, g.nx), oy = rel_node(hd.y, ty0, g.ny);
+    atomicMin(&s_b[0], ox);
+    atomicMax(&s_b[1], ox);
+    atomicMin(&s_b[2], oy);
+    atomicMax(&s_b[3], oy);
+    atomicMin(&s_b[4], hd.z);
+    atomicMax(&s_b[5], hd.z + hd.w);
+  }
+  __syncthreads();
+  const int zlo = s_b[4], zhi = s_b[5];
+  const bool any = zhi > zlo;
+  // staged region: columns [xlo4, xlo4 + SX) (xlo4 = first support column rounded down to a
+  // 16-byte piece), rows [ylo, ylo + rh)
+  const int xlo = any ? tx0 + s_b[0] : 0;
+  const int xlo4 = xlo >= 0 ? (xlo & ~3) : -((-xlo + 3) & ~3);
+  const int xoff = xlo4 - tx0;
+  const int oymin = any ? s_b[2] : 0;
+  const int rh = any ? s_b[3] - oymin + PX : 0;
+  const bool staged = any && !force_global && (s_b[1] + PX - xoff <= SX) && (rh <= kIsRows) &&
+                      (g.nx % 4 == 0) && (g.kM.px <= PX);
+  if (staged) {
+    if (tid < SX) {
+      int x = (xlo4 + tid) % g.nx;
+      s_xo[tid] = x < 0 ? x + g.nx : x;
+    }
+    if (tid < kIsRows) {
+      int y = (ty0 + oymin + tid) % g.ny;
+      s_yo[tid] = (y < 0 ? y + g.ny : y) * rowlen;
+    }
+    __syncthreads();
+  }
+  const float h2f = (float)(g.h * g.h);
+  // a warp's particles of one batch: i = base + warp + 8 q
+  for (int base = 0; base < cnt; base += 8 * PW) {
+    float acc[PW][NF];
+#pragma unroll
+    for (int q = 0; q < PW; ++q)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) acc[q][f] = 0.f;
+    if (staged) {
+      for (int zb = zlo; zb < zhi; zb += ZC) {
+        __syncthreads();  // the previous chunk's readers are done
+        // rows (f, zz, yy) of the chunk: a warp copies two rows per step (22 lanes, 11 pieces each)
+        const int sub = lane / kIsPieces, pc = lane - sub * kIsPieces;
+        if (sub < 2) {
+          for (int r = 2 * warp + sub; r < NF * ZC * kIsRows; r += 16) {
+            const int yy = r % kIsRows, zz = (r / kIsRows) % ZC, f = r / (kIsRows * ZC);
+            if (yy >= rh || zb + zz >= zhi) continue;
+            const float* src = grid + (size_t)f * fstride + (size_t)(zb + zz) * plane + s_yo[yy] + s_xo[4 * pc];
+            cp_async16(sg + f * FS + zz * kIsPS + yy * SX + 4 * pc, src);
+          }
+        }
+        cp_commit();
+        cp_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PW; ++q) {
+          const int i = base + warp + 8 * q;
+          if (i >= cnt || !lane_on) continue;
+          const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
+          const int4 hd = *reinterpret_cast<const int4*>(r);
+          const int c = zb + grp;
+          if (c < hd.z || c >= hd.z + hd.w) continue;
+          const int iz = c - hd.z;
+          const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
+          const float* pd = pm + stride;
+          const float wc = wz[c];
+          const bool xon = lx < px;  // lanes past the support read a staged column with weight 0
+          const float mzx = xon ? pm[2 * g.pxc + iz] * wc * pm[lx] : 0.f;
+          const float dzx = (NF == 6 && xon) ? pd[2 * g.pxc + iz] * wc * pd[lx] : 0.f;
+          const int ox = rel_node(hd.x, tx0, g.nx), oy = rel_node(hd.y, ty0, g.ny);
+          const float* sp = sg + grp * kIsPS + (oy - oymin) * SX + (ox - xoff) + lx;
+#pragma unroll
+          for (int iy = 0; iy < PX; ++iy) {
+            if (iy < px) {
+              const float wm = mzx * pm[g.pxc + iy];
+#pragma unroll
+              for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
+              if (NF == 6) {
+                const float wd = dzx * pd[g.pxc + iy];
+#pragma unroll
+                for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
+              }
+            }
+          }
+        }
+      }
+    } else if (any) {
+      // global-memory gather with the same lane walk (plane c = z0 + g, g + NG, ...)
+#pragma unroll
+      for (int q = 0; q < PW; ++q) {
+        const int i = base + warp + 8 * q;
+        if (i >= cnt || !lane_on) continue;
+        const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
+        const int4 hd = *reinterpret_cast<const int4*>(r);
+        const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
+        const float* pd = pm + stride;
+        int x = hd.x + lx;
+        if (x >= g.nx) x -= g.nx;
+        const bool xon = lx < px;
+        for (int iz = grp; iz < hd.w; iz += NG) {
+          const int c = hd.z + iz;
+          const float wc = wz[c];
+          const float mzx = xon ? pm[2 * g.pxc + iz] * wc * pm[lx] : 0.f;
+          const float dzx = (NF == 6 && xon) ? pd[2 * g.pxc + iz] * wc * pd[lx] : 0.f;
+          for (int iy = 0; iy < px; ++iy) {
+            int y = hd.y + iy;
+            if (y >= g.ny) y -= g.ny;
+            const float* gp = grid + (size_t)c * plane + (size_t)y * rowlen + (xon ? x : 0);
+            const float wm = mzx * pm[g.pxc + iy];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) acc[q][f] += gp[(size_t)f * fstride] * wm;
+            if (NF == 6) {
+              const float wd = dzx * pd[g.pxc + iy];
+#pragma unroll
+              for (int f = 3; f < NF; ++f) acc[q][f] += gp[(size_t)f * fstride] * wd;
+            }
+          }
+        }
+      }
+    }
+    // sums over the warp's lanes; lane 0 writes U (and Omega) of each of its particles
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+      const int i = base + warp + 8 * q;
+      if (i >= cnt) continue;  // warp-uniform
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[q][f] += __shfl_xor_sync(0xffffffffu, acc[q][f], off);
+      if (lane == 0) {
+        const int64_t j = sorted[p0 + i];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) U[3 * j + f] = widen_bits(acc[q][f] * h2f);
+        if (NF == 6) {
+#pragma unroll
+          for (int f = 0; f < 3; ++f) W[3 * j + f] = widen_bits(acc[q][3 + f] * h2f);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -1410,7 +1617,8 @@ int spread_prepare(Plan& p) {
   if (!(allow_smem(spread_kernel<T, 1, ZC6>) && allow_smem(spread_kernel<T, 0, ZC3>) &&
         allow_smem(spread_kernel<T, 2, ZC3>) && allow_smem(spread_kernel<T, 3, ZC3>) &&
         allow_smem(spread_kernel<T, 4, ZCS>) && allow_smem(interp_tile_kernel<T, 4, ZI6>) &&
-        allow_smem(interp_tile_kernel<T, 0, ZI3>)))
+        allow_smem(interp_tile_kernel<T, 0, ZI3>) && allow_smem(interp_stage_kernel<6>) &&
+        allow_smem(interp_stage_kernel<3>)))
     return 0;
   int dev = 0, optin = 0;
   cudaFuncAttributes fa, fi;  // the spread modes declare the same static shared arrays; the tile
@@ -1459,6 +1667,13 @@ int interp_tile_fields(const Geometry& g) {
   return 3;
 }
 
+// the staged-grid interpolation applies (float plans; supports of at most kIsPX nodes; forces only
+// or spectral-curl torques with coinciding supports); returns the fields it sums (0: not applicable)
+int interp_stage_fields(const Geometry& g, int tsize) {
+  if (tsize != 1 || g.pxc > kIsPX) return 0;
+  return interp_tile_fields(g);
+}
+
 // tiles a support can overlap in x and y (a partial last tile can add one) and the partial-sum
 // buffer of the tile-gather interpolation, in values of the transform precision
 void interp_tile_slots(const Geometry& g, int& sxn, int& syn) {
@@ -1482,7 +1697,21 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
   const T* grid = reinterpret_cast<const T*>(p.grid);
   const T* wz = reinterpret_cast<const T*>(p.tab.wz);
   const int nf = interp_tile_fields(p.g);
-  if (p.interp_tile && nf > 0 && p.ipart) {
+  if constexpr (sizeof(T) == 4) {
+    const int ns = interp_stage_fields(p.g, 1);
+    if (p.interp_tile == 2 && ns > 0) {
+      const unsigned bins = (unsigned)(p.g.nbx * p.g.nby);
+      const int force_global = p.inject == 2 ? 1 : 0;  // test hook: every bin takes the global gather
+      if (ns == 6)
+        interp_stage_kernel<6><<<bins, kIsThreads, interp_stage_smem(6), s>>>(p.g, p.records, p.bin_start, p.sorted,
+                                                                            grid, wz, U, W, force_global);
+      else
+        interp_stage_kernel<3><<<bins, kIsThreads, interp_stage_smem(3), s>>>(p.g, p.records, p.bin_start, p.sorted,
+                                                                            grid, wz, U, W, force_global);
+      return;
+    }
+  }
+  if (p.interp_tile == 1 && nf > 0 && p.ipart) {
     int sxn, syn;
     interp_tile_slots(p.g, sxn, syn);
     T* part = reinterpret_cast<T*>(p.ipart);

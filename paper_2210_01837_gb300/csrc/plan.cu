@@ -343,13 +343,19 @@ dps_status allocate(Plan* p) {
       if (ft == DPS_ERR_CUDA) return ft;
     }
   }
-  // the tile-gather interpolation's partial sums (where it applies); the warp-per-particle gather
-  // stays the default (on the 1M-roller workload 9.7 against 8.5 ms), the autotuner tries both
+  // the tile-gather interpolation's partial sums (where it applies; a variant the autotuner tries)
   if (const size_t iv = interp_tile_values(g, p->max_n)) {
     if (!alloc(&p->ipart, iv * sizeof(T))) return DPS_ERR_OOM;
   }
-  p->interp_tile = 0;
-  if (const char* e = getenv("DPS_INTERP_TILE")) p->interp_tile = p->ipart && atoi(e) != 0;
+  // default: the staged gather where it applies, else a warp per particle; the autotuner tries the
+  // others
+  p->interp_tile = interp_stage_fields(g, (int)(sizeof(T) / 4)) > 0 ? 2 : 0;
+  if (const char* e = getenv("DPS_INTERP_TILE")) {
+    p->interp_tile = 0;
+    const int v = atoi(e);
+    if (v == 1 && p->ipart) p->interp_tile = 1;
+    if (v == 2 && interp_stage_fields(g, (int)(sizeof(T) / 4)) > 0) p->interp_tile = 2;
+  }
   if (!alloc((void**)&p->stage_in, nmax * 9 * sizeof(double))) return DPS_ERR_OOM;
   if (!alloc((void**)&p->stage_out, nmax * 6 * sizeof(double))) return DPS_ERR_OOM;
   if (!fft_smem_ok<T>(*p)) return DPS_ERR_INVALID_ARG;
@@ -623,7 +629,7 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   // init, records, 3 binning, spread, x pass, 5 per column chunk, x pass, interpolation (+ its
   // finishing kernel for the tile gather)
   // (+ the B-operand image kernel before each tensor-core transform)
-  out->launches_per_apply = 9 + 5 * p->nchunks + ((p->interp_tile && p->ipart) ? 1 : 0) +
+  out->launches_per_apply = 9 + 5 * p->nchunks + ((p->interp_tile == 1 && p->ipart) ? 1 : 0) +
                             p->nchunks * ((p->cheb_tc ? 1 : 0) + (p->cheb_tc_bwd ? 1 : 0));
   out->nchunks = p->nchunks;
   out->fft_col_width = 1 << p->col_lcw;
@@ -637,15 +643,17 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
 
 dps_status dpstokes_debug_inject(dps_plan_t plan, int32_t code) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || code < 0 || code > 1 || (code == 1 && !p->cheb_tc)) return DPS_ERR_INVALID_ARG;
+  if (!p || code < 0 || code > 2 || (code == 1 && !p->cheb_tc) || (code == 2 && p->interp_tile != 2))
+    return DPS_ERR_INVALID_ARG;
   p->inject = code;
   return DPS_OK;
 }
 
 dps_status dpstokes_plan_set_interp(dps_plan_t plan, int32_t variant) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || (variant != 0 && variant != 1)) return DPS_ERR_INVALID_ARG;
+  if (!p || variant < 0 || variant > 2) return DPS_ERR_INVALID_ARG;
   if (variant == 1 && !p->ipart) return DPS_ERR_INVALID_ARG;
+  if (variant == 2 && dps::interp_stage_fields(p->g, p->precision == DPS_FP64 ? 2 : 1) == 0) return DPS_ERR_INVALID_ARG;
   p->interp_tile = variant;
   return DPS_OK;
 }
@@ -713,12 +721,18 @@ dps_status dpstokes_plan_autotune(dps_plan_t plan, int64_t n, const double* posi
   }
   dps::set_chunks(*p, best_j);
   // 4. interpolation variant (tile gather or warp per particle), where both apply
-  if (p->ipart && st == DPS_OK) {
+  {
     const int inc = p->interp_tile;
-    p->interp_tile = 1 - inc;
-    st = measure(&t);
-    if (!(st == DPS_OK && better(t))) p->interp_tile = inc;
-    else best = t;
+    int best_v = inc;
+    for (int v = 0; v < 3 && st == DPS_OK; ++v) {
+      if (v == inc || (v == 1 && !p->ipart) ||
+          (v == 2 && dps::interp_stage_fields(p->g, p->precision == DPS_FP64 ? 2 : 1) == 0))
+        continue;
+      p->interp_tile = v;
+      st = measure(&t);
+      if (st == DPS_OK && better(t)) { best = t; best_v = v; }
+    }
+    p->interp_tile = best_v;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
