@@ -151,11 +151,14 @@ struct Plan {
                         // 2 (columns) register-staged with cp.async prefetch, 3 (columns) the same with
                         // TMA box loads
   alignas(64) unsigned char col_tmap[128];  // CUtensorMap of the grid for the TMA column pass
+  alignas(64) unsigned char interp_tmap[128];  // CUtensorMap of the grid for the staged interpolation
+  int interp_tma;       // interp_tmap holds a valid map
   int col_tma_rows;     // rows per TMA box of that pass
   int bvp_blocks_max;   // persistent solve blocks the workspace was allocated for
   int interp_tile;      // interpolation variant: 0 warp per particle, 1 tile gather, 2 staged grid (where they apply)
   int cheb_tc;          // forward Chebyshev transform on the tensor cores (tcgen05, mixed precision)
   int cheb_tc_bwd;      // backward Chebyshev transform on the tensor cores (spectral-curl torques)
+  int cheb_tc_bwd_parts;  // launches of the backward transform (output planes split beyond 96 nodes)
   int cheb_tc_grid;     // persistent blocks of that kernel
   int inject;           // failure injection of the next apply (dpstokes_debug_inject)
   void* ipart;          // partial sums of the tile-gather interpolation [slot][field][max_n] T
@@ -269,6 +272,9 @@ int interp_tile_fields(const Geometry& g);
 // the staged-grid interpolation (variant 2): fields it sums for this geometry and transform
 // precision (tsize 32-bit words per value), 0 where it does not apply
 int interp_stage_fields(const Geometry& g, int tsize);
+// encodes the staged interpolation's tensor map of the grid (float plans); false when the driver's
+// encoder cannot be obtained or refuses the map
+bool encode_interp_tmap(Plan& p);
 size_t interp_tile_values(const Geometry& g, int64_t max_n);
 template <typename T> void launch_fft_rows(const Plan& p, int dir, cudaStream_t s);
 template <typename T> void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s);

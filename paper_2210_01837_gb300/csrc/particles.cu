@@ -21,6 +21,8 @@
 // the records also hold the truncated derivative phi' of the dipole kernel in x, y and (imaged) z,
 // the spread adds (1/2) grad Delta_D x tau to the force density, and interpolation returns
 // Omega_j = (1/2) h^2 sum_g w_c u(x_g) x grad Delta_D(x_g - r_j).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <limits.h>
 #include <math.h>
 
@@ -1261,32 +1263,40 @@ __global__ void __launch_bounds__(256) interp_pair_kernel(Geometry g, int64_t n,
 // ---------------------------------------------------------------------------------------------
 // Interpolation with the grid staged in shared memory (float, supports of at most 6 nodes): a
 // block per particle bin.  The particles of a bin (32 x 8 nodes by position) have their supports'
-// first nodes within one node of each other per 32-node run, so their supports lie in a region of
-// at most 40 x 16 node columns; the block copies that region of the occupied planes into shared
-// memory, four planes at a time (16-byte cp.async pieces of whole rows, coalesced), and each warp
-// gathers its particles from there: lane group g (6 x-lanes) takes plane g of the four, walks the 6
-// support rows of that plane and adds the 6 fields (U from fields 0..2 with the monopole weights,
-// Omega from fields 3..5 with the dipole weights; forces only: U from fields 0..2).  A warp holds
-// the sums of up to 4 particles across the chunks and reduces them over its lanes at the end.
-// Where a bin's region would not fit (it cannot with the bins' construction, but the kernel checks)
-// the block gathers from global memory instead, with the same lane walk.
-// Shared layout: [field][plane of the chunk][row][44]; rows of 44 values (11 pieces of 16 bytes)
-// and planes 712 values apart, 8 banks apart modulo 32, so that the four lane groups reading the
-// same (row, column) of four planes hit 24 distinct banks.
+// first nodes within 33 x 9 of each other, so their supports lie in a region of at most 38 x 14
+// node columns; the block brings that region of the occupied planes into shared memory, four planes
+// at a time, and each warp gathers its particles from there: lane group g (6 x-lanes) takes plane
+// g of the four, walks the 6 support rows of that plane and adds the 6 fields (U from fields 0..2
+// with the monopole weights, Omega from fields 3..5 with the dipole weights; forces only: U from
+// fields 0..2).  A warp holds the sums of its 2 particles of a batch of 32 across the chunks and
+// reduces them over its lanes at the end of the batch.
+// Staging: where the region does not cross the periodic boundary, one TMA box load per chunk
+// (44 x 14 x 4 x fields of the grid's tensor map) into one of two buffers, the next chunk's load
+// in flight while the warps read the current one; each wait is bounded (about a second; on expiry
+// the block records kStatTimeout, waits again, bounded, for its loads in flight and leaves).  At the
+// boundary the block copies the wrapped rows with 16-byte cp.async pieces instead.  Where a bin's
+// region would not fit (it cannot with the bins' construction, but the kernel checks) the block
+// gathers from global memory with the same lane walk.
+// Shared layout per buffer: [field][plane of the chunk][row (14)][44]: planes 616 values apart, 8
+// banks apart modulo 32, so that the four lane groups reading the same (row, column) of four
+// planes hit 24 distinct banks.
 // ---------------------------------------------------------------------------------------------
-constexpr int kIsPX = 6;                  // support width the staged kernel handles
-constexpr int kIsGroups = 4;              // lane groups = planes per chunk
-constexpr int kIsSX = 44;                 // staged row length (values)
-constexpr int kIsPieces = kIsSX / 4;      // 16-byte pieces per row
-constexpr int kIsRows = 16;               // staged rows per plane (8 bin rows + support + margin)
-constexpr int kIsPS = 712;                // plane stride (values): 704 rounded up to 8 mod 32
-constexpr int kIsFS = kIsGroups * kIsPS;  // field stride (values)
-constexpr int kIsSlots = 4;               // particles per warp per batch
-constexpr int kIsThreads = 256;
-static_assert(kIsPS >= kIsSX * kIsRows && kIsPS % 32 == 8 && kIsPS % 4 == 0, "staged plane layout");
+constexpr int kIsPX = 6;                    // support width the staged kernel handles
+constexpr int kIsGroups = 4;                // lane groups = planes per chunk
+constexpr int kIsSX = 44;                   // staged row length (values)
+constexpr int kIsPieces = kIsSX / 4;        // 16-byte pieces per row
+constexpr int kIsRows = 14;                 // staged rows per plane (9 first-node rows + 5)
+constexpr int kIsPS = kIsSX * kIsRows;      // plane stride (values)
+constexpr int kIsFS = kIsGroups * kIsPS;    // field stride (values)
+constexpr int kIsSlots = 2;                 // particles per warp per batch
+constexpr int kIsThreads = 512;
+constexpr int kIsWarps = kIsThreads / 32;
+constexpr int kIsBatch = kIsWarps * kIsSlots;
+static_assert(kIsPS % 32 == 8 && (kIsSX * 4) % 16 == 0, "staged plane layout");
 static_assert(kIsGroups * kIsPX <= 32, "lane groups");
 
-__host__ __device__ constexpr size_t interp_stage_smem(int nf) { return (size_t)nf * kIsFS * sizeof(float); }
+__host__ __device__ constexpr size_t interp_stage_buf(int nf) { return (size_t)nf * kIsFS * sizeof(float); }
+__host__ __device__ constexpr size_t interp_stage_smem(int nf) { return 2 * interp_stage_buf(nf) + 128; }
 
 // offset of node v from t0 on a periodic axis of n nodes, in (-n/2, n/2]
 __device__ __forceinline__ int rel_node(int v, int t0, int n) {
@@ -1296,16 +1306,50 @@ __device__ __forceinline__ int rel_node(int v, int t0, int n) {
   return d;
 }
 
+__device__ __forceinline__ void is_bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void is_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity; false after about 2^31 cycles
+__device__ __forceinline__ bool is_wait(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+__device__ __forceinline__ void is_tma_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int f, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(smem_u32(bar))
+      : "memory");
+}
+
 template <int NF>
-__global__ void __launch_bounds__(kIsThreads, 2)
-interp_stage_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
-                    const int* __restrict__ sorted, const float* __restrict__ grid, const float* __restrict__ wz,
-                    double* __restrict__ U, double* __restrict__ W, int force_global) {
+__global__ void __launch_bounds__(kIsThreads, 1)
+interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geometry g, const uint32_t* __restrict__ rec,
+                    const int* __restrict__ bin_start, const int* __restrict__ sorted, const float* __restrict__ grid,
+                    const float* __restrict__ wz, double* __restrict__ U, double* __restrict__ W, int force_global,
+                    int* __restrict__ status) {
   constexpr int PX = kIsPX, NG = kIsGroups, ZC = kIsGroups, SX = kIsSX, FS = kIsFS, PW = kIsSlots;
-  extern __shared__ __align__(16) float sg[];  // [NF][ZC][kIsPS]
-  __shared__ int s_b[6];                       // bounds: ox min/max, oy min/max, z begin/end
-  __shared__ int s_xo[kIsSX];                  // wrapped x of each staged column
-  __shared__ int s_yo[kIsRows];                // wrapped y of each staged row, times the row length
+  constexpr int BUFV = NF * kIsFS;  // values per chunk buffer
+  extern __shared__ __align__(128) unsigned char is_raw[];
+  // two chunk buffers, 128-byte aligned (TMA destinations)
+  float* const sg = reinterpret_cast<float*>(is_raw + ((128u - (smem_u32(is_raw) & 127u)) & 127u));
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_b[6];           // bounds: ox min/max, oy min/max, z begin/end
+  __shared__ int s_xo[kIsSX];      // wrapped x of each staged column (cp.async path)
+  __shared__ int s_yo[kIsRows];    // wrapped y of each staged row times the row length
+  __shared__ int s_fail;           // a bounded wait ran out
   const int b = blockIdx.x;
   const int p0 = bin_start[b], cnt = bin_start[b + 1] - p0;
   if (cnt <= 0) return;
@@ -1317,6 +1361,7 @@ interp_stage_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __r
   const int rowlen = 2 * g.pitch;
   const size_t plane = (size_t)g.ny * rowlen, fstride = plane * g.nz;
   if (tid < 6) s_b[tid] = (tid & 1) ? INT_MIN : INT_MAX;
+  if (tid == 0) s_fail = 0;
   __syncthreads();
   for (int i = tid; i < cnt; i += kIsThreads) {
     const int4 hd = *reinterpret_cast<const int4*>(rec + (size_t)sorted[p0 + i] * rw);
@@ -1338,81 +1383,121 @@ interp_stage_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __r
   const int xlo4 = xlo >= 0 ? (xlo & ~3) : -((-xlo + 3) & ~3);
   const int xoff = xlo4 - tx0;
   const int oymin = any ? s_b[2] : 0;
+  const int ylo = ty0 + oymin;
   const int rh = any ? s_b[3] - oymin + PX : 0;
   const bool staged = any && !force_global && (s_b[1] + PX - xoff <= SX) && (rh <= kIsRows) &&
                       (g.nx % 4 == 0) && (g.kM.px <= PX);
-  if (staged) {
+  // TMA where the columns and rows read lie inside the grid (no periodic wrap)
+  const bool tma = staged && use_tma && xlo4 >= 0 && tx0 + s_b[1] + PX <= g.nx && ylo >= 0 && ylo + rh <= g.ny;
+  if (staged && !tma) {
     if (tid < SX) {
       int x = (xlo4 + tid) % g.nx;
       s_xo[tid] = x < 0 ? x + g.nx : x;
     }
     if (tid < kIsRows) {
-      int y = (ty0 + oymin + tid) % g.ny;
+      int y = (ylo + tid) % g.ny;
       s_yo[tid] = (y < 0 ? y + g.ny : y) * rowlen;
     }
-    __syncthreads();
   }
+  if (tma && tid == 0) {
+    is_bar_init(&s_bar[0]);
+    is_bar_init(&s_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
   const float h2f = (float)(g.h * g.h);
-  // a warp's particles of one batch: i = base + warp + 8 q
-  for (int base = 0; base < cnt; base += 8 * PW) {
-    float acc[PW][NF];
+  const int nch = staged ? (zhi - zlo + ZC - 1) / ZC : 1;
+  const int nbatch = (cnt + kIsBatch - 1) / kIsBatch;
+  const int total = nbatch * nch;  // (batch, chunk) steps
+  constexpr unsigned kBoxBytes = (unsigned)interp_stage_buf(NF);
+  auto issue = [&](int step) {  // thread 0: the TMA load of step's chunk into buffer step & 1
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of the buffer came first
+    is_expect_tx(&s_bar[step & 1], kBoxBytes);
+    is_tma_4d(sg + (step & 1) * BUFV, &tmap, xlo4, ylo, zlo + (step % nch) * ZC, 0, &s_bar[step & 1]);
+  };
+  if (tma && tid == 0) {
+    issue(0);
+    if (total > 1) issue(1);
+  }
+  float acc[PW][NF];
+  for (int step = 0; step < total; ++step) {
+    const int batch = step / nch, k = step - batch * nch;
+    const int base = batch * kIsBatch;
+    if (k == 0) {
 #pragma unroll
-    for (int q = 0; q < PW; ++q)
+      for (int q = 0; q < PW; ++q)
 #pragma unroll
-      for (int f = 0; f < NF; ++f) acc[q][f] = 0.f;
-    if (staged) {
-      for (int zb = zlo; zb < zhi; zb += ZC) {
-        __syncthreads();  // the previous chunk's readers are done
-        // rows (f, zz, yy) of the chunk: a warp copies two rows per step (22 lanes, 11 pieces each)
-        const int sub = lane / kIsPieces, pc = lane - sub * kIsPieces;
-        if (sub < 2) {
-          for (int r = 2 * warp + sub; r < NF * ZC * kIsRows; r += 16) {
-            const int yy = r % kIsRows, zz = (r / kIsRows) % ZC, f = r / (kIsRows * ZC);
-            if (yy >= rh || zb + zz >= zhi) continue;
-            const float* src = grid + (size_t)f * fstride + (size_t)(zb + zz) * plane + s_yo[yy] + s_xo[4 * pc];
-            cp_async16(sg + f * FS + zz * kIsPS + yy * SX + 4 * pc, src);
-          }
+        for (int f = 0; f < NF; ++f) acc[q][f] = 0.f;
+    }
+    const float* sb = sg + (step & 1) * BUFV;
+    if (tma) {
+      if (!is_wait(&s_bar[step & 1], (unsigned)(step >> 1) & 1u)) s_fail = 1;
+      __syncthreads();
+      if (s_fail) {
+        if (tid == 0) {
+          atomicOr(status, kStatTimeout);
+          // loads still in flight: this step's (if its wait ran out) and the next one's
+          is_wait(&s_bar[step & 1], (unsigned)(step >> 1) & 1u);
+          if (step + 1 < total) is_wait(&s_bar[(step + 1) & 1], (unsigned)((step + 1) >> 1) & 1u);
         }
-        cp_commit();
-        cp_wait_all();
         __syncthreads();
+        return;
+      }
+    } else if (staged) {
+      __syncthreads();  // the readers of this buffer two steps ago are done
+      const int zb = zlo + k * ZC;
+      // rows (f, zz, yy) of the chunk: a warp copies two rows per step (22 lanes, 11 pieces each)
+      const int sub = lane / kIsPieces, pc = lane - sub * kIsPieces;
+      if (sub < 2) {
+        for (int r = 2 * warp + sub; r < NF * ZC * kIsRows; r += 2 * kIsWarps) {
+          const int yy = r % kIsRows, zz = (r / kIsRows) % ZC, f = r / (kIsRows * ZC);
+          if (yy >= rh || zb + zz >= zhi) continue;
+          const float* src = grid + (size_t)f * fstride + (size_t)(zb + zz) * plane + s_yo[yy] + s_xo[4 * pc];
+          cp_async16(const_cast<float*>(sb) + f * FS + zz * kIsPS + yy * SX + 4 * pc, src);
+        }
+      }
+      cp_commit();
+      cp_wait_all();
+      __syncthreads();
+    }
+    if (staged) {
+      const int zb = zlo + k * ZC;
 #pragma unroll
-        for (int q = 0; q < PW; ++q) {
-          const int i = base + warp + 8 * q;
-          if (i >= cnt || !lane_on) continue;
-          const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
-          const int4 hd = *reinterpret_cast<const int4*>(r);
-          const int c = zb + grp;
-          if (c < hd.z || c >= hd.z + hd.w) continue;
-          const int iz = c - hd.z;
-          const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
-          const float* pd = pm + stride;
-          const float wc = wz[c];
-          const bool xon = lx < px;  // lanes past the support read a staged column with weight 0
-          const float mzx = xon ? pm[2 * g.pxc + iz] * wc * pm[lx] : 0.f;
-          const float dzx = (NF == 6 && xon) ? pd[2 * g.pxc + iz] * wc * pd[lx] : 0.f;
-          const int ox = rel_node(hd.x, tx0, g.nx), oy = rel_node(hd.y, ty0, g.ny);
-          const float* sp = sg + grp * kIsPS + (oy - oymin) * SX + (ox - xoff) + lx;
+      for (int q = 0; q < PW; ++q) {
+        const int i = base + warp + kIsWarps * q;
+        if (i >= cnt || !lane_on) continue;
+        const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
+        const int4 hd = *reinterpret_cast<const int4*>(r);
+        const int c = zb + grp;
+        if (c < hd.z || c >= hd.z + hd.w) continue;
+        const int iz = c - hd.z;
+        const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
+        const float* pd = pm + stride;
+        const float wc = wz[c];
+        const bool xon = lx < px;  // lanes past the support read a staged column with weight 0
+        const float mzx = xon ? pm[2 * g.pxc + iz] * wc * pm[lx] : 0.f;
+        const float dzx = (NF == 6 && xon) ? pd[2 * g.pxc + iz] * wc * pd[lx] : 0.f;
+        const int ox = rel_node(hd.x, tx0, g.nx), oy = rel_node(hd.y, ty0, g.ny);
+        const float* sp = sb + grp * kIsPS + (oy - oymin) * SX + (ox - xoff) + lx;
 #pragma unroll
-          for (int iy = 0; iy < PX; ++iy) {
-            if (iy < px) {
-              const float wm = mzx * pm[g.pxc + iy];
+        for (int iy = 0; iy < PX; ++iy) {
+          if (iy < px) {
+            const float wm = mzx * pm[g.pxc + iy];
 #pragma unroll
-              for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
-              if (NF == 6) {
-                const float wd = dzx * pd[g.pxc + iy];
+            for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
+            if (NF == 6) {
+              const float wd = dzx * pd[g.pxc + iy];
 #pragma unroll
-                for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
-              }
+              for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
             }
           }
         }
       }
     } else if (any) {
-      // global-memory gather with the same lane walk (plane c = z0 + g, g + NG, ...)
+      // global-memory gather with the same lane walk (planes hd.z + g, g + NG, ...)
 #pragma unroll
       for (int q = 0; q < PW; ++q) {
-        const int i = base + warp + 8 * q;
+        const int i = base + warp + kIsWarps * q;
         if (i >= cnt || !lane_on) continue;
         const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
         const int4 hd = *reinterpret_cast<const int4*>(r);
@@ -1442,24 +1527,30 @@ interp_stage_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __r
         }
       }
     }
-    // sums over the warp's lanes; lane 0 writes U (and Omega) of each of its particles
+    if (k == nch - 1) {
+      // sums over the warp's lanes; lane 0 writes U (and Omega) of each of its particles
 #pragma unroll
-    for (int q = 0; q < PW; ++q) {
-      const int i = base + warp + 8 * q;
-      if (i >= cnt) continue;  // warp-uniform
+      for (int q = 0; q < PW; ++q) {
+        const int i = base + warp + kIsWarps * q;
+        if (i >= cnt) continue;  // warp-uniform
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
+        for (int f = 0; f < NF; ++f)
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[q][f] += __shfl_xor_sync(0xffffffffu, acc[q][f], off);
-      if (lane == 0) {
-        const int64_t j = sorted[p0 + i];
+          for (int off = 16; off > 0; off >>= 1) acc[q][f] += __shfl_xor_sync(0xffffffffu, acc[q][f], off);
+        if (lane == 0) {
+          const int64_t j = sorted[p0 + i];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) U[3 * j + f] = widen_bits(acc[q][f] * h2f);
-        if (NF == 6) {
+          for (int f = 0; f < 3; ++f) U[3 * j + f] = widen_bits(acc[q][f] * h2f);
+          if (NF == 6) {
 #pragma unroll
-          for (int f = 0; f < 3; ++f) W[3 * j + f] = widen_bits(acc[q][3 + f] * h2f);
+            for (int f = 0; f < 3; ++f) W[3 * j + f] = widen_bits(acc[q][3 + f] * h2f);
+          }
         }
       }
+    }
+    if (tma) {
+      __syncthreads();  // every warp is done with this buffer
+      if (tid == 0 && step + 2 < total) issue(step + 2);
     }
   }
 }
@@ -1674,6 +1765,31 @@ int interp_stage_fields(const Geometry& g, int tsize) {
   return interp_tile_fields(g);
 }
 
+// the grid's real values as a rank-4 tensor (x, y, plane, field) with boxes of the staged layout:
+// kIsSX columns x kIsRows rows x kIsGroups planes x the kernel's fields
+bool encode_interp_tmap(Plan& p) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return false;
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const Geometry& g = p.g;
+  const int nf = interp_stage_fields(g, 1);
+  if (nf == 0 || g.nx < kIsSX) return false;
+  const size_t rowb = (size_t)2 * g.pitch * sizeof(float);
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)nf};
+  const cuuint64_t strides[3] = {(cuuint64_t)rowb, (cuuint64_t)(rowb * g.ny), (cuuint64_t)(rowb * g.ny * g.nz)};
+  const cuuint32_t box[4] = {(cuuint32_t)kIsSX, (cuuint32_t)kIsRows, (cuuint32_t)kIsGroups, (cuuint32_t)nf};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUtensorMap* map = reinterpret_cast<CUtensorMap*>(p.interp_tmap);
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.grid, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // tiles a support can overlap in x and y (a partial last tile can add one) and the partial-sum
 // buffer of the tile-gather interpolation, in values of the transform precision
 void interp_tile_slots(const Geometry& g, int& sxn, int& syn) {
@@ -1702,12 +1818,13 @@ void launch_interp(const Plan& p, int64_t n, double* U, double* W, cudaStream_t 
     if (p.interp_tile == 2 && ns > 0) {
       const unsigned bins = (unsigned)(p.g.nbx * p.g.nby);
       const int force_global = p.inject == 2 ? 1 : 0;  // test hook: every bin takes the global gather
+      const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(p.interp_tmap);
       if (ns == 6)
-        interp_stage_kernel<6><<<bins, kIsThreads, interp_stage_smem(6), s>>>(p.g, p.records, p.bin_start, p.sorted,
-                                                                            grid, wz, U, W, force_global);
+        interp_stage_kernel<6><<<bins, kIsThreads, interp_stage_smem(6), s>>>(
+            map, p.interp_tma, p.g, p.records, p.bin_start, p.sorted, grid, wz, U, W, force_global, p.status);
       else
-        interp_stage_kernel<3><<<bins, kIsThreads, interp_stage_smem(3), s>>>(p.g, p.records, p.bin_start, p.sorted,
-                                                                            grid, wz, U, W, force_global);
+        interp_stage_kernel<3><<<bins, kIsThreads, interp_stage_smem(3), s>>>(
+            map, p.interp_tma, p.g, p.records, p.bin_start, p.sorted, grid, wz, U, W, force_global, p.status);
       return;
     }
   }

@@ -362,6 +362,8 @@ dps_status allocate(Plan* p) {
   const int sp = spread_prepare<T>(*p);
   if (sp < 0) return DPS_ERR_INVALID_ARG;
   if (sp == 0) return DPS_ERR_CUDA;
+  // the staged interpolation's TMA view of the grid (without it every bin copies with cp.async)
+  p->interp_tma = interp_stage_fields(g, (int)(sizeof(T) / 4)) > 0 && encode_interp_tmap(*p) ? 1 : 0;
   // column chunks of the wavenumber-space pipeline (multiples of 32 columns, ~192 wide)
   // one chunk by default: measured on GB300, co-running the FP64 solve with the float transforms
   // slowed both (they compete for issue slots); DPS_CHUNKS in the environment or the autotuner may
@@ -630,7 +632,7 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
   // finishing kernel for the tile gather)
   // (+ the B-operand image kernel before each tensor-core transform)
   out->launches_per_apply = 9 + 5 * p->nchunks + ((p->interp_tile == 1 && p->ipart) ? 1 : 0) +
-                            p->nchunks * ((p->cheb_tc ? 1 : 0) + (p->cheb_tc_bwd ? 1 : 0));
+                            p->nchunks * ((p->cheb_tc ? 1 : 0) + (p->cheb_tc_bwd ? 2 * p->cheb_tc_bwd_parts - 1 : 0));
   out->nchunks = p->nchunks;
   out->fft_col_width = 1 << p->col_lcw;
   out->fft_register_rows = p->fft_reg[0];
