@@ -184,7 +184,7 @@ typedef struct {
   int32_t cheb_tensor_cores; /* Chebyshev transforms on the tensor cores (tcgen05, tf32
                                three-product split; mixed precision, nz <= 128): bit 0 the
                                forward transform, bit 1 the backward transform (spectral-curl
-                               torques, nz <= 96)                                               */
+                               torques; beyond 96 nodes in two launches of half the planes)    */
 } dps_plan_info;
 dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out);
 

@@ -524,12 +524,26 @@ __host__ __device__ inline int tc_nn(const Geometry& g, int clo, int chi) {
   return Spec::kForward ? nmax : (nq < 16 ? 16 : nq);
 }
 
+// The backward transform's output planes in `nparts` parts (one launch each) when five
+// accumulators of all of them would not fit the 512 tensor-memory columns: part `part` of the
+// occupied range [clo, chi], parts of a multiple of 16 planes; an empty part has lo > hi.
+__host__ __device__ inline void tc_part(int& clo, int& chi, int part, int nparts) {
+  if (nparts <= 1) return;
+  const int nocc = chi >= clo ? chi - clo + 1 : 0;
+  const int ph = ((nocc + nparts - 1) / nparts + 15) / 16 * 16;
+  const int lo = clo + part * ph;
+  chi = min(chi, lo + ph - 1);
+  clo = lo;
+}
+
 // The B operands of every K step of a product, tf32-split and laid out as in a stage, so that the
 // pipeline copies them with one bulk copy per step: image[ks][tab][hi, lo][nn rows x 8]
 template <typename Spec>
 __global__ void tc_bimage_kernel(Geometry g, typename Spec::Args a, const int* __restrict__ zrange,
-                                 unsigned char* __restrict__ img) {
-  const int clo = zrange[0], chi = zrange[1];
+                                 unsigned char* __restrict__ img, int part, int nparts) {
+  int clo = zrange[0], chi = zrange[1];
+  tc_part(clo, chi, part, nparts);
+  if (chi < clo && nparts > 1) return;  // an empty part
   const int nn = tc_nn<Spec>(g, clo, chi);
   const int nks = Spec::nks(g, clo, chi);
   const uint32_t step = (uint32_t)(2 * Spec::NT * nn * kTcK * 4);
@@ -545,11 +559,14 @@ template <typename Spec>
 __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, typename Spec::Args a,
                                                                 const unsigned char* __restrict__ bimg,
                                                                 const int* __restrict__ zrange, int kx0, int w,
-                                                                int* __restrict__ status, int inject) {
+                                                                int* __restrict__ status, int inject, int part,
+                                                                int nparts) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ TcShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int clo = zrange[0], chi = zrange[1];
+  int clo = zrange[0], chi = zrange[1];
+  tc_part(clo, chi, part, nparts);  // the backward transform's output planes of this launch
+  if (chi < clo && nparts > 1) return;  // an empty part (uniform over the grid)
   const int64_t ntiles = ((int64_t)w * g.ny + kTcWave - 1) / kTcWave;
   const int nmax = (g.nz + 15) / 16 * 16;  // the stage layout is sized for this
   const int nn = tc_nn<Spec>(g, clo, chi);
@@ -690,12 +707,14 @@ size_t tc_smem(const Geometry& g) {
 
 template <typename Spec>
 void launch_tc(const Plan& p, const typename Spec::Args& a, unsigned char* img, int kx0, int w, cudaStream_t s,
-               int inject = 0) {
+               int inject = 0, int nparts = 1) {
   const int64_t tiles = ((int64_t)w * p.g.ny + kTcWave - 1) / kTcWave;
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, p.cheb_tc_grid));
-  tc_bimage_kernel<Spec><<<64, 256, 0, s>>>(p.g, a, p.zrange, img);
-  cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status,
-                                                                      inject);
+  for (int part = 0; part < nparts; ++part) {
+    tc_bimage_kernel<Spec><<<64, 256, 0, s>>>(p.g, a, p.zrange, img, part, nparts);
+    cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status,
+                                                                        inject, part, nparts);
+  }
 }
 
 }  // namespace
@@ -723,9 +742,12 @@ int cheb_tc_prepare(Plan& p) {
     return 0;
   p.cheb_tc_grid = sms;
   if (tc_smem<FwdSpec<true>>(p.g) + 1024 <= (size_t)optin) p.cheb_tc = 1;
-  // backward: five accumulators of up to nz (rounded up to 16) columns must fit 512 columns
-  if (p.g.spectral_curl && 5 * cheb_tc_np(p.g) <= 512 && tc_smem<BwdSpec<2>>(p.g) + 1024 <= (size_t)optin)
+  // backward: five accumulators of the occupied planes (rounded up to 16) must fit 512 columns;
+  // beyond 96 nodes the planes go in two launches of at most 64 each
+  if (p.g.spectral_curl && tc_smem<BwdSpec<2>>(p.g) + 1024 <= (size_t)optin) {
     p.cheb_tc_bwd = 1;
+    p.cheb_tc_bwd_parts = 5 * cheb_tc_np(p.g) <= 512 ? 1 : 2;
+  }
   return 1;
 }
 
@@ -755,13 +777,13 @@ void launch_cheb_bwd_tc(const Plan& p, int kx0, int w, cudaStream_t s) {
   cplx<float>* grid = reinterpret_cast<cplx<float>*>(p.grid);
   if (g.mode == DPS_FREE)
     launch_tc<BwdSpec<0>>(p, BwdSpec<0>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, p.kt.bimg_b, kx0, w,
-                           s);
+                           s, 0, p.cheb_tc_bwd_parts);
   else if (g.mode == DPS_BOTTOM_WALL)
     launch_tc<BwdSpec<1>>(p, BwdSpec<1>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, p.kt.bimg_b, kx0, w,
-                           s);
+                           s, 0, p.cheb_tc_bwd_parts);
   else
     launch_tc<BwdSpec<2>>(p, BwdSpec<2>::Args{ict, icdt, sdt, p.kt.cpad, zeta, kbuf, kaux, grid}, p.kt.bimg_b, kx0, w,
-                           s);
+                           s, 0, p.cheb_tc_bwd_parts);
 }
 
 }  // namespace dps

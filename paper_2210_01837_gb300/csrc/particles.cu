@@ -1268,13 +1268,16 @@ __global__ void __launch_bounds__(256) interp_pair_kernel(Geometry g, int64_t n,
 // at a time, and each warp gathers its particles from there: lane group g (6 x-lanes) takes plane
 // g of the four, walks the 6 support rows of that plane and adds the 6 fields (U from fields 0..2
 // with the monopole weights, Omega from fields 3..5 with the dipole weights; forces only: U from
-// fields 0..2).  A warp holds the sums of its 2 particles of a batch of 32 across the chunks and
-// reduces them over its lanes at the end of the batch.
+// fields 0..2).  Each of 15 gather warps holds the sums of its 2 particles of a batch of 30 across
+// the chunks and reduces them over its lanes at the end of the batch.
 // Staging: where the region does not cross the periodic boundary, one TMA box load per chunk
-// (44 x 14 x 4 x fields of the grid's tensor map) into one of two buffers, the next chunk's load
-// in flight while the warps read the current one; each wait is bounded (about a second; on expiry
-// the block records kStatTimeout, waits again, bounded, for its loads in flight and leaves).  At the
-// boundary the block copies the wrapped rows with 16-byte cp.async pieces instead.  Where a bin's
+// (44 x 14 x 4 x fields of the grid's tensor map) into one of two buffers, issued by a sixteenth
+// warp: a buffer's `full` barrier completes with the load's bytes, its `empty` barrier when all
+// gather warps have read it, and the producer waits for `empty` before loading the next chunk into
+// it, so a gather warp waits only for the chunk it needs next.  Each wait is bounded (about a
+// second; on expiry the block records kStatTimeout, every role leaves its loop, and the producer
+// waits again, bounded, for its loads in flight before the block exits).  At the boundary the
+// block copies the wrapped rows with 16-byte cp.async pieces instead (block-wide barriers).  Where a bin's
 // region would not fit (it cannot with the bins' construction, but the kernel checks) the block
 // gathers from global memory with the same lane walk.
 // Shared layout per buffer: [field][plane of the chunk][row (14)][44]: planes 616 values apart, 8
@@ -1291,7 +1294,8 @@ constexpr int kIsFS = kIsGroups * kIsPS;    // field stride (values)
 constexpr int kIsSlots = 2;                 // particles per warp per batch
 constexpr int kIsThreads = 512;
 constexpr int kIsWarps = kIsThreads / 32;
-constexpr int kIsBatch = kIsWarps * kIsSlots;
+constexpr int kIsGatherWarps = kIsWarps - 1;  // the last warp issues the TMA loads
+constexpr int kIsBatch = kIsGatherWarps * kIsSlots;
 static_assert(kIsPS % 32 == 8 && (kIsSX * 4) % 16 == 0, "staged plane layout");
 static_assert(kIsGroups * kIsPX <= 32, "lane groups");
 
@@ -1306,14 +1310,18 @@ __device__ __forceinline__ int rel_node(int v, int t0, int n) {
   return d;
 }
 
-__device__ __forceinline__ void is_bar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void is_bar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void is_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void is_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// bounded wait for the phase with the given parity; false after about 2^31 cycles
-__device__ __forceinline__ bool is_wait(uint64_t* bar, unsigned parity) {
+// bounded wait for the phase with the given parity; false after about 2^31 cycles, or once the
+// block's failure flag (if given) is raised
+__device__ __forceinline__ bool is_wait(uint64_t* bar, unsigned parity, volatile int* fail) {
   const long long t0 = clock64();
   for (;;) {
     unsigned done;
@@ -1323,6 +1331,7 @@ __device__ __forceinline__ bool is_wait(uint64_t* bar, unsigned parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
+    if (fail && *fail) return false;
     if (clock64() - t0 > (1LL << 31)) return false;
   }
 }
@@ -1341,11 +1350,12 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
                     const float* __restrict__ wz, double* __restrict__ U, double* __restrict__ W, int force_global,
                     int* __restrict__ status) {
   constexpr int PX = kIsPX, NG = kIsGroups, ZC = kIsGroups, SX = kIsSX, FS = kIsFS, PW = kIsSlots;
+  constexpr int GW = kIsGatherWarps;
   constexpr int BUFV = NF * kIsFS;  // values per chunk buffer
   extern __shared__ __align__(128) unsigned char is_raw[];
   // two chunk buffers, 128-byte aligned (TMA destinations)
   float* const sg = reinterpret_cast<float*>(is_raw + ((128u - (smem_u32(is_raw) & 127u)) & 127u));
-  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ __align__(8) uint64_t s_full[2], s_empty[2];
   __shared__ int s_b[6];           // bounds: ox min/max, oy min/max, z begin/end
   __shared__ int s_xo[kIsSX];      // wrapped x of each staged column (cp.async path)
   __shared__ int s_yo[kIsRows];    // wrapped y of each staged row times the row length
@@ -1360,6 +1370,7 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
   const int rw = g.rec_words, stride = 2 * g.pxc + g.lzc, px = g.kM.px;
   const int rowlen = 2 * g.pitch;
   const size_t plane = (size_t)g.ny * rowlen, fstride = plane * g.nz;
+  volatile int* fail_flag = &s_fail;
   if (tid < 6) s_b[tid] = (tid & 1) ? INT_MIN : INT_MAX;
   if (tid == 0) s_fail = 0;
   __syncthreads();
@@ -1400,8 +1411,10 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
     }
   }
   if (tma && tid == 0) {
-    is_bar_init(&s_bar[0]);
-    is_bar_init(&s_bar[1]);
+    for (int i = 0; i < 2; ++i) {
+      is_bar_init(&s_full[i], 1);
+      is_bar_init(&s_empty[i], GW);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
@@ -1409,41 +1422,115 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
   const int nch = staged ? (zhi - zlo + ZC - 1) / ZC : 1;
   const int nbatch = (cnt + kIsBatch - 1) / kIsBatch;
   const int total = nbatch * nch;  // (batch, chunk) steps
-  constexpr unsigned kBoxBytes = (unsigned)interp_stage_buf(NF);
-  auto issue = [&](int step) {  // thread 0: the TMA load of step's chunk into buffer step & 1
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of the buffer came first
-    is_expect_tx(&s_bar[step & 1], kBoxBytes);
-    is_tma_4d(sg + (step & 1) * BUFV, &tmap, xlo4, ylo, zlo + (step % nch) * ZC, 0, &s_bar[step & 1]);
-  };
-  if (tma && tid == 0) {
-    issue(0);
-    if (total > 1) issue(1);
-  }
   float acc[PW][NF];
+  auto zero_acc = [&]() {
+#pragma unroll
+    for (int q = 0; q < PW; ++q)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) acc[q][f] = 0.f;
+  };
+  // this warp's particles of `batch` over the staged planes [zb, zb + ZC) of buffer sb
+  auto gather_staged = [&](const float* sb, int batch, int zb) {
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+      const int i = batch * kIsBatch + warp + GW * q;
+      if (i >= cnt || !lane_on) continue;
+      const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
+      const int4 hd = *reinterpret_cast<const int4*>(r);
+      const int c = zb + grp;
+      if (c < hd.z || c >= hd.z + hd.w) continue;
+      const int iz = c - hd.z;
+      const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
+      const float* pd = pm + stride;
+      const float wc = wz[c];
+      const bool xon = lx < px;  // lanes past the support read a staged column with weight 0
+      const float mzx = xon ? pm[2 * g.pxc + iz] * wc * pm[lx] : 0.f;
+      const float dzx = (NF == 6 && xon) ? pd[2 * g.pxc + iz] * wc * pd[lx] : 0.f;
+      const int ox = rel_node(hd.x, tx0, g.nx), oy = rel_node(hd.y, ty0, g.ny);
+      const float* sp = sb + grp * kIsPS + (oy - oymin) * SX + (ox - xoff) + lx;
+#pragma unroll
+      for (int iy = 0; iy < PX; ++iy) {
+        if (iy < px) {
+          const float wm = mzx * pm[g.pxc + iy];
+#pragma unroll
+          for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
+          if (NF == 6) {
+            const float wd = dzx * pd[g.pxc + iy];
+#pragma unroll
+            for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
+          }
+        }
+      }
+    }
+  };
+  // sums over the warp's lanes; lane 0 writes U (and Omega) of each of its particles of `batch`
+  auto finish = [&](int batch) {
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+      const int i = batch * kIsBatch + warp + GW * q;
+      if (i >= cnt) continue;  // warp-uniform
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[q][f] += __shfl_xor_sync(0xffffffffu, acc[q][f], off);
+      if (lane == 0) {
+        const int64_t j = sorted[p0 + i];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) U[3 * j + f] = widen_bits(acc[q][f] * h2f);
+        if (NF == 6) {
+#pragma unroll
+          for (int f = 0; f < 3; ++f) W[3 * j + f] = widen_bits(acc[q][3 + f] * h2f);
+        }
+      }
+    }
+  };
+  if (tma) {
+    constexpr unsigned kBoxBytes = (unsigned)interp_stage_buf(NF);
+    if (warp == GW) {
+      // producer: the TMA load of each step's chunk into buffer step & 1 once the gather warps
+      // have released the buffer's previous contents
+      if (lane == 0) {
+        int issued = 0;
+        for (int step = 0; step < total; ++step) {
+          const int bb = step & 1;
+          if (step >= 2 && !is_wait(&s_empty[bb], (unsigned)((step - 2) >> 1) & 1u, fail_flag)) {
+            if (!*fail_flag) atomicOr(status, kStatTimeout);
+            *fail_flag = 1;
+            break;
+          }
+          if (*fail_flag) break;
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of the buffer came first
+          is_expect_tx(&s_full[bb], kBoxBytes);
+          is_tma_4d(sg + bb * BUFV, &tmap, xlo4, ylo, zlo + (step % nch) * ZC, 0, &s_full[bb]);
+          ++issued;
+        }
+        // loads still in flight (a stop): wait, bounded, for the last one of each buffer
+        for (int st = issued - 2 < 0 ? 0 : issued - 2; st < issued; ++st)
+          is_wait(&s_full[st & 1], (unsigned)(st >> 1) & 1u, nullptr);
+      }
+    } else {
+      for (int step = 0; step < total; ++step) {
+        const int batch = step / nch, k = step - batch * nch, bb = step & 1;
+        if (k == 0) zero_acc();
+        if (!is_wait(&s_full[bb], (unsigned)(step >> 1) & 1u, fail_flag)) {
+          if (!*fail_flag) atomicOr(status, kStatTimeout);
+          *fail_flag = 1;
+          break;
+        }
+        gather_staged(sg + bb * BUFV, batch, zlo + k * ZC);
+        __syncwarp();
+        if (lane == 0) is_arrive(&s_empty[bb]);
+        if (k == nch - 1) finish(batch);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int step = 0; step < total; ++step) {
     const int batch = step / nch, k = step - batch * nch;
-    const int base = batch * kIsBatch;
-    if (k == 0) {
-#pragma unroll
-      for (int q = 0; q < PW; ++q)
-#pragma unroll
-        for (int f = 0; f < NF; ++f) acc[q][f] = 0.f;
-    }
-    const float* sb = sg + (step & 1) * BUFV;
-    if (tma) {
-      if (!is_wait(&s_bar[step & 1], (unsigned)(step >> 1) & 1u)) s_fail = 1;
-      __syncthreads();
-      if (s_fail) {
-        if (tid == 0) {
-          atomicOr(status, kStatTimeout);
-          // loads still in flight: this step's (if its wait ran out) and the next one's
-          is_wait(&s_bar[step & 1], (unsigned)(step >> 1) & 1u);
-          if (step + 1 < total) is_wait(&s_bar[(step + 1) & 1], (unsigned)((step + 1) >> 1) & 1u);
-        }
-        __syncthreads();
-        return;
-      }
-    } else if (staged) {
+    if (k == 0) zero_acc();
+    float* sb = sg + (step & 1) * BUFV;
+    if (staged) {
       __syncthreads();  // the readers of this buffer two steps ago are done
       const int zb = zlo + k * ZC;
       // rows (f, zz, yy) of the chunk: a warp copies two rows per step (22 lanes, 11 pieces each)
@@ -1453,51 +1540,18 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
           const int yy = r % kIsRows, zz = (r / kIsRows) % ZC, f = r / (kIsRows * ZC);
           if (yy >= rh || zb + zz >= zhi) continue;
           const float* src = grid + (size_t)f * fstride + (size_t)(zb + zz) * plane + s_yo[yy] + s_xo[4 * pc];
-          cp_async16(const_cast<float*>(sb) + f * FS + zz * kIsPS + yy * SX + 4 * pc, src);
+          cp_async16(sb + f * FS + zz * kIsPS + yy * SX + 4 * pc, src);
         }
       }
       cp_commit();
       cp_wait_all();
       __syncthreads();
-    }
-    if (staged) {
-      const int zb = zlo + k * ZC;
-#pragma unroll
-      for (int q = 0; q < PW; ++q) {
-        const int i = base + warp + kIsWarps * q;
-        if (i >= cnt || !lane_on) continue;
-        const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
-        const int4 hd = *reinterpret_cast<const int4*>(r);
-        const int c = zb + grp;
-        if (c < hd.z || c >= hd.z + hd.w) continue;
-        const int iz = c - hd.z;
-        const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
-        const float* pd = pm + stride;
-        const float wc = wz[c];
-        const bool xon = lx < px;  // lanes past the support read a staged column with weight 0
-        const float mzx = xon ? pm[2 * g.pxc + iz] * wc * pm[lx] : 0.f;
-        const float dzx = (NF == 6 && xon) ? pd[2 * g.pxc + iz] * wc * pd[lx] : 0.f;
-        const int ox = rel_node(hd.x, tx0, g.nx), oy = rel_node(hd.y, ty0, g.ny);
-        const float* sp = sb + grp * kIsPS + (oy - oymin) * SX + (ox - xoff) + lx;
-#pragma unroll
-        for (int iy = 0; iy < PX; ++iy) {
-          if (iy < px) {
-            const float wm = mzx * pm[g.pxc + iy];
-#pragma unroll
-            for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
-            if (NF == 6) {
-              const float wd = dzx * pd[g.pxc + iy];
-#pragma unroll
-              for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
-            }
-          }
-        }
-      }
-    } else if (any) {
+      if (warp < GW) gather_staged(sb, batch, zb);
+    } else if (any && warp < GW) {
       // global-memory gather with the same lane walk (planes hd.z + g, g + NG, ...)
 #pragma unroll
       for (int q = 0; q < PW; ++q) {
-        const int i = base + warp + kIsWarps * q;
+        const int i = batch * kIsBatch + warp + GW * q;
         if (i >= cnt || !lane_on) continue;
         const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
         const int4 hd = *reinterpret_cast<const int4*>(r);
@@ -1527,31 +1581,7 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
         }
       }
     }
-    if (k == nch - 1) {
-      // sums over the warp's lanes; lane 0 writes U (and Omega) of each of its particles
-#pragma unroll
-      for (int q = 0; q < PW; ++q) {
-        const int i = base + warp + kIsWarps * q;
-        if (i >= cnt) continue;  // warp-uniform
-#pragma unroll
-        for (int f = 0; f < NF; ++f)
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) acc[q][f] += __shfl_xor_sync(0xffffffffu, acc[q][f], off);
-        if (lane == 0) {
-          const int64_t j = sorted[p0 + i];
-#pragma unroll
-          for (int f = 0; f < 3; ++f) U[3 * j + f] = widen_bits(acc[q][f] * h2f);
-          if (NF == 6) {
-#pragma unroll
-            for (int f = 0; f < 3; ++f) W[3 * j + f] = widen_bits(acc[q][3 + f] * h2f);
-          }
-        }
-      }
-    }
-    if (tma) {
-      __syncthreads();  // every warp is done with this buffer
-      if (tid == 0 && step + 2 < total) issue(step + 2);
-    }
+    if (k == nch - 1 && warp < GW) finish(batch);
   }
 }
 

@@ -2,10 +2,11 @@
 precision: the forward transform, and the backward transform of the spectral-curl torque route)
 against the oracle and against the CUDA-core lane kernels they replace.
 
-Cases: every wall mode, forces only and with torques (six-field curl source), 17 to 97 Chebyshev
-nodes (accumulator widths 32 to 112 columns per output), ragged wavenumber tiles (fewer than 64
-wavenumbers in the last tile), plane ranges that end inside a K step of 8 planes, and a problem of a
-single tile.  Bars: 1e-5 relative L2 against the oracle (the mixed bar); 3e-6 against the lane
+Cases: every wall mode, forces only and with torques (six-field curl source), 17 to 113 Chebyshev
+nodes (accumulator widths 32 to 128 columns per output; beyond 96 nodes the backward transform's
+output planes go in two launches), ragged wavenumber tiles (fewer than 64 wavenumbers in the last
+tile), plane ranges that end inside a K step of 8 planes, a problem of a single tile, and a plane
+range narrow enough that the second backward launch has no planes.  Bars: 1e-5 relative L2 against the oracle (the mixed bar); 3e-6 against the lane
 kernel (the same contraction from tf32 operand pairs instead of float products, summed in another
 order: 1.3e-6 measured at 97 nodes).
 """
@@ -32,8 +33,8 @@ def _plan(params, torque, tc, monkeypatch):
     monkeypatch.setenv("DPS_CHEB_TC", "3" if tc else "0")
     plan = binding.Plan.from_params(params, with_torque=torque, precision="mixed", max_n=64)
     monkeypatch.delenv("DPS_CHEB_TC")
-    # bit 0 forward (nz <= 128), bit 1 backward (spectral-curl torques, nz <= 96)
-    want = (1 | (2 if torque and params["nz"] <= 96 else 0)) if tc else 0
+    # bit 0 forward (nz <= 128), bit 1 backward (spectral-curl torques)
+    want = (1 | (2 if torque else 0)) if tc else 0
     assert plan.info().cheb_tensor_cores == want
     return plan
 
@@ -45,6 +46,7 @@ CASES = [
     ("bottom_wall", 45, 35, 17, False),
     ("slit", 72, 72, 33, False),
     ("bottom_wall", 8, 8, 17, True),     # a single 64-wavenumber tile (5 x 8 wavenumbers)
+    ("slit", 40, 32, 113, True),         # backward in two launches of up to 64 planes
 ]
 
 
@@ -65,6 +67,26 @@ def test_tensor_core_forward_transform(mode, nx, ny, nz, torque, monkeypatch):
     if torque:
         assert rel_l2(W, W_ref) <= 1e-5
         assert rel_l2(W, W0) <= 3e-6
+
+
+def test_backward_in_two_launches_with_an_empty_second_part(monkeypatch):
+    """97 nodes with every particle in a thin layer near the wall: the occupied planes fit the first
+    of the backward transform's two launches, and the second launch has none."""
+    params = small_params("bottom_wall", nx=48, ny=40, nz=97, zmax=12.0, torque=True)
+    rng = np.random.default_rng(97)
+    n = 30
+    pos = np.stack([rng.uniform(0, params["Lx"], n), rng.uniform(0, params["Ly"], n), rng.uniform(1.7, 1.8, n)], axis=1)
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3))
+    U_ref, W_ref = mobility(oracle_params(params), pos, F, T)
+    got = []
+    for tc in (True, False):
+        plan = _plan(params, True, tc, monkeypatch)
+        got.append(gpu_mobility(params, pos, F, T, "mixed", plan=plan))
+        plan.close()
+    (U, W), (U0, W0) = got
+    assert rel_l2(U, U_ref) <= 1e-5 and rel_l2(W, W_ref) <= 1e-5
+    assert rel_l2(U, U0) <= 3e-6 and rel_l2(W, W0) <= 3e-6
 
 
 def test_tensor_cores_used_by_default_in_mixed_precision_only():
