@@ -167,11 +167,14 @@ def cpu_oracle_tile(div, seed_offset=3):
 
 def cpu_oracle_config(name, div=1, seed=0):
     """One oracle product of configuration `name` ("bw_small": whole; "slit_16k": a 1/div^2-area
-    tile with the same density, heights and h); returns seconds."""
+    tile with the same density, heights and h; "batch": system `seed` of the configuration-4
+    population, whole); returns seconds."""
     from oracle import Params, mobility
-    from paper_2210_01837_gb300.workloads import bw_small, slit_16k
+    from paper_2210_01837_gb300.workloads import batch_systems, bw_small, slit_16k
     if name == "bw_small":
         params, pos, F, T = bw_small()
+    elif name == "batch":
+        params, pos, F, T = batch_systems(count=256)[seed]
     else:
         params, pos, F, T = slit_16k(n=16384 // (div * div), nxy=384 // div, L=256.0 / div, seed_offset=2 + 100 * seed)
     t0 = time.perf_counter()
@@ -179,7 +182,7 @@ def cpu_oracle_config(name, div=1, seed=0):
     return time.perf_counter() - t0
 
 
-def _oracle_config_runs(name, div, procs, threads):
+def _oracle_config_runs(name, div, procs, threads, seeds=None):
     """Wall seconds of `procs` concurrent oracle products of `name`, each in a fresh interpreter
     with `threads` BLAS/OpenMP threads, and the per-process times."""
     env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
@@ -187,8 +190,9 @@ def _oracle_config_runs(name, div, procs, threads):
     t0 = time.perf_counter()
     kids = []
     for i in range(procs):
+        seed = seeds[i] if seeds is not None else i
         code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-                "print(json.dumps(bench.cpu_oracle_config(%r, %d, %d)))" % (ROOT, name, div, i))
+                "print(json.dumps(bench.cpu_oracle_config(%r, %d, %d)))" % (ROOT, name, div, seed))
         kids.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
                                      text=True, env=env))
     per = [json.loads(k.communicate(timeout=1800)[0].strip().splitlines()[-1]) for k in kids]
@@ -206,7 +210,23 @@ def oracle_configs():
     div = 4
     wall, per = _oracle_config_runs("slit_16k", div, cores, 1)
     t1, _ = _oracle_config_runs("slit_16k", div, 1, 1)
+    # configuration 4: every 8th of the 128 smallest systems (the whole population would take hours
+    # of oracle time), one per core at once; the batch's time extrapolated by nx ny nz^3 (the
+    # oracle's dense LU per wavenumber dominates: configurations 1 and 2 scale so within 15 %)
+    from paper_2210_01837_gb300.workloads import batch_systems
+    pop = batch_systems(count=256)
+    nodes = [p_["nx"] * p_["ny"] * float(p_["nz"]) ** 3 for p_, _, _, _ in pop]
+    order = sorted(range(len(pop)), key=lambda i: len(pop[i][1]))
+    sample = order[:128:8]
+    wall4, per4 = _oracle_config_runs("batch", 1, len(sample), 1, seeds=sample)
+    scale4 = sum(nodes) / sum(nodes[i] for i in sample)
     return {"cores": cores,
+            "batch": {"sample": f"{len(sample)} of the 128 smallest systems (every 8th by N; N "
+                                f"{len(pop[sample[0]][1])}-{len(pop[sample[-1]][1])}), one per core at once: "
+                                f"{wall4:.1f} s wall, {sum(per4):.1f} s of oracle time",
+                      "batch_oracle_s_extrapolated": sum(per4) * scale4,
+                      "rule": "oracle time per system proportional to nx ny nz^3; the 256 systems have "
+                              f"{scale4:.1f}x the sample's; one core"},
             "bw_small": {"wall_s_all_cores": c1_all, "wall_s_one_core": c1_one, "sample": "whole product, N=100"},
             "slit_16k": {"products_per_s_all_cores": cores / (wall * div * div),
                          "wall_s_one_core_extrapolated": t1 * div * div,
@@ -364,7 +384,10 @@ def configs_leg(binding, torch, dev, steps=5, warmup=3):
     from paper_2210_01837_gb300.workloads import bw_small, lanczos_layer, slit_16k
     tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
-    def ms(params, pos, F, T, precision, with_torque):
+    hbm, _ = peaks()
+    fracs = {}
+
+    def ms(params, pos, F, T, precision, with_torque, key=None):
         plan = binding.Plan.from_params(params, with_torque=with_torque, precision=precision, max_n=len(pos))
         d_pos, d_F = tdev(pos), tdev(F)
         d_T = tdev(T) if with_torque else None
@@ -381,18 +404,33 @@ def configs_leg(binding, torch, dev, steps=5, warmup=3):
         e1.record()
         torch.cuda.synchronize(dev)
         plan.check()
+        if key:
+            # fractions of the measured copy bandwidth of the HBM-bound stages (separate timed pass)
+            plan.enable_timing(True)
+            log = []
+            for _ in range(3):
+                plan.apply(d_pos, d_F, d_T, U, W)
+                log.append(plan.stage_times())
+            plan.enable_timing(False)
+            info = plan.info()
+            work = algorithmic(params, len(pos), occupied_planes(params, pos, info.alpha_M),
+                               4 if precision == "mixed" else 8, info.record_words * 4, fields=info.nfields)
+            st = {k: float(np.mean([l_[k] for l_ in log])) for k in log[0]}
+            fracs[key] = {k: round(work[k] / (st[k] * 1e-3) / 1e9 / hbm, 3)
+                          for k in ("spread", "fft_x_fwd", "fft_y_fwd", "fft_y_inv", "fft_x_inv", "interp")}
         plan.close()
         return round(e0.elapsed_time(e1) / steps, 4)
 
     out = {}
     p, pos, F, _ = bw_small()
-    out["bw_small_fp64_ms"] = ms(p, pos, F, None, "fp64", False)
+    out["bw_small_fp64_ms"] = ms(p, pos, F, None, "fp64", False, "bw_small_fp64")
     p, pos, F, T = slit_16k()
-    out["slit_16k_mixed_ms"] = ms(p, pos, F, T, "mixed", True)
-    out["slit_16k_fp64_ms"] = ms(p, pos, F, T, "fp64", True)
+    out["slit_16k_mixed_ms"] = ms(p, pos, F, T, "mixed", True, "slit_16k_mixed")
+    out["slit_16k_fp64_ms"] = ms(p, pos, F, T, "fp64", True, "slit_16k_fp64")
     p, pos, W = lanczos_layer(18, H=9.1)
     out["fig9_forces_663552_mixed_ms"] = ms(p, pos, W, None, "mixed", False)
     out["fig9_forces_663552_fp64_ms"] = ms(p, pos, W, None, "fp64", False)
+    out["stage_frac_hbm"] = fracs
     out["fig9_paper_v100_ms"] = 370.0
     out["note"] = ("CUDA events per product after 3 warm-up products; the paper's 370 ms is its V100 time for the "
                    "same-sized system (precision not stated), context only")
