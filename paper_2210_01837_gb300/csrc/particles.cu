@@ -1299,6 +1299,16 @@ constexpr int kIsBatch = kIsGatherWarps * kIsSlots;
 static_assert(kIsPS % 32 == 8 && (kIsSX * 4) % 16 == 0, "staged plane layout");
 static_assert(kIsGroups * kIsPX <= 32, "lane groups");
 
+constexpr int kIsZT = 64;  // z weights of a particle's table (records with more z slots: not staged)
+
+// a gather warp's table of one particle of the batch: the staged offset of its first support node,
+// its z support, and its weights (the z weights times the Clenshaw-Curtis weights of the planes)
+struct IsSlot {
+  int base, z0, zn, pad;
+  float mx[8], dx[8], my[8], dy[8];
+  float mz[kIsZT], dz[kIsZT];
+};
+
 __host__ __device__ constexpr size_t interp_stage_buf(int nf) { return (size_t)nf * kIsFS * sizeof(float); }
 __host__ __device__ constexpr size_t interp_stage_smem(int nf) { return 2 * interp_stage_buf(nf) + 128; }
 
@@ -1360,6 +1370,7 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
   __shared__ int s_xo[kIsSX];      // wrapped x of each staged column (cp.async path)
   __shared__ int s_yo[kIsRows];    // wrapped y of each staged row times the row length
   __shared__ int s_fail;           // a bounded wait ran out
+  __shared__ IsSlot s_slot[kIsGatherWarps][kIsSlots];
   const int b = blockIdx.x;
   const int p0 = bin_start[b], cnt = bin_start[b + 1] - p0;
   if (cnt <= 0) return;
@@ -1429,36 +1440,58 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
 #pragma unroll
       for (int f = 0; f < NF; ++f) acc[q][f] = 0.f;
   };
+  // this warp's tables of its particles of `batch` (warp-private: __syncwarp publishes them)
+  auto fill_tables = [&](int batch) {
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+      const int i = batch * kIsBatch + warp + GW * q;
+      if (i >= cnt) continue;  // warp-uniform
+      IsSlot& t = s_slot[warp][q];
+      const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
+      const int4 hd = *reinterpret_cast<const int4*>(r);
+      const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
+      const float* pd = pm + stride;
+      if (lane == 0) {
+        t.base = (rel_node(hd.y, ty0, g.ny) - oymin) * SX + (rel_node(hd.x, tx0, g.nx) - xoff);
+        t.z0 = hd.z;
+        t.zn = hd.w;
+      }
+      if (lane < 8) {  // zero past the support: those lanes and rows add nothing
+        const bool on = lane < px;
+        t.mx[lane] = on ? pm[lane] : 0.f;
+        t.my[lane] = on ? pm[g.pxc + lane] : 0.f;
+        t.dx[lane] = (NF == 6 && on) ? pd[lane] : 0.f;
+        t.dy[lane] = (NF == 6 && on) ? pd[g.pxc + lane] : 0.f;
+      }
+      for (int e = lane; e < hd.w; e += 32) {
+        const float wc = wz[hd.z + e];
+        t.mz[e] = pm[2 * g.pxc + e] * wc;
+        t.dz[e] = NF == 6 ? pd[2 * g.pxc + e] * wc : 0.f;
+      }
+    }
+    __syncwarp();
+  };
   // this warp's particles of `batch` over the staged planes [zb, zb + ZC) of buffer sb
   auto gather_staged = [&](const float* sb, int batch, int zb) {
 #pragma unroll
     for (int q = 0; q < PW; ++q) {
       const int i = batch * kIsBatch + warp + GW * q;
       if (i >= cnt || !lane_on) continue;
-      const uint32_t* r = rec + (size_t)sorted[p0 + i] * rw;
-      const int4 hd = *reinterpret_cast<const int4*>(r);
-      const int c = zb + grp;
-      if (c < hd.z || c >= hd.z + hd.w) continue;
-      const int iz = c - hd.z;
-      const float* pm = reinterpret_cast<const float*>(r + 8) + 6;
-      const float* pd = pm + stride;
-      const float wc = wz[c];
-      const bool xon = lx < px;  // lanes past the support read a staged column with weight 0
-      const float mzx = xon ? pm[2 * g.pxc + iz] * wc * pm[lx] : 0.f;
-      const float dzx = (NF == 6 && xon) ? pd[2 * g.pxc + iz] * wc * pd[lx] : 0.f;
-      const int ox = rel_node(hd.x, tx0, g.nx), oy = rel_node(hd.y, ty0, g.ny);
-      const float* sp = sb + grp * kIsPS + (oy - oymin) * SX + (ox - xoff) + lx;
+      const IsSlot& t = s_slot[warp][q];
+      const int iz = zb + grp - t.z0;
+      if (iz < 0 || iz >= t.zn) continue;
+      const float mzx = t.mz[iz] * t.mx[lx];
+      const float dzx = NF == 6 ? t.dz[iz] * t.dx[lx] : 0.f;
+      const float* sp = sb + grp * kIsPS + t.base + lx;
 #pragma unroll
       for (int iy = 0; iy < PX; ++iy) {
-        if (iy < px) {
-          const float wm = mzx * pm[g.pxc + iy];
+        const float wm = mzx * t.my[iy];
 #pragma unroll
-          for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
-          if (NF == 6) {
-            const float wd = dzx * pd[g.pxc + iy];
+        for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
+        if (NF == 6) {
+          const float wd = dzx * t.dy[iy];
 #pragma unroll
-            for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
-          }
+          for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
         }
       }
     }
@@ -1511,7 +1544,10 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
     } else {
       for (int step = 0; step < total; ++step) {
         const int batch = step / nch, k = step - batch * nch, bb = step & 1;
-        if (k == 0) zero_acc();
+        if (k == 0) {
+          zero_acc();
+          fill_tables(batch);
+        }
         if (!is_wait(&s_full[bb], (unsigned)(step >> 1) & 1u, fail_flag)) {
           if (!*fail_flag) atomicOr(status, kStatTimeout);
           *fail_flag = 1;
@@ -1528,7 +1564,10 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
   }
   for (int step = 0; step < total; ++step) {
     const int batch = step / nch, k = step - batch * nch;
-    if (k == 0) zero_acc();
+    if (k == 0) {
+      zero_acc();
+      if (staged && warp < GW) fill_tables(batch);
+    }
     float* sb = sg + (step & 1) * BUFV;
     if (staged) {
       __syncthreads();  // the readers of this buffer two steps ago are done
@@ -1791,7 +1830,7 @@ int interp_tile_fields(const Geometry& g) {
 // the staged-grid interpolation applies (float plans; supports of at most kIsPX nodes; forces only
 // or spectral-curl torques with coinciding supports); returns the fields it sums (0: not applicable)
 int interp_stage_fields(const Geometry& g, int tsize) {
-  if (tsize != 1 || g.pxc > kIsPX) return 0;
+  if (tsize != 1 || g.pxc > kIsPX || g.lzc > kIsZT) return 0;
   return interp_tile_fields(g);
 }
 
