@@ -54,8 +54,9 @@ constexpr int kTcWave = 64;    // wavenumbers per tile
 constexpr int kProducers = 256;
 constexpr int kTcThreads = 416;  // 8 producer warps, 4 epilogue warps, 1 MMA warp
 constexpr int kEpiWarp0 = 8, kMmaWarp = 12;
-constexpr int kStages = 4;
-constexpr uint32_t kATile = kTcRows * kTcK * 4;  // 4096 bytes: one A operand of one K step
+constexpr int kStages = 4;                       // most operand stages (fewer where they do not fit)
+constexpr size_t kTcSmemCap = 225 * 1024;        // dynamic shared memory the stages may take
+constexpr uint32_t kATile = umma::tile_bytes(kTcRows);  // one A operand of one K step (128 rows x 8)
 constexpr long long kWaitCycles = 1ll << 31;     // bounded waits: about one second at 2 GHz
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -208,7 +209,7 @@ struct FwdSpec {
     const cplx<float>* grid;
     cplx<float>* kbuf;
   };
-  __host__ __device__ static uint32_t stage_bytes(int nmax) { return (uint32_t)(2 * NQ * kATile + 2 * NT * nmax * kTcK * 4); }
+  __host__ __device__ static uint32_t stage_bytes(int nmax) { return (uint32_t)(2 * NQ * kATile + 2 * NT * umma::tile_bytes((uint32_t)nmax)); }
   struct Raw {
     cplx<float> v[4][NR];
   };
@@ -285,12 +286,12 @@ struct FwdSpec {
       const int c = clo + ks * kTcK + 4 * kg + cc;
       x[cc] = (n < g.nz && c <= chi) ? src[(size_t)c * a.npad + n] : 0.f;
     }
-    const uint32_t btile = (uint32_t)np * kTcK * 4;
+    const uint32_t btile = umma::tile_bytes((uint32_t)np);
     split_store(step + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)n, (uint32_t)(4 * kg)), x[0], x[1],
                 x[2], x[3]);
   }
   __device__ static void mma(const Geometry&, uint32_t sbase, uint32_t tacc, int ks, int np, uint32_t idesc) {
-    const uint32_t btile = (uint32_t)np * kTcK * 4;
+    const uint32_t btile = umma::tile_bytes((uint32_t)np);
     const uint32_t bbase = sbase + 2 * NQ * kATile;
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
@@ -342,7 +343,7 @@ struct BwdSpec {
     cplx<float>* grid;
   };
   __host__ __device__ static uint32_t stage_bytes(int nmax) {
-    return (uint32_t)(2 * NQ * kATile + 2 * NT * nmax * kTcK * 4);
+    return (uint32_t)(2 * NQ * kATile + 2 * NT * umma::tile_bytes((uint32_t)nmax));
   }
   // coefficient step: v[cc][q] = y_f[n], n = 8 ks + 4 grp + cc (half 0: f = u, v; half 1: f = w);
   // node step: v[q][fi] = amplitude q (cE, cG, tE, tG) of field f (half 0: u, v; half 1: w)
@@ -448,13 +449,13 @@ struct BwdSpec {
       }
       x[cc] = v;
     }
-    const uint32_t btile = (uint32_t)nq * kTcK * 4;
+    const uint32_t btile = umma::tile_bytes((uint32_t)nq);
     split_store(step + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)p, (uint32_t)(4 * kg)), x[0], x[1],
                 x[2], x[3]);
   }
   // every step: u, v, w += A_f B0;  du += A_u B1, dv += A_v B1
   __device__ static void mma(const Geometry&, uint32_t sbase, uint32_t tacc, int ks, int nq, uint32_t idesc) {
-    const uint32_t btile = (uint32_t)nq * kTcK * 4;
+    const uint32_t btile = umma::tile_bytes((uint32_t)nq);
     const uint32_t b0 = sbase + 2 * NQ * kATile, b1 = b0 + 2 * btile;
     const uint32_t acc = ks > 0 ? 1u : 0u;
     const uint32_t au = sbase, av = sbase + 2 * kATile, aw = sbase + 4 * kATile;
@@ -546,7 +547,7 @@ __global__ void tc_bimage_kernel(Geometry g, typename Spec::Args a, const int* _
   if (chi < clo && nparts > 1) return;  // an empty part
   const int nn = tc_nn<Spec>(g, clo, chi);
   const int nks = Spec::nks(g, clo, chi);
-  const uint32_t step = (uint32_t)(2 * Spec::NT * nn * kTcK * 4);
+  const uint32_t step = (uint32_t)(2 * Spec::NT * umma::tile_bytes((uint32_t)nn));
   const int items = nks * Spec::NT * nn * 2;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items; i += gridDim.x * blockDim.x) {
     const int kg = i & 1, r = (i >> 1) % nn, rest = (i >> 1) / nn;
@@ -570,12 +571,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
   const int64_t ntiles = ((int64_t)w * g.ny + kTcWave - 1) / kTcWave;
   const int nmax = (g.nz + 15) / 16 * 16;  // the stage layout is sized for this
   const int nn = tc_nn<Spec>(g, clo, chi);
-  const uint32_t bbytes = (uint32_t)(2 * Spec::NT * nn * kTcK * 4);  // B operands of one step
+  const uint32_t bbytes = (uint32_t)(2 * Spec::NT * umma::tile_bytes((uint32_t)nn));  // B operands of one step
   const int cols = Spec::NACC * nn;
   const int nbuf = 2 * cols <= 512 ? 2 : 1;
   const int need = nbuf * cols;
   const uint32_t tcols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
   const uint32_t stage_bytes = Spec::stage_bytes(nmax);
+  uint32_t dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const int nst = min(kStages, (int)((dyn - 1024u) / stage_bytes));  // operand stages launched with
   const int nks = Spec::nks(g, clo, chi);
   const uint32_t idesc = umma::idesc_tf32(kTcRows, (uint32_t)nn);
   volatile int* stop = &sh.stop;
@@ -617,8 +621,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
       Spec::load(g, a, clo, chi, 0, tk, raw);
       for (;;) {
         for (int ks = 0; ks < nks; ++ks, ++it) {
-          const int s = it % kStages;
-          if (!mbar_wait(&sh.empty[s], ((it / kStages) & 1) ^ 1, stop)) { fail(); break; }
+          const int s = it % nst;
+          if (!mbar_wait(&sh.empty[s], ((it / nst) & 1) ^ 1, stop)) { fail(); break; }
           unsigned char* st = smraw + (size_t)s * stage_bytes;
           const typename Spec::Raw cur = raw;
           // the next step's loads, issued before this step's stores
@@ -652,8 +656,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
       const uint32_t tacc = tmem + (uint32_t)(b * cols);
       bool ok = true;
       for (int ks = 0; ks < nks; ++ks, ++it) {
-        const int s = it % kStages;
-        if (!mbar_wait(&sh.full[s], (it / kStages) & 1, stop)) { fail(); ok = false; break; }
+        const int s = it % nst;
+        if (!mbar_wait(&sh.full[s], (it / nst) & 1, stop)) { fail(); ok = false; break; }
         tc_fence_after();
         if (inject) continue;  // failure injection: no MMAs and no completion signals
         if (lane == 0) {
@@ -669,7 +673,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
     if (*stop && it > 0 && !inject) {
       const unsigned last = it - 1;
       const long long t0 = clock64();
-      while (!mbar_test(&sh.empty[last % kStages], (last / kStages) & 1) && clock64() - t0 < kWaitCycles) {
+      while (!mbar_test(&sh.empty[last % nst], (last / nst) & 1) && clock64() - t0 < kWaitCycles) {
       }
     }
   } else {
@@ -702,7 +706,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
 
 template <typename Spec>
 size_t tc_smem(const Geometry& g) {
-  return (size_t)kStages * Spec::stage_bytes((g.nz + 15) / 16 * 16) + 1024;
+  // as many operand stages as fit (at most kStages); 0 when fewer than two fit
+  const size_t sb = Spec::stage_bytes((g.nz + 15) / 16 * 16);
+  const size_t n = std::min<size_t>(kStages, (kTcSmemCap - 1024) / sb);
+  return n >= 2 ? n * sb + 1024 : 0;
 }
 
 template <typename Spec>
@@ -723,7 +730,7 @@ int cheb_tc_np(const Geometry& g) { return (g.nz + 15) / 16 * 16; }
 
 size_t cheb_tc_image_bytes(const Geometry& g, bool backward) {
   const size_t nmax = (size_t)cheb_tc_np(g), ksteps = (size_t)(g.nz + kTcK - 1) / kTcK;
-  return (backward ? 2 * ksteps : ksteps) * 2 * 2 * nmax * kTcK * 4;
+  return (backward ? 2 * ksteps : ksteps) * 2 * 2 * umma::tile_bytes((uint32_t)nmax);
 }
 
 int cheb_tc_prepare(Plan& p) {
@@ -741,10 +748,11 @@ int cheb_tc_prepare(Plan& p) {
       !allow_smem(cheb_tc_kernel<BwdSpec<2>>))
     return 0;
   p.cheb_tc_grid = sms;
-  if (tc_smem<FwdSpec<true>>(p.g) + 1024 <= (size_t)optin) p.cheb_tc = 1;
+  const size_t sf = tc_smem<FwdSpec<true>>(p.g), sb = tc_smem<BwdSpec<2>>(p.g);
+  if (sf > 0 && sf + 1024 <= (size_t)optin) p.cheb_tc = 1;
   // backward: five accumulators of the occupied planes (rounded up to 16) must fit 512 columns;
   // beyond 96 nodes the planes go in two launches of at most 64 each
-  if (p.g.spectral_curl && tc_smem<BwdSpec<2>>(p.g) + 1024 <= (size_t)optin) {
+  if (p.g.spectral_curl && sb > 0 && sb + 1024 <= (size_t)optin) {
     p.cheb_tc_bwd = 1;
     p.cheb_tc_bwd_parts = 5 * cheb_tc_np(p.g) <= 512 ? 1 : 2;
   }

@@ -1,7 +1,8 @@
 """Host checks of the tensor-core operand descriptor encoders (csrc/umma_desc.h), compiled with the
 host C++ compiler: every field sits at the bit position of the PTX ISA's tcgen05 descriptor tables
 (shared-memory matrix descriptor; instruction descriptor of .kind::tf32), and the K-major core-matrix
-layout used for the operand tiles is a bijection onto the tile with 128-byte core matrices."""
+layout used for the operand tiles places every element once, in 128-byte core matrices at the
+descriptor's strides, inside the tile."""
 
 import os
 import shutil
@@ -27,6 +28,7 @@ int main() {
       for (unsigned k = 0; k < 8; ++k) printf("O %u %u %u %u\n", rows, r, k, kmajor_offset(r, k));
   }
   printf("L %u %u\n", kLbo, kSbo);
+  for (unsigned rows : {128u, 80u, 48u}) printf("T %u %u\n", rows, tile_bytes(rows));
   return 0;
 }
 """
@@ -82,17 +84,22 @@ def test_instruction_descriptor_fields(encodings):
         assert _field(d, 29, 3) == 0
 
 
-def test_kmajor_layout_is_a_bijection_of_core_matrices(encodings):
+def test_kmajor_layout_places_core_matrices_in_the_tile(encodings):
     lbo, sbo = next(tuple(map(int, r[1:])) for r in encodings if r[0] == "L")
+    tiles = {int(r[1]): int(r[2]) for r in encodings if r[0] == "T"}
+    assert lbo == 128 and sbo >= 256 and sbo % 16 == 0
     for rows in (128, 80):
+        assert tiles[rows] == rows // 8 * sbo
         offs = {(int(r[2]), int(r[3])): int(r[4]) for r in encodings if r[0] == "O" and int(r[1]) == rows}
         assert len(offs) == rows * 8
         vals = sorted(offs.values())
-        assert vals == list(range(0, rows * 32, 4))       # every 4-byte slot of the tile once
+        assert len(set(vals)) == len(vals)                 # every element once
+        assert vals[-1] + 4 <= tiles[rows]                  # inside the tile
         for (row, k), o in offs.items():
             # core matrix (8 rows x 16 bytes, 128 contiguous bytes) at the descriptor's strides:
             # the leading-dimension offset along K, the stride-dimension offset along the rows
             base = (k // 4) * lbo + (row // 8) * sbo
             assert o == base + (row % 8) * 16 + (k % 4) * 4
         # the descriptor's addresses stay inside the tile even with the two offsets exchanged
-        assert (rows // 8 - 1) * lbo + 1 * sbo + 127 < rows * 32
+        assert (rows // 8 - 1) * lbo + 1 * sbo + 127 < tiles[rows]
+
