@@ -1268,7 +1268,7 @@ __global__ void __launch_bounds__(256) interp_pair_kernel(Geometry g, int64_t n,
 // at a time, and each warp gathers its particles from there: lane group g (6 x-lanes) takes plane
 // g of the four, walks the 6 support rows of that plane and adds the 6 fields (U from fields 0..2
 // with the monopole weights, Omega from fields 3..5 with the dipole weights; forces only: U from
-// fields 0..2).  Each of 15 gather warps holds the sums of its 2 particles of a batch of 30 across
+// fields 0..2).  Each of 15 gather warps holds the sums of its 3 particles of a batch of 45 across
 // the chunks and reduces them over its lanes at the end of the batch.
 // Staging: where the region does not cross the periodic boundary, one TMA box load per chunk
 // (44 x 14 x 4 x fields of the grid's tensor map) into one of two buffers, issued by a sixteenth
@@ -1291,7 +1291,7 @@ constexpr int kIsPieces = kIsSX / 4;        // 16-byte pieces per row
 constexpr int kIsRows = 14;                 // staged rows per plane (9 first-node rows + 5)
 constexpr int kIsPS = kIsSX * kIsRows;      // plane stride (values)
 constexpr int kIsFS = kIsGroups * kIsPS;    // field stride (values)
-constexpr int kIsSlots = 2;                 // particles per warp per batch
+constexpr int kIsSlots = 3;                 // particles per warp per batch
 constexpr int kIsThreads = 512;
 constexpr int kIsWarps = kIsThreads / 32;
 constexpr int kIsGatherWarps = kIsWarps - 1;  // the last warp issues the TMA loads
