@@ -133,14 +133,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       : "memory");
 }
 
-// D += A_hi B_hi + A_hi B_lo + A_lo B_hi (A's lo tile follows its hi tile by one A tile, B's by
-// b_lo_delta)
-__device__ __forceinline__ void mma3(uint32_t d, uint32_t a_hi, uint32_t b_hi, uint32_t b_lo_delta, uint32_t idesc,
+// D += A_hi B_hi + A_hi B_lo + A_lo B_hi from shared-memory descriptors (A's lo tile follows its
+// hi tile by one A tile, B's by b_lo16 16-byte units).  A descriptor's start address is its low
+// field in 16-byte units, so the descriptor of an operand `off` bytes further is the stage's
+// descriptor plus off >> 4 (shared addresses stay below 256 KB: the field never carries): the
+// single issuing thread adds instead of encoding each descriptor anew.
+__device__ __forceinline__ void mma3(uint32_t d, uint64_t a_hi, uint64_t b_hi, uint32_t b_lo16, uint32_t idesc,
                                      uint32_t accumulate) {
-  using namespace umma;
-  mma_tf32(d, smem_desc(a_hi, kLbo, kSbo), smem_desc(b_hi, kLbo, kSbo), idesc, accumulate);
-  mma_tf32(d, smem_desc(a_hi, kLbo, kSbo), smem_desc(b_hi + b_lo_delta, kLbo, kSbo), idesc, 1u);
-  mma_tf32(d, smem_desc(a_hi + kATile, kLbo, kSbo), smem_desc(b_hi, kLbo, kSbo), idesc, 1u);
+  constexpr uint64_t kALo16 = kATile >> 4;
+  mma_tf32(d, a_hi, b_hi, idesc, accumulate);
+  mma_tf32(d, a_hi, b_hi + b_lo16, idesc, 1u);
+  mma_tf32(d, a_hi + kALo16, b_hi, idesc, 1u);
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -290,15 +293,16 @@ struct FwdSpec {
     split_store(step + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)n, (uint32_t)(4 * kg)), x[0], x[1],
                 x[2], x[3]);
   }
-  __device__ static void mma(const Geometry&, uint32_t sbase, uint32_t tacc, int ks, int np, uint32_t idesc) {
-    const uint32_t btile = umma::tile_bytes((uint32_t)np);
-    const uint32_t bbase = sbase + 2 * NQ * kATile;
+  // sdesc: the descriptor of the stage's first byte
+  __device__ static void mma(const Geometry&, uint64_t sdesc, uint32_t tacc, int ks, int np, uint32_t idesc) {
+    const uint32_t bt16 = umma::tile_bytes((uint32_t)np) >> 4;
+    const uint64_t bbase = sdesc + ((2 * NQ * kATile) >> 4);
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
       const uint32_t d = tacc + (uint32_t)(o * np);
       const int qa = CURL ? 2 * o : o;
-      mma3(d, sbase + (uint32_t)(2 * qa) * kATile, bbase, btile, idesc, ks > 0 ? 1u : 0u);
-      if (CURL && o < 2) mma3(d, sbase + (uint32_t)(2 * (2 * o + 1)) * kATile, bbase + 2 * btile, btile, idesc, 1u);
+      mma3(d, sdesc + ((2 * qa * kATile) >> 4), bbase, bt16, idesc, ks > 0 ? 1u : 0u);
+      if (CURL && o < 2) mma3(d, sdesc + ((2 * (2 * o + 1) * kATile) >> 4), bbase + 2 * bt16, bt16, idesc, 1u);
     }
   }
   // epilogue thread: TMEM lane `row` (wavenumber row >> 1, part row & 1); out_o[n] -> kbuf (zeros
@@ -454,16 +458,17 @@ struct BwdSpec {
                 x[2], x[3]);
   }
   // every step: u, v, w += A_f B0;  du += A_u B1, dv += A_v B1
-  __device__ static void mma(const Geometry&, uint32_t sbase, uint32_t tacc, int ks, int nq, uint32_t idesc) {
-    const uint32_t btile = umma::tile_bytes((uint32_t)nq);
-    const uint32_t b0 = sbase + 2 * NQ * kATile, b1 = b0 + 2 * btile;
+  // sdesc: the descriptor of the stage's first byte
+  __device__ static void mma(const Geometry&, uint64_t sdesc, uint32_t tacc, int ks, int nq, uint32_t idesc) {
+    const uint32_t bt16 = umma::tile_bytes((uint32_t)nq) >> 4;
+    const uint64_t b0 = sdesc + ((2 * NQ * kATile) >> 4), b1 = b0 + 2 * bt16;
     const uint32_t acc = ks > 0 ? 1u : 0u;
-    const uint32_t au = sbase, av = sbase + 2 * kATile, aw = sbase + 4 * kATile;
-    mma3(tacc + 0 * nq, au, b0, btile, idesc, acc);
-    mma3(tacc + 1 * nq, av, b0, btile, idesc, acc);
-    mma3(tacc + 2 * nq, aw, b0, btile, idesc, acc);
-    mma3(tacc + 3 * nq, au, b1, btile, idesc, acc);
-    mma3(tacc + 4 * nq, av, b1, btile, idesc, acc);
+    const uint64_t au = sdesc, av = sdesc + ((2 * kATile) >> 4), aw = sdesc + ((4 * kATile) >> 4);
+    mma3(tacc + 0 * nq, au, b0, bt16, idesc, acc);
+    mma3(tacc + 1 * nq, av, b0, bt16, idesc, acc);
+    mma3(tacc + 2 * nq, aw, b0, bt16, idesc, acc);
+    mma3(tacc + 3 * nq, au, b1, bt16, idesc, acc);
+    mma3(tacc + 4 * nq, av, b1, bt16, idesc, acc);
   }
   // epilogue thread: TMEM lane `row` = (wavenumber row >> 1, part row & 1); lanes 2j and 2j + 1 pair
   // up for the products with i
@@ -613,16 +618,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
   };
   if (warp < kEpiWarp0) {
     // ---- producers ------------------------------------------------------------------------
-    unsigned it = 0;  // K steps produced so far
+    int s = 0;        // stage of the next K step
+    unsigned ph = 0;  // its use parity (the stage ring's pass)
     typename Spec::Raw raw;
     int64_t tile = blockIdx.x;
     if (tile < ntiles && nks > 0) {
       TileK tk = tile_k(g, tile, tid & 63, kx0, w);
       Spec::load(g, a, clo, chi, 0, tk, raw);
       for (;;) {
-        for (int ks = 0; ks < nks; ++ks, ++it) {
-          const int s = it % nst;
-          if (!mbar_wait(&sh.empty[s], ((it / nst) & 1) ^ 1, stop)) { fail(); break; }
+        for (int ks = 0; ks < nks; ++ks) {
+          if (!mbar_wait(&sh.empty[s], ph ^ 1, stop)) { fail(); break; }
           unsigned char* st = smraw + (size_t)s * stage_bytes;
           const typename Spec::Raw cur = raw;
           // the next step's loads, issued before this step's stores
@@ -639,6 +644,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
           proxy_fence();
           if (tid != 0) mbar_arrive(&sh.full[s]);
           if (last) tk = ntk;
+          if (++s == nst) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
         if (*stop) break;
         tile += gridDim.x;
@@ -648,6 +657,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
   } else if (warp == kMmaWarp) {
     // ---- MMA issuer -----------------------------------------------------------------------
     unsigned it = 0, t = 0;
+    const uint64_t sdesc0 = umma::smem_desc(saddr(smraw), umma::kLbo, umma::kSbo);  // stage 0
+    int s = 0, ls = 0;           // stage of the next K step, of the last one issued
+    unsigned ph = 0, lph = 0;    // their use parities
     for (int64_t tile = blockIdx.x; tile < ntiles && nks > 0 && !*stop; tile += gridDim.x, ++t) {
       const int b = nbuf == 2 ? (int)(t & 1) : 0;
       const unsigned use = nbuf == 2 ? t >> 1 : t;  // earlier uses of this accumulator set
@@ -656,13 +668,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
       const uint32_t tacc = tmem + (uint32_t)(b * cols);
       bool ok = true;
       for (int ks = 0; ks < nks; ++ks, ++it) {
-        const int s = it % nst;
-        if (!mbar_wait(&sh.full[s], (it / nst) & 1, stop)) { fail(); ok = false; break; }
+        if (!mbar_wait(&sh.full[s], ph, stop)) { fail(); ok = false; break; }
         tc_fence_after();
+        ls = s;
+        lph = ph;
+        if (++s == nst) {
+          s = 0;
+          ph ^= 1u;
+        }
         if (inject) continue;  // failure injection: no MMAs and no completion signals
         if (lane == 0) {
-          Spec::mma(g, saddr(smraw + (size_t)s * stage_bytes), tacc, ks, nn, idesc);
-          mma_commit(&sh.empty[s]);  // the stage is free once these MMAs have read it
+          Spec::mma(g, sdesc0 + (((uint32_t)ls * stage_bytes) >> 4), tacc, ks, nn, idesc);
+          mma_commit(&sh.empty[ls]);  // the stage is free once these MMAs have read it
           if (ks + 1 == nks) mma_commit(&sh.acc_full[b]);
         }
         __syncwarp();
@@ -671,9 +688,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
     }
     // a stop: wait (bounded) for the MMAs already issued before the tensor memory is freed
     if (*stop && it > 0 && !inject) {
-      const unsigned last = it - 1;
       const long long t0 = clock64();
-      while (!mbar_test(&sh.empty[last % nst], (last / nst) & 1) && clock64() - t0 < kWaitCycles) {
+      while (!mbar_test(&sh.empty[ls], lph) && clock64() - t0 < kWaitCycles) {
       }
     }
   } else {

@@ -49,8 +49,7 @@ DPS_HD constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
 // offset kLbo = 128), 8-row groups follow each other (stride-dimension byte offset kSbo = 256).  A
 // tile of R rows spans tile_bytes(R) = (R / 8) * kSbo bytes; with offsets this small every address
 // the tensor core forms from the descriptor stays inside the tile.  (A padded stride of 272 bytes,
-// which makes the producers' 16-byte row stores conflict-free, measured 3 % faster for the forward
-// transform and 4 % slower for the backward one.)
+// which makes the producers' 16-byte row stores conflict-free, measured no faster.)
 constexpr uint32_t kLbo = 128, kSbo = 256;
 DPS_HD constexpr uint32_t kmajor_offset(uint32_t row, uint32_t k) {
   return (row >> 3) * kSbo + (k >> 2) * kLbo + (row & 7u) * 16u + (k & 3u) * 4u;

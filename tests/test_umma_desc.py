@@ -29,6 +29,13 @@ int main() {
   }
   printf("L %u %u\n", kLbo, kSbo);
   for (unsigned rows : {128u, 80u, 48u}) printf("T %u %u\n", rows, tile_bytes(rows));
+  // descriptor arithmetic used by the issuing thread: desc(a) + (off >> 4) == desc(a + off) for
+  // 16-byte aligned shared addresses below 256 KB
+  unsigned bad = 0;
+  for (unsigned a = 0; a < (1u << 18); a += 16 * 37)
+    for (unsigned off = 0; a + off < (1u << 18); off += 16 * 1021)
+      if (smem_desc(a, kLbo, kSbo) + (off >> 4) != smem_desc(a + off, kLbo, kSbo)) ++bad;
+  printf("A %u\n", bad);
   return 0;
 }
 """
@@ -103,3 +110,9 @@ def test_kmajor_layout_places_core_matrices_in_the_tile(encodings):
         # the descriptor's addresses stay inside the tile even with the two offsets exchanged
         assert (rows // 8 - 1) * lbo + 1 * sbo + 127 < tiles[rows]
 
+
+def test_descriptor_offsets_add(encodings):
+    """The issuing thread forms an operand's descriptor as the stage's descriptor plus the byte
+    offset in 16-byte units; that must equal encoding the operand's address (no carry out of the
+    14-bit start-address field for shared addresses below 256 KB)."""
+    assert next(int(r[1]) for r in encodings if r[0] == "A") == 0
