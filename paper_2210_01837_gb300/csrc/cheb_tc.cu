@@ -205,6 +205,8 @@ struct FwdSpec {
   static constexpr int NT = CURL ? 2 : 1;  // B operands: C (and DC)
   static constexpr int NACC = 3;
   static constexpr int NR = CURL ? 4 : 2;  // grid fields a producer thread reads per plane
+  static constexpr int kRingDepth = 0;      // loads one step ahead in registers (no staging ring)
+  static constexpr int kRingVals = 0;
   struct Args {
     const float* ct;   // [c][npad] C[n][c]
     const float* dct;  // [c][npad] DC[n][c]
@@ -354,8 +356,53 @@ struct BwdSpec {
   struct Raw {
     cplx<float> v[4][2];
   };
+  // the producers stage each step's values with cp.async kRingDepth - 1 steps ahead into a ring in
+  // shared memory (value e of thread t of a slot at slot[e * kProducers + t])
+  static constexpr int kRingDepth = 4;
+  static constexpr int kRingVals = 8;
   __host__ __device__ static int ncoef(const Geometry& g) { return (g.nz + kTcK - 1) / kTcK; }
   __host__ __device__ static int nks(const Geometry& g, int, int) { return ncoef(g) * (CORR ? 2 : 1); }
+  // the values `load` would read, copied asynchronously into ring slot `slot` (zeros where load
+  // reads none); completes in the calling thread's current cp.async group
+  __device__ static void load_async(const Geometry& g, const Args& a, int ks, const TileK& tk, cplx<float>* slot) {
+    const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int64_t K = (int64_t)g.nkx * g.ny;
+    const int N = g.nz;
+    const bool ok = tk.col >= 0;
+    if (ks < ncoef(g)) {
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int n = ks * kTcK + 4 * grp + cc;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int f = half == 0 ? q : 2;
+          const bool want = ok && n < N && (half == 0 || q == 0);
+          cplx<float>* dst = slot + (cc * 2 + q) * kProducers + tid;
+          if (want) cp_async8(dst, a.kbuf + ((size_t)f * N + n) * K + tk.kid);
+          else *dst = mk<float>(0.f, 0.f);
+        }
+      }
+    } else {
+      const bool amp = ok && tk.kid > 0 && !is_nyquist(g, tk.kid);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi) {
+          const int f = half == 0 ? fi : 2;
+          const bool want = amp && (q < 2 || CORR == 2) && (half == 0 || fi == 0);
+          cplx<float>* dst = slot + (q * 2 + fi) * kProducers + tid;
+          if (want) cp_async8(dst, a.kaux + (size_t)(4 * f + q) * K + tk.kid);
+          else *dst = mk<float>(0.f, 0.f);
+        }
+    }
+  }
+  __device__ static void from_ring(const cplx<float>* slot, Raw& r) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) r.v[i][q] = slot[(i * 2 + q) * kProducers + tid];
+  }
   __device__ static void load(const Geometry& g, const Args& a, int, int, int ks, const TileK& tk, Raw& r) {
     const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
     const int64_t K = (int64_t)g.nkx * g.ny;
@@ -584,7 +631,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
   const uint32_t stage_bytes = Spec::stage_bytes(nmax);
   uint32_t dyn;
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-  const int nst = min(kStages, (int)((dyn - 1024u) / stage_bytes));  // operand stages launched with
+  constexpr uint32_t kRingBytes = (uint32_t)(Spec::kRingDepth * Spec::kRingVals * kProducers * 8);
+  const int nst = min(kStages, (int)((dyn - 1024u - kRingBytes) / stage_bytes));  // operand stages launched with
   const int nks = Spec::nks(g, clo, chi);
   const uint32_t idesc = umma::idesc_tf32(kTcRows, (uint32_t)nn);
   volatile int* stop = &sh.stop;
@@ -616,7 +664,64 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
       atomicOr(status, kStatTimeout);
     }
   };
-  if (warp < kEpiWarp0) {
+  if constexpr (Spec::kRingDepth > 0) {
+    if (warp < kEpiWarp0) {
+      // ---- producers, staging through the ring --------------------------------------------
+      constexpr int D = Spec::kRingDepth;
+      cplx<float>* ring = reinterpret_cast<cplx<float>*>(smraw + (size_t)nst * stage_bytes);
+      auto slot = [&](int i) { return ring + (size_t)i * Spec::kRingVals * kProducers; };
+      if (blockIdx.x < ntiles && nks > 0) {
+        int64_t lt = blockIdx.x, st_tile = blockIdx.x;  // tiles of the next step to stage / to store
+        int lks = 0, sks = 0;
+        TileK ltk = tile_k(g, lt, tid & 63, kx0, w), stk = ltk;
+        // one cp.async group per step (an empty one past the last step), so that waiting for all
+        // but the D - 1 newest groups completes the current step's
+        auto stage_next = [&](int i) {
+          if (lt < ntiles) Spec::load_async(g, a, lks, ltk, slot(i));
+          cp_commit();
+          if (++lks == nks) {
+            lks = 0;
+            lt += gridDim.x;
+            if (lt < ntiles) ltk = tile_k(g, lt, tid & 63, kx0, w);
+          }
+        };
+        for (int i = 0; i < D - 1; ++i) stage_next(i);
+        int s = 0, rs = 0, ws = D - 1;  // operand stage; ring slots to read / to fill
+        unsigned ph = 0;
+        for (;;) {
+          if (!mbar_wait(&sh.empty[s], ph ^ 1, stop)) { fail(); break; }
+          unsigned char* st = smraw + (size_t)s * stage_bytes;
+          if (tid == 0) {
+            mbar_arrive_tx(&sh.full[s], bbytes);
+            bulk_copy(st + 2 * Spec::NQ * kATile, bimg + (size_t)sks * bbytes, bbytes, &sh.full[s]);
+          }
+          stage_next(ws);
+          ws = ws + 1 == D ? 0 : ws + 1;
+          asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 1) : "memory");
+          typename Spec::Raw cur;
+          Spec::from_ring(slot(rs), cur);
+          rs = rs + 1 == D ? 0 : rs + 1;
+          Spec::store(g, a, clo, chi, sks, stk, cur, st, nn);
+          proxy_fence();
+          if (tid != 0) mbar_arrive(&sh.full[s]);
+          if (++s == nst) {
+            s = 0;
+            ph ^= 1u;
+          }
+          if (++sks == nks) {
+            sks = 0;
+            st_tile += gridDim.x;
+            if (st_tile >= ntiles || *stop) break;
+            stk = tile_k(g, st_tile, tid & 63, kx0, w);
+          }
+        }
+        cp_wait_all();  // no copy into the ring outlives the loop
+      }
+    }
+  }
+  if (Spec::kRingDepth > 0 && warp < kEpiWarp0) {
+    // the producers above
+  } else if (warp < kEpiWarp0) {
     // ---- producers ------------------------------------------------------------------------
     int s = 0;        // stage of the next K step
     unsigned ph = 0;  // its use parity (the stage ring's pass)
@@ -724,8 +829,9 @@ template <typename Spec>
 size_t tc_smem(const Geometry& g) {
   // as many operand stages as fit (at most kStages); 0 when fewer than two fit
   const size_t sb = Spec::stage_bytes((g.nz + 15) / 16 * 16);
-  const size_t n = std::min<size_t>(kStages, (kTcSmemCap - 1024) / sb);
-  return n >= 2 ? n * sb + 1024 : 0;
+  const size_t ring = (size_t)Spec::kRingDepth * Spec::kRingVals * kProducers * 8;
+  const size_t n = std::min<size_t>(kStages, (kTcSmemCap - 1024 - ring) / sb);
+  return n >= 2 ? n * sb + ring + 1024 : 0;
 }
 
 template <typename Spec>
