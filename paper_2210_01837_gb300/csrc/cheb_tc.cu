@@ -18,7 +18,9 @@
 //             du = ICD y_u + SD corr_u, dv = ICD y_v + SD corr_v, where corr_f(z_j) is the wall
 //             correction at node j (bottom family (cE + cG zeta) e^{-k zeta}, top family
 //             (tE + tG xi) e^{-k xi}) and SD = ICD C its spectral derivative (reading B2); five
-//             accumulators.  The epilogue adds corr_f at the output nodes, forms
+//             accumulators, [u | du] and [v | dv] each filled by one MMA of N = 2 planes against
+//             [IC | ICD] (or [I | SD]), so that A_u and A_v are read once per step.  The epilogue
+//             adds corr_f at the output nodes, forms
 //             omega = (1/2)(i ky w - dv, du - i kx w, i kx v - i ky u) and scales by 1/(Nx Ny).
 //
 // The block is persistent over 64-wavenumber tiles and warp-specialised:
@@ -500,22 +502,22 @@ struct BwdSpec {
       }
       x[cc] = v;
     }
+    // [B0; B1] as one operand of 2 nq rows (hi), its lo part 2 btile further
     const uint32_t btile = umma::tile_bytes((uint32_t)nq);
-    split_store(step + (size_t)(2 * tab) * btile, btile, umma::kmajor_offset((uint32_t)p, (uint32_t)(4 * kg)), x[0], x[1],
-                x[2], x[3]);
+    split_store(step, 2 * btile, umma::kmajor_offset((uint32_t)(tab * nq + p), (uint32_t)(4 * kg)), x[0], x[1], x[2],
+                x[3]);
   }
-  // every step: u, v, w += A_f B0;  du += A_u B1, dv += A_v B1
+  // every step: [u | du] += A_u [B0 | B1], [v | dv] += A_v [B0 | B1] (N = 2 nq), w += A_w B0
   // sdesc: the descriptor of the stage's first byte
   __device__ static void mma(const Geometry&, uint64_t sdesc, uint32_t tacc, int ks, int nq, uint32_t idesc) {
-    const uint32_t bt16 = umma::tile_bytes((uint32_t)nq) >> 4;
-    const uint64_t b0 = sdesc + ((2 * NQ * kATile) >> 4), b1 = b0 + 2 * bt16;
+    const uint32_t lo16 = (2 * umma::tile_bytes((uint32_t)nq)) >> 4;  // the lo block of [B0; B1]
+    const uint64_t b0 = sdesc + ((2 * NQ * kATile) >> 4);
     const uint32_t acc = ks > 0 ? 1u : 0u;
+    const uint32_t idesc2 = idesc + (((uint32_t)nq >> 3) << 17);  // N = 2 nq (the N >> 3 field doubled)
     const uint64_t au = sdesc, av = sdesc + ((2 * kATile) >> 4), aw = sdesc + ((4 * kATile) >> 4);
-    mma3(tacc + 0 * nq, au, b0, bt16, idesc, acc);
-    mma3(tacc + 1 * nq, av, b0, bt16, idesc, acc);
-    mma3(tacc + 2 * nq, aw, b0, bt16, idesc, acc);
-    mma3(tacc + 3 * nq, au, b1, bt16, idesc, acc);
-    mma3(tacc + 4 * nq, av, b1, bt16, idesc, acc);
+    mma3(tacc + 0 * nq, au, b0, lo16, idesc2, acc);  // u, du
+    mma3(tacc + 2 * nq, av, b0, lo16, idesc2, acc);  // v, dv
+    mma3(tacc + 4 * nq, aw, b0, lo16, idesc, acc);   // w
   }
   // epilogue thread: TMEM lane `row` = (wavenumber row >> 1, part row & 1); lanes 2j and 2j + 1 pair
   // up for the products with i
@@ -531,10 +533,10 @@ struct BwdSpec {
     for (int p0 = 0; p0 < nq; p0 += 8) {
       float u[8], v[8], w[8], du[8], dv[8];
       tmem_ld8(tlane + (uint32_t)(0 * nq + p0), u);
-      tmem_ld8(tlane + (uint32_t)(1 * nq + p0), v);
-      tmem_ld8(tlane + (uint32_t)(2 * nq + p0), w);
-      tmem_ld8(tlane + (uint32_t)(3 * nq + p0), du);
-      tmem_ld8(tlane + (uint32_t)(4 * nq + p0), dv);
+      tmem_ld8(tlane + (uint32_t)(1 * nq + p0), du);
+      tmem_ld8(tlane + (uint32_t)(2 * nq + p0), v);
+      tmem_ld8(tlane + (uint32_t)(3 * nq + p0), dv);
+      tmem_ld8(tlane + (uint32_t)(4 * nq + p0), w);
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int c = clo + p0 + t;
