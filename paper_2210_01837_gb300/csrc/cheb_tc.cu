@@ -153,14 +153,21 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 8 consecutive 32-bit columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
+// 8 consecutive 32-bit columns of this thread's tensor-memory lane, in two steps so that several
+// loads share one wait: issue, then wait8 on each issued group (the first wait covers every load
+// issued before it; each wait also ties its group's registers, so that no use of them is scheduled
+// before the wait)
+__device__ __forceinline__ void tmem_issue8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr)
                : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait8(uint32_t (&r)[8], float (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
@@ -317,15 +324,22 @@ struct FwdSpec {
     const int N = g.nz, part = row & 1;
     float* kb = reinterpret_cast<float*>(a.kbuf) + 2 * (size_t)tk.kid + part;
     const size_t nstride = 2 * (size_t)K;
-    for (int o = 0; o < 3; ++o) {
-      for (int n0 = 0; n0 < np; n0 += 8) {
-        float v[8];
-        if (any) tmem_ld8(tlane + (uint32_t)(o * np + n0), v);
-        if (tk.col < 0) continue;
+    for (int n0 = 0; n0 < np; n0 += 8) {
+      float v[3][8];
+      if (any) {
+        uint32_t r[3][8];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) tmem_issue8(tlane + (uint32_t)(o * np + n0), r[o]);
+#pragma unroll
+        for (int o = 0; o < 3; ++o) tmem_wait8(r[o], v[o]);
+      }
+      if (tk.col < 0) continue;
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
         float* dst = kb + ((size_t)o * N + n0) * nstride;
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-          if (n0 + t < N) dst[(size_t)t * nstride] = any ? v[t] : 0.f;
+          if (n0 + t < N) dst[(size_t)t * nstride] = any ? v[o][t] : 0.f;
       }
     }
   }
@@ -532,11 +546,14 @@ struct BwdSpec {
     const float hx = tk.hkx * scale, hy = tk.hky * scale, hs = 0.5f * scale;
     for (int p0 = 0; p0 < nq; p0 += 8) {
       float u[8], v[8], w[8], du[8], dv[8];
-      tmem_ld8(tlane + (uint32_t)(0 * nq + p0), u);
-      tmem_ld8(tlane + (uint32_t)(1 * nq + p0), du);
-      tmem_ld8(tlane + (uint32_t)(2 * nq + p0), v);
-      tmem_ld8(tlane + (uint32_t)(3 * nq + p0), dv);
-      tmem_ld8(tlane + (uint32_t)(4 * nq + p0), w);
+      uint32_t r[5][8];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) tmem_issue8(tlane + (uint32_t)(q * nq + p0), r[q]);
+      tmem_wait8(r[0], u);
+      tmem_wait8(r[1], du);
+      tmem_wait8(r[2], v);
+      tmem_wait8(r[3], dv);
+      tmem_wait8(r[4], w);
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int c = clo + p0 + t;
