@@ -28,7 +28,8 @@
 //               registers), form and split the step's A operands and store them in the K-major
 //               core-matrix layout of one of kStages shared-memory stages, while one thread
 //               bulk-copies the step's B operands there from a per-product image (tc_bimage_kernel);
-//               arrive on the stage's `full` barrier;
+//               each thread fences its stores for the async proxy, and one lane per warp arrives
+//               on the stage's `full` barrier (warp-uniform waits and exits, decided by votes);
 //   warp 12     MMA issuer: waits for a full stage (and, at a tile's first step, for a free
 //               accumulator set), issues the step's MMAs, commits them to the stage's `empty`
 //               barrier and, after a tile's last step, to the accumulator set's `full` barrier;
@@ -63,11 +64,8 @@ constexpr long long kWaitCycles = 1ll << 31;     // bounded waits: about one sec
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
+// tf32 hi part of a float on the integer pipe (no conversion instruction; see tf32_rna_bits)
+__device__ __forceinline__ float tf32_rna(float x) { return __uint_as_float(umma::tf32_rna_bits(__float_as_uint(x))); }
 
 // four K-consecutive values of one operand row, split into the hi tile and the lo tile that
 // follows it `lo_delta` bytes later
@@ -657,7 +655,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
   volatile int* stop = &sh.stop;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&sh.full[s], kProducers);
+      mbar_init(&sh.full[s], kProducers / 32 + 1);  // a lane of each producer warp, and the B copy's arming
       mbar_init(&sh.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -708,7 +706,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
         int s = 0, rs = 0, ws = D - 1;  // operand stage; ring slots to read / to fill
         unsigned ph = 0;
         for (;;) {
-          if (!mbar_wait(&sh.empty[s], ph ^ 1, stop)) { fail(); break; }
+          // warp-uniform decisions: the warp's lanes arrive once, together (see below)
+          if (!__all_sync(0xffffffffu, mbar_wait(&sh.empty[s], ph ^ 1, stop))) { fail(); break; }
           unsigned char* st = smraw + (size_t)s * stage_bytes;
           if (tid == 0) {
             mbar_arrive_tx(&sh.full[s], bbytes);
@@ -722,7 +721,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
           rs = rs + 1 == D ? 0 : rs + 1;
           Spec::store(g, a, clo, chi, sks, stk, cur, st, nn);
           proxy_fence();
-          if (tid != 0) mbar_arrive(&sh.full[s]);
+          __syncwarp();  // the warp's stores, each fenced by its thread, before its one arrival
+          if (lane == 0) mbar_arrive(&sh.full[s]);
           if (++s == nst) {
             s = 0;
             ph ^= 1u;
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
           if (++sks == nks) {
             sks = 0;
             st_tile += gridDim.x;
-            if (st_tile >= ntiles || *stop) break;
+            if (__any_sync(0xffffffffu, st_tile >= ntiles || *stop)) break;
             stk = tile_k(g, st_tile, tid & 63, kx0, w);
           }
         }
@@ -751,7 +751,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
       Spec::load(g, a, clo, chi, 0, tk, raw);
       for (;;) {
         for (int ks = 0; ks < nks; ++ks) {
-          if (!mbar_wait(&sh.empty[s], ph ^ 1, stop)) { fail(); break; }
+          // warp-uniform decisions: the warp's lanes arrive once, together (see below)
+          if (!__all_sync(0xffffffffu, mbar_wait(&sh.empty[s], ph ^ 1, stop))) { fail(); break; }
           unsigned char* st = smraw + (size_t)s * stage_bytes;
           const typename Spec::Raw cur = raw;
           // the next step's loads, issued before this step's stores
@@ -766,14 +767,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
           if (ntile < ntiles) Spec::load(g, a, clo, chi, last ? 0 : ks + 1, ntk, raw);
           Spec::store(g, a, clo, chi, ks, tk, cur, st, nn);
           proxy_fence();
-          if (tid != 0) mbar_arrive(&sh.full[s]);
+          __syncwarp();  // the warp's stores, each fenced by its thread, before its one arrival
+          if (lane == 0) mbar_arrive(&sh.full[s]);
           if (last) tk = ntk;
           if (++s == nst) {
             s = 0;
             ph ^= 1u;
           }
         }
-        if (*stop) break;
+        if (__any_sync(0xffffffffu, *stop != 0)) break;
         tile += gridDim.x;
         if (tile >= ntiles) break;
       }

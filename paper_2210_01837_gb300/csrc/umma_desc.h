@@ -56,5 +56,11 @@ DPS_HD constexpr uint32_t kmajor_offset(uint32_t row, uint32_t k) {
 }
 DPS_HD constexpr uint32_t tile_bytes(uint32_t rows) { return (rows >> 3) * kSbo; }
 
+// tf32 rounding of a float's bit pattern, to nearest with ties away from zero (the rounding of
+// cvt.rna.tf32.f32): add half of the 13 dropped mantissa bits' range to the magnitude bits (the
+// sign bit is untouched; a carry moves into the exponent as rounding up should) and clear them.
+// Integer operations only, for finite inputs.
+DPS_HD constexpr uint32_t tf32_rna_bits(uint32_t x) { return (x + 0x1000u) & 0xFFFFE000u; }
+
 }  // namespace umma
 }  // namespace dps

@@ -36,6 +36,15 @@ int main() {
     for (unsigned off = 0; a + off < (1u << 18); off += 16 * 1021)
       if (smem_desc(a, kLbo, kSbo) + (off >> 4) != smem_desc(a + off, kLbo, kSbo)) ++bad;
   printf("A %u\n", bad);
+  // tf32 rounding of a spread of bit patterns (printed for the comparison in Python)
+  unsigned long long seed = 12345;
+  for (int i = 0; i < 20000; ++i) {
+    seed = seed * 6364136223846793005ull + 1442695040888963407ull;
+    unsigned x = (unsigned)(seed >> 32);
+    if ((x & 0x7F800000u) == 0x7F800000u) continue;  // finite inputs only
+    if (i % 7 == 0) x = (x & ~0x1FFFu) | 0x1000u;       // exact ties
+    printf("R %u %u\n", x, tf32_rna_bits(x));
+  }
   return 0;
 }
 """
@@ -116,3 +125,27 @@ def test_descriptor_offsets_add(encodings):
     offset in 16-byte units; that must equal encoding the operand's address (no carry out of the
     14-bit start-address field for shared addresses below 256 KB)."""
     assert next(int(r[1]) for r in encodings if r[0] == "A") == 0
+
+
+def test_tf32_rounding_is_round_to_nearest_ties_away(encodings):
+    """tf32_rna_bits against the definition: the nearest float with 10 mantissa bits, halfway cases
+    away from zero, computed exactly with Python integers and fractions (finite inputs; a carry may
+    reach infinity, as rounding up at the top of the range should)."""
+    from fractions import Fraction
+
+    def value(b):
+        s, e, m = b >> 31, (b >> 23) & 0xFF, b & 0x7FFFFF
+        v = Fraction(m, 1 << 23) * Fraction(2) ** (-126) if e == 0 else (1 + Fraction(m, 1 << 23)) * Fraction(2) ** (e - 127)
+        return -v if s else v
+
+    rows = [(int(r[1]), int(r[2])) for r in encodings if r[0] == "R"]
+    assert len(rows) > 15000
+    for x, y in rows:
+        assert y & 0x1FFF == 0 and (y >> 31) == (x >> 31)
+        if (y & 0x7F800000) == 0x7F800000:
+            continue  # rounded past the largest tf32 value
+        lo = x & ~0x1FFF                      # truncated (toward zero) tf32 neighbour
+        hi = lo + 0x2000                      # the next one away from zero
+        vx, vlo, vhi = abs(value(x)), abs(value(lo)), abs(value(hi))
+        want = hi if (vx - vlo) >= (vhi - vx) else lo
+        assert y == want, (hex(x), hex(y), hex(want))
