@@ -64,6 +64,14 @@ constexpr long long kWaitCycles = 1ll << 31;     // bounded waits: about one sec
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// 2^x by the special-function unit's approximation (ex2.approx; results below the normal range
+// flush to zero)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // tf32 hi part of a float on the integer pipe (no conversion instruction; see tf32_rna_bits)
 __device__ __forceinline__ float tf32_rna(float x) { return __uint_as_float(umma::tf32_rna_bits(__float_as_uint(x))); }
 
@@ -461,18 +469,21 @@ struct BwdSpec {
           im[q][cc] = r.v[cc][q].y;
         }
     } else {
-      // corr_f at the step's nodes: (cE + cG zeta) e^{-k zeta} (+ (tE + tG xi) e^{-k xi})
+      // corr_f at the step's nodes: (cE + cG zeta) e^{-k zeta} (+ (tE + tG xi) e^{-k xi}), the
+      // exponentials as 2^(-k log2(e) zeta) on the special-function unit (relative error about
+      // 2^-22, and |k log2(e) zeta| 2^-24 from the rounded argument: float level)
       const int j0 = (ks - ncoef(g)) * kTcK + 4 * grp;
+      const float kl = -tk.kk * 1.4426950408889634f;  // -k log2(e)
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int jn = j0 + cc;
         float z = 0.f, eb = 0.f, xi = 0.f, et = 0.f;
         if (jn < N) {
           z = a.zeta[jn];
-          eb = expf(-tk.kk * z);
+          eb = ex2_approx(kl * z);
           if (CORR == 2) {
             xi = a.zeta[N - 1 - jn];
-            et = expf(-tk.kk * xi);
+            et = ex2_approx(kl * xi);
           }
         }
 #pragma unroll
@@ -633,6 +644,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
                                                                 int nparts) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ TcShared sh;
+  __shared__ float s_zeta[128];  // backward: the node heights, read by every node step
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int clo = zrange[0], chi = zrange[1];
   tc_part(clo, chi, part, nparts);  // the backward transform's output planes of this launch
@@ -671,9 +683,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  if constexpr (!Spec::kForward) {
+    for (int i = tid; i < g.nz; i += kTcThreads) s_zeta[i] = a.zeta[i];  // nz <= 128 here
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if constexpr (!Spec::kForward) a.zeta = s_zeta;
   const uint32_t tmem = sh.tmem;
   auto fail = [&]() {
     if (!*stop) {
