@@ -1271,7 +1271,7 @@ __global__ void __launch_bounds__(256) interp_pair_kernel(Geometry g, int64_t n,
 // fields 0..2).  Each of 15 gather warps holds the sums of its 3 particles of a batch of 45 across
 // the chunks and reduces them over its lanes at the end of the batch.
 // Staging: where the region does not cross the periodic boundary, one TMA box load per chunk
-// (44 x 14 x 4 x fields of the grid's tensor map) into one of two buffers, issued by a sixteenth
+// (44 x 14 x 4 x fields of the grid's tensor map) into one of three buffers, issued by a sixteenth
 // warp: a buffer's `full` barrier completes with the load's bytes, its `empty` barrier when all
 // gather warps have read it, and the producer waits for `empty` before loading the next chunk into
 // it, so a gather warp waits only for the chunk it needs next.  Each wait is bounded (about a
@@ -1310,7 +1310,8 @@ struct IsSlot {
 };
 
 __host__ __device__ constexpr size_t interp_stage_buf(int nf) { return (size_t)nf * kIsFS * sizeof(float); }
-__host__ __device__ constexpr size_t interp_stage_smem(int nf) { return 2 * interp_stage_buf(nf) + 128; }
+constexpr int kIsBufs = 3;  // chunk buffers: TMA loads in flight while the warps read one
+__host__ __device__ constexpr size_t interp_stage_smem(int nf) { return kIsBufs * interp_stage_buf(nf) + 128; }
 
 // offset of node v from t0 on a periodic axis of n nodes, in (-n/2, n/2]
 __device__ __forceinline__ int rel_node(int v, int t0, int n) {
@@ -1365,7 +1366,7 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
   extern __shared__ __align__(128) unsigned char is_raw[];
   // two chunk buffers, 128-byte aligned (TMA destinations)
   float* const sg = reinterpret_cast<float*>(is_raw + ((128u - (smem_u32(is_raw) & 127u)) & 127u));
-  __shared__ __align__(8) uint64_t s_full[2], s_empty[2];
+  __shared__ __align__(8) uint64_t s_full[kIsBufs], s_empty[kIsBufs];
   __shared__ int s_b[6];           // bounds: ox min/max, oy min/max, z begin/end
   __shared__ int s_xo[kIsSX];      // wrapped x of each staged column (cp.async path)
   __shared__ int s_yo[kIsRows];    // wrapped y of each staged row times the row length
@@ -1422,7 +1423,7 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
     }
   }
   if (tma && tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kIsBufs; ++i) {
       is_bar_init(&s_full[i], 1);
       is_bar_init(&s_empty[i], GW);
     }
@@ -1520,13 +1521,13 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
   if (tma) {
     constexpr unsigned kBoxBytes = (unsigned)interp_stage_buf(NF);
     if (warp == GW) {
-      // producer: the TMA load of each step's chunk into buffer step & 1 once the gather warps
-      // have released the buffer's previous contents
+      // producer: the TMA load of each step's chunk into buffer step mod kIsBufs once the gather
+      // warps have released the buffer's previous contents (its use u - 1)
       if (lane == 0) {
-        int issued = 0;
+        int issued = 0, bb = 0, kz = 0;
+        unsigned u = 0;  // use of buffer bb
         for (int step = 0; step < total; ++step) {
-          const int bb = step & 1;
-          if (step >= 2 && !is_wait(&s_empty[bb], (unsigned)((step - 2) >> 1) & 1u, fail_flag)) {
+          if (step >= kIsBufs && !is_wait(&s_empty[bb], (u - 1u) & 1u, fail_flag)) {
             if (!*fail_flag) atomicOr(status, kStatTimeout);
             *fail_flag = 1;
             break;
@@ -1534,21 +1535,27 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
           if (*fail_flag) break;
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of the buffer came first
           is_expect_tx(&s_full[bb], kBoxBytes);
-          is_tma_4d(sg + bb * BUFV, &tmap, xlo4, ylo, zlo + (step % nch) * ZC, 0, &s_full[bb]);
+          is_tma_4d(sg + bb * BUFV, &tmap, xlo4, ylo, zlo + kz * ZC, 0, &s_full[bb]);
           ++issued;
+          if (++kz == nch) kz = 0;
+          if (++bb == kIsBufs) {
+            bb = 0;
+            ++u;
+          }
         }
         // loads still in flight (a stop): wait, bounded, for the last one of each buffer
-        for (int st = issued - 2 < 0 ? 0 : issued - 2; st < issued; ++st)
-          is_wait(&s_full[st & 1], (unsigned)(st >> 1) & 1u, nullptr);
+        for (int st = issued - kIsBufs < 0 ? 0 : issued - kIsBufs; st < issued; ++st)
+          is_wait(&s_full[st % kIsBufs], (unsigned)(st / kIsBufs) & 1u, nullptr);
       }
     } else {
+      int batch = 0, k = 0, bb = 0;
+      unsigned u = 0;
       for (int step = 0; step < total; ++step) {
-        const int batch = step / nch, k = step - batch * nch, bb = step & 1;
         if (k == 0) {
           zero_acc();
           fill_tables(batch);
         }
-        if (!is_wait(&s_full[bb], (unsigned)(step >> 1) & 1u, fail_flag)) {
+        if (!is_wait(&s_full[bb], u & 1u, fail_flag)) {
           if (!*fail_flag) atomicOr(status, kStatTimeout);
           *fail_flag = 1;
           break;
@@ -1557,6 +1564,14 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
         __syncwarp();
         if (lane == 0) is_arrive(&s_empty[bb]);
         if (k == nch - 1) finish(batch);
+        if (++bb == kIsBufs) {
+          bb = 0;
+          ++u;
+        }
+        if (++k == nch) {
+          k = 0;
+          ++batch;
+        }
       }
     }
     __syncthreads();
