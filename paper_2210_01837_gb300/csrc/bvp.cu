@@ -338,12 +338,12 @@ __device__ __noinline__ void zero_mode(const Geometry& g, const double* __restri
 // form (reading B3), slip lengths and wall velocities Eqs. A3, A8.  Written to kaux as the
 // node-value coefficients (cE + cG zeta) e^{-k zeta} + (tE + tG xi) e^{-k xi} per field.
 template <typename T, bool SLIP>
-__device__ __forceinline__ void wall_amplitudes(const Geometry& g, double kx, double ky, double kk,
+__device__ __forceinline__ void wall_amplitudes(const Geometry& g, double kx, double ky, double kk, double ik,
                                                 const cplx<double> (&vtop)[3], const cplx<double> (&vbot)[3],
                                                 const cplx<double> (&dtop)[2], const cplx<double> (&dbot)[2],
                                                 cplx<T>* __restrict__ kaux, int64_t kidx, int64_t K) {
   auto AUX = [&](int q) -> cplx<T>& { return kaux[(size_t)q * K + kidx]; };
-  const double sH = 2.0 / g.H;
+  const double sH = g.sH;
   (void)dtop;
   (void)dbot;
   (void)sH;
@@ -351,7 +351,7 @@ __device__ __forceinline__ void wall_amplitudes(const Geometry& g, double kx, do
 #pragma unroll
   for (int f = 0; f < 3; ++f) { cE[f] = cG[f] = tE[f] = tG[f] = mk<double>(0, 0); }
   if (g.mode != DPS_FREE) {
-    const double ex = kx / kk, ey = ky / kk;
+    const double ex = kx * ik, ey = ky * ik;  // ik = 1 / k
     auto Lp = [&](cplx<double> u, cplx<double> v) { return scl(u, ex) + scl(v, ey); };
     auto Tp = [&](cplx<double> u, cplx<double> v) { return scl(v, ex) - scl(u, ey); };
     // wall data (Eq. A3): minus the DP velocity, and with slip u_DP - l0 du_DP/dz at the bottom,
@@ -605,8 +605,9 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
   }
 
   // ---- velocity: three right-hand sides sharing the factorisation -------------------------------
-  const cplx<double> ik_top = scl(ptop, 1.0 / (2.0 * kk * g.eta));
-  const cplx<double> ik_bot = scl(pbot, 1.0 / (2.0 * kk * g.eta));
+  const double ik = 1.0 / kk;  // the one division per wavenumber
+  const cplx<double> ik_top = scl(ptop, 0.5 * inv_eta * ik);
+  const cplx<double> ik_bot = scl(pbot, 0.5 * inv_eta * ik);
   cplx<double> gt[3], gb[3];
   gt[0] = scl(mul_i(ik_top), -kx);
   gb[0] = scl(mul_i(ik_bot), kx);
@@ -750,7 +751,7 @@ __device__ __noinline__ bool solve_one(const Geometry& g, const double* __restri
     }
   }
 
-  wall_amplitudes<T, SLIP>(g, kx, ky, kk, vtop, vbot, dtop, dbot, kaux, kidx, K);
+  wall_amplitudes<T, SLIP>(g, kx, ky, kk, ik, vtop, vbot, dtop, dbot, kaux, kidx, K);
   return true;
 }
 
@@ -873,8 +874,8 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
   const T* tl = bandT;
   const T* td = bandT + N;
   const T* tu = bandT + 2 * N;
-  const double sH = 2.0 / g.H;
-  const double inv_eta = 1.0 / g.eta;
+  const double sH = g.sH;
+  const double inv_eta = g.inv_eta;
   const double kx = ki.kx, ky = ki.ky, kk = ki.kk, kap = kk * kk;
   const T tkx = (T)kx, tky = (T)ky, tsH = (T)sH, tie = (T)inv_eta;
   const cplx<T> zT = mk<T>((T)0, (T)0);
@@ -960,8 +961,9 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
   }
 
   // ---- velocity: three right-hand sides sharing the factorisation -------------------------------
-  const cplx<double> ik_top = scl(ptop, 1.0 / (2.0 * kk * g.eta));
-  const cplx<double> ik_bot = scl(pbot, 1.0 / (2.0 * kk * g.eta));
+  const double ik = 1.0 / kk;  // the one division per wavenumber
+  const cplx<double> ik_top = scl(ptop, 0.5 * inv_eta * ik);
+  const cplx<double> ik_bot = scl(pbot, 0.5 * inv_eta * ik);
   cplx<double> gt[3], gb[3];
   gt[0] = scl(mul_i(ik_top), -kx);
   gb[0] = scl(mul_i(ik_bot), kx);
@@ -1102,7 +1104,7 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
       rc = rn;
     }
   }
-  wall_amplitudes<T, SLIP>(g, kx, ky, kk, vtop, vbot, dtop, dbot, kaux, kidx, K);
+  wall_amplitudes<T, SLIP>(g, kx, ky, kk, ik, vtop, vbot, dtop, dbot, kaux, kidx, K);
 }
 
 // thread i of a chunk -> wavenumber, with the ky rows in the order 0, 1, ny-1, 2, ny-2, ...: the

@@ -66,6 +66,7 @@ struct EsKernel {
 // Everything a kernel needs to know about the problem (passed by value)
 struct Geometry {
   double Lx, Ly, zmin, zmax, H, h, inv_h;
+  double sH, inv_eta;  // 2 / H and 1 / eta (host divisions, so the solves do not repeat them)
   double eta;
   int mode;          // dps_wall_mode
   int nx, ny, nz;

@@ -83,8 +83,8 @@ extern "C" dps_status dpstokes_spread_noalloc(double Lx, double Ly, double zmin,
   Plan p;
   memset(&p, 0, sizeof(Plan));
   Geometry& g = p.g;
-  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin;
-  g.h = hx; g.inv_h = 1.0 / hx; g.eta = 1.0; g.mode = wall_mode;
+  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin; g.sH = 2.0 / g.H;
+  g.h = hx; g.inv_h = 1.0 / hx; g.eta = 1.0; g.inv_eta = 1.0; g.mode = wall_mode;
   g.nx = nx; g.ny = ny; g.nz = nz; g.nkx = nx / 2 + 1;
   g.pitch = (int)(ldx / 2);  // the spreading kernel writes rows of 2 * pitch values
   if (particle_geometry(g, kp, 2) != DPS_OK) return DPS_ERR_INVALID_ARG;

@@ -513,8 +513,8 @@ dps_status dpstokes_plan_create_ex(dps_plan_t* out, double Lx, double Ly, double
   if (!(kp->eta > 0) || !isfinite(kp->eta)) return DPS_ERR_INVALID_ARG;
   dps::Geometry g;
   memset(&g, 0, sizeof(g));
-  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin;
-  g.h = hx; g.inv_h = 1.0 / hx; g.eta = kp->eta; g.mode = wall_mode;
+  g.Lx = Lx; g.Ly = Ly; g.zmin = zmin; g.zmax = zmax; g.H = zmax - zmin; g.sH = 2.0 / g.H;
+  g.h = hx; g.inv_h = 1.0 / hx; g.eta = kp->eta; g.inv_eta = 1.0 / kp->eta; g.mode = wall_mode;
   g.nx = nx; g.ny = ny; g.nz = nz; g.nkx = nx / 2 + 1;
   g.pitch = (g.nkx + 31) / 32 * 32;
   // kernels, torque route, particle records and bins
