@@ -397,7 +397,7 @@ __device__ __forceinline__ void spread_list(const Geometry& g, const uint32_t* s
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
     if (dx < 0) dx += g.nx;
-    if (dx >= px) continue;
+    if (!LANE && dx >= px) continue;  // a lane list holds only candidates that cover gx
     int dy = gy - hd.y;
     if (dy < 0) dy += g.ny;
     const T* tv = reinterpret_cast<const T*>(r + 8);
@@ -432,7 +432,7 @@ __device__ __forceinline__ void spread_curl_list(const Geometry& g, const uint32
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
     if (dx < 0) dx += g.nx;
-    if (dx >= px) continue;
+    if (!LANE && dx >= px) continue;  // a lane list holds only candidates that cover gx
     int dy = gy - hd.y;
     if (dy < 0) dy += g.ny;
     const T* tv = reinterpret_cast<const T*>(r + 8);
@@ -470,7 +470,7 @@ __device__ __forceinline__ void spread_fused_list(const Geometry& g, const uint3
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
     if (dx < 0) dx += g.nx;
-    if (dx >= px) continue;
+    if (!LANE && dx >= px) continue;  // a lane list holds only candidates that cover gx
     int dy = gy - hd.y;
     if (dy < 0) dy += g.ny;
     const T* tv = reinterpret_cast<const T*>(r + 8);
@@ -498,6 +498,22 @@ __device__ __forceinline__ void spread_fused_list(const Geometry& g, const uint3
   }
 }
 
+// the force and torque at the head of a staged record's values (16-byte aligned: records are whole
+// 16-byte pieces and the values follow the two 16-byte heads), in vector loads
+__device__ __forceinline__ void load6(const float* tv, float (&v)[6]) {
+  const float4 a = *reinterpret_cast<const float4*>(tv);
+  const float2 b = *reinterpret_cast<const float2*>(tv + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+__device__ __forceinline__ void load6(const double* tv, double (&v)[6]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double2 a = reinterpret_cast<const double2*>(tv)[i];
+    v[2 * i] = a.x;
+    v[2 * i + 1] = a.y;
+  }
+}
+
 // Spectral-curl route with coinciding supports (m_M = m_D): each listed candidate adds F Delta_M to
 // the force fields and tau Delta_D to the torque fields in one walk (six accumulators per plane).
 template <typename T, int ZC, bool LANE>
@@ -511,15 +527,17 @@ __device__ __forceinline__ void spread_six_list(const Geometry& g, const uint32_
     if (hd.z + hd.w <= zb || hd.z >= zb + ZC) continue;  // no plane of this chunk (uniform)
     int dx = gx - hd.x;
     if (dx < 0) dx += g.nx;
-    if (dx >= px) continue;
+    if (!LANE && dx >= px) continue;  // a lane list holds only candidates that cover gx
     int dy = gy - hd.y;
     if (dy < 0) dy += g.ny;
     const T* tv = reinterpret_cast<const T*>(r + 8);
     const T* pm = tv + 6;           // monopole phi
     const T* pd = tv + 6 + stride;  // dipole phi
     const T mxy = pm[dx] * pm[g.pxc + dy], dxy = pd[dx] * pd[g.pxc + dy];
-    const T f0 = tv[0] * mxy, f1 = tv[1] * mxy, f2 = tv[2] * mxy;
-    const T t0 = tv[3] * dxy, t1 = tv[4] * dxy, t2 = tv[5] * dxy;
+    T v[6];
+    load6(tv, v);
+    const T f0 = v[0] * mxy, f1 = v[1] * mxy, f2 = v[2] * mxy;
+    const T t0 = v[3] * dxy, t1 = v[4] * dxy, t2 = v[5] * dxy;
 #pragma unroll
     for (int zz = 0; zz < ZC; ++zz) {
       const int iz = zb + zz - hd.z;
@@ -536,8 +554,10 @@ __device__ __forceinline__ void spread_six_list(const Geometry& g, const uint32_
   }
 }
 
-// Bins searched around tile (bx, by) (the rbx x rby neighbourhood, each bin once) and the prefix
-// sums of their particle counts; thread 0 fills them, the caller synchronises.
+// Bins searched around tile (bx, by) (the rbx x rby neighbourhood in (dy, dx) order, each bin at its
+// first occurrence) and the prefix sums of their particle counts.  Warp 0 fills them, each lane one
+// or two entries of the neighbourhood (at most 64, checked at plan creation): the counts are loaded
+// all at once and summed by a warp scan.  The caller synchronises.
 struct TileBins {
   int bins[64];
   int pref[65];
@@ -546,22 +566,51 @@ struct TileBins {
 
 __device__ __forceinline__ void tile_bins(const Geometry& g, const int* __restrict__ bin_start, int bx, int by,
                                           TileBins& tb) {
-  int nb = 0;
-  for (int dy = -g.rby; dy <= g.rby; ++dy) {
-    for (int dx = -g.rbx; dx <= g.rbx; ++dx) {
-      const int b = wrap_idx(by + dy, g.nby) * g.nbx + wrap_idx(bx + dx, g.nbx);
-      bool dup = false;
-      for (int i = 0; i < nb; ++i) dup = dup || (tb.bins[i] == b);
-      if (!dup && nb < 64) tb.bins[nb++] = b;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int wx = 2 * g.rbx + 1, nn = wx * (2 * g.rby + 1);
+  int b[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    b[h] = -1;
+    if (i < nn) b[h] = wrap_idx(by + i / wx - g.rby, g.nby) * g.nbx + wrap_idx(bx + i % wx - g.rbx, g.nbx);
+  }
+  // drop an entry when an earlier entry names the same bin (small grids wrap onto themselves)
+  bool keep0 = b[0] >= 0, keep1 = b[1] >= 0;
+  for (int k = 0; k < 32; ++k) {
+    const int o0 = __shfl_sync(0xffffffffu, b[0], k), o1 = __shfl_sync(0xffffffffu, b[1], k);
+    if (k < lane && o0 == b[0]) keep0 = false;
+    if (o0 == b[1] || (k < lane && o1 == b[1])) keep1 = false;
+  }
+  const int c0 = keep0 ? bin_start[b[0] + 1] - bin_start[b[0]] : 0;
+  const int c1 = keep1 ? bin_start[b[1] + 1] - bin_start[b[1]] : 0;
+  int s0 = c0, s1 = c1;  // inclusive scans over the lanes
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int t0 = __shfl_up_sync(0xffffffffu, s0, off), t1 = __shfl_up_sync(0xffffffffu, s1, off);
+    if (lane >= off) {
+      s0 += t0;
+      s1 += t1;
     }
   }
-  tb.nb = nb;
-  int acc = 0;
-  for (int i = 0; i < nb; ++i) {
-    tb.pref[i] = acc;
-    acc += bin_start[tb.bins[i] + 1] - bin_start[tb.bins[i]];
+  const int tot0 = __shfl_sync(0xffffffffu, s0, 31), tot1 = __shfl_sync(0xffffffffu, s1, 31);
+  const unsigned m0 = __ballot_sync(0xffffffffu, keep0), m1 = __ballot_sync(0xffffffffu, keep1);
+  if (keep0) {
+    const int p = __popc(m0 & below);
+    tb.bins[p] = b[0];
+    tb.pref[p] = s0 - c0;
   }
-  tb.pref[nb] = acc;
+  if (keep1) {
+    const int p = __popc(m0) + __popc(m1 & below);
+    tb.bins[p] = b[1];
+    tb.pref[p] = tot0 + s1 - c1;
+  }
+  if (lane == 0) {
+    const int nb = __popc(m0) + __popc(m1);
+    tb.nb = nb;
+    tb.pref[nb] = tot0 + tot1;
+  }
 }
 
 // One window of the tile's candidates: the particles of the searched bins (in bin order, each bin's
@@ -612,16 +661,22 @@ __device__ __forceinline__ int tile_candidates(const Geometry& g, const uint32_t
 // pass each); 2: kernel-derivative torques (the force density and the half-curl sources in one pass
 // over the 3 fields); 3: as 2 with coinciding supports (one list, one walk per candidate); 4: as 1
 // with coinciding supports (one walk per candidate writes all six fields).
+// Compiled for three resident blocks per SM in float (two in double): while one block gathers and
+// stages its candidates, the others keep the SM busy.  The modes with one candidate list keep one
+// list per warp in shared memory, so that three blocks fit beside kStage staged records of the
+// six-field mode.
 template <typename T, int MODE, int ZC>
-__global__ void __launch_bounds__(kSpreadThreads)
+__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 3 : 2)
 spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restrict__ bin_start,
               const int* __restrict__ sorted, const int* __restrict__ zrange, T* __restrict__ grid) {
+  constexpr bool TWO = MODE == 1 || MODE == 2;  // a second list (dipole kernel of another width)
+  constexpr int NL = TWO ? 2 : 1;
   extern __shared__ __align__(16) uint32_t srec[];   // g.stage_cap (<= kStage) staged records
   __shared__ TileBins s_tb;
   __shared__ int s_cand[kCandCap];
   __shared__ int s_warp[kSpreadThreads / 32];
-  __shared__ int s_wl[kSpreadThreads / 32][2][kStage];  // per-warp row lists (monopole, dipole)
-  __shared__ unsigned char s_ll[kSpreadThreads / 32][2][kLaneCap * 32];  // per-lane lists of the row lists
+  __shared__ int s_wl[kSpreadThreads / 32][NL][kStage];  // per-warp row lists (monopole, dipole)
+  __shared__ unsigned char s_ll[kSpreadThreads / 32][NL][kLaneCap * 32];  // per-lane lists of the row lists
   const int clo = zrange[0], chi = zrange[1];
   if (chi < clo) return;
   const int bx = blockIdx.x % g.nbx, by = blockIdx.x / g.nbx;
@@ -631,7 +686,7 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   const bool active = (gx < g.nx) && (gy < g.ny);
   const int tw = min(kTileX, g.nx - tx0), th = min(kTileY, g.ny - ty0);
   const int rw = g.rec_words;
-  if (tid == 0) tile_bins(g, bin_start, bx, by, s_tb);
+  if (warp == 0) tile_bins(g, bin_start, bx, by, s_tb);
   __syncthreads();
   (void)lane;
   const size_t plane = (size_t)g.ny * 2 * g.pitch;          // T values per z plane (real rows)
@@ -654,14 +709,13 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
     const int passed = tile_candidates(g, rec, bin_start, sorted, s_tb, tx0, ty0, tw, th, win0, s_cand, s_warp);
     const int ncand = min(passed, win1) - win0;
     if (ncand <= 0 && round > 0) break;
-    constexpr bool TWO = MODE == 1 || MODE == 2;
     constexpr int NA = MODE == 4 ? 6 : 3;  // fields accumulated per pass
     const bool once = ncand <= g.stage_cap;
     int nl0 = 0, nl1 = 0;
     int* wl0 = s_wl[warp][0];
-    int* wl1 = s_wl[warp][1];
+    int* wl1 = s_wl[warp][NL - 1];  // the one-list modes never fill or walk it
     unsigned char* ll0 = s_ll[warp][0];
-    unsigned char* ll1 = s_ll[warp][1];
+    unsigned char* ll1 = s_ll[warp][NL - 1];
     int lc0 = 0, lc1 = 0;
     bool lanes = false;  // warp-uniform: walk per-lane lists instead of the row lists
     if (once) {
@@ -834,7 +888,7 @@ interp_tile_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __re
   const bool active = (gx < g.nx) && (gy < g.ny);
   const int tw = min(kTileX, g.nx - tx0), th = min(kTileY, g.ny - ty0);
   const int rw = g.rec_words;
-  if (tid == 0) tile_bins(g, bin_start, bx, by, s_tb);
+  if (warp == 0) tile_bins(g, bin_start, bx, by, s_tb);
   __syncthreads();
   const size_t plane = (size_t)g.ny * 2 * g.pitch;
   const size_t fstride = plane * g.nz;
@@ -1303,7 +1357,7 @@ constexpr int kIsZT = 64;  // z weights of a particle's table (records with more
 
 // a gather warp's table of one particle of the batch: the staged offset of its first support node,
 // its z support, and its weights (the z weights times the Clenshaw-Curtis weights of the planes)
-struct IsSlot {
+struct __align__(16) IsSlot {
   int base, z0, zn, pad;
   float mx[8], dx[8], my[8], dy[8];
   float mz[kIsZT], dz[kIsZT];
@@ -1479,18 +1533,30 @@ interp_stage_kernel(const __grid_constant__ CUtensorMap tmap, int use_tma, Geome
       const int i = batch * kIsBatch + warp + GW * q;
       if (i >= cnt || !lane_on) continue;
       const IsSlot& t = s_slot[warp][q];
-      const int iz = zb + grp - t.z0;
-      if (iz < 0 || iz >= t.zn) continue;
+      const int4 head = *reinterpret_cast<const int4*>(&t.base);  // base, z0, zn in one load
+      const int iz = zb + grp - head.y;
+      if (iz < 0 || iz >= head.z) continue;
       const float mzx = t.mz[iz] * t.mx[lx];
       const float dzx = NF == 6 ? t.dz[iz] * t.dx[lx] : 0.f;
-      const float* sp = sb + grp * kIsPS + t.base + lx;
+      const float* sp = sb + grp * kIsPS + head.x + lx;
+      // the row weights (PX = 6) in vector loads: the table rows are 16-byte aligned
+      static_assert(PX == 6, "row weights loaded as 4 + 2");
+      const float4 my4 = *reinterpret_cast<const float4*>(t.my);
+      const float2 my2 = *reinterpret_cast<const float2*>(t.my + 4);
+      const float myv[PX] = {my4.x, my4.y, my4.z, my4.w, my2.x, my2.y};
+      float dyv[PX] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (NF == 6) {
+        const float4 dy4 = *reinterpret_cast<const float4*>(t.dy);
+        const float2 dy2 = *reinterpret_cast<const float2*>(t.dy + 4);
+        dyv[0] = dy4.x; dyv[1] = dy4.y; dyv[2] = dy4.z; dyv[3] = dy4.w; dyv[4] = dy2.x; dyv[5] = dy2.y;
+      }
 #pragma unroll
       for (int iy = 0; iy < PX; ++iy) {
-        const float wm = mzx * t.my[iy];
+        const float wm = mzx * myv[iy];
 #pragma unroll
         for (int f = 0; f < 3; ++f) acc[q][f] += sp[f * FS + iy * SX] * wm;
         if (NF == 6) {
-          const float wd = dzx * t.dy[iy];
+          const float wd = dzx * dyv[iy];
 #pragma unroll
           for (int f = 3; f < NF; ++f) acc[q][f] += sp[f * FS + iy * SX] * wd;
         }
