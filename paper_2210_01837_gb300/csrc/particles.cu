@@ -560,6 +560,7 @@ __device__ __forceinline__ void spread_six_list(const Geometry& g, const uint32_
 // all at once and summed by a warp scan.  The caller synchronises.
 struct TileBins {
   int bins[64];
+  int start[64];  // each bin's first entry in the sorted particle list
   int pref[65];
   int nb;
 };
@@ -583,8 +584,9 @@ __device__ __forceinline__ void tile_bins(const Geometry& g, const int* __restri
     if (k < lane && o0 == b[0]) keep0 = false;
     if (o0 == b[1] || (k < lane && o1 == b[1])) keep1 = false;
   }
-  const int c0 = keep0 ? bin_start[b[0] + 1] - bin_start[b[0]] : 0;
-  const int c1 = keep1 ? bin_start[b[1] + 1] - bin_start[b[1]] : 0;
+  const int a0 = keep0 ? bin_start[b[0]] : 0, a1 = keep1 ? bin_start[b[1]] : 0;
+  const int c0 = keep0 ? bin_start[b[0] + 1] - a0 : 0;
+  const int c1 = keep1 ? bin_start[b[1] + 1] - a1 : 0;
   int s0 = c0, s1 = c1;  // inclusive scans over the lanes
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -599,11 +601,13 @@ __device__ __forceinline__ void tile_bins(const Geometry& g, const int* __restri
   if (keep0) {
     const int p = __popc(m0 & below);
     tb.bins[p] = b[0];
+    tb.start[p] = a0;
     tb.pref[p] = s0 - c0;
   }
   if (keep1) {
     const int p = __popc(m0) + __popc(m1 & below);
     tb.bins[p] = b[1];
+    tb.start[p] = a1;
     tb.pref[p] = tot0 + s1 - c1;
   }
   if (lane == 0) {
@@ -633,7 +637,7 @@ __device__ __forceinline__ int tile_candidates(const Geometry& g, const uint32_t
     if (e < total) {
       int b = 0;
       while (b + 1 < nb && tb.pref[b + 1] <= e) ++b;
-      j = sorted[bin_start[tb.bins[b]] + (e - tb.pref[b])];
+      j = sorted[tb.start[b] + (e - tb.pref[b])];
       const uint32_t* r = rec + (size_t)j * rw;
       for (int K = 0; K < g.nkernels; ++K) {
         const int4 hd = reinterpret_cast<const int4*>(r)[K];
@@ -688,17 +692,17 @@ spread_kernel(Geometry g, const uint32_t* __restrict__ rec, const int* __restric
   const int rw = g.rec_words;
   if (warp == 0) tile_bins(g, bin_start, bx, by, s_tb);
   __syncthreads();
-  (void)lane;
   const size_t plane = (size_t)g.ny * 2 * g.pitch;          // T values per z plane (real rows)
   const size_t fstride = plane * g.nz;
   const size_t node = (size_t)gy * 2 * g.pitch + gx;
   // copy records [i0, i0 + cnt) of the candidate list into shared memory (16-byte pieces; records
   // are 16-byte aligned), all copies in flight at once
   auto stage = [&](int i0, int cnt) {
-    const int q = rw >> 2;
-    for (int t = tid; t < cnt * q; t += kSpreadThreads) {
-      const int i = t / q, w = t - i * q;
-      cp_async16(srec + (size_t)i * rw + 4 * w, rec + (size_t)s_cand[i0 + i] * rw + 4 * w);
+    const int q = rw >> 2;  // 16-byte pieces per record; a warp copies one record at a time
+    for (int i = warp; i < cnt; i += kSpreadThreads / 32) {
+      const uint32_t* src = rec + (size_t)s_cand[i0 + i] * rw;
+      uint32_t* dst = srec + (size_t)i * rw;
+      for (int w = lane; w < q; w += 32) cp_async16(dst + 4 * w, src + 4 * w);
     }
     cp_commit();
     cp_wait_all();
