@@ -438,10 +438,14 @@ dps_status dpstokes_debug_copy(dps_plan_t plan, int32_t which, void* dst, int64_
  * kernel records DPS_ERR_TIMEOUT in the status word (read by dpstokes_status), its blocks free
  * their tensor memory and leave, and the plan stays usable for the next apply.  code 2: in the
  * next apply every bin of the staged interpolation takes its global-memory gather (the path a bin
- * whose region does not fit in shared memory takes).  An injection applies to one apply and then
- * clears itself.  code 0 clears it.  DPS_ERR_INVALID_ARG for other codes, for code 1 on a plan
- * that does not use the tensor-core forward transform, or for code 2 on a plan whose
- * interpolation variant is not 2. */
+ * whose region does not fit in shared memory takes).  code 3: in the next apply the forward
+ * TMA-staged y-FFT column pass arms its buffers' barriers but issues no box load, so its bounded
+ * waits run out (about a second, then a second bounded wait for copies in flight, of which there
+ * are none): the kernel records DPS_ERR_TIMEOUT and its blocks leave.  An injection applies to one
+ * apply and then clears itself.  code 0 clears it.  DPS_ERR_INVALID_ARG for other codes, for code
+ * 1 on a plan that does not use the tensor-core forward transform, for code 2 on a plan whose
+ * interpolation variant is not 2, or for code 3 on a plan whose column pass is not the TMA-staged
+ * one (plan_info.fft_register_cols != 3). */
 dps_status dpstokes_debug_inject(dps_plan_t plan, int32_t code);
 
 #ifdef __cplusplus

@@ -695,8 +695,90 @@ __device__ __forceinline__ void reg_fft(cplx<T>* buf, const FftPlan& fp, int lb,
 constexpr int kRegMaxThreads = 512;
 #define DPS_REG_FFT_BOUNDS __launch_bounds__(kRegMaxThreads, sizeof(T) == 4 ? 2 : 1)
 
-// Row pass, forward, register-staged: two real rows packed as z = r0 + i r1, then the half-spectrum split.
+// Every stage but the last of a register-staged transform (at least two stages), into the shared
+// buffer; ends with a block barrier, so the last stage may read the buffer.
+template <typename T, int DIR, class Src>
+__device__ __forceinline__ void reg_fft_head(cplx<T>* buf, const FftPlan& fp, const cplx<T>* tw, const Src& gsrc) {
+  const ShBuf<T, 1> sb{buf, 0};
+  reg_stage_any<T, DIR, false>(fp, 0, 1, 0, tw, gsrc, sb, true);
+  __syncthreads();
+  int Ns = fp.radix[0];
+  for (int s = 1; s < fp.nstages - 1; ++s) {
+    reg_stage_any<T, DIR, false>(fp, s, Ns, 0, tw, sb, sb, true);
+    __syncthreads();
+    Ns *= fp.radix[s];
+  }
+}
+
+// The half-spectrum split of two packed real rows: X0_k = (z_k + conj z_{n-k}) / 2 and
+// X1_k = (z_k - conj z_{n-k}) / (2i), given z_k and zn = z_{n-k}.
 template <typename T>
+__device__ __forceinline__ void split_store(cplx<T>* c0, cplx<T>* c1, bool has1, int k, cplx<T> zk, cplx<T> zn) {
+  const T half = (T)0.5;
+  const cplx<T> zm = conjg(zn);
+  c0[k] = scl(zk + zm, half);
+  if (has1) {
+    const cplx<T> d = zk - zm;
+    c1[k] = mk<T>(half * d.y, -half * d.x);
+  }
+}
+
+// The last stage of the forward row transform (radix R even, span Ns = n / R a multiple of 32)
+// fused with the half-spectrum split, so the transform never returns to shared memory.  Butterfly
+// jj of the last stage yields z_k for k = jj + Ns r (r < R); the conjugate partner of k is
+// n - k = (Ns - jj) + Ns (R - 1 - r), a value of butterfly Ns - jj.  In warp w, lanes 0-15 take
+// butterflies x = 16 w + lane and lanes 16-31 their partners Ns - x (Ns / 2 in place of Ns - 0:
+// butterflies 0 and Ns / 2 are their own partners), so a lane receives its partner's values by a
+// shuffle with lane ^ 16, and every lane writes its values k <= n / 2 of both half spectra.
+template <typename T, int R>
+__device__ __forceinline__ void r2c_last_split(const cplx<T>* buf, const FftPlan& fp, const cplx<T>* __restrict__ tw,
+                                               cplx<T>* c0, cplx<T>* c1, bool has1) {
+  static_assert(R % 2 == 0, "the split pairs the outputs of an even radix");
+  const int Ns = fp.n / R, t = threadIdx.x;
+  if (t >= Ns) return;  // whole warps
+  const int lane = t & 31, x = 16 * (t >> 5) + (lane & 15);
+  const int jj = lane < 16 ? x : (x == 0 ? Ns / 2 : Ns - x);
+  cplx<T> v[R];
+  const int p0 = pad16(jj), sp = Ns + (Ns >> 4);  // Ns is a multiple of 16: the padding is linear in r
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = buf[p0 + r * sp];
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = v[r] * tw[jj * r];  // W_{Ns R}^{jj r} = W_n^{jj r}
+  Dft<T, R, -1>::run(v);
+  const bool self0 = jj == 0, selfh = 2 * jj == Ns;
+#pragma unroll
+  for (int r = 0; r < R / 2; ++r) {
+    cplx<T> q = v[R - 1 - r];
+    q.x = __shfl_xor_sync(0xffffffffu, q.x, 16);
+    q.y = __shfl_xor_sync(0xffffffffu, q.y, 16);
+    const cplx<T> zn = self0 ? v[(R - r) % R] : (selfh ? v[R - 1 - r] : q);
+    split_store(c0, c1, has1, jj + Ns * r, v[r], zn);
+  }
+  if (self0) split_store(c0, c1, has1, fp.n / 2, v[R / 2], v[R / 2]);
+}
+
+template <typename T>
+__device__ __forceinline__ void r2c_last_split_any(const cplx<T>* buf, const FftPlan& fp, const cplx<T>* tw,
+                                                   cplx<T>* c0, cplx<T>* c1, bool has1) {
+  switch (fp.radix[fp.nstages - 1]) {
+    case 16: r2c_last_split<T, 16>(buf, fp, tw, c0, c1, has1); break;
+    case 12: r2c_last_split<T, 12>(buf, fp, tw, c0, c1, has1); break;
+    case 8: r2c_last_split<T, 8>(buf, fp, tw, c0, c1, has1); break;
+    case 4: r2c_last_split<T, 4>(buf, fp, tw, c0, c1, has1); break;
+    default: r2c_last_split<T, 2>(buf, fp, tw, c0, c1, has1); break;
+  }
+}
+
+// whether a row factorisation takes the fused last stage (r2c_last_split)
+bool r2c_split_ok(const FftPlan& fp) {
+  if (fp.nstages < 2) return false;
+  const int R = fp.radix[fp.nstages - 1];
+  return R % 2 == 0 && R <= 16 && (fp.n / R) % 32 == 0;
+}
+
+// Row pass, forward, register-staged: two real rows packed as z = r0 + i r1, then the half-spectrum
+// split (SPLIT: in the last stage's registers, r2c_last_split; else from the shared buffer).
+template <typename T, bool SPLIT>
 __global__ void DPS_REG_FFT_BOUNDS row_r2c_reg_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
                                                       T* __restrict__ grid, const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -711,10 +793,17 @@ __global__ void DPS_REG_FFT_BOUNDS row_r2c_reg_kernel(Geometry g, FftPlan fp, co
     const bool has1 = 2 * j + 1 < g.ny;
     T* row0 = grid + ((size_t)(f * g.nz + c) * g.ny + 2 * j) * rowlen;
     const T* row1 = row0 + rowlen;
-    reg_fft<T, -1, true, false>(buf, fp, 0, tw, [&](int e, int) { return mk<T>(row0[e], has1 ? row1[e] : (T)0); },
-                         [](int, int, cplx<T>) {});
+    auto src = [&](int e, int) { return mk<T>(row0[e], has1 ? row1[e] : (T)0); };
     cplx<T>* c0 = reinterpret_cast<cplx<T>*>(row0);
     cplx<T>* c1 = reinterpret_cast<cplx<T>*>(row0 + rowlen);
+    if (SPLIT) {
+      // the next unit's first stage writes the buffer only after a block barrier (reg_stage), by
+      // which time every thread has read its last-stage inputs
+      reg_fft_head<T, -1>(buf, fp, tw, src);
+      r2c_last_split_any<T>(buf, fp, tw, c0, c1, has1);
+      continue;
+    }
+    reg_fft<T, -1, true, false>(buf, fp, 0, tw, src, [](int, int, cplx<T>) {});
     for (int k = threadIdx.x; k <= nx / 2; k += blockDim.x) {
       const cplx<T> zk = buf[pad16(k)];
       const cplx<T> zm = conjg(buf[pad16(k == 0 ? 0 : nx - k)]);
@@ -863,7 +952,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
 // tensor map into the buffer, densely ([y][b]); the first FFT stage reads that dense layout and its
 // in-place writes (after the stage's barrier) use the padded one.  Every wait is bounded (about a
 // second): on expiry the block records kStatTimeout, waits (bounded again) for its copies in flight
-// and leaves.
+// and leaves.  `withhold` (failure injection for tests) arms each buffer's barrier but issues no box
+// load, so the first wait runs out with no copy in flight.
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -905,7 +995,7 @@ template <typename T, int DIR>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxThreadsD, 1)
     col_tma_kernel(const __grid_constant__ CUtensorMap tmap, Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
                    cplx<T>* __restrict__ grid, const int* __restrict__ zrange, int* __restrict__ status, int lcw,
-                   int kxs, int kxe, int bh) {
+                   int kxs, int kxe, int bh, int withhold) {
   extern __shared__ __align__(16) unsigned char smraw[];  // realigned to 128 bytes below
   constexpr int PW = pipe_pad<T>(), SH = pipe_pad_shift<T>();
   const int cw = 1 << lcw;
@@ -931,6 +1021,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kPipeMaxThreadsF : kPipeMaxTh
     // the buffer's last contents were written by the generic proxy (the previous unit's stages)
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_expect_tx(&bars[w], bytes);
+    if (withhold) return;
     for (int r0 = 0; r0 < g.ny; r0 += bh) tma_load_2d(dst + (r0 << lcw), &tmap, 2 * kx0, y0 + r0, &bars[w]);
   };
   unsigned phase = 0;  // bit w: parity of the next completion of barrier w
@@ -1122,7 +1213,8 @@ int fft_set_row_variant(Plan& p, int reg) {
     const int th = reg_threads(p.fxr, 0);
     const size_t sm = reg_smem<T>(p.g.nx);
     p.fft_reg[0] = 1;
-    p.fft_grid[0] = resident_grid(row_r2c_reg_kernel<T>, th, sm, p.device);
+    p.fft_grid[0] = r2c_split_ok(p.fxr) ? resident_grid(row_r2c_reg_kernel<T, true>, th, sm, p.device)
+                                         : resident_grid(row_r2c_reg_kernel<T, false>, th, sm, p.device);
     p.fft_grid[1] = resident_grid(row_c2r_reg_kernel<T>, th, sm, p.device);
     return 1;
   }
@@ -1158,7 +1250,8 @@ bool reg_rows_default(const FftPlan& fp) {
 template <typename T>
 int fft_smem_ok(Plan& p) {
   if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
-      !allow_smem(col_kernel<T, +1>) || !allow_smem(row_r2c_reg_kernel<T>) || !allow_smem(row_c2r_reg_kernel<T>) ||
+      !allow_smem(col_kernel<T, +1>) || !allow_smem(row_r2c_reg_kernel<T, false>) ||
+      !allow_smem(row_r2c_reg_kernel<T, true>) || !allow_smem(row_c2r_reg_kernel<T>) ||
       !allow_smem(col_reg_kernel<T, -1>) || !allow_smem(col_reg_kernel<T, +1>) ||
       !allow_smem(col_pipe_kernel<T, -1>) || !allow_smem(col_pipe_kernel<T, +1>) ||
       !allow_smem(col_tma_kernel<T, -1>) || !allow_smem(col_tma_kernel<T, +1>))
@@ -1187,8 +1280,10 @@ void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
     const int th = reg_threads(p.fxr, 0);
     const size_t sm = reg_smem<T>(g.nx);
     T* grid = reinterpret_cast<T*>(p.grid);
-    if (dir < 0)
-      row_r2c_reg_kernel<T><<<p.fft_grid[0], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
+    if (dir < 0 && r2c_split_ok(p.fxr))
+      row_r2c_reg_kernel<T, true><<<p.fft_grid[0], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
+    else if (dir < 0)
+      row_r2c_reg_kernel<T, false><<<p.fft_grid[0], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
     else
       row_c2r_reg_kernel<T><<<p.fft_grid[1], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
     return;
@@ -1215,10 +1310,10 @@ void launch_fft_cols(const Plan& p, int dir, int kxs, int kxe, cudaStream_t s) {
     const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(p.col_tmap);
     if (dir < 0)
       col_tma_kernel<T, -1><<<p.fft_grid[2], th, sm, s>>>(map, g, p.fyr, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
-                                                          p.col_tma_rows);
+                                                          p.col_tma_rows, p.inject == 3 ? 1 : 0);
     else
       col_tma_kernel<T, +1><<<p.fft_grid[3], th, sm, s>>>(map, g, p.fyr, tsy, grid, p.zrange, p.status, lcw, kxs, kxe,
-                                                          p.col_tma_rows);
+                                                          p.col_tma_rows, 0);
     return;
   }
   if (p.fft_reg[1] == 2) {

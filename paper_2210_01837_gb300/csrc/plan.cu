@@ -645,7 +645,8 @@ dps_status dpstokes_plan_info(dps_plan_t plan, dps_plan_info* out) {
 
 dps_status dpstokes_debug_inject(dps_plan_t plan, int32_t code) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || code < 0 || code > 2 || (code == 1 && !p->cheb_tc) || (code == 2 && p->interp_tile != 2))
+  if (!p || code < 0 || code > 3 || (code == 1 && !p->cheb_tc) || (code == 2 && p->interp_tile != 2) ||
+      (code == 3 && p->fft_reg[1] != 3))
     return DPS_ERR_INVALID_ARG;
   p->inject = code;
   return DPS_OK;

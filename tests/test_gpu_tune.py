@@ -138,3 +138,28 @@ def test_every_pipeline_shape_keeps_the_product(precision, bar):
         with pytest.raises(binding.DpsError):
             plan.set_pipeline(*bad)
     plan.close()
+
+
+def test_tma_column_pass_wait_runs_out_and_the_plan_stays_usable():
+    """Failure injection: in one apply the forward TMA-staged column pass arms its buffers'
+    barriers but issues no box load, so its bounded waits run out (about a second, then a second
+    bounded wait that finds no copy in flight).  The kernel records DPS_ERR_TIMEOUT instead of
+    hanging, its blocks leave, and the next apply of the same plan gives the product it gave
+    before the injection (within 1e-6 relative L2: the binning's atomics leave the order of a
+    bin's particles, hence the summation order, open)."""
+    import torch
+    params = small_params("bottom_wall", nx=16, ny=512, nz=17, zmax=6.0)
+    pos, F, T = random_particles(params, 40, 19)
+    plan = binding.Plan.from_params(params, with_torque=True, precision="mixed", max_n=len(pos))
+    if plan.info().fft_register_cols != 3:
+        plan.set_fft(plan.info().fft_register_rows, 3, 4)
+    assert plan.info().fft_register_cols == 3
+    args = (to_dev(pos), to_dev(F), to_dev(T))
+    U0, W0 = (a.cpu().numpy() for a in plan.apply(*args, check=True))
+    plan.debug_inject(3)
+    plan.apply(*args)
+    torch.cuda.synchronize()
+    assert plan.status() == binding.DPS_ERR_TIMEOUT
+    U1, W1 = (a.cpu().numpy() for a in plan.apply(*args, check=True))
+    plan.close()
+    assert rel_l2(U1, U0) <= 1e-6 and rel_l2(W1, W0) <= 1e-6
