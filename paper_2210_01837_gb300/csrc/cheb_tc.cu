@@ -54,9 +54,17 @@ namespace {
 constexpr int kTcRows = 128;   // MMA M: 64 wavenumbers x (re, im)
 constexpr int kTcK = 8;        // K step (8 tf32 = 32 bytes per operand row)
 constexpr int kTcWave = 64;    // wavenumbers per tile
-constexpr int kProducers = 256;
-constexpr int kTcThreads = 416;  // 8 producer warps, 4 epilogue warps, 1 MMA warp
-constexpr int kEpiWarp0 = 8, kMmaWarp = 12;
+constexpr int kProducers = 256;  // producer threads of one group (8 warps)
+#ifndef DPS_TC_BWD_GROUPS
+#define DPS_TC_BWD_GROUPS 2
+#endif
+#ifndef DPS_TC_BWD_RING
+#define DPS_TC_BWD_RING 2
+#endif
+// warps of a transform: Spec::kGroups groups of 8 producer warps, then 4 epilogue warps and 1 MMA warp
+template <typename Spec> __host__ __device__ constexpr int tc_epi_warp0() { return 8 * Spec::kGroups; }
+template <typename Spec> __host__ __device__ constexpr int tc_mma_warp() { return 8 * Spec::kGroups + 4; }
+template <typename Spec> __host__ __device__ constexpr int tc_threads() { return 32 * (8 * Spec::kGroups + 5); }
 constexpr int kStages = 4;                       // most operand stages (fewer where they do not fit)
 constexpr size_t kTcSmemCap = 225 * 1024;        // dynamic shared memory the stages may take
 constexpr uint32_t kATile = umma::tile_bytes(kTcRows);  // one A operand of one K step (128 rows x 8)
@@ -222,6 +230,7 @@ struct FwdSpec {
   static constexpr int NR = CURL ? 4 : 2;  // grid fields a producer thread reads per plane
   static constexpr int kRingDepth = 0;      // loads one step ahead in registers (no staging ring)
   static constexpr int kRingVals = 0;
+  static constexpr int kGroups = 1;  // load and store index the producers by threadIdx.x
   struct Args {
     const float* ct;   // [c][npad] C[n][c]
     const float* dct;  // [c][npad] DC[n][c]
@@ -240,7 +249,7 @@ struct FwdSpec {
   // producer thread (j, grp, half): wavenumber j, planes 4 grp .. 4 grp + 3 of the step; half 0
   // reads fx, fy, ty, tz (forces only: fx, fy), half 1 reads fz, tx, ty (fz)
   __device__ static void load(const Geometry& g, const Args& a, int clo, int chi, int ks, const TileK& tk, Raw& r) {
-    const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;  // one producer group
     const size_t plane = (size_t)g.ny * g.pitch, fstride = (size_t)g.nz * plane;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
@@ -257,7 +266,7 @@ struct FwdSpec {
   }
   __device__ static void store(const Geometry& g, const Args& a, int clo, int chi, int ks, const TileK& tk,
                                const Raw& r, unsigned char* st, int np) {
-    const int tid = threadIdx.x, j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int tid = threadIdx.x, j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;  // one producer group
     const float hkx = tk.hkx, hky = tk.hky;
     float re[3][4], im[3][4];
 #pragma unroll
@@ -378,16 +387,18 @@ struct BwdSpec {
   struct Raw {
     cplx<float> v[4][2];
   };
-  // the producers stage each step's values with cp.async kRingDepth - 1 steps ahead into a ring in
-  // shared memory (value e of thread t of a slot at slot[e * kProducers + t])
-  static constexpr int kRingDepth = 4;
+  // two producer groups take alternate K steps; each stages its steps' values with cp.async
+  // kRingDepth - 1 of its own steps ahead into its ring in shared memory (value e of group thread t
+  // of a slot at slot[e * kProducers + t])
+  static constexpr int kGroups = DPS_TC_BWD_GROUPS;
+  static constexpr int kRingDepth = DPS_TC_BWD_RING;
   static constexpr int kRingVals = 8;
   __host__ __device__ static int ncoef(const Geometry& g) { return (g.nz + kTcK - 1) / kTcK; }
   __host__ __device__ static int nks(const Geometry& g, int, int) { return ncoef(g) * (CORR ? 2 : 1); }
   // the values `load` would read, copied asynchronously into ring slot `slot` (zeros where load
   // reads none); completes in the calling thread's current cp.async group
   __device__ static void load_async(const Geometry& g, const Args& a, int ks, const TileK& tk, cplx<float>* slot) {
-    const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int tid = threadIdx.x & (kProducers - 1), grp = (tid >> 6) & 1, half = tid >> 7;
     const int64_t K = (int64_t)g.nkx * g.ny;
     const int N = g.nz;
     const bool ok = tk.col >= 0;
@@ -419,14 +430,14 @@ struct BwdSpec {
     }
   }
   __device__ static void from_ring(const cplx<float>* slot, Raw& r) {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x & (kProducers - 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int q = 0; q < 2; ++q) r.v[i][q] = slot[(i * 2 + q) * kProducers + tid];
   }
   __device__ static void load(const Geometry& g, const Args& a, int, int, int ks, const TileK& tk, Raw& r) {
-    const int tid = threadIdx.x, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int tid = threadIdx.x & (kProducers - 1), grp = (tid >> 6) & 1, half = tid >> 7;
     const int64_t K = (int64_t)g.nkx * g.ny;
     const int N = g.nz;
     const bool ok = tk.col >= 0;
@@ -455,7 +466,7 @@ struct BwdSpec {
   }
   __device__ static void store(const Geometry& g, const Args& a, int, int, int ks, const TileK& tk, const Raw& r,
                                unsigned char* st, int) {
-    const int tid = threadIdx.x, j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;
+    const int tid = threadIdx.x & (kProducers - 1), j = tid & 63, grp = (tid >> 6) & 1, half = tid >> 7;
     const int N = g.nz;
     const uint32_t orow = umma::kmajor_offset((uint32_t)(2 * j), (uint32_t)(4 * grp));
     const uint32_t orow1 = umma::kmajor_offset((uint32_t)(2 * j + 1), (uint32_t)(4 * grp));
@@ -637,7 +648,7 @@ __global__ void tc_bimage_kernel(Geometry g, typename Spec::Args a, const int* _
 }
 
 template <typename Spec>
-__global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, typename Spec::Args a,
+__global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry g, typename Spec::Args a,
                                                                 const unsigned char* __restrict__ bimg,
                                                                 const int* __restrict__ zrange, int kx0, int w,
                                                                 int* __restrict__ status, int inject, int part,
@@ -660,7 +671,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
   const uint32_t stage_bytes = Spec::stage_bytes(nmax);
   uint32_t dyn;
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-  constexpr uint32_t kRingBytes = (uint32_t)(Spec::kRingDepth * Spec::kRingVals * kProducers * 8);
+  constexpr uint32_t kRingBytes = (uint32_t)(Spec::kGroups * Spec::kRingDepth * Spec::kRingVals * kProducers * 8);
+  constexpr int kEpiWarp0 = tc_epi_warp0<Spec>(), kMmaWarp = tc_mma_warp<Spec>();
   const int nst = min(kStages, (int)((dyn - 1024u - kRingBytes) / stage_bytes));  // operand stages launched with
   const int nks = Spec::nks(g, clo, chi);
   const uint32_t idesc = umma::idesc_tf32(kTcRows, (uint32_t)nn);
@@ -684,7 +696,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if constexpr (!Spec::kForward) {
-    for (int i = tid; i < g.nz; i += kTcThreads) s_zeta[i] = a.zeta[i];  // nz <= 128 here
+    for (int i = tid; i < g.nz; i += tc_threads<Spec>()) s_zeta[i] = a.zeta[i];  // nz <= 128 here
   }
   tc_fence_before();
   __syncthreads();
@@ -700,37 +712,57 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
   if constexpr (Spec::kRingDepth > 0) {
     if (warp < kEpiWarp0) {
       // ---- producers, staging through the ring --------------------------------------------
-      constexpr int D = Spec::kRingDepth;
-      cplx<float>* ring = reinterpret_cast<cplx<float>*>(smraw + (size_t)nst * stage_bytes);
+      // group gp takes the block's K steps q = gp, gp + G, gp + 2 G, ... (q counts the steps of the
+      // block's tiles in order, nks per tile; step q fills operand stage q mod nst, which the MMA
+      // warp consumes in the order of q), staging its own steps' values D - 1 of them ahead
+      constexpr int D = Spec::kRingDepth, G = Spec::kGroups;
+      const int gp = warp >> 3, gtid = tid & (kProducers - 1);
+      cplx<float>* ring = reinterpret_cast<cplx<float>*>(smraw + (size_t)nst * stage_bytes) +
+                          (size_t)gp * D * Spec::kRingVals * kProducers;
       auto slot = [&](int i) { return ring + (size_t)i * Spec::kRingVals * kProducers; };
-      if (blockIdx.x < ntiles && nks > 0) {
-        int64_t lt = blockIdx.x, st_tile = blockIdx.x;  // tiles of the next step to stage / to store
-        int lks = 0, sks = 0;
+      auto advance = [&](int64_t& tile, int& ks, int by) {  // (tile, step) of the step `by` (<= G) later
+        ks += by;
+        if (ks >= nks) {
+          ks -= nks;
+          tile += gridDim.x;
+          if (ks >= nks) {  // nks < G: one step per tile
+            ks -= nks;
+            tile += gridDim.x;
+          }
+        }
+      };
+      int64_t lt = blockIdx.x, st_tile = blockIdx.x;  // tiles of the next step to stage / to store
+      int lks = 0, sks = 0;
+      if (nks > 0) {
+        advance(lt, lks, gp);
+        advance(st_tile, sks, gp);
+      }
+      if (st_tile < ntiles && nks > 0) {
         TileK ltk = tile_k(g, lt, tid & 63, kx0, w), stk = ltk;
         // one cp.async group per step (an empty one past the last step), so that waiting for all
         // but the D - 1 newest groups completes the current step's
         auto stage_next = [&](int i) {
           if (lt < ntiles) Spec::load_async(g, a, lks, ltk, slot(i));
           cp_commit();
-          if (++lks == nks) {
-            lks = 0;
-            lt += gridDim.x;
-            if (lt < ntiles) ltk = tile_k(g, lt, tid & 63, kx0, w);
-          }
+          const int64_t t0 = lt;
+          advance(lt, lks, G);
+          if (lt != t0 && lt < ntiles) ltk = tile_k(g, lt, tid & 63, kx0, w);
         };
         for (int i = 0; i < D - 1; ++i) stage_next(i);
-        int s = 0, rs = 0, ws = D - 1;  // operand stage; ring slots to read / to fill
+        int s = gp, rs = 0, ws = D - 1;  // operand stage (G <= nst); ring slots to read / to fill
         unsigned ph = 0;
         for (;;) {
+          // the loads D - 1 own steps ahead go out first (their ring slot was read in the previous
+          // step), before the wait for a free operand stage
+          stage_next(ws);
+          ws = ws + 1 == D ? 0 : ws + 1;
           // warp-uniform decisions: the warp's lanes arrive once, together (see below)
           if (!__all_sync(0xffffffffu, mbar_wait(&sh.empty[s], ph ^ 1, stop))) { fail(); break; }
           unsigned char* st = smraw + (size_t)s * stage_bytes;
-          if (tid == 0) {
+          if (gtid == 0) {
             mbar_arrive_tx(&sh.full[s], bbytes);
             bulk_copy(st + 2 * Spec::NQ * kATile, bimg + (size_t)sks * bbytes, bbytes, &sh.full[s]);
           }
-          stage_next(ws);
-          ws = ws + 1 == D ? 0 : ws + 1;
           asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 1) : "memory");
           typename Spec::Raw cur;
           Spec::from_ring(slot(rs), cur);
@@ -739,13 +771,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) cheb_tc_kernel(Geometry g, type
           proxy_fence();
           __syncwarp();  // the warp's stores, each fenced by its thread, before its one arrival
           if (lane == 0) mbar_arrive(&sh.full[s]);
-          if (++s == nst) {
-            s = 0;
+          s += G;
+          if (s >= nst) {
+            s -= nst;
             ph ^= 1u;
           }
-          if (++sks == nks) {
-            sks = 0;
-            st_tile += gridDim.x;
+          const int64_t t0 = st_tile;
+          advance(st_tile, sks, G);
+          if (st_tile != t0) {
             if (__any_sync(0xffffffffu, st_tile >= ntiles || *stop)) break;
             stk = tile_k(g, st_tile, tid & 63, kx0, w);
           }
@@ -866,7 +899,7 @@ template <typename Spec>
 size_t tc_smem(const Geometry& g) {
   // as many operand stages as fit (at most kStages); 0 when fewer than two fit
   const size_t sb = Spec::stage_bytes((g.nz + 15) / 16 * 16);
-  const size_t ring = (size_t)Spec::kRingDepth * Spec::kRingVals * kProducers * 8;
+  const size_t ring = (size_t)Spec::kGroups * Spec::kRingDepth * Spec::kRingVals * kProducers * 8;
   const size_t n = std::min<size_t>(kStages, (kTcSmemCap - 1024 - ring) / sb);
   return n >= 2 ? n * sb + ring + 1024 : 0;
 }
@@ -878,7 +911,7 @@ void launch_tc(const Plan& p, const typename Spec::Args& a, unsigned char* img, 
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, p.cheb_tc_grid));
   for (int part = 0; part < nparts; ++part) {
     tc_bimage_kernel<Spec><<<64, 256, 0, s>>>(p.g, a, p.zrange, img, part, nparts);
-    cheb_tc_kernel<Spec><<<blocks, kTcThreads, tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status,
+    cheb_tc_kernel<Spec><<<blocks, tc_threads<Spec>(), tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status,
                                                                         inject, part, nparts);
   }
 }

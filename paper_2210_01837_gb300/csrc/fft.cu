@@ -816,8 +816,94 @@ __global__ void DPS_REG_FFT_BOUNDS row_r2c_reg_kernel(Geometry g, FftPlan fp, co
   }
 }
 
-// Row pass, inverse, register-staged: z_k = X0_k + i X1_k over the Hermitian extension, one FFT.
+// The first stage of the inverse row transform (radix R even, n / R a multiple of 32) reading each
+// half-spectrum value once.  Butterfly jj reads z_e, e = jj + (n / R) r, with z_e = X0_e + i X1_e
+// for e <= n / 2 and conj X0_{n-e} + i conj X1_{n-e} beyond; n - e is input R - 1 - r of
+// butterfly n / R - jj.  With the lane pairing of r2c_last_split (partners in lanes l and l ^ 16,
+// butterflies 0 and n / (2 R) their own partners), a lane reads its inputs below n / 2 (r < R / 2),
+// forms z_e and z_{n-e}, and hands z_{n-e} to its partner by a shuffle.  The stage then writes the
+// shared buffer after a block barrier, as reg_stage does.
+template <typename T, int R>
+__device__ __forceinline__ void c2r_first_pair(cplx<T>* buf, const FftPlan& fp, const cplx<T>* c0,
+                                               const cplx<T>* c1, bool has1) {
+  static_assert(R % 2 == 0, "the pairing needs an even radix");
+  const int nr = fp.n / R, t = threadIdx.x;
+  const bool act = t < nr;  // whole warps
+  cplx<T> v[R];  // initialised: an array left undefined on the idle threads' path is not kept in registers
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = mk<T>((T)0, (T)0);
+  int jj = 0;
+  if (act) {
+    const int lane = t & 31, x = 16 * (t >> 5) + (lane & 15);
+    jj = lane < 16 ? x : (x == 0 ? nr / 2 : nr - x);
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) {
+      const int k = jj + nr * r;  // below n / 2
+      const cplx<T> x0 = c0[k];
+      const cplx<T> x1 = has1 ? c1[k] : mk<T>((T)0, (T)0);
+      v[r] = x0 + mul_i(x1);
+      v[R - 1 - r] = conjg(x0) + mul_i(conjg(x1));  // z_{n-k}, the partner's input R - 1 - r
+    }
+#pragma unroll
+    for (int r = R / 2; r < R; ++r) {  // exchange the upper halves with the partner lane
+      v[r].x = __shfl_xor_sync(0xffffffffu, v[r].x, 16);
+      v[r].y = __shfl_xor_sync(0xffffffffu, v[r].y, 16);
+    }
+    if (jj == 0 || 2 * jj == nr) {  // their own partners (two lanes of the first warp): direct reads
+#pragma unroll
+      for (int r = R / 2; r < R; ++r) {
+        const int e = jj + nr * r;  // at least n / 2
+        const int k = e == fp.n / 2 ? e : fp.n - e;
+        const cplx<T> x0 = c0[k];
+        const cplx<T> x1 = has1 ? c1[k] : mk<T>((T)0, (T)0);
+        v[r] = e == fp.n / 2 ? x0 + mul_i(x1) : conjg(x0) + mul_i(conjg(x1));
+      }
+    }
+    Dft<T, R, +1>::run(v);
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad16(jj * R + r)] = v[r];
+  }
+}
+
 template <typename T>
+__device__ __forceinline__ void c2r_first_pair_any(cplx<T>* buf, const FftPlan& fp, const cplx<T>* c0,
+                                                   const cplx<T>* c1, bool has1) {
+  switch (fp.radix[0]) {
+    case 16: c2r_first_pair<T, 16>(buf, fp, c0, c1, has1); break;
+    case 12: c2r_first_pair<T, 12>(buf, fp, c0, c1, has1); break;
+    case 8: c2r_first_pair<T, 8>(buf, fp, c0, c1, has1); break;
+    case 4: c2r_first_pair<T, 4>(buf, fp, c0, c1, has1); break;
+    default: c2r_first_pair<T, 2>(buf, fp, c0, c1, has1); break;
+  }
+}
+
+// whether a row factorisation takes the paired first stage (c2r_first_pair)
+bool c2r_pair_ok(const FftPlan& fp) {
+  if (fp.nstages < 2) return false;
+  const int R = fp.radix[0];
+  return R % 2 == 0 && R <= 16 && (fp.n / R) % 32 == 0;
+}
+
+// Stages 1 .. S - 1 of a register-staged transform from the shared buffer (after the first stage
+// and a block barrier), the last writing through dst.
+template <typename T, int DIR, class Dst>
+__device__ __forceinline__ void reg_fft_tail(cplx<T>* buf, const FftPlan& fp, const cplx<T>* tw, const Dst& gdst) {
+  const ShBuf<T, 1> sb{buf, 0};
+  int Ns = fp.radix[0];
+  for (int s = 1; s < fp.nstages - 1; ++s) {
+    reg_stage_any<T, DIR, false>(fp, s, Ns, 0, tw, sb, sb, true);
+    __syncthreads();
+    Ns *= fp.radix[s];
+  }
+  reg_stage_any<T, DIR, false>(fp, fp.nstages - 1, Ns, 0, tw, sb, gdst, false);
+}
+
+// Row pass, inverse, register-staged: z_k = X0_k + i X1_k over the Hermitian extension, one FFT
+// (PAIR: the first stage reads each half-spectrum value once, c2r_first_pair).
+template <typename T, bool PAIR>
 __global__ void DPS_REG_FFT_BOUNDS row_c2r_reg_kernel(Geometry g, FftPlan fp, const cplx<T>* __restrict__ tw,
                                                       T* __restrict__ grid, const int* __restrict__ zrange) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -833,6 +919,15 @@ __global__ void DPS_REG_FFT_BOUNDS row_c2r_reg_kernel(Geometry g, FftPlan fp, co
     T* row1 = row0 + rowlen;
     const cplx<T>* c0 = reinterpret_cast<const cplx<T>*>(row0);
     const cplx<T>* c1 = reinterpret_cast<const cplx<T>*>(row1);
+    if (PAIR) {
+      c2r_first_pair_any<T>(buf, fp, c0, c1, has1);
+      __syncthreads();
+      reg_fft_tail<T, +1>(buf, fp, tw, [&](int a, int, cplx<T> v) {
+        row0[a] = v.x;
+        if (has1) row1[a] = v.y;
+      });
+      continue;
+    }
     reg_fft<T, +1, false, false>(
         buf, fp, 0, tw,
         [&](int e, int) {
@@ -1215,7 +1310,8 @@ int fft_set_row_variant(Plan& p, int reg) {
     p.fft_reg[0] = 1;
     p.fft_grid[0] = r2c_split_ok(p.fxr) ? resident_grid(row_r2c_reg_kernel<T, true>, th, sm, p.device)
                                          : resident_grid(row_r2c_reg_kernel<T, false>, th, sm, p.device);
-    p.fft_grid[1] = resident_grid(row_c2r_reg_kernel<T>, th, sm, p.device);
+    p.fft_grid[1] = c2r_pair_ok(p.fxr) ? resident_grid(row_c2r_reg_kernel<T, true>, th, sm, p.device)
+                                        : resident_grid(row_c2r_reg_kernel<T, false>, th, sm, p.device);
     return 1;
   }
   const size_t r2c = row_r2c_smem<T>(p.g), c2r = row_c2r_smem<T>(p.g);
@@ -1251,7 +1347,8 @@ template <typename T>
 int fft_smem_ok(Plan& p) {
   if (!allow_smem(row_r2c_kernel<T>) || !allow_smem(row_c2r_kernel<T>) || !allow_smem(col_kernel<T, -1>) ||
       !allow_smem(col_kernel<T, +1>) || !allow_smem(row_r2c_reg_kernel<T, false>) ||
-      !allow_smem(row_r2c_reg_kernel<T, true>) || !allow_smem(row_c2r_reg_kernel<T>) ||
+      !allow_smem(row_r2c_reg_kernel<T, true>) || !allow_smem(row_c2r_reg_kernel<T, false>) ||
+      !allow_smem(row_c2r_reg_kernel<T, true>) ||
       !allow_smem(col_reg_kernel<T, -1>) || !allow_smem(col_reg_kernel<T, +1>) ||
       !allow_smem(col_pipe_kernel<T, -1>) || !allow_smem(col_pipe_kernel<T, +1>) ||
       !allow_smem(col_tma_kernel<T, -1>) || !allow_smem(col_tma_kernel<T, +1>))
@@ -1284,8 +1381,10 @@ void launch_fft_rows(const Plan& p, int dir, cudaStream_t s) {
       row_r2c_reg_kernel<T, true><<<p.fft_grid[0], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
     else if (dir < 0)
       row_r2c_reg_kernel<T, false><<<p.fft_grid[0], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
+    else if (c2r_pair_ok(p.fxr))
+      row_c2r_reg_kernel<T, true><<<p.fft_grid[1], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
     else
-      row_c2r_reg_kernel<T><<<p.fft_grid[1], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
+      row_c2r_reg_kernel<T, false><<<p.fft_grid[1], th, sm, s>>>(g, p.fxr, twx, grid, p.zrange);
     return;
   }
   const int th = fft_threads(g.nx);
