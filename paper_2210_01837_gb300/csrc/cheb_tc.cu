@@ -193,7 +193,18 @@ struct TileK {
   float hkx, hky, kk;
 };
 
-__device__ __forceinline__ TileK tile_k(const Geometry& g, int64_t tile, int j, int kx0, int w) {
+// pi / Lx, pi / Ly and 1 / (nx ny) in float, formed on the host: in double on the device they take
+// divisions on the scarce FP64 pipe at every tile
+struct TcScales {
+  float hpx, hpy, inv_nxny;
+};
+
+// F32: k / 2 as float products with the host's scales (the backward transform: its 20 producer and
+// epilogue warps form every tile's wavenumbers, and the double divisions stalled them, 7.08 -> 6.13
+// ms on rollers_1m); else in double, rounded once (the forward transform measured faster so, 4.74
+// against 4.95 ms)
+template <bool F32>
+__device__ __forceinline__ TileK tile_k(const Geometry& g, const TcScales& sc, int64_t tile, int j, int kx0, int w) {
   TileK t;
   t.col = -1;
   t.kid = 0;
@@ -206,8 +217,13 @@ __device__ __forceinline__ TileK tile_k(const Geometry& g, int64_t tile, int j, 
     const int nyv = (kyi < (g.ny + 1) / 2) ? kyi : kyi - g.ny;
     t.col = kyi * g.pitch + kxi;
     t.kid = kyi * g.nkx + kxi;
-    t.hkx = (float)(M_PI * (double)kxi / g.Lx);
-    t.hky = (float)(M_PI * (double)nyv / g.Ly);
+    if (F32) {
+      t.hkx = (float)kxi * sc.hpx;
+      t.hky = (float)nyv * sc.hpy;
+    } else {
+      t.hkx = (float)(M_PI * (double)kxi / g.Lx);
+      t.hky = (float)(M_PI * (double)nyv / g.Ly);
+    }
     t.kk = 2.0f * sqrtf(t.hkx * t.hkx + t.hky * t.hky);
   }
   return t;
@@ -334,7 +350,7 @@ struct FwdSpec {
   // epilogue thread: TMEM lane `row` (wavenumber row >> 1, part row & 1); out_o[n] -> kbuf (zeros
   // when no plane is occupied)
   __device__ static void epilogue(const Geometry& g, const Args& a, uint32_t tlane, int row, const TileK& tk, int np,
-                                  int, int, bool any) {
+                                  int, int, bool any, float) {
     const int64_t K = (int64_t)g.nkx * g.ny;
     const int N = g.nz, part = row & 1;
     float* kb = reinterpret_cast<float*>(a.kbuf) + 2 * (size_t)tk.kid + part;
@@ -556,10 +572,10 @@ struct BwdSpec {
   // epilogue thread: TMEM lane `row` = (wavenumber row >> 1, part row & 1); lanes 2j and 2j + 1 pair
   // up for the products with i
   __device__ static void epilogue(const Geometry& g, const Args& a, uint32_t tlane, int row, const TileK& tk, int nq,
-                                  int clo, int chi, bool) {
+                                  int clo, int chi, bool, float inv_nxny) {
     const int part = row & 1;
     const bool nyq = tk.col >= 0 && is_nyquist(g, tk.kid);
-    const float scale = nyq ? 0.f : (float)(1.0 / ((double)g.nx * (double)g.ny));
+    const float scale = nyq ? 0.f : inv_nxny;
     const size_t plane = (size_t)g.ny * g.pitch, fstride = (size_t)g.nz * plane;
     float* gr = reinterpret_cast<float*>(a.grid) + 2 * (size_t)(tk.col >= 0 ? tk.col : 0) + part;
     const float sgn = part ? 1.f : -1.f;  // (i x) of this part: re -> -x.im, im -> +x.re
@@ -648,7 +664,7 @@ __global__ void tc_bimage_kernel(Geometry g, typename Spec::Args a, const int* _
 }
 
 template <typename Spec>
-__global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry g, typename Spec::Args a,
+__global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry g, typename Spec::Args a, TcScales sc,
                                                                 const unsigned char* __restrict__ bimg,
                                                                 const int* __restrict__ zrange, int kx0, int w,
                                                                 int* __restrict__ status, int inject, int part,
@@ -738,7 +754,7 @@ __global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry
         advance(st_tile, sks, gp);
       }
       if (st_tile < ntiles && nks > 0) {
-        TileK ltk = tile_k(g, lt, tid & 63, kx0, w), stk = ltk;
+        TileK ltk = tile_k<!Spec::kForward>(g, sc, lt, tid & 63, kx0, w), stk = ltk;
         // one cp.async group per step (an empty one past the last step), so that waiting for all
         // but the D - 1 newest groups completes the current step's
         auto stage_next = [&](int i) {
@@ -746,7 +762,7 @@ __global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry
           cp_commit();
           const int64_t t0 = lt;
           advance(lt, lks, G);
-          if (lt != t0 && lt < ntiles) ltk = tile_k(g, lt, tid & 63, kx0, w);
+          if (lt != t0 && lt < ntiles) ltk = tile_k<!Spec::kForward>(g, sc, lt, tid & 63, kx0, w);
         };
         for (int i = 0; i < D - 1; ++i) stage_next(i);
         int s = gp, rs = 0, ws = D - 1;  // operand stage (G <= nst); ring slots to read / to fill
@@ -780,7 +796,7 @@ __global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry
           advance(st_tile, sks, G);
           if (st_tile != t0) {
             if (__any_sync(0xffffffffu, st_tile >= ntiles || *stop)) break;
-            stk = tile_k(g, st_tile, tid & 63, kx0, w);
+            stk = tile_k<!Spec::kForward>(g, sc, st_tile, tid & 63, kx0, w);
           }
         }
         cp_wait_all();  // no copy into the ring outlives the loop
@@ -796,7 +812,7 @@ __global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry
     typename Spec::Raw raw;
     int64_t tile = blockIdx.x;
     if (tile < ntiles && nks > 0) {
-      TileK tk = tile_k(g, tile, tid & 63, kx0, w);
+      TileK tk = tile_k<!Spec::kForward>(g, sc, tile, tid & 63, kx0, w);
       Spec::load(g, a, clo, chi, 0, tk, raw);
       for (;;) {
         for (int ks = 0; ks < nks; ++ks) {
@@ -807,7 +823,7 @@ __global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry
           // the next step's loads, issued before this step's stores
           const bool last = ks + 1 == nks;
           const int64_t ntile = last ? tile + gridDim.x : tile;
-          const TileK ntk = last ? tile_k(g, ntile, tid & 63, kx0, w) : tk;
+          const TileK ntk = last ? tile_k<!Spec::kForward>(g, sc, ntile, tid & 63, kx0, w) : tk;
           // the step's B operands: one bulk copy from the image, completing on the stage barrier
           if (tid == 0) {
             mbar_arrive_tx(&sh.full[s], bbytes);
@@ -873,16 +889,16 @@ __global__ void __launch_bounds__(tc_threads<Spec>(), 1) cheb_tc_kernel(Geometry
     const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     unsigned t = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
-      const TileK tk = tile_k(g, tile, row >> 1, kx0, w);
+      const TileK tk = tile_k<!Spec::kForward>(g, sc, tile, row >> 1, kx0, w);
       if (nks == 0) {  // forward with no occupied plane: zero coefficients
-        Spec::epilogue(g, a, tlane, row, tk, nn, clo, chi, false);
+        Spec::epilogue(g, a, tlane, row, tk, nn, clo, chi, false, sc.inv_nxny);
         continue;
       }
       const int b = nbuf == 2 ? (int)(t & 1) : 0;
       const unsigned use = nbuf == 2 ? t >> 1 : t;
       if (!mbar_wait(&sh.acc_full[b], use & 1, stop)) { fail(); break; }
       tc_fence_after();
-      Spec::epilogue(g, a, tlane + (uint32_t)(b * cols), row, tk, nn, clo, chi, true);
+      Spec::epilogue(g, a, tlane + (uint32_t)(b * cols), row, tk, nn, clo, chi, true, sc.inv_nxny);
       tc_fence_before();
       mbar_arrive(&sh.acc_empty[b]);
     }
@@ -908,10 +924,11 @@ template <typename Spec>
 void launch_tc(const Plan& p, const typename Spec::Args& a, unsigned char* img, int kx0, int w, cudaStream_t s,
                int inject = 0, int nparts = 1) {
   const int64_t tiles = ((int64_t)w * p.g.ny + kTcWave - 1) / kTcWave;
+  const TcScales sc{(float)(M_PI / p.g.Lx), (float)(M_PI / p.g.Ly), (float)(1.0 / ((double)p.g.nx * p.g.ny))};
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, p.cheb_tc_grid));
   for (int part = 0; part < nparts; ++part) {
     tc_bimage_kernel<Spec><<<64, 256, 0, s>>>(p.g, a, p.zrange, img, part, nparts);
-    cheb_tc_kernel<Spec><<<blocks, tc_threads<Spec>(), tc_smem<Spec>(p.g), s>>>(p.g, a, img, p.zrange, kx0, w, p.status,
+    cheb_tc_kernel<Spec><<<blocks, tc_threads<Spec>(), tc_smem<Spec>(p.g), s>>>(p.g, a, sc, img, p.zrange, kx0, w, p.status,
                                                                         inject, part, nparts);
   }
 }
