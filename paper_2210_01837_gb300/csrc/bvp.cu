@@ -156,6 +156,24 @@ __device__ __forceinline__ KInfo kinfo(const Geometry& g, int64_t kidx) {
   return r;
 }
 
+// kinfo with the host's 2 pi / Lx and 2 pi / Ly, and 1 / |k| from one reciprocal square root (|k|
+// as its product with |k|^2): no division on the FP64 pipe, which bounds the table solve
+__device__ __forceinline__ KInfo kinfo_fast(const Geometry& g, int64_t kidx, double tpx, double tpy, double& ik) {
+  KInfo r;
+  const unsigned ku = (unsigned)kidx;  // wavenumbers < 2^31
+  r.kyi = (int)(ku / (unsigned)g.nkx);
+  r.kxi = (int)(ku - (unsigned)r.kyi * (unsigned)g.nkx);
+  r.nyq = ((g.nx % 2 == 0) && r.kxi == g.nx / 2) || ((g.ny % 2 == 0) && r.kyi == g.ny / 2);
+  r.zero = (r.kxi == 0 && r.kyi == 0);
+  const int nyv = (r.kyi < (g.ny + 1) / 2) ? r.kyi : r.kyi - g.ny;
+  r.kx = tpx * (double)r.kxi;
+  r.ky = tpy * (double)nyv;
+  const double k2 = r.kx * r.kx + r.ky * r.ky;
+  ik = r.zero ? 0.0 : rsqrt(k2);
+  r.kk = k2 * ik;
+  return r;
+}
+
 // grid element (field f, plane c) of wavenumber column (kyi, kxi)
 __device__ __forceinline__ size_t gidx(const Geometry& g, int f, int c, int kyi, int kxi) {
   return (((size_t)f * g.nz + c) * g.ny + kyi) * g.pitch + kxi;
@@ -850,9 +868,11 @@ template <typename T, bool SLIP>
 __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restrict__ band, const T* __restrict__ bandT,
                                        const double* __restrict__ fac, int64_t KP, cplx<T>* __restrict__ kbuf,
                                        cplx<T>* __restrict__ kaux, cplx<T>* __restrict__ pws,
-                                       cplx<double>* __restrict__ sw, int slots, int slot, int64_t kidx, int64_t K) {
+                                       cplx<double>* __restrict__ sw, int slots, int slot, int64_t kidx, int64_t K,
+                                       double tpx, double tpy) {
   const int N = g.nz;
-  const KInfo ki = kinfo(g, kidx);
+  double ik;
+  const KInfo ki = kinfo_fast(g, kidx, tpx, tpy, ik);
   if (ki.nyq) return;
   if (ki.zero) {
     zero_mode<T, SLIP>(g, band, bandT, kbuf, kaux, sw, slots, slot, kidx, K);
@@ -961,7 +981,6 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
   }
 
   // ---- velocity: three right-hand sides sharing the factorisation -------------------------------
-  const double ik = 1.0 / kk;  // the one division per wavenumber
   const cplx<double> ik_top = scl(ptop, 0.5 * inv_eta * ik);
   const cplx<double> ik_bot = scl(pbot, 0.5 * inv_eta * ik);
   cplx<double> gt[3], gb[3];
@@ -1124,13 +1143,14 @@ __global__ void __launch_bounds__(kBvpThreads, 3) solve_tab_kernel(Geometry g, c
                                                                 const double* __restrict__ fac, int64_t KP,
                                                                 cplx<T>* __restrict__ kbuf, cplx<T>* __restrict__ kaux,
                                                                 cplx<T>* __restrict__ pws, cplx<double>* __restrict__ sw,
-                                                                int kx0, int w) {
+                                                                int kx0, int w, double tpx, double tpy) {
   const int64_t K = (int64_t)g.nkx * g.ny;
   const int64_t total = (int64_t)w * g.ny;
   const int slots = gridDim.x * blockDim.x;
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t i = slot; i < total; i += slots)
-    solve_tab<T, SLIP>(g, band, bandT, fac, KP, kbuf, kaux, pws, sw, slots, slot, paired_kidx(g, i, kx0, w), K);
+    solve_tab<T, SLIP>(g, band, bandT, fac, KP, kbuf, kaux, pws, sw, slots, slot, paired_kidx(g, i, kx0, w), K, tpx,
+                       tpy);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1816,12 +1836,13 @@ void launch_bvp(const Plan& p, int part, int kx0, int w, cudaStream_t s) {
     double* fr = reinterpret_cast<double*>(base + 3 * N * slots * sizeof(cplx<double>));
     cplx<T>* pws = reinterpret_cast<cplx<T>*>(base + 3 * N * slots * (sizeof(cplx<double>) + sizeof(double)));
     const T* bandT = reinterpret_cast<const T*>(p.kt.bandT);
+    const double tpx = 2.0 * M_PI / g.Lx, tpy = 2.0 * M_PI / g.Ly;  // host divisions
     if (p.kt.fac && g.slip)
       solve_tab_kernel<T, true><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, bandT, p.kt.fac, p.kt.KP, kbuf, kaux,
-                                                                    pws, sw, kx0, w);
+                                                                    pws, sw, kx0, w, tpx, tpy);
     else if (p.kt.fac)
       solve_tab_kernel<T, false><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, bandT, p.kt.fac, p.kt.KP, kbuf,
-                                                                     kaux, pws, sw, kx0, w);
+                                                                     kaux, pws, sw, kx0, w, tpx, tpy);
     else if (g.slip)
       solve_kernel<T, true><<<p.bvp_blocks, kBvpThreads, 0, s>>>(g, p.tab.band, reinterpret_cast<const T*>(p.kt.bandT),
                                                                  kbuf, kaux, pws, sw, fr, kx0, w);
