@@ -934,8 +934,11 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
         const double U = vc, Dp = FAC(n, 1), idet = rc;
         const double beta_a = (par == 0) ? kk : (sH + kk);
         const cplx<double> rhs = wid(rt) - scl(s_next, U);
-        const cplx<double> c0 = scl(scl(rhs, beta_a) + scl(gacc, kap), idet);
-        const cplx<double> a = scl(scl(gacc, Dp) - scl(rhs, bc), idet);
+        // c0 = (beta_a rhs + kappa g) / det, a = (D' g - b rhs) / det, the 1/det folded into the
+        // per-wavenumber constants
+        const double cb = beta_a * idet, ck = kap * idet, cd = Dp * idet, cc = bc * idet;
+        const cplx<double> c0 = scl(rhs, cb) + scl(gacc, ck);
+        const cplx<double> a = scl(gacc, cd) - scl(rhs, cc);
         // ascending substitution; y = B B c + a in the transform precision
         cplx<double> cm = c0;
         cplx<T> tcm2 = zT, tcm = nar<T>(c0);
@@ -967,9 +970,8 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
           sc = sn;
           tc = tn;
         }
-        const double sgn = par ? -1.0 : 1.0;
         ptop = ptop + sp + a;
-        pbot = pbot + scl(sp + a, sgn);
+        pbot = par ? pbot - (sp + a) : pbot + (sp + a);  // T_n(-1) = (-1)^n
       }
       fc = fn;
       gc = gn;
@@ -981,15 +983,17 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
   }
 
   // ---- velocity: three right-hand sides sharing the factorisation -------------------------------
-  const cplx<double> ik_top = scl(ptop, 0.5 * inv_eta * ik);
-  const cplx<double> ik_bot = scl(pbot, 0.5 * inv_eta * ik);
+  // the boundary data halved here (the parity split below takes half their sum or difference)
+  const double qe = 0.25 * inv_eta, qk = qe * ik;
+  const cplx<double> ik_top = scl(ptop, qk);
+  const cplx<double> ik_bot = scl(pbot, qk);
   cplx<double> gt[3], gb[3];
   gt[0] = scl(mul_i(ik_top), -kx);
   gb[0] = scl(mul_i(ik_bot), kx);
   gt[1] = scl(mul_i(ik_top), -ky);
   gb[1] = scl(mul_i(ik_bot), ky);
-  gt[2] = scl(ptop, 0.5 * inv_eta);
-  gb[2] = scl(pbot, 0.5 * inv_eta);
+  gt[2] = scl(ptop, qe);
+  gb[2] = scl(pbot, qe);
   cplx<double> vtop[3], vbot[3];
   cplx<double> dtop[2], dbot[2];  // SLIP: y_s(+-1) of the tangential DP velocities
 #pragma unroll
@@ -1002,7 +1006,7 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       s_next[f] = mk<double>(0, 0);
-      gacc[f] = par ? scl(gt[f] + gb[f], 0.5) : scl(gt[f] - gb[f], 0.5);
+      gacc[f] = par ? gt[f] + gb[f] : gt[f] - gb[f];
     }
     cplx<T> dp_next = zT;
     cplx<T> pc1 = (nlast + 1 < N) ? PW(nlast + 1) : zT, pc0 = PW(nlast);
@@ -1040,15 +1044,15 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
       } else {
         const double U = vc, Dp = FAC(n, 1), idet = rc;
         const double beta_a = (par == 0) ? kk : (sH + kk);
-        const double sgn = par ? -1.0 : 1.0;
+        const double cb = beta_a * idet, ck = kap * idet, cd = Dp * idet, cc = bc * idet;  // 1/det folded in
         cplx<double> cm[3];
         cplx<T> tcm2[3], tcm[3];
         cplx<double> sp[3], sd[2];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
           const cplx<double> rhs = wid(rt[f]) - scl(s_next[f], U);
-          const cplx<double> c0 = scl(scl(rhs, beta_a) + scl(gacc[f], kap), idet);
-          const cplx<double> a = scl(scl(gacc[f], Dp) - scl(rhs, bc), idet);
+          const cplx<double> c0 = scl(rhs, cb) + scl(gacc[f], ck);
+          const cplx<double> a = scl(gacc[f], cd) - scl(rhs, cc);
           cm[f] = c0;
           tcm[f] = nar<T>(c0);
           tcm2[f] = zT;
@@ -1061,7 +1065,7 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
             }
           }
           vtop[f] = vtop[f] + a;
-          vbot[f] = vbot[f] + scl(a, sgn);
+          vbot[f] = par ? vbot[f] - a : vbot[f] + a;  // T_n(-1) = (-1)^n
           gacc[f] = a;  // reuse: a_par of this field
         }
         // ascending substitution for the three fields together
@@ -1103,13 +1107,13 @@ __device__ __noinline__ void solve_tab(const Geometry& g, const double* __restri
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
           vtop[f] = vtop[f] + sp[f];
-          vbot[f] = vbot[f] + scl(sp[f], sgn);
+          vbot[f] = par ? vbot[f] - sp[f] : vbot[f] + sp[f];
         }
         if (SLIP) {  // T_n'(-1) = (-1)^(n+1) n^2: the even part enters y_s(-1) negated
 #pragma unroll
           for (int f = 0; f < 2; ++f) {
             dtop[f] = dtop[f] + sd[f];
-            dbot[f] = dbot[f] + scl(sd[f], -sgn);
+            dbot[f] = par ? dbot[f] + sd[f] : dbot[f] - sd[f];
           }
         }
       }
