@@ -166,8 +166,8 @@ def cpu_oracle_tile(div, seed_offset=3):
 
 
 def cpu_oracle_config(name, div=1, seed=0):
-    """One oracle product of configuration `name` ("bw_small": whole; "slit_16k": a 1/div^2-area
-    tile with the same density, heights and h; "batch": system `seed` of the configuration-4
+    """One oracle product of workload `name` ("bw_small": whole; "slit_16k": a 1/div^2-area
+    tile with the same density, heights and h; "batch": system `seed` of the 256-system uneven
     population, whole); returns seconds."""
     from oracle import Params, mobility
     from paper_2210_01837_gb300.workloads import batch_systems, bw_small, slit_16k
@@ -200,19 +200,19 @@ def _oracle_config_runs(name, div, procs, threads, seeds=None):
 
 
 def oracle_configs():
-    """The oracle on configurations 1 and 2 on the host's cores: configuration 1 whole (one process
-    with every core's BLAS threads, and one process on one core); configuration 2 as one 1/16-area
-    tile per core, all at once, and one tile on one core (times x 16: work is linear in N and in
-    grid nodes)."""
+    """The oracle on the small workloads on the host's cores: the 100-sphere wall case (128^2 x 65)
+    whole (one process with every core's BLAS threads, and one process on one core); the 16k-sphere
+    slit (384^2 x 97) as one 1/16-area tile per core, all at once, and one tile on one core (times x
+    16: work is linear in N and in grid nodes); and a sample of the 256-system uneven batch."""
     cores = host_cores()
     c1_all, _ = _oracle_config_runs("bw_small", 1, 1, cores)
     c1_one, _ = _oracle_config_runs("bw_small", 1, 1, 1)
     div = 4
     wall, per = _oracle_config_runs("slit_16k", div, cores, 1)
     t1, _ = _oracle_config_runs("slit_16k", div, 1, 1)
-    # configuration 4: every 8th of the 128 smallest systems (the whole population would take hours
-    # of oracle time), one per core at once; the batch's time extrapolated by nx ny nz^3 (the
-    # oracle's dense LU per wavenumber dominates: configurations 1 and 2 scale so within 15 %)
+    # the 256-system batch: every 8th of the 128 smallest systems (the whole population would take
+    # hours of oracle time), one per core at once; the batch's time extrapolated by nx ny nz^3 (the
+    # oracle's dense LU per wavenumber dominates: the two small workloads scale so within 15 %)
     from paper_2210_01837_gb300.workloads import batch_systems
     pop = batch_systems(count=256)
     nodes = [p_["nx"] * p_["ny"] * float(p_["nz"]) ** 3 for p_, _, _, _ in pop]
@@ -578,13 +578,13 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=256, help="systems in the batched leg (0: skip batched and served legs)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="duration of each served leg (0: skip serving); the configuration asks for 60")
+                    help="duration of each served leg (0: skip serving); the serving workload asks for 60")
     ap.add_argument("--serve-population", type=int, default=64, help="systems in the served population")
     ap.add_argument("--no-deriv", action="store_true", help="skip the kernel-derivative torque-route leg")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Brownian-increment (Lanczos) leg")
-    ap.add_argument("--no-configs", action="store_true", help="skip the other-configuration timings")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' timings")
     ap.add_argument("--oracle-configs", action="store_true",
-                    help="also time the oracle on configurations 1 and 2 on the host cores (minutes)")
+                    help="also time the oracle on the small workloads and a batch sample on the host cores (minutes)")
     args = ap.parse_args()
 
     from paper_2210_01837_gb300.replicas import Collective, rank_env, replica_seed_offset, whole_job_rate
@@ -809,7 +809,7 @@ def main():
         for name, rate in (("half_capacity", 0.5 * capacity), ("0.8_capacity", 0.8 * capacity),
                            ("specified_2000", 2000.0)):
             legs[name] = served_leg(binding, torch, population, rate=rate, duration=args.serve_seconds)
-        served = {"population": f"serving_systems: {len(population)} systems drawn from the configuration-4 size "
+        served = {"population": f"serving_systems: {len(population)} systems drawn from the uneven-batch size "
                                 f"distribution, wall mode cycling over free / bottom wall / slit, forces + torques, "
                                 f"mixed; requests drawn uniformly from them",
                   "capacity_req_per_s": capacity,
