@@ -31,6 +31,7 @@
 #include <algorithm>
 
 #include "dps_internal.cuh"
+#include "fft_pair.h"
 
 namespace dps {
 
@@ -736,8 +737,7 @@ __device__ __forceinline__ void r2c_last_split(const cplx<T>* buf, const FftPlan
   static_assert(R % 2 == 0, "the split pairs the outputs of an even radix");
   const int Ns = fp.n / R, t = threadIdx.x;
   if (t >= Ns) return;  // whole warps
-  const int lane = t & 31, x = 16 * (t >> 5) + (lane & 15);
-  const int jj = lane < 16 ? x : (x == 0 ? Ns / 2 : Ns - x);
+  const int jj = pair_butterfly(t, Ns);
   cplx<T> v[R];
   const int p0 = pad16(jj), sp = Ns + (Ns >> 4);  // Ns is a multiple of 16: the padding is linear in r
 #pragma unroll
@@ -834,8 +834,7 @@ __device__ __forceinline__ void c2r_first_pair(cplx<T>* buf, const FftPlan& fp, 
   for (int r = 0; r < R; ++r) v[r] = mk<T>((T)0, (T)0);
   int jj = 0;
   if (act) {
-    const int lane = t & 31, x = 16 * (t >> 5) + (lane & 15);
-    jj = lane < 16 ? x : (x == 0 ? nr / 2 : nr - x);
+    jj = pair_butterfly(t, nr);
 #pragma unroll
     for (int r = 0; r < R / 2; ++r) {
       const int k = jj + nr * r;  // below n / 2
@@ -849,7 +848,7 @@ __device__ __forceinline__ void c2r_first_pair(cplx<T>* buf, const FftPlan& fp, 
       v[r].x = __shfl_xor_sync(0xffffffffu, v[r].x, 16);
       v[r].y = __shfl_xor_sync(0xffffffffu, v[r].y, 16);
     }
-    if (jj == 0 || 2 * jj == nr) {  // their own partners (two lanes of the first warp): direct reads
+    if (pair_self(jj, nr)) {  // their own partners (two lanes of the first warp): direct reads
 #pragma unroll
       for (int r = R / 2; r < R; ++r) {
         const int e = jj + nr * r;  // at least n / 2
