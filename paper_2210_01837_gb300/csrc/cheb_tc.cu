@@ -55,12 +55,6 @@ constexpr int kTcRows = 128;   // MMA M: 64 wavenumbers x (re, im)
 constexpr int kTcK = 8;        // K step (8 tf32 = 32 bytes per operand row)
 constexpr int kTcWave = 64;    // wavenumbers per tile
 constexpr int kProducers = 256;  // producer threads of one group (8 warps)
-#ifndef DPS_TC_BWD_GROUPS
-#define DPS_TC_BWD_GROUPS 2
-#endif
-#ifndef DPS_TC_BWD_RING
-#define DPS_TC_BWD_RING 2
-#endif
 // warps of a transform: Spec::kGroups groups of 8 producer warps, then 4 epilogue warps and 1 MMA warp
 template <typename Spec> __host__ __device__ constexpr int tc_epi_warp0() { return 8 * Spec::kGroups; }
 template <typename Spec> __host__ __device__ constexpr int tc_mma_warp() { return 8 * Spec::kGroups + 4; }
@@ -406,8 +400,8 @@ struct BwdSpec {
   // two producer groups take alternate K steps; each stages its steps' values with cp.async
   // kRingDepth - 1 of its own steps ahead into its ring in shared memory (value e of group thread t
   // of a slot at slot[e * kProducers + t])
-  static constexpr int kGroups = DPS_TC_BWD_GROUPS;
-  static constexpr int kRingDepth = DPS_TC_BWD_RING;
+  static constexpr int kGroups = 2;
+  static constexpr int kRingDepth = 2;
   static constexpr int kRingVals = 8;
   __host__ __device__ static int ncoef(const Geometry& g) { return (g.nz + kTcK - 1) / kTcK; }
   __host__ __device__ static int nks(const Geometry& g, int, int) { return ncoef(g) * (CORR ? 2 : 1); }
