@@ -2,8 +2,9 @@
 precision: the forward transform, and the backward transform of the spectral-curl torque route)
 against the oracle and against the CUDA-core lane kernels they replace.
 
-Cases: every wall mode, forces only and with torques (six-field curl source), 17 to 113 Chebyshev
-nodes (accumulator widths 32 to 128 columns per output; beyond 96 nodes the backward transform's
+Cases: every wall mode, forces only and with torques (six-field curl source), 8 to 113 Chebyshev
+nodes (8 and 9 in free space: one and two backward K steps per tile, against the backward's two
+producer groups that take alternate steps) (accumulator widths 32 to 128 columns per output; beyond 96 nodes the backward transform's
 output planes go in two launches), ragged wavenumber tiles (fewer than 64 wavenumbers in the last
 tile), plane ranges that end inside a K step of 8 planes, a problem of a single tile, and a plane
 range narrow enough that the second backward launch has no planes.  Bars: 1e-5 relative L2 against the oracle (the mixed bar); 3e-6 against the lane
@@ -47,6 +48,8 @@ CASES = [
     ("slit", 72, 72, 33, False),
     ("bottom_wall", 8, 8, 17, True),     # a single 64-wavenumber tile (5 x 8 wavenumbers)
     ("slit", 40, 32, 113, True),         # backward in two launches of up to 64 planes
+    ("free", 40, 36, 8, True),           # one backward K step per tile: fewer than the two producer groups
+    ("free", 40, 36, 9, True),           # two backward K steps per tile, one per producer group
 ]
 
 
